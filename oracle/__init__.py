@@ -1,0 +1,26 @@
+"""Plain, slow, FP64 CPU oracle for the Lanczos/Sternheimer dielectric path.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product package imports, links or
+runs this code.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may use it.
+
+The oracle follows the paper's definitions with no blocking, fusion or
+reordering beyond what the definitions state, so that each step can be read
+against the paper:
+
+* ``pw``        plane-wave sphere, real-space grid, dense Hamiltonian and exact
+                diagonalisation (the DFT ground state is an *input* of the
+                method; exact diagonalisation stands in for it).
+* ``coulomb``   square root of the (spherically truncated) Coulomb kernel.
+* ``response``  chi0 by the Adler-Wiser sum over states (Eq. P), its
+                Sternheimer form (Eqs. P1, fvpm, P2a, P2), the squared Hermitian
+                form at imaginary frequency (Eq. P2+), and the symmetrised
+                dielectric operator (Eq. epsilon).
+* ``lanczos``   Lanczos recursion with full Gram-Schmidt re-orthogonalisation
+                (Sec. Lanczos, Eq. krylov) and the inverse in the Lanczos basis.
+* ``gradient``  derivative of <phi|eps^-1(0)|phi> with respect to V_loc (not in
+                the paper; derived by third-order perturbation theory and pinned
+                by central finite differences).
+
+Parity pins for every function live in ``tests/test_oracle_*.py``.
+"""

@@ -1,0 +1,225 @@
+"""Independent-particle response chi0(omega) and the symmetric dielectric
+operator eps~ = 1 - v^1/2 chi0 v^1/2.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Three routes to chi0 f for a grid field f (all give the same result up to
+rounding; the tests pin them against each other and against closed forms):
+
+1. ``chi0_eqP``: Eq. P literally,
+       P(w) = 2 sum_{c,v} |c* v> [1/(w - (e_c - e_v)) - 1/(w + (e_c - e_v))] <v c*|
+   with the grid functions psi_c*(r) psi_v(r) and the grid inner product.
+   The factor 2 is spin (non-spin-polarised, Sec. The G0W0 method).
+2. ``chi0_sos``: Eq. P1 with Eq. fvpm written in the plane-wave basis,
+       chi0 f = -2 sum_v psi_v (x_v^- + x_v^+),
+       x_v^(-/+) = sum_c psi_c <psi_c|psi_v* f> / (e_c - e_v -/+ w).
+   Equal to route 1 because H is real in real space, so the occupied and
+   conduction spaces are closed under complex conjugation (c -> c* relabels
+   the conduction sum).  This analytic form is also the one used at complex w.
+3. ``chi0_sternheimer``: Eq. P2, solving (H - e_v -/+ w) x_v^(-/+) = P_c psi_v* f
+   iteratively in the plane-wave sphere, projecting on the conduction space at
+   every step (Sec. Avoiding summations, the paragraph after the SQMR footnote).
+
+The symmetric operator is Eq. epsilon: eps~ x = x - v^1/2 chi0 v^1/2 x.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse.linalg
+
+from . import coulomb
+from .pw import h_apply
+
+
+# ---------------------------------------------------------------------------
+# Route 1: Eq. P, literal
+# ---------------------------------------------------------------------------
+def chi0_eqP(gs, f, omega, chunk=256):
+    """(P(omega) f)(r) by Eq. P with every conduction state of a dense
+    diagonalisation.  f: (N_g,) grid field (real or complex)."""
+    sph = gs.sph
+    if gs.C_all is None:
+        raise ValueError("Eq. P needs all eigenstates (dense ground state)")
+    vol = sph.omega_vol
+    wgt = vol / sph.ng
+    psi_all = sph.to_grid(gs.C_all) / np.sqrt(vol)       # psi_n(r)
+    nv = gs.n_occ
+    out = np.zeros(sph.ng, dtype=np.complex128)
+    for v in range(nv):
+        for a in range(nv, len(gs.eps_all), chunk):
+            cs = slice(a, min(a + chunk, len(gs.eps_all)))
+            pair = np.conj(psi_all[cs]) * psi_all[v][None, :]   # |c* v>
+            coeff = wgt * (np.conj(pair) @ f)                    # <v c*|f>
+            d = gs.eps_all[cs] - gs.eps_all[v]
+            w = 2.0 * (1.0 / (omega - d) - 1.0 / (omega + d))
+            out += (w * coeff) @ pair
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Route 2: Eqs. P1 + fvpm in the plane-wave basis (dense resolvent)
+# ---------------------------------------------------------------------------
+def chi0_sos(gs, f, omega):
+    sph = gs.sph
+    if gs.C_all is None:
+        raise ValueError("sum over states needs all eigenstates")
+    vol = sph.omega_vol
+    u = gs.u
+    Cc = gs.C_all[gs.n_occ:]                 # (ncond, npw)
+    ec = gs.eps_all[gs.n_occ:]
+    out = np.zeros(sph.ng, dtype=np.complex128)
+    for v in range(gs.n_occ):
+        g = sph.to_sphere(np.conj(u[v]) * f)         # <G|psi_v* f>
+        a = np.conj(Cc) @ g                          # <psi_c|psi_v* f>
+        d = ec - gs.eps[v]
+        xm = (a / (d - omega)) @ Cc                  # x_v^-
+        xp = (a / (d + omega)) @ Cc                  # x_v^+
+        out += u[v] * sph.to_grid(xm + xp)
+    return -2.0 / vol * out
+
+
+# ---------------------------------------------------------------------------
+# Route 3: Sternheimer equations (Eq. P2) solved iteratively
+# ---------------------------------------------------------------------------
+def project_c(gs, y):
+    """P_c y = y - sum_v c_v <c_v|y> in the sphere."""
+    return y - (np.conj(gs.C) @ y) @ gs.C
+
+
+def solve_cg(apply_A, b, tol=1e-14, maxiter=20000):
+    """Textbook conjugate gradients for a Hermitian positive definite A.
+    Returns (x, iterations, relative residual of the recursion)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = np.vdot(r, r).real
+    bb = rr
+    if bb == 0.0:
+        return x, 0, 0.0
+    it = 0
+    while np.sqrt(rr / bb) > tol and it < maxiter:
+        Ap = apply_A(p)
+        alpha = rr / np.vdot(p, Ap).real
+        x = x + alpha * p
+        r = r - alpha * Ap
+        rr_new = np.vdot(r, r).real
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    return x, it, np.sqrt(rr / bb)
+
+
+def solve_general(apply_A, b, tol=1e-13):
+    """Non-Hermitian-positive cases (indefinite or complex shift): GMRES
+    (library routine) on the same projected operator."""
+    n = b.shape[0]
+    A = scipy.sparse.linalg.LinearOperator((n, n), matvec=apply_A,
+                                           dtype=np.complex128)
+    x, info = scipy.sparse.linalg.gmres(A, b, rtol=tol, atol=0.0,
+                                        restart=min(n, 400), maxiter=200)
+    if info != 0:
+        raise RuntimeError(f"gmres did not converge ({info})")
+    return x
+
+
+def sternheimer_solve(gs, v, shift, b, tol=1e-14, gap=None):
+    """Solve (H - e_v + shift) x = b in the conduction space (Eq. P2 with
+    shift = -/+ omega), P_c applied at every iteration."""
+    sph, vloc = gs.sph, gs.vloc
+    e = gs.eps[v]
+
+    def A(p):
+        return project_c(gs, h_apply(sph, vloc, p) - (e - shift) * p)
+
+    hpd = (np.imag(shift) == 0.0) and (gap is not None) and (np.real(shift) > -gap)
+    if hpd:
+        x, _, _ = solve_cg(A, b, tol)
+    else:
+        x = solve_general(A, b, tol)
+    return project_c(gs, x)
+
+
+def chi0_sternheimer(gs, f, omega, tol=1e-14, gaps=None):
+    """chi0 f by Eq. P2: two Sternheimer solves per occupied state (one when
+    omega = 0, where x^- = x^+)."""
+    sph = gs.sph
+    vol = sph.omega_vol
+    u = gs.u
+    out = np.zeros(sph.ng, dtype=np.complex128)
+    for v in range(gs.n_occ):
+        b = project_c(gs, sph.to_sphere(np.conj(u[v]) * f))
+        gap = None if gaps is None else gaps[v]
+        xm = sternheimer_solve(gs, v, -omega, b, tol, gap)
+        if omega == 0:
+            xs = 2.0 * xm
+        else:
+            xs = xm + sternheimer_solve(gs, v, +omega, b, tol, gap)
+        out += u[v] * sph.to_grid(xs)
+    return -2.0 / vol * out
+
+
+def conduction_gaps(gs, lowest_conduction):
+    """Per occupied state v: e_c(lowest) - e_v (CG applies to (H - e_v - w) on
+    P_c while w < this gap)."""
+    return lowest_conduction - gs.eps
+
+
+# ---------------------------------------------------------------------------
+# Eq. P2+: squared Hermitian form at imaginary frequency
+# ---------------------------------------------------------------------------
+def f_sum_imag(gs, v, f, w_im, tol=1e-14):
+    """Solve ((H - e_v)^2 + w^2) y = 2 (H - e_v) P_c psi_v* f (Eq. P2+ with
+    omega = i w); the solution is x^- + x^+ at omega = i w (Eq. fv)."""
+    sph, vloc = gs.sph, gs.vloc
+    e = gs.eps[v]
+
+    def Hs(p):
+        return project_c(gs, h_apply(sph, vloc, p) - e * p)
+
+    b = project_c(gs, sph.to_sphere(np.conj(gs.u[v]) * f))
+    rhs = 2.0 * Hs(b)
+    y, _, _ = solve_cg(lambda p: Hs(Hs(p)) + (w_im * w_im) * p, rhs, tol)
+    return project_c(gs, y)
+
+
+# ---------------------------------------------------------------------------
+# Eq. epsilon: the symmetric dielectric operator
+# ---------------------------------------------------------------------------
+class Dielectric:
+    """eps~(omega) x = x - v^1/2 chi0(omega) v^1/2 x with a chosen chi0 route."""
+
+    def __init__(self, gs, omega=0.0, kind=coulomb.TRUNCATED, route="sos",
+                 tol=1e-14, gaps=None):
+        self.gs, self.omega, self.route, self.tol = gs, omega, route, tol
+        self.sqv = np.sqrt(coulomb.vcoul(gs.sph, kind))
+        self.gaps = gaps
+
+    def chi0(self, f):
+        if self.route == "eqP":
+            return chi0_eqP(self.gs, f, self.omega)
+        if self.route == "sos":
+            return chi0_sos(self.gs, f, self.omega)
+        if self.route == "sternheimer":
+            return chi0_sternheimer(self.gs, f, self.omega, self.tol, self.gaps)
+        raise ValueError(self.route)
+
+    def sqrtv(self, x):
+        return coulomb.sqrt_v_apply(self.gs.sph, self.sqv, x)
+
+    def apply(self, x, real=None):
+        y = self.sqrtv(x)
+        dn = self.chi0(y)
+        out = x - self.sqrtv(dn)
+        if real is None:
+            real = np.isrealobj(x) and np.imag(self.omega) == 0
+        return out.real if real else out
+
+    def dense(self):
+        """eps~ as an N_g x N_g matrix, one column per grid point (tiny cells)."""
+        ng = self.gs.sph.ng
+        E = np.empty((ng, ng), dtype=np.complex128)
+        for j in range(ng):
+            e = np.zeros(ng)
+            e[j] = 1.0
+            E[:, j] = self.apply(e, real=False)
+        return E
