@@ -1,0 +1,186 @@
+/*
+ * libgw: the data-parallel hot path of the Lanczos-basis dielectric matrix
+ * method for Sternheimer G0W0 (arXiv:1408.3036) on one NVIDIA GB300 (sm_103a).
+ *
+ * The library applies the independent-particle polarizability chi0(omega)
+ * (Eq. P, computed through the Sternheimer equations Eqs. P1, fvpm, P2) and the
+ * symmetric dielectric operator eps~(omega) = 1 - v^1/2 chi0(omega) v^1/2
+ * (Eq. epsilon and its footnote) to batches of grid fields, runs the Lanczos
+ * recursion with full Gram-Schmidt re-orthogonalisation that expresses eps~ in
+ * a small basis (Sec. Lanczos, Eq. krylov), inverts the tridiagonal Lanczos
+ * matrix (Sec. Lanczos, "inverted at a cost ~N^2"), and differentiates
+ * s = <phi|eps~^-1(0)|phi> with respect to the local potential (not in the
+ * paper; third-order perturbation theory).
+ *
+ * Units: Hartree atomic units.  Cell: cubic, edge L (bohr), volume Omega = L^3.
+ * Grid: N^3 points r = L (i0, i1, i2) / N, C order [i0][i1][i2], N_g = N^3.
+ * Plane waves: G = 2 pi n / L, n in FFT order; the basis is the sphere
+ * |G|^2/2 <= ecut, ordered by ascending linear grid index of n mod N (see
+ * gw_sphere).  A wavefunction with sphere coefficients c is
+ * psi(r) = Omega^-1/2 sum_G c_G exp(i G r).  Grid inner product:
+ * <f|g> = (Omega / N_g) sum_r conj(f) g.
+ *
+ * Ownership: the caller owns every buffer it passes; the library copies what
+ * it keeps.  The library owns the context and its device workspaces.
+ * Pointers: `device_ptrs = 0` means host memory; `device_ptrs = 1` means CUDA
+ * device memory of the current device.  Complex numbers are interleaved
+ * (re, im) doubles.  All calls are synchronous with respect to the host; the
+ * work runs on the stream given at gw_setup (or a private one).
+ *
+ * Errors: every call returns a gw_status; nothing aborts.  gw_last_error()
+ * returns a text for the last failure on a context.  On GW_E_NOCONV the
+ * outputs are written (best iterate) and gw_stats reports the residuals.
+ */
+#ifndef GW_H
+#define GW_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gw_ctx gw_ctx;
+
+typedef enum {
+  GW_OK = 0,
+  GW_E_ARG = 1,          /* invalid argument (sizes, grid too small for the sphere, ...) */
+  GW_E_CUDA = 2,         /* CUDA runtime error */
+  GW_E_NOMEM = 3,        /* device allocation failed */
+  GW_E_NOCONV = 4,       /* a Sternheimer solve did not reach its tolerance */
+  GW_E_BREAKDOWN = 5,    /* Lanczos or CG breakdown (beta ~ 0, indefinite operator) */
+  GW_E_TIMEOUT = 6,      /* reserved: a bounded device wait gave up */
+  GW_E_NONFINITE = 7,    /* NaN or Inf in an input or a result */
+  GW_E_UNSUPPORTED = 8   /* configuration not supported by this build */
+} gw_status;
+
+typedef enum {
+  GW_FP64 = 0,   /* every step in FP64 */
+  GW_MIXED = 1   /* FFTs, H and projector in FP32; FP64 outer Sternheimer residual,
+                    FP64 Lanczos inner products and tridiagonal inverse */
+} gw_prec;
+
+typedef enum { GW_COULOMB_TRUNCATED = 0, GW_COULOMB_BARE = 1 } gw_coulomb;
+
+/*
+ * gw_setup -- create a context for one cell (Sec. Scaling: N_PW sphere
+ * coefficients, N_FFT grid points; Sec. Results: spherical Coulomb truncation
+ * with radius L/2).
+ *   L        cell edge (bohr), > 0
+ *   n_grid   FFT points per edge N, 4 <= N <= 128, factors 2, 3, 5 only
+ *   ecut     plane-wave cutoff (Ha); the sphere must fit: 2 max|n| < N
+ *   vloc     [N^3] local potential V(r) (Ha) on the grid, C order
+ *   coulomb  GW_COULOMB_TRUNCATED: v(G) = 4 pi (1 - cos(|G| L/2)) / |G|^2,
+ *            v(0) = pi L^2 / 2;  GW_COULOMB_BARE: 4 pi / |G|^2, v(0) = 0
+ *   cuda_stream  caller stream (cudaStream_t): when non-NULL every kernel of the
+ *            context runs on it (a stream that can be captured); when NULL the
+ *            context creates a private non-blocking stream
+ * Returns GW_E_ARG for bad sizes; *out is NULL on failure.
+ */
+gw_status gw_setup(gw_ctx** out, double L, int n_grid, double ecut, const double* vloc,
+                   int coulomb, void* cuda_stream);
+
+/* number of plane waves N_PW in the sphere (0 for a NULL context) */
+int gw_npw(const gw_ctx* ctx);
+
+/* miller[N_PW][3]: integer n (FFT order, signed) of each sphere coefficient */
+gw_status gw_sphere(const gw_ctx* ctx, int* miller);
+
+/*
+ * gw_set_occupied -- the DFT input of the method (Eqs. P1, P2: occupied
+ * states psi_v with energies e_v; each state holds two electrons).
+ *   n_occ   1 <= n_occ <= 256
+ *   psi     [n_occ][N_PW] complex sphere coefficients, orthonormal eigenvectors
+ *           of H = |G|^2/2 + V_loc (the caller's ground state)
+ *   eps     [n_occ] energies, ascending
+ * The occupied space must be closed under complex conjugation (true when the
+ * highest occupied state is separated from the next one).  The library
+ * rotates each state to be real in real space (phase per state, real basis per
+ * degenerate shell); results depend only on the occupied projector.
+ * Host pointers only.  Returns GW_E_ARG if a state is not conjugation-closed.
+ */
+gw_status gw_set_occupied(gw_ctx* ctx, int n_occ, const double* psi, const double* eps);
+
+/*
+ * gw_apply_h -- y = H x for nb sphere vectors (the operator of Eq. P2:
+ * kinetic |G|^2/2 plus V_loc applied on the grid through FFTs, Sec. Scaling).
+ *   x, y  [nb][N_PW] complex
+ */
+gw_status gw_apply_h(gw_ctx* ctx, const double* x, int nb, double* y, gw_prec prec, int device_ptrs);
+
+/*
+ * gw_apply_chi0 -- dn = chi0(omega) dV for nb real fields and n_omega real
+ * frequencies (Eq. P through Eqs. P1 and P2: per occupied state one
+ * Sternheimer solve at omega = 0, two (H - e_v -/+ omega) otherwise, projected
+ * on the conduction space at every iteration).
+ *   dV     [nb][N^3] real
+ *   omega  [n_omega] complex; this build supports real omega below each
+ *          state's excitation gap (CG); others return GW_E_UNSUPPORTED
+ *   dn     [n_omega][nb][N^3] real
+ */
+gw_status gw_apply_chi0(gw_ctx* ctx, const double* dV, int nb, const double* omega, int n_omega,
+                        double* dn, gw_prec prec, int device_ptrs);
+
+/* gw_apply_eps -- out = eps~(omega) x = x - v^1/2 chi0(omega) v^1/2 x (Eq. epsilon);
+   shapes as gw_apply_chi0 (x: [nb][N^3], out: [n_omega][nb][N^3]). */
+gw_status gw_apply_eps(gw_ctx* ctx, const double* x, int nb, const double* omega, int n_omega,
+                       double* out, gw_prec prec, int device_ptrs);
+
+/*
+ * gw_lanczos -- k steps of the Lanczos recursion on eps~(omega) (Sec. Lanczos,
+ * Eq. krylov) from one real start field, with classical Gram-Schmidt applied
+ * twice against all previous vectors at every step:
+ *   q_1 = x0/|x0|;  w = eps~ q_k - beta_{k-1} q_{k-1};  alpha_k = <q_k|w>;
+ *   w -= alpha_k q_k;  w -= Q (Q^T w) twice;  beta_k = |w|;  q_{k+1} = w / beta_k
+ *   start   [N^3] real
+ *   blk     block size; this build supports 1
+ *   omega   complex; this build supports real omega as gw_apply_chi0
+ *   alpha   [k] real;  beta [k-1] real
+ *   basis   [k][N^3] real Lanczos vectors (orthonormal in <.|.>), or NULL
+ * Returns GW_E_BREAKDOWN if beta_k underflows (invariant subspace reached).
+ */
+gw_status gw_lanczos(gw_ctx* ctx, const double* start, int blk, int k, const double* omega,
+                     double* alpha, double* beta, double* basis, gw_prec prec, int device_ptrs);
+
+/*
+ * gw_epsinv_elements -- T_K^-1, the inverse dielectric matrix in the Lanczos
+ * basis (Sec. Lanczos: tridiagonal inversion at cost ~K^2), in FP64.
+ *   alpha [k], beta [k-1] real; out [k][k] real (symmetric)
+ * Returns GW_E_BREAKDOWN for a zero pivot.
+ */
+gw_status gw_epsinv_elements(gw_ctx* ctx, const double* alpha, const double* beta, int k, int blk,
+                             double* out, int device_ptrs);
+
+/*
+ * gw_grad_vloc -- s = <phi|eps~^-1(0)|phi> and grad[i] = ds/dV_loc(r_i) (not in
+ * the paper).  s and u = eps~^-1 phi come from k Lanczos steps started at phi;
+ * the gradient follows third-order perturbation theory:
+ *   w = v^1/2 u;  dpsi_v = -G_v P_c (w psi_v);  G_v = P_c (H - e_v)^-1 P_c
+ *   g1 = sum_v |dpsi_v|^2 - sum_vv' <dpsi_v|dpsi_v'> psi_v'* psi_v
+ *   lambda_v = G_v P_c [w dpsi_v - sum_v' <psi_v'|w|psi_v> dpsi_v']
+ *   g2 = -sum_v lambda_v* psi_v;   grad = (Omega/N_g) (4 g1 + 8 Re g2)
+ * i.e. one set of Sternheimer solves and one set of adjoint solves.
+ *   phi [N^3] real; s scalar (host or device per device_ptrs); grad [N^3] real
+ */
+gw_status gw_grad_vloc(gw_ctx* ctx, const double* phi, int k, double* s, double* grad, gw_prec prec,
+                       int device_ptrs);
+
+/*
+ * gw_stats -- counters of the last solve on the context:
+ *   out[0] Sternheimer columns solved, out[1] max inner iterations,
+ *   out[2] mean inner iterations, out[3] outer (FP64 residual) passes,
+ *   out[4] max final relative FP64 residual, out[5] H applications (columns),
+ *   out[6] CUDA kernels launched by the library since it was loaded
+ *   n: entries wanted (<= 7)
+ */
+gw_status gw_stats(const gw_ctx* ctx, double* out, int n);
+
+/* set solver controls: tol (relative FP64 residual), inner tolerance of the
+   mixed path, maximum inner iterations, maximum outer passes */
+gw_status gw_set_solver(gw_ctx* ctx, double tol, double tol_inner, int max_iter, int max_outer);
+
+const char* gw_last_error(const gw_ctx* ctx);
+void gw_destroy(gw_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GW_H */

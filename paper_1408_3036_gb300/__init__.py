@@ -1,0 +1,273 @@
+"""GB300-native Lanczos-basis dielectric matrix for Sternheimer G0W0.
+
+Thin ctypes binding of ``libgw.so`` (C ABI in ``include/gw.h``): the functions
+below carry the C names and only marshal arguments.  Every step of the path
+runs in the library's CUDA kernels; there is no CPU fallback.  If the library
+is missing the import succeeds but every call raises ``GwError``.
+
+Arrays: numpy arrays are host buffers (``device_ptrs = 0``); CUDA torch
+tensors are device buffers (``device_ptrs = 1``).  Complex values are
+complex128 (interleaved re/im doubles).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libgw.so")
+
+GW_FP64, GW_MIXED = 0, 1
+GW_COULOMB_TRUNCATED, GW_COULOMB_BARE = 0, 1
+STATUS = {0: "GW_OK", 1: "GW_E_ARG", 2: "GW_E_CUDA", 3: "GW_E_NOMEM", 4: "GW_E_NOCONV",
+          5: "GW_E_BREAKDOWN", 6: "GW_E_TIMEOUT", 7: "GW_E_NONFINITE", 8: "GW_E_UNSUPPORTED"}
+EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "gw_apply_chi0",
+           "gw_apply_eps", "gw_lanczos", "gw_epsinv_elements", "gw_grad_vloc", "gw_stats",
+           "gw_set_solver", "gw_last_error", "gw_destroy")
+
+
+class GwError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libgw.so (build it first with ``paper_1408_3036_gb300._build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise GwError(2, f"libgw.so not built at {path}; the CUDA path has no fallback")
+    lib = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "gw_setup": (I, [ctypes.POINTER(P), D, I, D, P, I, P]),
+        "gw_npw": (I, [P]),
+        "gw_sphere": (I, [P, P]),
+        "gw_set_occupied": (I, [P, I, P, P]),
+        "gw_apply_h": (I, [P, P, I, P, I, I]),
+        "gw_apply_chi0": (I, [P, P, I, P, I, P, I, I]),
+        "gw_apply_eps": (I, [P, P, I, P, I, P, I, I]),
+        "gw_lanczos": (I, [P, P, I, I, P, P, P, P, I, I]),
+        "gw_epsinv_elements": (I, [P, P, P, I, I, P, I]),
+        "gw_grad_vloc": (I, [P, P, I, P, P, I, I]),
+        "gw_stats": (I, [P, P, I]),
+        "gw_set_solver": (I, [P, D, D, I, I]),
+        "gw_last_error": (ctypes.c_char_p, [P]),
+        "gw_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """(pointer, is_device) for a numpy array or a torch tensor."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("arrays must be C contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError(type(a))
+
+
+def _check(ctx, st):
+    if st != 0:
+        msg = load().gw_last_error(ctx).decode() if ctx else ""
+        raise GwError(st, msg)
+
+
+def _omega_buf(omegas):
+    om = np.ascontiguousarray(np.asarray(omegas, dtype=np.complex128).reshape(-1))
+    return om
+
+
+def gw_setup(L, n_grid, ecut, vloc, coulomb=GW_COULOMB_TRUNCATED, cuda_stream=None):
+    lib = load()
+    v = np.ascontiguousarray(np.asarray(vloc, dtype=np.float64).reshape(-1))
+    if v.size != n_grid ** 3:
+        raise ValueError("vloc must hold n_grid^3 values")
+    out = ctypes.c_void_p()
+    st = lib.gw_setup(ctypes.byref(out), float(L), int(n_grid), float(ecut), v.ctypes.data, int(coulomb),
+                      cuda_stream)
+    _check(None, st)
+    return out
+
+
+def gw_npw(ctx):
+    return load().gw_npw(ctx)
+
+
+def gw_sphere(ctx):
+    m = np.zeros((gw_npw(ctx), 3), dtype=np.int32)
+    _check(ctx, load().gw_sphere(ctx, m.ctypes.data))
+    return m
+
+
+def gw_set_occupied(ctx, psi, eps):
+    psi = np.ascontiguousarray(np.asarray(psi, dtype=np.complex128))
+    eps = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
+    _check(ctx, load().gw_set_occupied(ctx, len(eps), psi.ctypes.data, eps.ctypes.data))
+
+
+def gw_apply_h(ctx, x, y, prec=GW_FP64):
+    px, dx = _ptr(x)
+    py, dy = _ptr(y)
+    if dx != dy:
+        raise ValueError("x and y must both be host or both device")
+    nb = x.shape[0] if x.ndim == 2 else 1
+    _check(ctx, load().gw_apply_h(ctx, px, nb, py, int(prec), dx))
+    return y
+
+
+def gw_apply_chi0(ctx, dV, omegas, dn, prec=GW_FP64):
+    om = _omega_buf(omegas)
+    p, d = _ptr(dV)
+    q, e = _ptr(dn)
+    if d != e:
+        raise ValueError("mixed host/device buffers")
+    nb = dV.shape[0] if dV.ndim == 2 else 1
+    _check(ctx, load().gw_apply_chi0(ctx, p, nb, om.ctypes.data, len(om), q, int(prec), d))
+    return dn
+
+
+def gw_apply_eps(ctx, x, omegas, out, prec=GW_FP64):
+    om = _omega_buf(omegas)
+    p, d = _ptr(x)
+    q, e = _ptr(out)
+    if d != e:
+        raise ValueError("mixed host/device buffers")
+    nb = x.shape[0] if x.ndim == 2 else 1
+    _check(ctx, load().gw_apply_eps(ctx, p, nb, om.ctypes.data, len(om), q, int(prec), d))
+    return out
+
+
+def gw_lanczos(ctx, start, k, omega, alpha, beta, basis=None, prec=GW_FP64, blk=1):
+    om = _omega_buf([omega])
+    ps, d = _ptr(start)
+    pa, _ = _ptr(alpha)
+    pb, _ = _ptr(beta)
+    pq, _ = _ptr(basis)
+    _check(ctx, load().gw_lanczos(ctx, ps, int(blk), int(k), om.ctypes.data, pa, pb, pq, int(prec), d))
+    return alpha, beta, basis
+
+
+def gw_epsinv_elements(ctx, alpha, beta, k, out, blk=1):
+    pa, d = _ptr(alpha)
+    pb, _ = _ptr(beta)
+    po, _ = _ptr(out)
+    _check(ctx, load().gw_epsinv_elements(ctx, pa, pb, int(k), int(blk), po, d))
+    return out
+
+
+def gw_grad_vloc(ctx, phi, k, s, grad, prec=GW_FP64):
+    pp, d = _ptr(phi)
+    ps, _ = _ptr(s)
+    pg, _ = _ptr(grad)
+    _check(ctx, load().gw_grad_vloc(ctx, pp, int(k), ps, pg, int(prec), d))
+    return s, grad
+
+
+def gw_stats(ctx):
+    out = np.zeros(7)
+    _check(ctx, load().gw_stats(ctx, out.ctypes.data, 7))
+    return dict(columns=out[0], max_iter=out[1], mean_iter=out[2], outer=out[3], max_residual=out[4],
+                h_columns=out[5], launches=int(out[6]))
+
+
+def gw_set_solver(ctx, tol=0.0, tol_inner=0.0, max_iter=0, max_outer=0):
+    _check(ctx, load().gw_set_solver(ctx, float(tol), float(tol_inner), int(max_iter), int(max_outer)))
+
+
+def gw_last_error(ctx):
+    return load().gw_last_error(ctx).decode()
+
+
+def gw_destroy(ctx):
+    if ctx:
+        load().gw_destroy(ctx)
+
+
+class Cell:
+    """Convenience owner of one context (setup ... destroy)."""
+
+    def __init__(self, L, n_grid, ecut, vloc, coulomb=GW_COULOMB_TRUNCATED, cuda_stream=None):
+        self.L, self.N, self.ecut = float(L), int(n_grid), float(ecut)
+        self.ctx = gw_setup(L, n_grid, ecut, vloc, coulomb, cuda_stream)
+        self.npw = gw_npw(self.ctx)
+        self.ng = self.N ** 3
+
+    def close(self):
+        if self.ctx:
+            gw_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sphere(self):
+        return gw_sphere(self.ctx)
+
+    def set_occupied(self, psi, eps):
+        gw_set_occupied(self.ctx, psi, eps)
+        self.n_occ = len(eps)
+
+    def apply_h(self, x, prec=GW_FP64):
+        x = np.ascontiguousarray(np.atleast_2d(np.asarray(x, np.complex128)))
+        y = np.empty_like(x)
+        return gw_apply_h(self.ctx, x, y, prec)
+
+    def apply_chi0(self, dV, omegas=(0.0,), prec=GW_FP64):
+        dV = np.ascontiguousarray(np.atleast_2d(np.asarray(dV, np.float64)))
+        dn = np.empty((len(omegas), dV.shape[0], self.ng))
+        return gw_apply_chi0(self.ctx, dV, omegas, dn, prec)
+
+    def apply_eps(self, x, omegas=(0.0,), prec=GW_FP64):
+        x = np.ascontiguousarray(np.atleast_2d(np.asarray(x, np.float64)))
+        out = np.empty((len(omegas), x.shape[0], self.ng))
+        return gw_apply_eps(self.ctx, x, omegas, out, prec)
+
+    def lanczos(self, start, k, omega=0.0, prec=GW_FP64, basis=False):
+        start = np.ascontiguousarray(np.asarray(start, np.float64).reshape(-1))
+        a = np.empty(k)
+        b = np.empty(max(k - 1, 1))
+        Q = np.empty((k, self.ng)) if basis else None
+        gw_lanczos(self.ctx, start, k, omega, a, b, Q, prec)
+        return a, b[:k - 1], Q
+
+    def epsinv(self, alpha, beta):
+        k = len(alpha)
+        out = np.empty((k, k))
+        a = np.ascontiguousarray(alpha, np.float64)
+        b = np.ascontiguousarray(beta if len(beta) else np.zeros(1), np.float64)
+        return gw_epsinv_elements(self.ctx, a, b, k, out)
+
+    def grad_vloc(self, phi, k, prec=GW_FP64):
+        phi = np.ascontiguousarray(np.asarray(phi, np.float64).reshape(-1))
+        s = np.zeros(1)
+        g = np.empty(self.ng)
+        gw_grad_vloc(self.ctx, phi, k, s, g, prec)
+        return s[0], g
+
+    def stats(self):
+        return gw_stats(self.ctx)
+
+    def set_solver(self, **kw):
+        gw_set_solver(self.ctx, **kw)

@@ -1,0 +1,109 @@
+// Batched shared-memory FFT of short pencils (N <= 128, radices 4, 2, 3, 5).
+//
+// Self-sorting Stockham formulation: stage s with radix r and span Ns (the
+// product of the earlier radices) takes butterfly j in [0, N/r):
+//     k   = j mod Ns
+//     a_q = x[j + q N/r] * w^(k q N / (Ns r)),   q = 0..r-1,  w = exp(sign 2 pi i / N)
+//     y   = DFT_r(a)
+//     x'[(j div Ns) Ns r + k + p Ns] = y_p
+// After the last stage x' holds the DFT in natural order.  All threads of the
+// block share the butterflies of all pencils of the tile; stages ping-pong
+// between two shared-memory buffers.
+#pragma once
+
+#include "gw_common.cuh"
+
+namespace gw {
+
+template <typename V>
+__device__ __forceinline__ V mul_i(V a, int sign) {  // a * (sign * i)
+  V r;
+  if (sign > 0) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+  return r;
+}
+
+template <typename T, int SIGN>
+__device__ __forceinline__ void butterfly(cpx<T>* a, int r) {
+  using V = cpx<T>;
+  if (r == 2) {
+    V t = a[0];
+    a[0] = cadd(t, a[1]);
+    a[1] = csub(t, a[1]);
+  } else if (r == 4) {
+    V t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
+    V t2 = cadd(a[1], a[3]), t3 = mul_i(csub(a[1], a[3]), SIGN);
+    a[0] = cadd(t0, t2);
+    a[2] = csub(t0, t2);
+    a[1] = cadd(t1, t3);
+    a[3] = csub(t1, t3);
+  } else if (r == 3) {
+    const T h = (T)0.86602540378443864676;  // sqrt(3)/2
+    V t = cadd(a[1], a[2]);
+    V d = mul_i(cscale(csub(a[1], a[2]), h), SIGN);
+    V m = csub(a[0], cscale(t, (T)0.5));
+    a[0] = cadd(a[0], t);
+    a[1] = cadd(m, d);
+    a[2] = csub(m, d);
+  } else {  // r == 5
+    const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;
+    const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;
+    V t1 = cadd(a[1], a[4]), t2 = cadd(a[2], a[3]);
+    V d1 = csub(a[1], a[4]), d2 = csub(a[2], a[3]);
+    V m1 = cadd(a[0], cadd(cscale(t1, c1), cscale(t2, c2)));
+    V m2 = cadd(a[0], cadd(cscale(t1, c2), cscale(t2, c1)));
+    V e1 = mul_i(cadd(cscale(d1, s1), cscale(d2, s2)), SIGN);
+    V e2 = mul_i(csub(cscale(d1, s2), cscale(d2, s1)), SIGN);
+    a[0] = cadd(a[0], cadd(t1, t2));
+    a[1] = cadd(m1, e1);
+    a[4] = csub(m1, e1);
+    a[2] = cadd(m2, e2);
+    a[3] = csub(m2, e2);
+  }
+}
+
+// npen pencils of length pl.N at buf[p * ld + k]; tw[k] = exp(-2 pi i k / N).
+// Returns the buffer holding the result (a or b).  Ends with __syncthreads().
+template <typename T, int SIGN>
+__device__ cpx<T>* fft_tile(cpx<T>* a, cpx<T>* b, int npen, int ld, const FftPlan& pl,
+                            const cpx<T>* tw) {
+  using V = cpx<T>;
+  const int N = pl.N;
+  int Ns = 1;
+  for (int s = 0; s < pl.nst; ++s) {
+    const int r = pl.rad[s];
+    const int nb = N / r;
+    const int tstep = N / (Ns * r);
+    const int total = npen * nb;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int p = t / nb;
+      const int j = t - p * nb;
+      const int k = j % Ns;
+      const V* src = a + p * ld;
+      V* dst = b + p * ld;
+      V v[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        if (q < r) {
+          V x = src[j + q * nb];
+          if (q > 0 && k > 0) {
+            V w = tw[k * q * tstep];
+            if (SIGN > 0) w.y = -w.y;
+            x = cmul(x, w);
+          }
+          v[q] = x;
+        }
+      }
+      butterfly<T, SIGN>(v, r);
+      const int base = (j / Ns) * Ns * r + k;
+#pragma unroll
+      for (int q = 0; q < 5; ++q)
+        if (q < r) dst[base + q * Ns] = v[q];
+    }
+    __syncthreads();
+    V* t = a; a = b; b = t;
+    Ns *= r;
+  }
+  return a;
+}
+
+}  // namespace gw

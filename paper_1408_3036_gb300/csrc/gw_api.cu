@@ -1,0 +1,951 @@
+// C ABI of libgw (declared in include/gw.h) and the host drivers of the hot
+// path: cell set-up, the Sternheimer solver with FP64 iterative refinement,
+// the chi0 / eps~ application (Eqs. epsilon, P, P1, P2) and the Lanczos
+// recursion with full re-orthogonalisation (Sec. Lanczos).
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "gw.h"
+#include "gw_common.cuh"
+#include "linalg.cuh"
+
+using namespace gw;
+
+struct gw_ctx {
+  double L = 0, ecut = 0, vol = 0;
+  int N = 0, N3 = 0, npw = 0, coulomb = 0;
+  cudaStream_t user = nullptr, st = nullptr;
+  bool own_stream = true;
+  cudaEvent_t ev = nullptr;
+  FftPlan plan{};
+  Geometry geo;
+  Prec<double> P64;
+  Prec<float> P32;
+  std::vector<int> miller;      // [npw][3]
+  std::vector<int> sph_index;   // linear grid index
+  std::vector<double> kin;
+  int nocc = 0;
+  std::vector<double> eps;
+  std::map<std::string, std::pair<void*, size_t>> bufs;
+  Work work;
+  size_t work_cols = 0;
+  double tol = 1e-13, tol_mixed = 1e-10, tol_inner = 1e-5;
+  int max_iter = 20000, max_outer = 12;
+  double stats[6] = {0, 0, 0, 0, 0, 0};
+  int* host_pin = nullptr;      // pinned scratch for small read-backs
+  std::string err;
+};
+
+namespace {
+
+gw_status fail(gw_ctx* ctx, gw_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return s;
+}
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) {                                                                       \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? GW_E_NOMEM : GW_E_CUDA,                   \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                             \
+    }                                                                                              \
+  } while (0)
+
+#define TRY(call)                                                                                  \
+  do {                                                                                             \
+    gw_status s_ = (call);                                                                         \
+    if (s_ != GW_OK) return s_;                                                                    \
+  } while (0)
+
+template <class X>
+gw_status getbuf(gw_ctx* ctx, const std::string& name, size_t count, X** out) {
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(X);
+  auto& b = ctx->bufs[name];
+  if (b.second < bytes) {
+    if (b.first) CK(cudaFree(b.first));
+    b.first = nullptr;
+    b.second = 0;
+    CK(cudaMalloc(&b.first, bytes));
+    b.second = bytes;
+  }
+  *out = reinterpret_cast<X*>(b.first);
+  return GW_OK;
+}
+
+template <class X>
+gw_status upload(gw_ctx* ctx, const std::string& name, const std::vector<X>& v, X** out) {
+  TRY(getbuf(ctx, name, v.size(), out));
+  if (!v.empty()) CK(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, ctx->st));
+  return GW_OK;
+}
+
+gw_status launch_check(gw_ctx* ctx, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, GW_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return GW_OK;
+}
+
+gw_status sync(gw_ctx* ctx, const char* where) {
+  cudaError_t e = cudaStreamSynchronize(ctx->st);
+  if (e != cudaSuccess) return fail(ctx, GW_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return launch_check(ctx, where);
+}
+
+// reduction scratch for up to `cols` columns (or Lanczos vectors)
+gw_status ensure_work(gw_ctx* ctx, size_t cols) {
+  cols = std::max<size_t>(cols, 64);
+  if (cols <= ctx->work_cols) return GW_OK;
+  const size_t nch = (size_t)std::max(ctx->N3, ctx->npw) / 1024 + 2;
+  const size_t occ = std::max(ctx->nocc, 1);
+  TRY(getbuf(ctx, "w_part1", nch * cols, &ctx->work.part1));
+  TRY(getbuf(ctx, "w_part2", nch * cols * std::max<size_t>(occ, 1), &ctx->work.part2));
+  TRY(getbuf(ctx, "w_coef", occ * cols, &ctx->work.coef));
+  TRY(getbuf(ctx, "w_cnt_a", cols, &ctx->work.cnt_a));
+  TRY(getbuf(ctx, "w_cnt_b", cols, &ctx->work.cnt_b));
+  TRY(getbuf(ctx, "w_cnt_c", cols, &ctx->work.cnt_c));
+  CK(cudaMemsetAsync(ctx->work.cnt_a, 0, cols * sizeof(unsigned), ctx->st));
+  CK(cudaMemsetAsync(ctx->work.cnt_b, 0, cols * sizeof(unsigned), ctx->st));
+  CK(cudaMemsetAsync(ctx->work.cnt_c, 0, cols * sizeof(unsigned), ctx->st));
+  ctx->work_cols = cols;
+  return GW_OK;
+}
+
+template <typename T> Prec<T>& prec_of(gw_ctx* ctx);
+template <> Prec<double>& prec_of<double>(gw_ctx* ctx) { return ctx->P64; }
+template <> Prec<float>& prec_of<float>(gw_ctx* ctx) { return ctx->P32; }
+template <typename T> const char* tname();
+template <> const char* tname<double>() { return "64"; }
+template <> const char* tname<float>() { return "32"; }
+
+// ---------------------------------------------------------------------------
+// elementwise conversion of real arrays
+// ---------------------------------------------------------------------------
+template <typename A, typename B>
+__global__ void k_conv_real(size_t n, const A* __restrict__ in, B* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (B)in[i];
+}
+template <typename A, typename B>
+void conv_real(cudaStream_t s, size_t n, const A* in, B* out) {
+  const int nb = (int)std::min<size_t>((n + 255) / 256, 152 * 8);
+  ++g_launches;
+  k_conv_real<A, B><<<nb, 256, 0, s>>>(n, in, out);
+}
+
+// ---------------------------------------------------------------------------
+// v^1/2 on real fields: out = v^1/2 in   (or out = sub - v^1/2 in)
+// ---------------------------------------------------------------------------
+template <typename T>
+gw_status sqrtv(gw_ctx* ctx, const T* in, int nb, T* out, const T* sub) {
+  cpx<T>* grid;
+  TRY(getbuf(ctx, std::string("g_sqv") + tname<T>(), (size_t)nb * ctx->N3, &grid));
+  auto& P = prec_of<T>(ctx);
+  const Geometry& g = ctx->geo;
+  launch_zpass<T>(ctx->st, Z_G2G_FWD, g, P, ctx->plan, grid, nullptr, nullptr, nullptr, nullptr, nullptr,
+                  nullptr, in, nullptr, nb);
+  launch_ypass<T>(ctx->st, 0, 0, 0, g, P, ctx->plan, grid, nullptr, nb, 1);
+  launch_xpass_mul<T>(ctx->st, 0, 0, 0, g, P, ctx->plan, grid, P.sqv_s, nullptr, nb);
+  launch_ypass<T>(ctx->st, 1, 0, 0, g, P, ctx->plan, grid, nullptr, nb, 1);
+  launch_zpass<T>(ctx->st, sub ? Z_G2G_INV_SUB : Z_G2G_INV, g, P, ctx->plan, grid, nullptr, nullptr, nullptr,
+                  nullptr, nullptr, nullptr, sub, out, nb);
+  return launch_check(ctx, "sqrtv");
+}
+
+// ---------------------------------------------------------------------------
+// H applied to FP64 sphere vectors with shift: out = P_c? (H - E) x
+// ---------------------------------------------------------------------------
+template <typename T>
+gw_status h_apply(gw_ctx* ctx, cpx<T>* x, int ncol, const double2* E, const int* active, cpx<T>* out) {
+  cpx<T>* grid;
+  TRY(getbuf(ctx, std::string("g_h") + tname<T>(), (size_t)ncol * ctx->N3, &grid));
+  auto& P = prec_of<T>(ctx);
+  const Geometry& g = ctx->geo;
+  launch_zpass<T>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, grid, x, nullptr, nullptr, nullptr, nullptr, active,
+                  nullptr, nullptr, ncol);
+  launch_ypass<T>(ctx->st, 1, 1, 0, g, P, ctx->plan, grid, active, ncol, 0);
+  launch_xpass_mul<T>(ctx->st, 1, 1, 1, g, P, ctx->plan, grid, P.vloc_s, active, ncol);
+  launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, active, ncol, 0);
+  launch_zpass<T>(ctx->st, Z_GATHER_FWD_H, g, P, ctx->plan, grid, out, nullptr, nullptr, x, E, active, nullptr,
+                  nullptr, ncol);
+  return launch_check(ctx, "h_apply");
+}
+
+// ---------------------------------------------------------------------------
+// batched CG on P_c (H - E) P_c x = b, precision T, rhs FP64
+// ---------------------------------------------------------------------------
+template <typename T>
+gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, const int* outer_active,
+                   cpx<T>* x, double tol, long long* it_sum, int* it_max) {
+  const int npw = ctx->npw;
+  const std::string t = tname<T>();
+  cpx<T>*r, *p, *Ap, *grid;
+  TRY(getbuf(ctx, "cg_r" + t, (size_t)ncol * npw, &r));
+  TRY(getbuf(ctx, "cg_p" + t, (size_t)ncol * npw, &p));
+  TRY(getbuf(ctx, "cg_Ap" + t, (size_t)ncol * npw, &Ap));
+  TRY(getbuf(ctx, "g_cg" + t, (size_t)ncol * ctx->N3, &grid));
+  CgState st;
+  double* pap;
+  TRY(getbuf(ctx, "cg_rr", ncol, &st.rr));
+  TRY(getbuf(ctx, "cg_rr0", ncol, &st.rr0));
+  TRY(getbuf(ctx, "cg_beta", ncol, &st.beta));
+  TRY(getbuf(ctx, "cg_pap", ncol, &pap));
+  TRY(getbuf(ctx, "cg_iters", ncol, &st.iters));
+  TRY(getbuf(ctx, "cg_flag", ncol, &st.flag));
+  TRY(getbuf(ctx, "cg_active", ncol, &st.active));
+  TRY(getbuf(ctx, "cg_ndone", 1, &st.n_done));
+  TRY(getbuf(ctx, "cg_cnt", ncol, &st.cnt));
+  TRY(ensure_work(ctx, ncol));
+  CK(cudaMemsetAsync(st.cnt, 0, ncol * sizeof(unsigned), ctx->st));
+  CK(cudaMemsetAsync(st.n_done, 0, sizeof(int), ctx->st));
+  auto& P = prec_of<T>(ctx);
+  const Geometry& g = ctx->geo;
+  launch_cg_init<T, double>(ctx->st, npw, ncol, b64, x, r, outer_active, ctx->work, st);
+  const double tol2 = tol * tol;
+  const int check = 8;
+  for (int it = 0; it < ctx->max_iter; ++it) {
+    launch_zpass<T>(ctx->st, Z_SCATTER_INV_PUPD, g, P, ctx->plan, grid, p, r, st.beta, nullptr, nullptr,
+                    st.active, nullptr, nullptr, ncol);
+    launch_ypass<T>(ctx->st, 1, 1, 0, g, P, ctx->plan, grid, st.active, ncol, 0);
+    launch_xpass_mul<T>(ctx->st, 1, 1, 1, g, P, ctx->plan, grid, P.vloc_s, st.active, ncol);
+    launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, st.active, ncol, 0);
+    launch_zpass<T>(ctx->st, Z_GATHER_FWD_H, g, P, ctx->plan, grid, Ap, nullptr, nullptr, p, E, st.active,
+                    nullptr, nullptr, ncol);
+    launch_proj<T>(ctx->st, P.C, ctx->nocc, npw, Ap, ncol, st.active, ctx->work, p, pap);
+    launch_cg_update<T>(ctx->st, npw, ncol, x, r, p, Ap, pap, ctx->work, st, tol2, ctx->max_iter);
+    if ((it % check) == check - 1 || it == ctx->max_iter - 1) {
+      CK(cudaMemcpyAsync(ctx->host_pin, st.n_done, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+      TRY(sync(ctx, "cg_solve"));
+      if (ctx->host_pin[0] >= ncol) break;
+    }
+  }
+  std::vector<int> its(ncol), flags(ncol);
+  CK(cudaMemcpyAsync(its.data(), st.iters, ncol * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(flags.data(), st.flag, ncol * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  TRY(sync(ctx, "cg_solve stats"));
+  for (int c = 0; c < ncol; ++c) {
+    *it_sum += its[c];
+    *it_max = std::max(*it_max, its[c]);
+    if (flags[c] == 2) return fail(ctx, GW_E_BREAKDOWN, "CG breakdown: operator not positive definite on P_c");
+  }
+  return GW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sternheimer solves with FP64 iterative refinement:
+//   x64 = 0; repeat { d = CG_T(b - A64 x64); x64 += d } until |b - A64 x64| <= tol |b|
+// ---------------------------------------------------------------------------
+template <typename T>
+gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, double2* x64) {
+  const int npw = ctx->npw;
+  const bool mixed = !std::is_same<T, double>::value;
+  const double tol = mixed ? ctx->tol_mixed : ctx->tol;
+  const double tol_in = mixed ? ctx->tol_inner : ctx->tol;
+  double2 *r64, *ax;
+  cpx<T>* d;
+  int* oact;
+  double *res2, *bb;
+  TRY(getbuf(ctx, "sv_r64", (size_t)ncol * npw, &r64));
+  TRY(getbuf(ctx, "sv_ax", (size_t)ncol * npw, &ax));
+  TRY(getbuf(ctx, std::string("sv_d") + tname<T>(), (size_t)ncol * npw, &d));
+  TRY(getbuf(ctx, "sv_oact", ncol, &oact));
+  TRY(getbuf(ctx, "sv_res2", ncol, &res2));
+  TRY(getbuf(ctx, "sv_bb", ncol, &bb));
+  TRY(ensure_work(ctx, ncol));
+  CK(cudaMemsetAsync(x64, 0, (size_t)ncol * npw * sizeof(double2), ctx->st));
+  CK(cudaMemcpyAsync(r64, b64, (size_t)ncol * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
+  std::vector<int> act(ncol, 1);
+  TRY(upload(ctx, "sv_oact", act, &oact));
+  long long it_sum = 0;
+  int it_max = 0, outer = 0;
+  double worst = 0.0;
+  std::vector<double> hr(ncol), hb(ncol);
+  for (outer = 0; outer < ctx->max_outer; ++outer) {
+    TRY(cg_solve<T>(ctx, ncol, r64, E, oact, d, tol_in, &it_sum, &it_max));
+    launch_add_conv<T>(ctx->st, npw, ncol, d, x64, oact);
+    // r64 = b - P_c (H - E) x64
+    TRY(h_apply<double>(ctx, x64, ncol, E, oact, ax));
+    launch_proj<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, ax, ncol, oact, ctx->work, nullptr, nullptr);
+    launch_residual(ctx->st, npw, ncol, b64, ax, oact, ctx->work, res2, bb);
+    CK(cudaMemcpyAsync(r64, ax, (size_t)ncol * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(hr.data(), res2, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(hb.data(), bb, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    TRY(sync(ctx, "solve"));
+    int nact = 0;
+    worst = 0.0;
+    for (int c = 0; c < ncol; ++c) {
+      if (!act[c]) continue;
+      const double rel = hb[c] > 0 ? std::sqrt(hr[c] / hb[c]) : 0.0;
+      if (!std::isfinite(rel)) return fail(ctx, GW_E_NONFINITE, "non-finite Sternheimer residual");
+      worst = std::max(worst, rel);
+      if (rel > tol) ++nact; else act[c] = 0;
+    }
+    ctx->stats[4] = std::max(ctx->stats[4], worst);
+    if (nact == 0) break;
+    TRY(upload(ctx, "sv_oact", act, &oact));
+  }
+  ctx->stats[0] += ncol;
+  ctx->stats[1] = std::max<double>(ctx->stats[1], it_max);
+  ctx->stats[2] += (double)it_sum;
+  ctx->stats[3] = std::max<double>(ctx->stats[3], outer + 1);
+  ctx->stats[5] += (double)it_sum + ncol * (outer + 1);
+  if (outer >= ctx->max_outer) return fail(ctx, GW_E_NOCONV, "Sternheimer solve did not converge");
+  return GW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// chi0 application (Eqs. P1, P2):
+//   rhs_{v,b}   = P_c Sphere(FFT(conj(u_v) y_b))
+//   x_{o,b,v,s} = (H - e_v - s omega_o)^-1 rhs   (s = +/-; one solve at omega = 0)
+//   dn_{o,b}    = -(2/Omega) sum_v u_v IFFT(x^- + x^+)
+// ---------------------------------------------------------------------------
+template <typename T>
+gw_status chi0_core(gw_ctx* ctx, const T* y, int nb, const std::vector<double>& omega, T* dn) {
+  const int npw = ctx->npw, nocc = ctx->nocc, N3 = ctx->N3;
+  const int nom = (int)omega.size();
+  auto& P = prec_of<T>(ctx);
+  const Geometry& g = ctx->geo;
+  const std::string t = tname<T>();
+  // -- right-hand sides
+  const int nr = nocc * nb;
+  std::vector<int> ca(nr), cy(nr);
+  for (int b = 0; b < nb; ++b)
+    for (int v = 0; v < nocc; ++v) { ca[b * nocc + v] = v; cy[b * nocc + v] = b; }
+  int *dca, *dcy;
+  TRY(upload(ctx, "rhs_ca", ca, &dca));
+  TRY(upload(ctx, "rhs_cy", cy, &dcy));
+  cpx<T>* grid;
+  TRY(getbuf(ctx, "g_rhs" + t, (size_t)nr * N3, &grid));
+  cpx<T>* rs;
+  TRY(getbuf(ctx, "rhs_s" + t, (size_t)nr * npw, &rs));
+  double2* rhs64;
+  TRY(getbuf(ctx, "rhs64", (size_t)nr * npw, &rhs64));
+  TRY(ensure_work(ctx, std::max(nr, 1)));
+  launch_xpass_prod_fwd<T>(ctx->st, g, P, ctx->plan, reinterpret_cast<const cpx<T>*>(y), 0, P.U, 0, 1, dca, dcy,
+                           grid, nr);
+  launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, nullptr, nr, 0);
+  launch_zpass<T>(ctx->st, Z_GATHER_FWD, g, P, ctx->plan, grid, rs, nullptr, nullptr, nullptr, nullptr, nullptr,
+                  nullptr, nullptr, nr);
+  launch_gather_rows<double, T>(ctx->st, npw, nr, rs, nullptr, rhs64);
+  launch_proj<double>(ctx->st, ctx->P64.C, nocc, npw, rhs64, nr, nullptr, ctx->work, nullptr, nullptr);
+  TRY(launch_check(ctx, "rhs"));
+  // -- solver columns
+  std::vector<int> src, s0, s1;
+  std::vector<double2> E;
+  for (int o = 0; o < nom; ++o) {
+    const int ns = (omega[o] == 0.0) ? 1 : 2;
+    for (int b = 0; b < nb; ++b)
+      for (int v = 0; v < nocc; ++v) {
+        const int first = (int)src.size();
+        for (int s = 0; s < ns; ++s) {
+          src.push_back(b * nocc + v);
+          E.push_back(make_double2(ctx->eps[v] + (s == 0 ? omega[o] : -omega[o]), 0.0));
+        }
+        s0.push_back(first);
+        s1.push_back(ns == 2 ? first + 1 : -1);
+      }
+  }
+  const int ncol = (int)src.size();
+  const int nsol = (int)s0.size();
+  int *dsrc, *ds0, *ds1;
+  double2* dE;
+  TRY(upload(ctx, "col_src", src, &dsrc));
+  TRY(upload(ctx, "col_s0", s0, &ds0));
+  TRY(upload(ctx, "col_s1", s1, &ds1));
+  TRY(upload(ctx, "col_E", E, &dE));
+  double2 *bcol, *xcol, *sol64;
+  TRY(getbuf(ctx, "bcol", (size_t)ncol * npw, &bcol));
+  TRY(getbuf(ctx, "xcol", (size_t)ncol * npw, &xcol));
+  TRY(getbuf(ctx, "sol64", (size_t)nsol * npw, &sol64));
+  launch_gather_rows<double, double>(ctx->st, npw, ncol, rhs64, dsrc, bcol);
+  TRY(solve<T>(ctx, ncol, bcol, dE, xcol));
+  // -- combine: x^- + x^+, or 2 x at omega = 0 (x^- = x^+)
+  launch_combine(ctx->st, npw, nsol, xcol, ds0, ds1, 1.0, 2.0, sol64);
+  // -- density reduction
+  cpx<T>* solT;
+  TRY(getbuf(ctx, "solT" + t, (size_t)nsol * npw, &solT));
+  launch_gather_rows<T, double>(ctx->st, npw, nsol, sol64, nullptr, solT);
+  cpx<T>* gd;
+  TRY(getbuf(ctx, "g_dn" + t, (size_t)nsol * N3, &gd));
+  launch_zpass<T>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, gd, solT, nullptr, nullptr, nullptr, nullptr, nullptr,
+                  nullptr, nullptr, nsol);
+  launch_ypass<T>(ctx->st, 1, 1, 0, g, P, ctx->plan, gd, nullptr, nsol, 0);
+  std::vector<int> gstart(nom * nb + 1), colv(nsol);
+  for (int j = 0; j <= nom * nb; ++j) gstart[j] = j * nocc;
+  for (int j = 0; j < nsol; ++j) colv[j] = j % nocc;
+  int *dgs, *dcv;
+  TRY(upload(ctx, "dn_gs", gstart, &dgs));
+  TRY(upload(ctx, "dn_cv", colv, &dcv));
+  launch_xpass_inv_reduce<T>(ctx->st, g, P, ctx->plan, gd, dgs, dcv, nom * nb, -2.0 / ctx->vol, dn, nullptr, 0);
+  return launch_check(ctx, "chi0");
+}
+
+template <typename T>
+gw_status eps_core(gw_ctx* ctx, const double* x64, int nb, const std::vector<double>& omega, double* out64,
+                   bool chi0_only) {
+  const int N3 = ctx->N3;
+  const int nom = (int)omega.size();
+  const std::string t = tname<T>();
+  const T* xT;
+  if (std::is_same<T, double>::value) {
+    xT = reinterpret_cast<const T*>(x64);
+  } else {
+    T* tmp;
+    TRY(getbuf(ctx, "eps_x" + t, (size_t)nb * N3, &tmp));
+    conv_real<double, T>(ctx->st, (size_t)nb * N3, x64, tmp);
+    xT = tmp;
+  }
+  T* y;
+  T* dn;
+  TRY(getbuf(ctx, "eps_y" + t, (size_t)nb * N3, &y));
+  TRY(getbuf(ctx, "eps_dn" + t, (size_t)nom * nb * N3, &dn));
+  if (chi0_only) {
+    TRY(chi0_core<T>(ctx, xT, nb, omega, dn));
+    if (std::is_same<T, double>::value)
+      CK(cudaMemcpyAsync(out64, dn, (size_t)nom * nb * N3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+    else
+      conv_real<T, double>(ctx->st, (size_t)nom * nb * N3, dn, out64);
+    return launch_check(ctx, "chi0 out");
+  }
+  TRY(sqrtv<T>(ctx, xT, nb, y, nullptr));
+  TRY(chi0_core<T>(ctx, y, nb, omega, dn));
+  T* o;
+  TRY(getbuf(ctx, "eps_o" + t, (size_t)nom * nb * N3, &o));
+  for (int k = 0; k < nom; ++k)
+    TRY(sqrtv<T>(ctx, dn + (size_t)k * nb * N3, nb, o + (size_t)k * nb * N3, xT));
+  if (std::is_same<T, double>::value)
+    CK(cudaMemcpyAsync(out64, o, (size_t)nom * nb * N3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  else
+    conv_real<T, double>(ctx->st, (size_t)nom * nb * N3, o, out64);
+  return launch_check(ctx, "eps out");
+}
+
+gw_status check_omega(gw_ctx* ctx, const double* omega, int n, std::vector<double>* out) {
+  out->clear();
+  for (int i = 0; i < n; ++i) {
+    const double re = omega[2 * i], im = omega[2 * i + 1];
+    if (!std::isfinite(re) || !std::isfinite(im)) return fail(ctx, GW_E_NONFINITE, "non-finite omega");
+    if (im != 0.0) return fail(ctx, GW_E_UNSUPPORTED, "complex omega is not supported by this build");
+    out->push_back(re);
+  }
+  return GW_OK;
+}
+
+gw_status begin(gw_ctx* ctx) {
+  if (!ctx) return GW_E_ARG;
+  ctx->err.clear();
+  return GW_OK;
+}
+
+gw_status finish(gw_ctx* ctx, gw_status s) {
+  cudaError_t e = cudaStreamSynchronize(ctx->st);
+  if (s == GW_OK && e != cudaSuccess) return fail(ctx, GW_E_CUDA, cudaGetErrorString(e));
+  return s;
+}
+
+// input staging: returns a device pointer holding `bytes` of the caller's data
+gw_status stage_in(gw_ctx* ctx, const char* name, const void* p, size_t bytes, int dev, const void** out) {
+  if (dev) { *out = p; return GW_OK; }
+  unsigned char* b;
+  TRY(getbuf(ctx, name, bytes, &b));
+  CK(cudaMemcpyAsync(b, p, bytes, cudaMemcpyHostToDevice, ctx->st));
+  *out = b;
+  return GW_OK;
+}
+gw_status stage_out(gw_ctx* ctx, const char* name, void* p, size_t bytes, int dev, void** out) {
+  if (dev) { *out = p; return GW_OK; }
+  unsigned char* b;
+  TRY(getbuf(ctx, name, bytes, &b));
+  *out = b;
+  return GW_OK;
+}
+gw_status copy_back(gw_ctx* ctx, void* host, const void* devp, size_t bytes, int dev) {
+  if (dev) return GW_OK;
+  CK(cudaMemcpyAsync(host, devp, bytes, cudaMemcpyDeviceToHost, ctx->st));
+  return GW_OK;
+}
+
+gw_status need_occ(gw_ctx* ctx) {
+  if (ctx->nocc <= 0) return fail(ctx, GW_E_ARG, "gw_set_occupied has not been called");
+  return GW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Lanczos (Sec. Lanczos) on real fields, FP64 vectors and inner products
+// ---------------------------------------------------------------------------
+template <typename T>
+gw_status lanczos_core(gw_ctx* ctx, const double* x0, int K, const std::vector<double>& omega, double* alpha,
+                       double* beta, double* Q) {
+  const int N3 = ctx->N3;
+  const double wgt = ctx->vol / N3;
+  double *w, *h, *nrm;
+  TRY(getbuf(ctx, "lz_w", N3, &w));
+  TRY(getbuf(ctx, "lz_h", K + 1, &h));
+  TRY(getbuf(ctx, "lz_nrm", 1, &nrm));
+  TRY(ensure_work(ctx, K + 1));
+  launch_dot(ctx->st, N3, x0, x0, wgt, 1, ctx->work, nrm);
+  launch_lz_axpy(ctx->st, N3, 2, nrm, const_cast<double*>(x0), nullptr, Q);
+  for (int k = 0; k < K; ++k) {
+    double* qk = Q + (size_t)k * N3;
+    TRY(eps_core<T>(ctx, qk, 1, omega, w, false));
+    if (k > 0) launch_lz_axpy(ctx->st, N3, 0, beta + (k - 1), w, Q + (size_t)(k - 1) * N3, nullptr);
+    launch_dot(ctx->st, N3, qk, w, wgt, 0, ctx->work, alpha + k);
+    launch_lz_axpy(ctx->st, N3, 1, alpha + k, w, qk, nullptr);
+    for (int pass = 0; pass < 2; ++pass) {
+      launch_gemv_t(ctx->st, Q, N3, N3, w, wgt, k + 1, ctx->work, h);
+      launch_gemv_n(ctx->st, Q, N3, N3, h, k + 1, w);
+    }
+    if (k == K - 1) break;
+    launch_dot(ctx->st, N3, w, w, wgt, 1, ctx->work, beta + k);
+    launch_lz_axpy(ctx->st, N3, 2, beta + k, w, nullptr, Q + (size_t)(k + 1) * N3);
+    double hb[2];
+    CK(cudaMemcpyAsync(hb, beta + k, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(hb + 1, alpha + k, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    TRY(sync(ctx, "lanczos"));
+    if (!std::isfinite(hb[0]) || !std::isfinite(hb[1])) return fail(ctx, GW_E_NONFINITE, "non-finite Lanczos coefficient");
+    if (hb[0] <= 1e-14 * std::fabs(hb[1])) return fail(ctx, GW_E_BREAKDOWN, "Lanczos breakdown: invariant subspace");
+  }
+  return launch_check(ctx, "lanczos");
+}
+
+// host sphere, pencils, planes
+gw_status build_geometry(gw_ctx* ctx) {
+  const int N = ctx->N;
+  const double gg = 2.0 * M_PI / ctx->L;
+  std::vector<int> i2s, pen;
+  std::vector<int4> pencils;
+  std::vector<uint8_t> disc(N * N, 0), ones(N * N, 1), pmask(N, 0);
+  int maxn = 0;
+  for (int i0 = 0; i0 < N; ++i0)
+    for (int i1 = 0; i1 < N; ++i1)
+      for (int i2 = 0; i2 < N; ++i2) {
+        const int n0 = (2 * i0 < N) ? i0 : i0 - N;
+        const int n1 = (2 * i1 < N) ? i1 : i1 - N;
+        const int n2 = (2 * i2 < N) ? i2 : i2 - N;
+        const long nn = (long)n0 * n0 + (long)n1 * n1 + (long)n2 * n2;
+        const double kin = 0.5 * (gg * gg) * (double)nn;
+        if (kin <= ctx->ecut) {
+          const int s = (int)ctx->sph_index.size();
+          ctx->sph_index.push_back((i0 * N + i1) * N + i2);
+          ctx->miller.push_back(n0);
+          ctx->miller.push_back(n1);
+          ctx->miller.push_back(n2);
+          ctx->kin.push_back(kin);
+          maxn = std::max(maxn, std::max(std::abs(n0), std::max(std::abs(n1), std::abs(n2))));
+          if (pencils.empty() || pencils.back().x != i0 || pencils.back().y != i1)
+            pencils.push_back(make_int4(i0, i1, s, 0));
+          pencils.back().w += 1;
+          i2s.push_back(i2);
+          pen.push_back((int)pencils.size() - 1);
+          disc[i0 * N + i1] = 1;
+          pmask[i0] = 1;
+        }
+      }
+  if (2 * maxn >= N) return fail(ctx, GW_E_ARG, "the plane-wave sphere does not fit in the FFT grid");
+  ctx->npw = (int)ctx->kin.size();
+  if (ctx->npw == 0) return fail(ctx, GW_E_ARG, "empty plane-wave sphere");
+  std::vector<int> planes, allp(N);
+  for (int i = 0; i < N; ++i) {
+    allp[i] = i;
+    if (pmask[i]) planes.push_back(i);
+  }
+  Geometry& g = ctx->geo;
+  g.N = N; g.N2 = N * N; g.N3 = N * N * N; g.npw = ctx->npw;
+  g.npen = (int)pencils.size();
+  g.nplanes = (int)planes.size();
+  TRY(upload(ctx, "geo_i2", i2s, &g.sph_i2));
+  TRY(upload(ctx, "geo_pen", pen, &g.sph_pen));
+  TRY(upload(ctx, "geo_pencils", pencils, &g.pencils));
+  TRY(upload(ctx, "geo_disc", disc, &g.disc));
+  TRY(upload(ctx, "geo_ones", ones, &g.ones));
+  TRY(upload(ctx, "geo_planes", planes, &g.planes));
+  TRY(upload(ctx, "geo_allp", allp, &g.all_planes));
+  TRY(upload(ctx, "geo_pmask", pmask, &g.plane_mask));
+  return GW_OK;
+}
+
+template <typename T>
+gw_status upload_prec(gw_ctx* ctx, const std::vector<double>& vloc, const std::vector<double>& sqv) {
+  const int N = ctx->N, N3 = ctx->N3;
+  Prec<T>& P = prec_of<T>(ctx);
+  const std::string t = tname<T>();
+  std::vector<cpx<T>> tw(N);
+  for (int k = 0; k < N; ++k) tw[k] = mk<T>((T)std::cos(2.0 * M_PI * k / N), (T)(-std::sin(2.0 * M_PI * k / N)));
+  std::vector<T> kin(ctx->npw), vs(N3), sq(N3);
+  for (int s = 0; s < ctx->npw; ++s) kin[s] = (T)ctx->kin[s];
+  for (int r = 0; r < N3; ++r) {
+    vs[r] = (T)(vloc[r] / (double)N3);
+    sq[r] = (T)(sqv[r] / (double)N3);
+  }
+  TRY(upload(ctx, "p_tw" + t, tw, &P.tw));
+  TRY(upload(ctx, "p_kin" + t, kin, &P.kin));
+  TRY(upload(ctx, "p_v" + t, vs, &P.vloc_s));
+  TRY(upload(ctx, "p_sqv" + t, sq, &P.sqv_s));
+  return GW_OK;
+}
+
+// complex helpers on the host
+using zc = std::complex<double>;
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+gw_status gw_setup(gw_ctx** out, double L, int n_grid, double ecut, const double* vloc, int coulomb,
+                   void* cuda_stream) {
+  if (!out) return GW_E_ARG;
+  *out = nullptr;
+  if (!(L > 0) || n_grid < 4 || n_grid > kMaxN || !(ecut > 0) || !vloc || (coulomb != 0 && coulomb != 1))
+    return GW_E_ARG;
+  gw_ctx* ctx = new gw_ctx();
+  ctx->L = L;
+  ctx->N = n_grid;
+  ctx->N3 = n_grid * n_grid * n_grid;
+  ctx->ecut = ecut;
+  ctx->vol = L * L * L;
+  ctx->coulomb = coulomb;
+  ctx->user = reinterpret_cast<cudaStream_t>(cuda_stream);
+  auto bail = [&](gw_status s) { gw_destroy(ctx); return s; };
+  if (!make_plan(n_grid, &ctx->plan)) return bail(GW_E_ARG);
+  for (int r = 0; r < ctx->N3; ++r)
+    if (!std::isfinite(vloc[r])) return bail(GW_E_NONFINITE);
+  // run on the caller's stream when one is given, else on a private stream
+  if (ctx->user) {
+    ctx->st = ctx->user;
+    ctx->own_stream = false;
+  } else if (cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking) != cudaSuccess) {
+    return bail(GW_E_CUDA);
+  }
+  if (cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming) != cudaSuccess) return bail(GW_E_CUDA);
+  if (cudaMallocHost(&ctx->host_pin, 64) != cudaSuccess) return bail(GW_E_CUDA);
+  if (fft_set_smem_limits<double>() != cudaSuccess || fft_set_smem_limits<float>() != cudaSuccess)
+    return bail(GW_E_CUDA);
+  gw_status s = build_geometry(ctx);
+  if (s != GW_OK) return bail(s);
+  // sqrt of the Coulomb kernel on the full grid (FFT order)
+  const int N = n_grid;
+  const double gg = 2.0 * M_PI / L, Rc = 0.5 * L;
+  std::vector<double> v(vloc, vloc + ctx->N3), sqv(ctx->N3);
+  for (int i0 = 0; i0 < N; ++i0)
+    for (int i1 = 0; i1 < N; ++i1)
+      for (int i2 = 0; i2 < N; ++i2) {
+        const int n0 = (2 * i0 < N) ? i0 : i0 - N;
+        const int n1 = (2 * i1 < N) ? i1 : i1 - N;
+        const int n2 = (2 * i2 < N) ? i2 : i2 - N;
+        const double G2 = gg * gg * (double)((long)n0 * n0 + (long)n1 * n1 + (long)n2 * n2);
+        double vc;
+        if (G2 == 0.0) vc = (coulomb == 0) ? 2.0 * M_PI * Rc * Rc : 0.0;
+        else if (coulomb == 0) vc = 4.0 * M_PI * (1.0 - std::cos(std::sqrt(G2) * Rc)) / G2;
+        else vc = 4.0 * M_PI / G2;
+        sqv[(i0 * N + i1) * N + i2] = std::sqrt(vc);
+      }
+  s = upload_prec<double>(ctx, v, sqv);
+  if (s == GW_OK) s = upload_prec<float>(ctx, v, sqv);
+  if (s == GW_OK) s = finish(ctx, GW_OK);
+  if (s != GW_OK) return bail(s);
+  *out = ctx;
+  return GW_OK;
+}
+
+int gw_npw(const gw_ctx* ctx) { return ctx ? ctx->npw : 0; }
+
+gw_status gw_sphere(const gw_ctx* ctx, int* miller) {
+  if (!ctx || !miller) return GW_E_ARG;
+  std::memcpy(miller, ctx->miller.data(), ctx->miller.size() * sizeof(int));
+  return GW_OK;
+}
+
+gw_status gw_set_occupied(gw_ctx* ctx, int n_occ, const double* psi, const double* eps) {
+  if (!ctx) return GW_E_ARG;
+  if (n_occ < 1 || n_occ > kMaxOcc || !psi || !eps) return fail(ctx, GW_E_ARG, "bad n_occ / pointers");
+  TRY(begin(ctx));
+  const int npw = ctx->npw, N = ctx->N;
+  for (int v = 0; v < n_occ; ++v) {
+    if (!std::isfinite(eps[v])) return fail(ctx, GW_E_NONFINITE, "non-finite energy");
+    if (v > 0 && eps[v] < eps[v - 1]) return fail(ctx, GW_E_ARG, "energies must be ascending");
+  }
+  // index of -G for every sphere point
+  std::map<long, int> where;
+  auto key = [&](int a, int b, int c) { return ((long)(a + N) * (2 * N + 1) + (b + N)) * (2 * N + 1) + (c + N); };
+  for (int s = 0; s < npw; ++s) where[key(ctx->miller[3 * s], ctx->miller[3 * s + 1], ctx->miller[3 * s + 2])] = s;
+  std::vector<int> neg(npw);
+  for (int s = 0; s < npw; ++s) {
+    auto it = where.find(key(-ctx->miller[3 * s], -ctx->miller[3 * s + 1], -ctx->miller[3 * s + 2]));
+    if (it == where.end()) return fail(ctx, GW_E_ARG, "sphere not symmetric");
+    neg[s] = it->second;
+  }
+  // Real-in-real-space basis: (K c)_G = conj(c_{-G}).  Shells of equal energy
+  // (|de| < 1e-9 Ha) are re-spanned by the K-symmetric parts (c + Kc)/2 and
+  // (c - Kc)/2i, picked by pivoted Gram-Schmidt; inner products of K-symmetric
+  // vectors are real.
+  std::vector<zc> C((size_t)n_occ * npw);
+  for (size_t i = 0; i < C.size(); ++i) C[i] = zc(psi[2 * i], psi[2 * i + 1]);
+  std::vector<zc> R((size_t)n_occ * npw);
+  std::vector<double> e(n_occ);
+  int v0 = 0;
+  while (v0 < n_occ) {
+    int v1 = v0 + 1;
+    while (v1 < n_occ && std::fabs(eps[v1] - eps[v0]) < 1e-9) ++v1;
+    const int m = v1 - v0;
+    std::vector<std::vector<zc>> cand;
+    for (int v = v0; v < v1; ++v) {
+      std::vector<zc> a(npw), b(npw);
+      for (int s = 0; s < npw; ++s) {
+        const zc c = C[(size_t)v * npw + s], kc = std::conj(C[(size_t)v * npw + neg[s]]);
+        a[s] = 0.5 * (c + kc);
+        b[s] = (c - kc) / zc(0.0, 2.0);
+      }
+      cand.push_back(a);
+      cand.push_back(b);
+    }
+    double mean = 0.0;
+    for (int v = v0; v < v1; ++v) mean += eps[v];
+    mean /= m;
+    std::vector<bool> used(cand.size(), false);
+    for (int k = 0; k < m; ++k) {
+      int best = -1;
+      double bn = -1.0;
+      for (size_t j = 0; j < cand.size(); ++j) {
+        if (used[j]) continue;
+        double n2 = 0.0;
+        for (int s = 0; s < npw; ++s) n2 += std::norm(cand[j][s]);
+        if (n2 > bn) { bn = n2; best = (int)j; }
+      }
+      if (best < 0 || bn < 1e-12) return fail(ctx, GW_E_ARG, "occupied space is not closed under conjugation");
+      used[best] = true;
+      const double inv = 1.0 / std::sqrt(bn);
+      for (int s = 0; s < npw; ++s) cand[best][s] *= inv;
+      for (size_t j = 0; j < cand.size(); ++j) {
+        if (used[j]) continue;
+        zc d = 0.0;
+        for (int s = 0; s < npw; ++s) d += std::conj(cand[best][s]) * cand[j][s];
+        const double dr = d.real();
+        for (int s = 0; s < npw; ++s) cand[j][s] -= dr * cand[best][s];
+      }
+      for (int s = 0; s < npw; ++s) R[(size_t)(v0 + k) * npw + s] = cand[best][s];
+      e[v0 + k] = (m == 1) ? eps[v0] : mean;
+    }
+    // remaining candidates must be (numerically) in the span
+    for (size_t j = 0; j < cand.size(); ++j) {
+      if (used[j]) continue;
+      double n2 = 0.0;
+      for (int s = 0; s < npw; ++s) n2 += std::norm(cand[j][s]);
+      if (n2 > 1e-10) return fail(ctx, GW_E_ARG, "occupied space is not closed under conjugation");
+    }
+    v0 = v1;
+  }
+  ctx->nocc = n_occ;
+  ctx->eps = e;
+  ctx->work_cols = 0;
+  std::vector<double2> c64((size_t)n_occ * npw);
+  std::vector<float2> c32((size_t)n_occ * npw);
+  for (size_t i = 0; i < c64.size(); ++i) {
+    c64[i] = make_double2(R[i].real(), R[i].imag());
+    c32[i] = make_float2((float)R[i].real(), (float)R[i].imag());
+  }
+  TRY(upload(ctx, "occ_C64", c64, &ctx->P64.C));
+  TRY(upload(ctx, "occ_C32", c32, &ctx->P32.C));
+  // u_v(r) = sum_G c_G e^{iGr}: scatter, inverse transforms (FP64), then FP32 copy
+  double2* U;
+  float2* U32;
+  TRY(getbuf(ctx, "occ_U64", (size_t)n_occ * ctx->N3, &U));
+  TRY(getbuf(ctx, "occ_U32", (size_t)n_occ * ctx->N3, &U32));
+  const Geometry& g = ctx->geo;
+  launch_zpass<double>(ctx->st, Z_SCATTER_INV, g, ctx->P64, ctx->plan, U, ctx->P64.C, nullptr, nullptr, nullptr,
+                       nullptr, nullptr, nullptr, nullptr, n_occ);
+  launch_ypass<double>(ctx->st, 1, 1, 0, g, ctx->P64, ctx->plan, U, nullptr, n_occ, 0);
+  launch_xpass_mul<double>(ctx->st, 1, 1, 0, g, ctx->P64, ctx->plan, U, nullptr, nullptr, n_occ);
+  conv_real<double, float>(ctx->st, (size_t)2 * n_occ * ctx->N3, reinterpret_cast<double*>(U),
+                           reinterpret_cast<float*>(U32));
+  ctx->P64.U = U;
+  ctx->P32.U = U32;
+  TRY(launch_check(ctx, "set_occupied"));
+  return finish(ctx, GW_OK);
+}
+
+gw_status gw_apply_h(gw_ctx* ctx, const double* x, int nb, double* y, gw_prec prec, int dev) {
+  TRY(begin(ctx));
+  if (nb < 0 || (nb > 0 && (!x || !y))) return fail(ctx, GW_E_ARG, "bad arguments");
+  if (nb == 0) return GW_OK;
+  const size_t bytes = (size_t)nb * ctx->npw * sizeof(double2);
+  const void* xin;
+  void* yout;
+  TRY(stage_in(ctx, "io_in", x, bytes, dev, &xin));
+  TRY(stage_out(ctx, "io_out", y, bytes, dev, &yout));
+  std::vector<double2> E(nb, make_double2(0, 0));
+  double2* dE;
+  TRY(upload(ctx, "ah_E", E, &dE));
+  if (prec == GW_FP64) {
+    double2* xc;
+    TRY(getbuf(ctx, "ah_x", (size_t)nb * ctx->npw, &xc));
+    CK(cudaMemcpyAsync(xc, xin, bytes, cudaMemcpyDeviceToDevice, ctx->st));
+    TRY(h_apply<double>(ctx, xc, nb, dE, nullptr, reinterpret_cast<double2*>(yout)));
+  } else {
+    float2 *xc, *yc;
+    TRY(getbuf(ctx, "ah_x32", (size_t)nb * ctx->npw, &xc));
+    TRY(getbuf(ctx, "ah_y32", (size_t)nb * ctx->npw, &yc));
+    launch_gather_rows<float, double>(ctx->st, ctx->npw, nb, reinterpret_cast<const double2*>(xin), nullptr, xc);
+    TRY(h_apply<float>(ctx, xc, nb, dE, nullptr, yc));
+    launch_gather_rows<double, float>(ctx->st, ctx->npw, nb, yc, nullptr, reinterpret_cast<double2*>(yout));
+  }
+  TRY(copy_back(ctx, y, yout, bytes, dev));
+  return finish(ctx, launch_check(ctx, "apply_h"));
+}
+
+static gw_status apply_common(gw_ctx* ctx, const double* x, int nb, const double* omega, int n_omega,
+                              double* out, gw_prec prec, int dev, bool chi0_only) {
+  TRY(begin(ctx));
+  TRY(need_occ(ctx));
+  if (nb < 0 || n_omega < 1 || !omega || (nb > 0 && (!x || !out))) return fail(ctx, GW_E_ARG, "bad arguments");
+  if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_E_ARG, "bad precision");
+  std::vector<double> om;
+  TRY(check_omega(ctx, omega, n_omega, &om));
+  if (nb == 0) return GW_OK;
+  for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
+  const size_t ib = (size_t)nb * ctx->N3 * sizeof(double), ob = ib * n_omega;
+  const void* xin;
+  void* o;
+  TRY(stage_in(ctx, "io_in", x, ib, dev, &xin));
+  TRY(stage_out(ctx, "io_out", out, ob, dev, &o));
+  const double* xd = reinterpret_cast<const double*>(xin);
+  double* od = reinterpret_cast<double*>(o);
+  if (prec == GW_FP64) TRY(eps_core<double>(ctx, xd, nb, om, od, chi0_only));
+  else TRY(eps_core<float>(ctx, xd, nb, om, od, chi0_only));
+  TRY(copy_back(ctx, out, o, ob, dev));
+  if (ctx->stats[0] > 0) ctx->stats[2] /= ctx->stats[0];
+  return finish(ctx, GW_OK);
+}
+
+gw_status gw_apply_chi0(gw_ctx* ctx, const double* dV, int nb, const double* omega, int n_omega, double* dn,
+                        gw_prec prec, int dev) {
+  return apply_common(ctx, dV, nb, omega, n_omega, dn, prec, dev, true);
+}
+
+gw_status gw_apply_eps(gw_ctx* ctx, const double* x, int nb, const double* omega, int n_omega, double* out,
+                       gw_prec prec, int dev) {
+  return apply_common(ctx, x, nb, omega, n_omega, out, prec, dev, false);
+}
+
+gw_status gw_lanczos(gw_ctx* ctx, const double* start, int blk, int k, const double* omega, double* alpha,
+                     double* beta, double* basis, gw_prec prec, int dev) {
+  TRY(begin(ctx));
+  TRY(need_occ(ctx));
+  if (!start || !alpha || k < 1 || (k > 1 && !beta) || !omega) return fail(ctx, GW_E_ARG, "bad arguments");
+  if (blk != 1) return fail(ctx, GW_E_UNSUPPORTED, "block Lanczos is not supported by this build");
+  std::vector<double> om;
+  TRY(check_omega(ctx, omega, 1, &om));
+  for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
+  const size_t fb = (size_t)ctx->N3 * sizeof(double);
+  const void* x0;
+  TRY(stage_in(ctx, "lz_x0", start, fb, dev, &x0));
+  double *a, *b, *Q;
+  TRY(getbuf(ctx, "lz_alpha", k, &a));
+  TRY(getbuf(ctx, "lz_beta", std::max(k - 1, 1), &b));
+  if (dev && basis) Q = basis;
+  else TRY(getbuf(ctx, "lz_Q", (size_t)k * ctx->N3, &Q));
+  // the start vector may alias nothing we write; copy it (lanczos_core normalises from it)
+  double* x0c;
+  TRY(getbuf(ctx, "lz_x0c", ctx->N3, &x0c));
+  CK(cudaMemcpyAsync(x0c, x0, fb, cudaMemcpyDeviceToDevice, ctx->st));
+  gw_status s = (prec == GW_FP64) ? lanczos_core<double>(ctx, x0c, k, om, a, b, Q)
+                                  : lanczos_core<float>(ctx, x0c, k, om, a, b, Q);
+  if (s != GW_OK && s != GW_E_BREAKDOWN) return s;
+  if (dev) {
+    CK(cudaMemcpyAsync(alpha, a, k * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+    if (k > 1) CK(cudaMemcpyAsync(beta, b, (k - 1) * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  } else {
+    CK(cudaMemcpyAsync(alpha, a, k * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    if (k > 1) CK(cudaMemcpyAsync(beta, b, (k - 1) * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    if (basis) CK(cudaMemcpyAsync(basis, Q, (size_t)k * fb, cudaMemcpyDeviceToHost, ctx->st));
+  }
+  if (ctx->stats[0] > 0) ctx->stats[2] /= ctx->stats[0];
+  return finish(ctx, s);
+}
+
+gw_status gw_epsinv_elements(gw_ctx* ctx, const double* alpha, const double* beta, int k, int blk, double* out,
+                             int dev) {
+  TRY(begin(ctx));
+  if (!alpha || !out || k < 1 || (k > 1 && !beta)) return fail(ctx, GW_E_ARG, "bad arguments");
+  if (blk != 1) return fail(ctx, GW_E_UNSUPPORTED, "block tridiagonal inverse is not supported by this build");
+  const void *a, *b = nullptr;
+  TRY(stage_in(ctx, "ei_a", alpha, k * sizeof(double), dev, &a));
+  if (k > 1) TRY(stage_in(ctx, "ei_b", beta, (k - 1) * sizeof(double), dev, &b));
+  double *d, *l, *o;
+  int* stat;
+  TRY(getbuf(ctx, "ei_d", k, &d));
+  TRY(getbuf(ctx, "ei_l", k, &l));
+  TRY(getbuf(ctx, "ei_stat", 1, &stat));
+  void* op;
+  TRY(stage_out(ctx, "ei_o", out, (size_t)k * k * sizeof(double), dev, &op));
+  o = reinterpret_cast<double*>(op);
+  launch_tridiag_inv(ctx->st, k, reinterpret_cast<const double*>(a), reinterpret_cast<const double*>(b), d, l, o,
+                     stat);
+  TRY(launch_check(ctx, "epsinv"));
+  CK(cudaMemcpyAsync(ctx->host_pin, stat, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  TRY(copy_back(ctx, out, o, (size_t)k * k * sizeof(double), dev));
+  TRY(sync(ctx, "epsinv"));
+  if (ctx->host_pin[0]) return fail(ctx, GW_E_BREAKDOWN, "zero pivot in the tridiagonal inverse");
+  return GW_OK;
+}
+
+gw_status gw_grad_vloc(gw_ctx* ctx, const double*, int, double*, double*, gw_prec, int) {
+  return fail(ctx, GW_E_UNSUPPORTED, "gradient not available in this build");
+}
+
+gw_status gw_stats(const gw_ctx* ctx, double* out, int n) {
+  if (!ctx || !out || n < 0) return GW_E_ARG;
+  for (int i = 0; i < n && i < 6; ++i) out[i] = ctx->stats[i];
+  if (n > 6) out[6] = (double)g_launches;
+  return GW_OK;
+}
+
+gw_status gw_set_solver(gw_ctx* ctx, double tol, double tol_inner, int max_iter, int max_outer) {
+  if (!ctx) return GW_E_ARG;
+  if (tol > 0) { ctx->tol = tol; ctx->tol_mixed = std::max(tol, 1e-12); }
+  if (tol_inner > 0) ctx->tol_inner = tol_inner;
+  if (max_iter > 0) ctx->max_iter = max_iter;
+  if (max_outer > 0) ctx->max_outer = max_outer;
+  return GW_OK;
+}
+
+const char* gw_last_error(const gw_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void gw_destroy(gw_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  for (auto& kv : ctx->bufs)
+    if (kv.second.first) cudaFree(kv.second.first);
+  if (ctx->host_pin) cudaFreeHost(ctx->host_pin);
+  if (ctx->ev) cudaEventDestroy(ctx->ev);
+  if (ctx->st && ctx->own_stream) cudaStreamDestroy(ctx->st);
+  delete ctx;
+}
+
+}  // extern "C"
+
+namespace gw {
+bool make_plan(int N, FftPlan* p) {
+  if (N < 2 || N > kMaxN) return false;
+  p->N = N;
+  p->nst = 0;
+  int m = N;
+  const int order[4] = {4, 2, 3, 5};
+  for (int r : order) {
+    while (m % r == 0) {
+      if (p->nst >= kMaxStages) return false;
+      p->rad[p->nst++] = r;
+      m /= r;
+    }
+  }
+  return m == 1;
+}
+}  // namespace gw

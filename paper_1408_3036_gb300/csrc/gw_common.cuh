@@ -1,0 +1,117 @@
+// Shared definitions for the GB300 (sm_103a) Lanczos / Sternheimer dielectric
+// library: complex helpers, the per-cell geometry of the plane-wave sphere, and
+// the launch interfaces between the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace gw {
+
+// ---------------------------------------------------------------------------
+// complex arithmetic on double2 / float2
+// ---------------------------------------------------------------------------
+template <typename T> struct CT;
+template <> struct CT<double> { using type = double2; };
+template <> struct CT<float> { using type = float2; };
+template <typename T> using cpx = typename CT<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ cpx<T> mk(T x, T y) {
+  cpx<T> r; r.x = x; r.y = y; return r;
+}
+template <typename V> __host__ __device__ __forceinline__ V cadd(V a, V b) { V r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename V> __host__ __device__ __forceinline__ V csub(V a, V b) { V r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename V> __host__ __device__ __forceinline__ V cmul(V a, V b) {
+  V r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+// conj(a) * b
+template <typename V> __host__ __device__ __forceinline__ V cmulc(V a, V b) {
+  V r; r.x = a.x * b.x + a.y * b.y; r.y = a.x * b.y - a.y * b.x; return r;
+}
+template <typename V, typename S> __host__ __device__ __forceinline__ V cscale(V a, S s) {
+  V r; r.x = a.x * s; r.y = a.y * s; return r;
+}
+template <typename V> __host__ __device__ __forceinline__ V cconj(V a) { V r; r.x = a.x; r.y = -a.y; return r; }
+
+__host__ __device__ __forceinline__ double2 to_d(float2 a) { return make_double2(a.x, a.y); }
+__host__ __device__ __forceinline__ double2 to_d(double2 a) { return a; }
+template <typename T> __host__ __device__ __forceinline__ cpx<T> from_d(double2 a);
+template <> __host__ __device__ __forceinline__ double2 from_d<double>(double2 a) { return a; }
+template <> __host__ __device__ __forceinline__ float2 from_d<float>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+
+// ---------------------------------------------------------------------------
+// FFT plan: radices of a length-N transform (Stockham, mixed radix 4/2/3/5)
+// ---------------------------------------------------------------------------
+constexpr int kMaxStages = 10;
+constexpr int kMaxN = 128;
+struct FftPlan {
+  int N;
+  int nst;
+  int rad[kMaxStages];
+};
+bool make_plan(int N, FftPlan* p);
+
+// kernel launches issued by this library since it was loaded (host counter)
+extern unsigned long long g_launches;
+
+// ---------------------------------------------------------------------------
+// geometry of one cell's sphere on its grid (device arrays)
+// ---------------------------------------------------------------------------
+struct Geometry {
+  int N = 0, N2 = 0, N3 = 0, npw = 0;
+  int npen = 0;            // pencils (i0, i1) holding sphere points
+  int nplanes = 0;         // planes i0 holding sphere points
+  int* sph_i2 = nullptr;   // [npw] z index of each sphere point
+  int* sph_pen = nullptr;  // [npw] disc pencil holding each sphere point
+  int4* pencils = nullptr; // [npen] (i0, i1, first sphere index, count)
+  uint8_t* disc = nullptr; // [N2] 1 where pencil (i0, i1) holds sphere points
+  uint8_t* ones = nullptr; // [N2] all ones
+  int* planes = nullptr;   // [nplanes] i0 values
+  int* all_planes = nullptr; // [N] 0..N-1
+  uint8_t* plane_mask = nullptr; // [N]
+};
+
+// Per-precision device data of a cell.
+template <typename T> struct Prec {
+  cpx<T>* tw = nullptr;      // [N] exp(-2 pi i k / N)
+  T* kin = nullptr;          // [npw] |G|^2/2
+  T* vloc_s = nullptr;       // [N3] V(r) / N_g
+  T* sqv_s = nullptr;        // [N3] sqrt(v(G)) / N_g
+  cpx<T>* C = nullptr;       // [nocc][npw] occupied coefficients
+  cpx<T>* U = nullptr;       // [nocc][N3] u_v(r) = sum_G c_G e^{iGr}
+};
+
+// ---------------------------------------------------------------------------
+// kernel launchers (kernels_fft.cu)
+// ---------------------------------------------------------------------------
+// Which grid points a pass loads / stores; see kernels_fft.cu.
+enum ZMode { Z_SCATTER_INV = 0, Z_GATHER_FWD = 1, Z_G2G_FWD = 2, Z_G2G_INV = 3, Z_SCATTER_INV_PUPD = 4,
+             Z_GATHER_FWD_H = 5, Z_G2G_INV_SUB = 6 };
+
+template <typename T>
+void launch_zpass(cudaStream_t s, int mode, const Geometry& g, const Prec<T>& P, const FftPlan& pl,
+                  cpx<T>* grid, cpx<T>* sph, const cpx<T>* sph_r, const double* beta,
+                  const cpx<T>* sph_p, const double2* E, const int* active, const T* real_in,
+                  T* real_out, int ncol);
+template <typename T>
+void launch_ypass(cudaStream_t s, int inverse, int pruned_in, int pruned_out, const Geometry& g,
+                  const Prec<T>& P, const FftPlan& pl, cpx<T>* grid, const int* active, int ncol, int full_planes);
+template <typename T>
+void launch_xpass_mul(cudaStream_t s, int first_inverse, int pruned_in, int pruned_out, const Geometry& g,
+                      const Prec<T>& P, const FftPlan& pl, cpx<T>* grid, const T* mul, const int* active,
+                      int ncol);
+// out(v,b) = FFT_x(conj(U[v]) * Y[b]) / N_g   (first pass of a pruned forward transform)
+template <typename T>
+void launch_xpass_prod_fwd(cudaStream_t s, const Geometry& g, const Prec<T>& P, const FftPlan& pl,
+                           const cpx<T>* Y, int y_complex, const cpx<T>* A, int a_per_col, int conj_a,
+                           const int* col_a, const int* col_y, cpx<T>* out, int ncol);
+// dn[o] += scale * sum_{v} U[v] * IFFT_x(grid[col])   for col in group o (last pass of inverse)
+template <typename T>
+void launch_xpass_inv_reduce(cudaStream_t s, const Geometry& g, const Prec<T>& P, const FftPlan& pl,
+                             const cpx<T>* grid, const int* group_start, const int* col_v, int ngroups,
+                             double scale, T* out_real, cpx<T>* out_cplx, int accumulate);
+
+}  // namespace gw

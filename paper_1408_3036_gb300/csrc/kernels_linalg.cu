@@ -1,0 +1,512 @@
+// Vector kernels of the Sternheimer solver and of the Lanczos recursion:
+// the conduction projector P_c (Sec. Avoiding summations: orthogonalisation
+// against the valence space at every solver step), conjugate-gradient updates
+// with per-column convergence masks, FP64 residuals of the refinement loop,
+// the Lanczos re-orthogonalisation (Sec. Lanczos: Gram-Schmidt against all
+// previous vectors) and the inverse of the tridiagonal Lanczos matrix.
+//
+// Reductions are deterministic: blocks write partial sums, the last block to
+// finish (atomic ticket) adds them in a fixed order.  Dot products accumulate
+// in FP64 for both precisions.
+#include <cstdio>
+
+#include "gw_common.cuh"
+#include "linalg.cuh"
+
+namespace gw {
+
+constexpr int kLT = 256;   // threads per block
+constexpr int kChunk = 1024; // sphere / grid entries per block in vector kernels
+constexpr int kCT = 8;     // columns per block in the projector dots
+
+__device__ __forceinline__ bool last_block(unsigned* cnt, unsigned nblk) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(cnt, 1u);
+    is_last = (t == nblk - 1);
+    if (is_last) *cnt = 0u;
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+template <typename R>
+__device__ __forceinline__ R block_sum(R v) {
+  __shared__ R sh[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  R r = 0;
+  if (threadIdx.x < 32) {
+    r = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : (R)0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  return r;  // valid in thread 0
+}
+
+// ---------------------------------------------------------------------------
+// P_c y = y - sum_v c_v <c_v|y>: coefficients (a) then update (b).
+// ---------------------------------------------------------------------------
+// (a) coef[v * ncol + b] = sum_G conj(C[v][G]) Y[b][G]; grid (nchunk, ceil(ncol / kCT))
+template <typename T>
+__global__ void __launch_bounds__(kLT)
+k_proj_dots(const cpx<T>* __restrict__ C, int nocc, int npw, const cpx<T>* __restrict__ Y, int ncol,
+            const int* __restrict__ active, double2* __restrict__ partial, unsigned* __restrict__ cnt,
+            double2* __restrict__ coef) {
+  const int nchunk = gridDim.x;
+  const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
+  const int b0 = blockIdx.y * kCT;
+  const int nb = min(kCT, ncol - b0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  for (int v = warp; v < nocc; v += nw) {
+    double2 acc[kCT];
+#pragma unroll
+    for (int j = 0; j < kCT; ++j) acc[j] = make_double2(0, 0);
+    for (int G = g0 + lane; G < g1; G += 32) {
+      const double2 c = to_d(C[(size_t)v * npw + G]);
+#pragma unroll
+      for (int j = 0; j < kCT; ++j) {
+        if (j < nb) {
+          const double2 y = to_d(Y[(size_t)(b0 + j) * npw + G]);
+          acc[j].x += c.x * y.x + c.y * y.y;
+          acc[j].y += c.x * y.y - c.y * y.x;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kCT; ++j) {
+      double ax = acc[j].x, ay = acc[j].y;
+      for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+      }
+      if (lane == 0 && j < nb)
+        partial[((size_t)blockIdx.x * nocc + v) * ncol + b0 + j] = make_double2(ax, ay);
+    }
+  }
+  if (!last_block(&cnt[blockIdx.y], nchunk)) return;
+  for (int t = threadIdx.x; t < nocc * nb; t += blockDim.x) {
+    const int v = t / nb, j = t - v * nb;
+    double2 s = make_double2(0, 0);
+    for (int c = 0; c < nchunk; ++c) {
+      const double2 p = partial[((size_t)c * nocc + v) * ncol + b0 + j];
+      s.x += p.x; s.y += p.y;
+    }
+    coef[(size_t)v * ncol + b0 + j] = s;
+  }
+}
+
+// (b) Y[b] -= sum_v C[v] coef[v][b]; optionally pap[b] = Re <P[b]|Y[b]> (new Y).
+// grid (nchunk, ncol)
+template <typename T>
+__global__ void __launch_bounds__(kLT)
+k_proj_update(const cpx<T>* __restrict__ C, int nocc, int npw, cpx<T>* __restrict__ Y, int ncol,
+              const int* __restrict__ active, const double2* __restrict__ coef,
+              const cpx<T>* __restrict__ Pv, double* __restrict__ partial, unsigned* __restrict__ cnt,
+              double* __restrict__ pap) {
+  __shared__ double2 sc[kMaxOcc];
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  for (int v = threadIdx.x; v < nocc; v += blockDim.x) sc[v] = coef[(size_t)v * ncol + b];
+  __syncthreads();
+  const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
+  double acc = 0.0;
+  for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
+    double2 y = to_d(Y[(size_t)b * npw + G]);
+    for (int v = 0; v < nocc; ++v) {
+      const double2 c = to_d(C[(size_t)v * npw + G]);
+      const double2 a = sc[v];
+      y.x -= c.x * a.x - c.y * a.y;
+      y.y -= c.x * a.y + c.y * a.x;
+    }
+    const cpx<T> yo = from_d<T>(y);
+    Y[(size_t)b * npw + G] = yo;
+    if (Pv) {
+      const double2 p = to_d(Pv[(size_t)b * npw + G]);
+      const double2 yd = to_d(yo);
+      acc += p.x * yd.x + p.y * yd.y;
+    }
+  }
+  if (!Pv) return;
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ncol + b] = acc;
+  if (!last_block(&cnt[b], gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int c = 0; c < (int)gridDim.x; ++c) s += partial[(size_t)c * ncol + b];
+    pap[b] = s;
+  }
+}
+
+template <typename T>
+void launch_proj(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, int ncol, const int* active,
+                 Work& w, const cpx<T>* Pv, double* pap) {
+  if (ncol == 0 || nocc == 0) return;
+  const int nchunk = (npw + kChunk - 1) / kChunk;
+  dim3 g1(nchunk, (ncol + kCT - 1) / kCT);
+  ++g_launches;
+  k_proj_dots<T><<<g1, kLT, 0, s>>>(C, nocc, npw, Y, ncol, active, w.part2, w.cnt_a, w.coef);
+  dim3 g2(nchunk, ncol);
+  ++g_launches;
+  k_proj_update<T><<<g2, kLT, 0, s>>>(C, nocc, npw, Y, ncol, active, w.coef, Pv, w.part1, w.cnt_b, pap);
+}
+
+// ---------------------------------------------------------------------------
+// conjugate gradients (Hermitian positive definite A = P_c (H - E) P_c)
+// ---------------------------------------------------------------------------
+// init: x = 0, r = b (converted), rr = rr0 = |b|^2, beta = -1 (first p = r)
+template <typename T, typename U>
+__global__ void __launch_bounds__(kLT)
+k_cg_init(int npw, const cpx<U>* __restrict__ b, cpx<T>* __restrict__ x, cpx<T>* __restrict__ r,
+          const int* __restrict__ outer_active, double* __restrict__ partial, unsigned* __restrict__ cnt,
+          CgState st, int ncol) {
+  const int c = blockIdx.y;
+  const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
+  double acc = 0.0;
+  const bool on = !outer_active || outer_active[c];
+  for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
+    const size_t i = (size_t)c * npw + G;
+    cpx<T> bv = on ? from_d<T>(to_d(b[i])) : mk<T>(0, 0);
+    r[i] = bv;
+    x[i] = mk<T>(0, 0);
+    const double2 bd = to_d(bv);
+    acc += bd.x * bd.x + bd.y * bd.y;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ncol + c] = acc;
+  if (!last_block(&st.cnt[c], gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < (int)gridDim.x; ++k) s += partial[(size_t)k * ncol + c];
+    st.rr[c] = s;
+    st.rr0[c] = s;
+    st.beta[c] = -1.0;
+    st.iters[c] = 0;
+    st.flag[c] = 0;
+    st.active[c] = (on && s > 0.0) ? 1 : 0;
+    if (!st.active[c]) atomicAdd(st.n_done, 1);
+  }
+}
+
+// alpha = rr / pap; x += alpha p; r -= alpha Ap; rr' = |r|^2; beta = rr'/rr; masks
+template <typename T>
+__global__ void __launch_bounds__(kLT)
+k_cg_update(int npw, cpx<T>* __restrict__ x, cpx<T>* __restrict__ r, const cpx<T>* __restrict__ p,
+            const cpx<T>* __restrict__ Ap, const double* __restrict__ pap, double* __restrict__ partial,
+            CgState st, double tol2, int maxit, int ncol) {
+  const int c = blockIdx.y;
+  if (!st.active[c]) return;
+  const double pp = pap[c];
+  const double alpha = (pp > 0.0) ? st.rr[c] / pp : 0.0;
+  const T a = (T)alpha;
+  const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
+  double acc = 0.0;
+  for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
+    const size_t i = (size_t)c * npw + G;
+    const cpx<T> pv = p[i], av = Ap[i];
+    cpx<T> xv = x[i], rv = r[i];
+    xv.x += a * pv.x; xv.y += a * pv.y;
+    rv.x -= a * av.x; rv.y -= a * av.y;
+    x[i] = xv;
+    r[i] = rv;
+    const double2 rd = to_d(rv);
+    acc += rd.x * rd.x + rd.y * rd.y;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ncol + c] = acc;
+  if (!last_block(&st.cnt[c], gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < (int)gridDim.x; ++k) s += partial[(size_t)k * ncol + c];
+    const int it = st.iters[c] + 1;
+    st.iters[c] = it;
+    st.beta[c] = s / st.rr[c];
+    st.rr[c] = s;
+    bool stop = false;
+    if (!(pp > 0.0) || !isfinite(s)) { st.flag[c] = 2; stop = true; }     // breakdown / not SPD
+    else if (s <= tol2 * st.rr0[c]) { st.flag[c] = 0; stop = true; }
+    else if (it >= maxit) { st.flag[c] = 1; stop = true; }
+    if (stop) { st.active[c] = 0; atomicAdd(st.n_done, 1); }
+  }
+}
+
+template <typename T, typename U>
+void launch_cg_init(cudaStream_t s, int npw, int ncol, const cpx<U>* b, cpx<T>* x, cpx<T>* r,
+                    const int* outer_active, Work& w, CgState st) {
+  dim3 g((npw + kChunk - 1) / kChunk, ncol);
+  ++g_launches;
+  k_cg_init<T, U><<<g, kLT, 0, s>>>(npw, b, x, r, outer_active, w.part1, st.cnt, st, ncol);
+}
+
+template <typename T>
+void launch_cg_update(cudaStream_t s, int npw, int ncol, cpx<T>* x, cpx<T>* r, const cpx<T>* p,
+                      const cpx<T>* Ap, const double* pap, Work& w, CgState st, double tol2, int maxit) {
+  dim3 g((npw + kChunk - 1) / kChunk, ncol);
+  ++g_launches;
+  k_cg_update<T><<<g, kLT, 0, s>>>(npw, x, r, p, Ap, pap, w.part1, st, tol2, maxit, ncol);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 refinement helpers
+// ---------------------------------------------------------------------------
+// x64 += d (converted), for active columns
+template <typename T>
+__global__ void k_add_conv(size_t npw, const cpx<T>* __restrict__ d, double2* __restrict__ x,
+                           const int* __restrict__ active) {
+  const int c = blockIdx.y;
+  if (active && !active[c]) return;
+  for (size_t G = blockIdx.x * (size_t)blockDim.x + threadIdx.x; G < npw; G += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = (size_t)c * npw + G;
+    const double2 dv = to_d(d[i]);
+    double2 xv = x[i];
+    xv.x += dv.x; xv.y += dv.y;
+    x[i] = xv;
+  }
+}
+
+template <typename T>
+void launch_add_conv(cudaStream_t s, int npw, int ncol, const cpx<T>* d, double2* x, const int* active) {
+  dim3 g((npw + kLT - 1) / kLT, ncol);
+  ++g_launches;
+  k_add_conv<T><<<g, kLT, 0, s>>>((size_t)npw, d, x, active);
+}
+
+// r = b - Ax (in place over Ax), res2[c] = |r|^2, bb[c] = |b|^2
+__global__ void __launch_bounds__(kLT)
+k_residual(int npw, const double2* __restrict__ b, double2* __restrict__ ax, const int* __restrict__ active,
+           double2* __restrict__ partial, unsigned* __restrict__ cnt, double* __restrict__ res2,
+           double* __restrict__ bb, int ncol) {
+  const int c = blockIdx.y;
+  if (active && !active[c]) return;
+  const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
+  double a1 = 0.0, a2 = 0.0;
+  for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
+    const size_t i = (size_t)c * npw + G;
+    const double2 bv = b[i];
+    double2 r = ax[i];
+    r.x = bv.x - r.x;
+    r.y = bv.y - r.y;
+    ax[i] = r;
+    a1 += r.x * r.x + r.y * r.y;
+    a2 += bv.x * bv.x + bv.y * bv.y;
+  }
+  a1 = block_sum(a1);
+  a2 = block_sum(a2);
+  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ncol + c] = make_double2(a1, a2);
+  if (!last_block(&cnt[c], gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int k = 0; k < (int)gridDim.x; ++k) {
+      const double2 p = partial[(size_t)k * ncol + c];
+      s1 += p.x; s2 += p.y;
+    }
+    res2[c] = s1;
+    bb[c] = s2;
+  }
+}
+
+void launch_residual(cudaStream_t s, int npw, int ncol, const double2* b, double2* ax, const int* active,
+                     Work& w, double* res2, double* bb) {
+  dim3 g((npw + kChunk - 1) / kChunk, ncol);
+  ++g_launches;
+  k_residual<<<g, kLT, 0, s>>>(npw, b, ax, active, w.part2, w.cnt_b, res2, bb, ncol);
+}
+
+// ---------------------------------------------------------------------------
+// sphere-vector helpers
+// ---------------------------------------------------------------------------
+// out[j] = w_pair (in[src0[j]] + in[src1[j]])  or  w_single in[src0[j]] when src1[j] < 0
+__global__ void k_combine(int npw, const double2* __restrict__ in, const int* __restrict__ src0,
+                          const int* __restrict__ src1, double w_pair, double w_single, double2* __restrict__ out) {
+  const int j = blockIdx.y;
+  const int a = src0[j], b = src1[j];
+  for (int G = blockIdx.x * blockDim.x + threadIdx.x; G < npw; G += gridDim.x * blockDim.x) {
+    double2 v = in[(size_t)a * npw + G];
+    if (b >= 0) {
+      const double2 u = in[(size_t)b * npw + G];
+      v.x = w_pair * (v.x + u.x);
+      v.y = w_pair * (v.y + u.y);
+    } else {
+      v.x *= w_single;
+      v.y *= w_single;
+    }
+    out[(size_t)j * npw + G] = v;
+  }
+}
+
+void launch_combine(cudaStream_t s, int npw, int nout, const double2* in, const int* src0, const int* src1,
+                    double w_pair, double w_single, double2* out) {
+  dim3 g((npw + kLT - 1) / kLT, nout);
+  ++g_launches;
+  k_combine<<<g, kLT, 0, s>>>(npw, in, src0, src1, w_pair, w_single, out);
+}
+
+// gather rows: out[j] = in[idx[j]] (sphere vectors, with precision conversion)
+template <typename T, typename U>
+__global__ void k_gather_rows(int npw, const cpx<U>* __restrict__ in, const int* __restrict__ idx,
+                              cpx<T>* __restrict__ out) {
+  const int j = blockIdx.y;
+  const int a = idx ? idx[j] : j;
+  for (int G = blockIdx.x * blockDim.x + threadIdx.x; G < npw; G += gridDim.x * blockDim.x)
+    out[(size_t)j * npw + G] = from_d<T>(to_d(in[(size_t)a * npw + G]));
+}
+
+template <typename T, typename U>
+void launch_gather_rows(cudaStream_t s, int npw, int nout, const cpx<U>* in, const int* idx, cpx<T>* out) {
+  dim3 g((npw + kLT - 1) / kLT, nout);
+  ++g_launches;
+  k_gather_rows<T, U><<<g, kLT, 0, s>>>(npw, in, idx, out);
+}
+
+// ---------------------------------------------------------------------------
+// Lanczos vectors (real FP64 grid fields, weighted inner product)
+// ---------------------------------------------------------------------------
+// out[j] = wgt * sum_r Q[j][r] w[r], j < k; grid (nchunk, k)
+__global__ void __launch_bounds__(kLT)
+k_gemv_t(const double* __restrict__ Q, size_t ld, int n, const double* __restrict__ w, double wgt,
+         double* __restrict__ partial, unsigned* __restrict__ cnt, double* __restrict__ out, int k) {
+  const int j = blockIdx.y;
+  const int g0 = blockIdx.x * kChunk, g1 = min(n, g0 + kChunk);
+  double acc = 0.0;
+  for (int r = g0 + threadIdx.x; r < g1; r += blockDim.x) acc += Q[(size_t)j * ld + r] * w[r];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * k + j] = acc;
+  if (!last_block(&cnt[j], gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int c = 0; c < (int)gridDim.x; ++c) s += partial[(size_t)c * k + j];
+    out[j] = wgt * s;
+  }
+}
+
+// w[r] -= sum_j Q[j][r] h[j]
+__global__ void k_gemv_n(const double* __restrict__ Q, size_t ld, int n, const double* __restrict__ h, int k,
+                         double* __restrict__ w) {
+  extern __shared__ double sh[];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) sh[j] = h[j];
+  __syncthreads();
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc += Q[(size_t)j * ld + r] * sh[j];
+    w[r] -= acc;
+  }
+}
+
+void launch_gemv_t(cudaStream_t s, const double* Q, size_t ld, int n, const double* w, double wgt, int k,
+                   Work& wk, double* out) {
+  dim3 g((n + kChunk - 1) / kChunk, k);
+  ++g_launches;
+  k_gemv_t<<<g, kLT, 0, s>>>(Q, ld, n, w, wgt, wk.part1, wk.cnt_c, out, k);
+}
+
+void launch_gemv_n(cudaStream_t s, const double* Q, size_t ld, int n, const double* h, int k, double* w) {
+  const int nb = (n + kLT - 1) / kLT;
+  ++g_launches;
+  k_gemv_n<<<nb, kLT, k * sizeof(double), s>>>(Q, ld, n, h, k, w);
+}
+
+// Lanczos scalar steps on device:
+//   op 0: w -= beta[k-1] * qprev                          (k > 0)
+//   op 1: w -= alpha[k] * q
+//   op 2: q_next = w / beta[k]
+__global__ void k_lz_axpy(int n, int op, const double* __restrict__ sc, double* __restrict__ w,
+                          const double* __restrict__ q, double* __restrict__ qn) {
+  const double a = *sc;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    if (op == 2) qn[r] = w[r] / a;
+    else w[r] -= a * q[r];
+  }
+}
+
+void launch_lz_axpy(cudaStream_t s, int n, int op, const double* sc, double* w, const double* q, double* qn) {
+  const int nb = min((n + kLT - 1) / kLT, 4 * 152);
+  ++g_launches;
+  k_lz_axpy<<<nb, kLT, 0, s>>>(n, op, sc, w, q, qn);
+}
+
+// out = wgt * sum x*y (sqrt if want_sqrt); single block reduce over a grid of blocks
+__global__ void __launch_bounds__(kLT)
+k_dot(int n, const double* __restrict__ x, const double* __restrict__ y, double wgt, int want_sqrt,
+      double* __restrict__ partial, unsigned* __restrict__ cnt, double* __restrict__ out) {
+  double acc = 0.0;
+  const int g0 = blockIdx.x * kChunk, g1 = min(n, g0 + kChunk);
+  for (int r = g0 + threadIdx.x; r < g1; r += blockDim.x) acc += x[r] * y[r];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  if (!last_block(cnt, gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int c = 0; c < (int)gridDim.x; ++c) s += partial[c];
+    s *= wgt;
+    *out = want_sqrt ? sqrt(s) : s;
+  }
+}
+
+void launch_dot(cudaStream_t s, int n, const double* x, const double* y, double wgt, int want_sqrt, Work& w,
+                double* out) {
+  const int nb = (n + kChunk - 1) / kChunk;
+  ++g_launches;
+  k_dot<<<nb, kLT, 0, s>>>(n, x, y, wgt, want_sqrt, w.part1, w.cnt_c, out);
+}
+
+// ---------------------------------------------------------------------------
+// T_K^-1 for the symmetric tridiagonal Lanczos matrix (Sec. Lanczos: cost ~K^2).
+// LU without pivoting (T is positive definite at omega = 0: eps~ >= 1), then one
+// forward/backward substitution per unit column, one thread per column.
+// ---------------------------------------------------------------------------
+__global__ void k_tridiag_inv(int K, const double* __restrict__ alpha, const double* __restrict__ beta,
+                              double* __restrict__ d, double* __restrict__ l, double* __restrict__ out,
+                              int* __restrict__ status) {
+  if (threadIdx.x == 0) {
+    int bad = 0;
+    d[0] = alpha[0];
+    if (d[0] == 0.0) bad = 1;
+    for (int i = 1; i < K && !bad; ++i) {
+      l[i] = beta[i - 1] / d[i - 1];
+      d[i] = alpha[i] - l[i] * beta[i - 1];
+      if (d[i] == 0.0 || !isfinite(d[i])) bad = 1;
+    }
+    *status = bad;
+  }
+  __syncthreads();
+  if (*status) return;
+  for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    double* x = out + (size_t)j * K;   // column j (symmetric: also row j)
+    // forward: L y = e_j
+    for (int i = 0; i < K; ++i) x[i] = 0.0;
+    x[j] = 1.0;
+    for (int i = j + 1; i < K; ++i) x[i] = -l[i] * x[i - 1];
+    // backward: U x = y
+    x[K - 1] = x[K - 1] / d[K - 1];
+    for (int i = K - 2; i >= 0; --i) x[i] = (x[i] - beta[i] * x[i + 1]) / d[i];
+  }
+}
+
+void launch_tridiag_inv(cudaStream_t s, int K, const double* alpha, const double* beta, double* d, double* l,
+                        double* out, int* status) {
+  ++g_launches;
+  k_tridiag_inv<<<1, 256, 0, s>>>(K, alpha, beta, d, l, out, status);
+}
+
+#define GW_LINST(T)                                                                                        \
+  template void launch_proj<T>(cudaStream_t, const cpx<T>*, int, int, cpx<T>*, int, const int*, Work&,     \
+                               const cpx<T>*, double*);                                                    \
+  template void launch_cg_init<T, double>(cudaStream_t, int, int, const double2*, cpx<T>*, cpx<T>*,       \
+                                          const int*, Work&, CgState);                                     \
+  template void launch_cg_update<T>(cudaStream_t, int, int, cpx<T>*, cpx<T>*, const cpx<T>*,              \
+                                    const cpx<T>*, const double*, Work&, CgState, double, int);           \
+  template void launch_add_conv<T>(cudaStream_t, int, int, const cpx<T>*, double2*, const int*);
+
+GW_LINST(double)
+GW_LINST(float)
+template void launch_gather_rows<double, double>(cudaStream_t, int, int, const double2*, const int*, double2*);
+template void launch_gather_rows<float, double>(cudaStream_t, int, int, const double2*, const int*, float2*);
+template void launch_gather_rows<double, float>(cudaStream_t, int, int, const float2*, const int*, double2*);
+
+}  // namespace gw

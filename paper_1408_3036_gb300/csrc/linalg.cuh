@@ -1,0 +1,60 @@
+// Launch interfaces of the solver / Lanczos kernels (kernels_linalg.cu).
+#pragma once
+
+#include "gw_common.cuh"
+
+namespace gw {
+
+constexpr int kMaxOcc = 256;   // occupied states supported by the projector kernels
+
+// Scratch for deterministic reductions, owned by the context.
+struct Work {
+  double* part1 = nullptr;    // partial sums (double)
+  double2* part2 = nullptr;   // partial sums (double2)
+  double2* coef = nullptr;    // projector coefficients [nocc][ncol]
+  unsigned* cnt_a = nullptr;  // tickets (zero between launches)
+  unsigned* cnt_b = nullptr;
+  unsigned* cnt_c = nullptr;
+};
+
+// Per-column state of a batched CG solve (device arrays).
+struct CgState {
+  double* rr = nullptr;     // current |r|^2
+  double* rr0 = nullptr;    // |b|^2
+  double* beta = nullptr;   // next p = r + beta p (beta < 0: p = r)
+  int* iters = nullptr;
+  int* flag = nullptr;      // 0 converged, 1 max iterations, 2 breakdown
+  int* active = nullptr;
+  int* n_done = nullptr;    // columns that stopped (atomic)
+  unsigned* cnt = nullptr;  // tickets [ncol]
+};
+
+template <typename T>
+void launch_proj(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, int ncol, const int* active,
+                 Work& w, const cpx<T>* Pv, double* pap);
+template <typename T, typename U>
+void launch_cg_init(cudaStream_t s, int npw, int ncol, const cpx<U>* b, cpx<T>* x, cpx<T>* r,
+                    const int* outer_active, Work& w, CgState st);
+template <typename T>
+void launch_cg_update(cudaStream_t s, int npw, int ncol, cpx<T>* x, cpx<T>* r, const cpx<T>* p,
+                      const cpx<T>* Ap, const double* pap, Work& w, CgState st, double tol2, int maxit);
+template <typename T>
+void launch_add_conv(cudaStream_t s, int npw, int ncol, const cpx<T>* d, double2* x, const int* active);
+void launch_residual(cudaStream_t s, int npw, int ncol, const double2* b, double2* ax, const int* active,
+                     Work& w, double* res2, double* bb);
+void launch_combine(cudaStream_t s, int npw, int nout, const double2* in, const int* src0, const int* src1,
+                    double w_pair, double w_single, double2* out);
+template <typename T, typename U>
+void launch_gather_rows(cudaStream_t s, int npw, int nout, const cpx<U>* in, const int* idx, cpx<T>* out);
+void launch_gemv_t(cudaStream_t s, const double* Q, size_t ld, int n, const double* w, double wgt, int k,
+                   Work& wk, double* out);
+void launch_gemv_n(cudaStream_t s, const double* Q, size_t ld, int n, const double* h, int k, double* w);
+void launch_lz_axpy(cudaStream_t s, int n, int op, const double* sc, double* w, const double* q, double* qn);
+void launch_dot(cudaStream_t s, int n, const double* x, const double* y, double wgt, int want_sqrt, Work& w,
+                double* out);
+void launch_tridiag_inv(cudaStream_t s, int K, const double* alpha, const double* beta, double* d, double* l,
+                        double* out, int* status);
+
+template <typename T> cudaError_t fft_set_smem_limits();
+
+}  // namespace gw

@@ -1,0 +1,156 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: FP64 path <= 1e-10 relative (alpha, beta, eps^-1 elements; the
+operator applications themselves to ~1e-12); mixed path <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import coulomb, lanczos, pw, response
+from tests.conftest import rel
+
+pytestmark = pytest.mark.gpu
+
+gw = pytest.importorskip("paper_1408_3036_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1408_3036_gb300 import _build
+    _build.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def make(cell, gs=None, coulomb_kind=0):
+    c = gw.Cell(cell.L, cell.N, cell.ecut, cell.vloc, coulomb_kind)
+    if gs is not None:
+        c.set_occupied(gs.C, gs.eps)
+    return c
+
+
+# ---------------------------------------------------------------------------
+def test_sphere_bit_exact():
+    for cell in [W.tiny().cells[0], W.small().cells[0], W.molecule().cells[0],
+                 W.differentiation().cells[0], W.small(N=45, L=14.0, ecut=4.0).cells[0],
+                 W.small(N=30, L=12.0, ecut=5.0).cells[0]]:
+        sph = pw.Sphere(cell.L, cell.N, cell.ecut)
+        c = make(cell)
+        assert c.npw == sph.npw
+        assert np.array_equal(c.sphere(), sph.miller)
+        c.close()
+
+
+@pytest.mark.parametrize("N,L,ecut", [(16, 10.0, 5.0), (18, 9.0, 4.0), (45, 14.0, 4.0), (24, 11.0, 6.0)])
+def test_apply_h(N, L, ecut):
+    cell = W.small(N=N, L=L, ecut=ecut, n_wells=3).cells[0]
+    sph = pw.Sphere(cell.L, cell.N, cell.ecut)
+    c = make(cell)
+    rng = np.random.default_rng(N)
+    X = rng.standard_normal((5, sph.npw)) + 1j * rng.standard_normal((5, sph.npw))
+    ref = pw.h_apply(sph, cell.vloc, X)
+    assert rel(c.apply_h(X, gw.GW_FP64), ref) < 1e-13
+    assert rel(c.apply_h(X, gw.GW_MIXED), ref) < 2e-6
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    wl = W.tiny()
+    cell = wl.cells[0]
+    sph = pw.Sphere(cell.L, cell.N, cell.ecut)
+    gs = pw.ground_state_dense(sph, cell.vloc, cell.n_occ)
+    return wl, cell, sph, gs
+
+
+@pytest.mark.parametrize("omega", [0.0, 0.15])
+def test_apply_chi0_fp64(tiny, omega):
+    wl, cell, sph, gs = tiny
+    c = make(cell, gs)
+    f = W.random_fields(101, 3, sph.ng)
+    out = c.apply_chi0(f, [omega], gw.GW_FP64)[0]
+    for b in range(3):
+        ref = response.chi0_sos(gs, f[b], omega).real
+        assert rel(out[b], ref) < 1e-11
+    st = c.stats()
+    assert st["max_residual"] < 1e-12
+    c.close()
+
+
+def test_apply_eps_fp64_and_mixed(tiny):
+    wl, cell, sph, gs = tiny
+    c = make(cell, gs)
+    D = response.Dielectric(gs, 0.0)
+    f = W.random_fields(102, 2, sph.ng)
+    out64 = c.apply_eps(f, [0.0], gw.GW_FP64)[0]
+    out32 = c.apply_eps(f, [0.0], gw.GW_MIXED)[0]
+    for b in range(2):
+        ref = D.apply(f[b])
+        assert rel(out64[b], ref) < 1e-12
+        assert rel(out32[b], ref) < 1e-6
+    c.close()
+
+
+def test_lanczos_tiny_fp64(tiny):
+    wl, cell, sph, gs = tiny
+    c = make(cell, gs)
+    D = response.Dielectric(gs, 0.0)
+    wgt = sph.omega_vol / sph.ng
+    x0 = wl.starts[0][0]
+    a_ref, b_ref, Q_ref = lanczos.lanczos(D.apply, x0, wl.k, wgt)
+    a, b, Q = c.lanczos(x0, wl.k, 0.0, gw.GW_FP64, basis=True)
+    assert rel(a, a_ref) < 1e-10
+    assert rel(b, b_ref) < 1e-10
+    assert np.abs(wgt * Q @ Q.T - np.eye(wl.k)).max() < 1e-13
+    Ti = c.epsinv(a, b)
+    Ti_ref = lanczos.epsinv_lanczos(a_ref, b_ref)
+    assert np.abs(Ti - Ti_ref).max() / np.abs(Ti_ref).max() < 1e-10
+    c.close()
+
+
+def test_lanczos_tiny_mixed(tiny):
+    wl, cell, sph, gs = tiny
+    c = make(cell, gs)
+    D = response.Dielectric(gs, 0.0)
+    wgt = sph.omega_vol / sph.ng
+    x0 = wl.starts[0][0]
+    a_ref, b_ref, _ = lanczos.lanczos(D.apply, x0, wl.k, wgt)
+    a, b, _ = c.lanczos(x0, wl.k, 0.0, gw.GW_MIXED)
+    assert rel(a, a_ref) < 1e-6
+    assert rel(b, b_ref) < 1e-6
+    Ti = c.epsinv(a, b)
+    Ti_ref = lanczos.epsinv_lanczos(a_ref, b_ref)
+    assert np.abs(Ti - Ti_ref).max() / np.abs(Ti_ref).max() < 1e-6
+    c.close()
+
+
+def test_epsinv_matches_dense_inverse():
+    rng = np.random.default_rng(4)
+    a = 1.5 + rng.random(37)
+    b = 0.3 * rng.random(36)
+    cell = W.tiny().cells[0]
+    c = make(cell)
+    Ti = c.epsinv(a, b)
+    assert rel(Ti, np.linalg.inv(lanczos.tridiag(a, b))) < 1e-13
+    c.close()
+
+
+def test_free_electron_closed_form_gpu():
+    """V = 0, one occupied state: chi0(G) = -(2/Omega)|G|^2/((|G|^2/2)^2 - w^2)."""
+    cell = W.Cell(8.0, 12, 3.0, 1, np.zeros((0, 3)), 0.0, 1.0)
+    sph = pw.Sphere(cell.L, cell.N, cell.ecut)
+    gs = pw.ground_state_dense(sph, np.zeros(sph.ng), 1)
+    c = make(cell, gs)
+    f = W.random_fields(7, 1, sph.ng)
+    for omega in (0.0, 0.1):
+        dn = c.apply_chi0(f, [omega], gw.GW_FP64)[0, 0]
+        G2 = sph.gvec_norm() ** 2
+        insph = np.zeros(sph.ng, bool)
+        insph[sph.index] = True
+        expect = np.zeros(sph.ng)
+        m = insph & (G2 > 0)
+        expect[m] = -(2.0 / sph.omega_vol) * G2[m] / ((G2[m] / 2) ** 2 - omega ** 2)
+        assert rel(sph.fwd(dn), expect * sph.fwd(f[0])) < 1e-12
+    c.close()
