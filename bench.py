@@ -1,0 +1,408 @@
+"""Benchmark: eps~ applications per second on one GB300 (mixed vs FP64).
+
+Workload (molecule-sized static screening, the configuration the headline
+metric is quoted on): cubic cell L = 20 bohr, 48^3 grid, 10 Ha cutoff
+(~12k plane waves), 8 seeded Gaussian wells (D = -3 Ha, sigma = 0.8 bohr),
+16 occupied states, omega = 0, 100 Lanczos steps with full
+re-orthogonalisation.  One step = one complete 100-step Lanczos run = 100 eps~
+applications (unit of work: one eps~ application to one column at one omega).
+
+Inputs are synthetic (workloads.py); the occupied states come from the
+library's own H application inside a block LOBPCG (input preparation, not
+timed).  Inside a step the 16-column working set (~14 MB) stays in L2; L2 is
+flushed between timed steps by writing a 512 MB buffer.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "eps~ applies/sec & % HBM roofline, mixed vs FP64 GPU at <=1e-6 rel err"
+UNIT = "applies/s"
+WORKLOAD = ("molecule static screening: L=20 bohr, grid 48^3, ecut 10 Ha (12053 PW), 8 Gaussian wells "
+            "(D=-3 Ha, sigma=0.8 bohr), N_occ=16, omega=0, K=100 Lanczos steps, CGS2")
+SAMPLE_STATES = (0, 5, 10, 15)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (reported baseline; runs before any CUDA call)
+# ---------------------------------------------------------------------------
+def oracle_sample(wl, states=SAMPLE_STATES):
+    """One eps~ application of the workload by the oracle's Sternheimer route,
+    restricted to a subset of the occupied-state solves; returns applies/s
+    scaled to the full sum over occupied states."""
+    from oracle import pw, response
+    c = wl.cells[0]
+    sph = pw.Sphere(c.L, c.N, c.ecut)
+    vloc = c.vloc
+    t0 = time.perf_counter()
+    gs, w, _ = pw.ground_state_iterative(sph, vloc, c.n_occ, tol=1e-9, maxiter=500)
+    t_gs = time.perf_counter() - t0
+    gaps = w[c.n_occ] - gs.eps
+    D = response.Dielectric(gs, 0.0, route="sternheimer", gaps=gaps)
+    x = wl.starts[0][0]
+    t0 = time.perf_counter()
+    y = D.sqrtv(x).real
+    dn = response.chi0_sternheimer(gs, y, 0.0, 1e-14, gaps, states=list(states))
+    D.sqrtv(dn)
+    t = time.perf_counter() - t0
+    t_full = t * c.n_occ / len(states)
+    return dict(value=1.0 / t_full, unit=UNIT, cores=1, kind="oracle",
+                sample=(f"one eps~ application of the molecule workload, Sternheimer solves for occupied "
+                        f"states {list(states)} of {c.n_occ} (FP64 CG to 1e-14), time scaled by "
+                        f"{c.n_occ}/{len(states)}; ground state (LOBPCG, {t_gs:.1f} s) not timed"),
+                seconds=t)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = W.molecule()
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up effects worth a full sample
+    vals = []
+    samp = None
+    t_total = 0.0
+    for _ in range(max(1, args.steps)):
+        samp = oracle_sample(wl, SAMPLE_STATES[:2] if args.steps > 1 else SAMPLE_STATES)
+        vals.append(samp["value"])
+        t_total += samp["seconds"]
+    v = float(np.median(vals))
+    line = dict(metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * 100.0 / v, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, l2="n/a (CPU)"),
+                cpu_baseline=dict(value=v, unit=UNIT, cores=samp["cores"], kind="oracle", sample=samp["sample"]),
+                e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.p = None
+        return self
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except Exception:
+                continue
+        if not sm:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["unavailable"], samples=0)
+        return dict(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(mx)), reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per column-iteration of each kernel class
+# ---------------------------------------------------------------------------
+def class_bytes(miller, N, npw, nocc, s):
+    """Per column-iteration (and per-launch shared) algorithmic bytes of the
+    inner CG loop kernels; s = bytes per complex value."""
+    n = np.mod(miller, N)
+    D = len({(a, b) for a, b in zip(n[:, 0], n[:, 1])})        # disc pencils
+    P0 = len(set(n[:, 0]))                                     # planes cut by the sphere
+    real = s // 2
+    col = {
+        "z_scatter_inv": 3 * npw * s + D * N * s,
+        "y_inv": D * N * s + P0 * N * N * s,
+        "x_h": 2 * P0 * N * N * s,
+        "y_fwd": P0 * N * N * s + D * N * s,
+        "z_gather_h": D * N * s + 2 * npw * s,
+        "proj": 4 * npw * s,
+        "cg_update": 6 * npw * s,
+    }
+    shared = {
+        "z_scatter_inv": 8 * npw, "y_inv": 0, "x_h": N ** 3 * real, "y_fwd": 0,
+        "z_gather_h": 8 * npw + npw * real, "proj": 2 * nocc * npw * s, "cg_update": 0,
+    }
+    return col, shared, dict(D=D, P0=P0)
+
+
+def src_hash():
+    h = hashlib.sha256()
+    for f in ("fft.cuh", "kernels_fft.cu", "kernels_linalg.cu", "gw_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1408_3036_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_class):
+    """DRAM bytes per column-iteration of a kernel class from a committed ncu
+    summary, if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            t = json.load(f)
+        e = t.get(kernel_class)
+        if e and e.get("src") == src_hash():
+            return e
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = W.molecule()
+    K = args.lanczos_k
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_sample(wl)            # before any CUDA call in this process
+        cpu.pop("seconds", None)
+
+    import torch
+    import paper_1408_3036_gb300 as gw
+    from paper_1408_3036_gb300 import _build
+    from paper_1408_3036_gb300.groundstate import lowest_states
+    _build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    c = wl.cells[0]
+    attempt = 0
+    while True:
+        cell = gw.Cell(c.L, c.N, c.ecut, c.vloc, 0, stream.cuda_stream)
+        eps, psi, res = lowest_states(cell, c.n_occ, tol=1e-10)
+        if res > 1e-8:
+            raise RuntimeError(f"ground state did not converge (residual {res:.2e})")
+        if eps[c.n_occ] - eps[c.n_occ - 1] > 1e-3 or attempt >= 5:
+            break
+        attempt += 1
+        wl = W.molecule(attempt)
+        c = wl.cells[0]
+    cell.set_occupied(psi, eps[:c.n_occ])
+    ng = cell.ng
+    dev = torch.device("cuda", local)
+    start = torch.tensor(wl.starts[0][0], dtype=torch.float64, device=dev)
+    alpha = torch.empty(K, dtype=torch.float64, device=dev)
+    beta = torch.empty(max(K - 1, 1), dtype=torch.float64, device=dev)
+    Q = torch.empty((K, ng), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(prec):
+        gw.gw_lanczos(cell.ctx, start, K, 0.0, alpha, beta, Q, prec)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    prec = gw.GW_MIXED if args.prec == "mixed" else gw.GW_FP64
+    for _ in range(args.warmup):
+        step(prec)
+    # --- timed region: K steps, CUDA events on the work stream, L2 flushed between steps
+    launches0 = gw.gw_stats(cell.ctx)["launches"]
+    times = []
+    it_cols = 0.0
+    cols = 0.0
+    dominant = args.profile_class
+    gw.gw_profile(cell.ctx, 1 << gw.PROFILE_CLASSES.index(dominant))
+    barrier()
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.nvtx.range_push("timed")
+            e0.record(stream)
+            step(prec)
+            e1.record(stream)
+            torch.cuda.nvtx.range_pop()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            st = gw.gw_stats(cell.ctx)
+            it_cols += st["columns"] * st["mean_iter"]
+            cols += st["columns"]
+    barrier()
+    prof = gw.gw_profile_read(cell.ctx)
+    gw.gw_profile(cell.ctx, 0)
+    launches = gw.gw_stats(cell.ctx)["launches"] - launches0
+    stats_last = gw.gw_stats(cell.ctx)
+    total_ms = float(sum(times))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps * K / (total_ms / 1e3)
+    alpha_mixed = alpha.cpu().numpy().copy()
+    beta_mixed = beta[:K - 1].cpu().numpy().copy()
+
+    # --- roofline of the dominant inner-loop kernel (measured live above)
+    miller = cell.sphere()
+    s = 8 if prec == gw.GW_MIXED else 16
+    colb, shared, geo = class_bytes(miller, c.N, cell.npw, c.n_occ, s)
+    ms_dom, n_dom = prof[dominant]
+    alg_bytes = it_cols * colb[dominant] + n_dom * shared[dominant]
+    hbm, hbm_kind = peaks()
+    achieved = alg_bytes / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else None
+    tr = ncu_traffic(dominant)
+    traffic = None
+    if tr is not None and n_dom > 0:
+        traffic = tr["dram_bytes_per_col_iter"] * it_cols / n_dom
+    roofline = dict(bound="hbm", kernel=dominant, achieved=achieved, peak=hbm, unit="GB/s",
+                    frac=(achieved / hbm if achieved else None), peak_kind=hbm_kind,
+                    traffic=traffic, alg_bytes_per_launch=alg_bytes / max(n_dom, 1),
+                    alg_bytes_per_col_iter=colb[dominant], kernel_ms_share=ms_dom / total_ms,
+                    launches=n_dom)
+
+    # --- FP64 path (fewer Lanczos steps: FP64 throughput on GB300 is low)
+    fp64 = None
+    if not args.no_fp64:
+        K64 = min(K, args.fp64_k)
+        a64 = torch.empty(K64, dtype=torch.float64, device=dev)
+        b64 = torch.empty(max(K64 - 1, 1), dtype=torch.float64, device=dev)
+        Q64 = torch.empty((K64, ng), dtype=torch.float64, device=dev)
+        gw.gw_lanczos(cell.ctx, start, K64, 0.0, a64, b64, Q64, gw.GW_FP64)   # warm-up
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gw.gw_lanczos(cell.ctx, start, K64, 0.0, a64, b64, Q64, gw.GW_FP64)
+        e1.record(stream)
+        e1.synchronize()
+        t64 = e0.elapsed_time(e1)
+        a64h, b64h = a64.cpu().numpy(), b64[:K64 - 1].cpu().numpy()
+        st64 = gw.gw_stats(cell.ctx)
+        err_a = float(np.abs(alpha_mixed[:K64] - a64h).max() / np.abs(a64h).max())
+        err_b = float(np.abs(beta_mixed[:K64 - 1] - b64h).max() / np.abs(b64h).max()) if K64 > 1 else 0.0
+        fp64 = dict(value=K64 / (t64 / 1e3), unit=UNIT, lanczos_steps=K64, ms=t64,
+                    mean_iter=st64["mean_iter"], max_iter=st64["max_iter"],
+                    mixed_vs_fp64_rel_err=dict(alpha=err_a, beta=err_b))
+
+    # --- end to end through the C ABI with host buffers (pinned), copies inside the region
+    h_start = torch.tensor(wl.starts[0][0], dtype=torch.float64).pin_memory()
+    h_alpha = torch.empty(K, dtype=torch.float64).pin_memory()
+    h_beta = torch.empty(max(K - 1, 1), dtype=torch.float64).pin_memory()
+    flush.fill_(1.0)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    gw.gw_lanczos(cell.ctx, h_start, K, 0.0, h_alpha, h_beta, None, prec)
+    e1.record(stream)
+    e1.synchronize()
+    te2e = e0.elapsed_time(e1)
+    e2e = dict(value=world * K / (te2e / 1e3), unit=UNIT, h2d_bytes_per_step=ng * 8,
+               d2h_bytes_per_step=(2 * K - 1) * 8)
+
+    if rank == 0:
+        line = dict(
+            metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+            ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+            dtype="f32+f64-refine" if prec == gw.GW_MIXED else "f64", data="synthetic",
+            config=dict(workload=WORKLOAD, parallelism=("replicas" if world > 1 else "single"),
+                        precision=args.prec, lanczos_steps=K,
+                        l2="working set (~14 MB) L2-resident inside a step; L2 flushed (512 MB write) "
+                           "between timed steps",
+                        ground_state_residual=res, gap_homo_lumo=float(eps[c.n_occ] - eps[c.n_occ - 1]),
+                        sternheimer_mean_iter=stats_last["mean_iter"], sternheimer_max_iter=stats_last["max_iter"],
+                        column_iterations_per_step=it_cols / args.steps, geometry=geo),
+            roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
+            clocks=clk.summary(), fp64=fp64, profile_ms={k: v[0] for k, v in prof.items() if v[1]},
+        )
+        print(json.dumps(line))
+    cell.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--lanczos-k", type=int, default=100)
+    ap.add_argument("--fp64-k", type=int, default=10)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-class", default="x_h")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

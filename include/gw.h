@@ -72,7 +72,8 @@ typedef enum { GW_COULOMB_TRUNCATED = 0, GW_COULOMB_BARE = 1 } gw_coulomb;
  *            v(0) = pi L^2 / 2;  GW_COULOMB_BARE: 4 pi / |G|^2, v(0) = 0
  *   cuda_stream  caller stream (cudaStream_t): when non-NULL every kernel of the
  *            context runs on it (a stream that can be captured); when NULL the
- *            context creates a private non-blocking stream
+ *            context creates a private blocking stream, ordered with the
+ *            legacy default stream
  * Returns GW_E_ARG for bad sizes; *out is NULL on failure.
  */
 gw_status gw_setup(gw_ctx** out, double L, int n_grid, double ecut, const double* vloc,
@@ -176,6 +177,19 @@ gw_status gw_stats(const gw_ctx* ctx, double* out, int n);
 /* set solver controls: tol (relative FP64 residual), inner tolerance of the
    mixed path, maximum inner iterations, maximum outer passes */
 gw_status gw_set_solver(gw_ctx* ctx, double tol, double tol_inner, int max_iter, int max_outer);
+
+/*
+ * gw_profile -- time selected kernel classes with CUDA events on the work
+ * stream (one event pair around each launch; mask 0 turns timing off).
+ * Classes: 0 scatter + inverse z pass (with the CG p update), 1 inverse y pass,
+ * 2 x pass with V_loc (H), 3 forward y pass, 4 forward z pass + gather + kinetic
+ * and shift, 5 projector P_c, 6 CG update, 7 FP64 refinement residual
+ * (H apply + P_c), 8 reserved.
+ * gw_profile_read -- per class: total milliseconds and launches since the last
+ * read (synchronises the stream; resets the totals).
+ */
+gw_status gw_profile(gw_ctx* ctx, unsigned mask);
+gw_status gw_profile_read(gw_ctx* ctx, double* ms, long long* count, int n);
 
 const char* gw_last_error(const gw_ctx* ctx);
 void gw_destroy(gw_ctx* ctx);

@@ -139,14 +139,15 @@ def sternheimer_solve(gs, v, shift, b, tol=1e-14, gap=None):
     return project_c(gs, x)
 
 
-def chi0_sternheimer(gs, f, omega, tol=1e-14, gaps=None):
+def chi0_sternheimer(gs, f, omega, tol=1e-14, gaps=None, states=None):
     """chi0 f by Eq. P2: two Sternheimer solves per occupied state (one when
-    omega = 0, where x^- = x^+)."""
+    omega = 0, where x^- = x^+).  ``states`` restricts the sum over occupied
+    states to a subset (a partial sum, for timing samples only)."""
     sph = gs.sph
     vol = sph.omega_vol
     u = gs.u
     out = np.zeros(sph.ng, dtype=np.complex128)
-    for v in range(gs.n_occ):
+    for v in (range(gs.n_occ) if states is None else states):
         b = project_c(gs, sph.to_sphere(np.conj(u[v]) * f))
         gap = None if gaps is None else gaps[v]
         xm = sternheimer_solve(gs, v, -omega, b, tol, gap)

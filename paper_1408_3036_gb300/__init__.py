@@ -25,7 +25,9 @@ STATUS = {0: "GW_OK", 1: "GW_E_ARG", 2: "GW_E_CUDA", 3: "GW_E_NOMEM", 4: "GW_E_N
           5: "GW_E_BREAKDOWN", 6: "GW_E_TIMEOUT", 7: "GW_E_NONFINITE", 8: "GW_E_UNSUPPORTED"}
 EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "gw_apply_chi0",
            "gw_apply_eps", "gw_lanczos", "gw_epsinv_elements", "gw_grad_vloc", "gw_stats",
-           "gw_set_solver", "gw_last_error", "gw_destroy")
+           "gw_set_solver", "gw_profile", "gw_profile_read", "gw_last_error", "gw_destroy")
+PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
+                   "refine_fp64", "other")
 
 
 class GwError(RuntimeError):
@@ -59,6 +61,8 @@ def load(path=LIB_PATH):
         "gw_grad_vloc": (I, [P, P, I, P, P, I, I]),
         "gw_stats": (I, [P, P, I]),
         "gw_set_solver": (I, [P, D, D, I, I]),
+        "gw_profile": (I, [P, ctypes.c_uint]),
+        "gw_profile_read": (I, [P, P, P, I]),
         "gw_last_error": (ctypes.c_char_p, [P]),
         "gw_destroy": (None, [P]),
     }
@@ -191,6 +195,18 @@ def gw_stats(ctx):
 
 def gw_set_solver(ctx, tol=0.0, tol_inner=0.0, max_iter=0, max_outer=0):
     _check(ctx, load().gw_set_solver(ctx, float(tol), float(tol_inner), int(max_iter), int(max_outer)))
+
+
+def gw_profile(ctx, mask):
+    _check(ctx, load().gw_profile(ctx, int(mask)))
+
+
+def gw_profile_read(ctx):
+    n = len(PROFILE_CLASSES)
+    ms = np.zeros(n)
+    cnt = np.zeros(n, dtype=np.int64)
+    _check(ctx, load().gw_profile_read(ctx, ms.ctypes.data, cnt.ctypes.data, n))
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROFILE_CLASSES)}
 
 
 def gw_last_error(ctx):

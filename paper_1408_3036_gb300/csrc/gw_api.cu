@@ -35,11 +35,16 @@ struct gw_ctx {
   std::map<std::string, std::pair<void*, size_t>> bufs;
   Work work;
   size_t work_cols = 0;
-  double tol = 1e-13, tol_mixed = 1e-10, tol_inner = 1e-5;
+  double tol = 1e-13, tol_mixed = 1e-10, tol_inner = 1e-4;
   int max_iter = 20000, max_outer = 12;
   double stats[6] = {0, 0, 0, 0, 0, 0};
   int* host_pin = nullptr;      // pinned scratch for small read-backs
   std::string err;
+  // optional per-kernel-class timing with CUDA events on the work stream
+  unsigned prof_mask = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<int, int>>> ev_used;   // (class, (start, end))
+  size_t ev_next = 0;
 };
 
 namespace {
@@ -102,7 +107,8 @@ gw_status sync(gw_ctx* ctx, const char* where) {
 gw_status ensure_work(gw_ctx* ctx, size_t cols) {
   cols = std::max<size_t>(cols, 64);
   if (cols <= ctx->work_cols) return GW_OK;
-  const size_t nch = (size_t)std::max(ctx->N3, ctx->npw) / 1024 + 2;
+  // enough partial slots for chunks of 1024 grid points and of 256 sphere entries
+  const size_t nch = std::max<size_t>((size_t)ctx->N3 / 1024, (size_t)ctx->npw / 256) + 2;
   const size_t occ = std::max(ctx->nocc, 1);
   TRY(getbuf(ctx, "w_part1", nch * cols, &ctx->work.part1));
   TRY(getbuf(ctx, "w_part2", nch * cols * std::max<size_t>(occ, 1), &ctx->work.part2));
@@ -110,12 +116,51 @@ gw_status ensure_work(gw_ctx* ctx, size_t cols) {
   TRY(getbuf(ctx, "w_cnt_a", cols, &ctx->work.cnt_a));
   TRY(getbuf(ctx, "w_cnt_b", cols, &ctx->work.cnt_b));
   TRY(getbuf(ctx, "w_cnt_c", cols, &ctx->work.cnt_c));
+  TRY(getbuf(ctx, "w_cnt_d", cols, &ctx->work.cnt_d));
+  TRY(getbuf(ctx, "w_part_d", cols * ((size_t)ctx->geo.npen / 16 + 2) * occ, &ctx->work.part_d));
+  CK(cudaMemsetAsync(ctx->work.cnt_d, 0, cols * sizeof(unsigned), ctx->st));
   CK(cudaMemsetAsync(ctx->work.cnt_a, 0, cols * sizeof(unsigned), ctx->st));
   CK(cudaMemsetAsync(ctx->work.cnt_b, 0, cols * sizeof(unsigned), ctx->st));
   CK(cudaMemsetAsync(ctx->work.cnt_c, 0, cols * sizeof(unsigned), ctx->st));
   ctx->work_cols = cols;
   return GW_OK;
 }
+
+
+// ---------------------------------------------------------------------------
+// per-kernel-class timing (gw_profile): an event pair around each launch of a
+// selected class, resolved by gw_profile_read
+// ---------------------------------------------------------------------------
+enum ProfClass { PC_ZSCAT = 0, PC_YINV = 1, PC_XH = 2, PC_YFWD = 3, PC_ZGATH = 4, PC_PROJ = 5, PC_CGUPD = 6,
+                 PC_REFINE = 7, PC_OTHER = 8, PC_N = 9 };
+
+int prof_begin(gw_ctx* ctx, int cls) {
+  if (!(ctx->prof_mask & (1u << cls))) return -1;
+  if (ctx->ev_next + 2 > ctx->ev_pool.size()) {
+    for (int i = 0; i < 256; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      ctx->ev_pool.push_back(e);
+    }
+  }
+  const int a = (int)ctx->ev_next;
+  ctx->ev_next += 2;
+  cudaEventRecord(ctx->ev_pool[a], ctx->st);
+  return a;
+}
+
+void prof_end(gw_ctx* ctx, int cls, int a) {
+  if (a < 0) return;
+  cudaEventRecord(ctx->ev_pool[a + 1], ctx->st);
+  ctx->ev_used.push_back({cls, {a, a + 1}});
+}
+
+#define PROF(cls, stmt)                  \
+  do {                                   \
+    const int pa_ = prof_begin(ctx, cls); \
+    stmt;                                \
+    prof_end(ctx, cls, pa_);             \
+  } while (0)
 
 template <typename T> Prec<T>& prec_of(gw_ctx* ctx);
 template <> Prec<double>& prec_of<double>(gw_ctx* ctx) { return ctx->P64; }
@@ -207,18 +252,26 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
   auto& P = prec_of<T>(ctx);
   const Geometry& g = ctx->geo;
   launch_cg_init<T, double>(ctx->st, npw, ncol, b64, x, r, outer_active, ctx->work, st);
+  GatherDots dots;
+  dots.C = P.C;
+  dots.nocc = ctx->nocc;
+  dots.ncol = ncol;
+  dots.part = ctx->work.part_d;
+  dots.cnt = ctx->work.cnt_d;
+  dots.coef = ctx->work.coef;
   const double tol2 = tol * tol;
   const int check = 8;
   for (int it = 0; it < ctx->max_iter; ++it) {
-    launch_zpass<T>(ctx->st, Z_SCATTER_INV_PUPD, g, P, ctx->plan, grid, p, r, st.beta, nullptr, nullptr,
-                    st.active, nullptr, nullptr, ncol);
-    launch_ypass<T>(ctx->st, 1, 1, 0, g, P, ctx->plan, grid, st.active, ncol, 0);
-    launch_xpass_mul<T>(ctx->st, 1, 1, 1, g, P, ctx->plan, grid, P.vloc_s, st.active, ncol);
-    launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, st.active, ncol, 0);
-    launch_zpass<T>(ctx->st, Z_GATHER_FWD_H, g, P, ctx->plan, grid, Ap, nullptr, nullptr, p, E, st.active,
-                    nullptr, nullptr, ncol);
-    launch_proj<T>(ctx->st, P.C, ctx->nocc, npw, Ap, ncol, st.active, ctx->work, p, pap);
-    launch_cg_update<T>(ctx->st, npw, ncol, x, r, p, Ap, pap, ctx->work, st, tol2, ctx->max_iter);
+    PROF(PC_ZSCAT, launch_zpass<T>(ctx->st, Z_SCATTER_INV_PUPD, g, P, ctx->plan, grid, p, r, st.beta, nullptr,
+                                   nullptr, st.active, nullptr, nullptr, ncol));
+    PROF(PC_YINV, launch_ypass<T>(ctx->st, 1, 1, 0, g, P, ctx->plan, grid, st.active, ncol, 0));
+    PROF(PC_XH, launch_xpass_mul<T>(ctx->st, 1, 1, 1, g, P, ctx->plan, grid, P.vloc_s, st.active, ncol));
+    PROF(PC_YFWD, launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, st.active, ncol, 0));
+    PROF(PC_ZGATH, launch_zpass<T>(ctx->st, Z_GATHER_FWD_H, g, P, ctx->plan, grid, Ap, nullptr, nullptr, p, E,
+                                   st.active, nullptr, nullptr, ncol, &dots));
+    PROF(PC_PROJ, launch_proj_update<T>(ctx->st, P.C, ctx->nocc, npw, Ap, ncol, st.active, ctx->work.coef,
+                                        ctx->work, p, pap));
+    PROF(PC_CGUPD, launch_cg_update<T>(ctx->st, npw, ncol, x, r, p, Ap, pap, ctx->work, st, tol2, ctx->max_iter));
     if ((it % check) == check - 1 || it == ctx->max_iter - 1) {
       CK(cudaMemcpyAsync(ctx->host_pin, st.n_done, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
       TRY(sync(ctx, "cg_solve"));
@@ -232,8 +285,20 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
   for (int c = 0; c < ncol; ++c) {
     *it_sum += its[c];
     *it_max = std::max(*it_max, its[c]);
-    if (flags[c] == 2) return fail(ctx, GW_E_BREAKDOWN, "CG breakdown: operator not positive definite on P_c");
   }
+  // FP32 inner solves of the refinement loop stop at a breakdown (p^H A p
+  // <= 0 from rounding once the FP32 recursion has gone as far as it can);
+  // the FP64 outer residual decides.  In FP64 a breakdown is an error.
+  for (int c = 0; c < ncol; ++c)
+    if (flags[c] == 2 && std::is_same<T, double>::value) {
+      double2 hE;
+      CK(cudaMemcpy(&hE, E + c, sizeof(double2), cudaMemcpyDeviceToHost));
+      char buf[160];
+      std::snprintf(buf, sizeof(buf),
+                    "CG breakdown in column %d (shift E = %.6g) after %d iterations: (H - E) is not positive "
+                    "definite on P_c", c, hE.x, its[c]);
+      return fail(ctx, GW_E_BREAKDOWN, buf);
+    }
   return GW_OK;
 }
 
@@ -270,8 +335,12 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
     TRY(cg_solve<T>(ctx, ncol, r64, E, oact, d, tol_in, &it_sum, &it_max));
     launch_add_conv<T>(ctx->st, npw, ncol, d, x64, oact);
     // r64 = b - P_c (H - E) x64
-    TRY(h_apply<double>(ctx, x64, ncol, E, oact, ax));
-    launch_proj<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, ax, ncol, oact, ctx->work, nullptr, nullptr);
+    {
+      const int pa = prof_begin(ctx, PC_REFINE);
+      TRY(h_apply<double>(ctx, x64, ncol, E, oact, ax));
+      launch_proj<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, ax, ncol, oact, ctx->work, nullptr, nullptr);
+      prof_end(ctx, PC_REFINE, pa);
+    }
     launch_residual(ctx->st, npw, ncol, b64, ax, oact, ctx->work, res2, bb);
     CK(cudaMemcpyAsync(r64, ax, (size_t)ncol * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
     CK(cudaMemcpyAsync(hr.data(), res2, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
@@ -286,9 +355,13 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
       worst = std::max(worst, rel);
       if (rel > tol) ++nact; else act[c] = 0;
     }
-    ctx->stats[4] = std::max(ctx->stats[4], worst);
     if (nact == 0) break;
     TRY(upload(ctx, "sv_oact", act, &oact));
+  }
+  {
+    double fin = 0.0;        // final relative FP64 residual over all columns
+    for (int c = 0; c < ncol; ++c) fin = std::max(fin, hb[c] > 0 ? std::sqrt(hr[c] / hb[c]) : 0.0);
+    ctx->stats[4] = std::max(ctx->stats[4], fin);
   }
   ctx->stats[0] += ncol;
   ctx->stats[1] = std::max<double>(ctx->stats[1], it_max);
@@ -622,7 +695,9 @@ gw_status gw_setup(gw_ctx** out, double L, int n_grid, double ecut, const double
   if (ctx->user) {
     ctx->st = ctx->user;
     ctx->own_stream = false;
-  } else if (cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking) != cudaSuccess) {
+  } else if (cudaStreamCreateWithFlags(&ctx->st, cudaStreamDefault) != cudaSuccess) {
+    // a blocking stream: ordered with the legacy default stream, where callers
+    // without a stream of their own (e.g. torch's default stream) put their work
     return bail(GW_E_CUDA);
   }
   if (cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming) != cudaSuccess) return bail(GW_E_CUDA);
@@ -683,26 +758,55 @@ gw_status gw_set_occupied(gw_ctx* ctx, int n_occ, const double* psi, const doubl
     if (it == where.end()) return fail(ctx, GW_E_ARG, "sphere not symmetric");
     neg[s] = it->second;
   }
-  // Real-in-real-space basis: (K c)_G = conj(c_{-G}).  Shells of equal energy
-  // (|de| < 1e-9 Ha) are re-spanned by the K-symmetric parts (c + Kc)/2 and
-  // (c - Kc)/2i, picked by pivoted Gram-Schmidt; inner products of K-symmetric
-  // vectors are real.
+  // Real-in-real-space basis: (K c)_G = conj(c_{-G}), H K = K H.
+  //  * a state that is K-symmetric up to a phase (|<c|Kc>| ~ 1: the usual,
+  //    non-degenerate case) is multiplied by that phase and its K-symmetric
+  //    part kept;
+  //  * a degenerate shell (consecutive energies within 1e-6 Ha) whose states
+  //    are mixed is re-spanned by the K-symmetric parts (c + Kc)/2 and
+  //    (c - Kc)/2i, picked by pivoted Gram-Schmidt (inner products of
+  //    K-symmetric vectors are real), energies set to the shell mean;
+  //  * finally all states are re-orthonormalised (modified Gram-Schmidt).
+  auto kdot = [&](const zc* c) {       // <c|Kc> = sum_G conj(c_G) conj(c_{-G})
+    zc z = 0.0;
+    for (int s = 0; s < npw; ++s) z += std::conj(c[s]) * std::conj(c[neg[s]]);
+    return z;
+  };
   std::vector<zc> C((size_t)n_occ * npw);
   for (size_t i = 0; i < C.size(); ++i) C[i] = zc(psi[2 * i], psi[2 * i + 1]);
   std::vector<zc> R((size_t)n_occ * npw);
   std::vector<double> e(n_occ);
   int v0 = 0;
   while (v0 < n_occ) {
+    const zc z = kdot(&C[(size_t)v0 * npw]);
+    if (std::abs(z) > 1.0 - 1e-3) {
+      const zc ph = std::exp(zc(0.0, 0.5 * std::arg(z)));   // c = ph^-1 * (K-symmetric)
+      zc* out = &R[(size_t)v0 * npw];
+      for (int s = 0; s < npw; ++s) out[s] = ph * C[(size_t)v0 * npw + s];
+      for (int s = 0; s < npw; ++s)
+        if (neg[s] > s) {
+          const zc a = 0.5 * (out[s] + std::conj(out[neg[s]]));
+          out[s] = a;
+          out[neg[s]] = std::conj(a);
+        } else if (neg[s] == s) {
+          out[s] = zc(out[s].real(), 0.0);
+        }
+      e[v0] = eps[v0];
+      ++v0;
+      continue;
+    }
     int v1 = v0 + 1;
-    while (v1 < n_occ && std::fabs(eps[v1] - eps[v0]) < 1e-9) ++v1;
+    while (v1 < n_occ && std::fabs(eps[v1] - eps[v1 - 1]) < 1e-6) ++v1;
     const int m = v1 - v0;
     std::vector<std::vector<zc>> cand;
+    double norm0 = 0.0;
     for (int v = v0; v < v1; ++v) {
       std::vector<zc> a(npw), b(npw);
       for (int s = 0; s < npw; ++s) {
         const zc c = C[(size_t)v * npw + s], kc = std::conj(C[(size_t)v * npw + neg[s]]);
         a[s] = 0.5 * (c + kc);
         b[s] = (c - kc) / zc(0.0, 2.0);
+        norm0 += std::norm(c);
       }
       cand.push_back(a);
       cand.push_back(b);
@@ -720,7 +824,7 @@ gw_status gw_set_occupied(gw_ctx* ctx, int n_occ, const double* psi, const doubl
         for (int s = 0; s < npw; ++s) n2 += std::norm(cand[j][s]);
         if (n2 > bn) { bn = n2; best = (int)j; }
       }
-      if (best < 0 || bn < 1e-12) return fail(ctx, GW_E_ARG, "occupied space is not closed under conjugation");
+      if (best < 0 || bn < 1e-8) return fail(ctx, GW_E_ARG, "occupied space is not closed under conjugation");
       used[best] = true;
       const double inv = 1.0 / std::sqrt(bn);
       for (int s = 0; s < npw; ++s) cand[best][s] *= inv;
@@ -732,16 +836,31 @@ gw_status gw_set_occupied(gw_ctx* ctx, int n_occ, const double* psi, const doubl
         for (int s = 0; s < npw; ++s) cand[j][s] -= dr * cand[best][s];
       }
       for (int s = 0; s < npw; ++s) R[(size_t)(v0 + k) * npw + s] = cand[best][s];
-      e[v0 + k] = (m == 1) ? eps[v0] : mean;
+      e[v0 + k] = mean;
     }
-    // remaining candidates must be (numerically) in the span
+    // what is left must be (numerically) inside the span of the shell
     for (size_t j = 0; j < cand.size(); ++j) {
       if (used[j]) continue;
       double n2 = 0.0;
       for (int s = 0; s < npw; ++s) n2 += std::norm(cand[j][s]);
-      if (n2 > 1e-10) return fail(ctx, GW_E_ARG, "occupied space is not closed under conjugation");
+      if (n2 > 1e-8 * norm0) return fail(ctx, GW_E_ARG, "occupied space is not closed under conjugation");
     }
     v0 = v1;
+  }
+  for (int v = 0; v < n_occ; ++v) {     // modified Gram-Schmidt (real inner products)
+    zc* a = &R[(size_t)v * npw];
+    for (int u = 0; u < v; ++u) {
+      const zc* b = &R[(size_t)u * npw];
+      zc d = 0.0;
+      for (int s = 0; s < npw; ++s) d += std::conj(b[s]) * a[s];
+      const double dr = d.real();
+      for (int s = 0; s < npw; ++s) a[s] -= dr * b[s];
+    }
+    double n2 = 0.0;
+    for (int s = 0; s < npw; ++s) n2 += std::norm(a[s]);
+    if (!(n2 > 0.5)) return fail(ctx, GW_E_ARG, "occupied states are not orthonormal");
+    const double inv = 1.0 / std::sqrt(n2);
+    for (int s = 0; s < npw; ++s) a[s] *= inv;
   }
   ctx->nocc = n_occ;
   ctx->eps = e;
@@ -917,6 +1036,28 @@ gw_status gw_set_solver(gw_ctx* ctx, double tol, double tol_inner, int max_iter,
   return GW_OK;
 }
 
+gw_status gw_profile(gw_ctx* ctx, unsigned mask) {
+  if (!ctx) return GW_E_ARG;
+  ctx->prof_mask = mask & ((1u << PC_N) - 1u);
+  ctx->ev_used.clear();
+  ctx->ev_next = 0;
+  return GW_OK;
+}
+
+gw_status gw_profile_read(gw_ctx* ctx, double* ms, long long* count, int n) {
+  if (!ctx || !ms || !count || n < 0) return GW_E_ARG;
+  CK(cudaStreamSynchronize(ctx->st));
+  for (int i = 0; i < n; ++i) { ms[i] = 0.0; count[i] = 0; }
+  for (auto& u : ctx->ev_used) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, ctx->ev_pool[u.second.first], ctx->ev_pool[u.second.second]));
+    if (u.first < n) { ms[u.first] += t; count[u.first] += 1; }
+  }
+  ctx->ev_used.clear();
+  ctx->ev_next = 0;
+  return GW_OK;
+}
+
 const char* gw_last_error(const gw_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 void gw_destroy(gw_ctx* ctx) {
@@ -925,6 +1066,7 @@ void gw_destroy(gw_ctx* ctx) {
   for (auto& kv : ctx->bufs)
     if (kv.second.first) cudaFree(kv.second.first);
   if (ctx->host_pin) cudaFreeHost(ctx->host_pin);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->ev) cudaEventDestroy(ctx->ev);
   if (ctx->st && ctx->own_stream) cudaStreamDestroy(ctx->st);
   delete ctx;

@@ -84,6 +84,34 @@ template <typename T> struct Prec {
   cpx<T>* U = nullptr;       // [nocc][N3] u_v(r) = sum_G c_G e^{iGr}
 };
 
+// Deterministic cross-block reduction: every block writes its partial sums,
+// then takes a ticket; the block drawing the last ticket sees all partials
+// (after the fences) and resets the ticket for the next launch.
+__device__ __forceinline__ bool last_block(unsigned* cnt, unsigned nblk) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(cnt, 1u);
+    is_last = (t == nblk - 1);
+    if (is_last) *cnt = 0u;
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+// Projector coefficients fused into a gather pass: coef[v * ncol + col] =
+// <C_v|out_col> = sum_G conj(C[v][G]) out[col][G].
+struct GatherDots {
+  const void* C = nullptr;     // cpx<T> [nocc][npw]
+  int nocc = 0;
+  int ncol = 0;
+  double2* part = nullptr;     // [ncol][blocks per column][nocc]
+  unsigned* cnt = nullptr;     // [ncol] tickets
+  double2* coef = nullptr;     // [nocc][ncol]
+};
+
 // ---------------------------------------------------------------------------
 // kernel launchers (kernels_fft.cu)
 // ---------------------------------------------------------------------------
@@ -95,7 +123,7 @@ template <typename T>
 void launch_zpass(cudaStream_t s, int mode, const Geometry& g, const Prec<T>& P, const FftPlan& pl,
                   cpx<T>* grid, cpx<T>* sph, const cpx<T>* sph_r, const double* beta,
                   const cpx<T>* sph_p, const double2* E, const int* active, const T* real_in,
-                  T* real_out, int ncol);
+                  T* real_out, int ncol, const GatherDots* dots = nullptr);
 template <typename T>
 void launch_ypass(cudaStream_t s, int inverse, int pruned_in, int pruned_out, const Geometry& g,
                   const Prec<T>& P, const FftPlan& pl, cpx<T>* grid, const int* active, int ncol, int full_planes);

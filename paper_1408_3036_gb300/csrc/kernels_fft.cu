@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kThreads)
 k_zpass(int mode, Geometry g, Prec<T> P, FftPlan pl, cpx<T>* __restrict__ grid,
         cpx<T>* __restrict__ sph, const cpx<T>* __restrict__ sph_r, const double* __restrict__ beta,
         const cpx<T>* __restrict__ sph_p, const double2* __restrict__ E, const int* __restrict__ active,
-        const T* __restrict__ real_in, T* __restrict__ real_out) {
+        const T* __restrict__ real_in, T* __restrict__ real_out, GatherDots dots) {
   using V = cpx<T>;
   extern __shared__ unsigned char smem_raw[];
   const int N = g.N, LD = N + 1;
@@ -121,6 +121,38 @@ k_zpass(int mode, Geometry g, Prec<T> P, FftPlan pl, cpx<T>* __restrict__ grid,
       }
       sph[scol + s] = val;
     }
+    if (dots.C) {
+      // <C_v | out> over this tile's sphere entries: one warp per v, lanes over G
+      __syncthreads();
+      const cpx<T>* Cv = reinterpret_cast<const cpx<T>*>(dots.C);
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      const int nblk = gridDim.x;
+      for (int v = warp; v < dots.nocc; v += nw) {
+        T ax = 0, ay = 0;
+        for (int s = s0 + lane; s < s1; s += 32) {
+          const V c = Cv[(size_t)v * g.npw + s];
+          const V y = sph[scol + s];
+          ax += c.x * y.x + c.y * y.y;
+          ay += c.x * y.y - c.y * y.x;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          ax += __shfl_xor_sync(0xffffffffu, ax, o);
+          ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        }
+        if (lane == 0) dots.part[((size_t)col * nblk + blockIdx.x) * dots.nocc + v] = make_double2(ax, ay);
+      }
+      if (last_block(&dots.cnt[col], nblk)) {
+        for (int v = threadIdx.x; v < dots.nocc; v += blockDim.x) {
+          double sx = 0.0, sy = 0.0;
+          for (int b = 0; b < nblk; ++b) {
+            const double2 p = dots.part[((size_t)col * nblk + b) * dots.nocc + v];
+            sx += p.x;
+            sy += p.y;
+          }
+          dots.coef[(size_t)v * dots.ncol + col] = make_double2(sx, sy);
+        }
+      }
+    }
   } else {
     for (int e = threadIdx.x; e < np * N; e += blockDim.x) {
       const int p = e / N, k = e - p * N;
@@ -140,7 +172,7 @@ template <typename T>
 void launch_zpass(cudaStream_t s, int mode, const Geometry& g, const Prec<T>& P, const FftPlan& pl,
                   cpx<T>* grid, cpx<T>* sph, const cpx<T>* sph_r, const double* beta,
                   const cpx<T>* sph_p, const double2* E, const int* active, const T* real_in,
-                  T* real_out, int ncol) {
+                  T* real_out, int ncol, const GatherDots* dots) {
   const bool disc_list = (mode == Z_SCATTER_INV || mode == Z_SCATTER_INV_PUPD || mode == Z_GATHER_FWD ||
                           mode == Z_GATHER_FWD_H);
   const int npen = disc_list ? g.npen : g.N2;
@@ -148,8 +180,10 @@ void launch_zpass(cudaStream_t s, int mode, const Geometry& g, const Prec<T>& P,
   dim3 grd((npen + kP - 1) / kP, ncol);
   const size_t sm = tile_smem<T>(g.N, 2);
   ++g_launches;
+  GatherDots d;
+  if (dots) d = *dots;
   k_zpass<T><<<grd, kThreads, sm, s>>>(mode, g, P, pl, grid, sph, sph_r, beta, sph_p, E, active,
-                                        real_in, real_out);
+                                        real_in, real_out, d);
 }
 
 // ---------------------------------------------------------------------------
@@ -444,7 +478,7 @@ cudaError_t fft_set_smem_limits() {
 #define GW_INST(T)                                                                                         \
   template void launch_zpass<T>(cudaStream_t, int, const Geometry&, const Prec<T>&, const FftPlan&,      \
                                 cpx<T>*, cpx<T>*, const cpx<T>*, const double*, const cpx<T>*,           \
-                                const double2*, const int*, const T*, T*, int);                          \
+                                const double2*, const int*, const T*, T*, int, const GatherDots*);       \
   template void launch_ypass<T>(cudaStream_t, int, int, int, const Geometry&, const Prec<T>&,            \
                                 const FftPlan&, cpx<T>*, const int*, int, int);                          \
   template void launch_xpass_mul<T>(cudaStream_t, int, int, int, const Geometry&, const Prec<T>&,        \

@@ -19,20 +19,6 @@ constexpr int kLT = 256;   // threads per block
 constexpr int kChunk = 1024; // sphere / grid entries per block in vector kernels
 constexpr int kCT = 8;     // columns per block in the projector dots
 
-__device__ __forceinline__ bool last_block(unsigned* cnt, unsigned nblk) {
-  __shared__ bool is_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned t = atomicAdd(cnt, 1u);
-    is_last = (t == nblk - 1);
-    if (is_last) *cnt = 0u;
-  }
-  __syncthreads();
-  if (is_last) __threadfence();
-  return is_last;
-}
-
 template <typename R>
 __device__ __forceinline__ R block_sum(R v) {
   __shared__ R sh[32];
@@ -52,6 +38,8 @@ __device__ __forceinline__ R block_sum(R v) {
 // ---------------------------------------------------------------------------
 // P_c y = y - sum_v c_v <c_v|y>: coefficients (a) then update (b).
 // ---------------------------------------------------------------------------
+constexpr int kChunkP = 256;  // sphere entries per block in the projector coefficients
+
 // (a) coef[v * ncol + b] = sum_G conj(C[v][G]) Y[b][G]; grid (nchunk, ceil(ncol / kCT))
 template <typename T>
 __global__ void __launch_bounds__(kLT)
@@ -59,35 +47,35 @@ k_proj_dots(const cpx<T>* __restrict__ C, int nocc, int npw, const cpx<T>* __res
             const int* __restrict__ active, double2* __restrict__ partial, unsigned* __restrict__ cnt,
             double2* __restrict__ coef) {
   const int nchunk = gridDim.x;
-  const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
+  const int g0 = blockIdx.x * kChunkP, g1 = min(npw, g0 + kChunkP);
   const int b0 = blockIdx.y * kCT;
   const int nb = min(kCT, ncol - b0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
   for (int v = warp; v < nocc; v += nw) {
-    double2 acc[kCT];
+    T ax[kCT], ay[kCT];
 #pragma unroll
-    for (int j = 0; j < kCT; ++j) acc[j] = make_double2(0, 0);
+    for (int j = 0; j < kCT; ++j) { ax[j] = 0; ay[j] = 0; }
     for (int G = g0 + lane; G < g1; G += 32) {
-      const double2 c = to_d(C[(size_t)v * npw + G]);
+      const cpx<T> c = C[(size_t)v * npw + G];
 #pragma unroll
       for (int j = 0; j < kCT; ++j) {
         if (j < nb) {
-          const double2 y = to_d(Y[(size_t)(b0 + j) * npw + G]);
-          acc[j].x += c.x * y.x + c.y * y.y;
-          acc[j].y += c.x * y.y - c.y * y.x;
+          const cpx<T> y = Y[(size_t)(b0 + j) * npw + G];
+          ax[j] += c.x * y.x + c.y * y.y;
+          ay[j] += c.x * y.y - c.y * y.x;
         }
       }
     }
 #pragma unroll
     for (int j = 0; j < kCT; ++j) {
-      double ax = acc[j].x, ay = acc[j].y;
+      double sx = ax[j], sy = ay[j];
       for (int o = 16; o > 0; o >>= 1) {
-        ax += __shfl_xor_sync(0xffffffffu, ax, o);
-        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
       }
       if (lane == 0 && j < nb)
-        partial[((size_t)blockIdx.x * nocc + v) * ncol + b0 + j] = make_double2(ax, ay);
+        partial[((size_t)blockIdx.x * nocc + v) * ncol + b0 + j] = make_double2(sx, sy);
     }
   }
   if (!last_block(&cnt[blockIdx.y], nchunk)) return;
@@ -102,35 +90,33 @@ k_proj_dots(const cpx<T>* __restrict__ C, int nocc, int npw, const cpx<T>* __res
   }
 }
 
-// (b) Y[b] -= sum_v C[v] coef[v][b]; optionally pap[b] = Re <P[b]|Y[b]> (new Y).
-// grid (nchunk, ncol)
+// (b) Y[b] -= sum_v C[v] coef[v][b] (precision T); optionally pap[b] = Re <P[b]|Y[b]> (new Y),
+// accumulated in FP64.  grid (nchunk, ncol)
 template <typename T>
 __global__ void __launch_bounds__(kLT)
 k_proj_update(const cpx<T>* __restrict__ C, int nocc, int npw, cpx<T>* __restrict__ Y, int ncol,
               const int* __restrict__ active, const double2* __restrict__ coef,
               const cpx<T>* __restrict__ Pv, double* __restrict__ partial, unsigned* __restrict__ cnt,
               double* __restrict__ pap) {
-  __shared__ double2 sc[kMaxOcc];
+  __shared__ cpx<T> sc[kMaxOcc];
   const int b = blockIdx.y;
   if (active && !active[b]) return;
-  for (int v = threadIdx.x; v < nocc; v += blockDim.x) sc[v] = coef[(size_t)v * ncol + b];
+  for (int v = threadIdx.x; v < nocc; v += blockDim.x) sc[v] = from_d<T>(coef[(size_t)v * ncol + b]);
   __syncthreads();
   const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
   double acc = 0.0;
   for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
-    double2 y = to_d(Y[(size_t)b * npw + G]);
+    cpx<T> y = Y[(size_t)b * npw + G];
     for (int v = 0; v < nocc; ++v) {
-      const double2 c = to_d(C[(size_t)v * npw + G]);
-      const double2 a = sc[v];
+      const cpx<T> c = C[(size_t)v * npw + G];
+      const cpx<T> a = sc[v];
       y.x -= c.x * a.x - c.y * a.y;
       y.y -= c.x * a.y + c.y * a.x;
     }
-    const cpx<T> yo = from_d<T>(y);
-    Y[(size_t)b * npw + G] = yo;
+    Y[(size_t)b * npw + G] = y;
     if (Pv) {
-      const double2 p = to_d(Pv[(size_t)b * npw + G]);
-      const double2 yd = to_d(yo);
-      acc += p.x * yd.x + p.y * yd.y;
+      const cpx<T> p = Pv[(size_t)b * npw + G];
+      acc += (double)(p.x * y.x + p.y * y.y);
     }
   }
   if (!Pv) return;
@@ -148,13 +134,21 @@ template <typename T>
 void launch_proj(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, int ncol, const int* active,
                  Work& w, const cpx<T>* Pv, double* pap) {
   if (ncol == 0 || nocc == 0) return;
-  const int nchunk = (npw + kChunk - 1) / kChunk;
+  const int nchunk = (npw + kChunkP - 1) / kChunkP;
   dim3 g1(nchunk, (ncol + kCT - 1) / kCT);
   ++g_launches;
   k_proj_dots<T><<<g1, kLT, 0, s>>>(C, nocc, npw, Y, ncol, active, w.part2, w.cnt_a, w.coef);
+  launch_proj_update<T>(s, C, nocc, npw, Y, ncol, active, w.coef, w, Pv, pap);
+}
+
+template <typename T>
+void launch_proj_update(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, int ncol,
+                        const int* active, const double2* coef, Work& w, const cpx<T>* Pv, double* pap) {
+  if (ncol == 0 || nocc == 0) return;
+  const int nchunk = (npw + kChunk - 1) / kChunk;
   dim3 g2(nchunk, ncol);
   ++g_launches;
-  k_proj_update<T><<<g2, kLT, 0, s>>>(C, nocc, npw, Y, ncol, active, w.coef, Pv, w.part1, w.cnt_b, pap);
+  k_proj_update<T><<<g2, kLT, 0, s>>>(C, nocc, npw, Y, ncol, active, coef, Pv, w.part1, w.cnt_b, pap);
 }
 
 // ---------------------------------------------------------------------------
@@ -495,6 +489,8 @@ void launch_tridiag_inv(cudaStream_t s, int K, const double* alpha, const double
 }
 
 #define GW_LINST(T)                                                                                        \
+  template void launch_proj_update<T>(cudaStream_t, const cpx<T>*, int, int, cpx<T>*, int, const int*,     \
+                                      const double2*, Work&, const cpx<T>*, double*);                      \
   template void launch_proj<T>(cudaStream_t, const cpx<T>*, int, int, cpx<T>*, int, const int*, Work&,     \
                                const cpx<T>*, double*);                                                    \
   template void launch_cg_init<T, double>(cudaStream_t, int, int, const double2*, cpx<T>*, cpx<T>*,       \

@@ -15,6 +15,8 @@ struct Work {
   unsigned* cnt_a = nullptr;  // tickets (zero between launches)
   unsigned* cnt_b = nullptr;
   unsigned* cnt_c = nullptr;
+  unsigned* cnt_d = nullptr;  // tickets of the dots fused into the gather pass
+  double2* part_d = nullptr;  // their partial sums
 };
 
 // Per-column state of a batched CG solve (device arrays).
@@ -32,6 +34,9 @@ struct CgState {
 template <typename T>
 void launch_proj(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, int ncol, const int* active,
                  Work& w, const cpx<T>* Pv, double* pap);
+template <typename T>
+void launch_proj_update(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, int ncol,
+                        const int* active, const double2* coef, Work& w, const cpx<T>* Pv, double* pap);
 template <typename T, typename U>
 void launch_cg_init(cudaStream_t s, int npw, int ncol, const cpx<U>* b, cpx<T>* x, cpx<T>* r,
                     const int* outer_active, Work& w, CgState st);
