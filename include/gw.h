@@ -174,8 +174,18 @@ gw_status gw_grad_vloc(gw_ctx* ctx, const double* phi, int k, double* s, double*
  */
 gw_status gw_stats(const gw_ctx* ctx, double* out, int n);
 
-/* set solver controls: tol (relative FP64 residual), inner tolerance of the
-   mixed path, maximum inner iterations, maximum outer passes */
+/*
+ * gw_set_solver -- Sternheimer solver controls (0 or negative keeps a value):
+ *   tol        normwise backward error |b - A x| / (|A| |x| + |b|) that every
+ *              column must reach, measured in FP64 (default 1e-13 for GW_FP64;
+ *              the mixed path uses max(tol, 1e-13), default 1e-11); a pass
+ *              that does not halve the error ends the refinement when the error
+ *              is already within 10 tol (round-off and input-accuracy floor)
+ *   tol_inner  relative residual at which each FP32 inner CG pass of the mixed
+ *              path stops before the next FP64 residual (default 1e-4)
+ *   max_iter   inner CG iterations per pass;  max_outer  FP64 residual passes
+ * The paper solves Eq. P2 until |A x - b|^2 < 1e-20 Ha^2 (Sec. Results).
+ */
 gw_status gw_set_solver(gw_ctx* ctx, double tol, double tol_inner, int max_iter, int max_outer);
 
 /*

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -35,7 +36,9 @@ struct gw_ctx {
   std::map<std::string, std::pair<void*, size_t>> bufs;
   Work work;
   size_t work_cols = 0;
-  double tol = 1e-13, tol_mixed = 1e-10, tol_inner = 1e-4;
+  double tol = 1e-13, tol_mixed = 1e-11, tol_inner = 1e-4;   // backward errors (FP64 / mixed), inner
+  double anorm = 1.0;           // bound on |H - E| used by the backward error
+  double vmax = 0.0;            // max |V_loc|
   int max_iter = 20000, max_outer = 12;
   double stats[6] = {0, 0, 0, 0, 0, 0};
   int* host_pin = nullptr;      // pinned scratch for small read-backs
@@ -227,7 +230,7 @@ gw_status h_apply(gw_ctx* ctx, cpx<T>* x, int ncol, const double2* E, const int*
 // ---------------------------------------------------------------------------
 template <typename T>
 gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, const int* outer_active,
-                   cpx<T>* x, double tol, long long* it_sum, int* it_max) {
+                   cpx<T>* x, double tol, const double* rr_abs, long long* it_sum, int* it_max) {
   const int npw = ctx->npw;
   const std::string t = tname<T>();
   cpx<T>*r, *p, *Ap, *grid;
@@ -246,12 +249,15 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
   TRY(getbuf(ctx, "cg_active", ncol, &st.active));
   TRY(getbuf(ctx, "cg_ndone", 1, &st.n_done));
   TRY(getbuf(ctx, "cg_cnt", ncol, &st.cnt));
+  TRY(getbuf(ctx, "cg_rrstop", ncol, &st.rr_stop));
+  TRY(getbuf(ctx, "cg_rrmin", ncol, &st.rr_min));
+  st.rr_abs = rr_abs;
   TRY(ensure_work(ctx, ncol));
   CK(cudaMemsetAsync(st.cnt, 0, ncol * sizeof(unsigned), ctx->st));
   CK(cudaMemsetAsync(st.n_done, 0, sizeof(int), ctx->st));
   auto& P = prec_of<T>(ctx);
   const Geometry& g = ctx->geo;
-  launch_cg_init<T, double>(ctx->st, npw, ncol, b64, x, r, outer_active, ctx->work, st);
+  launch_cg_init<T, double>(ctx->st, npw, ncol, b64, x, r, outer_active, ctx->work, st, tol * tol, 0.0);
   GatherDots dots;
   dots.C = P.C;
   dots.nocc = ctx->nocc;
@@ -272,10 +278,37 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
     PROF(PC_PROJ, launch_proj_update<T>(ctx->st, P.C, ctx->nocc, npw, Ap, ncol, st.active, ctx->work.coef,
                                         ctx->work, p, pap));
     PROF(PC_CGUPD, launch_cg_update<T>(ctx->st, npw, ncol, x, r, p, Ap, pap, ctx->work, st, tol2, ctx->max_iter));
+    if (const char* tr = std::getenv("GW_DEBUG_TRACE")) {   // per-iteration trace of one column
+      const int tc = std::atoi(tr);
+      if (tc >= 0 && tc < ncol) {
+        double v3[3];
+        CK(cudaMemcpyAsync(v3, st.rr + tc, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(v3 + 1, pap + tc, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(v3 + 2, st.rr0 + tc, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        TRY(sync(ctx, "trace"));
+        std::fprintf(stderr, "trace it %d rel %.3e pap %.6e\n", it, std::sqrt(v3[0] / v3[2]), v3[1]);
+      }
+    }
     if ((it % check) == check - 1 || it == ctx->max_iter - 1) {
       CK(cudaMemcpyAsync(ctx->host_pin, st.n_done, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
       TRY(sync(ctx, "cg_solve"));
       if (ctx->host_pin[0] >= ncol) break;
+    }
+  }
+  if (std::getenv("GW_DEBUG_TICKETS")) {       // all tickets must be back at zero
+    TRY(sync(ctx, "tickets"));
+    const size_t wc = ctx->work_cols;
+    std::vector<unsigned> t(wc);
+    const unsigned* arrs[4] = {ctx->work.cnt_a, ctx->work.cnt_b, ctx->work.cnt_d, st.cnt};
+    const size_t lens[4] = {wc, wc, wc, (size_t)ncol};
+    for (int a = 0; a < 4; ++a) {
+      CK(cudaMemcpy(t.data(), arrs[a], lens[a] * sizeof(unsigned), cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < lens[a]; ++i)
+        if (t[i]) {
+          char buf[128];
+          std::snprintf(buf, sizeof(buf), "ticket array %d entry %zu left at %u", a, i, t[i]);
+          return fail(ctx, GW_E_CUDA, buf);
+        }
     }
   }
   std::vector<int> its(ncol), flags(ncol);
@@ -292,11 +325,15 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
   for (int c = 0; c < ncol; ++c)
     if (flags[c] == 2 && std::is_same<T, double>::value) {
       double2 hE;
+      double hrr = 0, hrr0 = 0, hpap = 0;
       CK(cudaMemcpy(&hE, E + c, sizeof(double2), cudaMemcpyDeviceToHost));
-      char buf[160];
+      CK(cudaMemcpy(&hrr, st.rr + c, sizeof(double), cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(&hrr0, st.rr0 + c, sizeof(double), cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(&hpap, pap + c, sizeof(double), cudaMemcpyDeviceToHost));
+      char buf[256];
       std::snprintf(buf, sizeof(buf),
-                    "CG breakdown in column %d (shift E = %.6g) after %d iterations: (H - E) is not positive "
-                    "definite on P_c", c, hE.x, its[c]);
+                    "CG breakdown in column %d (shift E = %.6g) after %d iterations (|r|^2 = %.3e of %.3e, "
+                    "p^H A p = %.3e): (H - E) is not positive definite on P_c", c, hE.x, its[c], hrr, hrr0, hpap);
       return fail(ctx, GW_E_BREAKDOWN, buf);
     }
   return GW_OK;
@@ -304,35 +341,42 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
 
 // ---------------------------------------------------------------------------
 // Sternheimer solves with FP64 iterative refinement:
-//   x64 = 0; repeat { d = CG_T(b - A64 x64); x64 += d } until |b - A64 x64| <= tol |b|
+//   x64 = 0; repeat { d = CG_T(b - A64 x64); x64 += d } until the normwise
+//   backward error |b - A64 x64| / (|A| |x64| + |b|) <= tol for every column.
+// |A| is bounded by max |G|^2/2 + max |V| + max |E| (set with the occupied
+// states).  Each inner solve stops at tol_inner relative to its own right-hand
+// side, or at a tenth of the final target, whichever is larger.
 // ---------------------------------------------------------------------------
 template <typename T>
 gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, double2* x64) {
   const int npw = ctx->npw;
   const bool mixed = !std::is_same<T, double>::value;
   const double tol = mixed ? ctx->tol_mixed : ctx->tol;
-  const double tol_in = mixed ? ctx->tol_inner : ctx->tol;
+  const double tol_in = mixed ? ctx->tol_inner : std::max(1e2 * ctx->tol, 1e-11);
   double2 *r64, *ax;
   cpx<T>* d;
   int* oact;
-  double *res2, *bb;
+  double *res2, *bb, *xx, *rra;
   TRY(getbuf(ctx, "sv_r64", (size_t)ncol * npw, &r64));
   TRY(getbuf(ctx, "sv_ax", (size_t)ncol * npw, &ax));
   TRY(getbuf(ctx, std::string("sv_d") + tname<T>(), (size_t)ncol * npw, &d));
   TRY(getbuf(ctx, "sv_oact", ncol, &oact));
   TRY(getbuf(ctx, "sv_res2", ncol, &res2));
   TRY(getbuf(ctx, "sv_bb", ncol, &bb));
+  TRY(getbuf(ctx, "sv_xx", ncol, &xx));
   TRY(ensure_work(ctx, ncol));
   CK(cudaMemsetAsync(x64, 0, (size_t)ncol * npw * sizeof(double2), ctx->st));
   CK(cudaMemcpyAsync(r64, b64, (size_t)ncol * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
   std::vector<int> act(ncol, 1);
   TRY(upload(ctx, "sv_oact", act, &oact));
+  std::vector<double> hr(ncol, 0.0), hb(ncol, 0.0), hx(ncol, 0.0), habs(ncol, 0.0);
+  TRY(upload(ctx, "sv_rra", habs, &rra));
   long long it_sum = 0;
   int it_max = 0, outer = 0;
-  double worst = 0.0;
-  std::vector<double> hr(ncol), hb(ncol);
-  for (outer = 0; outer < ctx->max_outer; ++outer) {
-    TRY(cg_solve<T>(ctx, ncol, r64, E, oact, d, tol_in, &it_sum, &it_max));
+  bool done = false;
+  double prev_worst = 1e300;
+  for (outer = 0; outer < ctx->max_outer && !done; ++outer) {
+    TRY(cg_solve<T>(ctx, ncol, r64, E, oact, d, tol_in, rra, &it_sum, &it_max));
     launch_add_conv<T>(ctx->st, npw, ncol, d, x64, oact);
     // r64 = b - P_c (H - E) x64
     {
@@ -341,34 +385,89 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
       launch_proj<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, ax, ncol, oact, ctx->work, nullptr, nullptr);
       prof_end(ctx, PC_REFINE, pa);
     }
-    launch_residual(ctx->st, npw, ncol, b64, ax, oact, ctx->work, res2, bb);
+    launch_residual(ctx->st, npw, ncol, b64, ax, x64, oact, ctx->work, res2, bb, xx);
     CK(cudaMemcpyAsync(r64, ax, (size_t)ncol * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
+    if (const char* dv = std::getenv("GW_DEBUG_VAL")) {      // valence content of the FP64 residual
+      const int tc = std::atoi(dv);
+      if (tc >= 0 && tc < ncol) {
+        double2* tmp;
+        TRY(getbuf(ctx, "dbg_tmp", (size_t)ncol * npw, &tmp));
+        CK(cudaMemcpyAsync(tmp, r64, (size_t)ncol * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
+        launch_proj<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, tmp, ncol, nullptr, ctx->work, nullptr, nullptr);
+        std::vector<double2> cf((size_t)ctx->nocc * ncol);
+        CK(cudaMemcpyAsync(cf.data(), ctx->work.coef, cf.size() * sizeof(double2), cudaMemcpyDeviceToHost, ctx->st));
+        TRY(sync(ctx, "dbg"));
+        double vn = 0.0;
+        for (int v = 0; v < ctx->nocc; ++v) vn += cf[(size_t)v * ncol + tc].x * cf[(size_t)v * ncol + tc].x +
+                                                  cf[(size_t)v * ncol + tc].y * cf[(size_t)v * ncol + tc].y;
+        double rr = 0.0;
+        CK(cudaMemcpy(&rr, res2 + tc, sizeof(double), cudaMemcpyDeviceToHost));
+        std::fprintf(stderr, "outer %d column %d |r| %.3e valence part %.3e\n", outer, tc, std::sqrt(rr),
+                     std::sqrt(vn));
+        std::vector<double2> hv((size_t)npw), hx2((size_t)npw);
+        CK(cudaMemcpy(hv.data(), r64 + (size_t)tc * npw, npw * sizeof(double2), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(hx2.data(), x64 + (size_t)tc * npw, npw * sizeof(double2), cudaMemcpyDeviceToHost));
+        char fn[64];
+        std::snprintf(fn, sizeof(fn), "gpurun_out/dbg_r_%d.bin", outer);
+        if (FILE* f = std::fopen(fn, "wb")) { std::fwrite(hv.data(), sizeof(double2), npw, f); std::fclose(f); }
+        std::snprintf(fn, sizeof(fn), "gpurun_out/dbg_x_%d.bin", outer);
+        if (FILE* f = std::fopen(fn, "wb")) { std::fwrite(hx2.data(), sizeof(double2), npw, f); std::fclose(f); }
+      }
+    }
     CK(cudaMemcpyAsync(hr.data(), res2, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaMemcpyAsync(hb.data(), bb, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(hx.data(), xx, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     TRY(sync(ctx, "solve"));
     int nact = 0;
-    worst = 0.0;
     for (int c = 0; c < ncol; ++c) {
       if (!act[c]) continue;
-      const double rel = hb[c] > 0 ? std::sqrt(hr[c] / hb[c]) : 0.0;
-      if (!std::isfinite(rel)) return fail(ctx, GW_E_NONFINITE, "non-finite Sternheimer residual");
-      worst = std::max(worst, rel);
-      if (rel > tol) ++nact; else act[c] = 0;
+      const double scale = ctx->anorm * std::sqrt(hx[c]) + std::sqrt(hb[c]);
+      const double be = scale > 0 ? std::sqrt(hr[c]) / scale : 0.0;
+      if (!std::isfinite(be)) return fail(ctx, GW_E_NONFINITE, "non-finite Sternheimer residual");
+      habs[c] = 0.01 * tol * tol * scale * scale;
+      if (be > tol) ++nact; else act[c] = 0;
     }
-    if (nact == 0) break;
-    TRY(upload(ctx, "sv_oact", act, &oact));
+    // stagnation: a pass that does not halve the worst backward error ends the
+    // refinement (accepted within 10x of the target: the floor set by rounding
+    // and by the accuracy of the occupied states)
+    double worst = 0.0;
+    for (int c = 0; c < ncol; ++c) {
+      const double scale = ctx->anorm * std::sqrt(hx[c]) + std::sqrt(hb[c]);
+      if (act[c] && scale > 0) worst = std::max(worst, std::sqrt(hr[c]) / scale);
+    }
+    done = (nact == 0) || (outer > 0 && worst > 0.5 * prev_worst && worst <= 10.0 * tol);
+    prev_worst = worst;
+    if (!done) {
+      TRY(upload(ctx, "sv_oact", act, &oact));
+      TRY(upload(ctx, "sv_rra", habs, &rra));
+    }
   }
   {
-    double fin = 0.0;        // final relative FP64 residual over all columns
+    double fin = 0.0;        // final relative FP64 residual |b - A x| / |b| over all columns
     for (int c = 0; c < ncol; ++c) fin = std::max(fin, hb[c] > 0 ? std::sqrt(hr[c] / hb[c]) : 0.0);
     ctx->stats[4] = std::max(ctx->stats[4], fin);
   }
   ctx->stats[0] += ncol;
   ctx->stats[1] = std::max<double>(ctx->stats[1], it_max);
   ctx->stats[2] += (double)it_sum;
-  ctx->stats[3] = std::max<double>(ctx->stats[3], outer + 1);
-  ctx->stats[5] += (double)it_sum + ncol * (outer + 1);
-  if (outer >= ctx->max_outer) return fail(ctx, GW_E_NOCONV, "Sternheimer solve did not converge");
+  ctx->stats[3] = std::max<double>(ctx->stats[3], outer);
+  ctx->stats[5] += (double)it_sum + ncol * outer;
+  if (!done) {
+    int wc = -1;
+    double wbe = -1.0;
+    for (int c = 0; c < ncol; ++c) {
+      if (!act[c]) continue;
+      const double scale = ctx->anorm * std::sqrt(hx[c]) + std::sqrt(hb[c]);
+      const double be = scale > 0 ? std::sqrt(hr[c]) / scale : 0.0;
+      if (be > wbe) { wbe = be; wc = c; }
+    }
+    char buf[256];
+    std::snprintf(buf, sizeof(buf),
+                  "Sternheimer solve did not converge: column %d backward error %.3e (tol %.1e), |r|/|b| = %.3e, "
+                  "|x|/|b| = %.3e after %d passes", wc, wbe, tol,
+                  wc >= 0 ? std::sqrt(hr[wc] / hb[wc]) : 0.0, wc >= 0 ? std::sqrt(hx[wc] / hb[wc]) : 0.0, outer);
+    return fail(ctx, GW_E_NOCONV, buf);
+  }
   return GW_OK;
 }
 
@@ -406,6 +505,9 @@ gw_status chi0_core(gw_ctx* ctx, const T* y, int nb, const std::vector<double>& 
   launch_zpass<T>(ctx->st, Z_GATHER_FWD, g, P, ctx->plan, grid, rs, nullptr, nullptr, nullptr, nullptr, nullptr,
                   nullptr, nullptr, nr);
   launch_gather_rows<double, T>(ctx->st, npw, nr, rs, nullptr, rhs64);
+  // P_c twice: psi_v* y has a large component along the occupied states
+  // (e.g. <psi_v|y psi_v>), and one pass leaves |C C^H - 1| times it behind
+  launch_proj<double>(ctx->st, ctx->P64.C, nocc, npw, rhs64, nr, nullptr, ctx->work, nullptr, nullptr);
   launch_proj<double>(ctx->st, ctx->P64.C, nocc, npw, rhs64, nr, nullptr, ctx->work, nullptr, nullptr);
   TRY(launch_check(ctx, "rhs"));
   // -- solver columns
@@ -710,6 +812,7 @@ gw_status gw_setup(gw_ctx** out, double L, int n_grid, double ecut, const double
   const int N = n_grid;
   const double gg = 2.0 * M_PI / L, Rc = 0.5 * L;
   std::vector<double> v(vloc, vloc + ctx->N3), sqv(ctx->N3);
+  for (double x : v) ctx->vmax = std::max(ctx->vmax, std::fabs(x));
   for (int i0 = 0; i0 < N; ++i0)
     for (int i1 = 0; i1 < N; ++i1)
       for (int i2 = 0; i2 < N; ++i2) {
@@ -847,10 +950,10 @@ gw_status gw_set_occupied(gw_ctx* ctx, int n_occ, const double* psi, const doubl
     }
     v0 = v1;
   }
-  for (int v = 0; v < n_occ; ++v) {     // modified Gram-Schmidt (real inner products)
+  for (int v = 0; v < n_occ; ++v) {     // modified Gram-Schmidt, twice (real inner products)
     zc* a = &R[(size_t)v * npw];
-    for (int u = 0; u < v; ++u) {
-      const zc* b = &R[(size_t)u * npw];
+    for (int u2 = 0; u2 < 2 * v; ++u2) {
+      const zc* b = &R[(size_t)(u2 % v) * npw];
       zc d = 0.0;
       for (int s = 0; s < npw; ++s) d += std::conj(b[s]) * a[s];
       const double dr = d.real();
@@ -864,6 +967,12 @@ gw_status gw_set_occupied(gw_ctx* ctx, int n_occ, const double* psi, const doubl
   }
   ctx->nocc = n_occ;
   ctx->eps = e;
+  {
+    double kmax = 0.0, emax = 0.0;
+    for (double k : ctx->kin) kmax = std::max(kmax, k);
+    for (double x : e) emax = std::max(emax, std::fabs(x));
+    ctx->anorm = kmax + ctx->vmax + emax;
+  }
   ctx->work_cols = 0;
   std::vector<double2> c64((size_t)n_occ * npw);
   std::vector<float2> c32((size_t)n_occ * npw);
@@ -872,6 +981,12 @@ gw_status gw_set_occupied(gw_ctx* ctx, int n_occ, const double* psi, const doubl
     c32[i] = make_float2((float)R[i].real(), (float)R[i].imag());
   }
   TRY(upload(ctx, "occ_C64", c64, &ctx->P64.C));
+  if (std::getenv("GW_DEBUG_VAL")) {
+    if (FILE* f = std::fopen("gpurun_out/dbg_C64.bin", "wb")) {
+      std::fwrite(c64.data(), sizeof(double2), c64.size(), f);
+      std::fclose(f);
+    }
+  }
   TRY(upload(ctx, "occ_C32", c32, &ctx->P32.C));
   // u_v(r) = sum_G c_G e^{iGr}: scatter, inverse transforms (FP64), then FP32 copy
   double2* U;
@@ -1029,7 +1144,7 @@ gw_status gw_stats(const gw_ctx* ctx, double* out, int n) {
 
 gw_status gw_set_solver(gw_ctx* ctx, double tol, double tol_inner, int max_iter, int max_outer) {
   if (!ctx) return GW_E_ARG;
-  if (tol > 0) { ctx->tol = tol; ctx->tol_mixed = std::max(tol, 1e-12); }
+  if (tol > 0) { ctx->tol = tol; ctx->tol_mixed = std::max(tol, 1e-13); }
   if (tol_inner > 0) ctx->tol_inner = tol_inner;
   if (max_iter > 0) ctx->max_iter = max_iter;
   if (max_outer > 0) ctx->max_outer = max_outer;

@@ -159,7 +159,7 @@ template <typename T, typename U>
 __global__ void __launch_bounds__(kLT)
 k_cg_init(int npw, const cpx<U>* __restrict__ b, cpx<T>* __restrict__ x, cpx<T>* __restrict__ r,
           const int* __restrict__ outer_active, double* __restrict__ partial, unsigned* __restrict__ cnt,
-          CgState st, int ncol) {
+          CgState st, int ncol, double tol_in2, double tol_abs2) {
   const int c = blockIdx.y;
   const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
   double acc = 0.0;
@@ -180,6 +180,10 @@ k_cg_init(int npw, const cpx<U>* __restrict__ b, cpx<T>* __restrict__ x, cpx<T>*
     for (int k = 0; k < (int)gridDim.x; ++k) s += partial[(size_t)k * ncol + c];
     st.rr[c] = s;
     st.rr0[c] = s;
+    st.rr_min[c] = s;
+    // relative target of this pass, but never below what the refinement needs
+    // overall (a fraction of the final tolerance on the original right-hand side)
+    st.rr_stop[c] = fmax(tol_in2 * s, st.rr_abs ? st.rr_abs[c] : tol_abs2 * s);
     st.beta[c] = -1.0;
     st.iters[c] = 0;
     st.flag[c] = 0;
@@ -223,8 +227,10 @@ k_cg_update(int npw, cpx<T>* __restrict__ x, cpx<T>* __restrict__ r, const cpx<T
     st.beta[c] = s / st.rr[c];
     st.rr[c] = s;
     bool stop = false;
+    st.rr_min[c] = fmin(st.rr_min[c], s);
     if (!(pp > 0.0) || !isfinite(s)) { st.flag[c] = 2; stop = true; }     // breakdown / not SPD
-    else if (s <= tol2 * st.rr0[c]) { st.flag[c] = 0; stop = true; }
+    else if (s <= st.rr_stop[c]) { st.flag[c] = 0; stop = true; }
+    else if (s > 1e4 * st.rr_min[c]) { st.flag[c] = 3; stop = true; }      // past the round-off floor
     else if (it >= maxit) { st.flag[c] = 1; stop = true; }
     if (stop) { st.active[c] = 0; atomicAdd(st.n_done, 1); }
   }
@@ -232,10 +238,10 @@ k_cg_update(int npw, cpx<T>* __restrict__ x, cpx<T>* __restrict__ r, const cpx<T
 
 template <typename T, typename U>
 void launch_cg_init(cudaStream_t s, int npw, int ncol, const cpx<U>* b, cpx<T>* x, cpx<T>* r,
-                    const int* outer_active, Work& w, CgState st) {
+                    const int* outer_active, Work& w, CgState st, double tol_in2, double tol_abs2) {
   dim3 g((npw + kChunk - 1) / kChunk, ncol);
   ++g_launches;
-  k_cg_init<T, U><<<g, kLT, 0, s>>>(npw, b, x, r, outer_active, w.part1, st.cnt, st, ncol);
+  k_cg_init<T, U><<<g, kLT, 0, s>>>(npw, b, x, r, outer_active, w.part1, st.cnt, st, ncol, tol_in2, tol_abs2);
 }
 
 template <typename T>
@@ -271,15 +277,15 @@ void launch_add_conv(cudaStream_t s, int npw, int ncol, const cpx<T>* d, double2
   k_add_conv<T><<<g, kLT, 0, s>>>((size_t)npw, d, x, active);
 }
 
-// r = b - Ax (in place over Ax), res2[c] = |r|^2, bb[c] = |b|^2
+// r = b - Ax (in place over Ax), res2[c] = |r|^2, bb[c] = |b|^2, xx[c] = |x|^2
 __global__ void __launch_bounds__(kLT)
-k_residual(int npw, const double2* __restrict__ b, double2* __restrict__ ax, const int* __restrict__ active,
-           double2* __restrict__ partial, unsigned* __restrict__ cnt, double* __restrict__ res2,
-           double* __restrict__ bb, int ncol) {
+k_residual(int npw, const double2* __restrict__ b, double2* __restrict__ ax, const double2* __restrict__ x,
+           const int* __restrict__ active, double* __restrict__ partial, unsigned* __restrict__ cnt,
+           double* __restrict__ res2, double* __restrict__ bb, double* __restrict__ xx, int ncol) {
   const int c = blockIdx.y;
   if (active && !active[c]) return;
   const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
-  double a1 = 0.0, a2 = 0.0;
+  double a1 = 0.0, a2 = 0.0, a3 = 0.0;
   for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
     const size_t i = (size_t)c * npw + G;
     const double2 bv = b[i];
@@ -289,27 +295,34 @@ k_residual(int npw, const double2* __restrict__ b, double2* __restrict__ ax, con
     ax[i] = r;
     a1 += r.x * r.x + r.y * r.y;
     a2 += bv.x * bv.x + bv.y * bv.y;
+    if (x) { const double2 xv = x[i]; a3 += xv.x * xv.x + xv.y * xv.y; }
   }
   a1 = block_sum(a1);
   a2 = block_sum(a2);
-  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ncol + c] = make_double2(a1, a2);
+  a3 = block_sum(a3);
+  if (threadIdx.x == 0) {
+    double* pp = partial + 3 * ((size_t)blockIdx.x * ncol + c);
+    pp[0] = a1; pp[1] = a2; pp[2] = a3;
+  }
   if (!last_block(&cnt[c], gridDim.x)) return;
   if (threadIdx.x == 0) {
-    double s1 = 0.0, s2 = 0.0;
+    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
     for (int k = 0; k < (int)gridDim.x; ++k) {
-      const double2 p = partial[(size_t)k * ncol + c];
-      s1 += p.x; s2 += p.y;
+      const double* pp = partial + 3 * ((size_t)k * ncol + c);
+      s1 += pp[0]; s2 += pp[1]; s3 += pp[2];
     }
     res2[c] = s1;
     bb[c] = s2;
+    if (xx) xx[c] = s3;
   }
 }
 
-void launch_residual(cudaStream_t s, int npw, int ncol, const double2* b, double2* ax, const int* active,
-                     Work& w, double* res2, double* bb) {
+void launch_residual(cudaStream_t s, int npw, int ncol, const double2* b, double2* ax, const double2* x,
+                     const int* active, Work& w, double* res2, double* bb, double* xx) {
   dim3 g((npw + kChunk - 1) / kChunk, ncol);
   ++g_launches;
-  k_residual<<<g, kLT, 0, s>>>(npw, b, ax, active, w.part2, w.cnt_b, res2, bb, ncol);
+  k_residual<<<g, kLT, 0, s>>>(npw, b, ax, x, active, reinterpret_cast<double*>(w.part2), w.cnt_b, res2, bb,
+                                xx, ncol);
 }
 
 // ---------------------------------------------------------------------------
@@ -494,7 +507,7 @@ void launch_tridiag_inv(cudaStream_t s, int K, const double* alpha, const double
   template void launch_proj<T>(cudaStream_t, const cpx<T>*, int, int, cpx<T>*, int, const int*, Work&,     \
                                const cpx<T>*, double*);                                                    \
   template void launch_cg_init<T, double>(cudaStream_t, int, int, const double2*, cpx<T>*, cpx<T>*,       \
-                                          const int*, Work&, CgState);                                     \
+                                          const int*, Work&, CgState, double, double);                     \
   template void launch_cg_update<T>(cudaStream_t, int, int, cpx<T>*, cpx<T>*, const cpx<T>*,              \
                                     const cpx<T>*, const double*, Work&, CgState, double, int);           \
   template void launch_add_conv<T>(cudaStream_t, int, int, const cpx<T>*, double2*, const int*);

@@ -25,8 +25,11 @@ struct CgState {
   double* rr0 = nullptr;    // |b|^2
   double* beta = nullptr;   // next p = r + beta p (beta < 0: p = r)
   int* iters = nullptr;
-  int* flag = nullptr;      // 0 converged, 1 max iterations, 2 breakdown
+  int* flag = nullptr;      // 0 converged, 1 max iterations, 2 breakdown, 3 diverging (round-off floor)
   int* active = nullptr;
+  double* rr_stop = nullptr;  // stop when |r|^2 <= rr_stop
+  double* rr_min = nullptr;   // smallest |r|^2 seen (divergence guard)
+  const double* rr_abs = nullptr;   // per-column absolute |r|^2 target of the refinement
   int* n_done = nullptr;    // columns that stopped (atomic)
   unsigned* cnt = nullptr;  // tickets [ncol]
 };
@@ -39,14 +42,14 @@ void launch_proj_update(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<
                         const int* active, const double2* coef, Work& w, const cpx<T>* Pv, double* pap);
 template <typename T, typename U>
 void launch_cg_init(cudaStream_t s, int npw, int ncol, const cpx<U>* b, cpx<T>* x, cpx<T>* r,
-                    const int* outer_active, Work& w, CgState st);
+                    const int* outer_active, Work& w, CgState st, double tol_in2, double tol_abs2);
 template <typename T>
 void launch_cg_update(cudaStream_t s, int npw, int ncol, cpx<T>* x, cpx<T>* r, const cpx<T>* p,
                       const cpx<T>* Ap, const double* pap, Work& w, CgState st, double tol2, int maxit);
 template <typename T>
 void launch_add_conv(cudaStream_t s, int npw, int ncol, const cpx<T>* d, double2* x, const int* active);
-void launch_residual(cudaStream_t s, int npw, int ncol, const double2* b, double2* ax, const int* active,
-                     Work& w, double* res2, double* bb);
+void launch_residual(cudaStream_t s, int npw, int ncol, const double2* b, double2* ax, const double2* x,
+                     const int* active, Work& w, double* res2, double* bb, double* xx);
 void launch_combine(cudaStream_t s, int npw, int nout, const double2* in, const int* src0, const int* src1,
                     double w_pair, double w_single, double2* out);
 template <typename T, typename U>
