@@ -106,4 +106,52 @@ __device__ cpx<T>* fft_tile(cpx<T>* a, cpx<T>* b, int npen, int ld, const FftPla
   return a;
 }
 
+// Generalised tile FFT: npen pencils, pencil p element k at buf[p * ps + k * es].
+// PFAST selects the thread mapping: consecutive threads take consecutive
+// pencils (PFAST, for pencils adjacent in memory: es > 1, ps = 1) or
+// consecutive butterflies of one pencil (contiguous pencils: es = 1).
+template <typename T, int SIGN, bool PFAST>
+__device__ cpx<T>* fft_tile2(cpx<T>* a, cpx<T>* b, int npen, int ps, int es, const FftPlan& pl,
+                             const cpx<T>* tw) {
+  using V = cpx<T>;
+  const int N = pl.N;
+  int Ns = 1;
+  for (int s = 0; s < pl.nst; ++s) {
+    const int r = pl.rad[s];
+    const int nb = N / r;
+    const int tstep = N / (Ns * r);
+    const int total = npen * nb;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      int p, j;
+      if (PFAST) { j = t / npen; p = t - j * npen; }
+      else { p = t / nb; j = t - p * nb; }
+      const int k = j % Ns;
+      const V* src = a + p * ps;
+      V* dst = b + p * ps;
+      V v[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        if (q < r) {
+          V x = src[(j + q * nb) * es];
+          if (q > 0 && k > 0) {
+            V w = tw[k * q * tstep];
+            if (SIGN > 0) w.y = -w.y;
+            x = cmul(x, w);
+          }
+          v[q] = x;
+        }
+      }
+      butterfly<T, SIGN>(v, r);
+      const int base = (j / Ns) * Ns * r + k;
+#pragma unroll
+      for (int q = 0; q < 5; ++q)
+        if (q < r) dst[(base + q * Ns) * es] = v[q];
+    }
+    __syncthreads();
+    V* t = a; a = b; b = t;
+    Ns *= r;
+  }
+  return a;
+}
+
 }  // namespace gw

@@ -38,6 +38,10 @@ struct gw_ctx {
   size_t work_cols = 0;
   double tol = 1e-13, tol_mixed = 1e-11, tol_inner = 1e-4;   // backward errors (FP64 / mixed), inner
   double anorm = 1.0;           // bound on |H - E| used by the backward error
+  bool no_persistent = false;   // force the multi-launch CG (tests)
+  long long pcg_iters = 0;      // iterations run by persistent launches
+  int pcg_launch_blocks = 0;
+  bool ptime_init = false;
   double vmax = 0.0;            // max |V_loc|
   int max_iter = 20000, max_outer = 12;
   double stats[6] = {0, 0, 0, 0, 0, 0};
@@ -340,6 +344,75 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
 }
 
 // ---------------------------------------------------------------------------
+// the same CG pass as cg_solve in one cooperative launch (kernels_cg.cu)
+// ---------------------------------------------------------------------------
+template <typename T>
+gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, const int* outer_active,
+                              cpx<T>* x, double tol, const double* rr_abs, long long* it_sum, int* it_max) {
+  const int npw = ctx->npw;
+  const std::string t = tname<T>();
+  const int nchunk = (npw + 1023) / 1024;
+  cpx<T>*r, *p, *Ap, *grid;
+  TRY(getbuf(ctx, "cg_r" + t, (size_t)ncol * npw, &r));
+  TRY(getbuf(ctx, "cg_p" + t, (size_t)ncol * npw, &p));
+  TRY(getbuf(ctx, "cg_Ap" + t, (size_t)ncol * npw, &Ap));
+  TRY(getbuf(ctx, "g_cg" + t, (size_t)ncol * ctx->N3, &grid));
+  double2* dpart;
+  double *ppart, *rpart, *rr_out;
+  unsigned* bar;
+  int *err, *iters, *flags;
+  TRY(getbuf(ctx, "pcg_dpart", (size_t)ncol * ctx->geo.nplanes * ctx->nocc, &dpart));
+  TRY(getbuf(ctx, "pcg_ppart", (size_t)ncol * nchunk, &ppart));
+  TRY(getbuf(ctx, "pcg_rpart", (size_t)ncol * nchunk, &rpart));
+  TRY(getbuf(ctx, "pcg_rr", ncol, &rr_out));
+  TRY(getbuf(ctx, "pcg_bar", 1, &bar));
+  TRY(getbuf(ctx, "pcg_err", 1, &err));
+  TRY(getbuf(ctx, "pcg_iters", ncol, &iters));
+  TRY(getbuf(ctx, "pcg_flags", ncol, &flags));
+  CK(cudaMemsetAsync(bar, 0, sizeof(unsigned), ctx->st));
+  CK(cudaMemsetAsync(err, 0, sizeof(int), ctx->st));
+  int used = 0;
+  const int pa = prof_begin(ctx, PC_XH);
+  unsigned long long* ptime = nullptr;
+  if (std::getenv("GW_DEBUG_PHASES")) {
+    TRY(getbuf(ctx, "pcg_ptime", 8, &ptime));
+    if (!ctx->ptime_init) {
+      CK(cudaMemsetAsync(ptime, 0, 8 * sizeof(unsigned long long), ctx->st));
+      ctx->ptime_init = true;
+    }
+  }
+  CK(launch_cg_persistent<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), ctx->nocc, npw, ncol, b64, outer_active,
+                             E, rr_abs, tol * tol, ctx->max_iter, x, r, p, Ap, grid, dpart, ppart, rpart, bar, err,
+                             iters, flags, rr_out, &used, ptime));
+  if (ptime) {
+    unsigned long long h[8];
+    CK(cudaMemcpyAsync(h, ptime, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
+    TRY(sync(ctx, "ptime"));
+    std::fprintf(stderr, "phases(ms) A %.2f B %.2f C %.2f D %.2f E %.2f conv %.2f  blocks %d\n", h[0] * 1e-6,
+                 h[1] * 1e-6, h[2] * 1e-6, h[3] * 1e-6, h[4] * 1e-6, h[5] * 1e-6, used);
+  }
+  prof_end(ctx, PC_XH, pa);
+  std::vector<int> its(ncol), fl(ncol);
+  int herr = 0;
+  CK(cudaMemcpyAsync(its.data(), iters, ncol * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(fl.data(), flags, ncol * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  TRY(sync(ctx, "cg_persistent"));
+  if (herr) return fail(ctx, GW_E_TIMEOUT, "persistent CG: a grid barrier timed out");
+  int imax = 0;
+  for (int c = 0; c < ncol; ++c) {
+    *it_sum += its[c];
+    *it_max = std::max(*it_max, its[c]);
+    imax = std::max(imax, its[c]);
+    if (fl[c] == 2 && std::is_same<T, double>::value)
+      return fail(ctx, GW_E_BREAKDOWN, "CG breakdown: (H - E) is not positive definite on P_c");
+  }
+  ctx->pcg_iters += imax;       // iterations of the whole launch (bounded by the slowest column)
+  ctx->pcg_launch_blocks = used;
+  return GW_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Sternheimer solves with FP64 iterative refinement:
 //   x64 = 0; repeat { d = CG_T(b - A64 x64); x64 += d } until the normwise
 //   backward error |b - A64 x64| / (|A| |x64| + |b|) <= tol for every column.
@@ -376,7 +449,10 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
   bool done = false;
   double prev_worst = 1e300;
   for (outer = 0; outer < ctx->max_outer && !done; ++outer) {
-    TRY(cg_solve<T>(ctx, ncol, r64, E, oact, d, tol_in, rra, &it_sum, &it_max));
+    if (ncol <= kPersistentMaxCols && !ctx->no_persistent)
+      TRY(cg_solve_persistent<T>(ctx, ncol, r64, E, oact, d, tol_in, rra, &it_sum, &it_max));
+    else
+      TRY(cg_solve<T>(ctx, ncol, r64, E, oact, d, tol_in, rra, &it_sum, &it_max));
     launch_add_conv<T>(ctx->st, npw, ncol, d, x64, oact);
     // r64 = b - P_c (H - E) x64
     {
@@ -476,12 +552,16 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
 //   rhs_{v,b}   = P_c Sphere(FFT(conj(u_v) y_b))
 //   x_{o,b,v,s} = (H - e_v - s omega_o)^-1 rhs   (s = +/-; one solve at omega = 0)
 //   dn_{o,b}    = -(2/Omega) sum_v u_v IFFT(x^- + x^+)
+// The right-hand sides and the density reduction (a few transforms per
+// column) run in FP64; the Sternheimer solves (hundreds of H applications per
+// column) run with inner precision S and FP64 refinement.
 // ---------------------------------------------------------------------------
-template <typename T>
-gw_status chi0_core(gw_ctx* ctx, const T* y, int nb, const std::vector<double>& omega, T* dn) {
+template <typename S>
+gw_status chi0_core(gw_ctx* ctx, const double* y, int nb, const std::vector<double>& omega, double* dn) {
+  using T = double;
   const int npw = ctx->npw, nocc = ctx->nocc, N3 = ctx->N3;
   const int nom = (int)omega.size();
-  auto& P = prec_of<T>(ctx);
+  auto& P = ctx->P64;
   const Geometry& g = ctx->geo;
   const std::string t = tname<T>();
   // -- right-hand sides
@@ -539,7 +619,7 @@ gw_status chi0_core(gw_ctx* ctx, const T* y, int nb, const std::vector<double>& 
   TRY(getbuf(ctx, "xcol", (size_t)ncol * npw, &xcol));
   TRY(getbuf(ctx, "sol64", (size_t)nsol * npw, &sol64));
   launch_gather_rows<double, double>(ctx->st, npw, ncol, rhs64, dsrc, bcol);
-  TRY(solve<T>(ctx, ncol, bcol, dE, xcol));
+  TRY(solve<S>(ctx, ncol, bcol, dE, xcol));
   // -- combine: x^- + x^+, or 2 x at omega = 0 (x^- = x^+)
   launch_combine(ctx->st, npw, nsol, xcol, ds0, ds1, 1.0, 2.0, sol64);
   // -- density reduction
@@ -561,43 +641,22 @@ gw_status chi0_core(gw_ctx* ctx, const T* y, int nb, const std::vector<double>& 
   return launch_check(ctx, "chi0");
 }
 
-template <typename T>
+template <typename S>
 gw_status eps_core(gw_ctx* ctx, const double* x64, int nb, const std::vector<double>& omega, double* out64,
                    bool chi0_only) {
   const int N3 = ctx->N3;
   const int nom = (int)omega.size();
-  const std::string t = tname<T>();
-  const T* xT;
-  if (std::is_same<T, double>::value) {
-    xT = reinterpret_cast<const T*>(x64);
-  } else {
-    T* tmp;
-    TRY(getbuf(ctx, "eps_x" + t, (size_t)nb * N3, &tmp));
-    conv_real<double, T>(ctx->st, (size_t)nb * N3, x64, tmp);
-    xT = tmp;
-  }
-  T* y;
-  T* dn;
-  TRY(getbuf(ctx, "eps_y" + t, (size_t)nb * N3, &y));
-  TRY(getbuf(ctx, "eps_dn" + t, (size_t)nom * nb * N3, &dn));
   if (chi0_only) {
-    TRY(chi0_core<T>(ctx, xT, nb, omega, dn));
-    if (std::is_same<T, double>::value)
-      CK(cudaMemcpyAsync(out64, dn, (size_t)nom * nb * N3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
-    else
-      conv_real<T, double>(ctx->st, (size_t)nom * nb * N3, dn, out64);
+    TRY(chi0_core<S>(ctx, x64, nb, omega, out64));
     return launch_check(ctx, "chi0 out");
   }
-  TRY(sqrtv<T>(ctx, xT, nb, y, nullptr));
-  TRY(chi0_core<T>(ctx, y, nb, omega, dn));
-  T* o;
-  TRY(getbuf(ctx, "eps_o" + t, (size_t)nom * nb * N3, &o));
+  double *y, *dn;
+  TRY(getbuf(ctx, "eps_y", (size_t)nb * N3, &y));
+  TRY(getbuf(ctx, "eps_dn", (size_t)nom * nb * N3, &dn));
+  TRY(sqrtv<double>(ctx, x64, nb, y, nullptr));
+  TRY(chi0_core<S>(ctx, y, nb, omega, dn));
   for (int k = 0; k < nom; ++k)
-    TRY(sqrtv<T>(ctx, dn + (size_t)k * nb * N3, nb, o + (size_t)k * nb * N3, xT));
-  if (std::is_same<T, double>::value)
-    CK(cudaMemcpyAsync(out64, o, (size_t)nom * nb * N3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
-  else
-    conv_real<T, double>(ctx->st, (size_t)nom * nb * N3, o, out64);
+    TRY(sqrtv<double>(ctx, dn + (size_t)k * nb * N3, nb, out64 + (size_t)k * nb * N3, x64));
   return launch_check(ctx, "eps out");
 }
 
@@ -730,6 +789,18 @@ gw_status build_geometry(gw_ctx* ctx) {
     allp[i] = i;
     if (pmask[i]) planes.push_back(i);
   }
+  // first sphere entry / disc pencil of every plane (sphere order is i0-major)
+  std::vector<int> plane_sph, plane_pen, i1s(ctx->npw);
+  for (size_t pi = 0; pi < planes.size(); ++pi) {
+    int s0 = -1, p0 = -1;
+    for (size_t k = 0; k < pencils.size(); ++k)
+      if (pencils[k].x == planes[pi]) { p0 = (int)k; s0 = pencils[k].z; break; }
+    plane_sph.push_back(s0);
+    plane_pen.push_back(p0);
+  }
+  plane_sph.push_back(ctx->npw);
+  plane_pen.push_back((int)pencils.size());
+  for (int s = 0; s < ctx->npw; ++s) i1s[s] = pencils[pen[s]].y;
   Geometry& g = ctx->geo;
   g.N = N; g.N2 = N * N; g.N3 = N * N * N; g.npw = ctx->npw;
   g.npen = (int)pencils.size();
@@ -742,6 +813,9 @@ gw_status build_geometry(gw_ctx* ctx) {
   TRY(upload(ctx, "geo_planes", planes, &g.planes));
   TRY(upload(ctx, "geo_allp", allp, &g.all_planes));
   TRY(upload(ctx, "geo_pmask", pmask, &g.plane_mask));
+  TRY(upload(ctx, "geo_plane_sph", plane_sph, &g.plane_sph));
+  TRY(upload(ctx, "geo_plane_pen", plane_pen, &g.plane_pen));
+  TRY(upload(ctx, "geo_i1", i1s, &g.sph_i1));
   return GW_OK;
 }
 
@@ -804,6 +878,7 @@ gw_status gw_setup(gw_ctx** out, double L, int n_grid, double ecut, const double
   }
   if (cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming) != cudaSuccess) return bail(GW_E_CUDA);
   if (cudaMallocHost(&ctx->host_pin, 64) != cudaSuccess) return bail(GW_E_CUDA);
+  if (const char* e = std::getenv("GW_MULTI_LAUNCH_CG")) ctx->no_persistent = (e[0] == '1');
   if (fft_set_smem_limits<double>() != cudaSuccess || fft_set_smem_limits<float>() != cudaSuccess)
     return bail(GW_E_CUDA);
   gw_status s = build_geometry(ctx);

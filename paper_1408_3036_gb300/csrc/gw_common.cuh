@@ -70,6 +70,9 @@ struct Geometry {
   uint8_t* disc = nullptr; // [N2] 1 where pencil (i0, i1) holds sphere points
   uint8_t* ones = nullptr; // [N2] all ones
   int* planes = nullptr;   // [nplanes] i0 values
+  int* plane_sph = nullptr;  // [nplanes + 1] first sphere entry of each plane (entries are i0-major)
+  int* plane_pen = nullptr;  // [nplanes + 1] first disc pencil of each plane
+  int* sph_i1 = nullptr;     // [npw] y index of each sphere point
   int* all_planes = nullptr; // [N] 0..N-1
   uint8_t* plane_mask = nullptr; // [N]
 };

@@ -1,0 +1,501 @@
+// Persistent conjugate-gradient solver for the Sternheimer equations
+// (Eq. P2: (H - e_v -/+ w) x = P_c psi_v* dV, projected on the conduction
+// space at every step as in Sec. Avoiding summations).
+//
+// One cooperative launch runs a whole CG pass for every column (occupied
+// state x field x frequency) with per-column convergence masks.  The CTAs are
+// all resident and step through five phases per iteration, separated by a
+// grid barrier (bounded spin: a barrier that waits too long sets an error flag
+// and every CTA returns):
+//   A  per (column, plane i0): p = r + beta p on the plane's sphere entries,
+//      scatter, z-IFFT of the disc rows, y-IFFT of the plane (all in shared
+//      memory), store the plane
+//   B  per (column, i1, 16 i2): x-IFFT, * V(r)/N_g, x-FFT (planes of the sphere)
+//   C  per (column, plane): y-FFT, z-FFT of the disc rows, gather the sphere
+//      entries, Ap = (Vp)_G + (|G|^2/2 - E) p_G, partial <C_v|Ap> of the plane
+//   D  per (column, 1024 entries): coef = sum of the plane partials,
+//      Ap -= C coef (P_c), partial p^H Ap
+//   E  per (column, 1024 entries): alpha = rr / p^H Ap, x += alpha p,
+//      r -= alpha Ap, partial |r|^2
+// After E every CTA sums the partials of every column in the same order, so
+// all CTAs take the same convergence decisions without another barrier.
+#include <algorithm>
+#include <cstdio>
+
+#include "fft.cuh"
+#include "gw_common.cuh"
+#include "linalg.cuh"
+
+namespace gw {
+
+constexpr int kPT = 256;        // threads per CTA
+constexpr int kPChunk = 1024;   // sphere entries per task in phases D and E
+constexpr int kPX = 16;         // i2 width of a phase-B tile
+constexpr unsigned kSpinLimit = 1u << 24;
+
+template <typename T>
+struct PcgArgs {
+  Geometry g;
+  FftPlan pl;
+  const cpx<T>* tw;
+  const T* kin;
+  const T* vloc_s;
+  const cpx<T>* C;
+  int nocc, npw, ncol, nchunk;
+  const double2* b64;
+  const int* outer_active;
+  const double2* E;
+  const double* rr_abs;
+  double tol_in2;
+  int maxit;
+  cpx<T>* x;
+  cpx<T>* r;
+  cpx<T>* p;
+  cpx<T>* Ap;
+  cpx<T>* grid;
+  double2* dpart;   // [ncol][nplanes][nocc]
+  double* ppart;    // [ncol][nchunk]
+  double* rpart;    // [ncol][nchunk]
+  unsigned* bar;
+  int* err;
+  int* iters_out;
+  int* flag_out;
+  double* rr_out;
+  unsigned long long* ptime;   // optional [8]: ns spent per phase, measured by CTA 0
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned nblk) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned old = atomicAdd(bar, 1u);
+    const unsigned target = (old / nblk + 1u) * nblk;
+    unsigned spins = 0;
+    int good = 1;
+    while (*(volatile unsigned*)bar < target) {
+      if (*(volatile int*)err) { good = 0; break; }
+      if (++spins > kSpinLimit) { atomicExch(err, 1); good = 0; break; }
+      __nanosleep(64);
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ double dsum_block(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
+  return r;   // thread 0
+}
+
+struct PcgLayout {
+  size_t dbl, ints, red, coef, tw, A, B, total;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline PcgLayout pcg_layout(int N, int ncol, int nocc, int vsize) {
+  PcgLayout L;
+  L.dbl = 0;
+  L.ints = align16(L.dbl + (size_t)4 * ncol * sizeof(double));
+  L.red = align16(L.ints + (size_t)(3 * ncol + N) * sizeof(int));
+  L.coef = align16(L.red + 32 * sizeof(double));
+  L.tw = align16(L.coef + (size_t)nocc * 2 * sizeof(double));
+  L.A = align16(L.tw + (size_t)N * vsize);
+  L.B = align16(L.A + (size_t)N * (N + 1) * vsize);
+  L.total = align16(L.B + (size_t)N * (N + 1) * vsize);
+  return L;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
+  using V = cpx<T>;
+  extern __shared__ unsigned char smem_raw[];
+  const Geometry& g = a.g;
+  const int N = g.N, LDp = N + 1;
+  const int ncol = a.ncol;
+  // ---- shared memory: column state, then the FFT work area (offsets: pcg_layout)
+  const PcgLayout L = pcg_layout(N, ncol, a.nocc, (int)sizeof(V));
+  double* st_rr = reinterpret_cast<double*>(smem_raw + L.dbl);
+  double* st_min = st_rr + ncol;
+  double* st_stop = st_min + ncol;
+  double* st_beta = st_stop + ncol;
+  int* st_act = reinterpret_cast<int*>(smem_raw + L.ints);
+  int* st_it = st_act + ncol;
+  int* st_flag = st_it + ncol;
+  int* rowmap = st_flag + ncol;                               // [N]
+  double* red = reinterpret_cast<double*>(smem_raw + L.red);  // [32] block sums
+  double2* coef = reinterpret_cast<double2*>(smem_raw + L.coef);  // [nocc]
+  V* stw = reinterpret_cast<V*>(smem_raw + L.tw);             // [N]
+  V* A = reinterpret_cast<V*>(smem_raw + L.A);                // [N][LDp]
+  V* B = reinterpret_cast<V*>(smem_raw + L.B);                // [N][LDp]
+  __shared__ double bcast;
+
+  for (int k = threadIdx.x; k < N; k += blockDim.x) stw[k] = a.tw[k];
+  const unsigned nblk = gridDim.x;
+  const int npl = g.nplanes;
+
+  // ---- phase 0: r = b, x = 0, partial |b|^2
+  for (int task = blockIdx.x; task < ncol * a.nchunk; task += gridDim.x) {
+    const int c = task / a.nchunk, ch = task - c * a.nchunk;
+    const bool on = !a.outer_active || a.outer_active[c];
+    const int g0 = ch * kPChunk, g1 = min(a.npw, g0 + kPChunk);
+    double acc = 0.0;
+    for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
+      const size_t i = (size_t)c * a.npw + G;
+      const V bv = on ? from_d<T>(a.b64[i]) : mk<T>(0, 0);
+      a.r[i] = bv;
+      a.x[i] = mk<T>(0, 0);
+      const double2 bd = to_d(bv);
+      acc += bd.x * bd.x + bd.y * bd.y;
+    }
+    acc = dsum_block<T>(acc, red);
+    if (threadIdx.x == 0) a.rpart[(size_t)c * a.nchunk + ch] = acc;
+  }
+  if (!grid_barrier(a.bar, a.err, nblk)) return;
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < a.nchunk; ++k) s += a.rpart[(size_t)c * a.nchunk + k];
+    const bool on = !a.outer_active || a.outer_active[c];
+    st_rr[c] = s;
+    st_min[c] = s;
+    st_stop[c] = fmax(a.tol_in2 * s, a.rr_abs ? a.rr_abs[c] : 0.0);
+    st_beta[c] = -1.0;
+    st_act[c] = (on && s > 0.0) ? 1 : 0;
+    st_it[c] = 0;
+    st_flag[c] = 0;
+  }
+  __syncthreads();
+
+  unsigned long long tprev = gtimer();
+  auto mark = [&](int ph) {
+    if (a.ptime && blockIdx.x == 0 && threadIdx.x == 0) {
+      const unsigned long long t = gtimer();
+      a.ptime[ph] += t - tprev;
+      tprev = t;
+    }
+  };
+  for (int it = 0; it < a.maxit; ++it) {
+    int any = 0;
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) any |= st_act[c];
+    if (!__syncthreads_or(any)) break;
+
+    // ---- phase A: p update, scatter, z-IFFT (disc rows), y-IFFT (plane)
+    for (int task = blockIdx.x; task < ncol * npl; task += gridDim.x) {
+      const int c = task / npl, pi = task - c * npl;
+      if (!st_act[c]) continue;
+      const int i0 = g.planes[pi];
+      const int s0 = g.plane_sph[pi], s1 = g.plane_sph[pi + 1];
+      const int q0 = g.plane_pen[pi], npp = g.plane_pen[pi + 1] - q0;
+      const double bt = st_beta[c];
+      const size_t sc = (size_t)c * a.npw;
+      for (int e = threadIdx.x; e < npp * LDp; e += blockDim.x) A[e] = mk<T>(0, 0);
+      for (int k = threadIdx.x; k < N; k += blockDim.x) rowmap[k] = -1;
+      __syncthreads();
+      for (int k = threadIdx.x; k < npp; k += blockDim.x) rowmap[g.pencils[q0 + k].y] = k;
+      for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        const V rv = a.r[sc + s];
+        V val = rv;
+        if (bt >= 0.0) {
+          const V pv = a.p[sc + s];
+          val = mk<T>(rv.x + (T)bt * pv.x, rv.y + (T)bt * pv.y);
+        }
+        a.p[sc + s] = val;
+        A[(g.sph_pen[s] - q0) * LDp + g.sph_i2[s]] = val;
+      }
+      __syncthreads();
+      V* R = fft_tile2<T, +1, false>(A, B, npp, LDp, 1, a.pl, stw);
+      V* Q = (R == A) ? B : A;
+      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int i1 = e / N, i2 = e - i1 * N;
+        const int k = rowmap[i1];
+        Q[i1 * LDp + i2] = (k >= 0) ? R[k * LDp + i2] : mk<T>(0, 0);
+      }
+      __syncthreads();
+      V* S = fft_tile2<T, +1, true>(Q, R, N, 1, LDp, a.pl, stw);
+      const size_t base = (size_t)c * g.N3 + (size_t)i0 * g.N2;
+      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int i1 = e / N, i2 = e - i1 * N;
+        a.grid[base + e] = S[i1 * LDp + i2];
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(a.bar, a.err, nblk)) return;
+    mark(0);
+
+    // ---- phase B: x-IFFT, * V / N_g, x-FFT on (column, i1) slabs: pencils along i0
+    // for every i2, element (i0, i2) at A[i0 * LDp + i2] (consecutive threads take
+    // consecutive i2: coalesced global rows, conflict-free shared accesses)
+    for (int task = blockIdx.x; task < ncol * N; task += gridDim.x) {
+      const int c = task / N, i1 = task - c * N;
+      if (!st_act[c]) continue;
+      const size_t base = (size_t)c * g.N3 + (size_t)i1 * N;
+      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int i0 = e / N, i2 = e - i0 * N;
+        A[i0 * LDp + i2] = g.plane_mask[i0] ? a.grid[base + (size_t)i0 * g.N2 + i2] : mk<T>(0, 0);
+      }
+      __syncthreads();
+      V* R = fft_tile2<T, +1, true>(A, B, N, 1, LDp, a.pl, stw);
+      V* Q = (R == A) ? B : A;
+      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int i0 = e / N, i2 = e - i0 * N;
+        const T m = a.vloc_s[(size_t)i0 * g.N2 + (size_t)i1 * N + i2];
+        const V v = R[i0 * LDp + i2];
+        R[i0 * LDp + i2] = mk<T>(v.x * m, v.y * m);
+      }
+      __syncthreads();
+      V* S = fft_tile2<T, -1, true>(R, Q, N, 1, LDp, a.pl, stw);
+      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int i0 = e / N, i2 = e - i0 * N;
+        if (g.plane_mask[i0]) a.grid[base + (size_t)i0 * g.N2 + i2] = S[i0 * LDp + i2];
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(a.bar, a.err, nblk)) return;
+    mark(1);
+
+    // ---- phase C: y-FFT, z-FFT of the disc rows, gather + kinetic + shift, partial dots
+    for (int task = blockIdx.x; task < ncol * npl; task += gridDim.x) {
+      const int c = task / npl, pi = task - c * npl;
+      if (!st_act[c]) continue;
+      const int i0 = g.planes[pi];
+      const int s0 = g.plane_sph[pi], s1 = g.plane_sph[pi + 1];
+      const int q0 = g.plane_pen[pi], npp = g.plane_pen[pi + 1] - q0;
+      const size_t sc = (size_t)c * a.npw;
+      const size_t base = (size_t)c * g.N3 + (size_t)i0 * g.N2;
+      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int i1 = e / N, i2 = e - i1 * N;
+        A[i1 * LDp + i2] = a.grid[base + e];
+      }
+      __syncthreads();
+      V* R = fft_tile2<T, -1, true>(A, B, N, 1, LDp, a.pl, stw);
+      V* Q = (R == A) ? B : A;
+      for (int e = threadIdx.x; e < npp * N; e += blockDim.x) {
+        const int k = e / N, i2 = e - k * N;
+        Q[k * LDp + i2] = R[g.pencils[q0 + k].y * LDp + i2];
+      }
+      __syncthreads();
+      V* S = fft_tile2<T, -1, false>(Q, R, npp, LDp, 1, a.pl, stw);
+      const double2 Ec = a.E[c];
+      for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        V val = S[(g.sph_pen[s] - q0) * LDp + g.sph_i2[s]];
+        const V pv = a.p[sc + s];
+        const T dr = a.kin[s] - (T)Ec.x, di = -(T)Ec.y;
+        val.x += dr * pv.x - di * pv.y;
+        val.y += dr * pv.y + di * pv.x;
+        a.Ap[sc + s] = val;
+      }
+      __syncthreads();
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      for (int v = warp; v < a.nocc; v += nw) {
+        T ax = 0, ay = 0;
+        for (int s = s0 + lane; s < s1; s += 32) {
+          const V cv = a.C[(size_t)v * a.npw + s];
+          const V y = a.Ap[sc + s];
+          ax += cv.x * y.x + cv.y * y.y;
+          ay += cv.x * y.y - cv.y * y.x;
+        }
+        double dx = ax, dy = ay;
+        for (int o = 16; o > 0; o >>= 1) {
+          dx += __shfl_xor_sync(0xffffffffu, dx, o);
+          dy += __shfl_xor_sync(0xffffffffu, dy, o);
+        }
+        if (lane == 0) a.dpart[((size_t)c * npl + pi) * a.nocc + v] = make_double2(dx, dy);
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(a.bar, a.err, nblk)) return;
+    mark(2);
+
+    // ---- phase D: P_c on Ap, partial p^H Ap
+    for (int task = blockIdx.x; task < ncol * a.nchunk; task += gridDim.x) {
+      const int c = task / a.nchunk, ch = task - c * a.nchunk;
+      if (!st_act[c]) continue;
+      // coef[v] = sum over planes of the partials: stage all partials in shared
+      // memory with every thread loading (independent loads in flight), then
+      // add them in plane order per v
+      {
+        const double2* src = a.dpart + (size_t)c * npl * a.nocc;
+        // A and B are adjacent: 2 N (N+1) complex values of scratch
+        const bool staged = (size_t)npl * a.nocc * sizeof(double2) <= 2 * (size_t)N * LDp * sizeof(V);
+        const double2* stage = staged ? reinterpret_cast<const double2*>(A) : src;
+        if (staged) {
+          double2* st = reinterpret_cast<double2*>(A);
+          for (int e = threadIdx.x; e < npl * a.nocc; e += blockDim.x) st[e] = src[e];
+        }
+        __syncthreads();
+        for (int v = threadIdx.x; v < a.nocc; v += blockDim.x) {
+          double sx = 0.0, sy = 0.0;
+          for (int pi = 0; pi < npl; ++pi) {
+            const double2 q = stage[pi * a.nocc + v];
+            sx += q.x;
+            sy += q.y;
+          }
+          coef[v] = make_double2(sx, sy);
+        }
+        __syncthreads();
+      }
+      const int g0 = ch * kPChunk, g1 = min(a.npw, g0 + kPChunk);
+      const size_t sc = (size_t)c * a.npw;
+      double acc = 0.0;
+      for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
+        V y = a.Ap[sc + G];
+        int v = 0;
+        for (; v + 8 <= a.nocc; v += 8) {          // eight independent loads in flight
+          V cv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) cv[u] = a.C[(size_t)(v + u) * a.npw + G];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const V k = from_d<T>(coef[v + u]);
+            y.x -= cv[u].x * k.x - cv[u].y * k.y;
+            y.y -= cv[u].x * k.y + cv[u].y * k.x;
+          }
+        }
+        for (; v < a.nocc; ++v) {
+          const V cv = a.C[(size_t)v * a.npw + G];
+          const V k = from_d<T>(coef[v]);
+          y.x -= cv.x * k.x - cv.y * k.y;
+          y.y -= cv.x * k.y + cv.y * k.x;
+        }
+        a.Ap[sc + G] = y;
+        const V pv = a.p[sc + G];
+        acc += (double)(pv.x * y.x + pv.y * y.y);
+      }
+      acc = dsum_block<T>(acc, red);
+      if (threadIdx.x == 0) a.ppart[(size_t)c * a.nchunk + ch] = acc;
+      __syncthreads();
+    }
+    if (!grid_barrier(a.bar, a.err, nblk)) return;
+    mark(3);
+
+    // ---- phase E: x += alpha p, r -= alpha Ap, partial |r|^2
+    for (int task = blockIdx.x; task < ncol * a.nchunk; task += gridDim.x) {
+      const int c = task / a.nchunk, ch = task - c * a.nchunk;
+      if (!st_act[c]) continue;
+      if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < a.nchunk; ++k) s += a.ppart[(size_t)c * a.nchunk + k];
+        bcast = s;
+      }
+      __syncthreads();
+      const double pap = bcast;
+      const T al = (T)((pap > 0.0) ? st_rr[c] / pap : 0.0);
+      const int g0 = ch * kPChunk, g1 = min(a.npw, g0 + kPChunk);
+      const size_t sc = (size_t)c * a.npw;
+      double acc = 0.0;
+      for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
+        const size_t i = sc + G;
+        const V pv = a.p[i], av = a.Ap[i];
+        V xv = a.x[i], rv = a.r[i];
+        xv.x += al * pv.x;
+        xv.y += al * pv.y;
+        rv.x -= al * av.x;
+        rv.y -= al * av.y;
+        a.x[i] = xv;
+        a.r[i] = rv;
+        const double2 rd = to_d(rv);
+        acc += rd.x * rd.x + rd.y * rd.y;
+      }
+      acc = dsum_block<T>(acc, red);
+      if (threadIdx.x == 0) a.rpart[(size_t)c * a.nchunk + ch] = acc;
+      __syncthreads();
+    }
+    if (!grid_barrier(a.bar, a.err, nblk)) return;
+    mark(4);
+
+    // ---- convergence decisions (identical in every CTA)
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+      if (!st_act[c]) continue;
+      double s = 0.0, pp = 0.0;
+      for (int k = 0; k < a.nchunk; ++k) {
+        s += a.rpart[(size_t)c * a.nchunk + k];
+        pp += a.ppart[(size_t)c * a.nchunk + k];
+      }
+      const int itc = st_it[c] + 1;
+      st_it[c] = itc;
+      st_beta[c] = s / st_rr[c];
+      st_rr[c] = s;
+      st_min[c] = fmin(st_min[c], s);
+      int stop = 0;
+      if (!(pp > 0.0) || !isfinite(s)) { st_flag[c] = 2; stop = 1; }
+      else if (s <= st_stop[c]) { st_flag[c] = 0; stop = 1; }
+      else if (s > 1e4 * st_min[c]) { st_flag[c] = 3; stop = 1; }
+      else if (itc >= a.maxit) { st_flag[c] = 1; stop = 1; }
+      if (stop) st_act[c] = 0;
+    }
+    __syncthreads();
+    mark(5);
+  }
+  if (blockIdx.x == 0) {
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+      a.iters_out[c] = st_it[c];
+      a.flag_out[c] = st_act[c] ? 1 : st_flag[c];
+      a.rr_out[c] = st_rr[c];
+    }
+  }
+}
+
+template <typename T>
+static size_t pcg_smem(int N, int ncol, int nocc) {
+  return pcg_layout(N, ncol, nocc, (int)sizeof(cpx<T>)).total;
+}
+
+template <typename T>
+cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPlan& pl, const Prec<T>& P, int nocc,
+                                 int npw, int ncol, const double2* b64, const int* outer_active, const double2* E,
+                                 const double* rr_abs, double tol_in2, int maxit, cpx<T>* x, cpx<T>* r, cpx<T>* p,
+                                 cpx<T>* Ap, cpx<T>* grid, double2* dpart, double* ppart, double* rpart,
+                                 unsigned* bar, int* err, int* iters, int* flags, double* rr_out, int* grid_used,
+                                 unsigned long long* ptime) {
+  PcgArgs<T> a;
+  a.g = g; a.pl = pl; a.tw = P.tw; a.kin = P.kin; a.vloc_s = P.vloc_s; a.C = P.C;
+  a.nocc = nocc; a.npw = npw; a.ncol = ncol; a.nchunk = (npw + kPChunk - 1) / kPChunk;
+  a.b64 = b64; a.outer_active = outer_active; a.E = E; a.rr_abs = rr_abs; a.tol_in2 = tol_in2; a.maxit = maxit;
+  a.x = x; a.r = r; a.p = p; a.Ap = Ap; a.grid = grid; a.dpart = dpart; a.ppart = ppart; a.rpart = rpart;
+  a.bar = bar; a.err = err; a.iters_out = iters; a.flag_out = flags; a.rr_out = rr_out; a.ptime = ptime;
+  const size_t sm = pcg_smem<T>(g.N, ncol, nocc);
+  cudaError_t e = cudaFuncSetAttribute(k_cg_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, per = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_persistent<T>, kPT, sm)) != cudaSuccess)
+    return e;
+  if (per < 1) return cudaErrorInvalidConfiguration;
+  const int ntask = ncol * std::max(g.N, g.nplanes);
+  const int nblk = std::min(per * nsm, std::max(ntask, 1));
+  *grid_used = nblk;
+  void* args[] = {&a};
+  ++g_launches;
+  return cudaLaunchCooperativeKernel((const void*)k_cg_persistent<T>, dim3(nblk), dim3(kPT), args, sm, s);
+}
+
+template cudaError_t launch_cg_persistent<float>(cudaStream_t, const Geometry&, const FftPlan&, const Prec<float>&,
+                                                 int, int, int, const double2*, const int*, const double2*,
+                                                 const double*, double, int, float2*, float2*, float2*, float2*,
+                                                 float2*, double2*, double*, double*, unsigned*, int*, int*, int*,
+                                                 double*, int*, unsigned long long*);
+template cudaError_t launch_cg_persistent<double>(cudaStream_t, const Geometry&, const FftPlan&, const Prec<double>&,
+                                                  int, int, int, const double2*, const int*, const double2*,
+                                                  const double*, double, int, double2*, double2*, double2*,
+                                                  double2*, double2*, double2*, double*, double*, unsigned*, int*,
+                                                  int*, int*, double*, int*, unsigned long long*);
+
+}  // namespace gw

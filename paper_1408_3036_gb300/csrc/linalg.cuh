@@ -65,4 +65,14 @@ void launch_tridiag_inv(cudaStream_t s, int K, const double* alpha, const double
 
 template <typename T> cudaError_t fft_set_smem_limits();
 
+// whole CG pass in one cooperative launch (kernels_cg.cu)
+template <typename T>
+cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPlan& pl, const Prec<T>& P, int nocc,
+                                 int npw, int ncol, const double2* b64, const int* outer_active, const double2* E,
+                                 const double* rr_abs, double tol_in2, int maxit, cpx<T>* x, cpx<T>* r, cpx<T>* p,
+                                 cpx<T>* Ap, cpx<T>* grid, double2* dpart, double* ppart, double* rpart,
+                                 unsigned* bar, int* err, int* iters, int* flags, double* rr_out, int* grid_used,
+                                 unsigned long long* ptime = nullptr);
+constexpr int kPersistentMaxCols = 256;
+
 }  // namespace gw

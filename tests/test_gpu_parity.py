@@ -154,3 +154,20 @@ def test_free_electron_closed_form_gpu():
         expect[m] = -(2.0 / sph.omega_vol) * G2[m] / ((G2[m] / 2) ** 2 - omega ** 2)
         assert rel(sph.fwd(dn), expect * sph.fwd(f[0])) < 1e-12
     c.close()
+
+
+def test_persistent_cg_matches_multi_launch(tiny, monkeypatch):
+    """The one-launch persistent CG and the multi-launch CG agree."""
+    wl, cell, sph, gs = tiny
+    f = W.random_fields(103, 2, sph.ng)
+    c1 = make(cell, gs)
+    out1 = c1.apply_eps(f, [0.0], gw.GW_FP64)
+    out1m = c1.apply_eps(f, [0.0], gw.GW_MIXED)
+    c1.close()
+    monkeypatch.setenv("GW_MULTI_LAUNCH_CG", "1")
+    c2 = make(cell, gs)
+    out2 = c2.apply_eps(f, [0.0], gw.GW_FP64)
+    out2m = c2.apply_eps(f, [0.0], gw.GW_MIXED)
+    c2.close()
+    assert rel(out1, out2) < 1e-12
+    assert rel(out1m, out2m) < 1e-8
