@@ -36,7 +36,7 @@ struct gw_ctx {
   std::map<std::string, std::pair<void*, size_t>> bufs;
   Work work;
   size_t work_cols = 0;
-  double tol = 1e-13, tol_mixed = 1e-11, tol_inner = 1e-4;   // backward errors (FP64 / mixed), inner
+  double tol = 1e-13, tol_mixed = 1e-12, tol_inner = 1e-4;   // backward errors (FP64 / mixed), inner
   double anorm = 1.0;           // bound on |H - E| used by the backward error
   bool no_persistent = false;   // force the multi-launch CG (tests)
   long long pcg_iters = 0;      // iterations run by persistent launches
@@ -518,6 +518,10 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
       TRY(upload(ctx, "sv_rra", habs, &rra));
     }
   }
+  // The solution lies in P_c.  Inner passes in FP32 leave valence components
+  // at the FP32 rounding level that the residual cannot see (P_c removes them
+  // from A x) but the density reduction would: project them out in FP64.
+  launch_proj<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, x64, ncol, nullptr, ctx->work, nullptr, nullptr);
   {
     double fin = 0.0;        // final relative FP64 residual |b - A x| / |b| over all columns
     for (int c = 0; c < ncol; ++c) fin = std::max(fin, hb[c] > 0 ? std::sqrt(hr[c] / hb[c]) : 0.0);
@@ -746,6 +750,151 @@ gw_status lanczos_core(gw_ctx* ctx, const double* x0, int K, const std::vector<d
     if (hb[0] <= 1e-14 * std::fabs(hb[1])) return fail(ctx, GW_E_BREAKDOWN, "Lanczos breakdown: invariant subspace");
   }
   return launch_check(ctx, "lanczos");
+}
+
+// ---------------------------------------------------------------------------
+// Derivative of s = <phi|eps~^-1(0)|phi> with respect to V_loc(r_i) (not in the
+// paper; third-order perturbation theory, see include/gw.h):
+//   Lanczos from phi -> T^-1, s = |phi|^2 (T^-1)_11, u = |phi| Q T^-1 e_1
+//   w = v^1/2 u;  dpsi_v = -G_v P_c (w psi_v)          (Sternheimer solves)
+//   g1 = sum |dpsi_v|^2 - sum S_vv' psi_v'* psi_v,  S = <dpsi|dpsi>
+//   eta_v = P_c [w dpsi_v - sum_v' W_v'v dpsi_v'],  W = <psi|w|psi>
+//   lambda_v = G_v eta_v                                (adjoint solves)
+//   g2 = -sum_v lambda_v* psi_v;  grad = (Omega/N_g)(4 g1 + 8 Re g2)
+// The occupied states are real in real space, so conj(u_v) = u_v and
+// Re(lambda* u) = Re(lambda u).  Lanczos vectors are kept (checkpointed) and
+// dpsi is recomputed from them rather than stored across the Lanczos run.
+// ---------------------------------------------------------------------------
+template <typename S>
+gw_status grad_core(gw_ctx* ctx, const double* phi, int K, double* s_out, double* grad) {
+  const int N3 = ctx->N3, npw = ctx->npw, nocc = ctx->nocc;
+  const double vol = ctx->vol, wgt = vol / N3;
+  const Geometry& g = ctx->geo;
+  auto& P = ctx->P64;
+  TRY(ensure_work(ctx, std::max(K + 1, nocc * nocc)));
+  // -- Lanczos from phi with the basis kept
+  double *a, *b, *Q, *x0c, *Ti, *d, *l, *u, *w, *h;
+  int* stat;
+  TRY(getbuf(ctx, "gr_alpha", K, &a));
+  TRY(getbuf(ctx, "gr_beta", std::max(K - 1, 1), &b));
+  TRY(getbuf(ctx, "gr_Q", (size_t)K * N3, &Q));
+  TRY(getbuf(ctx, "gr_x0", N3, &x0c));
+  CK(cudaMemcpyAsync(x0c, phi, (size_t)N3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  std::vector<double> om(1, 0.0);
+  gw_status st = lanczos_core<S>(ctx, x0c, K, om, a, b, Q);
+  if (st != GW_OK && st != GW_E_BREAKDOWN) return st;
+  // -- T^-1 and s
+  TRY(getbuf(ctx, "gr_Ti", (size_t)K * K, &Ti));
+  TRY(getbuf(ctx, "gr_d", K, &d));
+  TRY(getbuf(ctx, "gr_l", K, &l));
+  TRY(getbuf(ctx, "gr_stat", 1, &stat));
+  launch_tridiag_inv(ctx->st, K, a, b, d, l, Ti, stat);
+  std::vector<double> t0(K);
+  double pn2 = 0.0;
+  {
+    double* nrm;
+    TRY(getbuf(ctx, "gr_nrm", 1, &nrm));
+    launch_dot(ctx->st, N3, phi, phi, wgt, 0, ctx->work, nrm);
+    CK(cudaMemcpyAsync(t0.data(), Ti, K * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));  // column 0
+    CK(cudaMemcpyAsync(&pn2, nrm, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(ctx->host_pin, stat, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    TRY(sync(ctx, "grad T^-1"));
+    if (ctx->host_pin[0]) return fail(ctx, GW_E_BREAKDOWN, "zero pivot in the tridiagonal inverse");
+  }
+  *s_out = pn2 * t0[0];
+  // u = |phi| sum_k Q_k (T^-1)_k0
+  std::vector<double> hm(K);
+  for (int k = 0; k < K; ++k) hm[k] = -std::sqrt(pn2) * t0[k];
+  TRY(upload(ctx, "gr_h", hm, &h));
+  TRY(getbuf(ctx, "gr_u", N3, &u));
+  TRY(getbuf(ctx, "gr_w", N3, &w));
+  CK(cudaMemsetAsync(u, 0, (size_t)N3 * sizeof(double), ctx->st));
+  launch_gemv_n(ctx->st, Q, N3, N3, h, K, u);
+  TRY(sqrtv<double>(ctx, u, 1, w, nullptr));
+  // -- first-order orbitals: (H - e_v) x_v = P_c(u_v w), dpsi_v = -x_v (sphere coefficients)
+  std::vector<int> cv(nocc), cz(nocc, 0), src(nocc);
+  std::vector<double2> E(nocc);
+  for (int v = 0; v < nocc; ++v) { cv[v] = v; src[v] = v; E[v] = make_double2(ctx->eps[v], 0.0); }
+  int *dcv, *dcz;
+  double2* dE;
+  TRY(upload(ctx, "gr_cv", cv, &dcv));
+  TRY(upload(ctx, "gr_cz", cz, &dcz));
+  TRY(upload(ctx, "gr_E", E, &dE));
+  double2 *grid, *rhs, *dC, *dU, *eta, *lam, *Sg, *Wm;
+  TRY(getbuf(ctx, "gr_grid", (size_t)nocc * N3, &grid));
+  TRY(getbuf(ctx, "gr_rhs", (size_t)nocc * npw, &rhs));
+  TRY(getbuf(ctx, "gr_dC", (size_t)nocc * npw, &dC));
+  TRY(getbuf(ctx, "gr_dU", (size_t)nocc * N3, &dU));
+  TRY(getbuf(ctx, "gr_eta", (size_t)nocc * npw, &eta));
+  TRY(getbuf(ctx, "gr_lam", (size_t)nocc * npw, &lam));
+  TRY(getbuf(ctx, "gr_S", (size_t)nocc * nocc, &Sg));
+  TRY(getbuf(ctx, "gr_W", (size_t)nocc * nocc, &Wm));
+  auto sphere_of_product = [&](const double2* A, int a_conj, double2* out) {
+    // out[v] = P_c Sphere(FFT(A_v w)) (twice projected)
+    launch_xpass_prod_fwd<double>(ctx->st, g, P, ctx->plan, reinterpret_cast<const double2*>(w), 0, A, 0, a_conj,
+                                  dcv, dcz, grid, nocc);
+    launch_ypass<double>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, nullptr, nocc, 0);
+    launch_zpass<double>(ctx->st, Z_GATHER_FWD, g, P, ctx->plan, grid, out, nullptr, nullptr, nullptr, nullptr,
+                         nullptr, nullptr, nullptr, nocc);
+  };
+  sphere_of_product(P.U, 0, rhs);
+  launch_proj<double>(ctx->st, P.C, nocc, npw, rhs, nocc, nullptr, ctx->work, nullptr, nullptr);
+  launch_proj<double>(ctx->st, P.C, nocc, npw, rhs, nocc, nullptr, ctx->work, nullptr, nullptr);
+  TRY(launch_check(ctx, "grad rhs"));
+  TRY(solve<S>(ctx, nocc, rhs, dE, dC));
+  // dC = -x  (dpsi coefficients); dU_v = IFFT(dC_v) on the grid
+  {
+    std::vector<int> one(nocc, -1);
+    int* dnone;
+    TRY(upload(ctx, "gr_none", one, &dnone));
+    int* dsrc;
+    TRY(upload(ctx, "gr_src", src, &dsrc));
+    launch_combine(ctx->st, npw, nocc, dC, dsrc, dnone, 1.0, -1.0, dC);
+  }
+  launch_zpass<double>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, dU, dC, nullptr, nullptr, nullptr, nullptr, nullptr,
+                       nullptr, nullptr, nocc);
+  launch_ypass<double>(ctx->st, 1, 1, 0, g, P, ctx->plan, dU, nullptr, nocc, 0);
+  launch_xpass_mul<double>(ctx->st, 1, 1, 0, g, P, ctx->plan, dU, nullptr, nullptr, nocc);
+  // S = <dpsi|dpsi> (sphere), W = <psi|w|psi> (grid)
+  launch_gram<double>(ctx->st, dC, nocc, npw, dC, nocc, ctx->work, Sg);
+  launch_wmat(ctx->st, P.U, w, N3, nocc, ctx->work, Wm);
+  // g1 on the grid
+  double *g1, *g2;
+  TRY(getbuf(ctx, "gr_g1", N3, &g1));
+  TRY(getbuf(ctx, "gr_g2", N3, &g2));
+  launch_g1(ctx->st, dU, P.U, Sg, N3, nocc, 1.0 / vol, g1);
+  // eta_v = P_c [Sphere(FFT(w dU_v)) - sum_v' W[v'][v] dC_v']
+  {
+    std::vector<int> cself(nocc);
+    for (int v = 0; v < nocc; ++v) cself[v] = v;
+    int* dself;
+    TRY(upload(ctx, "gr_cself", cself, &dself));
+    launch_xpass_prod_fwd<double>(ctx->st, g, P, ctx->plan, reinterpret_cast<const double2*>(w), 0, dU, 1, 0, dself,
+                                  dcz, grid, nocc);
+    launch_ypass<double>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, nullptr, nocc, 0);
+    launch_zpass<double>(ctx->st, Z_GATHER_FWD, g, P, ctx->plan, grid, eta, nullptr, nullptr, nullptr, nullptr,
+                         nullptr, nullptr, nullptr, nocc);
+    // eta_v -= sum_v' dC_v' W[v'][v]: the projector update with C := dC and coef[v' * ncol + v] = W[v'][v]
+    launch_proj_update<double>(ctx->st, dC, nocc, npw, eta, nocc, nullptr, Wm, ctx->work, nullptr, nullptr);
+    launch_proj<double>(ctx->st, P.C, nocc, npw, eta, nocc, nullptr, ctx->work, nullptr, nullptr);
+    launch_proj<double>(ctx->st, P.C, nocc, npw, eta, nocc, nullptr, ctx->work, nullptr, nullptr);
+  }
+  TRY(launch_check(ctx, "grad eta"));
+  TRY(solve<S>(ctx, nocc, eta, dE, lam));
+  // Re g2 = -(1/Omega) Re sum_v lambda_v(r) u_v(r)
+  launch_zpass<double>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, grid, lam, nullptr, nullptr, nullptr, nullptr,
+                       nullptr, nullptr, nullptr, nocc);
+  launch_ypass<double>(ctx->st, 1, 1, 0, g, P, ctx->plan, grid, nullptr, nocc, 0);
+  {
+    std::vector<int> gs(2);
+    gs[0] = 0;
+    gs[1] = nocc;
+    int* dgs;
+    TRY(upload(ctx, "gr_gs", gs, &dgs));
+    launch_xpass_inv_reduce<double>(ctx->st, g, P, ctx->plan, grid, dgs, dcv, 1, -1.0 / vol, g2, nullptr, 0);
+  }
+  launch_grad_combine(ctx->st, N3, g1, g2, wgt, grad);
+  return launch_check(ctx, "grad");
 }
 
 // host sphere, pencils, planes
@@ -1206,8 +1355,28 @@ gw_status gw_epsinv_elements(gw_ctx* ctx, const double* alpha, const double* bet
   return GW_OK;
 }
 
-gw_status gw_grad_vloc(gw_ctx* ctx, const double*, int, double*, double*, gw_prec, int) {
-  return fail(ctx, GW_E_UNSUPPORTED, "gradient not available in this build");
+gw_status gw_grad_vloc(gw_ctx* ctx, const double* phi, int k, double* s, double* grad, gw_prec prec, int dev) {
+  TRY(begin(ctx));
+  TRY(need_occ(ctx));
+  if (!phi || !s || !grad || k < 1) return fail(ctx, GW_E_ARG, "bad arguments");
+  if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_E_ARG, "bad precision");
+  for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
+  const size_t fb = (size_t)ctx->N3 * sizeof(double);
+  const void* ph;
+  void* go;
+  TRY(stage_in(ctx, "gr_phi", phi, fb, dev, &ph));
+  TRY(stage_out(ctx, "gr_out", grad, fb, dev, &go));
+  double sv = 0.0;
+  gw_status st = (prec == GW_FP64)
+                     ? grad_core<double>(ctx, reinterpret_cast<const double*>(ph), k, &sv, reinterpret_cast<double*>(go))
+                     : grad_core<float>(ctx, reinterpret_cast<const double*>(ph), k, &sv, reinterpret_cast<double*>(go));
+  if (st != GW_OK) return st;
+  TRY(copy_back(ctx, grad, go, fb, dev));
+  TRY(sync(ctx, "grad"));
+  if (dev) CK(cudaMemcpy(s, &sv, sizeof(double), cudaMemcpyHostToDevice));
+  else *s = sv;
+  if (ctx->stats[0] > 0) ctx->stats[2] /= ctx->stats[0];
+  return GW_OK;
 }
 
 gw_status gw_stats(const gw_ctx* ctx, double* out, int n) {

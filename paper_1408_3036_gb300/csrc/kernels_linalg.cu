@@ -8,6 +8,7 @@
 // Reductions are deterministic: blocks write partial sums, the last block to
 // finish (atomic ticket) adds them in a fixed order.  Dot products accumulate
 // in FP64 for both precisions.
+#include <algorithm>
 #include <cstdio>
 
 #include "gw_common.cuh"
@@ -139,6 +140,98 @@ void launch_proj(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, 
   ++g_launches;
   k_proj_dots<T><<<g1, kLT, 0, s>>>(C, nocc, npw, Y, ncol, active, w.part2, w.cnt_a, w.coef);
   launch_proj_update<T>(s, C, nocc, npw, Y, ncol, active, w.coef, w, Pv, pap);
+}
+
+// Gram matrix only: coef[v * ncol + b] = sum_G conj(C[v][G]) Y[b][G]
+template <typename T>
+void launch_gram(cudaStream_t s, const cpx<T>* C, int nocc, int npw, const cpx<T>* Y, int ncol, Work& w,
+                 double2* out) {
+  if (ncol == 0 || nocc == 0) return;
+  const int nchunk = (npw + kChunkP - 1) / kChunkP;
+  dim3 g1(nchunk, (ncol + kCT - 1) / kCT);
+  ++g_launches;
+  k_proj_dots<T><<<g1, kLT, 0, s>>>(C, nocc, npw, Y, ncol, nullptr, w.part2, w.cnt_a, out);
+}
+
+// ---------------------------------------------------------------------------
+// adjoint (derivative of <phi|eps~^-1(0)|phi> w.r.t. V_loc) grid kernels
+// ---------------------------------------------------------------------------
+// W[v][v'] = (1/N_g) sum_r conj(U_v) w U_v'; grid (nchunk over N_g, nocc*nocc)
+__global__ void __launch_bounds__(kLT)
+k_wmat(const double2* __restrict__ U, const double* __restrict__ w, int n, int nocc,
+       double2* __restrict__ partial, unsigned* __restrict__ cnt, double2* __restrict__ W) {
+  const int pair = blockIdx.y;
+  const int v = pair / nocc, vp = pair - v * nocc;
+  const int g0 = blockIdx.x * kChunk, g1 = min(n, g0 + kChunk);
+  double ax = 0.0, ay = 0.0;
+  for (int r = g0 + threadIdx.x; r < g1; r += blockDim.x) {
+    const double2 a = U[(size_t)v * n + r], b = U[(size_t)vp * n + r];
+    const double wr = w[r];
+    ax += wr * (a.x * b.x + a.y * b.y);
+    ay += wr * (a.x * b.y - a.y * b.x);
+  }
+  ax = block_sum(ax);
+  ay = block_sum(ay);
+  const int np = nocc * nocc;
+  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * np + pair] = make_double2(ax, ay);
+  if (!last_block(&cnt[pair], gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double sx = 0.0, sy = 0.0;
+    for (int k = 0; k < (int)gridDim.x; ++k) {
+      const double2 q = partial[(size_t)k * np + pair];
+      sx += q.x;
+      sy += q.y;
+    }
+    W[pair] = make_double2(sx / n, sy / n);
+  }
+}
+
+void launch_wmat(cudaStream_t s, const double2* U, const double* w, int n, int nocc, Work& wk, double2* W) {
+  dim3 g((n + kChunk - 1) / kChunk, nocc * nocc);
+  ++g_launches;
+  k_wmat<<<g, kLT, 0, s>>>(U, w, n, nocc, wk.part2, wk.cnt_c, W);
+}
+
+// g1[r] = (sum_v |dU_v|^2 - sum_{v v'} S[v][v'] conj(U_v'(r)) U_v(r)) / vol
+__global__ void k_g1(const double2* __restrict__ dU, const double2* __restrict__ U, const double2* __restrict__ S,
+                     int n, int nocc, double inv_vol, double* __restrict__ g1) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int v = 0; v < nocc; ++v) {
+      const double2 d = dU[(size_t)v * n + r];
+      acc += d.x * d.x + d.y * d.y;
+      const double2 uv = U[(size_t)v * n + r];
+      for (int vp = 0; vp < nocc; ++vp) {
+        const double2 uvp = U[(size_t)vp * n + r];
+        const double2 sv = S[(size_t)v * nocc + vp];
+        // Re( S[v][v'] conj(U_v') U_v )
+        const double cx = uvp.x * uv.x + uvp.y * uv.y;   // conj(uvp) * uv
+        const double cy = uvp.x * uv.y - uvp.y * uv.x;
+        acc -= sv.x * cx - sv.y * cy;
+      }
+    }
+    g1[r] = acc * inv_vol;
+  }
+}
+
+void launch_g1(cudaStream_t s, const double2* dU, const double2* U, const double2* S, int n, int nocc,
+               double inv_vol, double* g1) {
+  const int nb = std::min((n + kLT - 1) / kLT, 152 * 8);
+  ++g_launches;
+  k_g1<<<nb, kLT, 0, s>>>(dU, U, S, n, nocc, inv_vol, g1);
+}
+
+// grad = wgt (4 g1 + 8 g2)
+__global__ void k_grad_combine(int n, const double* __restrict__ g1, const double* __restrict__ g2, double wgt,
+                               double* __restrict__ grad) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+    grad[r] = wgt * (4.0 * g1[r] + 8.0 * g2[r]);
+}
+
+void launch_grad_combine(cudaStream_t s, int n, const double* g1, const double* g2, double wgt, double* grad) {
+  const int nb = std::min((n + kLT - 1) / kLT, 152 * 8);
+  ++g_launches;
+  k_grad_combine<<<nb, kLT, 0, s>>>(n, g1, g2, wgt, grad);
 }
 
 template <typename T>
@@ -502,6 +595,7 @@ void launch_tridiag_inv(cudaStream_t s, int K, const double* alpha, const double
 }
 
 #define GW_LINST(T)                                                                                        \
+  template void launch_gram<T>(cudaStream_t, const cpx<T>*, int, int, const cpx<T>*, int, Work&, double2*); \
   template void launch_proj_update<T>(cudaStream_t, const cpx<T>*, int, int, cpx<T>*, int, const int*,     \
                                       const double2*, Work&, const cpx<T>*, double*);                      \
   template void launch_proj<T>(cudaStream_t, const cpx<T>*, int, int, cpx<T>*, int, const int*, Work&,     \

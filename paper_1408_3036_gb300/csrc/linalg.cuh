@@ -40,6 +40,13 @@ void launch_proj(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, 
 template <typename T>
 void launch_proj_update(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, int ncol,
                         const int* active, const double2* coef, Work& w, const cpx<T>* Pv, double* pap);
+template <typename T>
+void launch_gram(cudaStream_t s, const cpx<T>* C, int nocc, int npw, const cpx<T>* Y, int ncol, Work& w,
+                 double2* out);
+void launch_wmat(cudaStream_t s, const double2* U, const double* w, int n, int nocc, Work& wk, double2* W);
+void launch_g1(cudaStream_t s, const double2* dU, const double2* U, const double2* S, int n, int nocc,
+               double inv_vol, double* g1);
+void launch_grad_combine(cudaStream_t s, int n, const double* g1, const double* g2, double wgt, double* grad);
 template <typename T, typename U>
 void launch_cg_init(cudaStream_t s, int npw, int ncol, const cpx<U>* b, cpx<T>* x, cpx<T>* r,
                     const int* outer_active, Work& w, CgState st, double tol_in2, double tol_abs2);
