@@ -151,6 +151,28 @@ gw_status gw_epsinv_elements(gw_ctx* ctx, const double* alpha, const double* bet
                              double* out, int device_ptrs);
 
 /*
+ * gw_epsinv_elements_noalloc -- the same T_K^-1 as gw_epsinv_elements, for
+ * callers that cannot allocate device memory when they need it (their memory
+ * is held by another allocator, or a cudaMalloc/cudaFree and its implicit
+ * device synchronisation is not acceptable at that point).  The paper has no
+ * counterpart: this is a deployment variant of the tridiagonal inverse.
+ *   alpha [k], beta [k-1], out [k][k]: DEVICE pointers owned by the caller
+ *   k         1 <= k <= 4096; larger k returns GW_E_ARG (use gw_epsinv_elements)
+ *   cuda_stream  stream the work is ordered on (may be 0); the call returns
+ *             after that stream has finished it
+ * It needs no context and calls no cudaMalloc/cudaFree: its pivots,
+ * multipliers and zero-pivot flag live in one fixed 64 KB __device__ array in
+ * the library, which every GPU that loads the library keeps until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress with the device current); make that first call before
+ * any stream capture on the device.  All calls on a device share the array:
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.  Returns GW_E_BREAKDOWN for a zero pivot.
+ */
+gw_status gw_epsinv_elements_noalloc(const double* alpha, const double* beta, int k, double* out,
+                                     void* cuda_stream);
+
+/*
  * gw_grad_vloc -- s = <phi|eps~^-1(0)|phi> and grad[i] = ds/dV_loc(r_i) (not in
  * the paper).  s and u = eps~^-1 phi come from k Lanczos steps started at phi;
  * the gradient follows third-order perturbation theory:

@@ -25,7 +25,8 @@ STATUS = {0: "GW_OK", 1: "GW_E_ARG", 2: "GW_E_CUDA", 3: "GW_E_NOMEM", 4: "GW_E_N
           5: "GW_E_BREAKDOWN", 6: "GW_E_TIMEOUT", 7: "GW_E_NONFINITE", 8: "GW_E_UNSUPPORTED"}
 EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "gw_apply_chi0",
            "gw_apply_eps", "gw_lanczos", "gw_epsinv_elements", "gw_grad_vloc", "gw_stats",
-           "gw_set_solver", "gw_profile", "gw_profile_read", "gw_last_error", "gw_destroy")
+           "gw_set_solver", "gw_profile", "gw_profile_read", "gw_last_error", "gw_destroy",
+           "gw_epsinv_elements_noalloc")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
                    "refine_fp64", "other")
 
@@ -58,6 +59,7 @@ def load(path=LIB_PATH):
         "gw_apply_eps": (I, [P, P, I, P, I, P, I, I]),
         "gw_lanczos": (I, [P, P, I, I, P, P, P, P, I, I]),
         "gw_epsinv_elements": (I, [P, P, P, I, I, P, I]),
+        "gw_epsinv_elements_noalloc": (I, [P, P, I, P, P]),
         "gw_grad_vloc": (I, [P, P, I, P, P, I, I]),
         "gw_stats": (I, [P, P, I]),
         "gw_set_solver": (I, [P, D, D, I, I]),
@@ -175,6 +177,18 @@ def gw_epsinv_elements(ctx, alpha, beta, k, out, blk=1):
     pb, _ = _ptr(beta)
     po, _ = _ptr(out)
     _check(ctx, load().gw_epsinv_elements(ctx, pa, pb, int(k), int(blk), po, d))
+    return out
+
+
+def gw_epsinv_elements_noalloc(alpha, beta, k, out, cuda_stream=None):
+    """T_K^-1 without a context or any device allocation (device tensors only);
+    see include/gw.h for the shared fixed scratch and its limits."""
+    pa, d = _ptr(alpha)
+    pb, _ = _ptr(beta)
+    po, e = _ptr(out)
+    if not (d and e):
+        raise ValueError("device buffers required")
+    _check(None, load().gw_epsinv_elements_noalloc(pa, pb, int(k), po, cuda_stream))
     return out
 
 
