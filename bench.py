@@ -163,13 +163,22 @@ class Clocks:
 # algorithmic bytes per column-iteration of each kernel class
 # ---------------------------------------------------------------------------
 def class_bytes(miller, N, npw, nocc, s):
-    """Per column-iteration (and per-launch shared) algorithmic bytes of the
-    inner CG loop kernels; s = bytes per complex value."""
+    """Algorithmic bytes of the inner CG kernels per column-iteration, and per
+    launch-iteration for data shared by all columns; s = bytes per complex value.
+
+    persistent_cg (one launch = one CG pass, five phases per iteration):
+      A  read r, p, write p (3 N_PW s); write the planes of the sphere (P0 N^2 s)
+      B  read + write those planes (2 P0 N^2 s); V shared (N^3 real)
+      C  read the planes (P0 N^2 s); read p, write Ap (2 N_PW s); C_v shared (n_occ N_PW s)
+      D  read + write Ap, read p (3 N_PW s); C_v shared again
+      E  read p, Ap, x, r, write x, r (6 N_PW s)
+    """
     n = np.mod(miller, N)
     D = len({(a, b) for a, b in zip(n[:, 0], n[:, 1])})        # disc pencils
     P0 = len(set(n[:, 0]))                                     # planes cut by the sphere
     real = s // 2
     col = {
+        "persistent_cg": 14 * npw * s + 4 * P0 * N * N * s,
         "z_scatter_inv": 3 * npw * s + D * N * s,
         "y_inv": D * N * s + P0 * N * N * s,
         "x_h": 2 * P0 * N * N * s,
@@ -179,6 +188,7 @@ def class_bytes(miller, N, npw, nocc, s):
         "cg_update": 6 * npw * s,
     }
     shared = {
+        "persistent_cg": N ** 3 * real + 2 * nocc * npw * s,
         "z_scatter_inv": 8 * npw, "y_inv": 0, "x_h": N ** 3 * real, "y_fwd": 0,
         "z_gather_h": 8 * npw + npw * real, "proj": 2 * nocc * npw * s, "cg_update": 0,
     }
@@ -272,6 +282,7 @@ def run_gpu(args):
     times = []
     it_cols = 0.0
     cols = 0.0
+    it_launch = 0
     dominant = args.profile_class
     gw.gw_profile(cell.ctx, 1 << gw.PROFILE_CLASSES.index(dominant))
     barrier()
@@ -290,6 +301,7 @@ def run_gpu(args):
             st = gw.gw_stats(cell.ctx)
             it_cols += st["columns"] * st["mean_iter"]
             cols += st["columns"]
+            it_launch += st["launch_iterations"]
     barrier()
     prof = gw.gw_profile_read(cell.ctx)
     gw.gw_profile(cell.ctx, 0)
@@ -310,7 +322,8 @@ def run_gpu(args):
     s = 8 if prec == gw.GW_MIXED else 16
     colb, shared, geo = class_bytes(miller, c.N, cell.npw, c.n_occ, s)
     ms_dom, n_dom = prof[dominant]
-    alg_bytes = it_cols * colb[dominant] + n_dom * shared[dominant]
+    per_launch_units = it_launch if dominant == "persistent_cg" else n_dom
+    alg_bytes = it_cols * colb[dominant] + per_launch_units * shared[dominant]
     hbm, hbm_kind = peaks()
     achieved = alg_bytes / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else None
     tr = ncu_traffic(dominant)
@@ -321,7 +334,7 @@ def run_gpu(args):
                     frac=(achieved / hbm if achieved else None), peak_kind=hbm_kind,
                     traffic=traffic, alg_bytes_per_launch=alg_bytes / max(n_dom, 1),
                     alg_bytes_per_col_iter=colb[dominant], kernel_ms_share=ms_dom / total_ms,
-                    launches=n_dom)
+                    launches=n_dom, column_iterations=it_cols, launch_iterations=it_launch)
 
     # --- FP64 path (fewer Lanczos steps: FP64 throughput on GB300 is low)
     fp64 = None
@@ -397,7 +410,7 @@ def main():
     ap.add_argument("--fp64-k", type=int, default=10)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-class", default="x_h")
+    ap.add_argument("--profile-class", default="persistent_cg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

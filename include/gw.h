@@ -191,8 +191,10 @@ gw_status gw_grad_vloc(gw_ctx* ctx, const double* phi, int k, double* s, double*
  *   out[0] Sternheimer columns solved, out[1] max inner iterations,
  *   out[2] mean inner iterations, out[3] outer (FP64 residual) passes,
  *   out[4] max final relative FP64 residual, out[5] H applications (columns),
- *   out[6] CUDA kernels launched by the library since it was loaded
- *   n: entries wanted (<= 7)
+ *   out[6] CUDA kernels launched by the library since it was loaded,
+ *   out[7] iterations run by persistent CG launches (each launch counts the
+ *          iterations of its slowest column)
+ *   n: entries wanted (<= 8)
  */
 gw_status gw_stats(const gw_ctx* ctx, double* out, int n);
 
@@ -213,10 +215,10 @@ gw_status gw_set_solver(gw_ctx* ctx, double tol, double tol_inner, int max_iter,
 /*
  * gw_profile -- time selected kernel classes with CUDA events on the work
  * stream (one event pair around each launch; mask 0 turns timing off).
- * Classes: 0 scatter + inverse z pass (with the CG p update), 1 inverse y pass,
- * 2 x pass with V_loc (H), 3 forward y pass, 4 forward z pass + gather + kinetic
- * and shift, 5 projector P_c, 6 CG update, 7 FP64 refinement residual
- * (H apply + P_c), 8 reserved.
+ * Classes (multi-launch CG): 0 scatter + inverse z pass (with the CG p update),
+ * 1 inverse y pass, 2 x pass with V_loc (H), 3 forward y pass, 4 forward z pass
+ * + gather + kinetic and shift, 5 projector P_c, 6 CG update; 7 FP64
+ * refinement residual (H apply + P_c); 8 persistent CG launch (all phases).
  * gw_profile_read -- per class: total milliseconds and launches since the last
  * read (synchronises the stream; resets the totals).
  */

@@ -28,7 +28,7 @@ EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "
            "gw_set_solver", "gw_profile", "gw_profile_read", "gw_last_error", "gw_destroy",
            "gw_epsinv_elements_noalloc")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
-                   "refine_fp64", "other")
+                   "refine_fp64", "persistent_cg")
 
 
 class GwError(RuntimeError):
@@ -201,10 +201,10 @@ def gw_grad_vloc(ctx, phi, k, s, grad, prec=GW_FP64):
 
 
 def gw_stats(ctx):
-    out = np.zeros(7)
-    _check(ctx, load().gw_stats(ctx, out.ctypes.data, 7))
+    out = np.zeros(8)
+    _check(ctx, load().gw_stats(ctx, out.ctypes.data, 8))
     return dict(columns=out[0], max_iter=out[1], mean_iter=out[2], outer=out[3], max_residual=out[4],
-                h_columns=out[5], launches=int(out[6]))
+                h_columns=out[5], launches=int(out[6]), launch_iterations=int(out[7]))
 
 
 def gw_set_solver(ctx, tol=0.0, tol_inner=0.0, max_iter=0, max_outer=0):

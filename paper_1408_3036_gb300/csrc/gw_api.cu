@@ -139,7 +139,7 @@ gw_status ensure_work(gw_ctx* ctx, size_t cols) {
 // selected class, resolved by gw_profile_read
 // ---------------------------------------------------------------------------
 enum ProfClass { PC_ZSCAT = 0, PC_YINV = 1, PC_XH = 2, PC_YFWD = 3, PC_ZGATH = 4, PC_PROJ = 5, PC_CGUPD = 6,
-                 PC_REFINE = 7, PC_OTHER = 8, PC_N = 9 };
+                 PC_REFINE = 7, PC_PCG = 8, PC_N = 9 };
 
 int prof_begin(gw_ctx* ctx, int cls) {
   if (!(ctx->prof_mask & (1u << cls))) return -1;
@@ -391,7 +391,7 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
     std::fprintf(stderr, "phases(ms) A %.2f B %.2f C %.2f D %.2f E %.2f conv %.2f  blocks %d\n", h[0] * 1e-6,
                  h[1] * 1e-6, h[2] * 1e-6, h[3] * 1e-6, h[4] * 1e-6, h[5] * 1e-6, used);
   }
-  prof_end(ctx, PC_XH, pa);
+  prof_end(ctx, PC_PCG, pa);
   std::vector<int> its(ncol), fl(ncol);
   int herr = 0;
   CK(cudaMemcpyAsync(its.data(), iters, ncol * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
@@ -1269,6 +1269,7 @@ static gw_status apply_common(gw_ctx* ctx, const double* x, int nb, const double
   TRY(check_omega(ctx, omega, n_omega, &om));
   if (nb == 0) return GW_OK;
   for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
+  ctx->pcg_iters = 0;
   const size_t ib = (size_t)nb * ctx->N3 * sizeof(double), ob = ib * n_omega;
   const void* xin;
   void* o;
@@ -1302,6 +1303,7 @@ gw_status gw_lanczos(gw_ctx* ctx, const double* start, int blk, int k, const dou
   std::vector<double> om;
   TRY(check_omega(ctx, omega, 1, &om));
   for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
+  ctx->pcg_iters = 0;
   const size_t fb = (size_t)ctx->N3 * sizeof(double);
   const void* x0;
   TRY(stage_in(ctx, "lz_x0", start, fb, dev, &x0));
@@ -1383,6 +1385,7 @@ gw_status gw_stats(const gw_ctx* ctx, double* out, int n) {
   if (!ctx || !out || n < 0) return GW_E_ARG;
   for (int i = 0; i < n && i < 6; ++i) out[i] = ctx->stats[i];
   if (n > 6) out[6] = (double)g_launches;
+  if (n > 7) out[7] = (double)ctx->pcg_iters;
   return GW_OK;
 }
 
