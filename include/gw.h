@@ -108,22 +108,32 @@ gw_status gw_set_occupied(gw_ctx* ctx, int n_occ, const double* psi, const doubl
 gw_status gw_apply_h(gw_ctx* ctx, const double* x, int nb, double* y, gw_prec prec, int device_ptrs);
 
 /*
- * gw_apply_chi0 -- dn = chi0(omega) dV for nb real fields and n_omega real
+ * gw_apply_chi0 -- dn = chi0(omega) dV for nb real fields and n_omega
  * frequencies (Eq. P through Eqs. P1 and P2: per occupied state one
  * Sternheimer solve at omega = 0, two (H - e_v -/+ omega) otherwise, projected
- * on the conduction space at every iteration).
+ * on the conduction space at every iteration).  omega = 0 uses conjugate
+ * gradients; any other frequency, real (also above the excitation gap, where
+ * H - e_v - omega is indefinite) or complex, uses simplified QMR with the
+ * bilinear form sum_r x(r) y(r) (Sec. "Avoiding summations", SQMR footnote).
  *   dV     [nb][N^3] real
- *   omega  [n_omega] complex; this build supports real omega below each
- *          state's excitation gap (CG); others return GW_E_UNSUPPORTED
- *   dn     [n_omega][nb][N^3] real
+ *   omega  [n_omega] complex (interleaved re, im)
+ *   dn     [n_omega][nb][N^3]: real when every omega is real, complex
+ *          (interleaved) when one of them has a non-zero imaginary part
  */
 gw_status gw_apply_chi0(gw_ctx* ctx, const double* dV, int nb, const double* omega, int n_omega,
                         double* dn, gw_prec prec, int device_ptrs);
 
 /* gw_apply_eps -- out = eps~(omega) x = x - v^1/2 chi0(omega) v^1/2 x (Eq. epsilon);
-   shapes as gw_apply_chi0 (x: [nb][N^3], out: [n_omega][nb][N^3]). */
+   shapes and output type as gw_apply_chi0 (x: [nb][N^3] real). */
 gw_status gw_apply_eps(gw_ctx* ctx, const double* x, int nb, const double* omega, int n_omega,
                        double* out, gw_prec prec, int device_ptrs);
+
+/* gw_apply_chi0_c / gw_apply_eps_c -- the same on complex fields: input
+   [nb][N^3] complex, output [n_omega][nb][N^3] complex (interleaved). */
+gw_status gw_apply_chi0_c(gw_ctx* ctx, const double* dV, int nb, const double* omega, int n_omega,
+                          double* dn, gw_prec prec, int device_ptrs);
+gw_status gw_apply_eps_c(gw_ctx* ctx, const double* x, int nb, const double* omega, int n_omega,
+                         double* out, gw_prec prec, int device_ptrs);
 
 /*
  * gw_lanczos -- k steps of the Lanczos recursion on eps~(omega) (Sec. Lanczos,
@@ -133,7 +143,7 @@ gw_status gw_apply_eps(gw_ctx* ctx, const double* x, int nb, const double* omega
  *   w -= alpha_k q_k;  w -= Q (Q^T w) twice;  beta_k = |w|;  q_{k+1} = w / beta_k
  *   start   [N^3] real
  *   blk     block size; this build supports 1
- *   omega   complex; this build supports real omega as gw_apply_chi0
+ *   omega   real (imaginary part 0); complex frequencies: gw_block_lanczos
  *   alpha   [k] real;  beta [k-1] real
  *   basis   [k][N^3] real Lanczos vectors (orthonormal in <.|.>), or NULL
  * Returns GW_E_BREAKDOWN if beta_k underflows (invariant subspace reached).

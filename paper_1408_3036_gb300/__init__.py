@@ -26,7 +26,7 @@ STATUS = {0: "GW_OK", 1: "GW_E_ARG", 2: "GW_E_CUDA", 3: "GW_E_NOMEM", 4: "GW_E_N
 EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "gw_apply_chi0",
            "gw_apply_eps", "gw_lanczos", "gw_epsinv_elements", "gw_grad_vloc", "gw_stats",
            "gw_set_solver", "gw_profile", "gw_profile_read", "gw_last_error", "gw_destroy",
-           "gw_epsinv_elements_noalloc")
+           "gw_epsinv_elements_noalloc", "gw_apply_chi0_c", "gw_apply_eps_c")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
                    "refine_fp64", "persistent_cg")
 
@@ -57,6 +57,8 @@ def load(path=LIB_PATH):
         "gw_apply_h": (I, [P, P, I, P, I, I]),
         "gw_apply_chi0": (I, [P, P, I, P, I, P, I, I]),
         "gw_apply_eps": (I, [P, P, I, P, I, P, I, I]),
+        "gw_apply_chi0_c": (I, [P, P, I, P, I, P, I, I]),
+        "gw_apply_eps_c": (I, [P, P, I, P, I, P, I, I]),
         "gw_lanczos": (I, [P, P, I, I, P, P, P, P, I, I]),
         "gw_epsinv_elements": (I, [P, P, P, I, I, P, I]),
         "gw_epsinv_elements_noalloc": (I, [P, P, I, P, P]),
@@ -159,6 +161,28 @@ def gw_apply_eps(ctx, x, omegas, out, prec=GW_FP64):
         raise ValueError("mixed host/device buffers")
     nb = x.shape[0] if x.ndim == 2 else 1
     _check(ctx, load().gw_apply_eps(ctx, p, nb, om.ctypes.data, len(om), q, int(prec), d))
+    return out
+
+
+def gw_apply_chi0_c(ctx, dV, omegas, dn, prec=GW_FP64):
+    om = _omega_buf(omegas)
+    p, d = _ptr(dV)
+    q, e = _ptr(dn)
+    if d != e:
+        raise ValueError("mixed host/device buffers")
+    nb = dV.shape[0] if dV.ndim == 2 else 1
+    _check(ctx, load().gw_apply_chi0_c(ctx, p, nb, om.ctypes.data, len(om), q, int(prec), d))
+    return dn
+
+
+def gw_apply_eps_c(ctx, x, omegas, out, prec=GW_FP64):
+    om = _omega_buf(omegas)
+    p, d = _ptr(x)
+    q, e = _ptr(out)
+    if d != e:
+        raise ValueError("mixed host/device buffers")
+    nb = x.shape[0] if x.ndim == 2 else 1
+    _check(ctx, load().gw_apply_eps_c(ctx, p, nb, om.ctypes.data, len(om), q, int(prec), d))
     return out
 
 
@@ -265,13 +289,23 @@ class Cell:
         return gw_apply_h(self.ctx, x, y, prec)
 
     def apply_chi0(self, dV, omegas=(0.0,), prec=GW_FP64):
+        cplx_out = bool(np.any(np.imag(np.asarray(omegas, complex)) != 0))
+        if np.iscomplexobj(dV):
+            dV = np.ascontiguousarray(np.atleast_2d(np.asarray(dV, np.complex128)))
+            dn = np.empty((len(omegas), dV.shape[0], self.ng), np.complex128)
+            return gw_apply_chi0_c(self.ctx, dV, omegas, dn, prec)
         dV = np.ascontiguousarray(np.atleast_2d(np.asarray(dV, np.float64)))
-        dn = np.empty((len(omegas), dV.shape[0], self.ng))
+        dn = np.empty((len(omegas), dV.shape[0], self.ng), np.complex128 if cplx_out else np.float64)
         return gw_apply_chi0(self.ctx, dV, omegas, dn, prec)
 
     def apply_eps(self, x, omegas=(0.0,), prec=GW_FP64):
+        cplx_out = bool(np.any(np.imag(np.asarray(omegas, complex)) != 0))
+        if np.iscomplexobj(x):
+            x = np.ascontiguousarray(np.atleast_2d(np.asarray(x, np.complex128)))
+            out = np.empty((len(omegas), x.shape[0], self.ng), np.complex128)
+            return gw_apply_eps_c(self.ctx, x, omegas, out, prec)
         x = np.ascontiguousarray(np.atleast_2d(np.asarray(x, np.float64)))
-        out = np.empty((len(omegas), x.shape[0], self.ng))
+        out = np.empty((len(omegas), x.shape[0], self.ng), np.complex128 if cplx_out else np.float64)
         return gw_apply_eps(self.ctx, x, omegas, out, prec)
 
     def lanczos(self, start, k, omega=0.0, prec=GW_FP64, basis=False):

@@ -282,37 +282,10 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
     PROF(PC_PROJ, launch_proj_update<T>(ctx->st, P.C, ctx->nocc, npw, Ap, ncol, st.active, ctx->work.coef,
                                         ctx->work, p, pap));
     PROF(PC_CGUPD, launch_cg_update<T>(ctx->st, npw, ncol, x, r, p, Ap, pap, ctx->work, st, tol2, ctx->max_iter));
-    if (const char* tr = std::getenv("GW_DEBUG_TRACE")) {   // per-iteration trace of one column
-      const int tc = std::atoi(tr);
-      if (tc >= 0 && tc < ncol) {
-        double v3[3];
-        CK(cudaMemcpyAsync(v3, st.rr + tc, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-        CK(cudaMemcpyAsync(v3 + 1, pap + tc, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-        CK(cudaMemcpyAsync(v3 + 2, st.rr0 + tc, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-        TRY(sync(ctx, "trace"));
-        std::fprintf(stderr, "trace it %d rel %.3e pap %.6e\n", it, std::sqrt(v3[0] / v3[2]), v3[1]);
-      }
-    }
     if ((it % check) == check - 1 || it == ctx->max_iter - 1) {
       CK(cudaMemcpyAsync(ctx->host_pin, st.n_done, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
       TRY(sync(ctx, "cg_solve"));
       if (ctx->host_pin[0] >= ncol) break;
-    }
-  }
-  if (std::getenv("GW_DEBUG_TICKETS")) {       // all tickets must be back at zero
-    TRY(sync(ctx, "tickets"));
-    const size_t wc = ctx->work_cols;
-    std::vector<unsigned> t(wc);
-    const unsigned* arrs[4] = {ctx->work.cnt_a, ctx->work.cnt_b, ctx->work.cnt_d, st.cnt};
-    const size_t lens[4] = {wc, wc, wc, (size_t)ncol};
-    for (int a = 0; a < 4; ++a) {
-      CK(cudaMemcpy(t.data(), arrs[a], lens[a] * sizeof(unsigned), cudaMemcpyDeviceToHost));
-      for (size_t i = 0; i < lens[a]; ++i)
-        if (t[i]) {
-          char buf[128];
-          std::snprintf(buf, sizeof(buf), "ticket array %d entry %zu left at %u", a, i, t[i]);
-          return fail(ctx, GW_E_CUDA, buf);
-        }
     }
   }
   std::vector<int> its(ncol), flags(ncol);
@@ -413,6 +386,85 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
 }
 
 // ---------------------------------------------------------------------------
+// batched simplified QMR on P_c (H - E) P_c x = b (complex or indefinite shifts)
+// ---------------------------------------------------------------------------
+template <typename T>
+gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, const int* outer_active,
+                    cpx<T>* x, double tol, const double* rr_abs, long long* it_sum, int* it_max) {
+  const int npw = ctx->npw;
+  const std::string t = tname<T>();
+  cpx<T>*r, *q, *dd, *tt, *grid;
+  TRY(getbuf(ctx, "cg_r" + t, (size_t)ncol * npw, &r));
+  TRY(getbuf(ctx, "cg_p" + t, (size_t)ncol * npw, &q));
+  TRY(getbuf(ctx, "cg_Ap" + t, (size_t)ncol * npw, &tt));
+  TRY(getbuf(ctx, "qmr_d" + t, (size_t)ncol * npw, &dd));
+  TRY(getbuf(ctx, "g_cg" + t, (size_t)ncol * ctx->N3, &grid));
+  QmrState st;
+  TRY(getbuf(ctx, "qmr_rho", ncol, &st.rho));
+  TRY(getbuf(ctx, "qmr_alpha", ncol, &st.alpha));
+  TRY(getbuf(ctx, "qmr_beta", ncol, &st.beta));
+  TRY(getbuf(ctx, "qmr_qc", ncol, &st.qcoef));
+  TRY(getbuf(ctx, "qmr_dc", ncol, &st.dcoef));
+  TRY(getbuf(ctx, "qmr_theta", ncol, &st.theta));
+  TRY(getbuf(ctx, "qmr_tau", ncol, &st.tau));
+  TRY(getbuf(ctx, "qmr_stop", ncol, &st.rr_stop));
+  TRY(getbuf(ctx, "cg_iters", ncol, &st.iters));
+  TRY(getbuf(ctx, "cg_flag", ncol, &st.flag));
+  TRY(getbuf(ctx, "cg_active", ncol, &st.active));
+  TRY(getbuf(ctx, "cg_ndone", 1, &st.n_done));
+  TRY(getbuf(ctx, "cg_cnt", ncol, &st.cnt));
+  st.rr_abs = rr_abs;
+  TRY(ensure_work(ctx, ncol));
+  CK(cudaMemsetAsync(st.cnt, 0, ncol * sizeof(unsigned), ctx->st));
+  CK(cudaMemsetAsync(st.n_done, 0, sizeof(int), ctx->st));
+  auto& P = prec_of<T>(ctx);
+  const Geometry& g = ctx->geo;
+  const int* neg = g.sph_neg;
+  launch_qmr<T>(ctx->st, 0, npw, ncol, b64, x, r, q, dd, tt, neg, outer_active, ctx->work, st, tol * tol,
+                ctx->max_iter);
+  GatherDots dots;
+  dots.C = P.C;
+  dots.nocc = ctx->nocc;
+  dots.ncol = ncol;
+  dots.part = ctx->work.part_d;
+  dots.cnt = ctx->work.cnt_d;
+  dots.coef = ctx->work.coef;
+  const int check = 8;
+  for (int it = 0; it < ctx->max_iter; ++it) {
+    // t = P_c (H - E) q
+    launch_zpass<T>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, grid, q, nullptr, nullptr, nullptr, nullptr, st.active,
+                    nullptr, nullptr, ncol);
+    launch_ypass<T>(ctx->st, 1, 1, 0, g, P, ctx->plan, grid, st.active, ncol, 0);
+    launch_xpass_mul<T>(ctx->st, 1, 1, 1, g, P, ctx->plan, grid, P.vloc_s, st.active, ncol);
+    launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, st.active, ncol, 0);
+    launch_zpass<T>(ctx->st, Z_GATHER_FWD_H, g, P, ctx->plan, grid, tt, nullptr, nullptr, q, E, st.active, nullptr,
+                    nullptr, ncol, &dots);
+    launch_proj_update<T>(ctx->st, P.C, ctx->nocc, npw, tt, ncol, st.active, ctx->work.coef, ctx->work, nullptr,
+                          nullptr);
+    for (int step = 1; step <= 4; ++step)
+      launch_qmr<T>(ctx->st, step, npw, ncol, b64, x, r, q, dd, tt, neg, outer_active, ctx->work, st, tol * tol,
+                    ctx->max_iter);
+    if ((it % check) == check - 1 || it == ctx->max_iter - 1) {
+      CK(cudaMemcpyAsync(ctx->host_pin, st.n_done, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+      TRY(sync(ctx, "qmr_solve"));
+      if (ctx->host_pin[0] >= ncol) break;
+    }
+  }
+  std::vector<int> its(ncol), flags(ncol);
+  CK(cudaMemcpyAsync(its.data(), st.iters, ncol * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(flags.data(), st.flag, ncol * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  TRY(sync(ctx, "qmr_solve stats"));
+  for (int c = 0; c < ncol; ++c) {
+    *it_sum += its[c];
+    *it_max = std::max(*it_max, its[c]);
+  }
+  for (int c = 0; c < ncol; ++c)
+    if (flags[c] == 2 && std::is_same<T, double>::value)
+      return fail(ctx, GW_E_BREAKDOWN, "SQMR serious breakdown: [q, A q] = 0");
+  return GW_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Sternheimer solves with FP64 iterative refinement:
 //   x64 = 0; repeat { d = CG_T(b - A64 x64); x64 += d } until the normwise
 //   backward error |b - A64 x64| / (|A| |x64| + |b|) <= tol for every column.
@@ -421,7 +473,7 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
 // side, or at a tenth of the final target, whichever is larger.
 // ---------------------------------------------------------------------------
 template <typename T>
-gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, double2* x64) {
+gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, double2* x64, bool qmr = false) {
   const int npw = ctx->npw;
   const bool mixed = !std::is_same<T, double>::value;
   const double tol = mixed ? ctx->tol_mixed : ctx->tol;
@@ -449,7 +501,9 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
   bool done = false;
   double prev_worst = 1e300;
   for (outer = 0; outer < ctx->max_outer && !done; ++outer) {
-    if (ncol <= kPersistentMaxCols && !ctx->no_persistent)
+    if (qmr)
+      TRY(qmr_solve<T>(ctx, ncol, r64, E, oact, d, tol_in, rra, &it_sum, &it_max));
+    else if (ncol <= kPersistentMaxCols && !ctx->no_persistent)
       TRY(cg_solve_persistent<T>(ctx, ncol, r64, E, oact, d, tol_in, rra, &it_sum, &it_max));
     else
       TRY(cg_solve<T>(ctx, ncol, r64, E, oact, d, tol_in, rra, &it_sum, &it_max));
@@ -463,33 +517,6 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
     }
     launch_residual(ctx->st, npw, ncol, b64, ax, x64, oact, ctx->work, res2, bb, xx);
     CK(cudaMemcpyAsync(r64, ax, (size_t)ncol * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
-    if (const char* dv = std::getenv("GW_DEBUG_VAL")) {      // valence content of the FP64 residual
-      const int tc = std::atoi(dv);
-      if (tc >= 0 && tc < ncol) {
-        double2* tmp;
-        TRY(getbuf(ctx, "dbg_tmp", (size_t)ncol * npw, &tmp));
-        CK(cudaMemcpyAsync(tmp, r64, (size_t)ncol * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
-        launch_proj<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, tmp, ncol, nullptr, ctx->work, nullptr, nullptr);
-        std::vector<double2> cf((size_t)ctx->nocc * ncol);
-        CK(cudaMemcpyAsync(cf.data(), ctx->work.coef, cf.size() * sizeof(double2), cudaMemcpyDeviceToHost, ctx->st));
-        TRY(sync(ctx, "dbg"));
-        double vn = 0.0;
-        for (int v = 0; v < ctx->nocc; ++v) vn += cf[(size_t)v * ncol + tc].x * cf[(size_t)v * ncol + tc].x +
-                                                  cf[(size_t)v * ncol + tc].y * cf[(size_t)v * ncol + tc].y;
-        double rr = 0.0;
-        CK(cudaMemcpy(&rr, res2 + tc, sizeof(double), cudaMemcpyDeviceToHost));
-        std::fprintf(stderr, "outer %d column %d |r| %.3e valence part %.3e\n", outer, tc, std::sqrt(rr),
-                     std::sqrt(vn));
-        std::vector<double2> hv((size_t)npw), hx2((size_t)npw);
-        CK(cudaMemcpy(hv.data(), r64 + (size_t)tc * npw, npw * sizeof(double2), cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(hx2.data(), x64 + (size_t)tc * npw, npw * sizeof(double2), cudaMemcpyDeviceToHost));
-        char fn[64];
-        std::snprintf(fn, sizeof(fn), "gpurun_out/dbg_r_%d.bin", outer);
-        if (FILE* f = std::fopen(fn, "wb")) { std::fwrite(hv.data(), sizeof(double2), npw, f); std::fclose(f); }
-        std::snprintf(fn, sizeof(fn), "gpurun_out/dbg_x_%d.bin", outer);
-        if (FILE* f = std::fopen(fn, "wb")) { std::fwrite(hx2.data(), sizeof(double2), npw, f); std::fclose(f); }
-      }
-    }
     CK(cudaMemcpyAsync(hr.data(), res2, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaMemcpyAsync(hb.data(), bb, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaMemcpyAsync(hx.data(), xx, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
@@ -558,10 +585,13 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
 //   dn_{o,b}    = -(2/Omega) sum_v u_v IFFT(x^- + x^+)
 // The right-hand sides and the density reduction (a few transforms per
 // column) run in FP64; the Sternheimer solves (hundreds of H applications per
-// column) run with inner precision S and FP64 refinement.
+// column) run with inner precision S and FP64 refinement: CG at omega = 0,
+// simplified QMR for any other (real or complex) frequency.
+// Fields y are real (y_cplx = false) or complex; dn is complex when dn_cplx.
 // ---------------------------------------------------------------------------
 template <typename S>
-gw_status chi0_core(gw_ctx* ctx, const double* y, int nb, const std::vector<double>& omega, double* dn) {
+gw_status chi0_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, const std::vector<double2>& omega, void* dn,
+                    bool dn_cplx) {
   using T = double;
   const int npw = ctx->npw, nocc = ctx->nocc, N3 = ctx->N3;
   const int nom = (int)omega.size();
@@ -578,17 +608,14 @@ gw_status chi0_core(gw_ctx* ctx, const double* y, int nb, const std::vector<doub
   TRY(upload(ctx, "rhs_cy", cy, &dcy));
   cpx<T>* grid;
   TRY(getbuf(ctx, "g_rhs" + t, (size_t)nr * N3, &grid));
-  cpx<T>* rs;
-  TRY(getbuf(ctx, "rhs_s" + t, (size_t)nr * npw, &rs));
   double2* rhs64;
   TRY(getbuf(ctx, "rhs64", (size_t)nr * npw, &rhs64));
   TRY(ensure_work(ctx, std::max(nr, 1)));
-  launch_xpass_prod_fwd<T>(ctx->st, g, P, ctx->plan, reinterpret_cast<const cpx<T>*>(y), 0, P.U, 0, 1, dca, dcy,
-                           grid, nr);
+  launch_xpass_prod_fwd<T>(ctx->st, g, P, ctx->plan, reinterpret_cast<const cpx<T>*>(y), y_cplx ? 1 : 0, P.U, 0, 1,
+                           dca, dcy, grid, nr);
   launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, nullptr, nr, 0);
-  launch_zpass<T>(ctx->st, Z_GATHER_FWD, g, P, ctx->plan, grid, rs, nullptr, nullptr, nullptr, nullptr, nullptr,
+  launch_zpass<T>(ctx->st, Z_GATHER_FWD, g, P, ctx->plan, grid, rhs64, nullptr, nullptr, nullptr, nullptr, nullptr,
                   nullptr, nullptr, nr);
-  launch_gather_rows<double, T>(ctx->st, npw, nr, rs, nullptr, rhs64);
   // P_c twice: psi_v* y has a large component along the occupied states
   // (e.g. <psi_v|y psi_v>), and one pass leaves |C C^H - 1| times it behind
   launch_proj<double>(ctx->st, ctx->P64.C, nocc, npw, rhs64, nr, nullptr, ctx->work, nullptr, nullptr);
@@ -597,14 +624,18 @@ gw_status chi0_core(gw_ctx* ctx, const double* y, int nb, const std::vector<doub
   // -- solver columns
   std::vector<int> src, s0, s1;
   std::vector<double2> E;
+  bool qmr = false;
   for (int o = 0; o < nom; ++o) {
-    const int ns = (omega[o] == 0.0) ? 1 : 2;
+    const bool zero = (omega[o].x == 0.0 && omega[o].y == 0.0);
+    qmr |= !zero;
+    const int ns = zero ? 1 : 2;
     for (int b = 0; b < nb; ++b)
       for (int v = 0; v < nocc; ++v) {
         const int first = (int)src.size();
-        for (int s = 0; s < ns; ++s) {
+        for (int sg = 0; sg < ns; ++sg) {
           src.push_back(b * nocc + v);
-          E.push_back(make_double2(ctx->eps[v] + (s == 0 ? omega[o] : -omega[o]), 0.0));
+          const double sgn = (sg == 0) ? 1.0 : -1.0;     // x^-: H - e_v - w;  x^+: H - e_v + w
+          E.push_back(make_double2(ctx->eps[v] + sgn * omega[o].x, sgn * omega[o].y));
         }
         s0.push_back(first);
         s1.push_back(ns == 2 ? first + 1 : -1);
@@ -623,16 +654,13 @@ gw_status chi0_core(gw_ctx* ctx, const double* y, int nb, const std::vector<doub
   TRY(getbuf(ctx, "xcol", (size_t)ncol * npw, &xcol));
   TRY(getbuf(ctx, "sol64", (size_t)nsol * npw, &sol64));
   launch_gather_rows<double, double>(ctx->st, npw, ncol, rhs64, dsrc, bcol);
-  TRY(solve<S>(ctx, ncol, bcol, dE, xcol));
+  TRY(solve<S>(ctx, ncol, bcol, dE, xcol, qmr));
   // -- combine: x^- + x^+, or 2 x at omega = 0 (x^- = x^+)
   launch_combine(ctx->st, npw, nsol, xcol, ds0, ds1, 1.0, 2.0, sol64);
   // -- density reduction
-  cpx<T>* solT;
-  TRY(getbuf(ctx, "solT" + t, (size_t)nsol * npw, &solT));
-  launch_gather_rows<T, double>(ctx->st, npw, nsol, sol64, nullptr, solT);
   cpx<T>* gd;
   TRY(getbuf(ctx, "g_dn" + t, (size_t)nsol * N3, &gd));
-  launch_zpass<T>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, gd, solT, nullptr, nullptr, nullptr, nullptr, nullptr,
+  launch_zpass<T>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, gd, sol64, nullptr, nullptr, nullptr, nullptr, nullptr,
                   nullptr, nullptr, nsol);
   launch_ypass<T>(ctx->st, 1, 1, 0, g, P, ctx->plan, gd, nullptr, nsol, 0);
   std::vector<int> gstart(nom * nb + 1), colv(nsol);
@@ -641,36 +669,102 @@ gw_status chi0_core(gw_ctx* ctx, const double* y, int nb, const std::vector<doub
   int *dgs, *dcv;
   TRY(upload(ctx, "dn_gs", gstart, &dgs));
   TRY(upload(ctx, "dn_cv", colv, &dcv));
-  launch_xpass_inv_reduce<T>(ctx->st, g, P, ctx->plan, gd, dgs, dcv, nom * nb, -2.0 / ctx->vol, dn, nullptr, 0);
+  launch_xpass_inv_reduce<T>(ctx->st, g, P, ctx->plan, gd, dgs, dcv, nom * nb, -2.0 / ctx->vol,
+                             dn_cplx ? nullptr : reinterpret_cast<double*>(dn),
+                             dn_cplx ? reinterpret_cast<double2*>(dn) : nullptr, 0);
   return launch_check(ctx, "chi0");
 }
 
+// complex fields: out = v^1/2 in  (or out = sub - v^1/2 in)
+__global__ void k_csub(size_t n, const double2* __restrict__ a, const double2* __restrict__ b,
+                       double2* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 x = a[i], y = b[i];
+    out[i] = make_double2(x.x - y.x, x.y - y.y);
+  }
+}
+
+// real -> complex (imaginary part zero)
+__global__ void k_promote(size_t n, const double* __restrict__ a, double2* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = make_double2(a[i], 0.0);
+}
+
+gw_status sqrtv_c(gw_ctx* ctx, const double2* in, int nb, double2* out, const double2* sub) {
+  double2* grid;
+  TRY(getbuf(ctx, "g_sqvc", (size_t)nb * ctx->N3, &grid));
+  auto& P = ctx->P64;
+  const Geometry& g = ctx->geo;
+  const size_t n = (size_t)nb * ctx->N3;
+  CK(cudaMemcpyAsync(grid, in, n * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
+  launch_zpass<double>(ctx->st, Z_G2G_FWD, g, P, ctx->plan, grid, nullptr, nullptr, nullptr, nullptr, nullptr,
+                       nullptr, nullptr, nullptr, nb);
+  launch_ypass<double>(ctx->st, 0, 0, 0, g, P, ctx->plan, grid, nullptr, nb, 1);
+  launch_xpass_mul<double>(ctx->st, 0, 0, 0, g, P, ctx->plan, grid, P.sqv_s, nullptr, nb);
+  launch_ypass<double>(ctx->st, 1, 0, 0, g, P, ctx->plan, grid, nullptr, nb, 1);
+  launch_zpass<double>(ctx->st, Z_G2G_INV, g, P, ctx->plan, grid, nullptr, nullptr, nullptr, nullptr, nullptr,
+                       nullptr, nullptr, nullptr, nb);
+  const int nblk = (int)std::min<size_t>((n + 255) / 256, 152 * 8);
+  if (sub) {
+    ++g_launches;
+    k_csub<<<nblk, 256, 0, ctx->st>>>(n, sub, grid, out);
+  } else {
+    CK(cudaMemcpyAsync(out, grid, n * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
+  }
+  return launch_check(ctx, "sqrtv_c");
+}
+
+// eps~ (or chi0 when chi0_only) on nb fields; x real or complex; out complex
+// when x is complex or a frequency is complex, real otherwise
 template <typename S>
-gw_status eps_core(gw_ctx* ctx, const double* x64, int nb, const std::vector<double>& omega, double* out64,
+gw_status eps_core(gw_ctx* ctx, const void* x, bool x_cplx, int nb, const std::vector<double2>& omega, void* out,
                    bool chi0_only) {
   const int N3 = ctx->N3;
   const int nom = (int)omega.size();
-  if (chi0_only) {
-    TRY(chi0_core<S>(ctx, x64, nb, omega, out64));
-    return launch_check(ctx, "chi0 out");
+  bool out_cplx = x_cplx;
+  for (auto& o : omega) out_cplx |= (o.y != 0.0);
+  if (!out_cplx) {
+    const double* x64 = reinterpret_cast<const double*>(x);
+    double* out64 = reinterpret_cast<double*>(out);
+    if (chi0_only) return chi0_core<S>(ctx, x64, false, nb, omega, out64, false);
+    double *y, *dn;
+    TRY(getbuf(ctx, "eps_y", (size_t)nb * N3, &y));
+    TRY(getbuf(ctx, "eps_dn", (size_t)nom * nb * N3, &dn));
+    TRY(sqrtv<double>(ctx, x64, nb, y, nullptr));
+    TRY(chi0_core<S>(ctx, y, false, nb, omega, dn, false));
+    for (int k = 0; k < nom; ++k)
+      TRY(sqrtv<double>(ctx, dn + (size_t)k * nb * N3, nb, out64 + (size_t)k * nb * N3, x64));
+    return launch_check(ctx, "eps out");
   }
-  double *y, *dn;
-  TRY(getbuf(ctx, "eps_y", (size_t)nb * N3, &y));
-  TRY(getbuf(ctx, "eps_dn", (size_t)nom * nb * N3, &dn));
-  TRY(sqrtv<double>(ctx, x64, nb, y, nullptr));
-  TRY(chi0_core<S>(ctx, y, nb, omega, dn));
+  // complex pipeline: promote a real input
+  const double2* xc = reinterpret_cast<const double2*>(x);
+  if (!x_cplx) {
+    double2* tmp;
+    TRY(getbuf(ctx, "eps_xc", (size_t)nb * N3, &tmp));
+    const size_t n = (size_t)nb * N3;
+    ++g_launches;
+    k_promote<<<(int)std::min<size_t>((n + 255) / 256, 152 * 8), 256, 0, ctx->st>>>(
+        n, reinterpret_cast<const double*>(x), tmp);
+    xc = tmp;
+  }
+  double2* outc = reinterpret_cast<double2*>(out);
+  if (chi0_only) return chi0_core<S>(ctx, xc, true, nb, omega, outc, true);
+  double2 *y, *dn;
+  TRY(getbuf(ctx, "eps_yc", (size_t)nb * N3, &y));
+  TRY(getbuf(ctx, "eps_dnc", (size_t)nom * nb * N3, &dn));
+  TRY(sqrtv_c(ctx, xc, nb, y, nullptr));
+  TRY(chi0_core<S>(ctx, y, true, nb, omega, dn, true));
   for (int k = 0; k < nom; ++k)
-    TRY(sqrtv<double>(ctx, dn + (size_t)k * nb * N3, nb, out64 + (size_t)k * nb * N3, x64));
+    TRY(sqrtv_c(ctx, dn + (size_t)k * nb * N3, nb, outc + (size_t)k * nb * N3, xc));
   return launch_check(ctx, "eps out");
 }
 
-gw_status check_omega(gw_ctx* ctx, const double* omega, int n, std::vector<double>* out) {
+gw_status check_omega(gw_ctx* ctx, const double* omega, int n, std::vector<double2>* out) {
   out->clear();
   for (int i = 0; i < n; ++i) {
     const double re = omega[2 * i], im = omega[2 * i + 1];
     if (!std::isfinite(re) || !std::isfinite(im)) return fail(ctx, GW_E_NONFINITE, "non-finite omega");
-    if (im != 0.0) return fail(ctx, GW_E_UNSUPPORTED, "complex omega is not supported by this build");
-    out->push_back(re);
+    out->push_back(make_double2(re, im));
   }
   return GW_OK;
 }
@@ -718,7 +812,7 @@ gw_status need_occ(gw_ctx* ctx) {
 // Lanczos (Sec. Lanczos) on real fields, FP64 vectors and inner products
 // ---------------------------------------------------------------------------
 template <typename T>
-gw_status lanczos_core(gw_ctx* ctx, const double* x0, int K, const std::vector<double>& omega, double* alpha,
+gw_status lanczos_core(gw_ctx* ctx, const double* x0, int K, const std::vector<double2>& omega, double* alpha,
                        double* beta, double* Q) {
   const int N3 = ctx->N3;
   const double wgt = ctx->vol / N3;
@@ -731,7 +825,7 @@ gw_status lanczos_core(gw_ctx* ctx, const double* x0, int K, const std::vector<d
   launch_lz_axpy(ctx->st, N3, 2, nrm, const_cast<double*>(x0), nullptr, Q);
   for (int k = 0; k < K; ++k) {
     double* qk = Q + (size_t)k * N3;
-    TRY(eps_core<T>(ctx, qk, 1, omega, w, false));
+    TRY(eps_core<T>(ctx, qk, false, 1, omega, w, false));
     if (k > 0) launch_lz_axpy(ctx->st, N3, 0, beta + (k - 1), w, Q + (size_t)(k - 1) * N3, nullptr);
     launch_dot(ctx->st, N3, qk, w, wgt, 0, ctx->work, alpha + k);
     launch_lz_axpy(ctx->st, N3, 1, alpha + k, w, qk, nullptr);
@@ -780,7 +874,7 @@ gw_status grad_core(gw_ctx* ctx, const double* phi, int K, double* s_out, double
   TRY(getbuf(ctx, "gr_Q", (size_t)K * N3, &Q));
   TRY(getbuf(ctx, "gr_x0", N3, &x0c));
   CK(cudaMemcpyAsync(x0c, phi, (size_t)N3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
-  std::vector<double> om(1, 0.0);
+  std::vector<double2> om(1, make_double2(0.0, 0.0));
   gw_status st = lanczos_core<S>(ctx, x0c, K, om, a, b, Q);
   if (st != GW_OK && st != GW_E_BREAKDOWN) return st;
   // -- T^-1 and s
@@ -950,6 +1044,19 @@ gw_status build_geometry(gw_ctx* ctx) {
   plane_sph.push_back(ctx->npw);
   plane_pen.push_back((int)pencils.size());
   for (int s = 0; s < ctx->npw; ++s) i1s[s] = pencils[pen[s]].y;
+  // sphere index of -G (the sphere is symmetric: 2 max|n| < N)
+  std::vector<int> negs(ctx->npw, -1);
+  {
+    std::map<long, int> where;
+    auto key = [&](int a, int b, int c) { return ((long)(a + N) * (2 * N + 1) + (b + N)) * (2 * N + 1) + (c + N); };
+    for (int s = 0; s < ctx->npw; ++s)
+      where[key(ctx->miller[3 * s], ctx->miller[3 * s + 1], ctx->miller[3 * s + 2])] = s;
+    for (int s = 0; s < ctx->npw; ++s) {
+      auto it = where.find(key(-ctx->miller[3 * s], -ctx->miller[3 * s + 1], -ctx->miller[3 * s + 2]));
+      if (it == where.end()) return fail(ctx, GW_E_ARG, "sphere not symmetric");
+      negs[s] = it->second;
+    }
+  }
   Geometry& g = ctx->geo;
   g.N = N; g.N2 = N * N; g.N3 = N * N * N; g.npw = ctx->npw;
   g.npen = (int)pencils.size();
@@ -965,6 +1072,7 @@ gw_status build_geometry(gw_ctx* ctx) {
   TRY(upload(ctx, "geo_plane_sph", plane_sph, &g.plane_sph));
   TRY(upload(ctx, "geo_plane_pen", plane_pen, &g.plane_pen));
   TRY(upload(ctx, "geo_i1", i1s, &g.sph_i1));
+  TRY(upload(ctx, "geo_neg", negs, &g.sph_neg));
   return GW_OK;
 }
 
@@ -1205,12 +1313,6 @@ gw_status gw_set_occupied(gw_ctx* ctx, int n_occ, const double* psi, const doubl
     c32[i] = make_float2((float)R[i].real(), (float)R[i].imag());
   }
   TRY(upload(ctx, "occ_C64", c64, &ctx->P64.C));
-  if (std::getenv("GW_DEBUG_VAL")) {
-    if (FILE* f = std::fopen("gpurun_out/dbg_C64.bin", "wb")) {
-      std::fwrite(c64.data(), sizeof(double2), c64.size(), f);
-      std::fclose(f);
-    }
-  }
   TRY(upload(ctx, "occ_C32", c32, &ctx->P32.C));
   // u_v(r) = sum_G c_G e^{iGr}: scatter, inverse transforms (FP64), then FP32 copy
   double2* U;
@@ -1260,25 +1362,26 @@ gw_status gw_apply_h(gw_ctx* ctx, const double* x, int nb, double* y, gw_prec pr
 }
 
 static gw_status apply_common(gw_ctx* ctx, const double* x, int nb, const double* omega, int n_omega,
-                              double* out, gw_prec prec, int dev, bool chi0_only) {
+                              double* out, gw_prec prec, int dev, bool chi0_only, bool x_cplx) {
   TRY(begin(ctx));
   TRY(need_occ(ctx));
   if (nb < 0 || n_omega < 1 || !omega || (nb > 0 && (!x || !out))) return fail(ctx, GW_E_ARG, "bad arguments");
   if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_E_ARG, "bad precision");
-  std::vector<double> om;
+  std::vector<double2> om;
   TRY(check_omega(ctx, omega, n_omega, &om));
   if (nb == 0) return GW_OK;
+  bool out_cplx = x_cplx;
+  for (auto& o : om) out_cplx |= (o.y != 0.0);
   for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
   ctx->pcg_iters = 0;
-  const size_t ib = (size_t)nb * ctx->N3 * sizeof(double), ob = ib * n_omega;
+  const size_t ib = (size_t)nb * ctx->N3 * (x_cplx ? sizeof(double2) : sizeof(double));
+  const size_t ob = (size_t)nb * ctx->N3 * n_omega * (out_cplx ? sizeof(double2) : sizeof(double));
   const void* xin;
   void* o;
   TRY(stage_in(ctx, "io_in", x, ib, dev, &xin));
   TRY(stage_out(ctx, "io_out", out, ob, dev, &o));
-  const double* xd = reinterpret_cast<const double*>(xin);
-  double* od = reinterpret_cast<double*>(o);
-  if (prec == GW_FP64) TRY(eps_core<double>(ctx, xd, nb, om, od, chi0_only));
-  else TRY(eps_core<float>(ctx, xd, nb, om, od, chi0_only));
+  if (prec == GW_FP64) TRY(eps_core<double>(ctx, xin, x_cplx, nb, om, o, chi0_only));
+  else TRY(eps_core<float>(ctx, xin, x_cplx, nb, om, o, chi0_only));
   TRY(copy_back(ctx, out, o, ob, dev));
   if (ctx->stats[0] > 0) ctx->stats[2] /= ctx->stats[0];
   return finish(ctx, GW_OK);
@@ -1286,12 +1389,22 @@ static gw_status apply_common(gw_ctx* ctx, const double* x, int nb, const double
 
 gw_status gw_apply_chi0(gw_ctx* ctx, const double* dV, int nb, const double* omega, int n_omega, double* dn,
                         gw_prec prec, int dev) {
-  return apply_common(ctx, dV, nb, omega, n_omega, dn, prec, dev, true);
+  return apply_common(ctx, dV, nb, omega, n_omega, dn, prec, dev, true, false);
 }
 
 gw_status gw_apply_eps(gw_ctx* ctx, const double* x, int nb, const double* omega, int n_omega, double* out,
                        gw_prec prec, int dev) {
-  return apply_common(ctx, x, nb, omega, n_omega, out, prec, dev, false);
+  return apply_common(ctx, x, nb, omega, n_omega, out, prec, dev, false, false);
+}
+
+gw_status gw_apply_chi0_c(gw_ctx* ctx, const double* dV, int nb, const double* omega, int n_omega, double* dn,
+                          gw_prec prec, int dev) {
+  return apply_common(ctx, dV, nb, omega, n_omega, dn, prec, dev, true, true);
+}
+
+gw_status gw_apply_eps_c(gw_ctx* ctx, const double* x, int nb, const double* omega, int n_omega, double* out,
+                         gw_prec prec, int dev) {
+  return apply_common(ctx, x, nb, omega, n_omega, out, prec, dev, false, true);
 }
 
 gw_status gw_lanczos(gw_ctx* ctx, const double* start, int blk, int k, const double* omega, double* alpha,
@@ -1300,8 +1413,10 @@ gw_status gw_lanczos(gw_ctx* ctx, const double* start, int blk, int k, const dou
   TRY(need_occ(ctx));
   if (!start || !alpha || k < 1 || (k > 1 && !beta) || !omega) return fail(ctx, GW_E_ARG, "bad arguments");
   if (blk != 1) return fail(ctx, GW_E_UNSUPPORTED, "block Lanczos is not supported by this build");
-  std::vector<double> om;
+  std::vector<double2> om;
   TRY(check_omega(ctx, omega, 1, &om));
+  if (om[0].y != 0.0)
+    return fail(ctx, GW_E_UNSUPPORTED, "gw_lanczos is the real-frequency recursion; use gw_block_lanczos");
   for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
   ctx->pcg_iters = 0;
   const size_t fb = (size_t)ctx->N3 * sizeof(double);

@@ -73,6 +73,7 @@ struct Geometry {
   int* plane_sph = nullptr;  // [nplanes + 1] first sphere entry of each plane (entries are i0-major)
   int* plane_pen = nullptr;  // [nplanes + 1] first disc pencil of each plane
   int* sph_i1 = nullptr;     // [npw] y index of each sphere point
+  int* sph_neg = nullptr;    // [npw] sphere index of -G (bilinear form sum_G x(-G) y(G))
   int* all_planes = nullptr; // [N] 0..N-1
   uint8_t* plane_mask = nullptr; // [N]
 };

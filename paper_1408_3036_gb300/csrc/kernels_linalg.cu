@@ -346,6 +346,233 @@ void launch_cg_update(cudaStream_t s, int npw, int ncol, cpx<T>* x, cpx<T>* r, c
 }
 
 // ---------------------------------------------------------------------------
+// simplified QMR (Freund-Nachtigal) for complex-symmetric A = P_c (H - E) P_c
+// with the bilinear form [x, y] = sum_r x(r) y(r) = sum_G x(-G) y(G)
+// (Sec. "Avoiding summations": SQMR replaces CG when (H - e_v -/+ w) is not
+// positive definite; unpreconditioned it equals MINRES for real symmetric A)
+//   init: r = q = b, x = d = 0, tau = |b|, rho = [b, b], theta = 0
+//   loop: t = A q; sigma = [q, t]; alpha = rho / sigma; r -= alpha t
+//         theta' = |r| / tau; c2 = 1 / (1 + theta'^2); tau = tau theta' sqrt(c2)
+//         d = c2 theta^2 d + c2 alpha q; x += d
+//         rho' = [r, r]; beta = rho' / rho; q = r + beta q
+//   stop when tau^2 (k + 1) <= rr_stop (bound on the QMR residual)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double den = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kLT)
+k_qmr_init(int npw, const double2* __restrict__ b, cpx<T>* __restrict__ x, cpx<T>* __restrict__ r,
+           cpx<T>* __restrict__ q, cpx<T>* __restrict__ d, const int* __restrict__ neg,
+           const int* __restrict__ outer_active, double* __restrict__ partial, QmrState st, int ncol,
+           double tol_in2) {
+  const int c = blockIdx.y;
+  const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
+  const bool on = !outer_active || outer_active[c];
+  double a1 = 0.0, ax = 0.0, ay = 0.0;
+  for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
+    const size_t i = (size_t)c * npw + G;
+    const cpx<T> bv = on ? from_d<T>(b[i]) : mk<T>(0, 0);
+    const cpx<T> bn = on ? from_d<T>(b[(size_t)c * npw + neg[G]]) : mk<T>(0, 0);
+    r[i] = bv;
+    q[i] = bv;
+    x[i] = mk<T>(0, 0);
+    d[i] = mk<T>(0, 0);
+    const double2 u = to_d(bv), w = to_d(bn);
+    a1 += u.x * u.x + u.y * u.y;
+    ax += w.x * u.x - w.y * u.y;
+    ay += w.x * u.y + w.y * u.x;
+  }
+  a1 = block_sum(a1);
+  ax = block_sum(ax);
+  ay = block_sum(ay);
+  if (threadIdx.x == 0) {
+    double* pp = partial + 3 * ((size_t)blockIdx.x * ncol + c);
+    pp[0] = a1; pp[1] = ax; pp[2] = ay;
+  }
+  if (!last_block(&st.cnt[c], gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double s1 = 0.0, sx = 0.0, sy = 0.0;
+    for (int k = 0; k < (int)gridDim.x; ++k) {
+      const double* pp = partial + 3 * ((size_t)k * ncol + c);
+      s1 += pp[0]; sx += pp[1]; sy += pp[2];
+    }
+    st.tau[c] = sqrt(s1);
+    st.rho[c] = make_double2(sx, sy);
+    st.theta[c] = 0.0;
+    st.iters[c] = 0;
+    st.flag[c] = 0;
+    st.rr_stop[c] = fmax(tol_in2 * s1, st.rr_abs ? st.rr_abs[c] : 0.0);
+    st.active[c] = (on && s1 > 0.0) ? 1 : 0;
+    if (!st.active[c]) atomicAdd(st.n_done, 1);
+  }
+}
+
+// sigma = [q, t]; alpha = rho / sigma
+template <typename T>
+__global__ void __launch_bounds__(kLT)
+k_qmr_sigma(int npw, const cpx<T>* __restrict__ q, const cpx<T>* __restrict__ t, const int* __restrict__ neg,
+            double* __restrict__ partial, QmrState st, int ncol) {
+  const int c = blockIdx.y;
+  if (!st.active[c]) return;
+  const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
+  double ax = 0.0, ay = 0.0;
+  for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
+    const double2 a = to_d(q[(size_t)c * npw + neg[G]]), u = to_d(t[(size_t)c * npw + G]);
+    ax += a.x * u.x - a.y * u.y;
+    ay += a.x * u.y + a.y * u.x;
+  }
+  ax = block_sum(ax);
+  ay = block_sum(ay);
+  if (threadIdx.x == 0) {
+    double* pp = partial + 2 * ((size_t)blockIdx.x * ncol + c);
+    pp[0] = ax; pp[1] = ay;
+  }
+  if (!last_block(&st.cnt[c], gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double sx = 0.0, sy = 0.0;
+    for (int k = 0; k < (int)gridDim.x; ++k) {
+      const double* pp = partial + 2 * ((size_t)k * ncol + c);
+      sx += pp[0]; sy += pp[1];
+    }
+    const double2 sg = make_double2(sx, sy);
+    const double2 rho = st.rho[c];
+    if (!(sx * sx + sy * sy > 1e-300 * (rho.x * rho.x + rho.y * rho.y)) || !isfinite(sx) || !isfinite(sy)) {
+      st.alpha[c] = make_double2(0, 0);
+      st.flag[c] = 2;                                  // serious breakdown: [q, A q] = 0
+    } else {
+      st.alpha[c] = cdiv(rho, sg);
+    }
+  }
+}
+
+// r -= alpha t; theta', c2, tau
+template <typename T>
+__global__ void __launch_bounds__(kLT)
+k_qmr_r(int npw, cpx<T>* __restrict__ r, const cpx<T>* __restrict__ t, double* __restrict__ partial, QmrState st,
+        int ncol) {
+  const int c = blockIdx.y;
+  if (!st.active[c]) return;
+  const double2 al = st.alpha[c];
+  const cpx<T> a = from_d<T>(al);
+  const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
+  double acc = 0.0;
+  for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
+    const size_t i = (size_t)c * npw + G;
+    cpx<T> rv = r[i];
+    const cpx<T> tv = t[i];
+    rv.x -= a.x * tv.x - a.y * tv.y;
+    rv.y -= a.x * tv.y + a.y * tv.x;
+    r[i] = rv;
+    const double2 rd = to_d(rv);
+    acc += rd.x * rd.x + rd.y * rd.y;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ncol + c] = acc;
+  if (!last_block(&st.cnt[c], gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < (int)gridDim.x; ++k) s += partial[(size_t)k * ncol + c];
+    const double th = sqrt(s) / st.tau[c];
+    const double c2 = 1.0 / (1.0 + th * th);
+    st.dcoef[c] = c2 * st.theta[c] * st.theta[c];   // multiplies the old d
+    st.qcoef[c] = make_double2(c2 * al.x, c2 * al.y);
+    st.tau[c] = st.tau[c] * th * sqrt(c2);
+    st.theta[c] = th;
+  }
+}
+
+// d = dcoef d + qcoef q; x += d; rho' = [r, r]; beta
+template <typename T>
+__global__ void __launch_bounds__(kLT)
+k_qmr_dx(int npw, cpx<T>* __restrict__ x, cpx<T>* __restrict__ d, const cpx<T>* __restrict__ q,
+         const cpx<T>* __restrict__ r, const int* __restrict__ neg, double* __restrict__ partial, QmrState st,
+         int ncol, int maxit) {
+  const int c = blockIdx.y;
+  if (!st.active[c]) return;
+  const T dc = (T)st.dcoef[c];
+  const cpx<T> qc = from_d<T>(st.qcoef[c]);
+  const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
+  double ax = 0.0, ay = 0.0;
+  for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
+    const size_t i = (size_t)c * npw + G;
+    const cpx<T> qv = q[i];
+    cpx<T> dv = d[i];
+    dv.x = dc * dv.x + (qc.x * qv.x - qc.y * qv.y);
+    dv.y = dc * dv.y + (qc.x * qv.y + qc.y * qv.x);
+    d[i] = dv;
+    cpx<T> xv = x[i];
+    xv.x += dv.x;
+    xv.y += dv.y;
+    x[i] = xv;
+    const double2 a = to_d(r[(size_t)c * npw + neg[G]]), u = to_d(r[i]);
+    ax += a.x * u.x - a.y * u.y;
+    ay += a.x * u.y + a.y * u.x;
+  }
+  ax = block_sum(ax);
+  ay = block_sum(ay);
+  if (threadIdx.x == 0) {
+    double* pp = partial + 2 * ((size_t)blockIdx.x * ncol + c);
+    pp[0] = ax; pp[1] = ay;
+  }
+  if (!last_block(&st.cnt[c], gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double sx = 0.0, sy = 0.0;
+    for (int k = 0; k < (int)gridDim.x; ++k) {
+      const double* pp = partial + 2 * ((size_t)k * ncol + c);
+      sx += pp[0]; sy += pp[1];
+    }
+    const double2 rn = make_double2(sx, sy);
+    const double2 rho = st.rho[c];
+    st.beta[c] = (rho.x * rho.x + rho.y * rho.y > 0.0) ? cdiv(rn, rho) : make_double2(0, 0);
+    st.rho[c] = rn;
+    const int it = st.iters[c] + 1;
+    st.iters[c] = it;
+    const double tau = st.tau[c];
+    bool stop = false;
+    if (st.flag[c] == 2 || !isfinite(tau)) { st.flag[c] = 2; stop = true; }
+    else if (tau * tau * (it + 1) <= st.rr_stop[c]) { st.flag[c] = 0; stop = true; }
+    else if (!(rn.x * rn.x + rn.y * rn.y > 0.0)) { st.flag[c] = 2; stop = true; }
+    else if (it >= maxit) { st.flag[c] = 1; stop = true; }
+    if (stop) { st.active[c] = 0; atomicAdd(st.n_done, 1); }
+  }
+}
+
+// q = r + beta q
+template <typename T>
+__global__ void k_qmr_q(int npw, cpx<T>* __restrict__ q, const cpx<T>* __restrict__ r, QmrState st) {
+  const int c = blockIdx.y;
+  if (!st.active[c]) return;
+  const cpx<T> b = from_d<T>(st.beta[c]);
+  for (int G = blockIdx.x * blockDim.x + threadIdx.x; G < npw; G += gridDim.x * blockDim.x) {
+    const size_t i = (size_t)c * npw + G;
+    const cpx<T> qv = q[i], rv = r[i];
+    q[i] = mk<T>(rv.x + b.x * qv.x - b.y * qv.y, rv.y + b.x * qv.y + b.y * qv.x);
+  }
+}
+
+template <typename T>
+void launch_qmr(cudaStream_t s, int step, int npw, int ncol, const double2* b, cpx<T>* x, cpx<T>* r, cpx<T>* q,
+                cpx<T>* d, const cpx<T>* t, const int* neg, const int* outer_active, Work& w, QmrState st,
+                double tol_in2, int maxit) {
+  dim3 g((npw + kChunk - 1) / kChunk, ncol);
+  double* part = reinterpret_cast<double*>(w.part2);
+  ++g_launches;
+  switch (step) {
+    case 0: k_qmr_init<T><<<g, kLT, 0, s>>>(npw, b, x, r, q, d, neg, outer_active, part, st, ncol, tol_in2); break;
+    case 1: k_qmr_sigma<T><<<g, kLT, 0, s>>>(npw, q, t, neg, part, st, ncol); break;
+    case 2: k_qmr_r<T><<<g, kLT, 0, s>>>(npw, r, t, part, st, ncol); break;
+    case 3: k_qmr_dx<T><<<g, kLT, 0, s>>>(npw, x, d, q, r, neg, part, st, ncol, maxit); break;
+    default: {
+      dim3 g2((npw + kLT - 1) / kLT, ncol);
+      k_qmr_q<T><<<g2, kLT, 0, s>>>(npw, q, r, st);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // FP64 refinement helpers
 // ---------------------------------------------------------------------------
 // x64 += d (converted), for active columns
@@ -595,6 +822,8 @@ void launch_tridiag_inv(cudaStream_t s, int K, const double* alpha, const double
 }
 
 #define GW_LINST(T)                                                                                        \
+  template void launch_qmr<T>(cudaStream_t, int, int, int, const double2*, cpx<T>*, cpx<T>*, cpx<T>*,       \
+                              cpx<T>*, const cpx<T>*, const int*, const int*, Work&, QmrState, double, int); \
   template void launch_gram<T>(cudaStream_t, const cpx<T>*, int, int, const cpx<T>*, int, Work&, double2*); \
   template void launch_proj_update<T>(cudaStream_t, const cpx<T>*, int, int, cpx<T>*, int, const int*,     \
                                       const double2*, Work&, const cpx<T>*, double*);                      \

@@ -34,9 +34,32 @@ struct CgState {
   unsigned* cnt = nullptr;  // tickets [ncol]
 };
 
+// Per-column state of a batched simplified-QMR solve (device arrays).
+struct QmrState {
+  double2* rho = nullptr;    // [r, r]
+  double2* alpha = nullptr;
+  double2* beta = nullptr;
+  double2* qcoef = nullptr;  // c^2 alpha
+  double* dcoef = nullptr;   // c^2 theta_old^2
+  double* theta = nullptr;
+  double* tau = nullptr;
+  double* rr_stop = nullptr;
+  const double* rr_abs = nullptr;
+  int* iters = nullptr;
+  int* flag = nullptr;       // 0 converged, 1 max iterations, 2 breakdown
+  int* active = nullptr;
+  int* n_done = nullptr;
+  unsigned* cnt = nullptr;
+};
+
 template <typename T>
 void launch_proj(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, int ncol, const int* active,
                  Work& w, const cpx<T>* Pv, double* pap);
+// step 0 init, 1 sigma/alpha, 2 residual, 3 d/x/rho/beta + stop test, 4 q update
+template <typename T>
+void launch_qmr(cudaStream_t s, int step, int npw, int ncol, const double2* b, cpx<T>* x, cpx<T>* r, cpx<T>* q,
+                cpx<T>* d, const cpx<T>* t, const int* neg, const int* outer_active, Work& w, QmrState st,
+                double tol_in2, int maxit);
 template <typename T>
 void launch_proj_update(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, int ncol,
                         const int* active, const double2* coef, Work& w, const cpx<T>* Pv, double* pap);

@@ -171,3 +171,55 @@ def test_persistent_cg_matches_multi_launch(tiny, monkeypatch):
     c2.close()
     assert rel(out1, out2) < 1e-12
     assert rel(out1m, out2m) < 1e-8
+
+
+@pytest.mark.parametrize("omega", [0.3 + 0.1j, 0.25j, 0.9, 1.7 + 0.05j])
+def test_apply_chi0_complex_and_indefinite(tiny, omega):
+    """Frequencies that need simplified QMR: complex, and real above the
+    excitation gap (H - e_v - w indefinite on P_c)."""
+    wl, cell, sph, gs = tiny
+    # keep clear of transitions (eps~ has poles at w = e_c - e_v)
+    dmin = np.min(np.abs(np.subtract.outer(gs.eps_all[gs.n_occ:], gs.eps).ravel() - abs(np.real(omega))))
+    assert np.imag(omega) != 0 or dmin > 1e-3
+    c = make(cell, gs)
+    f = W.random_fields(104, 2, sph.ng)
+    out = c.apply_chi0(f, [omega], gw.GW_FP64)[0]
+    outm = c.apply_chi0(f, [omega], gw.GW_MIXED)[0]
+    for b in range(2):
+        ref = response.chi0_sos(gs, f[b], omega)
+        if np.imag(omega) == 0:
+            ref = ref.real
+        assert rel(out[b], ref) < 1e-10
+        assert rel(outm[b], ref) < 1e-6
+    c.close()
+
+
+def test_apply_eps_complex_fields(tiny):
+    """Complex input fields at complex frequency (the bilinear Lanczos case)."""
+    wl, cell, sph, gs = tiny
+    c = make(cell, gs)
+    om = 0.4 + 0.1j
+    D = response.Dielectric(gs, om)
+    f = W.random_fields(105, 2, sph.ng, complex_=True)
+    out = c.apply_eps(f, [om], gw.GW_FP64)[0]
+    for b in range(2):
+        assert rel(out[b], D.apply(f[b], real=False)) < 1e-10
+    c.close()
+
+
+def test_free_electron_complex_frequency_gpu():
+    cell = W.Cell(8.0, 12, 3.0, 1, np.zeros((0, 3)), 0.0, 1.0)
+    sph = pw.Sphere(cell.L, cell.N, cell.ecut)
+    gs = pw.ground_state_dense(sph, np.zeros(sph.ng), 1)
+    c = make(cell, gs)
+    f = W.random_fields(8, 1, sph.ng)
+    omega = 0.1 + 0.2j
+    dn = c.apply_chi0(f, [omega], gw.GW_FP64)[0, 0]
+    G2 = sph.gvec_norm() ** 2
+    insph = np.zeros(sph.ng, bool)
+    insph[sph.index] = True
+    expect = np.zeros(sph.ng, complex)
+    m = insph & (G2 > 0)
+    expect[m] = -(2.0 / sph.omega_vol) * G2[m] / ((G2[m] / 2) ** 2 - omega ** 2)
+    assert rel(sph.fwd(dn), expect * sph.fwd(f[0])) < 1e-11
+    c.close()
