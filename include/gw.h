@@ -152,6 +152,38 @@ gw_status gw_lanczos(gw_ctx* ctx, const double* start, int blk, int k, const dou
                      double* alpha, double* beta, double* basis, gw_prec prec, int device_ptrs);
 
 /*
+ * gw_block_lanczos -- k block steps of the Lanczos recursion on eps~(omega)
+ * from a block of blk real start fields (Sec. Lanczos; block form, with
+ * classical Gram-Schmidt applied twice against all previous blocks):
+ *   W = eps~ Q_k - Q_{k-1} B_{k-1}^(H/T);  A_k = <Q_k|W>;  W -= Q_k A_k
+ *   W -= Q (Q^(H/T) W) twice;  W = Q_{k+1} B_k  (Cholesky of the Gram matrix)
+ * At real omega the inner product is Hermitian and A_k is Hermitian; at complex
+ * omega eps~ is complex symmetric and the recursion uses the bilinear form
+ * sum_r x(r) y(r) (A_k symmetric), with principal square roots in the
+ * factorisation.  Blocks are rows: vector j of block k is basis row k blk + j.
+ *   start  [blk][N^3] real, linearly independent; 1 <= blk <= 16
+ *   omega  complex (interleaved)
+ *   A      [k][blk][blk] complex, A[k][i][j] = <q_i|eps~ q_j>
+ *   B      [k-1][blk][blk] complex, upper triangular (B[k][i][j] = 0 for i > j)
+ *   basis  [k blk][N^3] complex Lanczos vectors, or NULL
+ * Returns GW_E_BREAKDOWN on rank loss (the outputs up to that step are valid).
+ */
+gw_status gw_block_lanczos(gw_ctx* ctx, const double* start, int blk, int k, const double* omega,
+                           double* A, double* B, double* basis, gw_prec prec, int device_ptrs);
+
+/*
+ * gw_epsinv_block -- inverse of the block-tridiagonal Lanczos matrix T with
+ * diagonal blocks A_k, B_k below and B_k^H (bilinear: B_k^T) above, i.e.
+ * eps~^-1 in the block Lanczos basis, by Gauss-Jordan elimination with partial
+ * pivoting on the GPU in FP64.
+ *   A [k][blk][blk], B [k-1][blk][blk] complex (as from gw_block_lanczos)
+ *   bilinear  1 for a complex-frequency (complex-symmetric) recursion
+ *   out [k blk][k blk] complex;  k blk <= 2048
+ */
+gw_status gw_epsinv_block(gw_ctx* ctx, const double* A, const double* B, int k, int blk, int bilinear,
+                          double* out, int device_ptrs);
+
+/*
  * gw_epsinv_elements -- T_K^-1, the inverse dielectric matrix in the Lanczos
  * basis (Sec. Lanczos: tridiagonal inversion at cost ~K^2), in FP64.
  *   alpha [k], beta [k-1] real; out [k][k] real (symmetric)

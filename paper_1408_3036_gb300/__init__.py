@@ -26,7 +26,8 @@ STATUS = {0: "GW_OK", 1: "GW_E_ARG", 2: "GW_E_CUDA", 3: "GW_E_NOMEM", 4: "GW_E_N
 EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "gw_apply_chi0",
            "gw_apply_eps", "gw_lanczos", "gw_epsinv_elements", "gw_grad_vloc", "gw_stats",
            "gw_set_solver", "gw_profile", "gw_profile_read", "gw_last_error", "gw_destroy",
-           "gw_epsinv_elements_noalloc", "gw_apply_chi0_c", "gw_apply_eps_c")
+           "gw_epsinv_elements_noalloc", "gw_apply_chi0_c", "gw_apply_eps_c", "gw_block_lanczos",
+           "gw_epsinv_block")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
                    "refine_fp64", "persistent_cg")
 
@@ -62,6 +63,8 @@ def load(path=LIB_PATH):
         "gw_lanczos": (I, [P, P, I, I, P, P, P, P, I, I]),
         "gw_epsinv_elements": (I, [P, P, P, I, I, P, I]),
         "gw_epsinv_elements_noalloc": (I, [P, P, I, P, P]),
+        "gw_block_lanczos": (I, [P, P, I, I, P, P, P, P, I, I]),
+        "gw_epsinv_block": (I, [P, P, P, I, I, I, P, I]),
         "gw_grad_vloc": (I, [P, P, I, P, P, I, I]),
         "gw_stats": (I, [P, P, I]),
         "gw_set_solver": (I, [P, D, D, I, I]),
@@ -196,6 +199,25 @@ def gw_lanczos(ctx, start, k, omega, alpha, beta, basis=None, prec=GW_FP64, blk=
     return alpha, beta, basis
 
 
+def gw_block_lanczos(ctx, start, k, omega, A, B, basis=None, prec=GW_FP64):
+    om = _omega_buf([omega])
+    ps, d = _ptr(start)
+    pa, _ = _ptr(A)
+    pb, _ = _ptr(B)
+    pq, _ = _ptr(basis)
+    blk = start.shape[0] if start.ndim == 2 else 1
+    _check(ctx, load().gw_block_lanczos(ctx, ps, int(blk), int(k), om.ctypes.data, pa, pb, pq, int(prec), d))
+    return A, B, basis
+
+
+def gw_epsinv_block(ctx, A, B, k, blk, bilinear, out):
+    pa, d = _ptr(A)
+    pb, _ = _ptr(B)
+    po, _ = _ptr(out)
+    _check(ctx, load().gw_epsinv_block(ctx, pa, pb, int(k), int(blk), int(bilinear), po, d))
+    return out
+
+
 def gw_epsinv_elements(ctx, alpha, beta, k, out, blk=1):
     pa, d = _ptr(alpha)
     pb, _ = _ptr(beta)
@@ -315,6 +337,21 @@ class Cell:
         Q = np.empty((k, self.ng)) if basis else None
         gw_lanczos(self.ctx, start, k, omega, a, b, Q, prec)
         return a, b[:k - 1], Q
+
+    def block_lanczos(self, start, k, omega=0.0, prec=GW_FP64, basis=False):
+        start = np.ascontiguousarray(np.atleast_2d(np.asarray(start, np.float64)))
+        blk = start.shape[0]
+        A = np.empty((k, blk, blk), np.complex128)
+        B = np.zeros((max(k - 1, 1), blk, blk), np.complex128)
+        Q = np.empty((k * blk, self.ng), np.complex128) if basis else None
+        gw_block_lanczos(self.ctx, start, k, omega, A, B, Q, prec)
+        return A, B[:k - 1], Q
+
+    def epsinv_block(self, A, B, bilinear=False):
+        k, blk = A.shape[0], A.shape[1]
+        out = np.empty((k * blk, k * blk), np.complex128)
+        Bb = np.ascontiguousarray(B if len(B) else np.zeros((1, blk, blk), np.complex128), np.complex128)
+        return gw_epsinv_block(self.ctx, np.ascontiguousarray(A, np.complex128), Bb, k, blk, bilinear, out)
 
     def epsinv(self, alpha, beta):
         k = len(alpha)

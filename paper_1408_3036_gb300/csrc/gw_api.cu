@@ -345,7 +345,7 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
   CK(cudaMemsetAsync(bar, 0, sizeof(unsigned), ctx->st));
   CK(cudaMemsetAsync(err, 0, sizeof(int), ctx->st));
   int used = 0;
-  const int pa = prof_begin(ctx, PC_XH);
+  const int pa = prof_begin(ctx, PC_PCG);
   unsigned long long* ptime = nullptr;
   if (std::getenv("GW_DEBUG_PHASES")) {
     TRY(getbuf(ctx, "pcg_ptime", 8, &ptime));
@@ -844,6 +844,140 @@ gw_status lanczos_core(gw_ctx* ctx, const double* x0, int K, const std::vector<d
     if (hb[0] <= 1e-14 * std::fabs(hb[1])) return fail(ctx, GW_E_BREAKDOWN, "Lanczos breakdown: invariant subspace");
   }
   return launch_check(ctx, "lanczos");
+}
+
+// ---------------------------------------------------------------------------
+// Block Lanczos on eps~(omega) (Sec. Lanczos, block form) on complex fields.
+// Hermitian inner product at real omega, bilinear form sum_r x(r) y(r) at
+// complex omega (eps~ is then complex symmetric).  Rows are vectors:
+//   W = eps~(Q_k) - B'_{k-1} Q_{k-1};  A_k = <Q_k|W>;  W -= A_k^T Q_k
+//   W -= H^T Q_all, H = <Q_all|W>   (twice: full re-orthogonalisation)
+//   W = R^T Q_{k+1} with G = <W|W> = R^H R (Hermitian) or R^T R (bilinear)
+// B' = conj(B) (Hermitian) or B (bilinear).  The block-sized factorisations run
+// on the host in FP64 (blk <= 16); everything N_g-sized runs on the GPU.
+// ---------------------------------------------------------------------------
+using zcd = std::complex<double>;
+
+// upper R with G = R^H R (herm) or G = R^T R (bilinear, principal square roots)
+static bool chol_upper(const std::vector<zcd>& G, int b, bool bilinear, std::vector<zcd>* R) {
+  R->assign((size_t)b * b, zcd(0, 0));
+  auto r = [&](int i, int j) -> zcd& { return (*R)[(size_t)i * b + j]; };
+  for (int i = 0; i < b; ++i) {
+    zcd s = G[(size_t)i * b + i];
+    for (int k = 0; k < i; ++k) s -= bilinear ? r(k, i) * r(k, i) : std::conj(r(k, i)) * r(k, i);
+    if (bilinear) {
+      if (!(std::abs(s) > 1e-300)) return false;
+      r(i, i) = std::sqrt(s);
+    } else {
+      if (!(s.real() > 0.0)) return false;
+      r(i, i) = std::sqrt(s.real());
+    }
+    for (int j = i + 1; j < b; ++j) {
+      zcd t = G[(size_t)i * b + j];
+      for (int k = 0; k < i; ++k) t -= bilinear ? r(k, i) * r(k, j) : std::conj(r(k, i)) * r(k, j);
+      r(i, j) = t / r(i, i);
+    }
+  }
+  return true;
+}
+
+// M = R^{-T} (rows of W R^{-1}), R upper triangular
+static std::vector<zcd> inv_transpose_upper(const std::vector<zcd>& R, int b) {
+  std::vector<zcd> inv((size_t)b * b, zcd(0, 0));   // inv = R^{-1}, upper
+  for (int j = 0; j < b; ++j) {
+    inv[(size_t)j * b + j] = 1.0 / R[(size_t)j * b + j];
+    for (int i = j - 1; i >= 0; --i) {
+      zcd s = 0.0;
+      for (int k = i + 1; k <= j; ++k) s += R[(size_t)i * b + k] * inv[(size_t)k * b + j];
+      inv[(size_t)i * b + j] = -s / R[(size_t)i * b + i];
+    }
+  }
+  std::vector<zcd> M((size_t)b * b);
+  for (int i = 0; i < b; ++i)
+    for (int j = 0; j < b; ++j) M[(size_t)i * b + j] = inv[(size_t)j * b + i];
+  return M;
+}
+
+template <typename S>
+gw_status block_lanczos_core(gw_ctx* ctx, const double* start, int blk, int K, double2 omega,
+                             std::vector<zcd>* Aout, std::vector<zcd>* Bout, double2* Q) {
+  const int N3 = ctx->N3;
+  const size_t n = (size_t)N3;
+  const double wgt = ctx->vol / N3;
+  const bool bil = (omega.y != 0.0);
+  const int cj = bil ? 0 : 1;
+  const int mmax = K * blk;
+  double2 *W, *X0, *gram, *part, *M;
+  unsigned* cnt;
+  TRY(getbuf(ctx, "bl_W", (size_t)blk * n, &W));
+  TRY(getbuf(ctx, "bl_X0", (size_t)blk * n, &X0));
+  TRY(getbuf(ctx, "bl_gram", (size_t)mmax * blk, &gram));
+  TRY(getbuf(ctx, "bl_part", ((n + 4095) / 4096) * (size_t)mmax * blk, &part));
+  TRY(getbuf(ctx, "bl_M", (size_t)blk * mmax, &M));
+  TRY(getbuf(ctx, "bl_cnt", (size_t)(blk + 7) / 8 + 1, &cnt));
+  CK(cudaMemsetAsync(cnt, 0, ((size_t)(blk + 7) / 8 + 1) * sizeof(unsigned), ctx->st));
+  std::vector<double2> om(1, omega);
+  auto gram_host = [&](const double2* X, int mx, const double2* Y, std::vector<zcd>* out) -> gw_status {
+    launch_cgram(ctx->st, X, mx, Y, blk, n, cj, wgt, part, cnt, gram);
+    std::vector<double2> h((size_t)mx * blk);
+    CK(cudaMemcpyAsync(h.data(), gram, h.size() * sizeof(double2), cudaMemcpyDeviceToHost, ctx->st));
+    TRY(sync(ctx, "block gram"));
+    out->resize(h.size());
+    for (size_t i = 0; i < h.size(); ++i) (*out)[i] = zcd(h[i].x, h[i].y);
+    return GW_OK;
+  };
+  auto combine = [&](const std::vector<zcd>& Mh, int my, int mx, const double2* X, double2* Y, int acc,
+                     double sign) -> gw_status {
+    std::vector<double2> h(Mh.size());
+    for (size_t i = 0; i < h.size(); ++i) h[i] = make_double2(Mh[i].real(), Mh[i].imag());
+    CK(cudaMemcpyAsync(M, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->st));
+    launch_cgemm_n(ctx->st, M, my, mx, X, n, Y, acc, sign);
+    return launch_check(ctx, "block combine");
+  };
+  // Q_0 from the real start block
+  {
+    const size_t tot = (size_t)blk * n;
+    ++g_launches;
+    k_promote<<<(int)std::min<size_t>((tot + 255) / 256, 152 * 8), 256, 0, ctx->st>>>(tot, start, X0);
+    std::vector<zcd> G, R;
+    TRY(gram_host(X0, blk, X0, &G));
+    if (!chol_upper(G, blk, bil, &R)) return fail(ctx, GW_E_BREAKDOWN, "start block is rank deficient");
+    TRY(combine(inv_transpose_upper(R, blk), blk, blk, X0, Q, 0, 1.0));
+  }
+  Aout->assign((size_t)K * blk * blk, zcd(0, 0));
+  Bout->assign((size_t)std::max(K - 1, 1) * blk * blk, zcd(0, 0));
+  for (int k = 0; k < K; ++k) {
+    double2* Qk = Q + (size_t)k * blk * n;
+    TRY(eps_core<S>(ctx, Qk, true, blk, om, W, false));
+    if (k > 0) {
+      std::vector<zcd> Bp(Bout->begin() + (size_t)(k - 1) * blk * blk, Bout->begin() + (size_t)k * blk * blk);
+      if (!bil)
+        for (auto& z : Bp) z = std::conj(z);
+      TRY(combine(Bp, blk, blk, Q + (size_t)(k - 1) * blk * n, W, 1, -1.0));
+    }
+    std::vector<zcd> Ak;
+    TRY(gram_host(Qk, blk, W, &Ak));
+    std::vector<zcd> AkT((size_t)blk * blk);
+    for (int i = 0; i < blk; ++i)
+      for (int j = 0; j < blk; ++j) AkT[(size_t)j * blk + i] = Ak[(size_t)i * blk + j];
+    TRY(combine(AkT, blk, blk, Qk, W, 1, -1.0));
+    const int m = (k + 1) * blk;
+    for (int pass = 0; pass < 2; ++pass) {
+      std::vector<zcd> H, HT((size_t)blk * m);
+      TRY(gram_host(Q, m, W, &H));
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < blk; ++j) HT[(size_t)j * m + i] = H[(size_t)i * blk + j];
+      TRY(combine(HT, blk, m, Q, W, 1, -1.0));
+    }
+    std::copy(Ak.begin(), Ak.end(), Aout->begin() + (size_t)k * blk * blk);
+    if (k == K - 1) break;
+    std::vector<zcd> G, R;
+    TRY(gram_host(W, blk, W, &G));
+    if (!chol_upper(G, blk, bil, &R)) return fail(ctx, GW_E_BREAKDOWN, "block Lanczos breakdown (rank loss)");
+    std::copy(R.begin(), R.end(), Bout->begin() + (size_t)k * blk * blk);
+    TRY(combine(inv_transpose_upper(R, blk), blk, blk, W, Q + (size_t)(k + 1) * blk * n, 0, 1.0));
+  }
+  return launch_check(ctx, "block lanczos");
 }
 
 // ---------------------------------------------------------------------------
@@ -1444,6 +1578,72 @@ gw_status gw_lanczos(gw_ctx* ctx, const double* start, int blk, int k, const dou
   }
   if (ctx->stats[0] > 0) ctx->stats[2] /= ctx->stats[0];
   return finish(ctx, s);
+}
+
+gw_status gw_block_lanczos(gw_ctx* ctx, const double* start, int blk, int k, const double* omega, double* A,
+                           double* B, double* basis, gw_prec prec, int dev) {
+  TRY(begin(ctx));
+  TRY(need_occ(ctx));
+  if (!start || !A || !omega || k < 1 || (k > 1 && !B) || blk < 1 || blk > 16)
+    return fail(ctx, GW_E_ARG, "bad arguments (1 <= blk <= 16)");
+  std::vector<double2> om;
+  TRY(check_omega(ctx, omega, 1, &om));
+  for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
+  ctx->pcg_iters = 0;
+  const size_t N3 = ctx->N3;
+  const void* x0;
+  TRY(stage_in(ctx, "bl_start", start, (size_t)blk * N3 * sizeof(double), dev, &x0));
+  double2* Q;
+  if (dev && basis) Q = reinterpret_cast<double2*>(basis);
+  else TRY(getbuf(ctx, "bl_Q", (size_t)k * blk * N3, &Q));
+  std::vector<zcd> Ah, Bh;
+  gw_status s = (prec == GW_FP64)
+                    ? block_lanczos_core<double>(ctx, reinterpret_cast<const double*>(x0), blk, k, om[0], &Ah, &Bh, Q)
+                    : block_lanczos_core<float>(ctx, reinterpret_cast<const double*>(x0), blk, k, om[0], &Ah, &Bh, Q);
+  if (s != GW_OK && s != GW_E_BREAKDOWN) return s;
+  const size_t na = (size_t)k * blk * blk, nbb = (size_t)(k - 1) * blk * blk;
+  if (dev) {
+    CK(cudaMemcpyAsync(A, Ah.data(), na * sizeof(zcd), cudaMemcpyHostToDevice, ctx->st));
+    if (k > 1) CK(cudaMemcpyAsync(B, Bh.data(), nbb * sizeof(zcd), cudaMemcpyHostToDevice, ctx->st));
+  } else {
+    std::memcpy(A, Ah.data(), na * sizeof(zcd));
+    if (k > 1) std::memcpy(B, Bh.data(), nbb * sizeof(zcd));
+    if (basis) CK(cudaMemcpyAsync(basis, Q, (size_t)k * blk * N3 * sizeof(double2), cudaMemcpyDeviceToHost, ctx->st));
+  }
+  if (ctx->stats[0] > 0) ctx->stats[2] /= ctx->stats[0];
+  return finish(ctx, s);
+}
+
+gw_status gw_epsinv_block(gw_ctx* ctx, const double* A, const double* B, int k, int blk, int bilinear, double* out,
+                          int dev) {
+  TRY(begin(ctx));
+  if (!A || !out || k < 1 || blk < 1 || (k > 1 && !B)) return fail(ctx, GW_E_ARG, "bad arguments");
+  const int n = k * blk;
+  if (n > 2048) return fail(ctx, GW_E_ARG, "block Lanczos matrix larger than 2048");
+  const size_t na = (size_t)k * blk * blk * sizeof(double2), nbb = (size_t)std::max(k - 1, 1) * blk * blk * sizeof(double2);
+  const void *a, *b = nullptr;
+  TRY(stage_in(ctx, "eb_a", A, na, dev, &a));
+  if (k > 1) TRY(stage_in(ctx, "eb_b", B, nbb, dev, &b));
+  else {
+    double2* z;
+    TRY(getbuf(ctx, "eb_bz", (size_t)blk * blk, &z));
+    b = z;
+  }
+  double2* T;
+  int* stat;
+  TRY(getbuf(ctx, "eb_T", (size_t)n * n, &T));
+  TRY(getbuf(ctx, "eb_stat", 1, &stat));
+  void* o;
+  TRY(stage_out(ctx, "eb_o", out, (size_t)n * n * sizeof(double2), dev, &o));
+  launch_block_tridiag(ctx->st, k, blk, reinterpret_cast<const double2*>(a), reinterpret_cast<const double2*>(b),
+                       bilinear ? 1 : 0, T);
+  launch_cinv(ctx->st, n, T, reinterpret_cast<double2*>(o), stat);
+  TRY(launch_check(ctx, "epsinv_block"));
+  CK(cudaMemcpyAsync(ctx->host_pin, stat, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  TRY(copy_back(ctx, out, o, (size_t)n * n * sizeof(double2), dev));
+  TRY(sync(ctx, "epsinv_block"));
+  if (ctx->host_pin[0]) return fail(ctx, GW_E_BREAKDOWN, "singular block-tridiagonal matrix");
+  return GW_OK;
 }
 
 gw_status gw_epsinv_elements(gw_ctx* ctx, const double* alpha, const double* beta, int k, int blk, double* out,

@@ -842,3 +842,229 @@ template void launch_gather_rows<float, double>(cudaStream_t, int, int, const do
 template void launch_gather_rows<double, float>(cudaStream_t, int, int, const float2*, const int*, double2*);
 
 }  // namespace gw
+
+namespace gw {
+
+// ---------------------------------------------------------------------------
+// block Lanczos on complex grid fields (Sec. Lanczos, block form; bilinear
+// form at complex frequency): Gram matrices and small-matrix combinations
+// ---------------------------------------------------------------------------
+constexpr int kGChunk = 4096;   // grid points per block in the Gram kernel
+constexpr int kGT = 8;          // Y columns per block
+
+// out[i * my + j] = wgt * sum_r op(X[i][r]) Y[j][r], op = conj (Hermitian) or identity (bilinear)
+// grid (nchunk, ceil(my / kGT)); one warp per i (strided), lanes over r
+__global__ void __launch_bounds__(kLT)
+k_cgram(const double2* __restrict__ X, int mx, const double2* __restrict__ Y, int my, size_t n, int conj_x,
+        double wgt, double2* __restrict__ partial, unsigned* __restrict__ cnt, double2* __restrict__ out) {
+  const int nchunk = gridDim.x;
+  const size_t r0 = (size_t)blockIdx.x * kGChunk, r1 = min(n, r0 + kGChunk);
+  const int j0 = blockIdx.y * kGT;
+  const int nj = min(kGT, my - j0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i < mx; i += nw) {
+    double ax[kGT], ay[kGT];
+#pragma unroll
+    for (int j = 0; j < kGT; ++j) { ax[j] = 0.0; ay[j] = 0.0; }
+    for (size_t r = r0 + lane; r < r1; r += 32) {
+      double2 x = X[(size_t)i * n + r];
+      if (conj_x) x.y = -x.y;
+#pragma unroll
+      for (int j = 0; j < kGT; ++j) {
+        if (j < nj) {
+          const double2 y = Y[(size_t)(j0 + j) * n + r];
+          ax[j] += x.x * y.x - x.y * y.y;
+          ay[j] += x.x * y.y + x.y * y.x;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kGT; ++j) {
+      double sx = ax[j], sy = ay[j];
+      for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      }
+      if (lane == 0 && j < nj) partial[((size_t)blockIdx.x * mx + i) * my + j0 + j] = make_double2(sx, sy);
+    }
+  }
+  if (!last_block(&cnt[blockIdx.y], nchunk)) return;
+  for (int t = threadIdx.x; t < mx * nj; t += blockDim.x) {
+    const int i = t / nj, j = t - i * nj;
+    double sx = 0.0, sy = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+      const double2 p = partial[((size_t)c * mx + i) * my + j0 + j];
+      sx += p.x;
+      sy += p.y;
+    }
+    out[(size_t)i * my + j0 + j] = make_double2(wgt * sx, wgt * sy);
+  }
+}
+
+void launch_cgram(cudaStream_t s, const double2* X, int mx, const double2* Y, int my, size_t n, int conj_x,
+                  double wgt, double2* partial, unsigned* cnt, double2* out) {
+  const int nchunk = (int)((n + kGChunk - 1) / kGChunk);
+  dim3 g(nchunk, (my + kGT - 1) / kGT);
+  ++g_launches;
+  k_cgram<<<g, kLT, 0, s>>>(X, mx, Y, my, n, conj_x, wgt, partial, cnt, out);
+}
+
+// Y[j][r] = (accumulate ? Y[j][r] : 0) + sign * sum_i M[j * mx + i] X[i][r],  j < my (<= 16)
+constexpr int kMT = 64;   // coefficients staged per pass
+__global__ void __launch_bounds__(kLT)
+k_cgemm_n(const double2* __restrict__ M, int my, int mx, const double2* __restrict__ X, size_t n,
+          double2* __restrict__ Y, int accumulate, double sign) {
+  __shared__ double2 sm[16 * kMT];
+  for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r - threadIdx.x < n;
+       r += (size_t)gridDim.x * blockDim.x) {
+    double2 acc[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = make_double2(0, 0);
+    for (int i0 = 0; i0 < mx; i0 += kMT) {
+      const int ni = min(kMT, mx - i0);
+      __syncthreads();
+      for (int t = threadIdx.x; t < my * ni; t += blockDim.x) {
+        const int j = t / ni, i = t - j * ni;
+        sm[j * kMT + i] = M[(size_t)j * mx + i0 + i];
+      }
+      __syncthreads();
+      if (r < n) {
+        for (int i = 0; i < ni; ++i) {
+          const double2 x = X[(size_t)(i0 + i) * n + r];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if (j < my) {
+              const double2 m = sm[j * kMT + i];
+              acc[j].x += m.x * x.x - m.y * x.y;
+              acc[j].y += m.x * x.y + m.y * x.x;
+            }
+          }
+        }
+      }
+    }
+    if (r < n) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (j < my) {
+          double2 y = accumulate ? Y[(size_t)j * n + r] : make_double2(0, 0);
+          y.x += sign * acc[j].x;
+          y.y += sign * acc[j].y;
+          Y[(size_t)j * n + r] = y;
+        }
+      }
+    }
+  }
+}
+
+void launch_cgemm_n(cudaStream_t s, const double2* M, int my, int mx, const double2* X, size_t n, double2* Y,
+                    int accumulate, double sign) {
+  const int nb = (int)std::min<size_t>((n + kLT - 1) / kLT, 152 * 8);
+  ++g_launches;
+  k_cgemm_n<<<nb, kLT, 0, s>>>(M, my, mx, X, n, Y, accumulate, sign);
+}
+
+// ---------------------------------------------------------------------------
+// inverse of a small dense complex matrix (the block-tridiagonal Lanczos
+// matrix) by Gauss-Jordan elimination with partial pivoting, one CTA.
+// Work: a [n][n] (destroyed), out [n][n] (starts as the identity).
+// ---------------------------------------------------------------------------
+__global__ void k_cinv(int n, double2* __restrict__ a, double2* __restrict__ out, int* __restrict__ status) {
+  __shared__ int piv;
+  __shared__ double2 pv;
+  for (size_t t = threadIdx.x; t < (size_t)n * n; t += blockDim.x) {
+    const size_t i = t / n, j = t - i * n;
+    out[t] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  if (threadIdx.x == 0) *status = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      int best = k;
+      double bm = -1.0;
+      for (int i = k; i < n; ++i) {
+        const double2 v = a[(size_t)i * n + k];
+        const double m = v.x * v.x + v.y * v.y;
+        if (m > bm) { bm = m; best = i; }
+      }
+      piv = best;
+      if (!(bm > 0.0) || !isfinite(bm)) *status = 1;
+    }
+    __syncthreads();
+    if (*status) return;
+    if (piv != k) {
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double2 t1 = a[(size_t)k * n + j]; a[(size_t)k * n + j] = a[(size_t)piv * n + j]; a[(size_t)piv * n + j] = t1;
+        double2 t2 = out[(size_t)k * n + j]; out[(size_t)k * n + j] = out[(size_t)piv * n + j]; out[(size_t)piv * n + j] = t2;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) pv = a[(size_t)k * n + k];
+    __syncthreads();
+    const double den = pv.x * pv.x + pv.y * pv.y;
+    const double2 inv = make_double2(pv.x / den, -pv.y / den);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {      // scale the pivot row
+      const double2 x = a[(size_t)k * n + j], y = out[(size_t)k * n + j];
+      a[(size_t)k * n + j] = make_double2(x.x * inv.x - x.y * inv.y, x.x * inv.y + x.y * inv.x);
+      out[(size_t)k * n + j] = make_double2(y.x * inv.x - y.y * inv.y, y.x * inv.y + y.y * inv.x);
+    }
+    __syncthreads();
+    for (size_t t = threadIdx.x; t < (size_t)n * n; t += blockDim.x) {   // eliminate column k elsewhere
+      const int i = (int)(t / n), j = (int)(t - (size_t)i * n);
+      if (i == k) continue;
+      const double2 f = a[(size_t)i * n + k];
+      if (j == k) continue;
+      const double2 x = a[(size_t)k * n + j], y = out[(size_t)k * n + j];
+      double2 ai = a[(size_t)i * n + j], oi = out[(size_t)i * n + j];
+      ai.x -= f.x * x.x - f.y * x.y; ai.y -= f.x * x.y + f.y * x.x;
+      oi.x -= f.x * y.x - f.y * y.y; oi.y -= f.x * y.y + f.y * y.x;
+      a[(size_t)i * n + j] = ai;
+      out[(size_t)i * n + j] = oi;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {      // column k of the inverse part
+      if (i == k) continue;
+      const double2 f = a[(size_t)i * n + k];
+      const double2 y = out[(size_t)k * n + k];
+      double2 oi = out[(size_t)i * n + k];
+      oi.x -= f.x * y.x - f.y * y.y; oi.y -= f.x * y.y + f.y * y.x;
+      out[(size_t)i * n + k] = oi;
+      a[(size_t)i * n + k] = make_double2(0, 0);
+    }
+    __syncthreads();
+  }
+}
+
+void launch_cinv(cudaStream_t s, int n, double2* a, double2* out, int* status) {
+  ++g_launches;
+  k_cinv<<<1, 1024, 0, s>>>(n, a, out, status);
+}
+
+// assemble the block-tridiagonal T: diagonal A_k, B_k below, B_k^H (Hermitian)
+// or B_k^T (bilinear) above; T [n][n] with n = K blk
+__global__ void k_block_tridiag(int K, int blk, const double2* __restrict__ A, const double2* __restrict__ B,
+                                int bilinear, double2* __restrict__ T) {
+  const int n = K * blk;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)n * n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t - (size_t)i * n);
+    const int bi = i / blk, bj = j / blk, ii = i - bi * blk, jj = j - bj * blk;
+    double2 v = make_double2(0, 0);
+    if (bi == bj) v = A[((size_t)bi * blk + ii) * blk + jj];
+    else if (bi == bj + 1) v = B[((size_t)bj * blk + ii) * blk + jj];
+    else if (bj == bi + 1) {
+      const double2 b = B[((size_t)bi * blk + jj) * blk + ii];
+      v = bilinear ? b : make_double2(b.x, -b.y);
+    }
+    T[t] = v;
+  }
+}
+
+void launch_block_tridiag(cudaStream_t s, int K, int blk, const double2* A, const double2* B, int bilinear,
+                          double2* T) {
+  const size_t n2 = (size_t)K * blk * K * blk;
+  const int nb = (int)std::min<size_t>((n2 + 255) / 256, 152 * 8);
+  ++g_launches;
+  k_block_tridiag<<<nb, 256, 0, s>>>(K, blk, A, B, bilinear, T);
+}
+
+}  // namespace gw

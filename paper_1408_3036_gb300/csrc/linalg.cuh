@@ -95,6 +95,15 @@ void launch_tridiag_inv(cudaStream_t s, int K, const double* alpha, const double
 
 template <typename T> cudaError_t fft_set_smem_limits();
 
+// block Lanczos helpers (complex grid fields)
+void launch_cgram(cudaStream_t s, const double2* X, int mx, const double2* Y, int my, size_t n, int conj_x,
+                  double wgt, double2* partial, unsigned* cnt, double2* out);
+void launch_cgemm_n(cudaStream_t s, const double2* M, int my, int mx, const double2* X, size_t n, double2* Y,
+                    int accumulate, double sign);
+void launch_cinv(cudaStream_t s, int n, double2* a, double2* out, int* status);
+void launch_block_tridiag(cudaStream_t s, int K, int blk, const double2* A, const double2* B, int bilinear,
+                          double2* T);
+
 // whole CG pass in one cooperative launch (kernels_cg.cu)
 template <typename T>
 cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPlan& pl, const Prec<T>& P, int nocc,

@@ -223,3 +223,30 @@ def test_free_electron_complex_frequency_gpu():
     expect[m] = -(2.0 / sph.omega_vol) * G2[m] / ((G2[m] / 2) ** 2 - omega ** 2)
     assert rel(sph.fwd(dn), expect * sph.fwd(f[0])) < 1e-11
     c.close()
+
+
+@pytest.mark.parametrize("blk,omega", [(3, 0.0), (1, 0.35 + 0.1j), (2, 0.6 + 0.15j)])
+def test_block_lanczos(tiny, blk, omega):
+    """Block (Hermitian, real omega) and complex-symmetric (bilinear, complex
+    omega) Lanczos against the oracle's recursion; T^-1 against a dense inverse."""
+    from oracle import lanczos as OL
+    wl, cell, sph, gs = tiny
+    wgt = sph.omega_vol / sph.ng
+    D = response.Dielectric(gs, omega)
+    X0 = W.random_fields(106, blk, sph.ng)
+    bil = np.imag(omega) != 0
+    K = 6
+    A_ref, B_ref, Q_ref = OL.block_lanczos(lambda X: np.array([D.apply(x, real=False) for x in X]),
+                                           X0.astype(complex), K, wgt, bilinear=bil)
+    c = make(cell, gs)
+    A, B, Q = c.block_lanczos(X0, K, omega, gw.GW_FP64, basis=True)
+    assert rel(A, A_ref) < 1e-10
+    assert rel(B, B_ref) < 1e-10
+    G = wgt * (Q @ Q.T if bil else Q.conj() @ Q.T)
+    assert np.abs(G - np.eye(K * blk)).max() < 1e-12
+    Ti = c.epsinv_block(A, B, bil)
+    T = OL.block_tridiag(A_ref, B_ref, bilinear=bil)
+    assert rel(Ti, np.linalg.inv(T)) < 1e-10
+    Am, Bm, _ = c.block_lanczos(X0, K, omega, gw.GW_MIXED)
+    assert rel(Am, A_ref) < 1e-6 and rel(Bm, B_ref) < 1e-6
+    c.close()
