@@ -270,6 +270,47 @@ gw_status gw_profile_read(gw_ctx* ctx, double* ms, long long* count, int n);
 const char* gw_last_error(const gw_ctx* ctx);
 void gw_destroy(gw_ctx* ctx);
 
+/*
+ * Batches of independent cells (the many-system workload: cells of different
+ * size, cutoff and occupation, each with its own Lanczos recursions).  The
+ * batch owns one context and one non-blocking CUDA stream per cell; a pool of
+ * host threads runs the cells concurrently on the current device.
+ */
+typedef struct gw_batch gw_batch;
+
+/*
+ * gw_batch_setup -- one context per cell, as gw_setup (per-cell L, n_grid,
+ * ecut, vloc[i] of n_grid[i]^3 doubles; coulomb shared).  n_workers <= 0 picks
+ * min(n_cells, 8).  Occupied states are set per cell through gw_batch_cell and
+ * gw_set_occupied.  On error nothing is allocated and *out is NULL.
+ */
+gw_status gw_batch_setup(gw_batch** out, int n_cells, const double* L, const int* n_grid, const double* ecut,
+                         const double* const* vloc, int coulomb, int n_workers);
+
+/* Number of cells; the context of cell i (owned by the batch; NULL if out of range). */
+int gw_batch_size(const gw_batch* b);
+gw_ctx* gw_batch_cell(gw_batch* b, int i);
+
+/*
+ * gw_batch_lanczos -- for every cell i and frequency w, k Lanczos steps on
+ * eps~(omega_w) of cell i from start[i] (host, n_grid[i]^3 doubles): the
+ * recursion of gw_lanczos at real omega, of gw_block_lanczos with block size
+ * 1 (bilinear form) at complex omega.
+ *   omega  [n_cells][n_omega] complex (interleaved): each cell its own
+ *          frequencies (a real frequency must keep clear of the cell's
+ *          transition energies, where eps~ has poles)
+ *   alpha  [n_cells][n_omega][k] complex (host);  beta [n_cells][n_omega][k-1]
+ *   cell_status  [n_cells] per-cell gw_status, or NULL
+ * Cells run concurrently; a failing cell stops its own remaining frequencies
+ * only.  Returns the status of the lowest-numbered failing cell (its message
+ * in gw_batch_last_error), else GW_OK.
+ */
+gw_status gw_batch_lanczos(gw_batch* b, const double* const* start, int k, int n_omega, const double* omega,
+                           double* alpha, double* beta, gw_prec prec, int* cell_status);
+
+const char* gw_batch_last_error(const gw_batch* b);
+void gw_batch_destroy(gw_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

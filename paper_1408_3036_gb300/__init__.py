@@ -27,7 +27,8 @@ EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "
            "gw_apply_eps", "gw_lanczos", "gw_epsinv_elements", "gw_grad_vloc", "gw_stats",
            "gw_set_solver", "gw_profile", "gw_profile_read", "gw_last_error", "gw_destroy",
            "gw_epsinv_elements_noalloc", "gw_apply_chi0_c", "gw_apply_eps_c", "gw_block_lanczos",
-           "gw_epsinv_block")
+           "gw_epsinv_block", "gw_batch_setup", "gw_batch_size", "gw_batch_cell", "gw_batch_lanczos",
+           "gw_batch_last_error", "gw_batch_destroy")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
                    "refine_fp64", "persistent_cg")
 
@@ -72,6 +73,12 @@ def load(path=LIB_PATH):
         "gw_profile_read": (I, [P, P, P, I]),
         "gw_last_error": (ctypes.c_char_p, [P]),
         "gw_destroy": (None, [P]),
+        "gw_batch_setup": (I, [ctypes.POINTER(P), I, P, P, P, P, I, I]),
+        "gw_batch_size": (I, [P]),
+        "gw_batch_cell": (P, [P, I]),
+        "gw_batch_lanczos": (I, [P, P, I, I, P, P, P, I, P]),
+        "gw_batch_last_error": (ctypes.c_char_p, [P]),
+        "gw_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -281,16 +288,17 @@ def gw_destroy(ctx):
 class Cell:
     """Convenience owner of one context (setup ... destroy)."""
 
-    def __init__(self, L, n_grid, ecut, vloc, coulomb=GW_COULOMB_TRUNCATED, cuda_stream=None):
+    def __init__(self, L, n_grid, ecut, vloc, coulomb=GW_COULOMB_TRUNCATED, cuda_stream=None, _ctx=None):
         self.L, self.N, self.ecut = float(L), int(n_grid), float(ecut)
-        self.ctx = gw_setup(L, n_grid, ecut, vloc, coulomb, cuda_stream)
+        self.owned = _ctx is None
+        self.ctx = gw_setup(L, n_grid, ecut, vloc, coulomb, cuda_stream) if _ctx is None else _ctx
         self.npw = gw_npw(self.ctx)
         self.ng = self.N ** 3
 
     def close(self):
-        if self.ctx:
+        if self.ctx and self.owned:
             gw_destroy(self.ctx)
-            self.ctx = None
+        self.ctx = None
 
     def __del__(self):
         try:
@@ -372,3 +380,100 @@ class Cell:
 
     def set_solver(self, **kw):
         gw_set_solver(self.ctx, **kw)
+
+
+def _check_batch(b, st):
+    if st != 0:
+        msg = load().gw_batch_last_error(b).decode() if b else ""
+        raise GwError(st, msg)
+
+
+def gw_batch_setup(cells, coulomb=GW_COULOMB_TRUNCATED, workers=0):
+    """cells: list of (L, n_grid, ecut, vloc).  Returns the batch handle."""
+    lib = load()
+    vs = [np.ascontiguousarray(np.asarray(c[3], np.float64).reshape(-1)) for c in cells]
+    for c, v in zip(cells, vs):
+        if v.size != int(c[1]) ** 3:
+            raise ValueError("vloc must hold n_grid^3 values")
+    n = len(cells)
+    L = np.array([c[0] for c in cells], np.float64)
+    N = np.array([c[1] for c in cells], np.int32)
+    E = np.array([c[2] for c in cells], np.float64)
+    vp = (ctypes.c_void_p * n)(*[v.ctypes.data for v in vs])
+    out = ctypes.c_void_p()
+    _check_batch(None, lib.gw_batch_setup(ctypes.byref(out), n, L.ctypes.data, N.ctypes.data, E.ctypes.data,
+                                          ctypes.cast(vp, ctypes.c_void_p), int(coulomb), int(workers)))
+    return out.value
+
+
+def gw_batch_size(b):
+    return load().gw_batch_size(b)
+
+
+def gw_batch_cell(b, i):
+    return load().gw_batch_cell(b, int(i))
+
+
+def gw_batch_lanczos(b, starts, k, omegas, alpha, beta, prec=GW_FP64, status=None):
+    """omegas: (n_cells, n_omega) complex, or (n_omega,) shared by all cells."""
+    n = len(starts)
+    sp = (ctypes.c_void_p * n)(*[x.ctypes.data for x in starts])
+    om = np.asarray(omegas, np.complex128)
+    om = np.ascontiguousarray(np.broadcast_to(om, (n, om.shape[-1])))
+    ps = status.ctypes.data if status is not None else None
+    _check_batch(b, load().gw_batch_lanczos(b, ctypes.cast(sp, ctypes.c_void_p), int(k), int(om.shape[1]),
+                                            om.ctypes.data, alpha.ctypes.data, beta.ctypes.data, int(prec), ps))
+    return alpha, beta
+
+
+def gw_batch_last_error(b):
+    return load().gw_batch_last_error(b).decode()
+
+
+def gw_batch_destroy(b):
+    load().gw_batch_destroy(b)
+
+
+class Batch:
+    """Independent cells run concurrently (gw_batch_*).  ``cells`` is a list of
+    (L, n_grid, ecut, vloc); ``cell(i)`` is a non-owning Cell view of cell i."""
+
+    def __init__(self, cells, coulomb=GW_COULOMB_TRUNCATED, workers=0):
+        self.b = gw_batch_setup(cells, coulomb, workers)
+        self.cells = [Cell(c[0], c[1], c[2], None, _ctx=gw_batch_cell(self.b, i)) for i, c in enumerate(cells)]
+
+    def __len__(self):
+        return gw_batch_size(self.b)
+
+    def cell(self, i):
+        return self.cells[i]
+
+    def lanczos(self, starts, k, omegas, prec=GW_FP64):
+        """alpha [n_cells][n_omega][k], beta [..][k-1] (complex), per-cell status.
+        A failing cell raises GwError after all cells ran; see ``last_status``."""
+        n = len(self.cells)
+        st = [np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1)) for x in starts]
+        if len(st) != n:
+            raise ValueError("one start field per cell")
+        for c, x in zip(self.cells, st):
+            if x.size != c.ng:
+                raise ValueError("start field size does not match its cell")
+        n_om = np.asarray(omegas).shape[-1]
+        A = np.empty((n, n_om, k), np.complex128)
+        B = np.empty((n, n_om, max(k - 1, 0)), np.complex128)
+        self.last_status = np.zeros(n, np.int32)
+        gw_batch_lanczos(self.b, st, k, omegas, A, B, prec, self.last_status)
+        return A, B
+
+    def close(self):
+        if getattr(self, "b", None):
+            for c in self.cells:
+                c.ctx = None
+            gw_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

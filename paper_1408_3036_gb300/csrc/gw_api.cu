@@ -41,6 +41,7 @@ struct gw_ctx {
   bool no_persistent = false;   // force the multi-launch CG (tests)
   long long pcg_iters = 0;      // iterations run by persistent launches
   int pcg_launch_blocks = 0;
+  int cta_div = 1;              // contexts sharing the GPU concurrently (batch mode)
   bool ptime_init = false;
   double vmax = 0.0;            // max |V_loc|
   int max_iter = 20000, max_outer = 12;
@@ -356,7 +357,7 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
   }
   CK(launch_cg_persistent<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), ctx->nocc, npw, ncol, b64, outer_active,
                              E, rr_abs, tol * tol, ctx->max_iter, x, r, p, Ap, grid, dpart, ppart, rpart, bar, err,
-                             iters, flags, rr_out, &used, ptime));
+                             iters, flags, rr_out, &used, ptime, ctx->cta_div));
   if (ptime) {
     unsigned long long h[8];
     CK(cudaMemcpyAsync(h, ptime, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
@@ -408,6 +409,8 @@ gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E,
   TRY(getbuf(ctx, "qmr_theta", ncol, &st.theta));
   TRY(getbuf(ctx, "qmr_tau", ncol, &st.tau));
   TRY(getbuf(ctx, "qmr_stop", ncol, &st.rr_stop));
+  TRY(getbuf(ctx, "qmr_qbest", ncol, &st.qbest));
+  TRY(getbuf(ctx, "qmr_itbest", ncol, &st.itbest));
   TRY(getbuf(ctx, "cg_iters", ncol, &st.iters));
   TRY(getbuf(ctx, "cg_flag", ncol, &st.flag));
   TRY(getbuf(ctx, "cg_active", ncol, &st.active));
@@ -458,6 +461,16 @@ gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E,
     *it_sum += its[c];
     *it_max = std::max(*it_max, its[c]);
   }
+  if (std::getenv("GW_DEBUG_QMR")) {
+    std::vector<double> qb(ncol), rs(ncol);
+    CK(cudaMemcpyAsync(qb.data(), st.qbest, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(rs.data(), st.rr_stop, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    TRY(sync(ctx, "qmr debug"));
+    for (int c = 0; c < ncol; ++c)
+      if (its[c] > 150 || c == 18)
+        std::fprintf(stderr, "qmr %s col %d it %d flag %d best/stop %.2e\n", tname<T>(), c, its[c], flags[c],
+                     std::sqrt(qb[c] / rs[c]));
+  }
   for (int c = 0; c < ncol; ++c)
     if (flags[c] == 2 && std::is_same<T, double>::value)
       return fail(ctx, GW_E_BREAKDOWN, "SQMR serious breakdown: [q, A q] = 0");
@@ -472,6 +485,17 @@ gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E,
 // states).  Each inner solve stops at tol_inner relative to its own right-hand
 // side, or at a tenth of the final target, whichever is larger.
 // ---------------------------------------------------------------------------
+// One inner solve in precision U: simplified QMR, or CG (one persistent launch
+// when the columns fit, else the multi-launch form).
+template <typename U>
+gw_status inner_solve(gw_ctx* ctx, bool qmr, int ncol, const double2* r64, const double2* E, const int* oact,
+                      cpx<U>* d, double tol_in, const double* rra, long long* it_sum, int* it_max) {
+  if (qmr) return qmr_solve<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, it_sum, it_max);
+  if (ncol <= kPersistentMaxCols && !ctx->no_persistent)
+    return cg_solve_persistent<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, it_sum, it_max);
+  return cg_solve<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, it_sum, it_max);
+}
+
 template <typename T>
 gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, double2* x64, bool qmr = false) {
   const int npw = ctx->npw;
@@ -500,14 +524,23 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
   int it_max = 0, outer = 0;
   bool done = false;
   double prev_worst = 1e300;
+  // Mixed path: a pass in which some column far from convergence does not
+  // drop its residual by 10x means the FP32 recurrence cannot resolve that
+  // system (a nearly singular, indefinite shift close to a transition); the
+  // remaining passes then run the inner solver in FP64.
+  bool esc = false;
+  double2* d64 = nullptr;
+  std::vector<double> hprev;
   for (outer = 0; outer < ctx->max_outer && !done; ++outer) {
-    if (qmr)
-      TRY(qmr_solve<T>(ctx, ncol, r64, E, oact, d, tol_in, rra, &it_sum, &it_max));
-    else if (ncol <= kPersistentMaxCols && !ctx->no_persistent)
-      TRY(cg_solve_persistent<T>(ctx, ncol, r64, E, oact, d, tol_in, rra, &it_sum, &it_max));
-    else
-      TRY(cg_solve<T>(ctx, ncol, r64, E, oact, d, tol_in, rra, &it_sum, &it_max));
-    launch_add_conv<T>(ctx->st, npw, ncol, d, x64, oact);
+    if (esc) {
+      if (!d64) TRY(getbuf(ctx, "sv_d64", (size_t)ncol * npw, &d64));
+      TRY(inner_solve<double>(ctx, qmr, ncol, r64, E, oact, reinterpret_cast<cpx<double>*>(d64),
+                              std::max(1e2 * ctx->tol, 1e-11), rra, &it_sum, &it_max));
+      launch_add_conv<double>(ctx->st, npw, ncol, reinterpret_cast<cpx<double>*>(d64), x64, oact);
+    } else {
+      TRY(inner_solve<T>(ctx, qmr, ncol, r64, E, oact, d, tol_in, rra, &it_sum, &it_max));
+      launch_add_conv<T>(ctx->st, npw, ncol, d, x64, oact);
+    }
     // r64 = b - P_c (H - E) x64
     {
       const int pa = prof_begin(ctx, PC_REFINE);
@@ -521,6 +554,13 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
     CK(cudaMemcpyAsync(hb.data(), bb, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaMemcpyAsync(hx.data(), xx, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     TRY(sync(ctx, "solve"));
+    if (std::getenv("GW_DEBUG_QMR")) {
+      for (int c = 0; c < ncol; ++c)
+        if (act[c] && hb[c] > 0 && std::sqrt(hr[c] / hb[c]) > 1e-9)
+          std::fprintf(stderr, "pass %d col %d |r|/|b| %.3e |x|/|b| %.3e\n", outer, c, std::sqrt(hr[c] / hb[c]),
+                       std::sqrt(hx[c] / hb[c]));
+    }
+    if (hprev.empty()) hprev = hb;
     int nact = 0;
     for (int c = 0; c < ncol; ++c) {
       if (!act[c]) continue;
@@ -528,7 +568,13 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
       const double be = scale > 0 ? std::sqrt(hr[c]) / scale : 0.0;
       if (!std::isfinite(be)) return fail(ctx, GW_E_NONFINITE, "non-finite Sternheimer residual");
       habs[c] = 0.01 * tol * tol * scale * scale;
-      if (be > tol) ++nact; else act[c] = 0;
+      if (be > tol) {
+        ++nact;
+        if (mixed && be > 1e3 * tol && hr[c] > 1e-2 * hprev[c]) esc = true;
+      } else {
+        act[c] = 0;
+      }
+      hprev[c] = hr[c];
     }
     // stagnation: a pass that does not halve the worst backward error ends the
     // refinement (accepted within 10x of the target: the floor set by rounding
@@ -1699,7 +1745,7 @@ gw_status gw_grad_vloc(gw_ctx* ctx, const double* phi, int k, double* s, double*
 gw_status gw_stats(const gw_ctx* ctx, double* out, int n) {
   if (!ctx || !out || n < 0) return GW_E_ARG;
   for (int i = 0; i < n && i < 6; ++i) out[i] = ctx->stats[i];
-  if (n > 6) out[6] = (double)g_launches;
+  if (n > 6) out[6] = (double)g_launches.load();
   if (n > 7) out[7] = (double)ctx->pcg_iters;
   return GW_OK;
 }
@@ -1768,3 +1814,9 @@ bool make_plan(int N, FftPlan* p) {
   return m == 1;
 }
 }  // namespace gw
+
+// Batch mode: contexts that share the GPU concurrently cap their persistent
+// grids at 1/n of the resident slots (see launch_cg_persistent).
+void gw_internal_set_cta_div(gw_ctx* ctx, int n) {
+  if (ctx) ctx->cta_div = n < 1 ? 1 : n;
+}

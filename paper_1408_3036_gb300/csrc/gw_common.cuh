@@ -3,6 +3,8 @@
 // the launch interfaces between the translation units.
 #pragma once
 
+#include <atomic>
+
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -55,7 +57,7 @@ struct FftPlan {
 bool make_plan(int N, FftPlan* p);
 
 // kernel launches issued by this library since it was loaded (host counter)
-extern unsigned long long g_launches;
+extern std::atomic<unsigned long long> g_launches;
 
 // ---------------------------------------------------------------------------
 // geometry of one cell's sphere on its grid (device arrays)

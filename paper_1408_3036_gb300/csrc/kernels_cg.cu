@@ -22,6 +22,8 @@
 #include <algorithm>
 #include <cstdio>
 
+#include <mutex>
+
 #include "fft.cuh"
 #include "gw_common.cuh"
 #include "linalg.cuh"
@@ -463,7 +465,7 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
                                  const double* rr_abs, double tol_in2, int maxit, cpx<T>* x, cpx<T>* r, cpx<T>* p,
                                  cpx<T>* Ap, cpx<T>* grid, double2* dpart, double* ppart, double* rpart,
                                  unsigned* bar, int* err, int* iters, int* flags, double* rr_out, int* grid_used,
-                                 unsigned long long* ptime) {
+                                 unsigned long long* ptime, int cta_div) {
   PcgArgs<T> a;
   a.g = g; a.pl = pl; a.tw = P.tw; a.kin = P.kin; a.vloc_s = P.vloc_s; a.C = P.C;
   a.nocc = nocc; a.npw = npw; a.ncol = ncol; a.nchunk = (npw + kPChunk - 1) / kPChunk;
@@ -471,8 +473,19 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
   a.x = x; a.r = r; a.p = p; a.Ap = Ap; a.grid = grid; a.dpart = dpart; a.ppart = ppart; a.rpart = rpart;
   a.bar = bar; a.err = err; a.iters_out = iters; a.flag_out = flags; a.rr_out = rr_out; a.ptime = ptime;
   const size_t sm = pcg_smem<T>(g.N, ncol, nocc);
-  cudaError_t e = cudaFuncSetAttribute(k_cg_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  {
+    // The attribute is per function and per process: only ever raise it, so a
+    // context on another host thread never sees its limit lowered under it.
+    static std::mutex mu;
+    static size_t raised = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (sm > raised) {
+      e = cudaFuncSetAttribute(k_cg_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+      raised = sm;
+    }
+  }
   int dev = 0, nsm = 0, per = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
@@ -480,7 +493,10 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
     return e;
   if (per < 1) return cudaErrorInvalidConfiguration;
   const int ntask = ncol * std::max(g.N, g.nplanes);
-  const int nblk = std::min(per * nsm, std::max(ntask, 1));
+  // cta_div contexts run concurrently (batch mode): each takes an equal share
+  // of the resident slots, so all their grids can be co-resident at once.
+  const int cap = std::max(1, per * nsm / std::max(cta_div, 1));
+  const int nblk = std::min(cap, std::max(ntask, 1));
   *grid_used = nblk;
   void* args[] = {&a};
   ++g_launches;
@@ -491,11 +507,11 @@ template cudaError_t launch_cg_persistent<float>(cudaStream_t, const Geometry&, 
                                                  int, int, int, const double2*, const int*, const double2*,
                                                  const double*, double, int, float2*, float2*, float2*, float2*,
                                                  float2*, double2*, double*, double*, unsigned*, int*, int*, int*,
-                                                 double*, int*, unsigned long long*);
+                                                 double*, int*, unsigned long long*, int);
 template cudaError_t launch_cg_persistent<double>(cudaStream_t, const Geometry&, const FftPlan&, const Prec<double>&,
                                                   int, int, int, const double2*, const int*, const double2*,
                                                   const double*, double, int, double2*, double2*, double2*,
                                                   double2*, double2*, double2*, double*, double*, unsigned*, int*,
-                                                  int*, int*, double*, int*, unsigned long long*);
+                                                  int*, int*, double*, int*, unsigned long long*, int);
 
 }  // namespace gw

@@ -20,7 +20,7 @@
 
 namespace gw {
 
-unsigned long long g_launches = 0;
+std::atomic<unsigned long long> g_launches{0};
 
 constexpr int kP = 16;          // pencils per tile
 constexpr int kThreads = 256;

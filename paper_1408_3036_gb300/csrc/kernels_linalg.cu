@@ -405,10 +405,14 @@ k_qmr_init(int npw, const double2* __restrict__ b, cpx<T>* __restrict__ x, cpx<T
     st.iters[c] = 0;
     st.flag[c] = 0;
     st.rr_stop[c] = fmax(tol_in2 * s1, st.rr_abs ? st.rr_abs[c] : 0.0);
+    st.qbest[c] = s1;
+    st.itbest[c] = 0;
     st.active[c] = (on && s1 > 0.0) ? 1 : 0;
     if (!st.active[c]) atomicAdd(st.n_done, 1);
   }
 }
+
+constexpr int kQmrStagWindow = 1000;
 
 // sigma = [q, t]; alpha = rho / sigma
 template <typename T>
@@ -531,11 +535,25 @@ k_qmr_dx(int npw, cpx<T>* __restrict__ x, cpx<T>* __restrict__ d, const cpx<T>* 
     const int it = st.iters[c] + 1;
     st.iters[c] = it;
     const double tau = st.tau[c];
+    // tau is the quasi-residual norm: for a Hermitian system (real frequency)
+    // it is the minimal-residual norm of the iterate, and the usual estimate of
+    // |b - A x| in the complex-symmetric case.  The FP64 refinement around the
+    // solve checks the true residual.
+    const double qb = tau * tau;
+    if (qb < 0.25 * st.qbest[c]) { st.qbest[c] = qb; st.itbest[c] = it; }
     bool stop = false;
     if (st.flag[c] == 2 || !isfinite(tau)) { st.flag[c] = 2; stop = true; }
-    else if (tau * tau * (it + 1) <= st.rr_stop[c]) { st.flag[c] = 0; stop = true; }
+    else if (qb <= st.rr_stop[c]) { st.flag[c] = 0; stop = true; }
     else if (!(rn.x * rn.x + rn.y * rn.y > 0.0)) { st.flag[c] = 2; stop = true; }
     else if (it >= maxit) { st.flag[c] = 1; stop = true; }
+    else if (it - st.itbest[c] > max(kQmrStagWindow, 2 * st.itbest[c])) {
+      // The estimate has not halved for a long stretch: the recurrence has reached
+      // the accuracy its working precision allows for this (nearly singular,
+      // indefinite) system.  Stop; the FP64 refinement around the solve
+      // continues from the iterate reached.
+      st.flag[c] = 4;
+      stop = true;
+    }
     if (stop) { st.active[c] = 0; atomicAdd(st.n_done, 1); }
   }
 }

@@ -45,8 +45,10 @@ struct QmrState {
   double* tau = nullptr;
   double* rr_stop = nullptr;
   const double* rr_abs = nullptr;
+  double* qbest = nullptr;   // smallest tau^2 so far (to within a factor 4)
+  int* itbest = nullptr;     // iteration at which qbest was last lowered
   int* iters = nullptr;
-  int* flag = nullptr;       // 0 converged, 1 max iterations, 2 breakdown
+  int* flag = nullptr;       // 0 converged, 1 max iterations, 2 breakdown, 4 stagnated
   int* active = nullptr;
   int* n_done = nullptr;
   unsigned* cnt = nullptr;
@@ -111,7 +113,7 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
                                  const double* rr_abs, double tol_in2, int maxit, cpx<T>* x, cpx<T>* r, cpx<T>* p,
                                  cpx<T>* Ap, cpx<T>* grid, double2* dpart, double* ppart, double* rpart,
                                  unsigned* bar, int* err, int* iters, int* flags, double* rr_out, int* grid_used,
-                                 unsigned long long* ptime = nullptr);
+                                 unsigned long long* ptime = nullptr, int cta_div = 1);
 constexpr int kPersistentMaxCols = 256;
 
 }  // namespace gw

@@ -152,6 +152,34 @@ def batch(attempt=0, n_cells=32):
     return Workload("batch", cells, omegas, starts, 40)
 
 
+SMALL_N = (12, 15, 16, 18, 20)
+
+
+def batch_small(attempt=0, n_cells=5):
+    """The uneven-batch recipe scaled down to sizes the oracle finishes in
+    seconds: L~U[6,9], N in {12..20} (>= 2R+1), ecut~U[2,4], N_occ~U{2..6},
+    wells U{2..5} (D=-2, sigma=1), K=8; frequencies 0, two real in [0,1] and
+    one complex."""
+    rng = _rng(13, attempt)
+    cells = []
+    for _ in range(n_cells):
+        L = rng.uniform(6.0, 9.0)
+        ecut = rng.uniform(2.0, 4.0)
+        R = math.sqrt(2.0 * ecut) * L / (2.0 * math.pi)
+        okN = [n for n in SMALL_N if n >= 2 * math.floor(R) + 1]
+        if not okN:
+            ecut = 0.5 * (2.0 * math.pi * (SMALL_N[-1] - 1) / 2 / L) ** 2
+            okN = [SMALL_N[-1]]
+        N = int(rng.choice(okN))
+        n_wells = int(rng.integers(2, 6))
+        centres = rng.uniform(0.0, L, size=(n_wells, 3))
+        n_occ = int(rng.integers(2, 7))
+        cells.append(Cell(L, N, ecut, n_occ, centres, -2.0, 1.0))
+    starts = [_starts(rng, c.ng, 1) for c in cells]
+    omegas = np.concatenate([[0.0], rng.uniform(0.0, 1.0, size=2), [0.3 + 0.1j]]).astype(complex)
+    return Workload("batch_small", cells, omegas, starts, 8)
+
+
 def redraw_omega(attempt_rng_seed, lo, hi):
     """Fresh frequency draw for the batch config when one lands within 1e-3 Ha
     of a transition (the caller decides; this only draws)."""
