@@ -103,8 +103,15 @@ def test_batch_uneven_full_size():
     A, B = b.lanczos(starts, wl.k, omegas, gw.GW_FP64)
     assert np.all(b.last_status == 0)
     assert np.abs(A.imag).max() == 0 and np.abs(B.imag).max() == 0
+    n_below = 0
     for i, (c, (sph, gs)) in enumerate(zip(cells, states)):
-        if i not in (0, len(cells) - 1):      # the smallest and the largest cell
+        gap = np.min(np.subtract.outer(gs.eps_all[gs.n_occ:], gs.eps))
+        for w, om in enumerate(omegas[i]):
+            if om.real < gap:
+                n_below += 1
+                ritz = np.linalg.eigvalsh(OL.tridiag(A[i, w].real, B[i, w].real))
+                assert ritz.min() > 1.0 - 1e-10
+        if i not in (0, len(cells) - 1):      # one at a time: the smallest and the largest cell
             continue
         one = gw.Cell(c.L, c.N, c.ecut, c.vloc)
         one.set_occupied(gs.C, gs.eps)
@@ -112,11 +119,8 @@ def test_batch_uneven_full_size():
             a1, b1, _ = one.lanczos(starts[i], wl.k, om.real, gw.GW_FP64)
             assert rel(A[i, w].real, a1) < 1e-10
             assert rel(B[i, w].real, b1) < 1e-10
-            gap = np.min(np.subtract.outer(gs.eps_all[gs.n_occ:], gs.eps))
-            if om.real < gap:
-                ritz = np.linalg.eigvalsh(OL.tridiag(A[i, w].real, B[i, w].real))
-                assert ritz.min() > 1.0 - 1e-10
         one.close()
+    assert n_below > 0
     # sampled output: alpha_1 = <q_1|eps~ q_1> of the smallest cell, by the oracle
     sph, gs = states[0]
     wgt = sph.omega_vol / sph.ng
