@@ -255,6 +255,18 @@ gw_status gw_stats(const gw_ctx* ctx, double* out, int n);
 gw_status gw_set_solver(gw_ctx* ctx, double tol, double tol_inner, int max_iter, int max_outer);
 
 /*
+ * gw_set_precond -- preconditioner of the Sternheimer solvers (CG and SQMR):
+ *   1 (default)  kinetic preconditioner of Teter, Payne and Allan, diagonal in
+ *                G, with the kinetic energy of the column's occupied state as
+ *                reference (symmetric, also in the bilinear form)
+ *   0            none, as in the paper (Sec. Avoiding summations: SQMR without
+ *                preconditioning)
+ * Both solve the same equations to the same tolerance; the preconditioner
+ * only changes the iteration count.  GW_E_ARG for any other kind.
+ */
+gw_status gw_set_precond(gw_ctx* ctx, int kind);
+
+/*
  * gw_profile -- time selected kernel classes with CUDA events on the work
  * stream (one event pair around each launch; mask 0 turns timing off).
  * Classes (multi-launch CG): 0 scatter + inverse z pass (with the CG p update),

@@ -42,6 +42,8 @@ struct gw_ctx {
   long long pcg_iters = 0;      // iterations run by persistent launches
   int pcg_launch_blocks = 0;
   int cta_div = 1;              // contexts sharing the GPU concurrently (batch mode)
+  int precond = 1;              // 1: kinetic (TPA) preconditioner in the Sternheimer solvers; 0: none
+  std::vector<double> tkin;     // kinetic energy of each occupied state (preconditioner reference)
   bool ptime_init = false;
   double vmax = 0.0;            // max |V_loc|
   int max_iter = 20000, max_outer = 12;
@@ -235,7 +237,7 @@ gw_status h_apply(gw_ctx* ctx, cpx<T>* x, int ncol, const double2* E, const int*
 // ---------------------------------------------------------------------------
 template <typename T>
 gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, const int* outer_active,
-                   cpx<T>* x, double tol, const double* rr_abs, long long* it_sum, int* it_max) {
+                   cpx<T>* x, double tol, const double* rr_abs, const double* tk, long long* it_sum, int* it_max) {
   const int npw = ctx->npw;
   const std::string t = tname<T>();
   cpx<T>*r, *p, *Ap, *grid;
@@ -256,13 +258,15 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
   TRY(getbuf(ctx, "cg_cnt", ncol, &st.cnt));
   TRY(getbuf(ctx, "cg_rrstop", ncol, &st.rr_stop));
   TRY(getbuf(ctx, "cg_rrmin", ncol, &st.rr_min));
+  TRY(getbuf(ctx, "cg_rz", ncol, &st.rz));
   st.rr_abs = rr_abs;
+  st.tk = tk;
   TRY(ensure_work(ctx, ncol));
   CK(cudaMemsetAsync(st.cnt, 0, ncol * sizeof(unsigned), ctx->st));
   CK(cudaMemsetAsync(st.n_done, 0, sizeof(int), ctx->st));
   auto& P = prec_of<T>(ctx);
   const Geometry& g = ctx->geo;
-  launch_cg_init<T, double>(ctx->st, npw, ncol, b64, x, r, outer_active, ctx->work, st, tol * tol, 0.0);
+  launch_cg_init<T, double>(ctx->st, npw, ncol, b64, x, r, outer_active, ctx->work, st, P.kin, tol * tol, 0.0);
   GatherDots dots;
   dots.C = P.C;
   dots.nocc = ctx->nocc;
@@ -274,7 +278,7 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
   const int check = 8;
   for (int it = 0; it < ctx->max_iter; ++it) {
     PROF(PC_ZSCAT, launch_zpass<T>(ctx->st, Z_SCATTER_INV_PUPD, g, P, ctx->plan, grid, p, r, st.beta, nullptr,
-                                   nullptr, st.active, nullptr, nullptr, ncol));
+                                   nullptr, st.active, nullptr, nullptr, ncol, nullptr, tk));
     PROF(PC_YINV, launch_ypass<T>(ctx->st, 1, 1, 0, g, P, ctx->plan, grid, st.active, ncol, 0));
     PROF(PC_XH, launch_xpass_mul<T>(ctx->st, 1, 1, 1, g, P, ctx->plan, grid, P.vloc_s, st.active, ncol));
     PROF(PC_YFWD, launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, st.active, ncol, 0));
@@ -282,7 +286,8 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
                                    st.active, nullptr, nullptr, ncol, &dots));
     PROF(PC_PROJ, launch_proj_update<T>(ctx->st, P.C, ctx->nocc, npw, Ap, ncol, st.active, ctx->work.coef,
                                         ctx->work, p, pap));
-    PROF(PC_CGUPD, launch_cg_update<T>(ctx->st, npw, ncol, x, r, p, Ap, pap, ctx->work, st, tol2, ctx->max_iter));
+    PROF(PC_CGUPD, launch_cg_update<T>(ctx->st, npw, ncol, x, r, p, Ap, pap, ctx->work, st, P.kin, tol2,
+                                           ctx->max_iter));
     if ((it % check) == check - 1 || it == ctx->max_iter - 1) {
       CK(cudaMemcpyAsync(ctx->host_pin, st.n_done, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
       TRY(sync(ctx, "cg_solve"));
@@ -322,7 +327,8 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
 // ---------------------------------------------------------------------------
 template <typename T>
 gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, const int* outer_active,
-                              cpx<T>* x, double tol, const double* rr_abs, long long* it_sum, int* it_max) {
+                              cpx<T>* x, double tol, const double* rr_abs, const double* tk, long long* it_sum,
+                              int* it_max) {
   const int npw = ctx->npw;
   const std::string t = tname<T>();
   const int nchunk = (npw + 1023) / 1024;
@@ -332,12 +338,13 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
   TRY(getbuf(ctx, "cg_Ap" + t, (size_t)ncol * npw, &Ap));
   TRY(getbuf(ctx, "g_cg" + t, (size_t)ncol * ctx->N3, &grid));
   double2* dpart;
-  double *ppart, *rpart, *rr_out;
+  double *ppart, *rpart, *zpart, *rr_out;
   unsigned* bar;
   int *err, *iters, *flags;
   TRY(getbuf(ctx, "pcg_dpart", (size_t)ncol * ctx->geo.nplanes * ctx->nocc, &dpart));
   TRY(getbuf(ctx, "pcg_ppart", (size_t)ncol * nchunk, &ppart));
   TRY(getbuf(ctx, "pcg_rpart", (size_t)ncol * nchunk, &rpart));
+  TRY(getbuf(ctx, "pcg_zpart", (size_t)ncol * nchunk, &zpart));
   TRY(getbuf(ctx, "pcg_rr", ncol, &rr_out));
   TRY(getbuf(ctx, "pcg_bar", 1, &bar));
   TRY(getbuf(ctx, "pcg_err", 1, &err));
@@ -356,7 +363,7 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
     }
   }
   CK(launch_cg_persistent<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), ctx->nocc, npw, ncol, b64, outer_active,
-                             E, rr_abs, tol * tol, ctx->max_iter, x, r, p, Ap, grid, dpart, ppart, rpart, bar, err,
+                             E, rr_abs, tol * tol, ctx->max_iter, x, r, p, Ap, grid, dpart, ppart, rpart, zpart, tk, bar, err,
                              iters, flags, rr_out, &used, ptime, ctx->cta_div));
   if (ptime) {
     unsigned long long h[8];
@@ -391,7 +398,7 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
 // ---------------------------------------------------------------------------
 template <typename T>
 gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, const int* outer_active,
-                    cpx<T>* x, double tol, const double* rr_abs, long long* it_sum, int* it_max) {
+                    cpx<T>* x, double tol, const double* rr_abs, const double* tk, long long* it_sum, int* it_max) {
   const int npw = ctx->npw;
   const std::string t = tname<T>();
   cpx<T>*r, *q, *dd, *tt, *grid;
@@ -417,13 +424,14 @@ gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E,
   TRY(getbuf(ctx, "cg_ndone", 1, &st.n_done));
   TRY(getbuf(ctx, "cg_cnt", ncol, &st.cnt));
   st.rr_abs = rr_abs;
+  st.tk = tk;
   TRY(ensure_work(ctx, ncol));
   CK(cudaMemsetAsync(st.cnt, 0, ncol * sizeof(unsigned), ctx->st));
   CK(cudaMemsetAsync(st.n_done, 0, sizeof(int), ctx->st));
   auto& P = prec_of<T>(ctx);
   const Geometry& g = ctx->geo;
   const int* neg = g.sph_neg;
-  launch_qmr<T>(ctx->st, 0, npw, ncol, b64, x, r, q, dd, tt, neg, outer_active, ctx->work, st, tol * tol,
+  launch_qmr<T>(ctx->st, 0, npw, ncol, b64, x, r, q, dd, tt, neg, outer_active, ctx->work, st, P.kin, tol * tol,
                 ctx->max_iter);
   GatherDots dots;
   dots.C = P.C;
@@ -445,7 +453,8 @@ gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E,
     launch_proj_update<T>(ctx->st, P.C, ctx->nocc, npw, tt, ncol, st.active, ctx->work.coef, ctx->work, nullptr,
                           nullptr);
     for (int step = 1; step <= 4; ++step)
-      launch_qmr<T>(ctx->st, step, npw, ncol, b64, x, r, q, dd, tt, neg, outer_active, ctx->work, st, tol * tol,
+      launch_qmr<T>(ctx->st, step, npw, ncol, b64, x, r, q, dd, tt, neg, outer_active, ctx->work, st, P.kin,
+                    tol * tol,
                     ctx->max_iter);
     if ((it % check) == check - 1 || it == ctx->max_iter - 1) {
       CK(cudaMemcpyAsync(ctx->host_pin, st.n_done, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
@@ -489,15 +498,17 @@ gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E,
 // when the columns fit, else the multi-launch form).
 template <typename U>
 gw_status inner_solve(gw_ctx* ctx, bool qmr, int ncol, const double2* r64, const double2* E, const int* oact,
-                      cpx<U>* d, double tol_in, const double* rra, long long* it_sum, int* it_max) {
-  if (qmr) return qmr_solve<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, it_sum, it_max);
+                      cpx<U>* d, double tol_in, const double* rra, const double* tk, long long* it_sum,
+                      int* it_max) {
+  if (qmr) return qmr_solve<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, tk, it_sum, it_max);
   if (ncol <= kPersistentMaxCols && !ctx->no_persistent)
-    return cg_solve_persistent<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, it_sum, it_max);
-  return cg_solve<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, it_sum, it_max);
+    return cg_solve_persistent<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, tk, it_sum, it_max);
+  return cg_solve<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, tk, it_sum, it_max);
 }
 
 template <typename T>
-gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, double2* x64, bool qmr = false) {
+gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, double2* x64, bool qmr = false,
+                const double* tk = nullptr) {
   const int npw = ctx->npw;
   const bool mixed = !std::is_same<T, double>::value;
   const double tol = mixed ? ctx->tol_mixed : ctx->tol;
@@ -535,10 +546,10 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
     if (esc) {
       if (!d64) TRY(getbuf(ctx, "sv_d64", (size_t)ncol * npw, &d64));
       TRY(inner_solve<double>(ctx, qmr, ncol, r64, E, oact, reinterpret_cast<cpx<double>*>(d64),
-                              std::max(1e2 * ctx->tol, 1e-11), rra, &it_sum, &it_max));
+                              std::max(1e2 * ctx->tol, 1e-11), rra, tk, &it_sum, &it_max));
       launch_add_conv<double>(ctx->st, npw, ncol, reinterpret_cast<cpx<double>*>(d64), x64, oact);
     } else {
-      TRY(inner_solve<T>(ctx, qmr, ncol, r64, E, oact, d, tol_in, rra, &it_sum, &it_max));
+      TRY(inner_solve<T>(ctx, qmr, ncol, r64, E, oact, d, tol_in, rra, tk, &it_sum, &it_max));
       launch_add_conv<T>(ctx->st, npw, ncol, d, x64, oact);
     }
     // r64 = b - P_c (H - E) x64
@@ -670,6 +681,7 @@ gw_status chi0_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, const std::
   // -- solver columns
   std::vector<int> src, s0, s1;
   std::vector<double2> E;
+  std::vector<double> tk;
   bool qmr = false;
   for (int o = 0; o < nom; ++o) {
     const bool zero = (omega[o].x == 0.0 && omega[o].y == 0.0);
@@ -682,6 +694,7 @@ gw_status chi0_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, const std::
           src.push_back(b * nocc + v);
           const double sgn = (sg == 0) ? 1.0 : -1.0;     // x^-: H - e_v - w;  x^+: H - e_v + w
           E.push_back(make_double2(ctx->eps[v] + sgn * omega[o].x, sgn * omega[o].y));
+          tk.push_back(ctx->tkin[v]);
         }
         s0.push_back(first);
         s1.push_back(ns == 2 ? first + 1 : -1);
@@ -695,12 +708,14 @@ gw_status chi0_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, const std::
   TRY(upload(ctx, "col_s0", s0, &ds0));
   TRY(upload(ctx, "col_s1", s1, &ds1));
   TRY(upload(ctx, "col_E", E, &dE));
+  double* dtk = nullptr;
+  if (ctx->precond) TRY(upload(ctx, "col_tk", tk, &dtk));
   double2 *bcol, *xcol, *sol64;
   TRY(getbuf(ctx, "bcol", (size_t)ncol * npw, &bcol));
   TRY(getbuf(ctx, "xcol", (size_t)ncol * npw, &xcol));
   TRY(getbuf(ctx, "sol64", (size_t)nsol * npw, &sol64));
   launch_gather_rows<double, double>(ctx->st, npw, ncol, rhs64, dsrc, bcol);
-  TRY(solve<S>(ctx, ncol, bcol, dE, xcol, qmr));
+  TRY(solve<S>(ctx, ncol, bcol, dE, xcol, qmr, dtk));
   // -- combine: x^- + x^+, or 2 x at omega = 0 (x^- = x^+)
   launch_combine(ctx->st, npw, nsol, xcol, ds0, ds1, 1.0, 2.0, sol64);
   // -- density reduction
@@ -1094,6 +1109,8 @@ gw_status grad_core(gw_ctx* ctx, const double* phi, int K, double* s_out, double
   TRY(upload(ctx, "gr_cv", cv, &dcv));
   TRY(upload(ctx, "gr_cz", cz, &dcz));
   TRY(upload(ctx, "gr_E", E, &dE));
+  double* dtk = nullptr;
+  if (ctx->precond) TRY(upload(ctx, "gr_tk", ctx->tkin, &dtk));
   double2 *grid, *rhs, *dC, *dU, *eta, *lam, *Sg, *Wm;
   TRY(getbuf(ctx, "gr_grid", (size_t)nocc * N3, &grid));
   TRY(getbuf(ctx, "gr_rhs", (size_t)nocc * npw, &rhs));
@@ -1115,7 +1132,7 @@ gw_status grad_core(gw_ctx* ctx, const double* phi, int K, double* s_out, double
   launch_proj<double>(ctx->st, P.C, nocc, npw, rhs, nocc, nullptr, ctx->work, nullptr, nullptr);
   launch_proj<double>(ctx->st, P.C, nocc, npw, rhs, nocc, nullptr, ctx->work, nullptr, nullptr);
   TRY(launch_check(ctx, "grad rhs"));
-  TRY(solve<S>(ctx, nocc, rhs, dE, dC));
+  TRY(solve<S>(ctx, nocc, rhs, dE, dC, false, dtk));
   // dC = -x  (dpsi coefficients); dU_v = IFFT(dC_v) on the grid
   {
     std::vector<int> one(nocc, -1);
@@ -1154,7 +1171,7 @@ gw_status grad_core(gw_ctx* ctx, const double* phi, int K, double* s_out, double
     launch_proj<double>(ctx->st, P.C, nocc, npw, eta, nocc, nullptr, ctx->work, nullptr, nullptr);
   }
   TRY(launch_check(ctx, "grad eta"));
-  TRY(solve<S>(ctx, nocc, eta, dE, lam));
+  TRY(solve<S>(ctx, nocc, eta, dE, lam, false, dtk));
   // Re g2 = -(1/Omega) Re sum_v lambda_v(r) u_v(r)
   launch_zpass<double>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, grid, lam, nullptr, nullptr, nullptr, nullptr,
                        nullptr, nullptr, nullptr, nocc);
@@ -1479,6 +1496,12 @@ gw_status gw_set_occupied(gw_ctx* ctx, int n_occ, const double* psi, const doubl
   }
   ctx->nocc = n_occ;
   ctx->eps = e;
+  ctx->tkin.assign(n_occ, 0.0);
+  for (int v = 0; v < n_occ; ++v) {     // T_v = sum_G |G|^2/2 |c_G|^2
+    double t = 0.0;
+    for (int s2 = 0; s2 < npw; ++s2) t += ctx->kin[s2] * std::norm(R[(size_t)v * npw + s2]);
+    ctx->tkin[v] = std::max(t, 1e-3);
+  }
   {
     double kmax = 0.0, emax = 0.0;
     for (double k : ctx->kin) kmax = std::max(kmax, k);
@@ -1756,6 +1779,13 @@ gw_status gw_set_solver(gw_ctx* ctx, double tol, double tol_inner, int max_iter,
   if (tol_inner > 0) ctx->tol_inner = tol_inner;
   if (max_iter > 0) ctx->max_iter = max_iter;
   if (max_outer > 0) ctx->max_outer = max_outer;
+  return GW_OK;
+}
+
+gw_status gw_set_precond(gw_ctx* ctx, int kind) {
+  if (!ctx) return GW_E_ARG;
+  if (kind != 0 && kind != 1) return fail(ctx, GW_E_ARG, "preconditioner kind must be 0 (none) or 1 (kinetic)");
+  ctx->precond = kind;
   return GW_OK;
 }
 

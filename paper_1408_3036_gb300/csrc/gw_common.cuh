@@ -90,6 +90,19 @@ template <typename T> struct Prec {
   cpx<T>* U = nullptr;       // [nocc][N3] u_v(r) = sum_G c_G e^{iGr}
 };
 
+// Kinetic preconditioner of the Sternheimer solvers (Teter, Payne and Allan,
+// Phys. Rev. B 40, 12255 (1989)): for x = (|G|^2/2) / T_ref, with T_ref the
+// kinetic energy of the occupied state of the column,
+//   K(x) = (27 + 18x + 12x^2 + 8x^3) / (27 + 18x + 12x^2 + 8x^3 + 16x^4),
+// 1 for x << 1 and 1/(2x) for x >> 1: a smooth inverse of the kinetic energy
+// that leaves the low-lying components alone.  K(-G) = K(G), so it is symmetric
+// in the bilinear form as well.
+template <typename T>
+__device__ __forceinline__ T tpa(T x) {
+  const T p = (T)27 + x * ((T)18 + x * ((T)12 + x * (T)8));
+  return p / (p + (T)16 * (x * x) * (x * x));
+}
+
 // Deterministic cross-block reduction: every block writes its partial sums,
 // then takes a ticket; the block drawing the last ticket sees all partials
 // (after the fences) and resets the ticket for the next launch.
@@ -129,7 +142,7 @@ template <typename T>
 void launch_zpass(cudaStream_t s, int mode, const Geometry& g, const Prec<T>& P, const FftPlan& pl,
                   cpx<T>* grid, cpx<T>* sph, const cpx<T>* sph_r, const double* beta,
                   const cpx<T>* sph_p, const double2* E, const int* active, const T* real_in,
-                  T* real_out, int ncol, const GatherDots* dots = nullptr);
+                  T* real_out, int ncol, const GatherDots* dots = nullptr, const double* tk = nullptr);
 template <typename T>
 void launch_ypass(cudaStream_t s, int inverse, int pruned_in, int pruned_out, const Geometry& g,
                   const Prec<T>& P, const FftPlan& pl, cpx<T>* grid, const int* active, int ncol, int full_planes);

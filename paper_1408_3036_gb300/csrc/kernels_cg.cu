@@ -7,7 +7,8 @@
 // all resident and step through five phases per iteration, separated by a
 // grid barrier (bounded spin: a barrier that waits too long sets an error flag
 // and every CTA returns):
-//   A  per (column, plane i0): p = r + beta p on the plane's sphere entries,
+//   A  per (column, plane i0): p = K r + beta p on the plane's sphere entries
+//      (K: kinetic preconditioner, 1 without one),
 //      scatter, z-IFFT of the disc rows, y-IFFT of the plane (all in shared
 //      memory), store the plane
 //   B  per (column, i1, 16 i2): x-IFFT, * V(r)/N_g, x-FFT (planes of the sphere)
@@ -15,8 +16,8 @@
 //      entries, Ap = (Vp)_G + (|G|^2/2 - E) p_G, partial <C_v|Ap> of the plane
 //   D  per (column, 1024 entries): coef = sum of the plane partials,
 //      Ap -= C coef (P_c), partial p^H Ap
-//   E  per (column, 1024 entries): alpha = rr / p^H Ap, x += alpha p,
-//      r -= alpha Ap, partial |r|^2
+//   E  per (column, 1024 entries): alpha = r^H K r / p^H Ap, x += alpha p,
+//      r -= alpha Ap, partials |r|^2 and r^H K r
 // After E every CTA sums the partials of every column in the same order, so
 // all CTAs take the same convergence decisions without another barrier.
 #include <algorithm>
@@ -58,6 +59,8 @@ struct PcgArgs {
   double2* dpart;   // [ncol][nplanes][nocc]
   double* ppart;    // [ncol][nchunk]
   double* rpart;    // [ncol][nchunk]
+  double* zpart;    // [ncol][nchunk] partial r^H K r
+  const double* tk; // per-column T_ref of the kinetic preconditioner, or null (none)
   unsigned* bar;
   int* err;
   int* iters_out;
@@ -115,7 +118,7 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 __host__ __device__ inline PcgLayout pcg_layout(int N, int ncol, int nocc, int vsize) {
   PcgLayout L;
   L.dbl = 0;
-  L.ints = align16(L.dbl + (size_t)4 * ncol * sizeof(double));
+  L.ints = align16(L.dbl + (size_t)5 * ncol * sizeof(double));
   L.red = align16(L.ints + (size_t)(3 * ncol + N) * sizeof(int));
   L.coef = align16(L.red + 32 * sizeof(double));
   L.tw = align16(L.coef + (size_t)nocc * 2 * sizeof(double));
@@ -138,6 +141,7 @@ __global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
   double* st_min = st_rr + ncol;
   double* st_stop = st_min + ncol;
   double* st_beta = st_stop + ncol;
+  double* st_rz = st_beta + ncol;                             // r^H K r
   int* st_act = reinterpret_cast<int*>(smem_raw + L.ints);
   int* st_it = st_act + ncol;
   int* st_flag = st_it + ncol;
@@ -158,24 +162,33 @@ __global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
     const int c = task / a.nchunk, ch = task - c * a.nchunk;
     const bool on = !a.outer_active || a.outer_active[c];
     const int g0 = ch * kPChunk, g1 = min(a.npw, g0 + kPChunk);
-    double acc = 0.0;
+    const T rtk = a.tk ? (T)(1.0 / a.tk[c]) : (T)0;
+    double acc = 0.0, accz = 0.0;
     for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
       const size_t i = (size_t)c * a.npw + G;
       const V bv = on ? from_d<T>(a.b64[i]) : mk<T>(0, 0);
       a.r[i] = bv;
       a.x[i] = mk<T>(0, 0);
       const double2 bd = to_d(bv);
-      acc += bd.x * bd.x + bd.y * bd.y;
+      const double n2 = bd.x * bd.x + bd.y * bd.y;
+      acc += n2;
+      accz += (rtk != (T)0 ? (double)tpa<T>(a.kin[G] * rtk) : 1.0) * n2;
     }
     acc = dsum_block<T>(acc, red);
     if (threadIdx.x == 0) a.rpart[(size_t)c * a.nchunk + ch] = acc;
+    accz = dsum_block<T>(accz, red);
+    if (threadIdx.x == 0) a.zpart[(size_t)c * a.nchunk + ch] = accz;
   }
   if (!grid_barrier(a.bar, a.err, nblk)) return;
   for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < a.nchunk; ++k) s += a.rpart[(size_t)c * a.nchunk + k];
+    double s = 0.0, z = 0.0;
+    for (int k = 0; k < a.nchunk; ++k) {
+      s += a.rpart[(size_t)c * a.nchunk + k];
+      z += a.zpart[(size_t)c * a.nchunk + k];
+    }
     const bool on = !a.outer_active || a.outer_active[c];
     st_rr[c] = s;
+    st_rz[c] = z;
     st_min[c] = s;
     st_stop[c] = fmax(a.tol_in2 * s, a.rr_abs ? a.rr_abs[c] : 0.0);
     st_beta[c] = -1.0;
@@ -206,13 +219,19 @@ __global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
       const int s0 = g.plane_sph[pi], s1 = g.plane_sph[pi + 1];
       const int q0 = g.plane_pen[pi], npp = g.plane_pen[pi + 1] - q0;
       const double bt = st_beta[c];
+      const T rtk = a.tk ? (T)(1.0 / a.tk[c]) : (T)0;
       const size_t sc = (size_t)c * a.npw;
       for (int e = threadIdx.x; e < npp * LDp; e += blockDim.x) A[e] = mk<T>(0, 0);
       for (int k = threadIdx.x; k < N; k += blockDim.x) rowmap[k] = -1;
       __syncthreads();
       for (int k = threadIdx.x; k < npp; k += blockDim.x) rowmap[g.pencils[q0 + k].y] = k;
       for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-        const V rv = a.r[sc + s];
+        V rv = a.r[sc + s];
+        if (rtk != (T)0) {                         // z = K r
+          const T k = tpa<T>(a.kin[s] * rtk);
+          rv.x *= k;
+          rv.y *= k;
+        }
         V val = rv;
         if (bt >= 0.0) {
           const V pv = a.p[sc + s];
@@ -398,10 +417,11 @@ __global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
       }
       __syncthreads();
       const double pap = bcast;
-      const T al = (T)((pap > 0.0) ? st_rr[c] / pap : 0.0);
+      const T al = (T)((pap > 0.0) ? st_rz[c] / pap : 0.0);
       const int g0 = ch * kPChunk, g1 = min(a.npw, g0 + kPChunk);
       const size_t sc = (size_t)c * a.npw;
-      double acc = 0.0;
+      const T rtk = a.tk ? (T)(1.0 / a.tk[c]) : (T)0;
+      double acc = 0.0, accz = 0.0;
       for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
         const size_t i = sc + G;
         const V pv = a.p[i], av = a.Ap[i];
@@ -413,10 +433,14 @@ __global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
         a.x[i] = xv;
         a.r[i] = rv;
         const double2 rd = to_d(rv);
-        acc += rd.x * rd.x + rd.y * rd.y;
+        const double n2 = rd.x * rd.x + rd.y * rd.y;
+        acc += n2;
+        accz += (rtk != (T)0 ? (double)tpa<T>(a.kin[G] * rtk) : 1.0) * n2;
       }
       acc = dsum_block<T>(acc, red);
       if (threadIdx.x == 0) a.rpart[(size_t)c * a.nchunk + ch] = acc;
+      accz = dsum_block<T>(accz, red);
+      if (threadIdx.x == 0) a.zpart[(size_t)c * a.nchunk + ch] = accz;
       __syncthreads();
     }
     if (!grid_barrier(a.bar, a.err, nblk)) return;
@@ -425,14 +449,16 @@ __global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
     // ---- convergence decisions (identical in every CTA)
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
       if (!st_act[c]) continue;
-      double s = 0.0, pp = 0.0;
+      double s = 0.0, z = 0.0, pp = 0.0;
       for (int k = 0; k < a.nchunk; ++k) {
         s += a.rpart[(size_t)c * a.nchunk + k];
+        z += a.zpart[(size_t)c * a.nchunk + k];
         pp += a.ppart[(size_t)c * a.nchunk + k];
       }
       const int itc = st_it[c] + 1;
       st_it[c] = itc;
-      st_beta[c] = s / st_rr[c];
+      st_beta[c] = z / st_rz[c];
+      st_rz[c] = z;
       st_rr[c] = s;
       st_min[c] = fmin(st_min[c], s);
       int stop = 0;
@@ -464,13 +490,14 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
                                  int npw, int ncol, const double2* b64, const int* outer_active, const double2* E,
                                  const double* rr_abs, double tol_in2, int maxit, cpx<T>* x, cpx<T>* r, cpx<T>* p,
                                  cpx<T>* Ap, cpx<T>* grid, double2* dpart, double* ppart, double* rpart,
-                                 unsigned* bar, int* err, int* iters, int* flags, double* rr_out, int* grid_used,
-                                 unsigned long long* ptime, int cta_div) {
+                                 double* zpart, const double* tk, unsigned* bar, int* err, int* iters, int* flags,
+                                 double* rr_out, int* grid_used, unsigned long long* ptime, int cta_div) {
   PcgArgs<T> a;
   a.g = g; a.pl = pl; a.tw = P.tw; a.kin = P.kin; a.vloc_s = P.vloc_s; a.C = P.C;
   a.nocc = nocc; a.npw = npw; a.ncol = ncol; a.nchunk = (npw + kPChunk - 1) / kPChunk;
   a.b64 = b64; a.outer_active = outer_active; a.E = E; a.rr_abs = rr_abs; a.tol_in2 = tol_in2; a.maxit = maxit;
   a.x = x; a.r = r; a.p = p; a.Ap = Ap; a.grid = grid; a.dpart = dpart; a.ppart = ppart; a.rpart = rpart;
+  a.zpart = zpart; a.tk = tk;
   a.bar = bar; a.err = err; a.iters_out = iters; a.flag_out = flags; a.rr_out = rr_out; a.ptime = ptime;
   const size_t sm = pcg_smem<T>(g.N, ncol, nocc);
   cudaError_t e = cudaSuccess;
@@ -506,12 +533,14 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
 template cudaError_t launch_cg_persistent<float>(cudaStream_t, const Geometry&, const FftPlan&, const Prec<float>&,
                                                  int, int, int, const double2*, const int*, const double2*,
                                                  const double*, double, int, float2*, float2*, float2*, float2*,
-                                                 float2*, double2*, double*, double*, unsigned*, int*, int*, int*,
-                                                 double*, int*, unsigned long long*, int);
+                                                 float2*, double2*, double*, double*, double*, const double*,
+                                                 unsigned*, int*, int*, int*, double*, int*, unsigned long long*,
+                                                 int);
 template cudaError_t launch_cg_persistent<double>(cudaStream_t, const Geometry&, const FftPlan&, const Prec<double>&,
                                                   int, int, int, const double2*, const int*, const double2*,
                                                   const double*, double, int, double2*, double2*, double2*,
-                                                  double2*, double2*, double2*, double*, double*, unsigned*, int*,
-                                                  int*, int*, double*, int*, unsigned long long*, int);
+                                                  double2*, double2*, double2*, double*, double*, double*,
+                                                  const double*, unsigned*, int*, int*, int*, double*, int*,
+                                                  unsigned long long*, int);
 
 }  // namespace gw

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kThreads)
 k_zpass(int mode, Geometry g, Prec<T> P, FftPlan pl, cpx<T>* __restrict__ grid,
         cpx<T>* __restrict__ sph, const cpx<T>* __restrict__ sph_r, const double* __restrict__ beta,
         const cpx<T>* __restrict__ sph_p, const double2* __restrict__ E, const int* __restrict__ active,
-        const T* __restrict__ real_in, T* __restrict__ real_out, GatherDots dots) {
+        const T* __restrict__ real_in, T* __restrict__ real_out, GatherDots dots, const double* __restrict__ tk) {
   using V = cpx<T>;
   extern __shared__ unsigned char smem_raw[];
   const int N = g.N, LD = N + 1;
@@ -66,15 +66,24 @@ k_zpass(int mode, Geometry g, Prec<T> P, FftPlan pl, cpx<T>* __restrict__ grid,
     for (int e = threadIdx.x; e < kP * LD; e += blockDim.x) A[e] = mk<T>(0, 0);
     __syncthreads();
     double bt = 0.0;
-    if (mode == Z_SCATTER_INV_PUPD) bt = beta[col];
+    T rtk = (T)0;                                    // 1 / T_ref of the column (0: no preconditioner)
+    if (mode == Z_SCATTER_INV_PUPD) {
+      bt = beta[col];
+      if (tk) rtk = (T)(1.0 / tk[col]);
+    }
     const int4 pa = g.pencils[p0], pb = g.pencils[p0 + np - 1];
     const int s0 = pa.z, s1 = pb.z + pb.w;          // sphere entries of the tile are contiguous
     for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
       V val;
       if (mode == Z_SCATTER_INV_PUPD) {
-        const V rv = sph_r[scol + s];
+        V rv = sph_r[scol + s];
+        if (rtk != (T)0) {                           // z = K r
+          const T k = tpa<T>(P.kin[s] * rtk);
+          rv.x *= k;
+          rv.y *= k;
+        }
         if (bt < 0.0) {
-          val = rv;                                  // first iteration: p = r
+          val = rv;                                  // first iteration: p = z
         } else {
           const V pv = sph[scol + s];
           val = mk<T>(rv.x + (T)bt * pv.x, rv.y + (T)bt * pv.y);
@@ -172,7 +181,7 @@ template <typename T>
 void launch_zpass(cudaStream_t s, int mode, const Geometry& g, const Prec<T>& P, const FftPlan& pl,
                   cpx<T>* grid, cpx<T>* sph, const cpx<T>* sph_r, const double* beta,
                   const cpx<T>* sph_p, const double2* E, const int* active, const T* real_in,
-                  T* real_out, int ncol, const GatherDots* dots) {
+                  T* real_out, int ncol, const GatherDots* dots, const double* tk) {
   const bool disc_list = (mode == Z_SCATTER_INV || mode == Z_SCATTER_INV_PUPD || mode == Z_GATHER_FWD ||
                           mode == Z_GATHER_FWD_H);
   const int npen = disc_list ? g.npen : g.N2;
@@ -183,7 +192,7 @@ void launch_zpass(cudaStream_t s, int mode, const Geometry& g, const Prec<T>& P,
   GatherDots d;
   if (dots) d = *dots;
   k_zpass<T><<<grd, kThreads, sm, s>>>(mode, g, P, pl, grid, sph, sph_r, beta, sph_p, E, active,
-                                        real_in, real_out, d);
+                                        real_in, real_out, d, tk);
 }
 
 // ---------------------------------------------------------------------------
@@ -478,7 +487,8 @@ cudaError_t fft_set_smem_limits() {
 #define GW_INST(T)                                                                                         \
   template void launch_zpass<T>(cudaStream_t, int, const Geometry&, const Prec<T>&, const FftPlan&,      \
                                 cpx<T>*, cpx<T>*, const cpx<T>*, const double*, const cpx<T>*,           \
-                                const double2*, const int*, const T*, T*, int, const GatherDots*);       \
+                                const double2*, const int*, const T*, T*, int, const GatherDots*,        \
+                                const double*);                                                          \
   template void launch_ypass<T>(cudaStream_t, int, int, int, const Geometry&, const Prec<T>&,            \
                                 const FftPlan&, cpx<T>*, const int*, int, int);                          \
   template void launch_xpass_mul<T>(cudaStream_t, int, int, int, const Geometry&, const Prec<T>&,        \

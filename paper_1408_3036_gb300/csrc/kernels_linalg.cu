@@ -247,15 +247,21 @@ void launch_proj_update(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<
 // ---------------------------------------------------------------------------
 // conjugate gradients (Hermitian positive definite A = P_c (H - E) P_c)
 // ---------------------------------------------------------------------------
-// init: x = 0, r = b (converted), rr = rr0 = |b|^2, beta = -1 (first p = r)
+// Preconditioner factor of sphere entry G for column c (1 without one).
+template <typename T>
+__device__ __forceinline__ T precond(const T* kin, const double* tk, int c, int G) {
+  return tk ? tpa<T>(kin[G] * (T)(1.0 / tk[c])) : (T)1;
+}
+
+// init: x = 0, r = b (converted), rr = rr0 = |b|^2, rz = r^H K r, beta = -1 (first p = K r)
 template <typename T, typename U>
 __global__ void __launch_bounds__(kLT)
 k_cg_init(int npw, const cpx<U>* __restrict__ b, cpx<T>* __restrict__ x, cpx<T>* __restrict__ r,
-          const int* __restrict__ outer_active, double* __restrict__ partial, unsigned* __restrict__ cnt,
+          const int* __restrict__ outer_active, double2* __restrict__ partial, const T* __restrict__ kin,
           CgState st, int ncol, double tol_in2, double tol_abs2) {
   const int c = blockIdx.y;
   const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
-  double acc = 0.0;
+  double acc = 0.0, accz = 0.0;
   const bool on = !outer_active || outer_active[c];
   for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
     const size_t i = (size_t)c * npw + G;
@@ -263,17 +269,25 @@ k_cg_init(int npw, const cpx<U>* __restrict__ b, cpx<T>* __restrict__ x, cpx<T>*
     r[i] = bv;
     x[i] = mk<T>(0, 0);
     const double2 bd = to_d(bv);
-    acc += bd.x * bd.x + bd.y * bd.y;
+    const double n2 = bd.x * bd.x + bd.y * bd.y;
+    acc += n2;
+    accz += (double)precond<T>(kin, st.tk, c, G) * n2;
   }
   acc = block_sum(acc);
-  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ncol + c] = acc;
+  accz = block_sum(accz);
+  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ncol + c] = make_double2(acc, accz);
   if (!last_block(&st.cnt[c], gridDim.x)) return;
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < (int)gridDim.x; ++k) s += partial[(size_t)k * ncol + c];
+    double s = 0.0, z = 0.0;
+    for (int k = 0; k < (int)gridDim.x; ++k) {
+      const double2 pk = partial[(size_t)k * ncol + c];
+      s += pk.x;
+      z += pk.y;
+    }
     st.rr[c] = s;
     st.rr0[c] = s;
     st.rr_min[c] = s;
+    st.rz[c] = z;
     // relative target of this pass, but never below what the refinement needs
     // overall (a fraction of the final tolerance on the original right-hand side)
     st.rr_stop[c] = fmax(tol_in2 * s, st.rr_abs ? st.rr_abs[c] : tol_abs2 * s);
@@ -285,19 +299,20 @@ k_cg_init(int npw, const cpx<U>* __restrict__ b, cpx<T>* __restrict__ x, cpx<T>*
   }
 }
 
-// alpha = rr / pap; x += alpha p; r -= alpha Ap; rr' = |r|^2; beta = rr'/rr; masks
+// alpha = rz / pap; x += alpha p; r -= alpha Ap; rr' = |r|^2, rz' = r^H K r;
+// beta = rz'/rz (the next p = K r + beta p is fused into the scatter); masks
 template <typename T>
 __global__ void __launch_bounds__(kLT)
 k_cg_update(int npw, cpx<T>* __restrict__ x, cpx<T>* __restrict__ r, const cpx<T>* __restrict__ p,
-            const cpx<T>* __restrict__ Ap, const double* __restrict__ pap, double* __restrict__ partial,
-            CgState st, double tol2, int maxit, int ncol) {
+            const cpx<T>* __restrict__ Ap, const double* __restrict__ pap, double2* __restrict__ partial,
+            const T* __restrict__ kin, CgState st, double tol2, int maxit, int ncol) {
   const int c = blockIdx.y;
   if (!st.active[c]) return;
   const double pp = pap[c];
-  const double alpha = (pp > 0.0) ? st.rr[c] / pp : 0.0;
+  const double alpha = (pp > 0.0) ? st.rz[c] / pp : 0.0;
   const T a = (T)alpha;
   const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
-  double acc = 0.0;
+  double acc = 0.0, accz = 0.0;
   for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
     const size_t i = (size_t)c * npw + G;
     const cpx<T> pv = p[i], av = Ap[i];
@@ -307,17 +322,25 @@ k_cg_update(int npw, cpx<T>* __restrict__ x, cpx<T>* __restrict__ r, const cpx<T
     x[i] = xv;
     r[i] = rv;
     const double2 rd = to_d(rv);
-    acc += rd.x * rd.x + rd.y * rd.y;
+    const double n2 = rd.x * rd.x + rd.y * rd.y;
+    acc += n2;
+    accz += (double)precond<T>(kin, st.tk, c, G) * n2;
   }
   acc = block_sum(acc);
-  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ncol + c] = acc;
+  accz = block_sum(accz);
+  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ncol + c] = make_double2(acc, accz);
   if (!last_block(&st.cnt[c], gridDim.x)) return;
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < (int)gridDim.x; ++k) s += partial[(size_t)k * ncol + c];
+    double s = 0.0, z = 0.0;
+    for (int k = 0; k < (int)gridDim.x; ++k) {
+      const double2 pk = partial[(size_t)k * ncol + c];
+      s += pk.x;
+      z += pk.y;
+    }
     const int it = st.iters[c] + 1;
     st.iters[c] = it;
-    st.beta[c] = s / st.rr[c];
+    st.beta[c] = z / st.rz[c];
+    st.rz[c] = z;
     st.rr[c] = s;
     bool stop = false;
     st.rr_min[c] = fmin(st.rr_min[c], s);
@@ -331,18 +354,19 @@ k_cg_update(int npw, cpx<T>* __restrict__ x, cpx<T>* __restrict__ r, const cpx<T
 
 template <typename T, typename U>
 void launch_cg_init(cudaStream_t s, int npw, int ncol, const cpx<U>* b, cpx<T>* x, cpx<T>* r,
-                    const int* outer_active, Work& w, CgState st, double tol_in2, double tol_abs2) {
+                    const int* outer_active, Work& w, CgState st, const T* kin, double tol_in2, double tol_abs2) {
   dim3 g((npw + kChunk - 1) / kChunk, ncol);
   ++g_launches;
-  k_cg_init<T, U><<<g, kLT, 0, s>>>(npw, b, x, r, outer_active, w.part1, st.cnt, st, ncol, tol_in2, tol_abs2);
+  k_cg_init<T, U><<<g, kLT, 0, s>>>(npw, b, x, r, outer_active, w.part2, kin, st, ncol, tol_in2, tol_abs2);
 }
 
 template <typename T>
 void launch_cg_update(cudaStream_t s, int npw, int ncol, cpx<T>* x, cpx<T>* r, const cpx<T>* p,
-                      const cpx<T>* Ap, const double* pap, Work& w, CgState st, double tol2, int maxit) {
+                      const cpx<T>* Ap, const double* pap, Work& w, CgState st, const T* kin, double tol2,
+                      int maxit) {
   dim3 g((npw + kChunk - 1) / kChunk, ncol);
   ++g_launches;
-  k_cg_update<T><<<g, kLT, 0, s>>>(npw, x, r, p, Ap, pap, w.part1, st, tol2, maxit, ncol);
+  k_cg_update<T><<<g, kLT, 0, s>>>(npw, x, r, p, Ap, pap, w.part2, kin, st, tol2, maxit, ncol);
 }
 
 // ---------------------------------------------------------------------------
@@ -350,12 +374,14 @@ void launch_cg_update(cudaStream_t s, int npw, int ncol, cpx<T>* x, cpx<T>* r, c
 // with the bilinear form [x, y] = sum_r x(r) y(r) = sum_G x(-G) y(G)
 // (Sec. "Avoiding summations": SQMR replaces CG when (H - e_v -/+ w) is not
 // positive definite; unpreconditioned it equals MINRES for real symmetric A)
-//   init: r = q = b, x = d = 0, tau = |b|, rho = [b, b], theta = 0
+// with the symmetric kinetic preconditioner K applied on the right (K = 1
+// without one):
+//   init: r = b, q = K b, x = d = 0, tau = |b|, rho = [b, K b], theta = 0
 //   loop: t = A q; sigma = [q, t]; alpha = rho / sigma; r -= alpha t
 //         theta' = |r| / tau; c2 = 1 / (1 + theta'^2); tau = tau theta' sqrt(c2)
 //         d = c2 theta^2 d + c2 alpha q; x += d
-//         rho' = [r, r]; beta = rho' / rho; q = r + beta q
-//   stop when tau^2 (k + 1) <= rr_stop (bound on the QMR residual)
+//         rho' = [r, K r]; beta = rho' / rho; q = K r + beta q
+//   stop when tau^2 <= rr_stop (tau: the quasi-residual norm)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
   const double den = b.x * b.x + b.y * b.y;
@@ -366,8 +392,8 @@ template <typename T>
 __global__ void __launch_bounds__(kLT)
 k_qmr_init(int npw, const double2* __restrict__ b, cpx<T>* __restrict__ x, cpx<T>* __restrict__ r,
            cpx<T>* __restrict__ q, cpx<T>* __restrict__ d, const int* __restrict__ neg,
-           const int* __restrict__ outer_active, double* __restrict__ partial, QmrState st, int ncol,
-           double tol_in2) {
+           const int* __restrict__ outer_active, double* __restrict__ partial, const T* __restrict__ kin,
+           QmrState st, int ncol, double tol_in2) {
   const int c = blockIdx.y;
   const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
   const bool on = !outer_active || outer_active[c];
@@ -376,14 +402,15 @@ k_qmr_init(int npw, const double2* __restrict__ b, cpx<T>* __restrict__ x, cpx<T
     const size_t i = (size_t)c * npw + G;
     const cpx<T> bv = on ? from_d<T>(b[i]) : mk<T>(0, 0);
     const cpx<T> bn = on ? from_d<T>(b[(size_t)c * npw + neg[G]]) : mk<T>(0, 0);
+    const T k = precond<T>(kin, st.tk, c, G);
     r[i] = bv;
-    q[i] = bv;
+    q[i] = mk<T>(k * bv.x, k * bv.y);               // q = K b
     x[i] = mk<T>(0, 0);
     d[i] = mk<T>(0, 0);
     const double2 u = to_d(bv), w = to_d(bn);
     a1 += u.x * u.x + u.y * u.y;
-    ax += w.x * u.x - w.y * u.y;
-    ay += w.x * u.y + w.y * u.x;
+    ax += (double)k * (w.x * u.x - w.y * u.y);       // rho = [b, K b]
+    ay += (double)k * (w.x * u.y + w.y * u.x);
   }
   a1 = block_sum(a1);
   ax = block_sum(ax);
@@ -492,8 +519,8 @@ k_qmr_r(int npw, cpx<T>* __restrict__ r, const cpx<T>* __restrict__ t, double* _
 template <typename T>
 __global__ void __launch_bounds__(kLT)
 k_qmr_dx(int npw, cpx<T>* __restrict__ x, cpx<T>* __restrict__ d, const cpx<T>* __restrict__ q,
-         const cpx<T>* __restrict__ r, const int* __restrict__ neg, double* __restrict__ partial, QmrState st,
-         int ncol, int maxit) {
+         const cpx<T>* __restrict__ r, const int* __restrict__ neg, double* __restrict__ partial,
+         const T* __restrict__ kin, QmrState st, int ncol, int maxit) {
   const int c = blockIdx.y;
   if (!st.active[c]) return;
   const T dc = (T)st.dcoef[c];
@@ -512,8 +539,9 @@ k_qmr_dx(int npw, cpx<T>* __restrict__ x, cpx<T>* __restrict__ d, const cpx<T>* 
     xv.y += dv.y;
     x[i] = xv;
     const double2 a = to_d(r[(size_t)c * npw + neg[G]]), u = to_d(r[i]);
-    ax += a.x * u.x - a.y * u.y;
-    ay += a.x * u.y + a.y * u.x;
+    const double k = (double)precond<T>(kin, st.tk, c, G);
+    ax += k * (a.x * u.x - a.y * u.y);              // rho' = [r, K r]
+    ay += k * (a.x * u.y + a.y * u.x);
   }
   ax = block_sum(ax);
   ay = block_sum(ay);
@@ -558,34 +586,38 @@ k_qmr_dx(int npw, cpx<T>* __restrict__ x, cpx<T>* __restrict__ d, const cpx<T>* 
   }
 }
 
-// q = r + beta q
+// q = K r + beta q
 template <typename T>
-__global__ void k_qmr_q(int npw, cpx<T>* __restrict__ q, const cpx<T>* __restrict__ r, QmrState st) {
+__global__ void k_qmr_q(int npw, cpx<T>* __restrict__ q, const cpx<T>* __restrict__ r, const T* __restrict__ kin,
+                        QmrState st) {
   const int c = blockIdx.y;
   if (!st.active[c]) return;
   const cpx<T> b = from_d<T>(st.beta[c]);
   for (int G = blockIdx.x * blockDim.x + threadIdx.x; G < npw; G += gridDim.x * blockDim.x) {
     const size_t i = (size_t)c * npw + G;
+    const T k = precond<T>(kin, st.tk, c, G);
     const cpx<T> qv = q[i], rv = r[i];
-    q[i] = mk<T>(rv.x + b.x * qv.x - b.y * qv.y, rv.y + b.x * qv.y + b.y * qv.x);
+    q[i] = mk<T>(k * rv.x + b.x * qv.x - b.y * qv.y, k * rv.y + b.x * qv.y + b.y * qv.x);
   }
 }
 
 template <typename T>
 void launch_qmr(cudaStream_t s, int step, int npw, int ncol, const double2* b, cpx<T>* x, cpx<T>* r, cpx<T>* q,
                 cpx<T>* d, const cpx<T>* t, const int* neg, const int* outer_active, Work& w, QmrState st,
-                double tol_in2, int maxit) {
+                const T* kin, double tol_in2, int maxit) {
   dim3 g((npw + kChunk - 1) / kChunk, ncol);
   double* part = reinterpret_cast<double*>(w.part2);
   ++g_launches;
   switch (step) {
-    case 0: k_qmr_init<T><<<g, kLT, 0, s>>>(npw, b, x, r, q, d, neg, outer_active, part, st, ncol, tol_in2); break;
+    case 0:
+      k_qmr_init<T><<<g, kLT, 0, s>>>(npw, b, x, r, q, d, neg, outer_active, part, kin, st, ncol, tol_in2);
+      break;
     case 1: k_qmr_sigma<T><<<g, kLT, 0, s>>>(npw, q, t, neg, part, st, ncol); break;
     case 2: k_qmr_r<T><<<g, kLT, 0, s>>>(npw, r, t, part, st, ncol); break;
-    case 3: k_qmr_dx<T><<<g, kLT, 0, s>>>(npw, x, d, q, r, neg, part, st, ncol, maxit); break;
+    case 3: k_qmr_dx<T><<<g, kLT, 0, s>>>(npw, x, d, q, r, neg, part, kin, st, ncol, maxit); break;
     default: {
       dim3 g2((npw + kLT - 1) / kLT, ncol);
-      k_qmr_q<T><<<g2, kLT, 0, s>>>(npw, q, r, st);
+      k_qmr_q<T><<<g2, kLT, 0, s>>>(npw, q, r, kin, st);
     }
   }
 }
@@ -841,16 +873,17 @@ void launch_tridiag_inv(cudaStream_t s, int K, const double* alpha, const double
 
 #define GW_LINST(T)                                                                                        \
   template void launch_qmr<T>(cudaStream_t, int, int, int, const double2*, cpx<T>*, cpx<T>*, cpx<T>*,       \
-                              cpx<T>*, const cpx<T>*, const int*, const int*, Work&, QmrState, double, int); \
+                              cpx<T>*, const cpx<T>*, const int*, const int*, Work&, QmrState, const T*, double,   \
+                              int);                                                                        \
   template void launch_gram<T>(cudaStream_t, const cpx<T>*, int, int, const cpx<T>*, int, Work&, double2*); \
   template void launch_proj_update<T>(cudaStream_t, const cpx<T>*, int, int, cpx<T>*, int, const int*,     \
                                       const double2*, Work&, const cpx<T>*, double*);                      \
   template void launch_proj<T>(cudaStream_t, const cpx<T>*, int, int, cpx<T>*, int, const int*, Work&,     \
                                const cpx<T>*, double*);                                                    \
   template void launch_cg_init<T, double>(cudaStream_t, int, int, const double2*, cpx<T>*, cpx<T>*,       \
-                                          const int*, Work&, CgState, double, double);                     \
+                                          const int*, Work&, CgState, const T*, double, double);           \
   template void launch_cg_update<T>(cudaStream_t, int, int, cpx<T>*, cpx<T>*, const cpx<T>*,              \
-                                    const cpx<T>*, const double*, Work&, CgState, double, int);           \
+                                    const cpx<T>*, const double*, Work&, CgState, const T*, double, int); \
   template void launch_add_conv<T>(cudaStream_t, int, int, const cpx<T>*, double2*, const int*);
 
 GW_LINST(double)

@@ -30,6 +30,8 @@ struct CgState {
   double* rr_stop = nullptr;  // stop when |r|^2 <= rr_stop
   double* rr_min = nullptr;   // smallest |r|^2 seen (divergence guard)
   const double* rr_abs = nullptr;   // per-column absolute |r|^2 target of the refinement
+  double* rz = nullptr;     // current r^H K r (K = kinetic preconditioner; = rr without one)
+  const double* tk = nullptr;       // per-column T_ref of the preconditioner, or null (none)
   int* n_done = nullptr;    // columns that stopped (atomic)
   unsigned* cnt = nullptr;  // tickets [ncol]
 };
@@ -45,6 +47,7 @@ struct QmrState {
   double* tau = nullptr;
   double* rr_stop = nullptr;
   const double* rr_abs = nullptr;
+  const double* tk = nullptr;   // per-column T_ref of the preconditioner, or null (none)
   double* qbest = nullptr;   // smallest tau^2 so far (to within a factor 4)
   int* itbest = nullptr;     // iteration at which qbest was last lowered
   int* iters = nullptr;
@@ -61,7 +64,7 @@ void launch_proj(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, 
 template <typename T>
 void launch_qmr(cudaStream_t s, int step, int npw, int ncol, const double2* b, cpx<T>* x, cpx<T>* r, cpx<T>* q,
                 cpx<T>* d, const cpx<T>* t, const int* neg, const int* outer_active, Work& w, QmrState st,
-                double tol_in2, int maxit);
+                const T* kin, double tol_in2, int maxit);
 template <typename T>
 void launch_proj_update(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, int ncol,
                         const int* active, const double2* coef, Work& w, const cpx<T>* Pv, double* pap);
@@ -74,10 +77,11 @@ void launch_g1(cudaStream_t s, const double2* dU, const double2* U, const double
 void launch_grad_combine(cudaStream_t s, int n, const double* g1, const double* g2, double wgt, double* grad);
 template <typename T, typename U>
 void launch_cg_init(cudaStream_t s, int npw, int ncol, const cpx<U>* b, cpx<T>* x, cpx<T>* r,
-                    const int* outer_active, Work& w, CgState st, double tol_in2, double tol_abs2);
+                    const int* outer_active, Work& w, CgState st, const T* kin, double tol_in2, double tol_abs2);
 template <typename T>
 void launch_cg_update(cudaStream_t s, int npw, int ncol, cpx<T>* x, cpx<T>* r, const cpx<T>* p,
-                      const cpx<T>* Ap, const double* pap, Work& w, CgState st, double tol2, int maxit);
+                      const cpx<T>* Ap, const double* pap, Work& w, CgState st, const T* kin, double tol2,
+                      int maxit);
 template <typename T>
 void launch_add_conv(cudaStream_t s, int npw, int ncol, const cpx<T>* d, double2* x, const int* active);
 void launch_residual(cudaStream_t s, int npw, int ncol, const double2* b, double2* ax, const double2* x,
@@ -112,8 +116,9 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
                                  int npw, int ncol, const double2* b64, const int* outer_active, const double2* E,
                                  const double* rr_abs, double tol_in2, int maxit, cpx<T>* x, cpx<T>* r, cpx<T>* p,
                                  cpx<T>* Ap, cpx<T>* grid, double2* dpart, double* ppart, double* rpart,
-                                 unsigned* bar, int* err, int* iters, int* flags, double* rr_out, int* grid_used,
-                                 unsigned long long* ptime = nullptr, int cta_div = 1);
+                                 double* zpart, const double* tk, unsigned* bar, int* err, int* iters, int* flags,
+                                 double* rr_out, int* grid_used, unsigned long long* ptime = nullptr,
+                                 int cta_div = 1);
 constexpr int kPersistentMaxCols = 256;
 
 }  // namespace gw

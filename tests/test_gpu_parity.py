@@ -250,3 +250,28 @@ def test_block_lanczos(tiny, blk, omega):
     Am, Bm, _ = c.block_lanczos(X0, K, omega, gw.GW_MIXED)
     assert rel(Am, A_ref) < 1e-6 and rel(Bm, B_ref) < 1e-6
     c.close()
+
+
+@pytest.mark.parametrize("omega", [0.0, 0.9, 0.3 + 0.1j])
+def test_preconditioner_same_solution(tiny, omega):
+    """The kinetic preconditioner changes the iteration count, not the answer:
+    both settings match the sum over states; the preconditioned solves take
+    fewer iterations."""
+    wl, cell, sph, gs = tiny
+    f = W.random_fields(107, 2, sph.ng)
+    c = make(cell, gs)
+    outs, its = [], []
+    for kind in (0, 1):
+        c.set_precond(kind)
+        outs.append(c.apply_chi0(f, [omega], gw.GW_FP64)[0])
+        its.append(c.stats()["mean_iter"])
+    for b in range(2):
+        ref = response.chi0_sos(gs, f[b], omega)
+        if np.imag(omega) == 0:
+            ref = ref.real
+        assert rel(outs[0][b], ref) < 1e-10
+        assert rel(outs[1][b], ref) < 1e-10
+    assert its[1] < its[0]
+    with pytest.raises(gw.GwError):
+        c.set_precond(2)
+    c.close()
