@@ -236,7 +236,9 @@ gw_status gw_grad_vloc(gw_ctx* ctx, const double* phi, int k, double* s, double*
  *   out[6] CUDA kernels launched by the library since it was loaded,
  *   out[7] iterations run by persistent CG launches (each launch counts the
  *          iterations of its slowest column)
- *   n: entries wanted (<= 8)
+ *   out[8] CTAs of the last persistent CG launch, out[9] its cluster size
+ *          (0: the grid-wide cooperative kernel)
+ *   n: entries wanted (<= 10)
  */
 gw_status gw_stats(const gw_ctx* ctx, double* out, int n);
 
@@ -248,7 +250,7 @@ gw_status gw_stats(const gw_ctx* ctx, double* out, int n);
  *              that does not halve the error ends the refinement when the error
  *              is already within 10 tol (round-off and input-accuracy floor)
  *   tol_inner  relative residual at which each FP32 inner CG pass of the mixed
- *              path stops before the next FP64 residual (default 1e-4)
+ *              path stops before the next FP64 residual (default 1e-5)
  *   max_iter   inner CG iterations per pass;  max_outer  FP64 residual passes
  * The paper solves Eq. P2 until |A x - b|^2 < 1e-20 Ha^2 (Sec. Results).
  */

@@ -255,10 +255,11 @@ def gw_grad_vloc(ctx, phi, k, s, grad, prec=GW_FP64):
 
 
 def gw_stats(ctx):
-    out = np.zeros(8)
-    _check(ctx, load().gw_stats(ctx, out.ctypes.data, 8))
+    out = np.zeros(10)
+    _check(ctx, load().gw_stats(ctx, out.ctypes.data, 10))
     return dict(columns=out[0], max_iter=out[1], mean_iter=out[2], outer=out[3], max_residual=out[4],
-                h_columns=out[5], launches=int(out[6]), launch_iterations=int(out[7]))
+                h_columns=out[5], launches=int(out[6]), launch_iterations=int(out[7]), launch_ctas=int(out[8]),
+                cluster=int(out[9]))
 
 
 def gw_set_solver(ctx, tol=0.0, tol_inner=0.0, max_iter=0, max_outer=0):

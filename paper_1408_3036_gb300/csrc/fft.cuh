@@ -61,71 +61,32 @@ __device__ __forceinline__ void butterfly(cpx<T>* a, int r) {
   }
 }
 
-// npen pencils of length pl.N at buf[p * ld + k]; tw[k] = exp(-2 pi i k / N).
-// Returns the buffer holding the result (a or b).  Ends with __syncthreads().
-template <typename T, int SIGN>
-__device__ cpx<T>* fft_tile(cpx<T>* a, cpx<T>* b, int npen, int ld, const FftPlan& pl,
-                            const cpx<T>* tw) {
-  using V = cpx<T>;
-  const int N = pl.N;
-  int Ns = 1;
-  for (int s = 0; s < pl.nst; ++s) {
-    const int r = pl.rad[s];
-    const int nb = N / r;
-    const int tstep = N / (Ns * r);
-    const int total = npen * nb;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int p = t / nb;
-      const int j = t - p * nb;
-      const int k = j % Ns;
-      const V* src = a + p * ld;
-      V* dst = b + p * ld;
-      V v[5];
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        if (q < r) {
-          V x = src[j + q * nb];
-          if (q > 0 && k > 0) {
-            V w = tw[k * q * tstep];
-            if (SIGN > 0) w.y = -w.y;
-            x = cmul(x, w);
-          }
-          v[q] = x;
-        }
-      }
-      butterfly<T, SIGN>(v, r);
-      const int base = (j / Ns) * Ns * r + k;
-#pragma unroll
-      for (int q = 0; q < 5; ++q)
-        if (q < r) dst[base + q * Ns] = v[q];
-    }
-    __syncthreads();
-    V* t = a; a = b; b = t;
-    Ns *= r;
-  }
-  return a;
-}
-
 // Generalised tile FFT: npen pencils, pencil p element k at buf[p * ps + k * es].
 // PFAST selects the thread mapping: consecutive threads take consecutive
 // pencils (PFAST, for pencils adjacent in memory: es > 1, ps = 1) or
-// consecutive butterflies of one pencil (contiguous pencils: es = 1).
+// consecutive butterflies of one pencil (contiguous pencils: es = 1).  The
+// index divisions use the plan's precomputed multiply-shift divisors.
+// Returns the buffer holding the result (a or b).  Ends with __syncthreads().
 template <typename T, int SIGN, bool PFAST>
 __device__ cpx<T>* fft_tile2(cpx<T>* a, cpx<T>* b, int npen, int ps, int es, const FftPlan& pl,
                              const cpx<T>* tw) {
   using V = cpx<T>;
   const int N = pl.N;
-  int Ns = 1;
+  FastDiv dpen = pl.dN;
+  if (PFAST && npen != N) dpen.set((unsigned)npen);
   for (int s = 0; s < pl.nst; ++s) {
     const int r = pl.rad[s];
-    const int nb = N / r;
-    const int tstep = N / (Ns * r);
+    const int nb = pl.nb[s];
+    const int Ns = pl.ns[s];
+    const int tstep = pl.dns[s].div(nb);          // N / (Ns r)
+    const FastDiv dnb = pl.dnb[s], dns = pl.dns[s];
     const int total = npen * nb;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
       int p, j;
-      if (PFAST) { j = t / npen; p = t - j * npen; }
-      else { p = t / nb; j = t - p * nb; }
-      const int k = j % Ns;
+      if (PFAST) { j = dpen.div(t); p = t - j * npen; }
+      else { p = dnb.div(t); j = t - p * nb; }
+      const int jq = dns.div(j);
+      const int k = j - jq * Ns;
       const V* src = a + p * ps;
       V* dst = b + p * ps;
       V v[5];
@@ -142,16 +103,21 @@ __device__ cpx<T>* fft_tile2(cpx<T>* a, cpx<T>* b, int npen, int ps, int es, con
         }
       }
       butterfly<T, SIGN>(v, r);
-      const int base = (j / Ns) * Ns * r + k;
+      const int base = jq * Ns * r + k;
 #pragma unroll
       for (int q = 0; q < 5; ++q)
         if (q < r) dst[(base + q * Ns) * es] = v[q];
     }
     __syncthreads();
-    V* t = a; a = b; b = t;
-    Ns *= r;
+    V* tmp = a; a = b; b = tmp;
   }
   return a;
+}
+
+// npen contiguous pencils of length pl.N at buf[p * ld + k]; tw[k] = exp(-2 pi i k / N).
+template <typename T, int SIGN>
+__device__ cpx<T>* fft_tile(cpx<T>* a, cpx<T>* b, int npen, int ld, const FftPlan& pl, const cpx<T>* tw) {
+  return fft_tile2<T, SIGN, false>(a, b, npen, ld, 1, pl, tw);
 }
 
 }  // namespace gw

@@ -36,11 +36,13 @@ struct gw_ctx {
   std::map<std::string, std::pair<void*, size_t>> bufs;
   Work work;
   size_t work_cols = 0;
-  double tol = 1e-13, tol_mixed = 1e-12, tol_inner = 1e-4;   // backward errors (FP64 / mixed), inner
+  double tol = 1e-13, tol_mixed = 1e-12, tol_inner = 1e-5;   // backward errors (FP64 / mixed), inner
   double anorm = 1.0;           // bound on |H - E| used by the backward error
   bool no_persistent = false;   // force the multi-launch CG (tests)
+  bool use_cluster = false;     // one thread-block cluster per column instead of the grid-wide kernel
   long long pcg_iters = 0;      // iterations run by persistent launches
   int pcg_launch_blocks = 0;
+  int pcg_cluster = 0;          // cluster size of the last persistent launch (0: grid-wide kernel)
   int cta_div = 1;              // contexts sharing the GPU concurrently (batch mode)
   int precond = 1;              // 1: kinetic (TPA) preconditioner in the Sternheimer solvers; 0: none
   std::vector<double> tkin;     // kinetic energy of each occupied state (preconditioner reference)
@@ -259,6 +261,8 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
   TRY(getbuf(ctx, "cg_rrstop", ncol, &st.rr_stop));
   TRY(getbuf(ctx, "cg_rrmin", ncol, &st.rr_min));
   TRY(getbuf(ctx, "cg_rz", ncol, &st.rz));
+  TRY(getbuf(ctx, "cg_rrbest", ncol, &st.rr_best));
+  TRY(getbuf(ctx, "cg_itbest", ncol, &st.it_best));
   st.rr_abs = rr_abs;
   st.tk = tk;
   TRY(ensure_work(ctx, ncol));
@@ -331,7 +335,7 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
                               int* it_max) {
   const int npw = ctx->npw;
   const std::string t = tname<T>();
-  const int nchunk = (npw + 1023) / 1024;
+  const int nchunk = (npw + kPcgChunk - 1) / kPcgChunk;
   cpx<T>*r, *p, *Ap, *grid;
   TRY(getbuf(ctx, "cg_r" + t, (size_t)ncol * npw, &r));
   TRY(getbuf(ctx, "cg_p" + t, (size_t)ncol * npw, &p));
@@ -341,7 +345,7 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
   double *ppart, *rpart, *zpart, *rr_out;
   unsigned* bar;
   int *err, *iters, *flags;
-  TRY(getbuf(ctx, "pcg_dpart", (size_t)ncol * ctx->geo.nplanes * ctx->nocc, &dpart));
+  TRY(getbuf(ctx, "pcg_dpart", (size_t)ncol * ctx->geo.nplanes * (2 * ctx->nocc + 1), &dpart));
   TRY(getbuf(ctx, "pcg_ppart", (size_t)ncol * nchunk, &ppart));
   TRY(getbuf(ctx, "pcg_rpart", (size_t)ncol * nchunk, &rpart));
   TRY(getbuf(ctx, "pcg_zpart", (size_t)ncol * nchunk, &zpart));
@@ -356,21 +360,40 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
   const int pa = prof_begin(ctx, PC_PCG);
   unsigned long long* ptime = nullptr;
   if (std::getenv("GW_DEBUG_PHASES")) {
-    TRY(getbuf(ctx, "pcg_ptime", 8, &ptime));
+    TRY(getbuf(ctx, "pcg_ptime", 16, &ptime));
     if (!ctx->ptime_init) {
-      CK(cudaMemsetAsync(ptime, 0, 8 * sizeof(unsigned long long), ctx->st));
+      CK(cudaMemsetAsync(ptime, 0, 16 * sizeof(unsigned long long), ctx->st));
       ctx->ptime_init = true;
     }
   }
-  CK(launch_cg_persistent<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), ctx->nocc, npw, ncol, b64, outer_active,
-                             E, rr_abs, tol * tol, ctx->max_iter, x, r, p, Ap, grid, dpart, ppart, rpart, zpart, tk, bar, err,
-                             iters, flags, rr_out, &used, ptime, ctx->cta_div));
+  // the cooperative grid-wide kernel, or (opt-in) one thread-block cluster per
+  // column when the column's planes fit in the cluster's shared memory
+  cudaError_t le = cudaErrorNotSupported;
+  if (ctx->use_cluster) {
+    int q = 0;
+    le = launch_cg_cluster<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), ctx->nocc, npw, ncol, b64, outer_active,
+                              E, rr_abs, tk, tol * tol, ctx->max_iter, x, r, p, Ap, iters, flags, rr_out, &q, ptime);
+    used = ncol * q;
+    ctx->pcg_cluster = q;
+  }
+  if (le == cudaErrorNotSupported) {
+    cudaGetLastError();
+    ctx->pcg_cluster = 0;
+    CK(launch_cg_persistent<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), ctx->nocc, npw, ncol, b64,
+                               outer_active, E, rr_abs, tol * tol, ctx->max_iter, x, r, p, Ap, grid, dpart, ppart,
+                               rpart, zpart, tk, bar, err, iters, flags, rr_out, &used, ptime, ctx->cta_div));
+  } else {
+    CK(le);
+  }
   if (ptime) {
-    unsigned long long h[8];
+    unsigned long long h[16];
     CK(cudaMemcpyAsync(h, ptime, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
     TRY(sync(ctx, "ptime"));
-    std::fprintf(stderr, "phases(ms) A %.2f B %.2f C %.2f D %.2f E %.2f conv %.2f  blocks %d\n", h[0] * 1e-6,
-                 h[1] * 1e-6, h[2] * 1e-6, h[3] * 1e-6, h[4] * 1e-6, h[5] * 1e-6, used);
+    const double w = 1e-6 / std::max(used, 1);   // mean work per CTA
+    std::fprintf(stderr,
+                 "phases(ms) A %.2f B %.2f C %.2f D %.2f E %.2f conv %.2f  blocks %d  work A %.2f B %.2f C %.2f "
+                 "E %.2f\n", h[0] * 1e-6, h[1] * 1e-6, h[2] * 1e-6, h[3] * 1e-6, h[4] * 1e-6, h[5] * 1e-6, used,
+                 h[8] * w, h[9] * w, h[10] * w, h[12] * w);
   }
   prof_end(ctx, PC_PCG, pa);
   std::vector<int> its(ncol), fl(ncol);
@@ -1333,6 +1356,7 @@ gw_status gw_setup(gw_ctx** out, double L, int n_grid, double ecut, const double
   if (cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming) != cudaSuccess) return bail(GW_E_CUDA);
   if (cudaMallocHost(&ctx->host_pin, 64) != cudaSuccess) return bail(GW_E_CUDA);
   if (const char* e = std::getenv("GW_MULTI_LAUNCH_CG")) ctx->no_persistent = (e[0] == '1');
+  if (const char* e = std::getenv("GW_CLUSTER_CG")) ctx->use_cluster = (e[0] == '1');
   if (fft_set_smem_limits<double>() != cudaSuccess || fft_set_smem_limits<float>() != cudaSuccess)
     return bail(GW_E_CUDA);
   gw_status s = build_geometry(ctx);
@@ -1770,6 +1794,8 @@ gw_status gw_stats(const gw_ctx* ctx, double* out, int n) {
   for (int i = 0; i < n && i < 6; ++i) out[i] = ctx->stats[i];
   if (n > 6) out[6] = (double)g_launches.load();
   if (n > 7) out[7] = (double)ctx->pcg_iters;
+  if (n > 8) out[8] = (double)ctx->pcg_launch_blocks;
+  if (n > 9) out[9] = (double)ctx->pcg_cluster;
   return GW_OK;
 }
 
@@ -1841,7 +1867,17 @@ bool make_plan(int N, FftPlan* p) {
       m /= r;
     }
   }
-  return m == 1;
+  if (m != 1) return false;
+  p->dN.set(N);
+  int span = 1;
+  for (int s = 0; s < p->nst; ++s) {
+    p->nb[s] = N / p->rad[s];
+    p->ns[s] = span;
+    p->dnb[s].set(p->nb[s]);
+    p->dns[s].set(span);
+    span *= p->rad[s];
+  }
+  return true;
 }
 }  // namespace gw
 

@@ -47,12 +47,34 @@ template <> __host__ __device__ __forceinline__ float2 from_d<float>(double2 a) 
 // ---------------------------------------------------------------------------
 // FFT plan: radices of a length-N transform (Stockham, mixed radix 4/2/3/5)
 // ---------------------------------------------------------------------------
+// Division by a runtime divisor 1 <= d < 2^31 as multiply-high, add and
+// shift (Granlund and Montgomery, PLDI 1994): with s = ceil(log2 d) and
+// m = floor(2^32 (2^s - d) / d) + 1, q = (umulhi(x, m) + x) >> s = floor(x / d)
+// for 0 <= x < 2^31.  Set on the host (the 64-bit division is slow on the GPU).
+struct FastDiv {
+  unsigned m = 1, s = 0;
+  __host__ __device__ void set(unsigned d) {
+    s = 0;
+    while ((1ull << s) < d) ++s;
+    m = (unsigned)(((1ull << 32) * ((1ull << s) - d)) / d + 1);
+  }
+  __host__ __device__ __forceinline__ int div(int x) const {
+    const unsigned long long hi = ((unsigned long long)(unsigned)x * m) >> 32;
+    return (int)((hi + (unsigned)x) >> s);
+  }
+};
+
 constexpr int kMaxStages = 10;
 constexpr int kMaxN = 128;
 struct FftPlan {
   int N;
   int nst;
   int rad[kMaxStages];
+  int nb[kMaxStages];       // N / rad: butterflies per pencil of each stage
+  int ns[kMaxStages];       // span Ns (product of the earlier radices)
+  FastDiv dN;               // division by N
+  FastDiv dnb[kMaxStages];  // by nb[s]
+  FastDiv dns[kMaxStages];  // by ns[s]
 };
 bool make_plan(int N, FftPlan* p);
 

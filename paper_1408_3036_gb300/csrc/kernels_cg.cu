@@ -4,7 +4,7 @@
 //
 // One cooperative launch runs a whole CG pass for every column (occupied
 // state x field x frequency) with per-column convergence masks.  The CTAs are
-// all resident and step through five phases per iteration, separated by a
+// all resident and step through four phases per iteration, separated by a
 // grid barrier (bounded spin: a barrier that waits too long sets an error flag
 // and every CTA returns):
 //   A  per (column, plane i0): p = K r + beta p on the plane's sphere entries
@@ -13,11 +13,12 @@
 //      memory), store the plane
 //   B  per (column, i1, 16 i2): x-IFFT, * V(r)/N_g, x-FFT (planes of the sphere)
 //   C  per (column, plane): y-FFT, z-FFT of the disc rows, gather the sphere
-//      entries, Ap = (Vp)_G + (|G|^2/2 - E) p_G, partial <C_v|Ap> of the plane
-//   D  per (column, 1024 entries): coef = sum of the plane partials,
-//      Ap -= C coef (P_c), partial p^H Ap
-//   E  per (column, 1024 entries): alpha = r^H K r / p^H Ap, x += alpha p,
-//      r -= alpha Ap, partials |r|^2 and r^H K r
+//      entries, Ap = (Vp)_G + (|G|^2/2 - E) p_G, the plane's partial sums
+//      <C_v|Ap>, <C_v|p> and p^H Ap
+//   E  per (column, 1024 entries): coef = sum of the plane partials,
+//      p^H P_c A p = p^H A p - sum_v conj(<C_v|p>) coef_v, alpha = r^H K r /
+//      p^H P_c A p, x += alpha p, r -= alpha (Ap - C coef) (P_c on the fly),
+//      partials |r|^2 and r^H K r
 // After E every CTA sums the partials of every column in the same order, so
 // all CTAs take the same convergence decisions without another barrier.
 #include <algorithm>
@@ -28,12 +29,12 @@
 #include "fft.cuh"
 #include "gw_common.cuh"
 #include "linalg.cuh"
+#include "pcg.cuh"
 
 namespace gw {
 
 constexpr int kPT = 256;        // threads per CTA
-constexpr int kPChunk = 1024;   // sphere entries per task in phases D and E
-constexpr int kPX = 16;         // i2 width of a phase-B tile
+constexpr int kPChunk = kPcgChunk;   // sphere entries per task in phases 0 and E
 constexpr unsigned kSpinLimit = 1u << 24;
 
 template <typename T>
@@ -56,8 +57,8 @@ struct PcgArgs {
   cpx<T>* p;
   cpx<T>* Ap;
   cpx<T>* grid;
-  double2* dpart;   // [ncol][nplanes][nocc]
-  double* ppart;    // [ncol][nchunk]
+  double2* dpart;   // [ncol][nplanes][2 nocc + 1] plane partial sums
+  double* ppart;    // [ncol][nchunk]: entry 0 of a column holds p^H P_c A p
   double* rpart;    // [ncol][nchunk]
   double* zpart;    // [ncol][nchunk] partial r^H K r
   const double* tk; // per-column T_ref of the kinetic preconditioner, or null (none)
@@ -66,14 +67,8 @@ struct PcgArgs {
   int* iters_out;
   int* flag_out;
   double* rr_out;
-  unsigned long long* ptime;   // optional [8]: ns spent per phase, measured by CTA 0
+  unsigned long long* ptime;   // optional [16] phase timing (see the kernel)
 };
-
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
 
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned nblk) {
   __shared__ int ok;
@@ -98,15 +93,27 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned n
 
 template <typename T>
 __device__ __forceinline__ double dsum_block(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (threadIdx.x == 0)
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
-  return r;   // thread 0
+  return dsum_block_f(v, sh);
+}
+
+// Copies n elements (e = 0..n-1, strided over the block) with U loads in
+// flight per thread: every load of a round is issued before the first store.
+constexpr int kLd = 4;
+template <int U, typename X, typename Ld, typename St>
+__device__ __forceinline__ void staged_copy(int n, Ld ld, St st) {
+  for (int e0 = threadIdx.x; e0 < n; e0 += U * (int)blockDim.x) {
+    X t[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      if (e < n) t[u] = ld(e);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      if (e < n) st(e, t[u]);
+    }
+  }
 }
 
 struct PcgLayout {
@@ -118,10 +125,10 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 __host__ __device__ inline PcgLayout pcg_layout(int N, int ncol, int nocc, int vsize) {
   PcgLayout L;
   L.dbl = 0;
-  L.ints = align16(L.dbl + (size_t)5 * ncol * sizeof(double));
-  L.red = align16(L.ints + (size_t)(3 * ncol + N) * sizeof(int));
+  L.ints = align16(L.dbl + (size_t)6 * ncol * sizeof(double));
+  L.red = align16(L.ints + (size_t)(4 * ncol + N) * sizeof(int));
   L.coef = align16(L.red + 32 * sizeof(double));
-  L.tw = align16(L.coef + (size_t)nocc * 2 * sizeof(double));
+  L.tw = align16(L.coef + (size_t)(2 * nocc + 1) * 2 * sizeof(double));
   L.A = align16(L.tw + (size_t)N * vsize);
   L.B = align16(L.A + (size_t)N * (N + 1) * vsize);
   L.total = align16(L.B + (size_t)N * (N + 1) * vsize);
@@ -129,7 +136,7 @@ __host__ __device__ inline PcgLayout pcg_layout(int N, int ncol, int nocc, int v
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
+__global__ void __launch_bounds__(kPT, sizeof(T) == 4 ? 2 : 1) k_cg_persistent(PcgArgs<T> a) {
   using V = cpx<T>;
   extern __shared__ unsigned char smem_raw[];
   const Geometry& g = a.g;
@@ -142,12 +149,14 @@ __global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
   double* st_stop = st_min + ncol;
   double* st_beta = st_stop + ncol;
   double* st_rz = st_beta + ncol;                             // r^H K r
+  double* st_best = st_rz + ncol;                             // stagnation guard
   int* st_act = reinterpret_cast<int*>(smem_raw + L.ints);
   int* st_it = st_act + ncol;
   int* st_flag = st_it + ncol;
-  int* rowmap = st_flag + ncol;                               // [N]
+  int* st_itb = st_flag + ncol;
+  int* rowmap = st_itb + ncol;                                // [N]
   double* red = reinterpret_cast<double*>(smem_raw + L.red);  // [32] block sums
-  double2* coef = reinterpret_cast<double2*>(smem_raw + L.coef);  // [nocc]
+  double2* coef = reinterpret_cast<double2*>(smem_raw + L.coef);  // [2 nocc + 1] plane sums
   V* stw = reinterpret_cast<V*>(smem_raw + L.tw);             // [N]
   V* A = reinterpret_cast<V*>(smem_raw + L.A);                // [N][LDp]
   V* B = reinterpret_cast<V*>(smem_raw + L.B);                // [N][LDp]
@@ -190,6 +199,8 @@ __global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
     st_rr[c] = s;
     st_rz[c] = z;
     st_min[c] = s;
+    st_best[c] = s;
+    st_itb[c] = 0;
     st_stop[c] = fmax(a.tol_in2 * s, a.rr_abs ? a.rr_abs[c] : 0.0);
     st_beta[c] = -1.0;
     st_act[c] = (on && s > 0.0) ? 1 : 0;
@@ -198,12 +209,18 @@ __global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
   }
   __syncthreads();
 
-  unsigned long long tprev = gtimer();
+  unsigned long long tprev = gtimer(), tphase = tprev;
+  // Optional timing (a.ptime): [ph] wall time of phase ph seen by CTA 0,
+  // [8 + ph] work time of phase ph summed over CTAs (before its barrier).
+  auto work = [&](int ph) {
+    if (a.ptime && threadIdx.x == 0) atomicAdd(&a.ptime[8 + ph], gtimer() - tphase);
+  };
   auto mark = [&](int ph) {
-    if (a.ptime && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (a.ptime && threadIdx.x == 0) {
       const unsigned long long t = gtimer();
-      a.ptime[ph] += t - tprev;
+      if (blockIdx.x == 0) a.ptime[ph] += t - tprev;
       tprev = t;
+      tphase = t;
     }
   };
   for (int it = 0; it < a.maxit; ++it) {
@@ -244,7 +261,7 @@ __global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
       V* R = fft_tile2<T, +1, false>(A, B, npp, LDp, 1, a.pl, stw);
       V* Q = (R == A) ? B : A;
       for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const int i1 = e / N, i2 = e - i1 * N;
+        const int i1 = a.pl.dN.div(e), i2 = e - i1 * N;
         const int k = rowmap[i1];
         Q[i1 * LDp + i2] = (k >= 0) ? R[k * LDp + i2] : mk<T>(0, 0);
       }
@@ -252,11 +269,12 @@ __global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
       V* S = fft_tile2<T, +1, true>(Q, R, N, 1, LDp, a.pl, stw);
       const size_t base = (size_t)c * g.N3 + (size_t)i0 * g.N2;
       for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const int i1 = e / N, i2 = e - i1 * N;
+        const int i1 = a.pl.dN.div(e), i2 = e - i1 * N;
         a.grid[base + e] = S[i1 * LDp + i2];
       }
       __syncthreads();
     }
+    work(0);
     if (!grid_barrier(a.bar, a.err, nblk)) return;
     mark(0);
 
@@ -267,15 +285,17 @@ __global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
       const int c = task / N, i1 = task - c * N;
       if (!st_act[c]) continue;
       const size_t base = (size_t)c * g.N3 + (size_t)i1 * N;
+#pragma unroll 4
       for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const int i0 = e / N, i2 = e - i0 * N;
+        const int i0 = a.pl.dN.div(e), i2 = e - i0 * N;
         A[i0 * LDp + i2] = g.plane_mask[i0] ? a.grid[base + (size_t)i0 * g.N2 + i2] : mk<T>(0, 0);
       }
       __syncthreads();
       V* R = fft_tile2<T, +1, true>(A, B, N, 1, LDp, a.pl, stw);
       V* Q = (R == A) ? B : A;
+#pragma unroll 4
       for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const int i0 = e / N, i2 = e - i0 * N;
+        const int i0 = a.pl.dN.div(e), i2 = e - i0 * N;
         const T m = a.vloc_s[(size_t)i0 * g.N2 + (size_t)i1 * N + i2];
         const V v = R[i0 * LDp + i2];
         R[i0 * LDp + i2] = mk<T>(v.x * m, v.y * m);
@@ -283,15 +303,18 @@ __global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
       __syncthreads();
       V* S = fft_tile2<T, -1, true>(R, Q, N, 1, LDp, a.pl, stw);
       for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const int i0 = e / N, i2 = e - i0 * N;
+        const int i0 = a.pl.dN.div(e), i2 = e - i0 * N;
         if (g.plane_mask[i0]) a.grid[base + (size_t)i0 * g.N2 + i2] = S[i0 * LDp + i2];
       }
       __syncthreads();
     }
+    work(1);
     if (!grid_barrier(a.bar, a.err, nblk)) return;
     mark(1);
 
-    // ---- phase C: y-FFT, z-FFT of the disc rows, gather + kinetic + shift, partial dots
+    // ---- phase C: y-FFT, z-FFT of the disc rows, gather + kinetic + shift, and
+    // the plane's partial sums <C_v|Ap>, <C_v|p> and p^H Ap (Ap before P_c)
+    const int ndp = 2 * a.nocc + 1;
     for (int task = blockIdx.x; task < ncol * npl; task += gridDim.x) {
       const int c = task / npl, pi = task - c * npl;
       if (!st_act[c]) continue;
@@ -300,90 +323,102 @@ __global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
       const int q0 = g.plane_pen[pi], npp = g.plane_pen[pi + 1] - q0;
       const size_t sc = (size_t)c * a.npw;
       const size_t base = (size_t)c * g.N3 + (size_t)i0 * g.N2;
+#pragma unroll 4
       for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const int i1 = e / N, i2 = e - i1 * N;
+        const int i1 = a.pl.dN.div(e), i2 = e - i1 * N;
         A[i1 * LDp + i2] = a.grid[base + e];
       }
       __syncthreads();
       V* R = fft_tile2<T, -1, true>(A, B, N, 1, LDp, a.pl, stw);
       V* Q = (R == A) ? B : A;
       for (int e = threadIdx.x; e < npp * N; e += blockDim.x) {
-        const int k = e / N, i2 = e - k * N;
+        const int k = a.pl.dN.div(e), i2 = e - k * N;
         Q[k * LDp + i2] = R[g.pencils[q0 + k].y * LDp + i2];
       }
       __syncthreads();
       V* S = fft_tile2<T, -1, false>(Q, R, npp, LDp, 1, a.pl, stw);
+      V* Wv = (S == Q) ? R : Q;                     // free buffer: the plane's Ap values
       const double2 Ec = a.E[c];
-      for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+      const int ns = s1 - s0;
+      for (int e = threadIdx.x; e < ns; e += blockDim.x) {
+        const int s = s0 + e;
         V val = S[(g.sph_pen[s] - q0) * LDp + g.sph_i2[s]];
         const V pv = a.p[sc + s];
         const T dr = a.kin[s] - (T)Ec.x, di = -(T)Ec.y;
         val.x += dr * pv.x - di * pv.y;
         val.y += dr * pv.y + di * pv.x;
         a.Ap[sc + s] = val;
+        Wv[e] = val;
       }
       __syncthreads();
-      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-      for (int v = warp; v < a.nocc; v += nw) {
-        T ax = 0, ay = 0;
-        for (int s = s0 + lane; s < s1; s += 32) {
-          const V cv = a.C[(size_t)v * a.npw + s];
-          const V y = a.Ap[sc + s];
-          ax += cv.x * y.x + cv.y * y.y;
-          ay += cv.x * y.y - cv.y * y.x;
-        }
-        double dx = ax, dy = ay;
-        for (int o = 16; o > 0; o >>= 1) {
-          dx += __shfl_xor_sync(0xffffffffu, dx, o);
-          dy += __shfl_xor_sync(0xffffffffu, dy, o);
-        }
-        if (lane == 0) a.dpart[((size_t)c * npl + pi) * a.nocc + v] = make_double2(dx, dy);
-      }
+      for (int e = threadIdx.x; e < ns; e += blockDim.x) S[e] = a.p[sc + s0 + e];   // the plane's p values
       __syncthreads();
+      double2* dp = a.dpart + ((size_t)c * npl + pi) * ndp;
+      plane_dots<T, false>(a.C, a.npw, a.nocc, S, Wv, s0, ns, dp, red);
     }
+    work(2);
     if (!grid_barrier(a.bar, a.err, nblk)) return;
     mark(2);
 
-    // ---- phase D: P_c on Ap, partial p^H Ap
+    // ---- phase E: coef = sum of the plane partials, p^H P_c A p, alpha;
+    // x += alpha p, r -= alpha P_c Ap (P_c applied on the fly), partials
+    // |r|^2 and r^H K r
     for (int task = blockIdx.x; task < ncol * a.nchunk; task += gridDim.x) {
       const int c = task / a.nchunk, ch = task - c * a.nchunk;
       if (!st_act[c]) continue;
-      // coef[v] = sum over planes of the partials: stage all partials in shared
-      // memory with every thread loading (independent loads in flight), then
-      // add them in plane order per v
       {
-        const double2* src = a.dpart + (size_t)c * npl * a.nocc;
-        // A and B are adjacent: 2 N (N+1) complex values of scratch
-        const bool staged = (size_t)npl * a.nocc * sizeof(double2) <= 2 * (size_t)N * LDp * sizeof(V);
+        // stage the plane partials in shared memory (every thread loading:
+        // independent loads in flight), then add them in plane order
+        const double2* src = a.dpart + (size_t)c * npl * ndp;
+        const bool staged = (size_t)npl * ndp * sizeof(double2) <= 2 * (size_t)N * LDp * sizeof(V);
         const double2* stage = staged ? reinterpret_cast<const double2*>(A) : src;
         if (staged) {
           double2* st = reinterpret_cast<double2*>(A);
-          for (int e = threadIdx.x; e < npl * a.nocc; e += blockDim.x) st[e] = src[e];
+          staged_copy<kLd, double2>(npl * ndp, [&](int e) { return src[e]; },
+                                    [&](int e, double2 v) { st[e] = v; });
         }
         __syncthreads();
-        for (int v = threadIdx.x; v < a.nocc; v += blockDim.x) {
+        for (int j = threadIdx.x; j < ndp; j += blockDim.x) {
           double sx = 0.0, sy = 0.0;
-          for (int pi = 0; pi < npl; ++pi) {
-            const double2 q = stage[pi * a.nocc + v];
-            sx += q.x;
-            sy += q.y;
+          for (int q = 0; q < npl; ++q) {
+            const double2 v = stage[q * ndp + j];
+            sx += v.x;
+            sy += v.y;
           }
-          coef[v] = make_double2(sx, sy);
+          coef[j] = make_double2(sx, sy);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          // p^H P_c A p = p^H A p - sum_v conj(<C_v|p>) <C_v|Ap>
+          double pap = coef[2 * a.nocc].x;
+          for (int v = 0; v < a.nocc; ++v) {
+            const double2 k = coef[v], q = coef[a.nocc + v];
+            pap -= q.x * k.x + q.y * k.y;
+          }
+          bcast = pap;
+          if (ch == 0) a.ppart[(size_t)c * a.nchunk] = pap;
         }
         __syncthreads();
       }
+      const double pap = bcast;
+      const T al = (T)((pap > 0.0) ? st_rz[c] / pap : 0.0);
       const int g0 = ch * kPChunk, g1 = min(a.npw, g0 + kPChunk);
       const size_t sc = (size_t)c * a.npw;
-      double acc = 0.0;
+      const T rtk = a.tk ? (T)(1.0 / a.tk[c]) : (T)0;
+      double acc = 0.0, accz = 0.0;
       for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
-        V y = a.Ap[sc + G];
+        const size_t i = sc + G;
+        V y = a.Ap[i];
+        const V pv = a.p[i];
+        V xv = a.x[i], rv = a.r[i];
+        const T kin = a.kin[G];
         int v = 0;
-        for (; v + 8 <= a.nocc; v += 8) {          // eight independent loads in flight
-          V cv[8];
+        for (; v + 4 <= a.nocc; v += 4) {          // four independent loads in flight
+          V cv[4];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) cv[u] = a.C[(size_t)(v + u) * a.npw + G];
+          for (int u = 0; u < 4; ++u) cv[u] = a.C[(size_t)(v + u) * a.npw + G];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
+          for (int u = 0; u < 4; ++u) {
             const V k = from_d<T>(coef[v + u]);
             y.x -= cv[u].x * k.x - cv[u].y * k.y;
             y.y -= cv[u].x * k.y + cv[u].y * k.x;
@@ -395,47 +430,16 @@ __global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
           y.x -= cv.x * k.x - cv.y * k.y;
           y.y -= cv.x * k.y + cv.y * k.x;
         }
-        a.Ap[sc + G] = y;
-        const V pv = a.p[sc + G];
-        acc += (double)(pv.x * y.x + pv.y * y.y);
-      }
-      acc = dsum_block<T>(acc, red);
-      if (threadIdx.x == 0) a.ppart[(size_t)c * a.nchunk + ch] = acc;
-      __syncthreads();
-    }
-    if (!grid_barrier(a.bar, a.err, nblk)) return;
-    mark(3);
-
-    // ---- phase E: x += alpha p, r -= alpha Ap, partial |r|^2
-    for (int task = blockIdx.x; task < ncol * a.nchunk; task += gridDim.x) {
-      const int c = task / a.nchunk, ch = task - c * a.nchunk;
-      if (!st_act[c]) continue;
-      if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < a.nchunk; ++k) s += a.ppart[(size_t)c * a.nchunk + k];
-        bcast = s;
-      }
-      __syncthreads();
-      const double pap = bcast;
-      const T al = (T)((pap > 0.0) ? st_rz[c] / pap : 0.0);
-      const int g0 = ch * kPChunk, g1 = min(a.npw, g0 + kPChunk);
-      const size_t sc = (size_t)c * a.npw;
-      const T rtk = a.tk ? (T)(1.0 / a.tk[c]) : (T)0;
-      double acc = 0.0, accz = 0.0;
-      for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
-        const size_t i = sc + G;
-        const V pv = a.p[i], av = a.Ap[i];
-        V xv = a.x[i], rv = a.r[i];
         xv.x += al * pv.x;
         xv.y += al * pv.y;
-        rv.x -= al * av.x;
-        rv.y -= al * av.y;
+        rv.x -= al * y.x;
+        rv.y -= al * y.y;
         a.x[i] = xv;
         a.r[i] = rv;
         const double2 rd = to_d(rv);
         const double n2 = rd.x * rd.x + rd.y * rd.y;
         acc += n2;
-        accz += (rtk != (T)0 ? (double)tpa<T>(a.kin[G] * rtk) : 1.0) * n2;
+        accz += (rtk != (T)0 ? (double)tpa<T>(kin * rtk) : 1.0) * n2;
       }
       acc = dsum_block<T>(acc, red);
       if (threadIdx.x == 0) a.rpart[(size_t)c * a.nchunk + ch] = acc;
@@ -443,29 +447,32 @@ __global__ void __launch_bounds__(kPT) k_cg_persistent(PcgArgs<T> a) {
       if (threadIdx.x == 0) a.zpart[(size_t)c * a.nchunk + ch] = accz;
       __syncthreads();
     }
+    work(4);
     if (!grid_barrier(a.bar, a.err, nblk)) return;
     mark(4);
 
     // ---- convergence decisions (identical in every CTA)
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
       if (!st_act[c]) continue;
-      double s = 0.0, z = 0.0, pp = 0.0;
+      double s = 0.0, z = 0.0;
       for (int k = 0; k < a.nchunk; ++k) {
         s += a.rpart[(size_t)c * a.nchunk + k];
         z += a.zpart[(size_t)c * a.nchunk + k];
-        pp += a.ppart[(size_t)c * a.nchunk + k];
       }
+      const double pp = a.ppart[(size_t)c * a.nchunk];
       const int itc = st_it[c] + 1;
       st_it[c] = itc;
       st_beta[c] = z / st_rz[c];
       st_rz[c] = z;
       st_rr[c] = s;
       st_min[c] = fmin(st_min[c], s);
+      if (s < 0.25 * st_best[c]) { st_best[c] = s; st_itb[c] = itc; }
       int stop = 0;
       if (!(pp > 0.0) || !isfinite(s)) { st_flag[c] = 2; stop = 1; }
       else if (s <= st_stop[c]) { st_flag[c] = 0; stop = 1; }
       else if (s > 1e4 * st_min[c]) { st_flag[c] = 3; stop = 1; }
       else if (itc >= a.maxit) { st_flag[c] = 1; stop = 1; }
+      else if (itc - st_itb[c] > max(kCgStagWindow, 2 * st_itb[c])) { st_flag[c] = 4; stop = 1; }
       if (stop) st_act[c] = 0;
     }
     __syncthreads();

@@ -96,7 +96,7 @@ k_zpass(int mode, Geometry g, Prec<T> P, FftPlan pl, cpx<T>* __restrict__ grid,
     }
   } else {
     for (int e = threadIdx.x; e < np * N; e += blockDim.x) {
-      const int p = e / N, k = e - p * N;
+      const int p = pl.dN.div(e), k = e - p * N;
       int i0, i1;
       if (disc_list) { const int4 pc = g.pencils[p0 + p]; i0 = pc.x; i1 = pc.y; }
       else { i0 = (p0 + p) / N; i1 = (p0 + p) - i0 * N; }
@@ -164,7 +164,7 @@ k_zpass(int mode, Geometry g, Prec<T> P, FftPlan pl, cpx<T>* __restrict__ grid,
     }
   } else {
     for (int e = threadIdx.x; e < np * N; e += blockDim.x) {
-      const int p = e / N, k = e - p * N;
+      const int p = pl.dN.div(e), k = e - p * N;
       int i0, i1;
       if (disc_list) { const int4 pc = g.pencils[p0 + p]; i0 = pc.x; i1 = pc.y; }
       else { i0 = (p0 + p) / N; i1 = (p0 + p) - i0 * N; }

@@ -287,6 +287,8 @@ k_cg_init(int npw, const cpx<U>* __restrict__ b, cpx<T>* __restrict__ x, cpx<T>*
     st.rr[c] = s;
     st.rr0[c] = s;
     st.rr_min[c] = s;
+    st.rr_best[c] = s;
+    st.it_best[c] = 0;
     st.rz[c] = z;
     // relative target of this pass, but never below what the refinement needs
     // overall (a fraction of the final tolerance on the original right-hand side)
@@ -344,10 +346,12 @@ k_cg_update(int npw, cpx<T>* __restrict__ x, cpx<T>* __restrict__ r, const cpx<T
     st.rr[c] = s;
     bool stop = false;
     st.rr_min[c] = fmin(st.rr_min[c], s);
+    if (s < 0.25 * st.rr_best[c]) { st.rr_best[c] = s; st.it_best[c] = it; }
     if (!(pp > 0.0) || !isfinite(s)) { st.flag[c] = 2; stop = true; }     // breakdown / not SPD
     else if (s <= st.rr_stop[c]) { st.flag[c] = 0; stop = true; }
     else if (s > 1e4 * st.rr_min[c]) { st.flag[c] = 3; stop = true; }      // past the round-off floor
     else if (it >= maxit) { st.flag[c] = 1; stop = true; }
+    else if (it - st.it_best[c] > max(kCgStagWindow, 2 * st.it_best[c])) { st.flag[c] = 4; stop = true; }
     if (stop) { st.active[c] = 0; atomicAdd(st.n_done, 1); }
   }
 }

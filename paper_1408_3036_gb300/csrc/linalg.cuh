@@ -25,10 +25,13 @@ struct CgState {
   double* rr0 = nullptr;    // |b|^2
   double* beta = nullptr;   // next p = r + beta p (beta < 0: p = r)
   int* iters = nullptr;
-  int* flag = nullptr;      // 0 converged, 1 max iterations, 2 breakdown, 3 diverging (round-off floor)
+  int* flag = nullptr;      // 0 converged, 1 max iterations, 2 breakdown, 3 diverging (round-off floor),
+                            // 4 stagnated (no 4x drop of |r|^2 in max(kCgStagWindow, 2 k_best) iterations)
   int* active = nullptr;
   double* rr_stop = nullptr;  // stop when |r|^2 <= rr_stop
   double* rr_min = nullptr;   // smallest |r|^2 seen (divergence guard)
+  double* rr_best = nullptr;  // |r|^2 at the last 4x improvement (stagnation guard)
+  int* it_best = nullptr;     // iteration of that improvement
   const double* rr_abs = nullptr;   // per-column absolute |r|^2 target of the refinement
   double* rz = nullptr;     // current r^H K r (K = kinetic preconditioner; = rr without one)
   const double* tk = nullptr;       // per-column T_ref of the preconditioner, or null (none)
@@ -119,6 +122,19 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
                                  double* zpart, const double* tk, unsigned* bar, int* err, int* iters, int* flags,
                                  double* rr_out, int* grid_used, unsigned long long* ptime = nullptr,
                                  int cta_div = 1);
+// One thread-block cluster per column (kernels_cgc.cu); cudaErrorNotSupported
+// when the column's planes do not fit in the shared memory of a cluster.
+template <typename T>
+cudaError_t launch_cg_cluster(cudaStream_t s, const Geometry& g, const FftPlan& pl, const Prec<T>& P, int nocc,
+                              int npw, int ncol, const double2* b64, const int* outer_active, const double2* E,
+                              const double* rr_abs, const double* tk, double tol_in2, int maxit, cpx<T>* x,
+                              cpx<T>* r, cpx<T>* p, cpx<T>* Ap, int* iters, int* flags, double* rr_out,
+                              int* q_used, unsigned long long* ptime = nullptr);
 constexpr int kPersistentMaxCols = 256;
+constexpr int kPcgChunk = 512;
+// A CG pass whose |r|^2 has not dropped 4x for max(kCgStagWindow, 2 k_best)
+// iterations has reached the accuracy of its working precision: it stops, and
+// the FP64 refinement around it continues from there.
+constexpr int kCgStagWindow = 100;   // sphere entries per task in the persistent CG's update phase
 
 }  // namespace gw

@@ -157,13 +157,20 @@ def test_free_electron_closed_form_gpu():
 
 
 def test_persistent_cg_matches_multi_launch(tiny, monkeypatch):
-    """The one-launch persistent CG and the multi-launch CG agree."""
+    """The one-launch CG (the grid-wide cooperative kernel, or one cluster per
+    column) and the multi-launch CG agree."""
     wl, cell, sph, gs = tiny
     f = W.random_fields(103, 2, sph.ng)
     c1 = make(cell, gs)
     out1 = c1.apply_eps(f, [0.0], gw.GW_FP64)
     out1m = c1.apply_eps(f, [0.0], gw.GW_MIXED)
     c1.close()
+    monkeypatch.setenv("GW_CLUSTER_CG", "1")        # one thread-block cluster per column
+    c3 = make(cell, gs)
+    out3 = c3.apply_eps(f, [0.0], gw.GW_FP64)
+    out3m = c3.apply_eps(f, [0.0], gw.GW_MIXED)
+    c3.close()
+    monkeypatch.delenv("GW_CLUSTER_CG")
     monkeypatch.setenv("GW_MULTI_LAUNCH_CG", "1")
     c2 = make(cell, gs)
     out2 = c2.apply_eps(f, [0.0], gw.GW_FP64)
@@ -171,6 +178,8 @@ def test_persistent_cg_matches_multi_launch(tiny, monkeypatch):
     c2.close()
     assert rel(out1, out2) < 1e-12
     assert rel(out1m, out2m) < 1e-8
+    assert rel(out1, out3) < 1e-12
+    assert rel(out1m, out3m) < 1e-8
 
 
 @pytest.mark.parametrize("omega", [0.3 + 0.1j, 0.25j, 0.9, 1.7 + 0.05j])
