@@ -166,19 +166,18 @@ def class_bytes(miller, N, npw, nocc, s):
     """Algorithmic bytes of the inner CG kernels per column-iteration, and per
     launch-iteration for data shared by all columns; s = bytes per complex value.
 
-    persistent_cg (one launch = one CG pass, five phases per iteration):
+    persistent_cg (one launch = one CG pass, four phases per iteration):
       A  read r, p, write p (3 N_PW s); write the planes of the sphere (P0 N^2 s)
       B  read + write those planes (2 P0 N^2 s); V shared (N^3 real)
       C  read the planes (P0 N^2 s); read p, write Ap (2 N_PW s); C_v shared (n_occ N_PW s)
-      D  read + write Ap, read p (3 N_PW s); C_v shared again
-      E  read p, Ap, x, r, write x, r (6 N_PW s)
+      E  read Ap, p, x, r, write x, r (6 N_PW s); C_v shared again
     """
     n = np.mod(miller, N)
     D = len({(a, b) for a, b in zip(n[:, 0], n[:, 1])})        # disc pencils
     P0 = len(set(n[:, 0]))                                     # planes cut by the sphere
     real = s // 2
     col = {
-        "persistent_cg": 14 * npw * s + 4 * P0 * N * N * s,
+        "persistent_cg": 11 * npw * s + 4 * P0 * N * N * s,
         "z_scatter_inv": 3 * npw * s + D * N * s,
         "y_inv": D * N * s + P0 * N * N * s,
         "x_h": 2 * P0 * N * N * s,
@@ -197,7 +196,7 @@ def class_bytes(miller, N, npw, nocc, s):
 
 def src_hash():
     h = hashlib.sha256()
-    for f in ("fft.cuh", "kernels_fft.cu", "kernels_linalg.cu", "gw_common.cuh"):
+    for f in ("fft.cuh", "kernels_fft.cu", "kernels_linalg.cu", "gw_common.cuh", "kernels_cg.cu", "pcg.cuh"):
         with open(os.path.join(ROOT, "paper_1408_3036_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -119,8 +119,8 @@ gw_status sync(gw_ctx* ctx, const char* where) {
 gw_status ensure_work(gw_ctx* ctx, size_t cols) {
   cols = std::max<size_t>(cols, 64);
   if (cols <= ctx->work_cols) return GW_OK;
-  // enough partial slots for chunks of 1024 grid points and of 256 sphere entries
-  const size_t nch = std::max<size_t>((size_t)ctx->N3 / 1024, (size_t)ctx->npw / 256) + 2;
+  // enough partial slots for chunks of 1024 grid points and of 128 sphere entries
+  const size_t nch = std::max<size_t>((size_t)ctx->N3 / 1024, (size_t)ctx->npw / 128) + 2;
   const size_t occ = std::max(ctx->nocc, 1);
   TRY(getbuf(ctx, "w_part1", nch * cols, &ctx->work.part1));
   TRY(getbuf(ctx, "w_part2", nch * cols * std::max<size_t>(occ, 1), &ctx->work.part2));

@@ -39,7 +39,7 @@ __device__ __forceinline__ R block_sum(R v) {
 // ---------------------------------------------------------------------------
 // P_c y = y - sum_v c_v <c_v|y>: coefficients (a) then update (b).
 // ---------------------------------------------------------------------------
-constexpr int kChunkP = 256;  // sphere entries per block in the projector coefficients
+constexpr int kChunkP = 128;  // sphere entries per block in the projector coefficients (spreads over all SMs)
 
 // (a) coef[v * ncol + b] = sum_G conj(C[v][G]) Y[b][G]; grid (nchunk, ceil(ncol / kCT))
 template <typename T>
