@@ -61,11 +61,51 @@ __device__ __forceinline__ void butterfly(cpx<T>* a, int r) {
   }
 }
 
+// Butterfly of a compile-time radix R (2, 3, 4 or 5).
+template <typename T, int SIGN, int R>
+__device__ __forceinline__ void butterfly_r(cpx<T>* a) {
+  butterfly<T, SIGN>(a, R);
+}
+
+// One Stockham stage of radix R over npen pencils (see fft_tile2).
+template <typename T, int SIGN, bool PFAST, int R>
+__device__ __forceinline__ void fft_stage(const cpx<T>* __restrict__ a, cpx<T>* __restrict__ b, int npen, int ps,
+                                          int es, int nb, int Ns, int tstep, const FastDiv& dpen,
+                                          const FastDiv& dnb, const FastDiv& dns, const cpx<T>* tw) {
+  using V = cpx<T>;
+  const int total = npen * nb;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int p, j;
+    if (PFAST) { j = dpen.div(t); p = t - j * npen; }
+    else { p = dnb.div(t); j = t - p * nb; }
+    const int jq = dns.div(j);
+    const int k = j - jq * Ns;
+    const V* src = a + p * ps;
+    V* dst = b + p * ps;
+    V v[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[q] = src[(j + q * nb) * es];
+    if (k > 0) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) {
+        V w = tw[k * q * tstep];
+        if (SIGN > 0) w.y = -w.y;
+        v[q] = cmul(v[q], w);
+      }
+    }
+    butterfly_r<T, SIGN, R>(v);
+    const int base = jq * Ns * R + k;
+#pragma unroll
+    for (int q = 0; q < R; ++q) dst[(base + q * Ns) * es] = v[q];
+  }
+}
+
 // Generalised tile FFT: npen pencils, pencil p element k at buf[p * ps + k * es].
 // PFAST selects the thread mapping: consecutive threads take consecutive
 // pencils (PFAST, for pencils adjacent in memory: es > 1, ps = 1) or
-// consecutive butterflies of one pencil (contiguous pencils: es = 1).  The
-// index divisions use the plan's precomputed multiply-shift divisors.
+// consecutive butterflies of one pencil (contiguous pencils: es = 1).  Each
+// stage runs a loop specialised for its radix; the index divisions use the
+// plan's precomputed multiply-shift divisors.
 // Returns the buffer holding the result (a or b).  Ends with __syncthreads().
 template <typename T, int SIGN, bool PFAST>
 __device__ cpx<T>* fft_tile2(cpx<T>* a, cpx<T>* b, int npen, int ps, int es, const FftPlan& pl,
@@ -75,38 +115,15 @@ __device__ cpx<T>* fft_tile2(cpx<T>* a, cpx<T>* b, int npen, int ps, int es, con
   FastDiv dpen = pl.dN;
   if (PFAST && npen != N) dpen.set((unsigned)npen);
   for (int s = 0; s < pl.nst; ++s) {
-    const int r = pl.rad[s];
     const int nb = pl.nb[s];
     const int Ns = pl.ns[s];
     const int tstep = pl.dns[s].div(nb);          // N / (Ns r)
     const FastDiv dnb = pl.dnb[s], dns = pl.dns[s];
-    const int total = npen * nb;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      int p, j;
-      if (PFAST) { j = dpen.div(t); p = t - j * npen; }
-      else { p = dnb.div(t); j = t - p * nb; }
-      const int jq = dns.div(j);
-      const int k = j - jq * Ns;
-      const V* src = a + p * ps;
-      V* dst = b + p * ps;
-      V v[5];
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        if (q < r) {
-          V x = src[(j + q * nb) * es];
-          if (q > 0 && k > 0) {
-            V w = tw[k * q * tstep];
-            if (SIGN > 0) w.y = -w.y;
-            x = cmul(x, w);
-          }
-          v[q] = x;
-        }
-      }
-      butterfly<T, SIGN>(v, r);
-      const int base = jq * Ns * r + k;
-#pragma unroll
-      for (int q = 0; q < 5; ++q)
-        if (q < r) dst[(base + q * Ns) * es] = v[q];
+    switch (pl.rad[s]) {
+      case 4: fft_stage<T, SIGN, PFAST, 4>(a, b, npen, ps, es, nb, Ns, tstep, dpen, dnb, dns, tw); break;
+      case 2: fft_stage<T, SIGN, PFAST, 2>(a, b, npen, ps, es, nb, Ns, tstep, dpen, dnb, dns, tw); break;
+      case 3: fft_stage<T, SIGN, PFAST, 3>(a, b, npen, ps, es, nb, Ns, tstep, dpen, dnb, dns, tw); break;
+      default: fft_stage<T, SIGN, PFAST, 5>(a, b, npen, ps, es, nb, Ns, tstep, dpen, dnb, dns, tw); break;
     }
     __syncthreads();
     V* tmp = a; a = b; b = tmp;

@@ -335,7 +335,7 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
                               int* it_max) {
   const int npw = ctx->npw;
   const std::string t = tname<T>();
-  const int nchunk = (npw + kPcgChunk - 1) / kPcgChunk;
+  const int nchunk = (npw + kPcgChunkMin - 1) / kPcgChunkMin;   // partial-sum slots per column
   cpx<T>*r, *p, *Ap, *grid;
   TRY(getbuf(ctx, "cg_r" + t, (size_t)ncol * npw, &r));
   TRY(getbuf(ctx, "cg_p" + t, (size_t)ncol * npw, &p));
@@ -381,7 +381,8 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
     ctx->pcg_cluster = 0;
     CK(launch_cg_persistent<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), ctx->nocc, npw, ncol, b64,
                                outer_active, E, rr_abs, tol * tol, ctx->max_iter, x, r, p, Ap, grid, dpart, ppart,
-                               rpart, zpart, tk, bar, err, iters, flags, rr_out, &used, ptime, ctx->cta_div));
+                               rpart, zpart, tk, bar, err, iters, flags, rr_out, &used, ptime, ctx->cta_div,
+                               nchunk));
   } else {
     CK(le);
   }

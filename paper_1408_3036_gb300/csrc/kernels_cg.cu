@@ -34,7 +34,6 @@
 namespace gw {
 
 constexpr int kPT = 256;        // threads per CTA
-constexpr int kPChunk = kPcgChunk;   // sphere entries per task in phases 0 and E
 constexpr unsigned kSpinLimit = 1u << 24;
 
 template <typename T>
@@ -45,7 +44,7 @@ struct PcgArgs {
   const T* kin;
   const T* vloc_s;
   const cpx<T>* C;
-  int nocc, npw, ncol, nchunk;
+  int nocc, npw, ncol, nchunk, chunk;   // phases 0 and E: nchunk tasks of chunk entries per column
   const double2* b64;
   const int* outer_active;
   const double2* E;
@@ -170,7 +169,7 @@ __global__ void __launch_bounds__(kPT, sizeof(T) == 4 ? 2 : 1) k_cg_persistent(P
   for (int task = blockIdx.x; task < ncol * a.nchunk; task += gridDim.x) {
     const int c = task / a.nchunk, ch = task - c * a.nchunk;
     const bool on = !a.outer_active || a.outer_active[c];
-    const int g0 = ch * kPChunk, g1 = min(a.npw, g0 + kPChunk);
+    const int g0 = ch * a.chunk, g1 = min(a.npw, g0 + a.chunk);
     const T rtk = a.tk ? (T)(1.0 / a.tk[c]) : (T)0;
     double acc = 0.0, accz = 0.0;
     for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
@@ -402,7 +401,7 @@ __global__ void __launch_bounds__(kPT, sizeof(T) == 4 ? 2 : 1) k_cg_persistent(P
       }
       const double pap = bcast;
       const T al = (T)((pap > 0.0) ? st_rz[c] / pap : 0.0);
-      const int g0 = ch * kPChunk, g1 = min(a.npw, g0 + kPChunk);
+      const int g0 = ch * a.chunk, g1 = min(a.npw, g0 + a.chunk);
       const size_t sc = (size_t)c * a.npw;
       const T rtk = a.tk ? (T)(1.0 / a.tk[c]) : (T)0;
       double acc = 0.0, accz = 0.0;
@@ -498,10 +497,11 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
                                  const double* rr_abs, double tol_in2, int maxit, cpx<T>* x, cpx<T>* r, cpx<T>* p,
                                  cpx<T>* Ap, cpx<T>* grid, double2* dpart, double* ppart, double* rpart,
                                  double* zpart, const double* tk, unsigned* bar, int* err, int* iters, int* flags,
-                                 double* rr_out, int* grid_used, unsigned long long* ptime, int cta_div) {
+                                 double* rr_out, int* grid_used, unsigned long long* ptime, int cta_div,
+                                 int max_chunks) {
   PcgArgs<T> a;
   a.g = g; a.pl = pl; a.tw = P.tw; a.kin = P.kin; a.vloc_s = P.vloc_s; a.C = P.C;
-  a.nocc = nocc; a.npw = npw; a.ncol = ncol; a.nchunk = (npw + kPChunk - 1) / kPChunk;
+  a.nocc = nocc; a.npw = npw; a.ncol = ncol;
   a.b64 = b64; a.outer_active = outer_active; a.E = E; a.rr_abs = rr_abs; a.tol_in2 = tol_in2; a.maxit = maxit;
   a.x = x; a.r = r; a.p = p; a.Ap = Ap; a.grid = grid; a.dpart = dpart; a.ppart = ppart; a.rpart = rpart;
   a.zpart = zpart; a.tk = tk;
@@ -532,6 +532,11 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
   const int cap = std::max(1, per * nsm / std::max(cta_div, 1));
   const int nblk = std::min(cap, std::max(ntask, 1));
   *grid_used = nblk;
+  // phases 0 and E: one round of tasks (columns x chunks <= CTAs), chunks a
+  // multiple of 32 entries, at most max_chunks per column (partial-sum slots)
+  a.nchunk = std::max(1, std::min(max_chunks, nblk / std::max(ncol, 1)));
+  a.chunk = (((npw + a.nchunk - 1) / a.nchunk) + 31) / 32 * 32;
+  a.nchunk = (npw + a.chunk - 1) / a.chunk;
   void* args[] = {&a};
   ++g_launches;
   return cudaLaunchCooperativeKernel((const void*)k_cg_persistent<T>, dim3(nblk), dim3(kPT), args, sm, s);
@@ -542,12 +547,12 @@ template cudaError_t launch_cg_persistent<float>(cudaStream_t, const Geometry&, 
                                                  const double*, double, int, float2*, float2*, float2*, float2*,
                                                  float2*, double2*, double*, double*, double*, const double*,
                                                  unsigned*, int*, int*, int*, double*, int*, unsigned long long*,
-                                                 int);
+                                                 int, int);
 template cudaError_t launch_cg_persistent<double>(cudaStream_t, const Geometry&, const FftPlan&, const Prec<double>&,
                                                   int, int, int, const double2*, const int*, const double2*,
                                                   const double*, double, int, double2*, double2*, double2*,
                                                   double2*, double2*, double2*, double*, double*, double*,
                                                   const double*, unsigned*, int*, int*, int*, double*, int*,
-                                                  unsigned long long*, int);
+                                                  unsigned long long*, int, int);
 
 }  // namespace gw

@@ -120,8 +120,8 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
                                  const double* rr_abs, double tol_in2, int maxit, cpx<T>* x, cpx<T>* r, cpx<T>* p,
                                  cpx<T>* Ap, cpx<T>* grid, double2* dpart, double* ppart, double* rpart,
                                  double* zpart, const double* tk, unsigned* bar, int* err, int* iters, int* flags,
-                                 double* rr_out, int* grid_used, unsigned long long* ptime = nullptr,
-                                 int cta_div = 1);
+                                 double* rr_out, int* grid_used, unsigned long long* ptime, int cta_div,
+                                 int max_chunks);
 // One thread-block cluster per column (kernels_cgc.cu); cudaErrorNotSupported
 // when the column's planes do not fit in the shared memory of a cluster.
 template <typename T>
@@ -131,7 +131,7 @@ cudaError_t launch_cg_cluster(cudaStream_t s, const Geometry& g, const FftPlan& 
                               cpx<T>* r, cpx<T>* p, cpx<T>* Ap, int* iters, int* flags, double* rr_out,
                               int* q_used, unsigned long long* ptime = nullptr);
 constexpr int kPersistentMaxCols = 256;
-constexpr int kPcgChunk = 512;
+constexpr int kPcgChunkMin = 64;   // smallest chunk (sphere entries) of the persistent CG's update phase
 // A CG pass whose |r|^2 has not dropped 4x for max(kCgStagWindow, 2 k_best)
 // iterations has reached the accuracy of its working precision: it stops, and
 // the FP64 refinement around it continues from there.
