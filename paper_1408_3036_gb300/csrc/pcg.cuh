@@ -26,53 +26,64 @@ __device__ __forceinline__ double dsum_block_f(double v, double* sh) {
 // Partial sums of one plane (entries s0 .. s0+ns-1 of the sphere):
 //   dp[v] = <C_v|Ap>, dp[nocc + v] = <C_v|p> (v < nocc), dp[2 nocc] = p^H Ap,
 // with the plane's Ap (W) and p (P) in shared memory (ACC: add the sums to dp
-// instead of storing them).  Warp w takes the
-// occupied states v = w, w + warps, ...; its lanes stride over the entries
-// with four loads of C in flight, then reduce with shuffles.
+// instead of storing them).  Warp w takes the occupied states v = w and
+// w + warps (then w + 2 warps, ...); its lanes stride over the entries with
+// the loads of C for both states and eight entries in flight together, then
+// reduce with shuffles.
 template <typename T, bool ACC>
 __device__ __forceinline__ void plane_dots(const cpx<T>* __restrict__ C, int npw, int nocc, const cpx<T>* P,
                                            const cpx<T>* W, int s0, int ns, double2* __restrict__ dp,
                                            double* red) {
   using V = cpx<T>;
+  constexpr int UE = 8;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int v = warp; v < nocc; v += nw) {
-    const V* Cv = C + (size_t)v * npw + s0;
-    T ax = 0, ay = 0, bx = 0, by = 0;
-    int e = lane;
-    for (; e + 96 < ns; e += 128) {
-      V cv[4];
+  for (int v0 = warp; v0 < nocc; v0 += 2 * nw) {
+    const int v1 = v0 + nw;
+    const bool two = v1 < nocc;
+    const V* C0 = C + (size_t)v0 * npw + s0;
+    const V* C1 = C + (size_t)(two ? v1 : v0) * npw + s0;
+    T a0x = 0, a0y = 0, b0x = 0, b0y = 0, a1x = 0, a1y = 0, b1x = 0, b1y = 0;
+    for (int e0 = lane; e0 < ns; e0 += 32 * UE) {
+      V c0[UE], c1[UE];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) cv[u] = Cv[e + 32 * u];
+      for (int u = 0; u < UE; ++u) {
+        const int e = e0 + 32 * u;
+        c0[u] = (e < ns) ? C0[e] : mk<T>(0, 0);
+        c1[u] = (e < ns && two) ? C1[e] : mk<T>(0, 0);
+      }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const V y = W[e + 32 * u], q = P[e + 32 * u];
-        ax += cv[u].x * y.x + cv[u].y * y.y;        // conj(C) Ap
-        ay += cv[u].x * y.y - cv[u].y * y.x;
-        bx += cv[u].x * q.x + cv[u].y * q.y;        // conj(C) p
-        by += cv[u].x * q.y - cv[u].y * q.x;
+      for (int u = 0; u < UE; ++u) {
+        const int e = e0 + 32 * u;
+        if (e < ns) {
+          const V y = W[e], q = P[e];
+          a0x += c0[u].x * y.x + c0[u].y * y.y;      // conj(C) Ap
+          a0y += c0[u].x * y.y - c0[u].y * y.x;
+          b0x += c0[u].x * q.x + c0[u].y * q.y;      // conj(C) p
+          b0y += c0[u].x * q.y - c0[u].y * q.x;
+          a1x += c1[u].x * y.x + c1[u].y * y.y;
+          a1y += c1[u].x * y.y - c1[u].y * y.x;
+          b1x += c1[u].x * q.x + c1[u].y * q.y;
+          b1y += c1[u].x * q.y - c1[u].y * q.x;
+        }
       }
     }
-    for (; e < ns; e += 32) {
-      const V cv = Cv[e], y = W[e], q = P[e];
-      ax += cv.x * y.x + cv.y * y.y;
-      ay += cv.x * y.y - cv.y * y.x;
-      bx += cv.x * q.x + cv.y * q.y;
-      by += cv.x * q.y - cv.y * q.x;
-    }
-    double r0 = ax, r1 = ay, r2 = bx, r3 = by;
-    for (int o = 16; o > 0; o >>= 1) {
-      r0 += __shfl_xor_sync(0xffffffffu, r0, o);
-      r1 += __shfl_xor_sync(0xffffffffu, r1, o);
-      r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-      r3 += __shfl_xor_sync(0xffffffffu, r3, o);
-    }
+    double r[8] = {(double)a0x, (double)a0y, (double)b0x, (double)b0y,
+                   (double)a1x, (double)a1y, (double)b1x, (double)b1y};
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      for (int o = 16; o > 0; o >>= 1) r[k] += __shfl_xor_sync(0xffffffffu, r[k], o);
     if (lane == 0) {
-      if (ACC) {
-        dp[v].x += r0; dp[v].y += r1;
-        dp[nocc + v].x += r2; dp[nocc + v].y += r3;
-      } else {
-        dp[v] = make_double2(r0, r1);
-        dp[nocc + v] = make_double2(r2, r3);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !two) break;
+        const int v = h ? v1 : v0;
+        if (ACC) {
+          dp[v].x += r[4 * h]; dp[v].y += r[4 * h + 1];
+          dp[nocc + v].x += r[4 * h + 2]; dp[nocc + v].y += r[4 * h + 3];
+        } else {
+          dp[v] = make_double2(r[4 * h], r[4 * h + 1]);
+          dp[nocc + v] = make_double2(r[4 * h + 2], r[4 * h + 3]);
+        }
       }
     }
   }
