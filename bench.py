@@ -203,16 +203,19 @@ def src_hash():
 
 
 def ncu_traffic(kernel_class):
-    """DRAM bytes per column-iteration of a kernel class from a committed ncu
-    summary, if it was taken on the current kernel sources."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per column-iteration of the persistent CG kernel from the
+    committed ncu summary, if it was taken on the current kernel sources."""
+    if kernel_class != "persistent_cg":
+        return None
+    p = os.path.join(ROOT, "profiles", "k_cg_persistent_molecule.md")
     try:
         with open(p) as f:
-            t = json.load(f)
-        e = t.get(kernel_class)
-        if e and e.get("src") == src_hash():
-            return e
-    except Exception:
+            for line in f:
+                if line.startswith("traffic-per-column-iteration:"):
+                    parts = line.split()
+                    if parts[3] == src_hash():
+                        return {"dram_bytes_per_col_iter": float(parts[1])}
+    except (OSError, IndexError, ValueError):
         pass
     return None
 

@@ -386,16 +386,6 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
   } else {
     CK(le);
   }
-  if (ptime) {
-    unsigned long long h[16];
-    CK(cudaMemcpyAsync(h, ptime, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
-    TRY(sync(ctx, "ptime"));
-    const double w = 1e-6 / std::max(used, 1);   // mean work per CTA
-    std::fprintf(stderr,
-                 "phases(ms) A %.2f B %.2f C %.2f D %.2f E %.2f conv %.2f  blocks %d  work A %.2f B %.2f C %.2f "
-                 "E %.2f\n", h[0] * 1e-6, h[1] * 1e-6, h[2] * 1e-6, h[3] * 1e-6, h[4] * 1e-6, h[5] * 1e-6, used,
-                 h[8] * w, h[9] * w, h[10] * w, h[12] * w);
-  }
   prof_end(ctx, PC_PCG, pa);
   std::vector<int> its(ncol), fl(ncol);
   int herr = 0;
@@ -411,6 +401,19 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
     imax = std::max(imax, its[c]);
     if (fl[c] == 2 && std::is_same<T, double>::value)
       return fail(ctx, GW_E_BREAKDOWN, "CG breakdown: (H - E) is not positive definite on P_c");
+  }
+  if (ptime) {
+    unsigned long long h[16];
+    CK(cudaMemcpyAsync(h, ptime, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
+    TRY(sync(ctx, "ptime"));
+    long long cit = 0;
+    for (int c = 0; c < ncol; ++c) cit += its[c];
+    const double w = 1e-6 / std::max(used, 1);   // mean work per CTA
+    std::fprintf(stderr,
+                 "pcg launch: column-iterations %lld, iterations %d; cumulative phases(ms) A %.2f B %.2f C %.2f "
+                 "D %.2f E %.2f conv %.2f  blocks %d  work A %.2f B %.2f C %.2f E %.2f\n", cit, imax,
+                 h[0] * 1e-6, h[1] * 1e-6, h[2] * 1e-6, h[3] * 1e-6, h[4] * 1e-6, h[5] * 1e-6, used, h[8] * w,
+                 h[9] * w, h[10] * w, h[12] * w);
   }
   ctx->pcg_iters += imax;       // iterations of the whole launch (bounded by the slowest column)
   ctx->pcg_launch_blocks = used;
