@@ -125,6 +125,31 @@ __device__ __forceinline__ T tpa(T x) {
   return p / (p + (T)16 * (x * x) * (x * x));
 }
 
+// Adds n records of W doubles (record k at p + k * stride) in index order --
+// the rounding of a plain loop -- with the loads of eight records in flight
+// (the last block of a reduction otherwise waits one memory round trip per
+// record).
+template <int W>
+__device__ __forceinline__ void sum_records(const double* __restrict__ p, int n, size_t stride, double* s) {
+#pragma unroll
+  for (int w = 0; w < W; ++w) s[w] = 0.0;
+  int k = 0;
+  for (; k + 8 <= n; k += 8) {
+    double t[8][W];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int w = 0; w < W; ++w) t[u][w] = p[(size_t)(k + u) * stride + w];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int w = 0; w < W; ++w) s[w] += t[u][w];
+  }
+  for (; k < n; ++k)
+#pragma unroll
+    for (int w = 0; w < W; ++w) s[w] += p[(size_t)k * stride + w];
+}
+
 // Deterministic cross-block reduction: every block writes its partial sums,
 // then takes a ticket; the block drawing the last ticket sees all partials
 // (after the fences) and resets the ticket for the next launch.

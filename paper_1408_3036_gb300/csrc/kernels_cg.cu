@@ -135,7 +135,7 @@ __host__ __device__ inline PcgLayout pcg_layout(int N, int ncol, int nocc, int v
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kPT, sizeof(T) == 4 ? 2 : 1) k_cg_persistent(PcgArgs<T> a) {
+__global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
   using V = cpx<T>;
   extern __shared__ unsigned char smem_raw[];
   const Geometry& g = a.g;
@@ -189,11 +189,9 @@ __global__ void __launch_bounds__(kPT, sizeof(T) == 4 ? 2 : 1) k_cg_persistent(P
   }
   if (!grid_barrier(a.bar, a.err, nblk)) return;
   for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
-    double s = 0.0, z = 0.0;
-    for (int k = 0; k < a.nchunk; ++k) {
-      s += a.rpart[(size_t)c * a.nchunk + k];
-      z += a.zpart[(size_t)c * a.nchunk + k];
-    }
+    double s, z;
+    sum_records<1>(a.rpart + (size_t)c * a.nchunk, a.nchunk, 1, &s);
+    sum_records<1>(a.zpart + (size_t)c * a.nchunk, a.nchunk, 1, &z);
     const bool on = !a.outer_active || a.outer_active[c];
     st_rr[c] = s;
     st_rz[c] = z;
@@ -453,11 +451,9 @@ __global__ void __launch_bounds__(kPT, sizeof(T) == 4 ? 2 : 1) k_cg_persistent(P
     // ---- convergence decisions (identical in every CTA)
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
       if (!st_act[c]) continue;
-      double s = 0.0, z = 0.0;
-      for (int k = 0; k < a.nchunk; ++k) {
-        s += a.rpart[(size_t)c * a.nchunk + k];
-        z += a.zpart[(size_t)c * a.nchunk + k];
-      }
+      double s, z;
+      sum_records<1>(a.rpart + (size_t)c * a.nchunk, a.nchunk, 1, &s);
+      sum_records<1>(a.zpart + (size_t)c * a.nchunk, a.nchunk, 1, &z);
       const double pp = a.ppart[(size_t)c * a.nchunk];
       const int itc = st_it[c] + 1;
       st_it[c] = itc;

@@ -152,13 +152,10 @@ k_zpass(int mode, Geometry g, Prec<T> P, FftPlan pl, cpx<T>* __restrict__ grid,
       }
       if (last_block(&dots.cnt[col], nblk)) {
         for (int v = threadIdx.x; v < dots.nocc; v += blockDim.x) {
-          double sx = 0.0, sy = 0.0;
-          for (int b = 0; b < nblk; ++b) {
-            const double2 p = dots.part[((size_t)col * nblk + b) * dots.nocc + v];
-            sx += p.x;
-            sy += p.y;
-          }
-          dots.coef[(size_t)v * dots.ncol + col] = make_double2(sx, sy);
+          double q[2];
+          sum_records<2>(reinterpret_cast<const double*>(dots.part + (size_t)col * nblk * dots.nocc + v), nblk,
+                         2 * (size_t)dots.nocc, q);
+          dots.coef[(size_t)v * dots.ncol + col] = make_double2(q[0], q[1]);
         }
       }
     }

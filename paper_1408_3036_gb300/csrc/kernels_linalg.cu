@@ -82,12 +82,10 @@ k_proj_dots(const cpx<T>* __restrict__ C, int nocc, int npw, const cpx<T>* __res
   if (!last_block(&cnt[blockIdx.y], nchunk)) return;
   for (int t = threadIdx.x; t < nocc * nb; t += blockDim.x) {
     const int v = t / nb, j = t - v * nb;
-    double2 s = make_double2(0, 0);
-    for (int c = 0; c < nchunk; ++c) {
-      const double2 p = partial[((size_t)c * nocc + v) * ncol + b0 + j];
-      s.x += p.x; s.y += p.y;
-    }
-    coef[(size_t)v * ncol + b0 + j] = s;
+    double q[2];
+    sum_records<2>(reinterpret_cast<const double*>(partial + (size_t)v * ncol + b0 + j), nchunk,
+                   2 * (size_t)nocc * ncol, q);
+    coef[(size_t)v * ncol + b0 + j] = make_double2(q[0], q[1]);
   }
 }
 
@@ -125,8 +123,8 @@ k_proj_update(const cpx<T>* __restrict__ C, int nocc, int npw, cpx<T>* __restric
   if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ncol + b] = acc;
   if (!last_block(&cnt[b], gridDim.x)) return;
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int c = 0; c < (int)gridDim.x; ++c) s += partial[(size_t)c * ncol + b];
+    double s;
+    sum_records<1>(partial + b, gridDim.x, ncol, &s);
     pap[b] = s;
   }
 }
@@ -176,13 +174,9 @@ k_wmat(const double2* __restrict__ U, const double* __restrict__ w, int n, int n
   if (threadIdx.x == 0) partial[(size_t)blockIdx.x * np + pair] = make_double2(ax, ay);
   if (!last_block(&cnt[pair], gridDim.x)) return;
   if (threadIdx.x == 0) {
-    double sx = 0.0, sy = 0.0;
-    for (int k = 0; k < (int)gridDim.x; ++k) {
-      const double2 q = partial[(size_t)k * np + pair];
-      sx += q.x;
-      sy += q.y;
-    }
-    W[pair] = make_double2(sx / n, sy / n);
+    double q[2];
+    sum_records<2>(reinterpret_cast<const double*>(partial + pair), gridDim.x, 2 * (size_t)np, q);
+    W[pair] = make_double2(q[0] / n, q[1] / n);
   }
 }
 
@@ -278,12 +272,9 @@ k_cg_init(int npw, const cpx<U>* __restrict__ b, cpx<T>* __restrict__ x, cpx<T>*
   if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ncol + c] = make_double2(acc, accz);
   if (!last_block(&st.cnt[c], gridDim.x)) return;
   if (threadIdx.x == 0) {
-    double s = 0.0, z = 0.0;
-    for (int k = 0; k < (int)gridDim.x; ++k) {
-      const double2 pk = partial[(size_t)k * ncol + c];
-      s += pk.x;
-      z += pk.y;
-    }
+    double q[2];
+    sum_records<2>(reinterpret_cast<const double*>(partial + c), gridDim.x, 2 * (size_t)ncol, q);
+    const double s = q[0], z = q[1];
     st.rr[c] = s;
     st.rr0[c] = s;
     st.rr_min[c] = s;
@@ -333,12 +324,9 @@ k_cg_update(int npw, cpx<T>* __restrict__ x, cpx<T>* __restrict__ r, const cpx<T
   if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ncol + c] = make_double2(acc, accz);
   if (!last_block(&st.cnt[c], gridDim.x)) return;
   if (threadIdx.x == 0) {
-    double s = 0.0, z = 0.0;
-    for (int k = 0; k < (int)gridDim.x; ++k) {
-      const double2 pk = partial[(size_t)k * ncol + c];
-      s += pk.x;
-      z += pk.y;
-    }
+    double q[2];
+    sum_records<2>(reinterpret_cast<const double*>(partial + c), gridDim.x, 2 * (size_t)ncol, q);
+    const double s = q[0], z = q[1];
     const int it = st.iters[c] + 1;
     st.iters[c] = it;
     st.beta[c] = z / st.rz[c];
@@ -425,11 +413,9 @@ k_qmr_init(int npw, const double2* __restrict__ b, cpx<T>* __restrict__ x, cpx<T
   }
   if (!last_block(&st.cnt[c], gridDim.x)) return;
   if (threadIdx.x == 0) {
-    double s1 = 0.0, sx = 0.0, sy = 0.0;
-    for (int k = 0; k < (int)gridDim.x; ++k) {
-      const double* pp = partial + 3 * ((size_t)k * ncol + c);
-      s1 += pp[0]; sx += pp[1]; sy += pp[2];
-    }
+    double q[3];
+    sum_records<3>(partial + 3 * (size_t)c, gridDim.x, 3 * (size_t)ncol, q);
+    const double s1 = q[0], sx = q[1], sy = q[2];
     st.tau[c] = sqrt(s1);
     st.rho[c] = make_double2(sx, sy);
     st.theta[c] = 0.0;
@@ -467,11 +453,9 @@ k_qmr_sigma(int npw, const cpx<T>* __restrict__ q, const cpx<T>* __restrict__ t,
   }
   if (!last_block(&st.cnt[c], gridDim.x)) return;
   if (threadIdx.x == 0) {
-    double sx = 0.0, sy = 0.0;
-    for (int k = 0; k < (int)gridDim.x; ++k) {
-      const double* pp = partial + 2 * ((size_t)k * ncol + c);
-      sx += pp[0]; sy += pp[1];
-    }
+    double q[2];
+    sum_records<2>(partial + 2 * (size_t)c, gridDim.x, 2 * (size_t)ncol, q);
+    const double sx = q[0], sy = q[1];
     const double2 sg = make_double2(sx, sy);
     const double2 rho = st.rho[c];
     if (!(sx * sx + sy * sy > 1e-300 * (rho.x * rho.x + rho.y * rho.y)) || !isfinite(sx) || !isfinite(sy)) {
@@ -508,8 +492,8 @@ k_qmr_r(int npw, cpx<T>* __restrict__ r, const cpx<T>* __restrict__ t, double* _
   if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ncol + c] = acc;
   if (!last_block(&st.cnt[c], gridDim.x)) return;
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < (int)gridDim.x; ++k) s += partial[(size_t)k * ncol + c];
+    double s;
+    sum_records<1>(partial + c, gridDim.x, ncol, &s);
     const double th = sqrt(s) / st.tau[c];
     const double c2 = 1.0 / (1.0 + th * th);
     st.dcoef[c] = c2 * st.theta[c] * st.theta[c];   // multiplies the old d
@@ -555,11 +539,9 @@ k_qmr_dx(int npw, cpx<T>* __restrict__ x, cpx<T>* __restrict__ d, const cpx<T>* 
   }
   if (!last_block(&st.cnt[c], gridDim.x)) return;
   if (threadIdx.x == 0) {
-    double sx = 0.0, sy = 0.0;
-    for (int k = 0; k < (int)gridDim.x; ++k) {
-      const double* pp = partial + 2 * ((size_t)k * ncol + c);
-      sx += pp[0]; sy += pp[1];
-    }
+    double q[2];
+    sum_records<2>(partial + 2 * (size_t)c, gridDim.x, 2 * (size_t)ncol, q);
+    const double sx = q[0], sy = q[1];
     const double2 rn = make_double2(sx, sy);
     const double2 rho = st.rho[c];
     st.beta[c] = (rho.x * rho.x + rho.y * rho.y > 0.0) ? cdiv(rn, rho) : make_double2(0, 0);
@@ -680,11 +662,9 @@ k_residual(int npw, const double2* __restrict__ b, double2* __restrict__ ax, con
   }
   if (!last_block(&cnt[c], gridDim.x)) return;
   if (threadIdx.x == 0) {
-    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    for (int k = 0; k < (int)gridDim.x; ++k) {
-      const double* pp = partial + 3 * ((size_t)k * ncol + c);
-      s1 += pp[0]; s2 += pp[1]; s3 += pp[2];
-    }
+    double q[3];
+    sum_records<3>(partial + 3 * (size_t)c, gridDim.x, 3 * (size_t)ncol, q);
+    const double s1 = q[0], s2 = q[1], s3 = q[2];
     res2[c] = s1;
     bb[c] = s2;
     if (xx) xx[c] = s3;
@@ -760,8 +740,8 @@ k_gemv_t(const double* __restrict__ Q, size_t ld, int n, const double* __restric
   if (threadIdx.x == 0) partial[(size_t)blockIdx.x * k + j] = acc;
   if (!last_block(&cnt[j], gridDim.x)) return;
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int c = 0; c < (int)gridDim.x; ++c) s += partial[(size_t)c * k + j];
+    double s;
+    sum_records<1>(partial + j, gridDim.x, k, &s);
     out[j] = wgt * s;
   }
 }
@@ -822,8 +802,8 @@ k_dot(int n, const double* __restrict__ x, const double* __restrict__ y, double 
   if (threadIdx.x == 0) partial[blockIdx.x] = acc;
   if (!last_block(cnt, gridDim.x)) return;
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int c = 0; c < (int)gridDim.x; ++c) s += partial[c];
+    double s;
+    sum_records<1>(partial, gridDim.x, 1, &s);
     s *= wgt;
     *out = want_sqrt ? sqrt(s) : s;
   }
@@ -946,13 +926,10 @@ k_cgram(const double2* __restrict__ X, int mx, const double2* __restrict__ Y, in
   if (!last_block(&cnt[blockIdx.y], nchunk)) return;
   for (int t = threadIdx.x; t < mx * nj; t += blockDim.x) {
     const int i = t / nj, j = t - i * nj;
-    double sx = 0.0, sy = 0.0;
-    for (int c = 0; c < nchunk; ++c) {
-      const double2 p = partial[((size_t)c * mx + i) * my + j0 + j];
-      sx += p.x;
-      sy += p.y;
-    }
-    out[(size_t)i * my + j0 + j] = make_double2(wgt * sx, wgt * sy);
+    double q[2];
+    sum_records<2>(reinterpret_cast<const double*>(partial + (size_t)i * my + j0 + j), nchunk,
+                   2 * (size_t)mx * my, q);
+    out[(size_t)i * my + j0 + j] = make_double2(wgt * q[0], wgt * q[1]);
   }
 }
 
