@@ -219,7 +219,8 @@ gw_status sqrtv(gw_ctx* ctx, const T* in, int nb, T* out, const T* sub) {
 // H applied to FP64 sphere vectors with shift: out = P_c? (H - E) x
 // ---------------------------------------------------------------------------
 template <typename T>
-gw_status h_apply(gw_ctx* ctx, cpx<T>* x, int ncol, const double2* E, const int* active, cpx<T>* out) {
+gw_status h_apply(gw_ctx* ctx, cpx<T>* x, int ncol, const double2* E, const int* active, cpx<T>* out,
+                  const GatherDots* dots = nullptr) {
   cpx<T>* grid;
   TRY(getbuf(ctx, std::string("g_h") + tname<T>(), (size_t)ncol * ctx->N3, &grid));
   auto& P = prec_of<T>(ctx);
@@ -230,7 +231,7 @@ gw_status h_apply(gw_ctx* ctx, cpx<T>* x, int ncol, const double2* E, const int*
   launch_xpass_mul<T>(ctx->st, 1, 1, 1, g, P, ctx->plan, grid, P.vloc_s, active, ncol);
   launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, active, ncol, 0);
   launch_zpass<T>(ctx->st, Z_GATHER_FWD_H, g, P, ctx->plan, grid, out, nullptr, nullptr, x, E, active, nullptr,
-                  nullptr, ncol);
+                  nullptr, ncol, dots);
   return launch_check(ctx, "h_apply");
 }
 
@@ -551,7 +552,11 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
   TRY(getbuf(ctx, "sv_res2", ncol, &res2));
   TRY(getbuf(ctx, "sv_bb", ncol, &bb));
   TRY(getbuf(ctx, "sv_xx", ncol, &xx));
+  double2 *cb, *cax;
+  TRY(getbuf(ctx, "sv_cb", (size_t)ctx->nocc * ncol, &cb));
+  TRY(getbuf(ctx, "sv_cax", (size_t)ctx->nocc * ncol, &cax));
   TRY(ensure_work(ctx, ncol));
+  launch_gram<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, b64, ncol, ctx->work, cb);   // C^H b
   CK(cudaMemsetAsync(x64, 0, (size_t)ncol * npw * sizeof(double2), ctx->st));
   CK(cudaMemcpyAsync(r64, b64, (size_t)ncol * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
   std::vector<int> act(ncol, 1);
@@ -579,14 +584,22 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
       TRY(inner_solve<T>(ctx, qmr, ncol, r64, E, oact, d, tol_in, rra, tk, &it_sum, &it_max));
       launch_add_conv<T>(ctx->st, npw, ncol, d, x64, oact);
     }
-    // r64 = b - P_c (H - E) x64
+    // r64 = P_c (b - (H - E) x64): C^H (H - E) x64 from the dots fused into the
+    // last transform pass, C^H b computed once per solve
     {
       const int pa = prof_begin(ctx, PC_REFINE);
-      TRY(h_apply<double>(ctx, x64, ncol, E, oact, ax));
-      launch_proj<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, ax, ncol, oact, ctx->work, nullptr, nullptr);
+      GatherDots dots;
+      dots.C = ctx->P64.C;
+      dots.nocc = ctx->nocc;
+      dots.ncol = ncol;
+      dots.part = ctx->work.part_d;
+      dots.cnt = ctx->work.cnt_d;
+      dots.coef = cax;
+      TRY(h_apply<double>(ctx, x64, ncol, E, oact, ax, &dots));
       prof_end(ctx, PC_REFINE, pa);
     }
-    launch_residual(ctx->st, npw, ncol, b64, ax, x64, oact, ctx->work, res2, bb, xx);
+    launch_residual(ctx->st, npw, ncol, b64, ax, x64, oact, ctx->work, res2, bb, xx, ctx->P64.C, ctx->nocc, cb,
+                    cax);
     CK(cudaMemcpyAsync(r64, ax, (size_t)ncol * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
     CK(cudaMemcpyAsync(hr.data(), res2, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaMemcpyAsync(hb.data(), bb, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
@@ -700,9 +713,9 @@ gw_status chi0_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, const std::
   launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, nullptr, nr, 0);
   launch_zpass<T>(ctx->st, Z_GATHER_FWD, g, P, ctx->plan, grid, rhs64, nullptr, nullptr, nullptr, nullptr, nullptr,
                   nullptr, nullptr, nr);
-  // P_c twice: psi_v* y has a large component along the occupied states
-  // (e.g. <psi_v|y psi_v>), and one pass leaves |C C^H - 1| times it behind
-  launch_proj<double>(ctx->st, ctx->P64.C, nocc, npw, rhs64, nr, nullptr, ctx->work, nullptr, nullptr);
+  // P_c once: psi_v* y has a large component along the occupied states (e.g.
+  // <psi_v|y psi_v>) and one pass leaves |C C^H - 1| times it behind; the
+  // solver's FP64 residual P_c (b - A x) removes that remnant
   launch_proj<double>(ctx->st, ctx->P64.C, nocc, npw, rhs64, nr, nullptr, ctx->work, nullptr, nullptr);
   TRY(launch_check(ctx, "rhs"));
   // -- solver columns

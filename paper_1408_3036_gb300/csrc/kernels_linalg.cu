@@ -633,13 +633,25 @@ void launch_add_conv(cudaStream_t s, int npw, int ncol, const cpx<T>* d, double2
   k_add_conv<T><<<g, kLT, 0, s>>>((size_t)npw, d, x, active);
 }
 
-// r = b - Ax (in place over Ax), res2[c] = |r|^2, bb[c] = |b|^2, xx[c] = |x|^2
+// r = b - Ax (in place over Ax), res2[c] = |r|^2, bb[c] = |b|^2, xx[c] = |x|^2.
+// With C: r = P_c (b - Ax) = b - Ax - sum_v C_v (cb[v][c] - cax[v][c]), where
+// cb = C^H b and cax = C^H Ax (coefficients [nocc][ncol]).
 __global__ void __launch_bounds__(kLT)
 k_residual(int npw, const double2* __restrict__ b, double2* __restrict__ ax, const double2* __restrict__ x,
            const int* __restrict__ active, double* __restrict__ partial, unsigned* __restrict__ cnt,
-           double* __restrict__ res2, double* __restrict__ bb, double* __restrict__ xx, int ncol) {
+           double* __restrict__ res2, double* __restrict__ bb, double* __restrict__ xx, int ncol,
+           const double2* __restrict__ C, int nocc, const double2* __restrict__ cb,
+           const double2* __restrict__ cax) {
+  __shared__ double2 sc[kMaxOcc];
   const int c = blockIdx.y;
   if (active && !active[c]) return;
+  if (C) {
+    for (int v = threadIdx.x; v < nocc; v += blockDim.x) {
+      const double2 u = cb[(size_t)v * ncol + c], w = cax[(size_t)v * ncol + c];
+      sc[v] = make_double2(u.x - w.x, u.y - w.y);
+    }
+    __syncthreads();
+  }
   const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
   double a1 = 0.0, a2 = 0.0, a3 = 0.0;
   for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
@@ -648,6 +660,13 @@ k_residual(int npw, const double2* __restrict__ b, double2* __restrict__ ax, con
     double2 r = ax[i];
     r.x = bv.x - r.x;
     r.y = bv.y - r.y;
+    if (C) {
+      for (int v = 0; v < nocc; ++v) {
+        const double2 cv = C[(size_t)v * npw + G], k = sc[v];
+        r.x -= cv.x * k.x - cv.y * k.y;
+        r.y -= cv.x * k.y + cv.y * k.x;
+      }
+    }
     ax[i] = r;
     a1 += r.x * r.x + r.y * r.y;
     a2 += bv.x * bv.x + bv.y * bv.y;
@@ -672,11 +691,12 @@ k_residual(int npw, const double2* __restrict__ b, double2* __restrict__ ax, con
 }
 
 void launch_residual(cudaStream_t s, int npw, int ncol, const double2* b, double2* ax, const double2* x,
-                     const int* active, Work& w, double* res2, double* bb, double* xx) {
+                     const int* active, Work& w, double* res2, double* bb, double* xx, const double2* C, int nocc,
+                     const double2* cb, const double2* cax) {
   dim3 g((npw + kChunk - 1) / kChunk, ncol);
   ++g_launches;
   k_residual<<<g, kLT, 0, s>>>(npw, b, ax, x, active, reinterpret_cast<double*>(w.part2), w.cnt_b, res2, bb,
-                                xx, ncol);
+                                xx, ncol, C, nocc, cb, cax);
 }
 
 // ---------------------------------------------------------------------------
