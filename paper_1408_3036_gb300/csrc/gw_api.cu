@@ -415,6 +415,9 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
                  "D %.2f E %.2f conv %.2f  blocks %d  work A %.2f B %.2f C %.2f E %.2f\n", cit, imax,
                  h[0] * 1e-6, h[1] * 1e-6, h[2] * 1e-6, h[3] * 1e-6, h[4] * 1e-6, h[5] * 1e-6, used, h[8] * w,
                  h[9] * w, h[10] * w, h[12] * w);
+    std::fprintf(stderr, "  column iterations:");
+    for (int c = 0; c < ncol && c < 64; ++c) std::fprintf(stderr, " %d", its[c]);
+    std::fprintf(stderr, "\n");
   }
   ctx->pcg_iters += imax;       // iterations of the whole launch (bounded by the slowest column)
   ctx->pcg_launch_blocks = used;
