@@ -301,7 +301,10 @@ typedef struct gw_batch gw_batch;
 gw_status gw_batch_setup(gw_batch** out, int n_cells, const double* L, const int* n_grid, const double* ecut,
                          const double* const* vloc, int coulomb, int n_workers);
 
-/* Number of cells; the context of cell i (owned by the batch; NULL if out of range). */
+/* Number of cells; the context of cell i (owned by the batch; NULL if out of range).
+ * A cell's context works on the batch's own non-blocking stream for that cell:
+ * device-pointer arguments passed to it must be complete before the call
+ * (synchronise the stream that produced them). */
 int gw_batch_size(const gw_batch* b);
 gw_ctx* gw_batch_cell(gw_batch* b, int i);
 
