@@ -106,6 +106,30 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# replicas: one independent copy of the workload per rank (the path does not
+# shard: one Lanczos recursion is sequential), no data-path collective
+# ---------------------------------------------------------------------------
+def replica_rate(local_ms, steps, k, world, group_max):
+    """Whole-job applications/s of `world` replicas: the applications of all
+    ranks over the slowest rank's time.  ``group_max(x)`` returns the maximum of
+    x over the ranks (identity for one rank).  Returns (rate, max_ms)."""
+    total = float(group_max(float(local_ms)))
+    return world * steps * k / (total / 1e3), total
+
+
+def torch_group_max(device=None):
+    """group_max over the default torch.distributed process group (any backend)."""
+    import torch
+    import torch.distributed as dist
+
+    def f(x):
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return f
+
+
+# ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 class Clocks:
@@ -309,13 +333,8 @@ def run_gpu(args):
     gw.gw_profile(cell.ctx, 0)
     launches = gw.gw_stats(cell.ctx)["launches"] - launches0
     stats_last = gw.gw_stats(cell.ctx)
-    total_ms = float(sum(times))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps * K / (total_ms / 1e3)
+    value, total_ms = replica_rate(float(sum(times)), args.steps, K, world,
+                                   torch_group_max(dev) if world > 1 else (lambda x: x))
     alpha_mixed = alpha.cpu().numpy().copy()
     beta_mixed = beta[:K - 1].cpu().numpy().copy()
 
