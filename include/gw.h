@@ -246,7 +246,7 @@ gw_status gw_stats(const gw_ctx* ctx, double* out, int n);
  * gw_set_solver -- Sternheimer solver controls (0 or negative keeps a value):
  *   tol        normwise backward error |b - A x| / (|A| |x| + |b|) that every
  *              column must reach, measured in FP64 (default 1e-13 for GW_FP64;
- *              the mixed path uses max(tol, 1e-13), default 1e-12); a pass
+ *              the mixed path uses max(tol, 1e-13), default 1e-10); a pass
  *              that does not halve the error ends the refinement when the error
  *              is already within 10 tol (round-off and input-accuracy floor)
  *   tol_inner  relative residual at which each FP32 inner CG pass of the mixed
