@@ -273,7 +273,7 @@ def run_gpu(args):
     attempt = 0
     while True:
         cell = gw.Cell(c.L, c.N, c.ecut, c.vloc, 0, stream.cuda_stream)
-        eps, psi, res = lowest_states(cell, c.n_occ, tol=1e-10)
+        eps, psi, res = lowest_states(cell, c.n_occ + args.deflation, tol=1e-10)
         if res > 1e-8:
             raise RuntimeError(f"ground state did not converge (residual {res:.2e})")
         if eps[c.n_occ] - eps[c.n_occ - 1] > 1e-3 or attempt >= 5:
@@ -281,7 +281,12 @@ def run_gpu(args):
         attempt += 1
         wl = W.molecule(attempt)
         c = wl.cells[0]
-    cell.set_occupied(psi, eps[:c.n_occ])
+    cell.set_occupied(psi[:c.n_occ], eps[:c.n_occ])
+    ndef = args.deflation
+    while ndef > 0 and eps[c.n_occ + ndef] - eps[c.n_occ + ndef - 1] <= 1e-3:   # keep shells whole
+        ndef -= 1
+    if ndef > 0:
+        cell.set_deflation(psi[c.n_occ:c.n_occ + ndef], eps[c.n_occ:c.n_occ + ndef])
     ng = cell.ng
     dev = torch.device("cuda", local)
     start = torch.tensor(wl.starts[0][0], dtype=torch.float64, device=dev)
@@ -408,6 +413,7 @@ def run_gpu(args):
                         l2="working set (~14 MB) L2-resident inside a step; L2 flushed (512 MB write) "
                            "between timed steps",
                         ground_state_residual=res, gap_homo_lumo=float(eps[c.n_occ] - eps[c.n_occ - 1]),
+                        deflation_states=ndef,
                         sternheimer_mean_iter=stats_last["mean_iter"], sternheimer_max_iter=stats_last["max_iter"],
                         column_iterations_per_step=it_cols / args.steps, geometry=geo),
             roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
@@ -433,6 +439,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-class", default="persistent_cg")
+    ap.add_argument("--deflation", type=int, default=0,
+                    help="lowest conduction states handed to the solvers as a deflation block (0: none)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -101,6 +101,22 @@ gw_status gw_sphere(const gw_ctx* ctx, int* miller);
 gw_status gw_set_occupied(gw_ctx* ctx, int n_occ, const double* psi, const double* eps);
 
 /*
+ * gw_set_deflation -- optional: the lowest n_def conduction states of the
+ * same Hamiltonian (eigenpairs above the occupied ones, sphere order as in
+ * gw_set_occupied, complete degenerate shells).  The Sternheimer solvers then
+ * iterate on the complement of the occupied and these states and add the
+ * latter's components exactly, x += sum_d D_d <D_d|b> / (e_d - e_v -/+ w), so
+ * that the columns of the states nearest the gap need far fewer iterations;
+ * the equations solved and the stopping test are unchanged (the FP64 residual
+ * uses the occupied projector only).  Not in the paper, which uses no
+ * conduction state at all.  n_def = 0 removes the block; gw_set_occupied
+ * removes it too.  Host pointers.  GW_E_ARG without occupied states, for
+ * energies below the highest occupied one, n_occ + n_def > 256, or a block
+ * not closed under conjugation.
+ */
+gw_status gw_set_deflation(gw_ctx* ctx, int n_def, const double* psi, const double* eps);
+
+/*
  * gw_apply_h -- y = H x for nb sphere vectors (the operator of Eq. P2:
  * kinetic |G|^2/2 plus V_loc applied on the grid through FFTs, Sec. Scaling).
  *   x, y  [nb][N_PW] complex

@@ -25,7 +25,7 @@ STATUS = {0: "GW_OK", 1: "GW_E_ARG", 2: "GW_E_CUDA", 3: "GW_E_NOMEM", 4: "GW_E_N
           5: "GW_E_BREAKDOWN", 6: "GW_E_TIMEOUT", 7: "GW_E_NONFINITE", 8: "GW_E_UNSUPPORTED"}
 EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "gw_apply_chi0",
            "gw_apply_eps", "gw_lanczos", "gw_epsinv_elements", "gw_grad_vloc", "gw_stats",
-           "gw_set_solver", "gw_set_precond", "gw_profile", "gw_profile_read", "gw_last_error", "gw_destroy",
+           "gw_set_solver", "gw_set_precond", "gw_set_deflation", "gw_profile", "gw_profile_read", "gw_last_error", "gw_destroy",
            "gw_epsinv_elements_noalloc", "gw_apply_chi0_c", "gw_apply_eps_c", "gw_block_lanczos",
            "gw_epsinv_block", "gw_batch_setup", "gw_batch_size", "gw_batch_cell", "gw_batch_lanczos",
            "gw_batch_last_error", "gw_batch_destroy")
@@ -70,6 +70,7 @@ def load(path=LIB_PATH):
         "gw_stats": (I, [P, P, I]),
         "gw_set_solver": (I, [P, D, D, I, I]),
         "gw_set_precond": (I, [P, I]),
+        "gw_set_deflation": (I, [P, I, P, P]),
         "gw_profile": (I, [P, ctypes.c_uint]),
         "gw_profile_read": (I, [P, P, P, I]),
         "gw_last_error": (ctypes.c_char_p, [P]),
@@ -266,6 +267,14 @@ def gw_set_solver(ctx, tol=0.0, tol_inner=0.0, max_iter=0, max_outer=0):
     _check(ctx, load().gw_set_solver(ctx, float(tol), float(tol_inner), int(max_iter), int(max_outer)))
 
 
+def gw_set_deflation(ctx, psi, eps):
+    """Lowest conduction states (rows of psi, sphere order) as a deflation block."""
+    psi = np.ascontiguousarray(np.asarray(psi, np.complex128))
+    eps = np.ascontiguousarray(np.asarray(eps, np.float64))
+    n = len(eps)
+    _check(ctx, load().gw_set_deflation(ctx, n, psi.ctypes.data if n else None, eps.ctypes.data if n else None))
+
+
 def gw_set_precond(ctx, kind):
     _check(ctx, load().gw_set_precond(ctx, int(kind)))
 
@@ -389,6 +398,9 @@ class Cell:
 
     def set_precond(self, kind):
         gw_set_precond(self.ctx, kind)
+
+    def set_deflation(self, psi, eps):
+        gw_set_deflation(self.ctx, psi, eps)
 
 
 def _check_batch(b, st):

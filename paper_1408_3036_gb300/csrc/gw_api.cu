@@ -33,6 +33,9 @@ struct gw_ctx {
   std::vector<double> kin;
   int nocc = 0;
   std::vector<double> eps;
+  std::vector<std::complex<double>> c_occ;   // realified occupied coefficients (host) [nocc][npw]
+  int ndef = 0;                  // deflation states (lowest conduction states) after the occupied rows of C
+  std::vector<double> eps_def;
   std::map<std::string, std::pair<void*, size_t>> bufs;
   Work work;
   size_t work_cols = 0;
@@ -60,6 +63,10 @@ struct gw_ctx {
 };
 
 namespace {
+
+// Rows of C the inner solvers project out: the occupied states and, when set,
+// the deflation states (whose components the solver adds analytically).
+inline int nproj(const gw_ctx* ctx) { return ctx->nocc + ctx->ndef; }
 
 gw_status fail(gw_ctx* ctx, gw_status s, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -121,7 +128,7 @@ gw_status ensure_work(gw_ctx* ctx, size_t cols) {
   if (cols <= ctx->work_cols) return GW_OK;
   // enough partial slots for chunks of 1024 grid points and of 128 sphere entries
   const size_t nch = std::max<size_t>((size_t)ctx->N3 / 1024, (size_t)ctx->npw / 128) + 2;
-  const size_t occ = std::max(ctx->nocc, 1);
+  const size_t occ = std::max(ctx->nocc + ctx->ndef, 1);
   TRY(getbuf(ctx, "w_part1", nch * cols, &ctx->work.part1));
   TRY(getbuf(ctx, "w_part2", nch * cols * std::max<size_t>(occ, 1), &ctx->work.part2));
   TRY(getbuf(ctx, "w_coef", occ * cols, &ctx->work.coef));
@@ -274,7 +281,7 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
   launch_cg_init<T, double>(ctx->st, npw, ncol, b64, x, r, outer_active, ctx->work, st, P.kin, tol * tol, 0.0);
   GatherDots dots;
   dots.C = P.C;
-  dots.nocc = ctx->nocc;
+  dots.nocc = nproj(ctx);
   dots.ncol = ncol;
   dots.part = ctx->work.part_d;
   dots.cnt = ctx->work.cnt_d;
@@ -289,7 +296,7 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
     PROF(PC_YFWD, launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, st.active, ncol, 0));
     PROF(PC_ZGATH, launch_zpass<T>(ctx->st, Z_GATHER_FWD_H, g, P, ctx->plan, grid, Ap, nullptr, nullptr, p, E,
                                    st.active, nullptr, nullptr, ncol, &dots));
-    PROF(PC_PROJ, launch_proj_update<T>(ctx->st, P.C, ctx->nocc, npw, Ap, ncol, st.active, ctx->work.coef,
+    PROF(PC_PROJ, launch_proj_update<T>(ctx->st, P.C, nproj(ctx), npw, Ap, ncol, st.active, ctx->work.coef,
                                         ctx->work, p, pap));
     PROF(PC_CGUPD, launch_cg_update<T>(ctx->st, npw, ncol, x, r, p, Ap, pap, ctx->work, st, P.kin, tol2,
                                            ctx->max_iter));
@@ -346,7 +353,7 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
   double *ppart, *rpart, *zpart, *rr_out;
   unsigned* bar;
   int *err, *iters, *flags;
-  TRY(getbuf(ctx, "pcg_dpart", (size_t)ncol * ctx->geo.nplanes * (2 * ctx->nocc + 1), &dpart));
+  TRY(getbuf(ctx, "pcg_dpart", (size_t)ncol * ctx->geo.nplanes * (2 * nproj(ctx) + 1), &dpart));
   TRY(getbuf(ctx, "pcg_ppart", (size_t)ncol * nchunk, &ppart));
   TRY(getbuf(ctx, "pcg_rpart", (size_t)ncol * nchunk, &rpart));
   TRY(getbuf(ctx, "pcg_zpart", (size_t)ncol * nchunk, &zpart));
@@ -372,7 +379,7 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
   cudaError_t le = cudaErrorNotSupported;
   if (ctx->use_cluster) {
     int q = 0;
-    le = launch_cg_cluster<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), ctx->nocc, npw, ncol, b64, outer_active,
+    le = launch_cg_cluster<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), nproj(ctx), npw, ncol, b64, outer_active,
                               E, rr_abs, tk, tol * tol, ctx->max_iter, x, r, p, Ap, iters, flags, rr_out, &q, ptime);
     used = ncol * q;
     ctx->pcg_cluster = q;
@@ -380,7 +387,7 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
   if (le == cudaErrorNotSupported) {
     cudaGetLastError();
     ctx->pcg_cluster = 0;
-    CK(launch_cg_persistent<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), ctx->nocc, npw, ncol, b64,
+    CK(launch_cg_persistent<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), nproj(ctx), npw, ncol, b64,
                                outer_active, E, rr_abs, tol * tol, ctx->max_iter, x, r, p, Ap, grid, dpart, ppart,
                                rpart, zpart, tk, bar, err, iters, flags, rr_out, &used, ptime, ctx->cta_div,
                                nchunk));
@@ -466,7 +473,7 @@ gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E,
                 ctx->max_iter);
   GatherDots dots;
   dots.C = P.C;
-  dots.nocc = ctx->nocc;
+  dots.nocc = nproj(ctx);
   dots.ncol = ncol;
   dots.part = ctx->work.part_d;
   dots.cnt = ctx->work.cnt_d;
@@ -481,7 +488,7 @@ gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E,
     launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, st.active, ncol, 0);
     launch_zpass<T>(ctx->st, Z_GATHER_FWD_H, g, P, ctx->plan, grid, tt, nullptr, nullptr, q, E, st.active, nullptr,
                     nullptr, ncol, &dots);
-    launch_proj_update<T>(ctx->st, P.C, ctx->nocc, npw, tt, ncol, st.active, ctx->work.coef, ctx->work, nullptr,
+    launch_proj_update<T>(ctx->st, P.C, nproj(ctx), npw, tt, ncol, st.active, ctx->work.coef, ctx->work, nullptr,
                           nullptr);
     for (int step = 1; step <= 4; ++step)
       launch_qmr<T>(ctx->st, step, npw, ncol, b64, x, r, q, dd, tt, neg, outer_active, ctx->work, st, P.kin,
@@ -560,6 +567,12 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
   TRY(getbuf(ctx, "sv_cax", (size_t)ctx->nocc * ncol, &cax));
   TRY(ensure_work(ctx, ncol));
   launch_gram<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, b64, ncol, ctx->work, cb);   // C^H b
+  double2* cdef = nullptr;
+  double* edef = nullptr;
+  if (ctx->ndef > 0) {
+    TRY(getbuf(ctx, "sv_cdef", (size_t)ctx->ndef * ncol, &cdef));
+    TRY(upload(ctx, "sv_edef", ctx->eps_def, &edef));
+  }
   CK(cudaMemsetAsync(x64, 0, (size_t)ncol * npw * sizeof(double2), ctx->st));
   CK(cudaMemcpyAsync(r64, b64, (size_t)ncol * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
   std::vector<int> act(ncol, 1);
@@ -578,6 +591,16 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
   double2* d64 = nullptr;
   std::vector<double> hprev;
   for (outer = 0; outer < ctx->max_outer && !done; ++outer) {
+    if (ctx->ndef > 0) {
+      // Deflation: the inner pass solves on the complement of the occupied and
+      // the deflation states, so the deflation components leave its right-hand
+      // side (r -= D <D|r>); they are added to x exactly after the pass:
+      // x += sum_d D_d <D_d|r> / (eps_d - E)
+      const double2* D = ctx->P64.C + (size_t)ctx->nocc * npw;
+      launch_gram<double>(ctx->st, D, ctx->ndef, npw, r64, ncol, ctx->work, cdef);
+      launch_proj_update<double>(ctx->st, D, ctx->ndef, npw, r64, ncol, oact, cdef, ctx->work, nullptr, nullptr);
+      launch_defl_scale(ctx->st, cdef, edef, E, ctx->ndef, ncol, oact);
+    }
     if (esc) {
       if (!d64) TRY(getbuf(ctx, "sv_d64", (size_t)ncol * npw, &d64));
       TRY(inner_solve<double>(ctx, qmr, ncol, r64, E, oact, reinterpret_cast<cpx<double>*>(d64),
@@ -587,6 +610,9 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
       TRY(inner_solve<T>(ctx, qmr, ncol, r64, E, oact, d, tol_in, rra, tk, &it_sum, &it_max));
       launch_add_conv<T>(ctx->st, npw, ncol, d, x64, oact);
     }
+    if (ctx->ndef > 0)                // the deflated components, exactly
+      launch_proj_update<double>(ctx->st, ctx->P64.C + (size_t)ctx->nocc * npw, ctx->ndef, npw, x64, ncol, oact,
+                                 cdef, ctx->work, nullptr, nullptr);
     // r64 = P_c (b - (H - E) x64): C^H (H - E) x64 from the dots fused into the
     // last transform pass, C^H b computed once per solve
     {
@@ -1344,6 +1370,151 @@ using zc = std::complex<double>;
 // ===========================================================================
 // C ABI
 // ===========================================================================
+namespace {
+// Real-in-real-space basis for a block of eigenstates (see the comments in
+// the body); with prior rows given, the block is also made orthogonal to them.
+// R receives the rows, e the energies (shell means inside degenerate shells).
+gw_status realify_block(gw_ctx* ctx, int n_occ, const double* psi, const double* eps,
+                        const std::vector<zc>* prior, int n_prior, std::vector<zc>* Rout,
+                        std::vector<double>* eout, const char* what) {
+  const int npw = ctx->npw, N = ctx->N;
+  // index of -G for every sphere point
+  std::map<long, int> where;
+  auto key = [&](int a, int b, int c) { return ((long)(a + N) * (2 * N + 1) + (b + N)) * (2 * N + 1) + (c + N); };
+  for (int s = 0; s < npw; ++s) where[key(ctx->miller[3 * s], ctx->miller[3 * s + 1], ctx->miller[3 * s + 2])] = s;
+  std::vector<int> neg(npw);
+  for (int s = 0; s < npw; ++s) {
+    auto it = where.find(key(-ctx->miller[3 * s], -ctx->miller[3 * s + 1], -ctx->miller[3 * s + 2]));
+    if (it == where.end()) return fail(ctx, GW_E_ARG, "sphere not symmetric");
+    neg[s] = it->second;
+  }
+  // Real-in-real-space basis: (K c)_G = conj(c_{-G}), H K = K H.
+  //  * a state that is K-symmetric up to a phase (|<c|Kc>| ~ 1: the usual,
+  //    non-degenerate case) is multiplied by that phase and its K-symmetric
+  //    part kept;
+  //  * a degenerate shell (consecutive energies within 1e-6 Ha) whose states
+  //    are mixed is re-spanned by the K-symmetric parts (c + Kc)/2 and
+  //    (c - Kc)/2i, picked by pivoted Gram-Schmidt (inner products of
+  //    K-symmetric vectors are real), energies set to the shell mean;
+  //  * finally all states are re-orthonormalised (modified Gram-Schmidt).
+  auto kdot = [&](const zc* c) {       // <c|Kc> = sum_G conj(c_G) conj(c_{-G})
+    zc z = 0.0;
+    for (int s = 0; s < npw; ++s) z += std::conj(c[s]) * std::conj(c[neg[s]]);
+    return z;
+  };
+  std::vector<zc> C((size_t)n_occ * npw);
+  for (size_t i = 0; i < C.size(); ++i) C[i] = zc(psi[2 * i], psi[2 * i + 1]);
+  std::vector<zc> R((size_t)n_occ * npw);
+  std::vector<double> e(n_occ);
+  int v0 = 0;
+  while (v0 < n_occ) {
+    const zc z = kdot(&C[(size_t)v0 * npw]);
+    if (std::abs(z) > 1.0 - 1e-3) {
+      const zc ph = std::exp(zc(0.0, 0.5 * std::arg(z)));   // c = ph^-1 * (K-symmetric)
+      zc* out = &R[(size_t)v0 * npw];
+      for (int s = 0; s < npw; ++s) out[s] = ph * C[(size_t)v0 * npw + s];
+      for (int s = 0; s < npw; ++s)
+        if (neg[s] > s) {
+          const zc a = 0.5 * (out[s] + std::conj(out[neg[s]]));
+          out[s] = a;
+          out[neg[s]] = std::conj(a);
+        } else if (neg[s] == s) {
+          out[s] = zc(out[s].real(), 0.0);
+        }
+      e[v0] = eps[v0];
+      ++v0;
+      continue;
+    }
+    int v1 = v0 + 1;
+    while (v1 < n_occ && std::fabs(eps[v1] - eps[v1 - 1]) < 1e-6) ++v1;
+    const int m = v1 - v0;
+    std::vector<std::vector<zc>> cand;
+    double norm0 = 0.0;
+    for (int v = v0; v < v1; ++v) {
+      std::vector<zc> a(npw), b(npw);
+      for (int s = 0; s < npw; ++s) {
+        const zc c = C[(size_t)v * npw + s], kc = std::conj(C[(size_t)v * npw + neg[s]]);
+        a[s] = 0.5 * (c + kc);
+        b[s] = (c - kc) / zc(0.0, 2.0);
+        norm0 += std::norm(c);
+      }
+      cand.push_back(a);
+      cand.push_back(b);
+    }
+    double mean = 0.0;
+    for (int v = v0; v < v1; ++v) mean += eps[v];
+    mean /= m;
+    std::vector<bool> used(cand.size(), false);
+    for (int k = 0; k < m; ++k) {
+      int best = -1;
+      double bn = -1.0;
+      for (size_t j = 0; j < cand.size(); ++j) {
+        if (used[j]) continue;
+        double n2 = 0.0;
+        for (int s = 0; s < npw; ++s) n2 += std::norm(cand[j][s]);
+        if (n2 > bn) { bn = n2; best = (int)j; }
+      }
+      if (best < 0 || bn < 1e-8) return fail(ctx, GW_E_ARG, std::string(what) + " space is not closed under conjugation");
+      used[best] = true;
+      const double inv = 1.0 / std::sqrt(bn);
+      for (int s = 0; s < npw; ++s) cand[best][s] *= inv;
+      for (size_t j = 0; j < cand.size(); ++j) {
+        if (used[j]) continue;
+        zc d = 0.0;
+        for (int s = 0; s < npw; ++s) d += std::conj(cand[best][s]) * cand[j][s];
+        const double dr = d.real();
+        for (int s = 0; s < npw; ++s) cand[j][s] -= dr * cand[best][s];
+      }
+      for (int s = 0; s < npw; ++s) R[(size_t)(v0 + k) * npw + s] = cand[best][s];
+      e[v0 + k] = mean;
+    }
+    // what is left must be (numerically) inside the span of the shell
+    for (size_t j = 0; j < cand.size(); ++j) {
+      if (used[j]) continue;
+      double n2 = 0.0;
+      for (int s = 0; s < npw; ++s) n2 += std::norm(cand[j][s]);
+      if (n2 > 1e-8 * norm0) return fail(ctx, GW_E_ARG, std::string(what) + " space is not closed under conjugation");
+    }
+    v0 = v1;
+  }
+  for (int v = 0; v < n_occ; ++v) {     // modified Gram-Schmidt, twice (real inner products)
+    zc* a = &R[(size_t)v * npw];
+    for (int u2 = 0; u2 < 2 * (v + n_prior); ++u2) {
+      const int u = u2 % (v + n_prior);
+      const zc* b = (u < n_prior) ? &(*prior)[(size_t)u * npw] : &R[(size_t)(u - n_prior) * npw];
+      zc d = 0.0;
+      for (int s = 0; s < npw; ++s) d += std::conj(b[s]) * a[s];
+      const double dr = d.real();
+      for (int s = 0; s < npw; ++s) a[s] -= dr * b[s];
+    }
+    double n2 = 0.0;
+    for (int s = 0; s < npw; ++s) n2 += std::norm(a[s]);
+    if (!(n2 > 0.5)) return fail(ctx, GW_E_ARG, std::string(what) + " states are not orthonormal");
+    const double inv = 1.0 / std::sqrt(n2);
+    for (int s = 0; s < npw; ++s) a[s] *= inv;
+  }
+  *Rout = std::move(R);
+  *eout = std::move(e);
+  return GW_OK;
+}
+
+// C on the device (FP64 and FP32): the occupied rows, then the deflation rows.
+gw_status upload_projector(gw_ctx* ctx, const std::vector<zc>& cdef) {
+  const size_t n = ctx->c_occ.size() + cdef.size();
+  std::vector<double2> c64(n);
+  std::vector<float2> c32(n);
+  for (size_t i = 0; i < n; ++i) {
+    const zc z = (i < ctx->c_occ.size()) ? ctx->c_occ[i] : cdef[i - ctx->c_occ.size()];
+    c64[i] = make_double2(z.real(), z.imag());
+    c32[i] = make_float2((float)z.real(), (float)z.imag());
+  }
+  TRY(upload(ctx, "occ_C64", c64, &ctx->P64.C));
+  TRY(upload(ctx, "occ_C32", c32, &ctx->P32.C));
+  return GW_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 gw_status gw_setup(gw_ctx** out, double L, int n_grid, double ecut, const double* vloc, int coulomb,
@@ -1424,120 +1595,9 @@ gw_status gw_set_occupied(gw_ctx* ctx, int n_occ, const double* psi, const doubl
     if (!std::isfinite(eps[v])) return fail(ctx, GW_E_NONFINITE, "non-finite energy");
     if (v > 0 && eps[v] < eps[v - 1]) return fail(ctx, GW_E_ARG, "energies must be ascending");
   }
-  // index of -G for every sphere point
-  std::map<long, int> where;
-  auto key = [&](int a, int b, int c) { return ((long)(a + N) * (2 * N + 1) + (b + N)) * (2 * N + 1) + (c + N); };
-  for (int s = 0; s < npw; ++s) where[key(ctx->miller[3 * s], ctx->miller[3 * s + 1], ctx->miller[3 * s + 2])] = s;
-  std::vector<int> neg(npw);
-  for (int s = 0; s < npw; ++s) {
-    auto it = where.find(key(-ctx->miller[3 * s], -ctx->miller[3 * s + 1], -ctx->miller[3 * s + 2]));
-    if (it == where.end()) return fail(ctx, GW_E_ARG, "sphere not symmetric");
-    neg[s] = it->second;
-  }
-  // Real-in-real-space basis: (K c)_G = conj(c_{-G}), H K = K H.
-  //  * a state that is K-symmetric up to a phase (|<c|Kc>| ~ 1: the usual,
-  //    non-degenerate case) is multiplied by that phase and its K-symmetric
-  //    part kept;
-  //  * a degenerate shell (consecutive energies within 1e-6 Ha) whose states
-  //    are mixed is re-spanned by the K-symmetric parts (c + Kc)/2 and
-  //    (c - Kc)/2i, picked by pivoted Gram-Schmidt (inner products of
-  //    K-symmetric vectors are real), energies set to the shell mean;
-  //  * finally all states are re-orthonormalised (modified Gram-Schmidt).
-  auto kdot = [&](const zc* c) {       // <c|Kc> = sum_G conj(c_G) conj(c_{-G})
-    zc z = 0.0;
-    for (int s = 0; s < npw; ++s) z += std::conj(c[s]) * std::conj(c[neg[s]]);
-    return z;
-  };
-  std::vector<zc> C((size_t)n_occ * npw);
-  for (size_t i = 0; i < C.size(); ++i) C[i] = zc(psi[2 * i], psi[2 * i + 1]);
-  std::vector<zc> R((size_t)n_occ * npw);
-  std::vector<double> e(n_occ);
-  int v0 = 0;
-  while (v0 < n_occ) {
-    const zc z = kdot(&C[(size_t)v0 * npw]);
-    if (std::abs(z) > 1.0 - 1e-3) {
-      const zc ph = std::exp(zc(0.0, 0.5 * std::arg(z)));   // c = ph^-1 * (K-symmetric)
-      zc* out = &R[(size_t)v0 * npw];
-      for (int s = 0; s < npw; ++s) out[s] = ph * C[(size_t)v0 * npw + s];
-      for (int s = 0; s < npw; ++s)
-        if (neg[s] > s) {
-          const zc a = 0.5 * (out[s] + std::conj(out[neg[s]]));
-          out[s] = a;
-          out[neg[s]] = std::conj(a);
-        } else if (neg[s] == s) {
-          out[s] = zc(out[s].real(), 0.0);
-        }
-      e[v0] = eps[v0];
-      ++v0;
-      continue;
-    }
-    int v1 = v0 + 1;
-    while (v1 < n_occ && std::fabs(eps[v1] - eps[v1 - 1]) < 1e-6) ++v1;
-    const int m = v1 - v0;
-    std::vector<std::vector<zc>> cand;
-    double norm0 = 0.0;
-    for (int v = v0; v < v1; ++v) {
-      std::vector<zc> a(npw), b(npw);
-      for (int s = 0; s < npw; ++s) {
-        const zc c = C[(size_t)v * npw + s], kc = std::conj(C[(size_t)v * npw + neg[s]]);
-        a[s] = 0.5 * (c + kc);
-        b[s] = (c - kc) / zc(0.0, 2.0);
-        norm0 += std::norm(c);
-      }
-      cand.push_back(a);
-      cand.push_back(b);
-    }
-    double mean = 0.0;
-    for (int v = v0; v < v1; ++v) mean += eps[v];
-    mean /= m;
-    std::vector<bool> used(cand.size(), false);
-    for (int k = 0; k < m; ++k) {
-      int best = -1;
-      double bn = -1.0;
-      for (size_t j = 0; j < cand.size(); ++j) {
-        if (used[j]) continue;
-        double n2 = 0.0;
-        for (int s = 0; s < npw; ++s) n2 += std::norm(cand[j][s]);
-        if (n2 > bn) { bn = n2; best = (int)j; }
-      }
-      if (best < 0 || bn < 1e-8) return fail(ctx, GW_E_ARG, "occupied space is not closed under conjugation");
-      used[best] = true;
-      const double inv = 1.0 / std::sqrt(bn);
-      for (int s = 0; s < npw; ++s) cand[best][s] *= inv;
-      for (size_t j = 0; j < cand.size(); ++j) {
-        if (used[j]) continue;
-        zc d = 0.0;
-        for (int s = 0; s < npw; ++s) d += std::conj(cand[best][s]) * cand[j][s];
-        const double dr = d.real();
-        for (int s = 0; s < npw; ++s) cand[j][s] -= dr * cand[best][s];
-      }
-      for (int s = 0; s < npw; ++s) R[(size_t)(v0 + k) * npw + s] = cand[best][s];
-      e[v0 + k] = mean;
-    }
-    // what is left must be (numerically) inside the span of the shell
-    for (size_t j = 0; j < cand.size(); ++j) {
-      if (used[j]) continue;
-      double n2 = 0.0;
-      for (int s = 0; s < npw; ++s) n2 += std::norm(cand[j][s]);
-      if (n2 > 1e-8 * norm0) return fail(ctx, GW_E_ARG, "occupied space is not closed under conjugation");
-    }
-    v0 = v1;
-  }
-  for (int v = 0; v < n_occ; ++v) {     // modified Gram-Schmidt, twice (real inner products)
-    zc* a = &R[(size_t)v * npw];
-    for (int u2 = 0; u2 < 2 * v; ++u2) {
-      const zc* b = &R[(size_t)(u2 % v) * npw];
-      zc d = 0.0;
-      for (int s = 0; s < npw; ++s) d += std::conj(b[s]) * a[s];
-      const double dr = d.real();
-      for (int s = 0; s < npw; ++s) a[s] -= dr * b[s];
-    }
-    double n2 = 0.0;
-    for (int s = 0; s < npw; ++s) n2 += std::norm(a[s]);
-    if (!(n2 > 0.5)) return fail(ctx, GW_E_ARG, "occupied states are not orthonormal");
-    const double inv = 1.0 / std::sqrt(n2);
-    for (int s = 0; s < npw; ++s) a[s] *= inv;
-  }
+  std::vector<zc> R;
+  std::vector<double> e;
+  TRY(realify_block(ctx, n_occ, psi, eps, nullptr, 0, &R, &e, "occupied"));
   ctx->nocc = n_occ;
   ctx->eps = e;
   ctx->tkin.assign(n_occ, 0.0);
@@ -1553,14 +1613,10 @@ gw_status gw_set_occupied(gw_ctx* ctx, int n_occ, const double* psi, const doubl
     ctx->anorm = kmax + ctx->vmax + emax;
   }
   ctx->work_cols = 0;
-  std::vector<double2> c64((size_t)n_occ * npw);
-  std::vector<float2> c32((size_t)n_occ * npw);
-  for (size_t i = 0; i < c64.size(); ++i) {
-    c64[i] = make_double2(R[i].real(), R[i].imag());
-    c32[i] = make_float2((float)R[i].real(), (float)R[i].imag());
-  }
-  TRY(upload(ctx, "occ_C64", c64, &ctx->P64.C));
-  TRY(upload(ctx, "occ_C32", c32, &ctx->P32.C));
+  ctx->c_occ = R;
+  ctx->ndef = 0;                      // a new occupied block drops any deflation block
+  ctx->eps_def.clear();
+  TRY(upload_projector(ctx, {}));
   // u_v(r) = sum_G c_G e^{iGr}: scatter, inverse transforms (FP64), then FP32 copy
   double2* U;
   float2* U32;
@@ -1576,6 +1632,27 @@ gw_status gw_set_occupied(gw_ctx* ctx, int n_occ, const double* psi, const doubl
   ctx->P64.U = U;
   ctx->P32.U = U32;
   TRY(launch_check(ctx, "set_occupied"));
+  return finish(ctx, GW_OK);
+}
+
+gw_status gw_set_deflation(gw_ctx* ctx, int n_def, const double* psi, const double* eps) {
+  if (!ctx) return GW_E_ARG;
+  TRY(begin(ctx));
+  if (ctx->nocc <= 0) return fail(ctx, GW_E_ARG, "gw_set_occupied has not been called");
+  if (n_def < 0 || ctx->nocc + n_def > kMaxOcc || (n_def > 0 && (!psi || !eps)))
+    return fail(ctx, GW_E_ARG, "bad n_def / pointers");
+  for (int d = 0; d < n_def; ++d) {
+    if (!std::isfinite(eps[d])) return fail(ctx, GW_E_NONFINITE, "non-finite energy");
+    if ((d > 0 && eps[d] < eps[d - 1]) || eps[d] < ctx->eps.back())
+      return fail(ctx, GW_E_ARG, "deflation energies must be ascending and above the occupied ones");
+  }
+  std::vector<zc> R;
+  std::vector<double> e;
+  if (n_def > 0) TRY(realify_block(ctx, n_def, psi, eps, &ctx->c_occ, ctx->nocc, &R, &e, "deflation"));
+  ctx->work_cols = 0;
+  ctx->ndef = n_def;
+  ctx->eps_def = e;
+  TRY(upload_projector(ctx, R));
   return finish(ctx, GW_OK);
 }
 

@@ -699,6 +699,28 @@ void launch_residual(cudaStream_t s, int npw, int ncol, const double2* b, double
                                 xx, ncol, C, nocc, cb, cax);
 }
 
+// Deflated components of a Sternheimer pass: coef[d][c] = <D_d|r_c> on entry;
+// on exit -<D_d|r_c> / (eps_d - E_c), the negated coefficients of
+// sum_d D_d <D_d|r_c> / (eps_d - E_c) for launch_proj_update (which subtracts).
+__global__ void k_defl_scale(double2* __restrict__ coef, const double* __restrict__ eps,
+                             const double2* __restrict__ E, int ndef, int ncol, const int* __restrict__ active) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ndef * ncol) return;
+  const int d = t / ncol, c = t - d * ncol;
+  if (active && !active[c]) return;
+  const double2 den = make_double2(eps[d] - E[c].x, -E[c].y);
+  const double2 q = cdiv(coef[t], den);
+  coef[t] = make_double2(-q.x, -q.y);
+}
+
+void launch_defl_scale(cudaStream_t s, double2* coef, const double* eps, const double2* E, int ndef, int ncol,
+                       const int* active) {
+  const int n = ndef * ncol;
+  if (n == 0) return;
+  ++g_launches;
+  k_defl_scale<<<(n + 255) / 256, 256, 0, s>>>(coef, eps, E, ndef, ncol, active);
+}
+
 // ---------------------------------------------------------------------------
 // sphere-vector helpers
 // ---------------------------------------------------------------------------

@@ -87,6 +87,8 @@ void launch_cg_update(cudaStream_t s, int npw, int ncol, cpx<T>* x, cpx<T>* r, c
                       int maxit);
 template <typename T>
 void launch_add_conv(cudaStream_t s, int npw, int ncol, const cpx<T>* d, double2* x, const int* active);
+void launch_defl_scale(cudaStream_t s, double2* coef, const double* eps, const double2* E, int ndef, int ncol,
+                       const int* active);
 void launch_residual(cudaStream_t s, int npw, int ncol, const double2* b, double2* ax, const double2* x,
                      const int* active, Work& w, double* res2, double* bb, double* xx, const double2* C = nullptr,
                      int nocc = 0, const double2* cb = nullptr, const double2* cax = nullptr);

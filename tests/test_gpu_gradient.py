@@ -56,3 +56,18 @@ def test_gradient_differentiation_config():
     assert abs(s64 - s_ref) < 1e-10 * abs(s_ref)
     assert rel(g64, g_ref) < 1e-8
     assert rel(g32, g_ref) < 1e-6
+
+
+def test_gradient_with_deflation():
+    """The adjoint's Sternheimer solves with a deflation block: same gradient."""
+    c, sph, gs, phi = _case(W.small(), [1.0, 2.0, 3.0])
+    s_ref, g_ref, _ = gradient.grad_vloc(gs, phi)
+    e = gs.eps_all
+    m = next(k for k in range(2, 12) if e[gs.n_occ + k] - e[gs.n_occ + k - 1] > 1e-3)
+    cell = gw.Cell(c.L, c.N, c.ecut, c.vloc)
+    cell.set_occupied(gs.C, gs.eps)
+    cell.set_deflation(gs.C_all[gs.n_occ:gs.n_occ + m], e[gs.n_occ:gs.n_occ + m])
+    s, g = cell.grad_vloc(phi, 30, gw.GW_FP64)
+    cell.close()
+    assert abs(s - s_ref) < 1e-9 * abs(s_ref)
+    assert rel(g, g_ref) < 1e-9

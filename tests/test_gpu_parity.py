@@ -284,3 +284,47 @@ def test_preconditioner_same_solution(tiny, omega):
     with pytest.raises(gw.GwError):
         c.set_precond(2)
     c.close()
+
+
+@pytest.mark.parametrize("omega", [0.0, 0.9, 0.3 + 0.1j])
+def test_deflation_same_solution(tiny, omega):
+    """Deflating the lowest conduction states changes the iterations, not the
+    answer (their components are added exactly): both match the sum over
+    states, and the solves at omega = 0 need fewer iterations."""
+    wl, cell, sph, gs = tiny
+    m = 5                                     # a clean cut: eps_all[9] - eps_all[8] = 0.045 Ha
+    D, eD = gs.C_all[gs.n_occ:gs.n_occ + m], gs.eps_all[gs.n_occ:gs.n_occ + m]
+    f = W.random_fields(108, 2, sph.ng)
+    c = make(cell, gs)
+    ref = [response.chi0_sos(gs, f[b], omega) for b in range(2)]
+    if np.imag(omega) == 0:
+        ref = [r.real for r in ref]
+    outs, its = [], []
+    for use in (False, True):
+        c.set_deflation(D if use else np.zeros((0, sph.npw)), eD if use else np.zeros(0))
+        for prec, tol in ((gw.GW_FP64, 1e-10), (gw.GW_MIXED, 1e-6)):
+            out = c.apply_chi0(f, [omega], prec)[0]
+            for b in range(2):
+                assert rel(out[b], ref[b]) < tol, (use, prec)
+            if prec == gw.GW_FP64:
+                its.append(c.stats()["mean_iter"])
+    if omega == 0.0:
+        assert its[1] < its[0]
+    # Lanczos with the block set: the oracle's alpha, beta
+    c.set_deflation(D, eD)
+    D0 = response.Dielectric(gs, 0.0)
+    a_ref, b_ref, _ = lanczos.lanczos(D0.apply, wl.starts[0][0], 8, sph.omega_vol / sph.ng)
+    a, b, _ = c.lanczos(wl.starts[0][0], 8, 0.0, gw.GW_FP64)
+    assert rel(a, a_ref) < 1e-10 and rel(b, b_ref) < 1e-10
+    c.close()
+
+
+def test_deflation_argument_checks(tiny):
+    wl, cell, sph, gs = tiny
+    c = make(cell)
+    with pytest.raises(gw.GwError):          # no occupied states yet
+        c.set_deflation(gs.C_all[4:6], gs.eps_all[4:6])
+    c.set_occupied(gs.C, gs.eps)
+    with pytest.raises(gw.GwError):          # below the highest occupied energy
+        c.set_deflation(gs.C_all[2:4], gs.eps_all[2:4])
+    c.close()
