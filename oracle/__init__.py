@@ -14,10 +14,14 @@ against the paper:
 * ``coulomb``   square root of the (spherically truncated) Coulomb kernel.
 * ``response``  chi0 by the Adler-Wiser sum over states (Eq. P), its
                 Sternheimer form (Eqs. P1, fvpm, P2a, P2), the squared Hermitian
-                form at imaginary frequency (Eq. P2+), and the symmetrised
-                dielectric operator (Eq. epsilon).
+                form at imaginary frequency (Eq. P2+), the model
+                polarizability with H -> T (Sec. Dielectric model, Eq.
+                model_eq), and the symmetrised dielectric operator (Eq.
+                epsilon).
 * ``lanczos``   Lanczos recursion with full Gram-Schmidt re-orthogonalisation
-                (Sec. Lanczos, Eq. krylov) and the inverse in the Lanczos basis.
+                (Sec. Lanczos, Eq. krylov), the inverse in the Lanczos basis,
+                and the split over an exact and a model basis (Eq.
+                subs_epsilon).
 * ``gradient``  derivative of <phi|eps^-1(0)|phi> with respect to V_loc (not in
                 the paper; derived by third-order perturbation theory and pinned
                 by central finite differences).

@@ -20,6 +20,9 @@ Readings:
   w -= Q (Q^H w) twice; beta_k = |w|; q_{k+1} = w / beta_k.
 * The inverse dielectric matrix in the Lanczos basis is T_K^-1 (dense solve);
   for a start vector phi, <phi|eps^-1|phi> ~ |phi|^2 (T_K^-1)_11.
+* Sec. Dielectric model (Eq. subs_epsilon): eps^-1 - 1 is split into
+  (eps^-1 - eps_m^-1), taken in the exact Lanczos basis, and (eps_m^-1 - 1),
+  taken in the Lanczos basis of the model operator (``epsinv_split``).
 """
 from __future__ import annotations
 
@@ -162,3 +165,31 @@ def quad_s(alpha, beta, phi_norm2):
     """s_K = |phi|^2 (T_K^-1)_11 (Gauss quadrature estimate of <phi|A^-1|phi>)."""
     Ti = epsinv_lanczos(alpha, beta)
     return phi_norm2 * Ti[0, 0]
+
+
+# ---------------------------------------------------------------------------
+# Sec. Dielectric model, Eq. subs_epsilon: eps^-1 - 1 split over two bases
+# ---------------------------------------------------------------------------
+def compress(apply, Q, weight=1.0):
+    """<Q|A Q>: the operator A in the orthonormal basis Q (rows), one
+    application per basis vector; M[i][j] = weight sum_r Q_i(r) (A Q_j)(r)."""
+    Q = np.asarray(Q)
+    AQ = np.array([apply(q) for q in Q])
+    return weight * (np.conj(Q) @ AQ.T)
+
+
+def epsinv_split(a, T, M, a_m, T_m):
+    """<phi_i|eps^-1 - 1|phi_j> by Eq. subs_epsilon,
+        eps^-1 - 1 = (eps^-1 - eps_m^-1) + (eps_m^-1 - 1),
+    the first part in the basis {l} of the exact operator, the second in the
+    basis {l~} of the model operator:
+        a_i^T (T^-1 - M^-1) a_j + a~_i^T (T~^-1 - 1) a~_j,
+    with T = <l|eps l'> (the Lanczos matrix), M = <l|eps_m l'> (the model in
+    the exact basis, from ``compress``), T~ = <l~|eps_m l~'> and the fields'
+    coefficients a = <l|phi> (m x k), a~ = <l~|phi> (m x k~).  Reading: in the
+    exact basis the model operator is compressed and then inverted, the same
+    way T^-1 stands for eps^-1 there."""
+    a, a_m = np.atleast_2d(a), np.atleast_2d(a_m)
+    D = np.linalg.inv(T) - np.linalg.inv(M)
+    D_m = np.linalg.inv(T_m) - np.eye(len(T_m))
+    return a @ D @ a.T + a_m @ D_m @ a_m.T

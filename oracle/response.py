@@ -4,7 +4,9 @@ operator eps~ = 1 - v^1/2 chi0 v^1/2.
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
 Three routes to chi0 f for a grid field f (all give the same result up to
-rounding; the tests pin them against each other and against closed forms):
+rounding; the tests pin them against each other and against closed forms),
+and a fourth, different operator, the model polarizability of Sec. Dielectric
+model (Eq. model_eq, ``chi0_model``, route "model" of ``Dielectric``):
 
 1. ``chi0_eqP``: Eq. P literally,
        P(w) = 2 sum_{c,v} |c* v> [1/(w - (e_c - e_v)) - 1/(w + (e_c - e_v))] <v c*|
@@ -166,6 +168,41 @@ def conduction_gaps(gs, lowest_conduction):
 
 
 # ---------------------------------------------------------------------------
+# Route 4: the model operator of Sec. Dielectric model (Eq. model_eq)
+# ---------------------------------------------------------------------------
+def chi0_model(gs, f, omega):
+    """P~(omega) f of Eq. model_eq: Eq. P2a with H replaced by the kinetic
+    operator T, which is diagonal in the plane-wave sphere.  Per occupied
+    state v,
+        b        = P_c <G|psi_v* f>
+        f~_v(-/+) = P_c [ b / (|G|^2/2 - e_v -/+ omega) ]
+    and, as in Eq. P1, P~ f = -2 sum_v psi_v (f~_v(-) + f~_v(+)).
+    The energies are the absolute e_v of the occupied states (the model is not
+    invariant under a constant shift of V_loc, unlike chi0).
+    Reading: where a denominator is exactly zero its reciprocal is taken as 0
+    (the pseudo-inverse of the diagonal).  That happens on an occupied plane
+    wave of a free-electron cell, where P_c b vanishes; elsewhere the model,
+    like chi0, is singular at such a real frequency."""
+    sph = gs.sph
+    vol = sph.omega_vol
+    u = gs.u
+
+    def pinv(d):
+        out = np.zeros_like(d, dtype=np.complex128)
+        nz = d != 0
+        out[nz] = 1.0 / d[nz]
+        return out
+
+    out = np.zeros(sph.ng, dtype=np.complex128)
+    for v in range(gs.n_occ):
+        b = project_c(gs, sph.to_sphere(np.conj(u[v]) * f))
+        xm = project_c(gs, b * pinv(sph.kin - gs.eps[v] - omega))
+        xp = project_c(gs, b * pinv(sph.kin - gs.eps[v] + omega))
+        out += u[v] * sph.to_grid(xm + xp)
+    return -2.0 / vol * out
+
+
+# ---------------------------------------------------------------------------
 # Eq. P2+: squared Hermitian form at imaginary frequency
 # ---------------------------------------------------------------------------
 def f_sum_imag(gs, v, f, w_im, tol=1e-14):
@@ -187,7 +224,8 @@ def f_sum_imag(gs, v, f, w_im, tol=1e-14):
 # Eq. epsilon: the symmetric dielectric operator
 # ---------------------------------------------------------------------------
 class Dielectric:
-    """eps~(omega) x = x - v^1/2 chi0(omega) v^1/2 x with a chosen chi0 route."""
+    """eps~(omega) x = x - v^1/2 chi0(omega) v^1/2 x with a chosen chi0 route
+    (route "model": the model operator eps~_model of Eq. model_eq)."""
 
     def __init__(self, gs, omega=0.0, kind=coulomb.TRUNCATED, route="sos",
                  tol=1e-14, gaps=None):
@@ -202,6 +240,8 @@ class Dielectric:
             return chi0_sos(self.gs, f, self.omega)
         if self.route == "sternheimer":
             return chi0_sternheimer(self.gs, f, self.omega, self.tol, self.gaps)
+        if self.route == "model":
+            return chi0_model(self.gs, f, self.omega)
         raise ValueError(self.route)
 
     def sqrtv(self, x):
