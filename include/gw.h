@@ -60,6 +60,12 @@ typedef enum {
 
 typedef enum { GW_COULOMB_TRUNCATED = 0, GW_COULOMB_BARE = 1 } gw_coulomb;
 
+/* Operator applied by the chi0 / eps~ / Lanczos entries (gw_set_operator). */
+typedef enum {
+  GW_OP_STERNHEIMER = 0,   /* chi0 through the Sternheimer equations (Eqs. P1, P2) */
+  GW_OP_MODEL = 1          /* the model polarizability of Sec. Dielectric model (Eq. model_eq) */
+} gw_operator;
+
 /*
  * gw_setup -- create a context for one cell (Sec. Scaling: N_PW sphere
  * coefficients, N_FFT grid points; Sec. Results: spherical Coulomb truncation
@@ -283,6 +289,50 @@ gw_status gw_set_solver(gw_ctx* ctx, double tol, double tol_inner, int max_iter,
  * only changes the iteration count.  GW_E_ARG for any other kind.
  */
 gw_status gw_set_precond(gw_ctx* ctx, int kind);
+
+/*
+ * gw_set_operator -- which polarizability gw_apply_chi0(_c), gw_apply_eps(_c),
+ * gw_lanczos, gw_block_lanczos and gw_batch_lanczos apply (default
+ * GW_OP_STERNHEIMER).  GW_OP_MODEL is the model operator of Sec. Dielectric
+ * model (Eq. model_eq): H is replaced by the kinetic operator T in Eq. P2a,
+ * so each Sternheimer solve becomes one division in the plane-wave sphere,
+ *   f~_v(-/+) = P_c [ (|G|^2/2 - e_v -/+ omega)^-1 P_c (psi_v* dV) ],
+ * summed over both signs and reduced as in Eq. P1.  The energies are the
+ * absolute e_v given to gw_set_occupied; a denominator that is exactly zero
+ * contributes zero (pseudo-inverse).  Under GW_OP_MODEL, GW_FP64 runs every
+ * step in FP64; GW_MIXED runs the transforms, projections and divisions of
+ * real fields at real frequencies in FP32 with the fields at the boundary and
+ * the Lanczos recursion in FP64 (complex fields or frequencies stay FP64).  No
+ * solver statistics are produced, and gw_grad_vloc returns GW_E_UNSUPPORTED.
+ * GW_E_ARG for any other value.
+ */
+gw_status gw_set_operator(gw_ctx* ctx, int op);
+
+/*
+ * gw_epsinv_split -- matrix elements of eps~^-1 - 1 at a real frequency from
+ * two Lanczos bases (Sec. Dielectric model, Eq. subs_epsilon):
+ *   eps~^-1 - 1 = (eps~^-1 - eps~_m^-1) + (eps~_m^-1 - 1),
+ * the first part in the basis {l} of the Sternheimer operator, the second in
+ * the basis {l~} of the model operator:
+ *   out[i][j] = a_i^T (T^-1 - M^-1) a_j + a~_i^T (T~^-1 - 1) a~_j,
+ *   a = <l|phi>, a~ = <l~|phi>, M = <l|eps~_m l'> (the model operator applied
+ *   to every vector of {l}: k model applications), T, T~ the tridiagonal
+ *   Lanczos matrices (alpha, beta) of the two recursions.
+ * The model operator in the exact basis is compressed to that basis and then
+ * inverted, the way T^-1 stands for eps~^-1 there.  Runs on the GPU in FP64
+ * whatever operator gw_set_operator selected.
+ *   phi      [m][N^3] real fields, 1 <= m <= 64
+ *   basis    [k][N^3], alpha [k], beta [k-1]: gw_lanczos with GW_OP_STERNHEIMER;
+ *            1 <= k <= 2048
+ *   basis_m  [k_m][N^3], alpha_m [k_m], beta_m [k_m-1]: gw_lanczos with
+ *            GW_OP_MODEL at the same omega; 1 <= k_m <= 4096
+ *   omega    the real frequency of both recursions
+ *   out      [m][m] real
+ * Returns GW_E_BREAKDOWN when T, T~ or M is singular.
+ */
+gw_status gw_epsinv_split(gw_ctx* ctx, const double* phi, int m, const double* basis, const double* alpha,
+                          const double* beta, int k, const double* basis_m, const double* alpha_m,
+                          const double* beta_m, int k_m, double omega, double* out, int device_ptrs);
 
 /*
  * gw_profile -- time selected kernel classes with CUDA events on the work

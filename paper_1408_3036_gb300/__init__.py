@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libgw.so")
 
 GW_FP64, GW_MIXED = 0, 1
 GW_COULOMB_TRUNCATED, GW_COULOMB_BARE = 0, 1
+GW_OP_STERNHEIMER, GW_OP_MODEL = 0, 1
 STATUS = {0: "GW_OK", 1: "GW_E_ARG", 2: "GW_E_CUDA", 3: "GW_E_NOMEM", 4: "GW_E_NOCONV",
           5: "GW_E_BREAKDOWN", 6: "GW_E_TIMEOUT", 7: "GW_E_NONFINITE", 8: "GW_E_UNSUPPORTED"}
 EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "gw_apply_chi0",
@@ -28,7 +29,7 @@ EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "
            "gw_set_solver", "gw_set_precond", "gw_set_deflation", "gw_profile", "gw_profile_read", "gw_last_error", "gw_destroy",
            "gw_epsinv_elements_noalloc", "gw_apply_chi0_c", "gw_apply_eps_c", "gw_block_lanczos",
            "gw_epsinv_block", "gw_batch_setup", "gw_batch_size", "gw_batch_cell", "gw_batch_lanczos",
-           "gw_batch_last_error", "gw_batch_destroy")
+           "gw_batch_last_error", "gw_batch_destroy", "gw_set_operator", "gw_epsinv_split")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
                    "refine_fp64", "persistent_cg")
 
@@ -70,6 +71,8 @@ def load(path=LIB_PATH):
         "gw_stats": (I, [P, P, I]),
         "gw_set_solver": (I, [P, D, D, I, I]),
         "gw_set_precond": (I, [P, I]),
+        "gw_set_operator": (I, [P, I]),
+        "gw_epsinv_split": (I, [P, P, I, P, P, P, I, P, P, P, I, D, P, I]),
         "gw_set_deflation": (I, [P, I, P, P]),
         "gw_profile": (I, [P, ctypes.c_uint]),
         "gw_profile_read": (I, [P, P, P, I]),
@@ -279,6 +282,31 @@ def gw_set_precond(ctx, kind):
     _check(ctx, load().gw_set_precond(ctx, int(kind)))
 
 
+def gw_set_operator(ctx, op):
+    """GW_OP_STERNHEIMER (Eqs. P1, P2) or GW_OP_MODEL (Eq. model_eq)."""
+    _check(ctx, load().gw_set_operator(ctx, int(op)))
+
+
+def gw_epsinv_split(ctx, phi, basis, alpha, beta, basis_m, alpha_m, beta_m, omega, out):
+    """<phi_i|eps~^-1 - 1|phi_j> from the Sternheimer basis (basis, alpha, beta)
+    and the model basis (basis_m, alpha_m, beta_m), Eq. subs_epsilon."""
+    pp, d = _ptr(phi)
+    m = phi.shape[0] if phi.ndim == 2 else 1
+    k, km = len(alpha), len(alpha_m)
+    pq, _ = _ptr(basis)
+    pa, _ = _ptr(alpha)
+    pb, _ = _ptr(beta)
+    pqm, _ = _ptr(basis_m)
+    pam, _ = _ptr(alpha_m)
+    pbm, _ = _ptr(beta_m)
+    po, e = _ptr(out)
+    if d != e:
+        raise ValueError("mixed host/device buffers")
+    _check(ctx, load().gw_epsinv_split(ctx, pp, int(m), pq, pa, pb, int(k), pqm, pam, pbm, int(km),
+                                       float(omega), po, d))
+    return out
+
+
 def gw_profile(ctx, mask):
     _check(ctx, load().gw_profile(ctx, int(mask)))
 
@@ -398,6 +426,17 @@ class Cell:
 
     def set_precond(self, kind):
         gw_set_precond(self.ctx, kind)
+
+    def set_operator(self, op):
+        gw_set_operator(self.ctx, op)
+
+    def epsinv_split(self, phi, lz, lz_model, omega=0.0):
+        """Eq. subs_epsilon from two host Lanczos results (alpha, beta, basis)."""
+        phi = np.ascontiguousarray(np.atleast_2d(np.asarray(phi, np.float64)))
+        a, b, Q = (np.ascontiguousarray(np.asarray(x, np.float64)) for x in lz)
+        am, bm, Qm = (np.ascontiguousarray(np.asarray(x, np.float64)) for x in lz_model)
+        out = np.zeros((phi.shape[0], phi.shape[0]))
+        return gw_epsinv_split(self.ctx, phi, Q, a, b, Qm, am, bm, omega, out)
 
     def set_deflation(self, psi, eps):
         gw_set_deflation(self.ctx, psi, eps)

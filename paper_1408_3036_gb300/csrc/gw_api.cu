@@ -10,6 +10,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "gw.h"
@@ -37,6 +38,7 @@ struct gw_ctx {
   int ndef = 0;                  // deflation states (lowest conduction states) after the occupied rows of C
   std::vector<double> eps_def;
   std::map<std::string, std::pair<void*, size_t>> bufs;
+  std::map<std::string, std::vector<unsigned char>> tables;   // last contents of read-only index tables
   Work work;
   size_t work_cols = 0;
   double tol = 1e-13, tol_mixed = 1e-10, tol_inner = 1e-5;   // backward errors (FP64 / mixed), inner
@@ -48,6 +50,7 @@ struct gw_ctx {
   int pcg_cluster = 0;          // cluster size of the last persistent launch (0: grid-wide kernel)
   int cta_div = 1;              // contexts sharing the GPU concurrently (batch mode)
   int precond = 1;              // 1: kinetic (TPA) preconditioner in the Sternheimer solvers; 0: none
+  int op = GW_OP_STERNHEIMER;   // operator of the chi0 / eps~ entries (GW_OP_MODEL: Eq. model_eq)
   std::vector<double> tkin;     // kinetic energy of each occupied state (preconditioner reference)
   bool ptime_init = false;
   double vmax = 0.0;            // max |V_loc|
@@ -107,6 +110,25 @@ template <class X>
 gw_status upload(gw_ctx* ctx, const std::string& name, const std::vector<X>& v, X** out) {
   TRY(getbuf(ctx, name, v.size(), out));
   if (!v.empty()) CK(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, ctx->st));
+  return GW_OK;
+}
+
+// Upload of a read-only table that kernels never write: skipped when the same
+// bytes were uploaded last under this name (the per-call column tables of an
+// application repeat from one Lanczos step to the next).
+template <class X>
+gw_status upload_table(gw_ctx* ctx, const std::string& name, const std::vector<X>& v, X** out) {
+  const size_t bytes = v.size() * sizeof(X);
+  auto& last = ctx->tables[name];
+  auto it = ctx->bufs.find(name);
+  if (bytes > 0 && it != ctx->bufs.end() && it->second.first && it->second.second >= bytes &&
+      last.size() == bytes && std::memcmp(last.data(), v.data(), bytes) == 0) {
+    *out = reinterpret_cast<X*>(it->second.first);
+    return GW_OK;
+  }
+  TRY(upload(ctx, name, v, out));
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(v.data());
+  last.assign(p, p + bytes);
   return GW_OK;
 }
 
@@ -715,9 +737,78 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
 // simplified QMR for any other (real or complex) frequency.
 // Fields y are real (y_cplx = false) or complex; dn is complex when dn_cplx.
 // ---------------------------------------------------------------------------
+gw_status chi0_reduce(gw_ctx* ctx, const double2* sol64, int nb, int nom, void* dn, bool dn_cplx);
+
+// ---------------------------------------------------------------------------
+// The model operator (Sec. Dielectric model, Eq. model_eq), every step in
+// precision T: H -> T in Eq. P2a turns each Sternheimer solve into one
+// division by the kinetic denominators,
+//   rhs_{b,v}  = P_c Sphere(FFT(conj(u_v) y_b))
+//   sol_{o,b,v} = P_c [ (pinv(|G|^2/2 - e_v - w_o) + pinv(|G|^2/2 - e_v + w_o)) rhs_{b,v} ]
+//   dn_{o,b}   = -(2/Omega) sum_v u_v IFFT(sol_{o,b,v})
+// (the two signs summed before the second projector, which is linear).
+// y: [nb][N_g] real or complex (interleaved) in T; dn: [nom][nb][N_g] in T.
+// ---------------------------------------------------------------------------
+template <typename T>
+gw_status chi0_model_core(gw_ctx* ctx, const T* y, bool y_cplx, int nb, const std::vector<double2>& omega, T* dn,
+                          bool dn_cplx) {
+  const int npw = ctx->npw, nocc = ctx->nocc;
+  const int nom = (int)omega.size();
+  const int nr = nocc * nb, nsol = nom * nr;
+  auto& P = prec_of<T>(ctx);
+  const Geometry& g = ctx->geo;
+  const std::string t = tname<T>();
+  std::vector<int> ca(nr), cy(nr), src(nsol), gstart(nom * nb + 1), colv(nsol);
+  std::vector<double2> Em(nsol), Ep(nsol);
+  for (int b = 0; b < nb; ++b)
+    for (int v = 0; v < nocc; ++v) { ca[b * nocc + v] = v; cy[b * nocc + v] = b; }
+  for (int o = 0; o < nom; ++o)
+    for (int b = 0; b < nb; ++b)
+      for (int v = 0; v < nocc; ++v) {
+        const int j = (o * nb + b) * nocc + v;
+        src[j] = b * nocc + v;
+        colv[j] = v;
+        Em[j] = make_double2(ctx->eps[v] + omega[o].x, omega[o].y);     // T - e_v - w
+        Ep[j] = make_double2(ctx->eps[v] - omega[o].x, -omega[o].y);    // T - e_v + w
+      }
+  for (int j = 0; j <= nom * nb; ++j) gstart[j] = j * nocc;
+  int *dca, *dcy, *dsrc, *dgs, *dcv;
+  double2 *dEm, *dEp;
+  TRY(upload_table(ctx, "mod_ca", ca, &dca));
+  TRY(upload_table(ctx, "mod_cy", cy, &dcy));
+  TRY(upload_table(ctx, "mod_src", src, &dsrc));
+  TRY(upload_table(ctx, "mod_em", Em, &dEm));
+  TRY(upload_table(ctx, "mod_ep", Ep, &dEp));
+  TRY(upload_table(ctx, "mod_gs", gstart, &dgs));
+  TRY(upload_table(ctx, "mod_cv", colv, &dcv));
+  cpx<T> *grid, *rhs, *sol;
+  TRY(getbuf(ctx, "mod_grid" + t, (size_t)std::max(nr, nsol) * ctx->N3, &grid));
+  TRY(getbuf(ctx, "mod_rhs" + t, (size_t)nr * npw, &rhs));
+  TRY(getbuf(ctx, "mod_sol" + t, (size_t)nsol * npw, &sol));
+  TRY(ensure_work(ctx, std::max(nsol, 1)));
+  launch_xpass_prod_fwd<T>(ctx->st, g, P, ctx->plan, reinterpret_cast<const cpx<T>*>(y), y_cplx ? 1 : 0, P.U, 0,
+                           1, dca, dcy, grid, nr);
+  launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, nullptr, nr, 0);
+  launch_zpass<T>(ctx->st, Z_GATHER_FWD, g, P, ctx->plan, grid, rhs, nullptr, nullptr, nullptr, nullptr, nullptr,
+                  nullptr, nullptr, nr);
+  launch_proj<T>(ctx->st, P.C, nocc, npw, rhs, nr, nullptr, ctx->work, nullptr, nullptr);
+  launch_model_scale<T>(ctx->st, npw, nsol, P.kin, rhs, dsrc, dEm, dEp, sol);
+  launch_proj<T>(ctx->st, P.C, nocc, npw, sol, nsol, nullptr, ctx->work, nullptr, nullptr);
+  launch_zpass<T>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, grid, sol, nullptr, nullptr, nullptr, nullptr, nullptr,
+                  nullptr, nullptr, nsol);
+  launch_ypass<T>(ctx->st, 1, 1, 0, g, P, ctx->plan, grid, nullptr, nsol, 0);
+  launch_xpass_inv_reduce<T>(ctx->st, g, P, ctx->plan, grid, dgs, dcv, nom * nb, -2.0 / ctx->vol,
+                             dn_cplx ? nullptr : dn, dn_cplx ? reinterpret_cast<cpx<T>*>(dn) : nullptr, 0);
+  for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
+  return launch_check(ctx, "chi0 model");
+}
+
 template <typename S>
 gw_status chi0_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, const std::vector<double2>& omega, void* dn,
                     bool dn_cplx) {
+  if (ctx->op == GW_OP_MODEL)
+    return chi0_model_core<double>(ctx, reinterpret_cast<const double*>(y), y_cplx, nb, omega,
+                                   reinterpret_cast<double*>(dn), dn_cplx);
   using T = double;
   const int npw = ctx->npw, nocc = ctx->nocc, N3 = ctx->N3;
   const int nom = (int)omega.size();
@@ -747,6 +838,9 @@ gw_status chi0_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, const std::
   // solver's FP64 residual P_c (b - A x) removes that remnant
   launch_proj<double>(ctx->st, ctx->P64.C, nocc, npw, rhs64, nr, nullptr, ctx->work, nullptr, nullptr);
   TRY(launch_check(ctx, "rhs"));
+  double2* sol64;
+  const int nsol = nom * nb * nocc;
+  TRY(getbuf(ctx, "sol64", (size_t)nsol * npw, &sol64));
   // -- solver columns
   std::vector<int> src, s0, s1;
   std::vector<double2> E;
@@ -770,7 +864,6 @@ gw_status chi0_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, const std::
       }
   }
   const int ncol = (int)src.size();
-  const int nsol = (int)s0.size();
   int *dsrc, *ds0, *ds1;
   double2* dE;
   TRY(upload(ctx, "col_src", src, &dsrc));
@@ -779,19 +872,29 @@ gw_status chi0_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, const std::
   TRY(upload(ctx, "col_E", E, &dE));
   double* dtk = nullptr;
   if (ctx->precond) TRY(upload(ctx, "col_tk", tk, &dtk));
-  double2 *bcol, *xcol, *sol64;
+  double2 *bcol, *xcol;
   TRY(getbuf(ctx, "bcol", (size_t)ncol * npw, &bcol));
   TRY(getbuf(ctx, "xcol", (size_t)ncol * npw, &xcol));
-  TRY(getbuf(ctx, "sol64", (size_t)nsol * npw, &sol64));
   launch_gather_rows<double, double>(ctx->st, npw, ncol, rhs64, dsrc, bcol);
   TRY(solve<S>(ctx, ncol, bcol, dE, xcol, qmr, dtk));
   // -- combine: x^- + x^+, or 2 x at omega = 0 (x^- = x^+)
   launch_combine(ctx->st, npw, nsol, xcol, ds0, ds1, 1.0, 2.0, sol64);
-  // -- density reduction
+  return chi0_reduce(ctx, sol64, nb, nom, dn, dn_cplx);
+}
+
+// density reduction of Eq. P1: dn_{o,b} = -(2/Omega) sum_v u_v IFFT(sol_{o,b,v}),
+// sol [nom][nb][nocc][npw] (x^- + x^+ per occupied state)
+gw_status chi0_reduce(gw_ctx* ctx, const double2* sol64, int nb, int nom, void* dn, bool dn_cplx) {
+  using T = double;
+  const int nocc = ctx->nocc, N3 = ctx->N3;
+  const int nsol = nom * nb * nocc;
+  auto& P = ctx->P64;
+  const Geometry& g = ctx->geo;
+  const std::string t = tname<T>();
   cpx<T>* gd;
   TRY(getbuf(ctx, "g_dn" + t, (size_t)nsol * N3, &gd));
-  launch_zpass<T>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, gd, sol64, nullptr, nullptr, nullptr, nullptr, nullptr,
-                  nullptr, nullptr, nsol);
+  launch_zpass<T>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, gd, const_cast<double2*>(sol64), nullptr, nullptr,
+                  nullptr, nullptr, nullptr, nullptr, nullptr, nsol);
   launch_ypass<T>(ctx->st, 1, 1, 0, g, P, ctx->plan, gd, nullptr, nsol, 0);
   std::vector<int> gstart(nom * nb + 1), colv(nsol);
   for (int j = 0; j <= nom * nb; ++j) gstart[j] = j * nocc;
@@ -856,6 +959,28 @@ gw_status eps_core(gw_ctx* ctx, const void* x, bool x_cplx, int nb, const std::v
   if (!out_cplx) {
     const double* x64 = reinterpret_cast<const double*>(x);
     double* out64 = reinterpret_cast<double*>(out);
+    if (ctx->op == GW_OP_MODEL && std::is_same<S, float>::value) {
+      // model operator, mixed: the transforms and projections in FP32, the
+      // fields at the boundary in FP64 (eps~ x = x - z with z from FP32)
+      float *x32, *y32, *dn32;
+      const size_t n = (size_t)nb * N3;
+      TRY(getbuf(ctx, "m32_x", n, &x32));
+      TRY(getbuf(ctx, "m32_y", n, &y32));
+      TRY(getbuf(ctx, "m32_dn", (size_t)nom * n, &dn32));
+      launch_cast(ctx->st, n, x64, x32);
+      if (chi0_only) {
+        TRY(chi0_model_core<float>(ctx, x32, false, nb, omega, dn32, false));
+        launch_cast(ctx->st, (size_t)nom * n, dn32, out64);
+        return launch_check(ctx, "chi0 model mixed");
+      }
+      TRY(sqrtv<float>(ctx, x32, nb, y32, nullptr));
+      TRY(chi0_model_core<float>(ctx, y32, false, nb, omega, dn32, false));
+      for (int k = 0; k < nom; ++k) {
+        TRY(sqrtv<float>(ctx, dn32 + (size_t)k * n, nb, y32, nullptr));
+        launch_sub_mixed(ctx->st, n, x64, y32, out64 + (size_t)k * n);
+      }
+      return launch_check(ctx, "eps model mixed");
+    }
     if (chi0_only) return chi0_core<S>(ctx, x64, false, nb, omega, out64, false);
     double *y, *dn;
     TRY(getbuf(ctx, "eps_y", (size_t)nb * N3, &y));
@@ -1865,6 +1990,8 @@ gw_status gw_epsinv_elements(gw_ctx* ctx, const double* alpha, const double* bet
 gw_status gw_grad_vloc(gw_ctx* ctx, const double* phi, int k, double* s, double* grad, gw_prec prec, int dev) {
   TRY(begin(ctx));
   TRY(need_occ(ctx));
+  if (ctx->op != GW_OP_STERNHEIMER)
+    return fail(ctx, GW_E_UNSUPPORTED, "the gradient is of the Sternheimer operator; set GW_OP_STERNHEIMER");
   if (!phi || !s || !grad || k < 1) return fail(ctx, GW_E_ARG, "bad arguments");
   if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_E_ARG, "bad precision");
   for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
@@ -1902,6 +2029,94 @@ gw_status gw_set_solver(gw_ctx* ctx, double tol, double tol_inner, int max_iter,
   if (tol_inner > 0) ctx->tol_inner = tol_inner;
   if (max_iter > 0) ctx->max_iter = max_iter;
   if (max_outer > 0) ctx->max_outer = max_outer;
+  return GW_OK;
+}
+
+gw_status gw_set_operator(gw_ctx* ctx, int op) {
+  if (!ctx) return GW_E_ARG;
+  if (op != GW_OP_STERNHEIMER && op != GW_OP_MODEL)
+    return fail(ctx, GW_E_ARG, "operator must be GW_OP_STERNHEIMER (0) or GW_OP_MODEL (1)");
+  ctx->op = op;
+  return GW_OK;
+}
+
+// Eq. subs_epsilon: <phi_i|eps~^-1 - 1|phi_j> = a_i^T (T^-1 - M^-1) a_j + am_i^T (Tm^-1 - 1) am_j
+// with a = <Q|phi>, am = <Qm|phi>, M = <Q|eps~_model Q> (model applied to the
+// exact basis), T and Tm the tridiagonal Lanczos matrices of the two bases.
+gw_status gw_epsinv_split(gw_ctx* ctx, const double* phi, int m, const double* basis, const double* alpha,
+                          const double* beta, int k, const double* basis_m, const double* alpha_m,
+                          const double* beta_m, int k_m, double omega, double* out, int dev) {
+  TRY(begin(ctx));
+  TRY(need_occ(ctx));
+  if (!phi || !basis || !alpha || !basis_m || !alpha_m || !out || m < 1 || m > 64 || k < 1 || k_m < 1 ||
+      k > 2048 || k_m > 4096 || (k > 1 && !beta) || (k_m > 1 && !beta_m))
+    return fail(ctx, GW_E_ARG, "bad arguments");
+  if (!std::isfinite(omega)) return fail(ctx, GW_E_NONFINITE, "non-finite omega");
+  for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
+  const int N3 = ctx->N3;
+  const double wgt = ctx->vol / N3;
+  const size_t fb = (size_t)N3 * sizeof(double);
+  const void *ph, *Qv, *Qmv, *al, *alm, *be = nullptr, *bem = nullptr;
+  TRY(stage_in(ctx, "sp_phi", phi, m * fb, dev, &ph));
+  TRY(stage_in(ctx, "sp_Q", basis, k * fb, dev, &Qv));
+  TRY(stage_in(ctx, "sp_Qm", basis_m, k_m * fb, dev, &Qmv));
+  TRY(stage_in(ctx, "sp_al", alpha, k * sizeof(double), dev, &al));
+  TRY(stage_in(ctx, "sp_alm", alpha_m, k_m * sizeof(double), dev, &alm));
+  if (k > 1) TRY(stage_in(ctx, "sp_be", beta, (k - 1) * sizeof(double), dev, &be));
+  if (k_m > 1) TRY(stage_in(ctx, "sp_bem", beta_m, (k_m - 1) * sizeof(double), dev, &bem));
+  const double* Q = reinterpret_cast<const double*>(Qv);
+  const double* Qm = reinterpret_cast<const double*>(Qmv);
+  const double* P = reinterpret_cast<const double*>(ph);
+  double *a, *am, *EQ, *Mt, *Ti, *Tmi, *d, *l;
+  double2 *Mc, *Mi;
+  int* stat;
+  const int nbc = std::min(k, 16);
+  TRY(getbuf(ctx, "sp_a", (size_t)m * k, &a));
+  TRY(getbuf(ctx, "sp_am", (size_t)m * k_m, &am));
+  TRY(getbuf(ctx, "sp_EQ", (size_t)nbc * N3, &EQ));
+  TRY(getbuf(ctx, "sp_Mt", (size_t)k * k, &Mt));
+  TRY(getbuf(ctx, "sp_Ti", (size_t)k * k, &Ti));
+  TRY(getbuf(ctx, "sp_Tmi", (size_t)k_m * k_m, &Tmi));
+  TRY(getbuf(ctx, "sp_d", std::max(k, k_m), &d));
+  TRY(getbuf(ctx, "sp_l", std::max(k, k_m), &l));
+  TRY(getbuf(ctx, "sp_Mc", (size_t)k * k, &Mc));
+  TRY(getbuf(ctx, "sp_Mi", (size_t)k * k, &Mi));
+  TRY(getbuf(ctx, "sp_stat", 3, &stat));
+  // the model operator in the exact basis: Mt[j][i] = <q_i|eps~_model q_j>
+  const int op0 = ctx->op;
+  ctx->op = GW_OP_MODEL;
+  const std::vector<double2> om{make_double2(omega, 0.0)};
+  for (int j0 = 0; j0 < k; j0 += nbc) {
+    const int nb = std::min(nbc, k - j0);
+    gw_status st = eps_core<double>(ctx, Q + (size_t)j0 * N3, false, nb, om, EQ, false);
+    if (st != GW_OK) { ctx->op = op0; return st; }
+    TRY(ensure_work(ctx, std::max(k, k_m) + 1));
+    for (int j = 0; j < nb; ++j)
+      launch_gemv_t(ctx->st, Q, N3, N3, EQ + (size_t)j * N3, wgt, k, ctx->work, Mt + (size_t)(j0 + j) * k);
+  }
+  ctx->op = op0;
+  // coefficients of the fields in both bases
+  TRY(ensure_work(ctx, std::max(k, k_m) + 1));
+  for (int i = 0; i < m; ++i) {
+    launch_gemv_t(ctx->st, Q, N3, N3, P + (size_t)i * N3, wgt, k, ctx->work, a + (size_t)i * k);
+    launch_gemv_t(ctx->st, Qm, N3, N3, P + (size_t)i * N3, wgt, k_m, ctx->work, am + (size_t)i * k_m);
+  }
+  // the three inverses and the two quadratic forms
+  launch_tridiag_inv(ctx->st, k, reinterpret_cast<const double*>(al), reinterpret_cast<const double*>(be), d, l,
+                     Ti, stat);
+  launch_tridiag_inv(ctx->st, k_m, reinterpret_cast<const double*>(alm), reinterpret_cast<const double*>(bem), d,
+                     l, Tmi, stat + 1);
+  launch_to_cplx(ctx->st, (size_t)k * k, Mt, Mc);
+  launch_cinv(ctx->st, k, Mc, Mi, stat + 2);
+  void* op;
+  TRY(stage_out(ctx, "sp_out", out, (size_t)m * m * sizeof(double), dev, &op));
+  launch_split_form(ctx->st, m, k, k_m, a, Ti, Mi, am, Tmi, reinterpret_cast<double*>(op));
+  TRY(launch_check(ctx, "epsinv_split"));
+  CK(cudaMemcpyAsync(ctx->host_pin, stat, 3 * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  TRY(copy_back(ctx, out, op, (size_t)m * m * sizeof(double), dev));
+  TRY(sync(ctx, "epsinv_split"));
+  if (ctx->host_pin[0] || ctx->host_pin[1] || ctx->host_pin[2])
+    return fail(ctx, GW_E_BREAKDOWN, "singular matrix in the split (tridiagonal or model Gram)");
   return GW_OK;
 }
 

@@ -750,6 +750,121 @@ void launch_combine(cudaStream_t s, int npw, int nout, const double2* in, const 
   k_combine<<<g, kLT, 0, s>>>(npw, in, src0, src1, w_pair, w_single, out);
 }
 
+// Kinetic denominators of the model operator (Sec. Dielectric model, Eq.
+// model_eq): out[j][G] = (1/(|G|^2/2 - Em_j) + 1/(|G|^2/2 - Ep_j)) in[src_j][G]
+// with Em = e_v + omega, Ep = e_v - omega (complex).  A reciprocal whose
+// denominator is exactly zero is taken as 0 (the pseudo-inverse of the
+// diagonal; such an entry of a projected right-hand side is zero).
+__device__ __forceinline__ double2 pinv_shift(double t, double2 e) {
+  const double dr = t - e.x, di = -e.y;
+  const double d2 = dr * dr + di * di;
+  if (d2 == 0.0) return make_double2(0.0, 0.0);
+  const double r = 1.0 / d2;
+  return make_double2(dr * r, -di * r);
+}
+
+// (the weights in FP64, the product in the precision T of the vectors)
+template <typename T>
+__global__ void k_model_scale(int npw, const T* __restrict__ kin, const cpx<T>* __restrict__ in,
+                              const int* __restrict__ src, const double2* __restrict__ Em,
+                              const double2* __restrict__ Ep, cpx<T>* __restrict__ out) {
+  const int j = blockIdx.y;
+  const int a = src[j];
+  const double2 em = Em[j], ep = Ep[j];
+  for (int G = blockIdx.x * blockDim.x + threadIdx.x; G < npw; G += gridDim.x * blockDim.x) {
+    const double t = (double)kin[G];
+    const double2 w = cadd(pinv_shift(t, em), pinv_shift(t, ep));
+    out[(size_t)j * npw + G] = cmul(from_d<T>(w), in[(size_t)a * npw + G]);
+  }
+}
+
+template <typename T>
+void launch_model_scale(cudaStream_t s, int npw, int nout, const T* kin, const cpx<T>* in, const int* src,
+                        const double2* Em, const double2* Ep, cpx<T>* out) {
+  if (nout == 0) return;
+  dim3 g((npw + kLT - 1) / kLT, nout);
+  ++g_launches;
+  k_model_scale<T><<<g, kLT, 0, s>>>(npw, kin, in, src, Em, Ep, out);
+}
+template void launch_model_scale<double>(cudaStream_t, int, int, const double*, const double2*, const int*,
+                                         const double2*, const double2*, double2*);
+template void launch_model_scale<float>(cudaStream_t, int, int, const float*, const float2*, const int*,
+                                        const double2*, const double2*, float2*);
+
+// precision changes at the boundary of an FP32 pipeline; out = x - z (FP64 result)
+__global__ void k_cast_df(size_t n, const double* __restrict__ x, float* __restrict__ y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+__global__ void k_cast_fd(size_t n, const float* __restrict__ x, double* __restrict__ y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+__global__ void k_sub_fd(size_t n, const double* __restrict__ x, const float* __restrict__ z,
+                         double* __restrict__ y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = x[i] - (double)z[i];
+}
+static int elem_blocks(size_t n) { return (int)std::min<size_t>((n + kLT - 1) / kLT, 152 * 8); }
+void launch_cast(cudaStream_t s, size_t n, const double* x, float* y) {
+  ++g_launches;
+  k_cast_df<<<elem_blocks(n), kLT, 0, s>>>(n, x, y);
+}
+void launch_cast(cudaStream_t s, size_t n, const float* x, double* y) {
+  ++g_launches;
+  k_cast_fd<<<elem_blocks(n), kLT, 0, s>>>(n, x, y);
+}
+void launch_sub_mixed(cudaStream_t s, size_t n, const double* x, const float* z, double* y) {
+  ++g_launches;
+  k_sub_fd<<<elem_blocks(n), kLT, 0, s>>>(n, x, z, y);
+}
+
+// Eq. subs_epsilon in the two bases: out[i][j] = sum_ab a_ia (Ti_ab - (M^-1)_ab) a_jb
+// + sum_ab am_ia (Tmi_ab - delta_ab) am_jb; one block per (i, j), rows a over
+// the threads, then an ordered block sum.  Mi holds the inverse of M^T, i.e.
+// (M^-1)_ab = Re Mi[b][a]; the matrices are read column-wise (X[b][a] for row a)
+// so that the threads' loads are contiguous (Ti and Tmi are symmetric).
+__global__ void __launch_bounds__(kLT)
+k_split_form(int m, int k, int km, const double* __restrict__ a, const double* __restrict__ Ti,
+             const double2* __restrict__ Mi, const double* __restrict__ am, const double* __restrict__ Tmi,
+             double* __restrict__ out) {
+  const int i = blockIdx.x, j = blockIdx.y;
+  const double* ai = a + (size_t)i * k;
+  const double* aj = a + (size_t)j * k;
+  const double* bi = am + (size_t)i * km;
+  const double* bj = am + (size_t)j * km;
+  double acc = 0.0;
+  for (int r = threadIdx.x; r < k; r += blockDim.x) {
+    double t = 0.0;
+    for (int c = 0; c < k; ++c) t += (Ti[(size_t)c * k + r] - Mi[(size_t)c * k + r].x) * aj[c];
+    acc += ai[r] * t;
+  }
+  for (int r = threadIdx.x; r < km; r += blockDim.x) {
+    double t = -bj[r];
+    for (int c = 0; c < km; ++c) t += Tmi[(size_t)c * km + r] * bj[c];
+    acc += bi[r] * t;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) out[(size_t)i * m + j] = acc;
+}
+
+void launch_split_form(cudaStream_t s, int m, int k, int km, const double* a, const double* Ti,
+                       const double2* Mi, const double* am, const double* Tmi, double* out) {
+  ++g_launches;
+  k_split_form<<<dim3(m, m), kLT, 0, s>>>(m, k, km, a, Ti, Mi, am, Tmi, out);
+}
+
+// real -> complex square matrix (imaginary part zero)
+__global__ void k_to_cplx(size_t n, const double* __restrict__ x, double2* __restrict__ y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = make_double2(x[i], 0.0);
+}
+
+void launch_to_cplx(cudaStream_t s, size_t n, const double* x, double2* y) {
+  ++g_launches;
+  k_to_cplx<<<(int)std::min<size_t>((n + kLT - 1) / kLT, 152 * 8), kLT, 0, s>>>(n, x, y);
+}
+
 // gather rows: out[j] = in[idx[j]] (sphere vectors, with precision conversion)
 template <typename T, typename U>
 __global__ void k_gather_rows(int npw, const cpx<U>* __restrict__ in, const int* __restrict__ idx,

@@ -94,6 +94,18 @@ void launch_residual(cudaStream_t s, int npw, int ncol, const double2* b, double
                      int nocc = 0, const double2* cb = nullptr, const double2* cax = nullptr);
 void launch_combine(cudaStream_t s, int npw, int nout, const double2* in, const int* src0, const int* src1,
                     double w_pair, double w_single, double2* out);
+// Eq. model_eq: out[j] = (pinv(T - Em_j) + pinv(T - Ep_j)) in[src_j] on the sphere
+template <typename T>
+void launch_model_scale(cudaStream_t s, int npw, int nout, const T* kin, const cpx<T>* in, const int* src,
+                        const double2* Em, const double2* Ep, cpx<T>* out);
+void launch_cast(cudaStream_t s, size_t n, const double* x, float* y);
+void launch_cast(cudaStream_t s, size_t n, const float* x, double* y);
+void launch_sub_mixed(cudaStream_t s, size_t n, const double* x, const float* z, double* y);   // y = x - z
+// Eq. subs_epsilon: out[m][m] from the coefficients a [m][k], am [m][km] and the
+// inverses Ti (exact basis), Mi (model in the exact basis, complex), Tmi (model basis)
+void launch_split_form(cudaStream_t s, int m, int k, int km, const double* a, const double* Ti,
+                       const double2* Mi, const double* am, const double* Tmi, double* out);
+void launch_to_cplx(cudaStream_t s, size_t n, const double* x, double2* y);
 template <typename T, typename U>
 void launch_gather_rows(cudaStream_t s, int npw, int nout, const cpx<U>* in, const int* idx, cpx<T>* out);
 void launch_gemv_t(cudaStream_t s, const double* Q, size_t ld, int n, const double* w, double wgt, int k,
