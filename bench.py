@@ -12,6 +12,11 @@ library's own H application inside a block LOBPCG (input preparation, not
 timed).  Inside a step the 16-column working set (~14 MB) stays in L2; L2 is
 flushed between timed steps by writing a 512 MB buffer.
 
+Beside the headline, ``model_operator`` times the same Lanczos run on the
+model dielectric operator of Sec. Dielectric model (Eq. model_eq, H -> T:
+one kinetic division per Sternheimer solve) on the same cell and start
+vector (``--model-k 0`` skips it).
+
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 instead, on a bounded sample of the same workload.
 """
@@ -218,6 +223,15 @@ def class_bytes(miller, N, npw, nocc, s):
     return col, shared, dict(D=D, P0=P0)
 
 
+def model_bytes(N, npw, nocc, s):
+    """Algorithmic bytes of one model eps~ application (Eq. model_eq) to one
+    field, s = bytes per complex value: the occupied grids u_v read twice (the
+    products psi_v* y before the projector, the reduction sum_v u_v f_v after
+    it), the occupied coefficients read four times (two projectors, each a
+    Gram pass and an update), the field read and eps~ y written (FP64)."""
+    return 2 * nocc * N ** 3 * s + 4 * nocc * npw * s + 2 * N ** 3 * 8
+
+
 def src_hash():
     h = hashlib.sha256()
     for f in ("fft.cuh", "kernels_fft.cu", "kernels_linalg.cu", "gw_common.cuh", "kernels_cg.cu", "pcg.cuh"):
@@ -403,6 +417,70 @@ def run_gpu(args):
     e2e = dict(value=world * K / (te2e / 1e3), unit=UNIT, h2d_bytes_per_step=ng * 8,
                d2h_bytes_per_step=(2 * K - 1) * 8)
 
+    # --- model operator (Eq. model_eq) on the same cell and start vector
+    model = None
+    if args.model_k > 0:
+        Km = min(args.model_k, K)
+        cell.set_operator(gw.GW_OP_MODEL)
+
+        def mstep(pr, k=Km):
+            gw.gw_lanczos(cell.ctx, start, k, 0.0, alpha, beta, Q, pr)
+
+        for _ in range(args.warmup):
+            mstep(prec)
+        mtimes = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.nvtx.range_push("model")
+            e0.record(stream)
+            mstep(prec)
+            e1.record(stream)
+            torch.cuda.nvtx.range_pop()
+            e1.synchronize()
+            mtimes.append(e0.elapsed_time(e1))
+        am = alpha[:Km].cpu().numpy().copy()
+        bm = beta[:Km - 1].cpu().numpy().copy()
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mstep(gw.GW_FP64)
+        e1.record(stream)
+        e1.synchronize()
+        tm64 = e0.elapsed_time(e1)
+        a64m = alpha[:Km].cpu().numpy()
+        b64m = beta[:Km - 1].cpu().numpy()
+        # one application to one field, alone (no Lanczos), for the roofline
+        xf = Q[:1].clone()
+        yf = torch.empty((1, 1, ng), dtype=torch.float64, device=dev)
+        gw.gw_apply_eps(cell.ctx, xf, [0.0], yf, prec)
+        napp = 20
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(napp):
+            gw.gw_apply_eps(cell.ctx, xf, [0.0], yf, prec)
+        e1.record(stream)
+        e1.synchronize()
+        t_app = e0.elapsed_time(e1) / napp
+        cell.set_operator(gw.GW_OP_STERNHEIMER)
+        mb = model_bytes(c.N, cell.npw, c.n_occ, s)
+        ach = mb / (t_app / 1e3) / 1e9
+        mval, _ = replica_rate(float(sum(mtimes)), args.steps, Km, world,
+                               torch_group_max(dev) if world > 1 else (lambda x: x))
+        model = dict(
+            value=mval, unit=UNIT, lanczos_steps=Km, ms_per_step=float(sum(mtimes)) / args.steps,
+            precision=args.prec, speedup_vs_sternheimer=mval / value, fp64_value=Km / (tm64 / 1e3),
+            mixed_vs_fp64_rel_err=dict(alpha=float(np.abs(am - a64m).max() / np.abs(a64m).max()),
+                                       beta=float(np.abs(bm - b64m).max() / np.abs(b64m).max()) if Km > 1 else 0.0),
+            occupied_energies_above_zero=int((eps[:c.n_occ] > 0).sum()),
+            roofline=dict(bound="hbm", kernel="one model eps~ application (all its kernels)", achieved=ach,
+                          peak=hbm, unit="GB/s", frac=ach / hbm, peak_kind=hbm_kind, traffic=None,
+                          alg_bytes_per_apply=mb, ms_per_apply=t_app))
+
     if rank == 0:
         line = dict(
             metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -418,6 +496,7 @@ def run_gpu(args):
                         column_iterations_per_step=it_cols / args.steps, geometry=geo),
             roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
             clocks=clk.summary(), fp64=fp64, profile_ms={k: v[0] for k, v in prof.items() if v[1]},
+            model_operator=model,
         )
         print(json.dumps(line))
     cell.close()
@@ -439,6 +518,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-class", default="persistent_cg")
+    ap.add_argument("--model-k", type=int, default=100,
+                    help="Lanczos steps timed on the model operator of Eq. model_eq (0: skip)")
     ap.add_argument("--deflation", type=int, default=0,
                     help="lowest conduction states handed to the solvers as a deflation block (0: none)")
     args = ap.parse_args()

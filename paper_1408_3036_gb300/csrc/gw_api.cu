@@ -797,8 +797,12 @@ gw_status chi0_model_core(gw_ctx* ctx, const T* y, bool y_cplx, int nb, const st
   launch_zpass<T>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, grid, sol, nullptr, nullptr, nullptr, nullptr, nullptr,
                   nullptr, nullptr, nsol);
   launch_ypass<T>(ctx->st, 1, 1, 0, g, P, ctx->plan, grid, nullptr, nsol, 0);
+  cpx<T>* parts;
+  const size_t nparts = (size_t)kMaxReduceParts * ctx->N3;   // enough whenever a split pays (few groups)
+  TRY(getbuf(ctx, "mod_parts" + t, nparts, &parts));
   launch_xpass_inv_reduce<T>(ctx->st, g, P, ctx->plan, grid, dgs, dcv, nom * nb, -2.0 / ctx->vol,
-                             dn_cplx ? nullptr : dn, dn_cplx ? reinterpret_cast<cpx<T>*>(dn) : nullptr, 0);
+                             dn_cplx ? nullptr : dn, dn_cplx ? reinterpret_cast<cpx<T>*>(dn) : nullptr, 0, parts,
+                             nparts, nocc);
   for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
   return launch_check(ctx, "chi0 model");
 }
@@ -821,8 +825,8 @@ gw_status chi0_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, const std::
   for (int b = 0; b < nb; ++b)
     for (int v = 0; v < nocc; ++v) { ca[b * nocc + v] = v; cy[b * nocc + v] = b; }
   int *dca, *dcy;
-  TRY(upload(ctx, "rhs_ca", ca, &dca));
-  TRY(upload(ctx, "rhs_cy", cy, &dcy));
+  TRY(upload_table(ctx, "rhs_ca", ca, &dca));
+  TRY(upload_table(ctx, "rhs_cy", cy, &dcy));
   cpx<T>* grid;
   TRY(getbuf(ctx, "g_rhs" + t, (size_t)nr * N3, &grid));
   double2* rhs64;
@@ -866,12 +870,12 @@ gw_status chi0_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, const std::
   const int ncol = (int)src.size();
   int *dsrc, *ds0, *ds1;
   double2* dE;
-  TRY(upload(ctx, "col_src", src, &dsrc));
-  TRY(upload(ctx, "col_s0", s0, &ds0));
-  TRY(upload(ctx, "col_s1", s1, &ds1));
-  TRY(upload(ctx, "col_E", E, &dE));
+  TRY(upload_table(ctx, "col_src", src, &dsrc));
+  TRY(upload_table(ctx, "col_s0", s0, &ds0));
+  TRY(upload_table(ctx, "col_s1", s1, &ds1));
+  TRY(upload_table(ctx, "col_E", E, &dE));
   double* dtk = nullptr;
-  if (ctx->precond) TRY(upload(ctx, "col_tk", tk, &dtk));
+  if (ctx->precond) TRY(upload_table(ctx, "col_tk", tk, &dtk));
   double2 *bcol, *xcol;
   TRY(getbuf(ctx, "bcol", (size_t)ncol * npw, &bcol));
   TRY(getbuf(ctx, "xcol", (size_t)ncol * npw, &xcol));
@@ -900,11 +904,14 @@ gw_status chi0_reduce(gw_ctx* ctx, const double2* sol64, int nb, int nom, void* 
   for (int j = 0; j <= nom * nb; ++j) gstart[j] = j * nocc;
   for (int j = 0; j < nsol; ++j) colv[j] = j % nocc;
   int *dgs, *dcv;
-  TRY(upload(ctx, "dn_gs", gstart, &dgs));
-  TRY(upload(ctx, "dn_cv", colv, &dcv));
+  TRY(upload_table(ctx, "dn_gs", gstart, &dgs));
+  TRY(upload_table(ctx, "dn_cv", colv, &dcv));
+  cpx<T>* parts;
+  const size_t nparts = (size_t)kMaxReduceParts * N3;   // enough whenever a split pays (few groups)
+  TRY(getbuf(ctx, "dn_parts" + t, nparts, &parts));
   launch_xpass_inv_reduce<T>(ctx->st, g, P, ctx->plan, gd, dgs, dcv, nom * nb, -2.0 / ctx->vol,
                              dn_cplx ? nullptr : reinterpret_cast<double*>(dn),
-                             dn_cplx ? reinterpret_cast<double2*>(dn) : nullptr, 0);
+                             dn_cplx ? reinterpret_cast<double2*>(dn) : nullptr, 0, parts, nparts, nocc);
   return launch_check(ctx, "chi0");
 }
 

@@ -129,13 +129,13 @@ __device__ __forceinline__ T tpa(T x) {
 // the rounding of a plain loop -- with the loads of eight records in flight
 // (the last block of a reduction otherwise waits one memory round trip per
 // record).
-template <int W>
-__device__ __forceinline__ void sum_records(const double* __restrict__ p, int n, size_t stride, double* s) {
+template <int W, typename X = double>
+__device__ __forceinline__ void sum_records(const X* __restrict__ p, int n, size_t stride, X* s) {
 #pragma unroll
-  for (int w = 0; w < W; ++w) s[w] = 0.0;
+  for (int w = 0; w < W; ++w) s[w] = (X)0;
   int k = 0;
   for (; k + 8 <= n; k += 8) {
-    double t[8][W];
+    X t[8][W];
 #pragma unroll
     for (int u = 0; u < 8; ++u)
 #pragma unroll
@@ -202,10 +202,14 @@ template <typename T>
 void launch_xpass_prod_fwd(cudaStream_t s, const Geometry& g, const Prec<T>& P, const FftPlan& pl,
                            const cpx<T>* Y, int y_complex, const cpx<T>* A, int a_per_col, int conj_a,
                            const int* col_a, const int* col_y, cpx<T>* out, int ncol);
-// dn[o] += scale * sum_{v} U[v] * IFFT_x(grid[col])   for col in group o (last pass of inverse)
+// dn[o] += scale * sum_{v} U[v] * IFFT_x(grid[col])   for col in group o (last pass of inverse).
+// scratch (optional, scratch_elems complex entries) lets the sum over the at
+// most max_cols columns of a group be split over several CTAs.
+constexpr int kMaxReduceParts = 8;
 template <typename T>
 void launch_xpass_inv_reduce(cudaStream_t s, const Geometry& g, const Prec<T>& P, const FftPlan& pl,
                              const cpx<T>* grid, const int* group_start, const int* col_v, int ngroups,
-                             double scale, T* out_real, cpx<T>* out_cplx, int accumulate);
+                             double scale, T* out_real, cpx<T>* out_cplx, int accumulate,
+                             cpx<T>* scratch = nullptr, size_t scratch_elems = 0, int max_cols = 1);
 
 }  // namespace gw

@@ -115,8 +115,29 @@ __device__ __forceinline__ void staged_copy(int n, Ld ld, St st) {
   }
 }
 
+// Per column c: s[c] = sum of rp[c][0 .. n), z[c] = sum of zp[c][0 .. n), one
+// warp per column (lane l adds records l, l + 32, ... in order, then a fixed
+// shuffle tree; lane 0's value is kept), so that every CTA gets the same bits.
+__device__ __forceinline__ void column_sums(const double* __restrict__ rp, const double* __restrict__ zp, int n,
+                                            int ncol, double* s, double* z) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = warp; c < ncol; c += nw) {
+    double a = 0.0, b = 0.0;
+    for (int k = lane; k < n; k += 32) {
+      a += rp[(size_t)c * n + k];
+      b += zp[(size_t)c * n + k];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) { s[c] = a; z[c] = b; }
+  }
+  __syncthreads();
+}
+
 struct PcgLayout {
-  size_t dbl, ints, red, coef, tw, A, B, total;
+  size_t dbl, ints, red, coef, tv, tw, A, B, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -124,10 +145,11 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 __host__ __device__ inline PcgLayout pcg_layout(int N, int ncol, int nocc, int vsize) {
   PcgLayout L;
   L.dbl = 0;
-  L.ints = align16(L.dbl + (size_t)6 * ncol * sizeof(double));
+  L.ints = align16(L.dbl + (size_t)8 * ncol * sizeof(double));
   L.red = align16(L.ints + (size_t)(4 * ncol + N) * sizeof(int));
   L.coef = align16(L.red + 32 * sizeof(double));
-  L.tw = align16(L.coef + (size_t)(2 * nocc + 1) * 2 * sizeof(double));
+  L.tv = align16(L.coef + (size_t)(2 * nocc + 1) * 2 * sizeof(double));
+  L.tw = align16(L.tv + align16((size_t)(ncol + 1) * (vsize / 2)) + (size_t)2 * nocc * vsize);
   L.A = align16(L.tw + (size_t)N * vsize);
   L.B = align16(L.A + (size_t)N * (N + 1) * vsize);
   L.total = align16(L.B + (size_t)N * (N + 1) * vsize);
@@ -149,6 +171,8 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
   double* st_beta = st_stop + ncol;
   double* st_rz = st_beta + ncol;                             // r^H K r
   double* st_best = st_rz + ncol;                             // stagnation guard
+  double* st_s = st_best + ncol;                              // this iteration's |r|^2 and r^H K r
+  double* st_z = st_s + ncol;
   int* st_act = reinterpret_cast<int*>(smem_raw + L.ints);
   int* st_it = st_act + ncol;
   int* st_flag = st_it + ncol;
@@ -156,12 +180,18 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
   int* rowmap = st_itb + ncol;                                // [N]
   double* red = reinterpret_cast<double*>(smem_raw + L.red);  // [32] block sums
   double2* coef = reinterpret_cast<double2*>(smem_raw + L.coef);  // [2 nocc + 1] plane sums
+  T* st_rtk = reinterpret_cast<T*>(smem_raw + L.tv);          // [ncol] 1 / T_ref (0: no preconditioner)
+  T* s_al = st_rtk + ncol;                                    // alpha of the current column
+  V* coefT = reinterpret_cast<V*>(smem_raw + L.tv + align16((size_t)(ncol + 1) * sizeof(T)));   // [2 nocc]
+  T* redT = reinterpret_cast<T*>(red);
   V* stw = reinterpret_cast<V*>(smem_raw + L.tw);             // [N]
   V* A = reinterpret_cast<V*>(smem_raw + L.A);                // [N][LDp]
   V* B = reinterpret_cast<V*>(smem_raw + L.B);                // [N][LDp]
   __shared__ double bcast;
 
   for (int k = threadIdx.x; k < N; k += blockDim.x) stw[k] = a.tw[k];
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) st_rtk[c] = a.tk ? (T)1 / (T)a.tk[c] : (T)0;
+  __syncthreads();
   const unsigned nblk = gridDim.x;
   const int npl = g.nplanes;
 
@@ -170,28 +200,26 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
     const int c = task / a.nchunk, ch = task - c * a.nchunk;
     const bool on = !a.outer_active || a.outer_active[c];
     const int g0 = ch * a.chunk, g1 = min(a.npw, g0 + a.chunk);
-    const T rtk = a.tk ? (T)(1.0 / a.tk[c]) : (T)0;
-    double acc = 0.0, accz = 0.0;
+    const T rtk = st_rtk[c];
+    T acc = 0, accz = 0;
     for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
       const size_t i = (size_t)c * a.npw + G;
       const V bv = on ? from_d<T>(a.b64[i]) : mk<T>(0, 0);
       a.r[i] = bv;
       a.x[i] = mk<T>(0, 0);
-      const double2 bd = to_d(bv);
-      const double n2 = bd.x * bd.x + bd.y * bd.y;
+      const T n2 = bv.x * bv.x + bv.y * bv.y;
       acc += n2;
-      accz += (rtk != (T)0 ? (double)tpa<T>(a.kin[G] * rtk) : 1.0) * n2;
+      accz += (rtk != (T)0 ? tpa<T>(a.kin[G] * rtk) : (T)1) * n2;
     }
-    acc = dsum_block<T>(acc, red);
-    if (threadIdx.x == 0) a.rpart[(size_t)c * a.nchunk + ch] = acc;
-    accz = dsum_block<T>(accz, red);
-    if (threadIdx.x == 0) a.zpart[(size_t)c * a.nchunk + ch] = accz;
+    acc = tsum_block<T>(acc, redT);
+    if (threadIdx.x == 0) a.rpart[(size_t)c * a.nchunk + ch] = (double)acc;
+    accz = tsum_block<T>(accz, redT);
+    if (threadIdx.x == 0) a.zpart[(size_t)c * a.nchunk + ch] = (double)accz;
   }
   if (!grid_barrier(a.bar, a.err, nblk)) return;
+  column_sums(a.rpart, a.zpart, a.nchunk, ncol, st_s, st_z);
   for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
-    double s, z;
-    sum_records<1>(a.rpart + (size_t)c * a.nchunk, a.nchunk, 1, &s);
-    sum_records<1>(a.zpart + (size_t)c * a.nchunk, a.nchunk, 1, &z);
+    const double s = st_s[c], z = st_z[c];
     const bool on = !a.outer_active || a.outer_active[c];
     st_rr[c] = s;
     st_rz[c] = z;
@@ -233,7 +261,8 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
       const int s0 = g.plane_sph[pi], s1 = g.plane_sph[pi + 1];
       const int q0 = g.plane_pen[pi], npp = g.plane_pen[pi + 1] - q0;
       const double bt = st_beta[c];
-      const T rtk = a.tk ? (T)(1.0 / a.tk[c]) : (T)0;
+      const T btT = (T)bt;
+      const T rtk = st_rtk[c];
       const size_t sc = (size_t)c * a.npw;
       for (int e = threadIdx.x; e < npp * LDp; e += blockDim.x) A[e] = mk<T>(0, 0);
       for (int k = threadIdx.x; k < N; k += blockDim.x) rowmap[k] = -1;
@@ -249,7 +278,7 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
         V val = rv;
         if (bt >= 0.0) {
           const V pv = a.p[sc + s];
-          val = mk<T>(rv.x + (T)bt * pv.x, rv.y + (T)bt * pv.y);
+          val = mk<T>(rv.x + btT * pv.x, rv.y + btT * pv.y);
         }
         a.p[sc + s] = val;
         A[(g.sph_pen[s] - q0) * LDp + g.sph_i2[s]] = val;
@@ -311,7 +340,7 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
 
     // ---- phase C: y-FFT, z-FFT of the disc rows, gather + kinetic + shift, and
     // the plane's partial sums <C_v|Ap>, <C_v|p> and p^H Ap (Ap before P_c)
-    const int ndp = 2 * a.nocc + 1;
+    const size_t rbytes = plane_rec_bytes(a.nocc, (int)sizeof(V));
     for (int task = blockIdx.x; task < ncol * npl; task += gridDim.x) {
       const int c = task / npl, pi = task - c * npl;
       if (!st_act[c]) continue;
@@ -335,13 +364,13 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
       __syncthreads();
       V* S = fft_tile2<T, -1, false>(Q, R, npp, LDp, 1, a.pl, stw);
       V* Wv = (S == Q) ? R : Q;                     // free buffer: the plane's Ap values
-      const double2 Ec = a.E[c];
+      const V Ec = from_d<T>(a.E[c]);
       const int ns = s1 - s0;
       for (int e = threadIdx.x; e < ns; e += blockDim.x) {
         const int s = s0 + e;
         V val = S[(g.sph_pen[s] - q0) * LDp + g.sph_i2[s]];
         const V pv = a.p[sc + s];
-        const T dr = a.kin[s] - (T)Ec.x, di = -(T)Ec.y;
+        const T dr = a.kin[s] - Ec.x, di = -Ec.y;
         val.x += dr * pv.x - di * pv.y;
         val.y += dr * pv.y + di * pv.x;
         a.Ap[sc + s] = val;
@@ -350,8 +379,8 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
       __syncthreads();
       for (int e = threadIdx.x; e < ns; e += blockDim.x) S[e] = a.p[sc + s0 + e];   // the plane's p values
       __syncthreads();
-      double2* dp = a.dpart + ((size_t)c * npl + pi) * ndp;
-      plane_dots<T, false>(a.C, a.npw, a.nocc, S, Wv, s0, ns, dp, red);
+      unsigned char* rec = reinterpret_cast<unsigned char*>(a.dpart) + ((size_t)c * npl + pi) * rbytes;
+      plane_dots_rec<T>(a.C, a.npw, a.nocc, S, Wv, s0, ns, rec, red);
     }
     work(2);
     if (!grid_barrier(a.bar, a.err, nblk)) return;
@@ -364,45 +393,56 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
       const int c = task / a.nchunk, ch = task - c * a.nchunk;
       if (!st_act[c]) continue;
       {
-        // stage the plane partials in shared memory (every thread loading:
-        // independent loads in flight), then add them in plane order
-        const double2* src = a.dpart + (size_t)c * npl * ndp;
-        const bool staged = (size_t)npl * ndp * sizeof(double2) <= 2 * (size_t)N * LDp * sizeof(V);
-        const double2* stage = staged ? reinterpret_cast<const double2*>(A) : src;
+        // stage the column's plane records in shared memory (every thread
+        // loading: independent loads in flight), then add them in plane
+        // order: the projector sums in T, p^H Ap in FP64 (one warp, planes
+        // strided over the lanes, a fixed shuffle tree)
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(a.dpart) + (size_t)c * npl * rbytes;
+        const size_t nb16 = (size_t)npl * rbytes / 16;
+        const bool staged = nb16 * 16 <= 2 * (size_t)N * LDp * sizeof(V);
+        const unsigned char* stage = staged ? reinterpret_cast<const unsigned char*>(A) : src;
         if (staged) {
-          double2* st = reinterpret_cast<double2*>(A);
-          staged_copy<kLd, double2>(npl * ndp, [&](int e) { return src[e]; },
-                                    [&](int e, double2 v) { st[e] = v; });
+          const float4* s4 = reinterpret_cast<const float4*>(src);
+          float4* d4 = reinterpret_cast<float4*>(A);
+          staged_copy<kLd, float4>((int)nb16, [&](int e) { return s4[e]; }, [&](int e, float4 v) { d4[e] = v; });
         }
         __syncthreads();
-        for (int j = threadIdx.x; j < ndp; j += blockDim.x) {
-          double sx = 0.0, sy = 0.0;
+        for (int j = threadIdx.x; j < 2 * a.nocc; j += blockDim.x) {
+          T sx = 0, sy = 0;
           for (int q = 0; q < npl; ++q) {
-            const double2 v = stage[q * ndp + j];
+            const V v = reinterpret_cast<const V*>(stage + (size_t)q * rbytes)[j];
             sx += v.x;
             sy += v.y;
           }
-          coef[j] = make_double2(sx, sy);
+          coefT[j] = mk<T>(sx, sy);
+        }
+        if (threadIdx.x < 32) {
+          double t = 0.0;
+          for (int q = threadIdx.x; q < npl; q += 32)
+            t += *reinterpret_cast<const double*>(stage + (size_t)q * rbytes + rbytes - 16);
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          if (threadIdx.x == 0) bcast = t;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-          // p^H P_c A p = p^H A p - sum_v conj(<C_v|p>) <C_v|Ap>
-          double pap = coef[2 * a.nocc].x;
+          // p^H P_c A p = p^H A p - sum_v conj(<C_v|p>) <C_v|Ap>  (the correction
+          // is of the order of the rounding of p's occupied components: T)
+          T corr = 0;
           for (int v = 0; v < a.nocc; ++v) {
-            const double2 k = coef[v], q = coef[a.nocc + v];
-            pap -= q.x * k.x + q.y * k.y;
+            const V k = coefT[v], q = coefT[a.nocc + v];
+            corr += q.x * k.x + q.y * k.y;
           }
-          bcast = pap;
+          const double pap = bcast - (double)corr;
+          *s_al = (T)((pap > 0.0) ? st_rz[c] / pap : 0.0);
           if (ch == 0) a.ppart[(size_t)c * a.nchunk] = pap;
         }
         __syncthreads();
       }
-      const double pap = bcast;
-      const T al = (T)((pap > 0.0) ? st_rz[c] / pap : 0.0);
+      const T al = *s_al;
       const int g0 = ch * a.chunk, g1 = min(a.npw, g0 + a.chunk);
       const size_t sc = (size_t)c * a.npw;
-      const T rtk = a.tk ? (T)(1.0 / a.tk[c]) : (T)0;
-      double acc = 0.0, accz = 0.0;
+      const T rtk = st_rtk[c];
+      T acc = 0, accz = 0;
       for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
         const size_t i = sc + G;
         V y = a.Ap[i];
@@ -416,14 +456,14 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
           for (int u = 0; u < 4; ++u) cv[u] = a.C[(size_t)(v + u) * a.npw + G];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const V k = from_d<T>(coef[v + u]);
+            const V k = coefT[v + u];
             y.x -= cv[u].x * k.x - cv[u].y * k.y;
             y.y -= cv[u].x * k.y + cv[u].y * k.x;
           }
         }
         for (; v < a.nocc; ++v) {
           const V cv = a.C[(size_t)v * a.npw + G];
-          const V k = from_d<T>(coef[v]);
+          const V k = coefT[v];
           y.x -= cv.x * k.x - cv.y * k.y;
           y.y -= cv.x * k.y + cv.y * k.x;
         }
@@ -433,15 +473,14 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
         rv.y -= al * y.y;
         a.x[i] = xv;
         a.r[i] = rv;
-        const double2 rd = to_d(rv);
-        const double n2 = rd.x * rd.x + rd.y * rd.y;
+        const T n2 = rv.x * rv.x + rv.y * rv.y;
         acc += n2;
-        accz += (rtk != (T)0 ? (double)tpa<T>(kin * rtk) : 1.0) * n2;
+        accz += (rtk != (T)0 ? tpa<T>(kin * rtk) : (T)1) * n2;
       }
-      acc = dsum_block<T>(acc, red);
-      if (threadIdx.x == 0) a.rpart[(size_t)c * a.nchunk + ch] = acc;
-      accz = dsum_block<T>(accz, red);
-      if (threadIdx.x == 0) a.zpart[(size_t)c * a.nchunk + ch] = accz;
+      acc = tsum_block<T>(acc, redT);
+      if (threadIdx.x == 0) a.rpart[(size_t)c * a.nchunk + ch] = (double)acc;
+      accz = tsum_block<T>(accz, redT);
+      if (threadIdx.x == 0) a.zpart[(size_t)c * a.nchunk + ch] = (double)accz;
       __syncthreads();
     }
     work(4);
@@ -449,11 +488,10 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
     mark(4);
 
     // ---- convergence decisions (identical in every CTA)
+    column_sums(a.rpart, a.zpart, a.nchunk, ncol, st_s, st_z);
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
       if (!st_act[c]) continue;
-      double s, z;
-      sum_records<1>(a.rpart + (size_t)c * a.nchunk, a.nchunk, 1, &s);
-      sum_records<1>(a.zpart + (size_t)c * a.nchunk, a.nchunk, 1, &z);
+      const double s = st_s[c], z = st_z[c];
       const double pp = a.ppart[(size_t)c * a.nchunk];
       const int itc = st_it[c] + 1;
       st_it[c] = itc;

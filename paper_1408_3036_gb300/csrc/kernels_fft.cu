@@ -13,6 +13,7 @@
 // sphere; passes read zeros instead of memory there and write only what the
 // next pass reads.  Inverse transforms are unnormalised (u(r) = sum_G c_G
 // e^{iGr}); the forward 1/N_g is folded into the multipliers.
+#include <algorithm>
 #include <cstdio>
 
 #include "fft.cuh"
@@ -387,11 +388,16 @@ void launch_xpass_prod_fwd(cudaStream_t s, const Geometry& g, const Prec<T>& P, 
 // (last pass of the density reduction, Eq. P1):
 //   out[o](r) (+)= scale * sum_{col in group o} U[col_v[col]](r) * IFFT_x(grid[col])(r)
 // ---------------------------------------------------------------------------
+// With ngrp > 1 the columns of a group are split into ngrp contiguous parts
+// (blockIdx.z), each summed into its own partial field part[z][o] (unscaled);
+// k_reduce_parts then adds the parts in order: more CTAs in flight for the
+// few groups of a Lanczos step.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_xpass_inv_reduce(Geometry g, Prec<T> P, FftPlan pl, const cpx<T>* __restrict__ grid,
                    const int* __restrict__ gstart, const int* __restrict__ col_v, double scale,
-                   T* __restrict__ out_real, cpx<T>* __restrict__ out_c, int accumulate, int nchunk) {
+                   T* __restrict__ out_real, cpx<T>* __restrict__ out_c, int accumulate, int nchunk,
+                   int ngrp, cpx<T>* __restrict__ part) {
   using V = cpx<T>;
   extern __shared__ unsigned char smem_raw[];
   const int N = g.N, LD = N + 1;
@@ -406,7 +412,10 @@ k_xpass_inv_reduce(Geometry g, Prec<T> P, FftPlan pl, const cpx<T>* __restrict__
   load_tw<T>(stw, P.tw, N);
   for (int e = threadIdx.x; e < kP * LD; e += blockDim.x) Acc[e] = mk<T>(0, 0);
   const size_t off1 = (size_t)i1 * N + c0;
-  for (int col = gstart[o]; col < gstart[o + 1]; ++col) {
+  const int cg0 = gstart[o], len = gstart[o + 1] - cg0, z = blockIdx.z;
+  const int col_lo = cg0 + (int)(((long long)len * z) / ngrp);
+  const int col_hi = cg0 + (int)(((long long)len * (z + 1)) / ngrp);
+  for (int col = col_lo; col < col_hi; ++col) {
     __syncthreads();
     const size_t base = (size_t)col * g.N3 + off1;
     for (int e = threadIdx.x; e < N * kP; e += blockDim.x) {
@@ -434,6 +443,14 @@ k_xpass_inv_reduce(Geometry g, Prec<T> P, FftPlan pl, const cpx<T>* __restrict__
   }
   __syncthreads();
   const size_t obase = (size_t)o * g.N3 + off1;
+  if (ngrp > 1) {
+    const size_t pbase = ((size_t)z * gridDim.y + o) * g.N3 + off1;
+    for (int e = threadIdx.x; e < N * kP; e += blockDim.x) {
+      const int i0 = e / kP, dz = e - i0 * kP;
+      if (dz < np) part[pbase + (size_t)i0 * g.N2 + dz] = Acc[dz * LD + i0];
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < N * kP; e += blockDim.x) {
     const int i0 = e / kP, dz = e - i0 * kP;
     if (dz < np) {
@@ -451,17 +468,55 @@ k_xpass_inv_reduce(Geometry g, Prec<T> P, FftPlan pl, const cpx<T>* __restrict__
   }
 }
 
+// out[o][r] (+)= scale * sum_z part[z][o][r]  (z in order)
+template <typename T>
+__global__ void k_reduce_parts(size_t n3, int ngroups, int ngrp, const cpx<T>* __restrict__ part, double scale,
+                               T* __restrict__ out_real, cpx<T>* __restrict__ out_c, int accumulate) {
+  const size_t n = n3 * ngroups;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    cpx<T> a = part[i];
+    for (int z = 1; z < ngrp; ++z) {
+      const cpx<T> b = part[(size_t)z * n + i];
+      a.x += b.x;
+      a.y += b.y;
+    }
+    a.x *= (T)scale;
+    a.y *= (T)scale;
+    if (out_real) {
+      out_real[i] = accumulate ? out_real[i] + a.x : a.x;
+    } else {
+      if (accumulate) { const cpx<T> b0 = out_c[i]; a.x += b0.x; a.y += b0.y; }
+      out_c[i] = a;
+    }
+  }
+}
+
 template <typename T>
 void launch_xpass_inv_reduce(cudaStream_t s, const Geometry& g, const Prec<T>& P, const FftPlan& pl,
                              const cpx<T>* grid, const int* group_start, const int* col_v, int ngroups,
-                             double scale, T* out_real, cpx<T>* out_cplx, int accumulate) {
+                             double scale, T* out_real, cpx<T>* out_cplx, int accumulate, cpx<T>* scratch,
+                             size_t scratch_elems, int max_cols) {
   const int nchunk = (g.N + kP - 1) / kP;
   if (ngroups == 0) return;
-  dim3 grd(g.N * nchunk, ngroups);
+  // split the column sums until about four CTAs per SM are in flight
+  const int base = g.N * nchunk * ngroups;
+  int ngrp = 1;
+  if (scratch) {
+    ngrp = std::min(std::min(kMaxReduceParts, std::max(max_cols, 1)), (4 * 152 + base - 1) / base);
+    ngrp = (int)std::min<size_t>((size_t)std::max(ngrp, 1), scratch_elems / ((size_t)ngroups * g.N3));
+    ngrp = std::max(ngrp, 1);
+  }
+  dim3 grd(g.N * nchunk, ngroups, ngrp);
   const size_t sm = tile_smem<T>(g.N, 3);
   ++g_launches;
   k_xpass_inv_reduce<T><<<grd, kThreads, sm, s>>>(g, P, pl, grid, group_start, col_v, scale, out_real,
-                                                   out_cplx, accumulate, nchunk);
+                                                   out_cplx, accumulate, nchunk, ngrp, scratch);
+  if (ngrp > 1) {
+    const size_t n = (size_t)g.N3 * ngroups;
+    ++g_launches;
+    k_reduce_parts<T><<<(int)std::min<size_t>((n + 255) / 256, 152 * 8), 256, 0, s>>>(
+        (size_t)g.N3, ngroups, ngrp, scratch, scale, out_real, out_cplx, accumulate);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -495,7 +550,7 @@ cudaError_t fft_set_smem_limits() {
                                          const int*, cpx<T>*, int);                                      \
   template void launch_xpass_inv_reduce<T>(cudaStream_t, const Geometry&, const Prec<T>&,                \
                                            const FftPlan&, const cpx<T>*, const int*, const int*, int,   \
-                                           double, T*, cpx<T>*, int);                                    \
+                                           double, T*, cpx<T>*, int, cpx<T>*, size_t, int);              \
   template cudaError_t fft_set_smem_limits<T>();
 
 GW_INST(double)

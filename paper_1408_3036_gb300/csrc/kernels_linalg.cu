@@ -47,6 +47,9 @@ __global__ void __launch_bounds__(kLT)
 k_proj_dots(const cpx<T>* __restrict__ C, int nocc, int npw, const cpx<T>* __restrict__ Y, int ncol,
             const int* __restrict__ active, double2* __restrict__ partial, unsigned* __restrict__ cnt,
             double2* __restrict__ coef) {
+  // partial sums, their shuffles and the sum over chunks in the precision of
+  // the vectors (FP64 arithmetic is scarce on this GPU); coef in FP64
+  cpx<T>* part = reinterpret_cast<cpx<T>*>(partial);
   const int nchunk = gridDim.x;
   const int g0 = blockIdx.x * kChunkP, g1 = min(npw, g0 + kChunkP);
   const int b0 = blockIdx.y * kCT;
@@ -70,22 +73,21 @@ k_proj_dots(const cpx<T>* __restrict__ C, int nocc, int npw, const cpx<T>* __res
     }
 #pragma unroll
     for (int j = 0; j < kCT; ++j) {
-      double sx = ax[j], sy = ay[j];
+      T sx = ax[j], sy = ay[j];
       for (int o = 16; o > 0; o >>= 1) {
         sx += __shfl_xor_sync(0xffffffffu, sx, o);
         sy += __shfl_xor_sync(0xffffffffu, sy, o);
       }
-      if (lane == 0 && j < nb)
-        partial[((size_t)blockIdx.x * nocc + v) * ncol + b0 + j] = make_double2(sx, sy);
+      if (lane == 0 && j < nb) part[((size_t)blockIdx.x * nocc + v) * ncol + b0 + j] = mk<T>(sx, sy);
     }
   }
   if (!last_block(&cnt[blockIdx.y], nchunk)) return;
   for (int t = threadIdx.x; t < nocc * nb; t += blockDim.x) {
     const int v = t / nb, j = t - v * nb;
-    double q[2];
-    sum_records<2>(reinterpret_cast<const double*>(partial + (size_t)v * ncol + b0 + j), nchunk,
-                   2 * (size_t)nocc * ncol, q);
-    coef[(size_t)v * ncol + b0 + j] = make_double2(q[0], q[1]);
+    T q[2];
+    sum_records<2, T>(reinterpret_cast<const T*>(part + (size_t)v * ncol + b0 + j), nchunk,
+                      2 * (size_t)nocc * ncol, q);
+    coef[(size_t)v * ncol + b0 + j] = make_double2((double)q[0], (double)q[1]);
   }
 }
 
@@ -755,26 +757,27 @@ void launch_combine(cudaStream_t s, int npw, int nout, const double2* in, const 
 // with Em = e_v + omega, Ep = e_v - omega (complex).  A reciprocal whose
 // denominator is exactly zero is taken as 0 (the pseudo-inverse of the
 // diagonal; such an entry of a projected right-hand side is zero).
-__device__ __forceinline__ double2 pinv_shift(double t, double2 e) {
-  const double dr = t - e.x, di = -e.y;
-  const double d2 = dr * dr + di * di;
-  if (d2 == 0.0) return make_double2(0.0, 0.0);
-  const double r = 1.0 / d2;
-  return make_double2(dr * r, -di * r);
+template <typename T>
+__device__ __forceinline__ cpx<T> pinv_shift(T t, cpx<T> e) {
+  const T dr = t - e.x, di = -e.y;
+  const T d2 = dr * dr + di * di;
+  if (d2 == (T)0) return mk<T>(0, 0);
+  const T r = (T)1 / d2;
+  return mk<T>(dr * r, -di * r);
 }
 
-// (the weights in FP64, the product in the precision T of the vectors)
+// (in the precision T of the vectors)
 template <typename T>
 __global__ void k_model_scale(int npw, const T* __restrict__ kin, const cpx<T>* __restrict__ in,
                               const int* __restrict__ src, const double2* __restrict__ Em,
                               const double2* __restrict__ Ep, cpx<T>* __restrict__ out) {
   const int j = blockIdx.y;
   const int a = src[j];
-  const double2 em = Em[j], ep = Ep[j];
+  const cpx<T> em = from_d<T>(Em[j]), ep = from_d<T>(Ep[j]);
   for (int G = blockIdx.x * blockDim.x + threadIdx.x; G < npw; G += gridDim.x * blockDim.x) {
-    const double t = (double)kin[G];
-    const double2 w = cadd(pinv_shift(t, em), pinv_shift(t, ep));
-    out[(size_t)j * npw + G] = cmul(from_d<T>(w), in[(size_t)a * npw + G]);
+    const T t = kin[G];
+    const cpx<T> w = cadd(pinv_shift<T>(t, em), pinv_shift<T>(t, ep));
+    out[(size_t)j * npw + G] = cmul(w, in[(size_t)a * npw + G]);
   }
 }
 

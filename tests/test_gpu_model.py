@@ -4,8 +4,8 @@ the two-basis split (Eq. subs_epsilon) on the GPU against the FP64 oracle.
 The model path has no iterative solve: with GW_FP64 every step is FP64
 arithmetic, so the applications agree with the oracle to rounding (1e-12
 relative) and the Lanczos coefficients and the split to 1e-10; with GW_MIXED
-the transforms run in FP32 (1e-6 for chi0, eps~ and the Lanczos
-coefficients).
+the transforms run in FP32 with no refinement (1e-6 for one application of
+chi0 or eps~, 1e-5 for the Lanczos coefficients after 20 steps).
 """
 import numpy as np
 import pytest
@@ -130,8 +130,11 @@ def test_model_lanczos(tiny):
     a, b, Q = c.lanczos(x0, K, 0.0, gw.GW_FP64, basis=True)
     assert rel(a, ar) < 1e-10 and rel(b, br) < 1e-10
     assert np.abs(w * Q @ Q.T - np.eye(K)).max() < 1e-12
+    # FP32 model operator, no refinement: each application carries the rounding
+    # of about a dozen FP32 transform passes (~1e-6 relative); the recursion
+    # passes it on to alpha and beta with a modest growth over K steps
     a32, b32, _ = c.lanczos(x0, K, 0.0, gw.GW_MIXED)
-    assert rel(a32, ar) < 1e-6 and rel(b32, br) < 1e-6
+    assert rel(a32, ar) < 1e-5 and rel(b32, br) < 1e-5
     c.close()
 
 
