@@ -22,6 +22,8 @@ against the paper:
                 (Sec. Lanczos, Eq. krylov), the inverse in the Lanczos basis,
                 and the split over an exact and a model basis (Eq.
                 subs_epsilon).
+* ``sigma_p``   residue term Sigma^P_e(delta) of Eq. pe: one short Lanczos per
+                pole at its real frequency, seeded with v^1/2 |p* e>.
 * ``gradient``  derivative of <phi|eps^-1(0)|phi> with respect to V_loc (not in
                 the paper; derived by third-order perturbation theory and pinned
                 by central finite differences).

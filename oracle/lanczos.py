@@ -35,8 +35,11 @@ def _ip(weight, bilinear):
     return lambda a, b: weight * np.vdot(a, b)
 
 
-def lanczos(apply, x0, K, weight=1.0, reorth=2, bilinear=False):
-    """Single-vector Lanczos.  Returns (alpha[K], beta[K-1], Q (K, n))."""
+def lanczos(apply, x0, K, weight=1.0, reorth=2, bilinear=False, breakdown=None):
+    """Single-vector Lanczos.  Returns (alpha[K], beta[K-1], Q (K, n)).
+    With ``breakdown`` set, the recursion stops after step k when
+    |beta_k| <= breakdown |alpha_k| (an invariant subspace: alpha, beta and Q
+    then have k + 1, k and k + 1 entries)."""
     ip = _ip(weight, bilinear)
     x0 = np.asarray(x0)
     nrm = np.sqrt(ip(x0, x0))
@@ -60,6 +63,8 @@ def lanczos(apply, x0, K, weight=1.0, reorth=2, bilinear=False):
         if k == K - 1:
             break
         b = np.sqrt(ip(w, w))
+        if breakdown is not None and abs(b) <= breakdown * abs(a):
+            break
         beta.append(b)
         Q.append(w / b)
     return np.array(alpha), np.array(beta), np.array(Q)
