@@ -335,6 +335,35 @@ gw_status gw_epsinv_split(gw_ctx* ctx, const double* phi, int m, const double* b
                           const double* beta_m, int k_m, double omega, double* out, int device_ptrs);
 
 /*
+ * gw_sigma_p -- the residue term of the correlation self-energy (Eq. pe):
+ *   Sigma^P_e(delta) = - sum_v <e v*|v^1/2 (eps^-1(w_ve) - 1) v^1/2|v* e> Theta(w_ve)
+ *                      + sum_c <e c*|v^1/2 (eps^-1(w_ce) - 1) v^1/2|c* e> Theta(-w_ce),
+ *   w_ne = e_n - e_e - delta, <r|n* e> = psi_n(r)* psi_e(r), Theta(0) = 1/2,
+ * each element from a separate Lanczos recursion of k steps on eps~(w) at its
+ * real frequency, seeded with phi = v^1/2 |p* e> (Sec. "Calculating the
+ * dielectric matrix and the integrand at different frequencies": four steps
+ * converge the term to 1 meV): <phi|eps~^-1 - 1|phi> ~ |phi|^2 ((T^-1)_11 - 1).
+ * A seed that is complex in real space runs as the stacked real pair (real
+ * part, imaginary part), which is the recursion of the complex vector in the
+ * Hermitian inner product; the recursion stops early at an invariant subspace.
+ * Uses the operator chosen by gw_set_operator and the solvers of gw_lanczos
+ * (CG at w = 0, SQMR otherwise).
+ *   psi_e   [N_PW] complex sphere coefficients of the state e
+ *   eps_e, delta  energies (Ha)
+ *   n       candidate pole states; psi [n][N_PW] complex, eps [n], occ [n]
+ *           (1 occupied: enters when w_ve >= 0; 0 conduction: when w_ce <= 0)
+ *   k       Lanczos steps per pole, 1 <= k <= 256
+ *   sigma   scalar out; terms [n] out (signed term of each state, 0 where
+ *           Theta excludes it), or NULL
+ * Pointers are all host or all device (device_ptrs).  Errors of a recursion
+ * (GW_E_NOCONV, GW_E_NONFINITE, ...) are returned as they are; a singular
+ * Lanczos matrix gives GW_E_BREAKDOWN.
+ */
+gw_status gw_sigma_p(gw_ctx* ctx, const double* psi_e, double eps_e, double delta, int n, const double* psi,
+                     const double* eps, const int* occ, int k, double* sigma, double* terms, gw_prec prec,
+                     int device_ptrs);
+
+/*
  * gw_profile -- time selected kernel classes with CUDA events on the work
  * stream (one event pair around each launch; mask 0 turns timing off).
  * Classes (multi-launch CG): 0 scatter + inverse z pass (with the CG p update),

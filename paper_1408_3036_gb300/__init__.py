@@ -29,7 +29,7 @@ EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "
            "gw_set_solver", "gw_set_precond", "gw_set_deflation", "gw_profile", "gw_profile_read", "gw_last_error", "gw_destroy",
            "gw_epsinv_elements_noalloc", "gw_apply_chi0_c", "gw_apply_eps_c", "gw_block_lanczos",
            "gw_epsinv_block", "gw_batch_setup", "gw_batch_size", "gw_batch_cell", "gw_batch_lanczos",
-           "gw_batch_last_error", "gw_batch_destroy", "gw_set_operator", "gw_epsinv_split")
+           "gw_batch_last_error", "gw_batch_destroy", "gw_set_operator", "gw_epsinv_split", "gw_sigma_p")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
                    "refine_fp64", "persistent_cg")
 
@@ -73,6 +73,7 @@ def load(path=LIB_PATH):
         "gw_set_precond": (I, [P, I]),
         "gw_set_operator": (I, [P, I]),
         "gw_epsinv_split": (I, [P, P, I, P, P, P, I, P, P, P, I, D, P, I]),
+        "gw_sigma_p": (I, [P, P, D, D, I, P, P, P, I, P, P, I, I]),
         "gw_set_deflation": (I, [P, I, P, P]),
         "gw_profile": (I, [P, ctypes.c_uint]),
         "gw_profile_read": (I, [P, P, P, I]),
@@ -307,6 +308,22 @@ def gw_epsinv_split(ctx, phi, basis, alpha, beta, basis_m, alpha_m, beta_m, omeg
     return out
 
 
+def gw_sigma_p(ctx, psi_e, eps_e, delta, psi, eps, occ, k, sigma, terms=None, prec=GW_FP64):
+    """Sigma^P_e(delta) of Eq. pe (one k-step Lanczos per pole); see include/gw.h."""
+    pe, d = _ptr(psi_e)
+    n = len(eps)
+    pp, _ = _ptr(psi)
+    pe2, _ = _ptr(eps)
+    po, _ = _ptr(occ)
+    ps, e = _ptr(sigma)
+    pt, _ = _ptr(terms)
+    if d != e:
+        raise ValueError("mixed host/device buffers")
+    _check(ctx, load().gw_sigma_p(ctx, pe, float(eps_e), float(delta), int(n), pp, pe2, po, int(k), ps, pt,
+                                  int(prec), d))
+    return sigma, terms
+
+
 def gw_profile(ctx, mask):
     _check(ctx, load().gw_profile(ctx, int(mask)))
 
@@ -429,6 +446,17 @@ class Cell:
 
     def set_operator(self, op):
         gw_set_operator(self.ctx, op)
+
+    def sigma_p(self, psi_e, eps_e, delta, psi, eps, occ, k=4, prec=GW_FP64):
+        """Sigma^P_e(delta) and the term of every candidate state (host arrays)."""
+        pe = np.ascontiguousarray(np.asarray(psi_e, np.complex128).reshape(-1))
+        pp = np.ascontiguousarray(np.atleast_2d(np.asarray(psi, np.complex128)))
+        ee = np.ascontiguousarray(np.asarray(eps, np.float64).reshape(-1))
+        oo = np.ascontiguousarray(np.asarray(occ, np.int32).reshape(-1))
+        sg = np.zeros(1)
+        tt = np.zeros(len(ee))
+        gw_sigma_p(self.ctx, pe, eps_e, delta, pp, ee, oo, k, sg, tt, prec)
+        return float(sg[0]), tt
 
     def epsinv_split(self, phi, lz, lz_model, omega=0.0):
         """Eq. subs_epsilon from two host Lanczos results (alpha, beta, basis)."""

@@ -915,6 +915,19 @@ gw_status chi0_reduce(gw_ctx* ctx, const double2* sol64, int nb, int nom, void* 
   return launch_check(ctx, "chi0");
 }
 
+// <r|p* e> = conj(u_p(r)) u_e(r) / Omega for the pole states p, split into the
+// real and imaginary parts: out[j][0][r], out[j][1][r]
+__global__ void k_pair_product(size_t n3, int np, const double2* __restrict__ up, const double2* __restrict__ ue,
+                               double inv_vol, double* __restrict__ out) {
+  const size_t n = n3 * np;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t j = i / n3, r = i - j * n3;
+    const double2 a = up[i], b = ue[r];
+    out[(2 * j) * n3 + r] = (a.x * b.x + a.y * b.y) * inv_vol;
+    out[(2 * j + 1) * n3 + r] = (a.x * b.y - a.y * b.x) * inv_vol;
+  }
+}
+
 // complex fields: out = v^1/2 in  (or out = sub - v^1/2 in)
 __global__ void k_csub(size_t n, const double2* __restrict__ a, const double2* __restrict__ b,
                        double2* __restrict__ out) {
@@ -1073,21 +1086,28 @@ gw_status need_occ(gw_ctx* ctx) {
 // ---------------------------------------------------------------------------
 // Lanczos (Sec. Lanczos) on real fields, FP64 vectors and inner products
 // ---------------------------------------------------------------------------
+// width = 2: the vectors are pairs (real part, imaginary part) of complex
+// fields stacked into one real vector of 2 N_g entries: for a real symmetric
+// eps~ (real omega) this is the Lanczos recursion of a complex start vector in
+// the Hermitian inner product.  *done (optional) receives the steps completed
+// (fewer than K at an invariant subspace, where GW_E_BREAKDOWN is returned).
 template <typename T>
 gw_status lanczos_core(gw_ctx* ctx, const double* x0, int K, const std::vector<double2>& omega, double* alpha,
-                       double* beta, double* Q) {
-  const int N3 = ctx->N3;
-  const double wgt = ctx->vol / N3;
+                       double* beta, double* Q, int width = 1, int* done = nullptr) {
+  const int N3 = width * ctx->N3;
+  const double wgt = ctx->vol / ctx->N3;
+  if (done) *done = 0;
   double *w, *h, *nrm;
   TRY(getbuf(ctx, "lz_w", N3, &w));
   TRY(getbuf(ctx, "lz_h", K + 1, &h));
   TRY(getbuf(ctx, "lz_nrm", 1, &nrm));
-  TRY(ensure_work(ctx, K + 1));
+  TRY(ensure_work(ctx, (size_t)width * (K + 1)));   // partial sums of the stacked length
   launch_dot(ctx->st, N3, x0, x0, wgt, 1, ctx->work, nrm);
   launch_lz_axpy(ctx->st, N3, 2, nrm, const_cast<double*>(x0), nullptr, Q);
   for (int k = 0; k < K; ++k) {
     double* qk = Q + (size_t)k * N3;
-    TRY(eps_core<T>(ctx, qk, false, 1, omega, w, false));
+    TRY(eps_core<T>(ctx, qk, false, width, omega, w, false));
+    if (done) *done = k + 1;
     if (k > 0) launch_lz_axpy(ctx->st, N3, 0, beta + (k - 1), w, Q + (size_t)(k - 1) * N3, nullptr);
     launch_dot(ctx->st, N3, qk, w, wgt, 0, ctx->work, alpha + k);
     launch_lz_axpy(ctx->st, N3, 1, alpha + k, w, qk, nullptr);
@@ -2125,6 +2145,133 @@ gw_status gw_epsinv_split(gw_ctx* ctx, const double* phi, int m, const double* b
   if (ctx->host_pin[0] || ctx->host_pin[1] || ctx->host_pin[2])
     return fail(ctx, GW_E_BREAKDOWN, "singular matrix in the split (tridiagonal or model Gram)");
   return GW_OK;
+}
+
+// Eq. pe: Sigma^P_e(delta) = - sum_v <e v*|v^1/2 (eps^-1(w_ve) - 1) v^1/2|v* e> Theta(w_ve)
+//                             + sum_c <e c*|...(w_ce)...|c* e> Theta(-w_ce),  w_ne = e_n - e_e - delta,
+// each element from k Lanczos steps on eps~(w_pe) seeded with phi = v^1/2 |p* e>:
+// <phi|eps~^-1 - 1|phi> ~ |phi|^2 ((T^-1)_11 - 1).
+gw_status gw_sigma_p(gw_ctx* ctx, const double* psi_e, double eps_e, double delta, int n, const double* psi,
+                     const double* eps, const int* occ, int k, double* sigma, double* terms, gw_prec prec,
+                     int dev) {
+  TRY(begin(ctx));
+  TRY(need_occ(ctx));
+  if (!psi_e || !sigma || n < 0 || (n > 0 && (!psi || !eps || !occ)) || k < 1 || k > 256)
+    return fail(ctx, GW_E_ARG, "bad arguments");
+  if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_E_ARG, "bad precision");
+  if (!std::isfinite(eps_e) || !std::isfinite(delta)) return fail(ctx, GW_E_NONFINITE, "non-finite energy");
+  for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
+  const int npw = ctx->npw, N3 = ctx->N3;
+  const double wgt = ctx->vol / N3;
+  // host copies of the small per-state inputs
+  std::vector<double> he(n);
+  std::vector<int> ho(n);
+  if (n > 0) {
+    if (dev) {
+      CK(cudaMemcpyAsync(he.data(), eps, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+      CK(cudaMemcpyAsync(ho.data(), occ, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+      TRY(sync(ctx, "sigma_p inputs"));
+    } else {
+      std::copy(eps, eps + n, he.begin());
+      std::copy(occ, occ + n, ho.begin());
+    }
+  }
+  // the poles that Theta keeps, with their weights -Theta(w) (occupied) or Theta(-w)
+  std::vector<int> pole;
+  std::vector<double> pw_, pom;
+  for (int j = 0; j < n; ++j) {
+    if (!std::isfinite(he[j])) return fail(ctx, GW_E_NONFINITE, "non-finite energy");
+    const double om = he[j] - eps_e - delta;
+    const double th = ho[j] ? (om > 0 ? 1.0 : (om == 0 ? 0.5 : 0.0)) : (om < 0 ? 1.0 : (om == 0 ? 0.5 : 0.0));
+    if (th == 0.0) continue;
+    pole.push_back(j);
+    pw_.push_back(ho[j] ? -th : th);
+    pom.push_back(om);
+  }
+  std::vector<double> hterms(n, 0.0);
+  double total = 0.0;
+  const int np = (int)pole.size();
+  if (np > 0) {
+    // grids u_e and u_p of the states (sphere -> grid, FP64), then the pair products
+    const void *pe, *pp;
+    TRY(stage_in(ctx, "sgp_psie", psi_e, (size_t)npw * sizeof(double2), dev, &pe));
+    TRY(stage_in(ctx, "sgp_psi", psi, (size_t)n * npw * sizeof(double2), dev, &pp));
+    double2 *cs, *ug;
+    double *seeds, *al, *be, *Q, *n2, *Ti, *d, *l;
+    int* stat;
+    TRY(getbuf(ctx, "sgp_cs", (size_t)(np + 1) * npw, &cs));
+    TRY(getbuf(ctx, "sgp_ug", (size_t)(np + 1) * N3, &ug));
+    for (int i = 0; i < np; ++i)
+      CK(cudaMemcpyAsync(cs + (size_t)i * npw, reinterpret_cast<const double2*>(pp) + (size_t)pole[i] * npw,
+                         npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(cs + (size_t)np * npw, pe, npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
+    const Geometry& g = ctx->geo;
+    launch_zpass<double>(ctx->st, Z_SCATTER_INV, g, ctx->P64, ctx->plan, ug, cs, nullptr, nullptr, nullptr, nullptr,
+                         nullptr, nullptr, nullptr, np + 1);
+    launch_ypass<double>(ctx->st, 1, 1, 0, g, ctx->P64, ctx->plan, ug, nullptr, np + 1, 0);
+    launch_xpass_mul<double>(ctx->st, 1, 1, 0, g, ctx->P64, ctx->plan, ug, nullptr, nullptr, np + 1);
+    double* prod;
+    TRY(getbuf(ctx, "sgp_prod", (size_t)2 * np * N3, &prod));
+    {
+      const size_t nn = (size_t)np * N3;
+      ++g_launches;
+      k_pair_product<<<(int)std::min<size_t>((nn + 255) / 256, 152 * 8), 256, 0, ctx->st>>>(
+          (size_t)N3, np, ug, ug + (size_t)np * N3, 1.0 / ctx->vol, prod);
+    }
+    // phi = v^1/2 |p* e> (real and imaginary parts as real fields), [np][2][N3]
+    TRY(getbuf(ctx, "sgp_seeds", (size_t)2 * np * N3, &seeds));
+    TRY(sqrtv<double>(ctx, prod, 2 * np, seeds, nullptr));
+    TRY(getbuf(ctx, "sgp_n2", 2 * np, &n2));
+    TRY(ensure_work(ctx, 64));
+    for (int j = 0; j < 2 * np; ++j)
+      launch_dot(ctx->st, N3, seeds + (size_t)j * N3, seeds + (size_t)j * N3, wgt, 0, ctx->work, n2 + j);
+    std::vector<double> hn2(2 * np);
+    CK(cudaMemcpyAsync(hn2.data(), n2, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    TRY(sync(ctx, "sigma_p seeds"));
+    TRY(getbuf(ctx, "sgp_al", k, &al));
+    TRY(getbuf(ctx, "sgp_be", k, &be));
+    TRY(getbuf(ctx, "sgp_Q", (size_t)2 * k * N3, &Q));
+    TRY(getbuf(ctx, "sgp_Ti", (size_t)k * k, &Ti));
+    TRY(getbuf(ctx, "sgp_d", k, &d));
+    TRY(getbuf(ctx, "sgp_l", k, &l));
+    TRY(getbuf(ctx, "sgp_stat", 1, &stat));
+    double* x0;
+    TRY(getbuf(ctx, "sgp_x0", (size_t)2 * N3, &x0));
+    for (int i = 0; i < np; ++i) {
+      const double nr = hn2[2 * i], ni = hn2[2 * i + 1];
+      const double nt = nr + ni;
+      if (!(nt > 0.0)) continue;                       // a vanishing seed: the term is 0
+      // a real seed (states real in real space) runs on N_g entries, a complex one on 2 N_g
+      const bool cplx = ni > 1e-24 * nt;
+      const double* src = seeds + (size_t)(2 * i + (cplx || nr > 0.0 ? 0 : 1)) * N3;
+      const int width = cplx ? 2 : 1;
+      CK(cudaMemcpyAsync(x0, src, (size_t)width * N3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+      const std::vector<double2> om{make_double2(pom[i], 0.0)};
+      int steps = 0;
+      gw_status st = (prec == GW_FP64) ? lanczos_core<double>(ctx, x0, k, om, al, be, Q, width, &steps)
+                                       : lanczos_core<float>(ctx, x0, k, om, al, be, Q, width, &steps);
+      if (st != GW_OK && st != GW_E_BREAKDOWN) return st;
+      ctx->err.clear();
+      launch_tridiag_inv(ctx->st, steps, al, be, d, l, Ti, stat);
+      double t11 = 0.0;
+      int hs = 0;
+      CK(cudaMemcpyAsync(&t11, Ti, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+      CK(cudaMemcpyAsync(&hs, stat, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+      TRY(sync(ctx, "sigma_p element"));
+      if (hs) return fail(ctx, GW_E_BREAKDOWN, "singular Lanczos matrix in a Sigma^P element");
+      hterms[pole[i]] = pw_[i] * (cplx ? nt : (nr > 0.0 ? nr : ni)) * (t11 - 1.0);
+    }
+    for (int j = 0; j < n; ++j) total += hterms[j];
+  }
+  if (dev) {
+    CK(cudaMemcpyAsync(sigma, &total, sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    if (terms && n > 0) CK(cudaMemcpyAsync(terms, hterms.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    TRY(sync(ctx, "sigma_p out"));
+  } else {
+    *sigma = total;
+    if (terms) std::copy(hterms.begin(), hterms.end(), terms);
+  }
+  return launch_check(ctx, "sigma_p");
 }
 
 gw_status gw_set_precond(gw_ctx* ctx, int kind) {
