@@ -15,7 +15,9 @@ flushed between timed steps by writing a 512 MB buffer.
 Beside the headline, ``model_operator`` times the same Lanczos run on the
 model dielectric operator of Sec. Dielectric model (Eq. model_eq, H -> T:
 one kinetic division per Sternheimer solve) on the same cell and start
-vector (``--model-k 0`` skips it).
+vector (``--model-k 0`` skips it), and ``sigma_p`` times the residue term of
+Eq. pe for the highest occupied state, one four-step Lanczos per pole at its
+real frequency (``--sigma-p-k 0`` skips it).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 instead, on a bounded sample of the same workload.
@@ -481,6 +483,39 @@ def run_gpu(args):
                           peak=hbm, unit="GB/s", frac=ach / hbm, peak_kind=hbm_kind, traffic=None,
                           alg_bytes_per_apply=mb, ms_per_apply=t_app))
 
+    # --- residue term Sigma^P_e(delta) of Eq. pe for e = HOMO (k-step Lanczos per pole at real w)
+    sigp = None
+    if args.sigma_p_k > 0:
+        ok = False
+        try:
+            eps_c, psi_c, res_c = lowest_states(cell, c.n_occ + 4, tol=1e-10)
+            ok = float(res_c) <= 1e-8
+        except Exception as exc:            # input preparation only; the leg is skipped
+            res_c = str(exc)
+        if ok:
+            cand = np.ascontiguousarray(psi_c[:c.n_occ + 4])
+            ce = np.ascontiguousarray(eps_c[:c.n_occ + 4])
+            oc = np.array([1] * c.n_occ + [0] * 4, np.int32)
+            gap = float(ce[c.n_occ] - ce[c.n_occ - 1])
+            e_h = float(ce[c.n_occ - 1])
+            rows = []
+            for delta in (-0.5 * gap, 1.5 * gap):
+                sg = np.zeros(1)
+                tt = np.zeros(len(ce))
+                gw.gw_sigma_p(cell.ctx, cand[c.n_occ - 1], e_h, delta, cand, ce, oc, args.sigma_p_k, sg, tt, prec)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                gw.gw_sigma_p(cell.ctx, cand[c.n_occ - 1], e_h, delta, cand, ce, oc, args.sigma_p_k, sg, tt, prec)
+                e1.record(stream)
+                e1.synchronize()
+                rows.append(dict(delta=delta, poles=int(np.count_nonzero(tt)), sigma=float(sg[0]),
+                                 ms=e0.elapsed_time(e1)))
+            sigp = dict(state="HOMO", k=args.sigma_p_k, precision=args.prec, candidates="16 occupied + 4 conduction",
+                        runs=rows)
+        else:
+            sigp = dict(skipped=f"conduction states not converged: {res_c}")
+
     if rank == 0:
         line = dict(
             metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -496,7 +531,7 @@ def run_gpu(args):
                         column_iterations_per_step=it_cols / args.steps, geometry=geo),
             roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
             clocks=clk.summary(), fp64=fp64, profile_ms={k: v[0] for k, v in prof.items() if v[1]},
-            model_operator=model,
+            model_operator=model, sigma_p=sigp,
         )
         print(json.dumps(line))
     cell.close()
@@ -520,6 +555,8 @@ def main():
     ap.add_argument("--profile-class", default="persistent_cg")
     ap.add_argument("--model-k", type=int, default=100,
                     help="Lanczos steps timed on the model operator of Eq. model_eq (0: skip)")
+    ap.add_argument("--sigma-p-k", type=int, default=4,
+                    help="Lanczos steps per pole of the Sigma^P leg (Eq. pe; 0: skip)")
     ap.add_argument("--deflation", type=int, default=0,
                     help="lowest conduction states handed to the solvers as a deflation block (0: none)")
     args = ap.parse_args()
