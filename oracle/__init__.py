@@ -24,6 +24,9 @@ against the paper:
                 subs_epsilon).
 * ``sigma_p``   residue term Sigma^P_e(delta) of Eq. pe: one short Lanczos per
                 pole at its real frequency, seeded with v^1/2 |p* e>.
+* ``recycle``   the dielectric matrix at imaginary frequencies from one small
+                basis per occupied state built from the static solutions
+                (Eq. recy_eq).
 * ``gradient``  derivative of <phi|eps^-1(0)|phi> with respect to V_loc (not in
                 the paper; derived by third-order perturbation theory and pinned
                 by central finite differences).

@@ -1,0 +1,62 @@
+"""Pins for the oracle's recycled-basis dielectric matrix (Eq. recy_eq).
+
+At w = 0 the exact static solutions lie in the recycled basis, so the Galerkin
+value is exact; when the 2 n_l recycled vectors span the whole conduction
+space the result is exact at every imaginary frequency.  Both are compared
+with the dielectric operator built from the sum over states.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import pw, recycle, response
+from tests.conftest import rel
+
+
+def _exact(gs, F, w):
+    D = response.Dielectric(gs, 1j * w if w else 0.0)
+    wg = gs.sph.omega_vol / gs.sph.ng
+    return np.array([[(wg * np.dot(F[i], D.apply(F[j], real=False) - F[j])).real for j in range(len(F))]
+                     for i in range(len(F))])
+
+
+def test_static_value_is_exact(small_case):
+    """x(0) is in the basis: the Galerkin value at w = 0 is exact."""
+    _, c, sph, gs = small_case
+    F = W.random_fields(61, 4, sph.ng)
+    got = recycle.recycle_eps(gs, F, [0.0])[0]
+    assert rel(got, _exact(gs, F, 0.0)) < 1e-10
+
+
+@pytest.mark.parametrize("w", [0.3, 1.0, 5.0])
+def test_complete_basis_is_exact_at_all_frequencies(w):
+    """27 plane waves, 2 occupied: 16 fields give 32 recycled vectors that span
+    the 25-dimensional conduction space (the dependent directions are dropped
+    by the truncation), so every imaginary frequency is exact."""
+    wl = W.small(N=8, L=6.0, ecut=2.0, n_occ=2, seed_idx=11)
+    c = wl.cells[0]
+    sph = pw.Sphere(c.L, c.N, c.ecut)
+    gs = pw.ground_state_dense(sph, c.vloc, c.n_occ)
+    assert sph.npw == 27
+    F = W.random_fields(62, 16, sph.ng)
+    for v in range(gs.n_occ):
+        B = recycle.b_vectors(gs, F, v)
+        assert recycle.recycled_basis(gs, v, B).shape[1] == sph.npw - gs.n_occ
+    got = recycle.recycle_eps(gs, F, [w])[0]
+    assert rel(got, _exact(gs, F, w)) < 1e-10
+
+
+def test_incomplete_basis_properties(small_case):
+    """With few fields the value is an approximation at w > 0 (exact at 0):
+    symmetric, positive on the diagonal and decreasing with w, close to the
+    exact matrix."""
+    _, c, sph, gs = small_case
+    F = W.random_fields(63, 3, sph.ng)
+    ws = [0.0, 0.5, 2.0, 10.0]
+    got = recycle.recycle_eps(gs, F, ws)
+    for o in range(len(ws)):
+        assert np.abs(got[o] - got[o].T).max() < 1e-12 * np.abs(got[o]).max()
+        assert (np.diag(got[o]) > 0).all()
+    assert (np.diff(np.array([np.diag(g) for g in got]), axis=0) < 0).all()
+    # six recycled vectors per state (the paper's bases hold hundreds): ~1% here
+    assert rel(got[1], _exact(gs, F, 0.5)) < 2e-2
