@@ -364,6 +364,32 @@ gw_status gw_sigma_p(gw_ctx* ctx, const double* psi_e, double eps_e, double delt
                      int device_ptrs);
 
 /*
+ * gw_recycle_eps -- the dielectric matrix in a basis of fields at any number of
+ * imaginary frequencies from one recycled basis per occupied state (Sec.
+ * "Calculating the dielectric matrix and the integrand at different
+ * frequencies", Eq. recy_eq):
+ *   out[o][l][l'] = <l| eps~(i w_o) - 1 |l'> = 4 sum_v <b_{l,v}| A_v^-1 |b_{l',v}>,
+ *   b_{l,v} = P_c <G| psi_v* v^1/2 l>,  A_v(i w) = ((H - e_v)^2 + w^2) (H - e_v)^-1,
+ * with A_v^-1 applied in the basis gamma_v spanned by the static Sternheimer
+ * solutions x_{l,v}(0) = (H - e_v)^-1 b_{l,v} (solved here, mixed or FP64 as
+ * prec says) and the high-frequency directions P_c (H - e_v) b_{l,v}: each of
+ * the 2 nl vectors is normalised, their Gram matrix is diagonalised (Jacobi,
+ * FP64) and directions with singular value below rtol times the largest are
+ * dropped; then H_v = gamma^H (H - e_v) gamma is diagonalised and every
+ * frequency costs only small dense algebra.  Exact at w = 0 and whenever the
+ * recycled vectors span the conduction space.  Uses the Sternheimer operator
+ * (GW_E_UNSUPPORTED under GW_OP_MODEL).
+ *   fields  [nl][N^3] real (e.g. the Lanczos basis of eps~(0)), 1 <= nl <= 256
+ *   w       [nw] imaginary frequencies w (the frequency is i w), 1 <= nw <= 4096
+ *   rtol    relative singular-value cut-off (0: 1e-6)
+ *   out     [nw][nl][nl] real;  kept (optional, host int): the smallest number
+ *           of recycled directions kept over the occupied states
+ * Returns GW_E_NOCONV if a Jacobi eigensolver does not converge in 40 sweeps.
+ */
+gw_status gw_recycle_eps(gw_ctx* ctx, const double* fields, int nl, const double* w, int nw, double rtol,
+                         double* out, int* kept, gw_prec prec, int device_ptrs);
+
+/*
  * gw_profile -- time selected kernel classes with CUDA events on the work
  * stream (one event pair around each launch; mask 0 turns timing off).
  * Classes (multi-launch CG): 0 scatter + inverse z pass (with the CG p update),

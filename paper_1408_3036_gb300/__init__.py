@@ -29,7 +29,7 @@ EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "
            "gw_set_solver", "gw_set_precond", "gw_set_deflation", "gw_profile", "gw_profile_read", "gw_last_error", "gw_destroy",
            "gw_epsinv_elements_noalloc", "gw_apply_chi0_c", "gw_apply_eps_c", "gw_block_lanczos",
            "gw_epsinv_block", "gw_batch_setup", "gw_batch_size", "gw_batch_cell", "gw_batch_lanczos",
-           "gw_batch_last_error", "gw_batch_destroy", "gw_set_operator", "gw_epsinv_split", "gw_sigma_p")
+           "gw_batch_last_error", "gw_batch_destroy", "gw_set_operator", "gw_epsinv_split", "gw_sigma_p", "gw_recycle_eps")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
                    "refine_fp64", "persistent_cg")
 
@@ -74,6 +74,7 @@ def load(path=LIB_PATH):
         "gw_set_operator": (I, [P, I]),
         "gw_epsinv_split": (I, [P, P, I, P, P, P, I, P, P, P, I, D, P, I]),
         "gw_sigma_p": (I, [P, P, D, D, I, P, P, P, I, P, P, I, I]),
+        "gw_recycle_eps": (I, [P, P, I, P, I, D, P, P, I, I]),
         "gw_set_deflation": (I, [P, I, P, P]),
         "gw_profile": (I, [P, ctypes.c_uint]),
         "gw_profile_read": (I, [P, P, P, I]),
@@ -324,6 +325,21 @@ def gw_sigma_p(ctx, psi_e, eps_e, delta, psi, eps, occ, k, sigma, terms=None, pr
     return sigma, terms
 
 
+def gw_recycle_eps(ctx, fields, w, out, rtol=0.0, prec=GW_FP64):
+    """<l|eps~(i w) - 1|l'> for every w from recycled per-state bases (Eq. recy_eq).
+    Returns the smallest number of recycled directions kept over the states."""
+    pf, d = _ptr(fields)
+    nl = fields.shape[0] if fields.ndim == 2 else 1
+    pw_, _ = _ptr(w)
+    po, e = _ptr(out)
+    if d != e:
+        raise ValueError("mixed host/device buffers")
+    kept = ctypes.c_int(0)
+    _check(ctx, load().gw_recycle_eps(ctx, pf, int(nl), pw_, int(len(w)), float(rtol), po, ctypes.byref(kept),
+                                      int(prec), d))
+    return kept.value
+
+
 def gw_profile(ctx, mask):
     _check(ctx, load().gw_profile(ctx, int(mask)))
 
@@ -457,6 +473,14 @@ class Cell:
         tt = np.zeros(len(ee))
         gw_sigma_p(self.ctx, pe, eps_e, delta, pp, ee, oo, k, sg, tt, prec)
         return float(sg[0]), tt
+
+    def recycle_eps(self, fields, w, rtol=0.0, prec=GW_FP64):
+        """(out [nw][nl][nl], kept) for imaginary frequencies w (host arrays)."""
+        F = np.ascontiguousarray(np.atleast_2d(np.asarray(fields, np.float64)))
+        ww = np.ascontiguousarray(np.asarray(w, np.float64).reshape(-1))
+        out = np.zeros((len(ww), F.shape[0], F.shape[0]))
+        kept = gw_recycle_eps(self.ctx, F, ww, out, rtol, prec)
+        return out, kept
 
     def epsinv_split(self, phi, lz, lz_model, omega=0.0):
         """Eq. subs_epsilon from two host Lanczos results (alpha, beta, basis)."""

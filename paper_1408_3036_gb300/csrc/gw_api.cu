@@ -739,6 +739,39 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
 // ---------------------------------------------------------------------------
 gw_status chi0_reduce(gw_ctx* ctx, const double2* sol64, int nb, int nom, void* dn, bool dn_cplx);
 
+// Right-hand sides of Eqs. P1, P2 in FP64: rhs[b * nocc + v] = P_c Sphere(FFT(conj(u_v) y_b))
+// for nb fields y (real, or complex when y_cplx), in the context buffer "rhs64".
+gw_status rhs_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, double2** out) {
+  using T = double;
+  const int npw = ctx->npw, nocc = ctx->nocc, N3 = ctx->N3;
+  auto& P = ctx->P64;
+  const Geometry& g = ctx->geo;
+  const std::string t = tname<T>();
+  const int nr = nocc * nb;
+  std::vector<int> ca(nr), cy(nr);
+  for (int b = 0; b < nb; ++b)
+    for (int v = 0; v < nocc; ++v) { ca[b * nocc + v] = v; cy[b * nocc + v] = b; }
+  int *dca, *dcy;
+  TRY(upload_table(ctx, "rhs_ca", ca, &dca));
+  TRY(upload_table(ctx, "rhs_cy", cy, &dcy));
+  cpx<T>* grid;
+  TRY(getbuf(ctx, "g_rhs" + t, (size_t)nr * N3, &grid));
+  double2* rhs64;
+  TRY(getbuf(ctx, "rhs64", (size_t)nr * npw, &rhs64));
+  TRY(ensure_work(ctx, std::max(nr, 1)));
+  launch_xpass_prod_fwd<T>(ctx->st, g, P, ctx->plan, reinterpret_cast<const cpx<T>*>(y), y_cplx ? 1 : 0, P.U, 0, 1,
+                           dca, dcy, grid, nr);
+  launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, nullptr, nr, 0);
+  launch_zpass<T>(ctx->st, Z_GATHER_FWD, g, P, ctx->plan, grid, rhs64, nullptr, nullptr, nullptr, nullptr, nullptr,
+                  nullptr, nullptr, nr);
+  // P_c once: psi_v* y has a large component along the occupied states (e.g.
+  // <psi_v|y psi_v>) and one pass leaves |C C^H - 1| times it behind; the
+  // solver's FP64 residual P_c (b - A x) removes that remnant
+  launch_proj<double>(ctx->st, ctx->P64.C, nocc, npw, rhs64, nr, nullptr, ctx->work, nullptr, nullptr);
+  *out = rhs64;
+  return launch_check(ctx, "rhs");
+}
+
 // ---------------------------------------------------------------------------
 // The model operator (Sec. Dielectric model, Eq. model_eq), every step in
 // precision T: H -> T in Eq. P2a turns each Sternheimer solve into one
@@ -813,35 +846,10 @@ gw_status chi0_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, const std::
   if (ctx->op == GW_OP_MODEL)
     return chi0_model_core<double>(ctx, reinterpret_cast<const double*>(y), y_cplx, nb, omega,
                                    reinterpret_cast<double*>(dn), dn_cplx);
-  using T = double;
-  const int npw = ctx->npw, nocc = ctx->nocc, N3 = ctx->N3;
+  const int npw = ctx->npw, nocc = ctx->nocc;
   const int nom = (int)omega.size();
-  auto& P = ctx->P64;
-  const Geometry& g = ctx->geo;
-  const std::string t = tname<T>();
-  // -- right-hand sides
-  const int nr = nocc * nb;
-  std::vector<int> ca(nr), cy(nr);
-  for (int b = 0; b < nb; ++b)
-    for (int v = 0; v < nocc; ++v) { ca[b * nocc + v] = v; cy[b * nocc + v] = b; }
-  int *dca, *dcy;
-  TRY(upload_table(ctx, "rhs_ca", ca, &dca));
-  TRY(upload_table(ctx, "rhs_cy", cy, &dcy));
-  cpx<T>* grid;
-  TRY(getbuf(ctx, "g_rhs" + t, (size_t)nr * N3, &grid));
   double2* rhs64;
-  TRY(getbuf(ctx, "rhs64", (size_t)nr * npw, &rhs64));
-  TRY(ensure_work(ctx, std::max(nr, 1)));
-  launch_xpass_prod_fwd<T>(ctx->st, g, P, ctx->plan, reinterpret_cast<const cpx<T>*>(y), y_cplx ? 1 : 0, P.U, 0, 1,
-                           dca, dcy, grid, nr);
-  launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, nullptr, nr, 0);
-  launch_zpass<T>(ctx->st, Z_GATHER_FWD, g, P, ctx->plan, grid, rhs64, nullptr, nullptr, nullptr, nullptr, nullptr,
-                  nullptr, nullptr, nr);
-  // P_c once: psi_v* y has a large component along the occupied states (e.g.
-  // <psi_v|y psi_v>) and one pass leaves |C C^H - 1| times it behind; the
-  // solver's FP64 residual P_c (b - A x) removes that remnant
-  launch_proj<double>(ctx->st, ctx->P64.C, nocc, npw, rhs64, nr, nullptr, ctx->work, nullptr, nullptr);
-  TRY(launch_check(ctx, "rhs"));
+  TRY(rhs_core(ctx, y, y_cplx, nb, &rhs64));
   double2* sol64;
   const int nsol = nom * nb * nocc;
   TRY(getbuf(ctx, "sol64", (size_t)nsol * npw, &sol64));
@@ -1667,6 +1675,131 @@ gw_status upload_projector(gw_ctx* ctx, const std::vector<zc>& cdef) {
 
 }  // namespace
 
+// Eq. recy_eq: <l|eps~(i w) - 1|l'> = 4 sum_v <b_{l,v}|A_v^-1(i w)|b_{l',v}> with A_v^-1
+// applied in the recycled basis of state v (the static solutions x(0) and the
+// high-frequency directions x(i inf) = P_c (H - e_v) b, orthonormalised through
+// the eigendecomposition of their Gram matrix).  F [nl][N_g] real fields on
+// the device; out [nw][nl][nl] on the device.
+template <typename S>
+gw_status recycle_core(gw_ctx* ctx, const double* F, int nl, const double* dw, int nw, double rtol, double* out,
+                       int* kept_min) {
+  const int npw = ctx->npw, nocc = ctx->nocc, N3 = ctx->N3;
+  const int m = 2 * nl, nc = nl * nocc, nx = nocc * m;
+  auto& P = ctx->P64;
+  // right-hand sides b[l * nocc + v]
+  double* y;
+  TRY(getbuf(ctx, "rc_y", (size_t)nl * N3, &y));
+  TRY(sqrtv<double>(ctx, F, nl, y, nullptr));
+  double2* b;
+  TRY(rhs_core(ctx, y, false, nl, &b));
+  double2* bcp;
+  TRY(getbuf(ctx, "rc_b", (size_t)nc * npw, &bcp));
+  CK(cudaMemcpyAsync(bcp, b, (size_t)nc * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
+  // x(0) (rows 0 .. nc-1 of xc) and x(i inf) (rows nc .. 2 nc - 1)
+  std::vector<double2> E(nc);
+  std::vector<double> tk(nc);
+  for (int j = 0; j < nc; ++j) {
+    E[j] = make_double2(ctx->eps[j % nocc], 0.0);
+    tk[j] = ctx->tkin[j % nocc];
+  }
+  double2* dE;
+  double* dtk = nullptr;
+  TRY(upload_table(ctx, "rc_E", E, &dE));
+  if (ctx->precond) TRY(upload_table(ctx, "rc_tk", tk, &dtk));
+  double2* xc;
+  TRY(getbuf(ctx, "rc_x", (size_t)2 * nc * npw, &xc));
+  for (int j0 = 0; j0 < nc; j0 += kPersistentMaxCols) {
+    const int nj = std::min(kPersistentMaxCols, nc - j0);
+    TRY(solve<S>(ctx, nj, bcp + (size_t)j0 * npw, dE + j0, xc + (size_t)j0 * npw, false, dtk ? dtk + j0 : nullptr));
+  }
+  TRY(h_apply<double>(ctx, bcp, nc, dE, nullptr, xc + (size_t)nc * npw));
+  TRY(ensure_work(ctx, std::max(nx, nc)));
+  launch_proj<double>(ctx->st, P.C, nocc, npw, xc + (size_t)nc * npw, nc, nullptr, ctx->work, nullptr, nullptr);
+  // per state v: X_v rows [x_{l,v}(0); x_{l,v}(i inf)] normalised, and b_v rows
+  std::vector<int> ix(nx), ib(nc), vrow(nx);
+  for (int v = 0; v < nocc; ++v)
+    for (int i = 0; i < m; ++i) {
+      ix[v * m + i] = (i < nl) ? i * nocc + v : nc + (i - nl) * nocc + v;
+      vrow[v * m + i] = v;
+    }
+  for (int v = 0; v < nocc; ++v)
+    for (int l = 0; l < nl; ++l) ib[v * nl + l] = l * nocc + v;
+  int *dix, *dib;
+  TRY(upload_table(ctx, "rc_ix", ix, &dix));
+  TRY(upload_table(ctx, "rc_ib", ib, &dib));
+  double2 *X, *HX, *B;
+  TRY(getbuf(ctx, "rc_X", (size_t)nx * npw, &X));
+  TRY(getbuf(ctx, "rc_HX", (size_t)nx * npw, &HX));
+  TRY(getbuf(ctx, "rc_B", (size_t)nc * npw, &B));
+  launch_gather_rows<double, double>(ctx->st, npw, nx, xc, dix, X);
+  launch_gather_rows<double, double>(ctx->st, npw, nc, bcp, dib, B);
+  launch_normalize_rows(ctx->st, X, nx, npw);
+  std::vector<double2> Ex(nx);
+  for (int j = 0; j < nx; ++j) Ex[j] = make_double2(ctx->eps[vrow[j]], 0.0);
+  double2* dEx;
+  TRY(upload_table(ctx, "rc_Ex", Ex, &dEx));
+  TRY(h_apply<double>(ctx, X, nx, dEx, nullptr, HX));
+  // Gram, Hamiltonian and right-hand-side matrices of every state (real: the
+  // fields and the occupied states are real in real space)
+  double2 *cg, *gpart;
+  unsigned* gcnt;
+  const int nchunk = (npw + 4095) / 4096;
+  TRY(getbuf(ctx, "rc_cg", (size_t)m * m, &cg));
+  TRY(getbuf(ctx, "rc_gpart", (size_t)nchunk * m * m, &gpart));
+  if (!ctx->bufs.count("rc_gcnt") || ctx->bufs["rc_gcnt"].second < (size_t)m * sizeof(unsigned)) {
+    TRY(getbuf(ctx, "rc_gcnt", (size_t)m, &gcnt));
+    CK(cudaMemsetAsync(gcnt, 0, (size_t)m * sizeof(unsigned), ctx->st));
+  } else {
+    TRY(getbuf(ctx, "rc_gcnt", (size_t)m, &gcnt));
+  }
+  double *Sm, *Hm, *Bm, *W, *T, *Hg, *Bg, *U, *C, *tmp;
+  const size_t mm = (size_t)m * m, mb = (size_t)m * nl;
+  TRY(getbuf(ctx, "rc_S", nocc * mm, &Sm));
+  TRY(getbuf(ctx, "rc_H", nocc * mm, &Hm));
+  TRY(getbuf(ctx, "rc_Bm", nocc * mb, &Bm));
+  TRY(getbuf(ctx, "rc_W", nocc * mm, &W));
+  TRY(getbuf(ctx, "rc_T", nocc * mm, &T));
+  TRY(getbuf(ctx, "rc_Hg", nocc * mm, &Hg));
+  TRY(getbuf(ctx, "rc_Bg", nocc * mb, &Bg));
+  TRY(getbuf(ctx, "rc_U", nocc * mm, &U));
+  TRY(getbuf(ctx, "rc_C", nocc * mb, &C));
+  TRY(getbuf(ctx, "rc_tmp", nocc * mm, &tmp));
+  for (int v = 0; v < nocc; ++v) {
+    const double2* Xv = X + (size_t)v * m * npw;
+    launch_cgram(ctx->st, Xv, m, Xv, m, npw, 1, 1.0, gpart, gcnt, cg);
+    launch_real_part(ctx->st, mm, cg, Sm + v * mm);
+    launch_cgram(ctx->st, Xv, m, HX + (size_t)v * m * npw, m, npw, 1, 1.0, gpart, gcnt, cg);
+    launch_real_part(ctx->st, mm, cg, Hm + v * mm);
+    launch_cgram(ctx->st, Xv, m, B + (size_t)v * nl * npw, nl, npw, 1, 1.0, gpart, gcnt, cg);
+    launch_real_part(ctx->st, mb, cg, Bm + v * mb);
+  }
+  launch_symmetrize(ctx->st, nocc, m, Sm);
+  launch_symmetrize(ctx->st, nocc, m, Hm);
+  int *sweeps, *kept;
+  TRY(getbuf(ctx, "rc_sweeps", (size_t)2 * nocc, &sweeps));
+  TRY(getbuf(ctx, "rc_kept", (size_t)nocc, &kept));
+  constexpr int kSweeps = 40;
+  CK(launch_jacobi_sym(ctx->st, nocc, m, Sm, W, 1e-14, kSweeps, sweeps));
+  launch_orth_transform(ctx->st, nocc, m, Sm, W, rtol * rtol, T, kept);
+  // H_gamma = T^T H T, b_gamma = T^T B; eigenvectors U of H_gamma; c = U^T b_gamma
+  launch_gemm_small(ctx->st, nocc, m, m, m, Hm, 0, T, 0, tmp);
+  launch_gemm_small(ctx->st, nocc, m, m, m, T, 1, tmp, 0, Hg);
+  launch_gemm_small(ctx->st, nocc, m, m, nl, T, 1, Bm, 0, Bg);
+  launch_symmetrize(ctx->st, nocc, m, Hg);
+  CK(launch_jacobi_sym(ctx->st, nocc, m, Hg, U, 1e-14, kSweeps, sweeps + nocc));
+  launch_gemm_small(ctx->st, nocc, m, m, nl, U, 1, Bg, 0, C);
+  launch_recycled_form(ctx->st, nocc, m, nl, nw, Hg, C, dw, out);
+  TRY(launch_check(ctx, "recycle"));
+  std::vector<int> hs(2 * nocc), hk(nocc);
+  CK(cudaMemcpyAsync(hs.data(), sweeps, 2 * nocc * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(hk.data(), kept, nocc * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  TRY(sync(ctx, "recycle"));
+  for (int v = 0; v < 2 * nocc; ++v)
+    if (hs[v] > kSweeps) return fail(ctx, GW_E_NOCONV, "Jacobi eigensolver did not converge in the recycled basis");
+  *kept_min = *std::min_element(hk.begin(), hk.end());
+  return GW_OK;
+}
+
 extern "C" {
 
 gw_status gw_setup(gw_ctx** out, double L, int n_grid, double ecut, const double* vloc, int coulomb,
@@ -2272,6 +2405,40 @@ gw_status gw_sigma_p(gw_ctx* ctx, const double* psi_e, double eps_e, double delt
     if (terms) std::copy(hterms.begin(), hterms.end(), terms);
   }
   return launch_check(ctx, "sigma_p");
+}
+
+gw_status gw_recycle_eps(gw_ctx* ctx, const double* fields, int nl, const double* w, int nw, double rtol,
+                         double* out, int* kept, gw_prec prec, int dev) {
+  TRY(begin(ctx));
+  TRY(need_occ(ctx));
+  if (!fields || !w || !out || nl < 1 || nl > 256 || nw < 1 || nw > 4096 || rtol < 0.0 || rtol >= 1.0)
+    return fail(ctx, GW_E_ARG, "bad arguments");
+  if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_E_ARG, "bad precision");
+  if (ctx->op != GW_OP_STERNHEIMER)
+    return fail(ctx, GW_E_UNSUPPORTED, "the recycled basis is built from Sternheimer solutions");
+  if (rtol == 0.0) rtol = 1e-6;
+  for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
+  const void *F, *W;
+  TRY(stage_in(ctx, "rce_F", fields, (size_t)nl * ctx->N3 * sizeof(double), dev, &F));
+  TRY(stage_in(ctx, "rce_w", w, (size_t)nw * sizeof(double), dev, &W));
+  std::vector<double> hw(nw);
+  CK(cudaMemcpyAsync(hw.data(), W, nw * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  TRY(sync(ctx, "recycle inputs"));
+  for (double x : hw)
+    if (!std::isfinite(x)) return fail(ctx, GW_E_NONFINITE, "non-finite frequency");
+  void* o;
+  TRY(stage_out(ctx, "rce_out", out, (size_t)nw * nl * nl * sizeof(double), dev, &o));
+  int km = 0;
+  gw_status st = (prec == GW_FP64)
+                     ? recycle_core<double>(ctx, reinterpret_cast<const double*>(F), nl,
+                                            reinterpret_cast<const double*>(W), nw, rtol, reinterpret_cast<double*>(o), &km)
+                     : recycle_core<float>(ctx, reinterpret_cast<const double*>(F), nl,
+                                           reinterpret_cast<const double*>(W), nw, rtol, reinterpret_cast<double*>(o), &km);
+  if (st != GW_OK) return st;
+  TRY(copy_back(ctx, out, o, (size_t)nw * nl * nl * sizeof(double), dev));
+  if (kept) *kept = km;
+  if (ctx->stats[0] > 0) ctx->stats[2] /= ctx->stats[0];
+  return finish(ctx, GW_OK);
 }
 
 gw_status gw_set_precond(gw_ctx* ctx, int kind) {

@@ -119,6 +119,19 @@ void launch_tridiag_inv(cudaStream_t s, int K, const double* alpha, const double
 
 template <typename T> cudaError_t fft_set_smem_limits();
 
+// small dense FP64 algebra of the recycled bases (kernels_small.cu)
+void launch_normalize_rows(cudaStream_t s, double2* rows, int nrows, size_t n);
+void launch_real_part(cudaStream_t s, size_t n, const double2* src, double* dst);
+void launch_symmetrize(cudaStream_t s, int nb, int m, double* A);
+cudaError_t launch_jacobi_sym(cudaStream_t s, int nb, int m, double* A, double* V, double tol, int max_sweeps,
+                              int* sweeps);
+void launch_gemm_small(cudaStream_t s, int nb, int r, int k, int c, const double* A, int ta, const double* B, int tb,
+                       double* C);
+void launch_orth_transform(cudaStream_t s, int nb, int m, const double* S, const double* W, double rel, double* T,
+                           int* kept);
+void launch_recycled_form(cudaStream_t s, int nbat, int m, int nl, int nw, const double* L, const double* c,
+                          const double* w, double* out);
+
 // block Lanczos helpers (complex grid fields)
 void launch_cgram(cudaStream_t s, const double2* X, int mx, const double2* Y, int my, size_t n, int conj_x,
                   double wgt, double2* partial, unsigned* cnt, double2* out);
