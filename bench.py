@@ -17,7 +17,10 @@ model dielectric operator of Sec. Dielectric model (Eq. model_eq, H -> T:
 one kinetic division per Sternheimer solve) on the same cell and start
 vector (``--model-k 0`` skips it), and ``sigma_p`` times the residue term of
 Eq. pe for the highest occupied state, one four-step Lanczos per pole at its
-real frequency (``--sigma-p-k 0`` skips it).
+real frequency (``--sigma-p-k 0`` skips it), and ``recycle`` builds
+eps~(i w) - 1 in the first Lanczos vectors at many imaginary frequencies from
+one recycled basis per occupied state (Eq. recy_eq; ``--recycle-nl 0`` skips
+it), against one direct application at w = 0.5i.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 instead, on a bounded sample of the same workload.
@@ -419,6 +422,45 @@ def run_gpu(args):
     e2e = dict(value=world * K / (te2e / 1e3), unit=UNIT, h2d_bytes_per_step=ng * 8,
                d2h_bytes_per_step=(2 * K - 1) * 8)
 
+    # --- eps~(i w) - 1 in the first Lanczos vectors from recycled per-state bases (Eq. recy_eq)
+    rec = None
+    if args.recycle_nl > 0:
+        nl = min(args.recycle_nl, K)
+        Fq = Q[:nl].contiguous()
+        w8 = np.array([0.05, 0.1, 0.2, 0.5, 1.0, 2.0, 5.0, 10.0])
+        w64 = np.geomspace(0.01, 100.0, 64)
+        o8 = torch.empty((len(w8), nl, nl), dtype=torch.float64, device=dev)
+        o64 = torch.empty((len(w64), nl, nl), dtype=torch.float64, device=dev)
+        tw8 = torch.tensor(w8, device=dev)
+        tw64 = torch.tensor(w64, device=dev)
+        kept = gw.gw_recycle_eps(cell.ctx, Fq, tw8, o8, 0.0, prec)      # warm-up
+        rt = []
+        for tw, oo in ((tw8, o8), (tw64, o64)):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            kept = gw.gw_recycle_eps(cell.ctx, Fq, tw, oo, 0.0, prec)
+            e1.record(stream)
+            e1.synchronize()
+            rt.append(e0.elapsed_time(e1))
+        # direct: nl eps~ applications at w = 0.5i (SQMR), then <l|.>
+        yd = torch.empty((1, nl, ng), dtype=torch.complex128, device=dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gw.gw_apply_eps(cell.ctx, Fq, [0.5j], torch.view_as_real(yd), prec)
+        e1.record(stream)
+        e1.synchronize()
+        t_dir = e0.elapsed_time(e1)
+        wgt = c.L ** 3 / ng
+        Ed = (wgt * (Fq @ (yd[0].real - Fq).T)).cpu().numpy()
+        Er = o8[3].cpu().numpy()
+        rec = dict(fields=nl, precision=args.prec, kept_min=int(kept), ms_8_frequencies=rt[0],
+                   ms_64_frequencies=rt[1], ms_per_extra_frequency=(rt[1] - rt[0]) / 56.0,
+                   direct_ms_one_frequency=t_dir,
+                   rel_err_vs_direct_at_0p5i=float(np.abs(Er - Ed).max() / np.abs(Ed).max()))
+
     # --- model operator (Eq. model_eq) on the same cell and start vector
     model = None
     if args.model_k > 0:
@@ -531,7 +573,7 @@ def run_gpu(args):
                         column_iterations_per_step=it_cols / args.steps, geometry=geo),
             roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
             clocks=clk.summary(), fp64=fp64, profile_ms={k: v[0] for k, v in prof.items() if v[1]},
-            model_operator=model, sigma_p=sigp,
+            model_operator=model, sigma_p=sigp, recycle=rec,
         )
         print(json.dumps(line))
     cell.close()
@@ -555,6 +597,8 @@ def main():
     ap.add_argument("--profile-class", default="persistent_cg")
     ap.add_argument("--model-k", type=int, default=100,
                     help="Lanczos steps timed on the model operator of Eq. model_eq (0: skip)")
+    ap.add_argument("--recycle-nl", type=int, default=20,
+                    help="Lanczos vectors in which eps~(i w) - 1 is built from recycled bases (Eq. recy_eq; 0: skip)")
     ap.add_argument("--sigma-p-k", type=int, default=4,
                     help="Lanczos steps per pole of the Sigma^P leg (Eq. pe; 0: skip)")
     ap.add_argument("--deflation", type=int, default=0,
