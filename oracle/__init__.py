@@ -27,6 +27,9 @@ against the paper:
 * ``recycle``   the dielectric matrix at imaginary frequencies from one small
                 basis per occupied state built from the static solutions
                 (Eq. recy_eq).
+* ``sigma_c``   the correlation self-energy Sigma^c_e(delta) (Eq. e_c): the
+                frequency integral, the Lorentzian analytic term and the
+                residue term, by the sum over states and in a basis of fields.
 * ``gradient``  derivative of <phi|eps^-1(0)|phi> with respect to V_loc (not in
                 the paper; derived by third-order perturbation theory and pinned
                 by central finite differences).
