@@ -390,6 +390,36 @@ gw_status gw_recycle_eps(gw_ctx* ctx, const double* fields, int nl, const double
                          double* out, int* kept, gw_prec prec, int device_ptrs);
 
 /*
+ * gw_sigma_c -- the correlation self-energy of an occupied state e (Eq. e_c):
+ *   Sigma^c_e(delta) = (1/pi) int_0^inf dw (sigma^N_e(i w) - sigma^N0_e(i w)) + Sigma^A_e + Sigma^P_e,
+ * evaluated in a basis {l} of fields as Eqs. ge, g0e, he and khe write it:
+ *   sigma^N(i w) = sum_ll' M_ll'(i w) <z_l| g(H - c, w) |z_l'>,  g(h) = h / (w^2 + h^2),
+ *   sigma^N0(i w) = f(w) sum_ll' M_ll'(0) <z_l| g(H - c, w) |z_l'>,  f(w) = alpha^2 / (w^2 + alpha^2),
+ *   Sigma^A = 1/2 sum_ll' M_ll'(0) (<z_l|Q_e|h+_l'> + <z_l|P_e|h-_l'>)   (Eq. khe for h+-),
+ * with c = e_e + delta, z_l = Phi_e v^1/2 |l*> (psi_e(r) (v^1/2 l)(r) in the
+ * plane-wave sphere), M = eps~^-1 - 1 in the basis from the recycled
+ * eps~(i w) (gw_recycle_eps) as (1 + E)^-1 - 1, <z|g(H - c)|z'> for every
+ * frequency from one block Lanczos recursion of k_h steps on H - c started
+ * with the z block (shift-Lanczos), h+ by the Sternheimer solver at the shift
+ * c - alpha, the P_e part in closed form on the occupied states below c, and
+ * Sigma^P from gw_sigma_p (k_p steps per pole).  The frequency integral uses
+ * w = (1 + t)/(1 - t) at n_freq Gauss-Legendre nodes in t.
+ * Written for e_HOMO <= e_e + delta < e_LUMO, where Q_e(delta) is the
+ * conduction projector; e_e + delta below the highest occupied energy returns
+ * GW_E_UNSUPPORTED, and staying below the lowest conduction energy is the
+ * caller's part (the library holds no conduction states).
+ *   e        occupied state (0 <= e < n_occ, in the order of gw_set_occupied)
+ *   alpha    Lorentzian width (Ha), > 0 (the paper takes 1 Ha)
+ *   n_freq   1 .. 64 (the paper: about 8 to 10 converge to 1 meV)
+ *   fields   [nl][N^3] real, orthonormal in <.|.> (e.g. the Lanczos basis of
+ *            eps~(0)); 1 <= nl <= 16
+ *   k_h      block Lanczos steps on H, k_h nl <= 512;  k_p as in gw_sigma_p
+ *   out      [4]: Sigma^c, the frequency integral, Sigma^A, Sigma^P (Ha)
+ */
+gw_status gw_sigma_c(gw_ctx* ctx, int e, double delta, double alpha, int n_freq, const double* fields, int nl,
+                     int k_h, int k_p, double* out, gw_prec prec, int device_ptrs);
+
+/*
  * gw_profile -- time selected kernel classes with CUDA events on the work
  * stream (one event pair around each launch; mask 0 turns timing off).
  * Classes (multi-launch CG): 0 scatter + inverse z pass (with the CG p update),

@@ -29,7 +29,7 @@ EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "
            "gw_set_solver", "gw_set_precond", "gw_set_deflation", "gw_profile", "gw_profile_read", "gw_last_error", "gw_destroy",
            "gw_epsinv_elements_noalloc", "gw_apply_chi0_c", "gw_apply_eps_c", "gw_block_lanczos",
            "gw_epsinv_block", "gw_batch_setup", "gw_batch_size", "gw_batch_cell", "gw_batch_lanczos",
-           "gw_batch_last_error", "gw_batch_destroy", "gw_set_operator", "gw_epsinv_split", "gw_sigma_p", "gw_recycle_eps")
+           "gw_batch_last_error", "gw_batch_destroy", "gw_set_operator", "gw_epsinv_split", "gw_sigma_p", "gw_recycle_eps", "gw_sigma_c")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
                    "refine_fp64", "persistent_cg")
 
@@ -75,6 +75,7 @@ def load(path=LIB_PATH):
         "gw_epsinv_split": (I, [P, P, I, P, P, P, I, P, P, P, I, D, P, I]),
         "gw_sigma_p": (I, [P, P, D, D, I, P, P, P, I, P, P, I, I]),
         "gw_recycle_eps": (I, [P, P, I, P, I, D, P, P, I, I]),
+        "gw_sigma_c": (I, [P, I, D, D, I, P, I, I, I, P, I, I]),
         "gw_set_deflation": (I, [P, I, P, P]),
         "gw_profile": (I, [P, ctypes.c_uint]),
         "gw_profile_read": (I, [P, P, P, I]),
@@ -340,6 +341,18 @@ def gw_recycle_eps(ctx, fields, w, out, rtol=0.0, prec=GW_FP64):
     return kept.value
 
 
+def gw_sigma_c(ctx, e, delta, alpha, n_freq, fields, k_h, k_p, out, prec=GW_FP64):
+    """Sigma^c of occupied state e (Eq. e_c): out[4] = total, integral, Sigma^A, Sigma^P."""
+    pf, d = _ptr(fields)
+    nl = fields.shape[0] if fields.ndim == 2 else 1
+    po, e2 = _ptr(out)
+    if d != e2:
+        raise ValueError("mixed host/device buffers")
+    _check(ctx, load().gw_sigma_c(ctx, int(e), float(delta), float(alpha), int(n_freq), pf, int(nl), int(k_h),
+                                  int(k_p), po, int(prec), d))
+    return out
+
+
 def gw_profile(ctx, mask):
     _check(ctx, load().gw_profile(ctx, int(mask)))
 
@@ -481,6 +494,13 @@ class Cell:
         out = np.zeros((len(ww), F.shape[0], F.shape[0]))
         kept = gw_recycle_eps(self.ctx, F, ww, out, rtol, prec)
         return out, kept
+
+    def sigma_c(self, e, delta, fields, alpha=1.0, n_freq=8, k_h=8, k_p=4, prec=GW_FP64):
+        """dict(total, integral, SA, SP) of Eq. e_c for occupied state e (host arrays)."""
+        F = np.ascontiguousarray(np.atleast_2d(np.asarray(fields, np.float64)))
+        out = np.zeros(4)
+        gw_sigma_c(self.ctx, e, delta, alpha, n_freq, F, k_h, k_p, out, prec)
+        return dict(total=out[0], integral=out[1], SA=out[2], SP=out[3])
 
     def epsinv_split(self, phi, lz, lz_model, omega=0.0):
         """Eq. subs_epsilon from two host Lanczos results (alpha, beta, basis)."""

@@ -1188,25 +1188,24 @@ static std::vector<zcd> inv_transpose_upper(const std::vector<zcd>& R, int b) {
   return M;
 }
 
-template <typename S>
-gw_status block_lanczos_core(gw_ctx* ctx, const double* start, int blk, int K, double2 omega,
-                             std::vector<zcd>* Aout, std::vector<zcd>* Bout, double2* Q) {
-  const int N3 = ctx->N3;
-  const size_t n = (size_t)N3;
-  const double wgt = ctx->vol / N3;
-  const bool bil = (omega.y != 0.0);
+// The block recursion on vectors of length n with inner-product weight wgt
+// (Hermitian, or bilinear when bil), for any operator op(Qk, W) applied to blk
+// rows: Q [K blk][n] receives the basis (Q_0 from the complex start block X0,
+// which is overwritten), A/B the block coefficients, R0 (optional) the factor
+// of the start block, X0 rows = sum_i R0[i][l] q_i.
+template <class Op>
+gw_status block_lanczos_run(gw_ctx* ctx, size_t n, double wgt, bool bil, int blk, int K, double2* X0, double2* Q,
+                            Op op, std::vector<zcd>* Aout, std::vector<zcd>* Bout, std::vector<zcd>* R0) {
   const int cj = bil ? 0 : 1;
   const int mmax = K * blk;
-  double2 *W, *X0, *gram, *part, *M;
+  double2 *W, *gram, *part, *M;
   unsigned* cnt;
   TRY(getbuf(ctx, "bl_W", (size_t)blk * n, &W));
-  TRY(getbuf(ctx, "bl_X0", (size_t)blk * n, &X0));
   TRY(getbuf(ctx, "bl_gram", (size_t)mmax * blk, &gram));
   TRY(getbuf(ctx, "bl_part", ((n + 4095) / 4096) * (size_t)mmax * blk, &part));
   TRY(getbuf(ctx, "bl_M", (size_t)blk * mmax, &M));
   TRY(getbuf(ctx, "bl_cnt", (size_t)(blk + 7) / 8 + 1, &cnt));
   CK(cudaMemsetAsync(cnt, 0, ((size_t)(blk + 7) / 8 + 1) * sizeof(unsigned), ctx->st));
-  std::vector<double2> om(1, omega);
   auto gram_host = [&](const double2* X, int mx, const double2* Y, std::vector<zcd>* out) -> gw_status {
     launch_cgram(ctx->st, X, mx, Y, blk, n, cj, wgt, part, cnt, gram);
     std::vector<double2> h((size_t)mx * blk);
@@ -1224,21 +1223,18 @@ gw_status block_lanczos_core(gw_ctx* ctx, const double* start, int blk, int K, d
     launch_cgemm_n(ctx->st, M, my, mx, X, n, Y, acc, sign);
     return launch_check(ctx, "block combine");
   };
-  // Q_0 from the real start block
   {
-    const size_t tot = (size_t)blk * n;
-    ++g_launches;
-    k_promote<<<(int)std::min<size_t>((tot + 255) / 256, 152 * 8), 256, 0, ctx->st>>>(tot, start, X0);
     std::vector<zcd> G, R;
     TRY(gram_host(X0, blk, X0, &G));
     if (!chol_upper(G, blk, bil, &R)) return fail(ctx, GW_E_BREAKDOWN, "start block is rank deficient");
     TRY(combine(inv_transpose_upper(R, blk), blk, blk, X0, Q, 0, 1.0));
+    if (R0) *R0 = R;
   }
   Aout->assign((size_t)K * blk * blk, zcd(0, 0));
   Bout->assign((size_t)std::max(K - 1, 1) * blk * blk, zcd(0, 0));
   for (int k = 0; k < K; ++k) {
     double2* Qk = Q + (size_t)k * blk * n;
-    TRY(eps_core<S>(ctx, Qk, true, blk, om, W, false));
+    TRY(op(Qk, W));
     if (k > 0) {
       std::vector<zcd> Bp(Bout->begin() + (size_t)(k - 1) * blk * blk, Bout->begin() + (size_t)k * blk * blk);
       if (!bil)
@@ -1268,6 +1264,21 @@ gw_status block_lanczos_core(gw_ctx* ctx, const double* start, int blk, int K, d
     TRY(combine(inv_transpose_upper(R, blk), blk, blk, W, Q + (size_t)(k + 1) * blk * n, 0, 1.0));
   }
   return launch_check(ctx, "block lanczos");
+}
+
+template <typename S>
+gw_status block_lanczos_core(gw_ctx* ctx, const double* start, int blk, int K, double2 omega,
+                             std::vector<zcd>* Aout, std::vector<zcd>* Bout, double2* Q) {
+  const int N3 = ctx->N3;
+  const size_t n = (size_t)N3;
+  double2* X0;
+  TRY(getbuf(ctx, "bl_X0", (size_t)blk * n, &X0));
+  const size_t tot = (size_t)blk * n;
+  ++g_launches;
+  k_promote<<<(int)std::min<size_t>((tot + 255) / 256, 152 * 8), 256, 0, ctx->st>>>(tot, start, X0);
+  const std::vector<double2> om(1, omega);
+  auto op = [&](double2* Qk, double2* W) -> gw_status { return eps_core<S>(ctx, Qk, true, blk, om, W, false); };
+  return block_lanczos_run(ctx, n, ctx->vol / N3, omega.y != 0.0, blk, K, X0, Q, op, Aout, Bout, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1800,6 +1811,291 @@ gw_status recycle_core(gw_ctx* ctx, const double* F, int nl, const double* dw, i
   return GW_OK;
 }
 
+// Eq. pe for candidate states given on the device (psi_e [N_PW], psi [n][N_PW]
+// complex) with host energies and occupations; *total and (*terms)[n] out.
+gw_status sigma_p_core(gw_ctx* ctx, const double2* psi_e, double eps_e, double delta, int n, const double2* psi,
+                       const std::vector<double>& he, const std::vector<int>& ho, int k, gw_prec prec,
+                       double* total_out, std::vector<double>* terms) {
+  const int npw = ctx->npw, N3 = ctx->N3;
+  const double wgt = ctx->vol / N3;
+  // the poles that Theta keeps, with their weights -Theta(w) (occupied) or Theta(-w)
+  std::vector<int> pole;
+  std::vector<double> pw_, pom;
+  for (int j = 0; j < n; ++j) {
+    if (!std::isfinite(he[j])) return fail(ctx, GW_E_NONFINITE, "non-finite energy");
+    const double om = he[j] - eps_e - delta;
+    const double th = ho[j] ? (om > 0 ? 1.0 : (om == 0 ? 0.5 : 0.0)) : (om < 0 ? 1.0 : (om == 0 ? 0.5 : 0.0));
+    if (th == 0.0) continue;
+    pole.push_back(j);
+    pw_.push_back(ho[j] ? -th : th);
+    pom.push_back(om);
+  }
+  std::vector<double>& hterms = *terms;
+  hterms.assign(n, 0.0);
+  double total = 0.0;
+  const int np = (int)pole.size();
+  if (np > 0) {
+    // grids u_e and u_p of the states (sphere -> grid, FP64), then the pair products
+    const double2* pe = psi_e;
+    const double2* pp = psi;
+    double2 *cs, *ug;
+    double *seeds, *al, *be, *Q, *n2, *Ti, *d, *l;
+    int* stat;
+    TRY(getbuf(ctx, "sgp_cs", (size_t)(np + 1) * npw, &cs));
+    TRY(getbuf(ctx, "sgp_ug", (size_t)(np + 1) * N3, &ug));
+    for (int i = 0; i < np; ++i)
+      CK(cudaMemcpyAsync(cs + (size_t)i * npw, pp + (size_t)pole[i] * npw,
+                         npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(cs + (size_t)np * npw, pe, npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
+    const Geometry& g = ctx->geo;
+    launch_zpass<double>(ctx->st, Z_SCATTER_INV, g, ctx->P64, ctx->plan, ug, cs, nullptr, nullptr, nullptr, nullptr,
+                         nullptr, nullptr, nullptr, np + 1);
+    launch_ypass<double>(ctx->st, 1, 1, 0, g, ctx->P64, ctx->plan, ug, nullptr, np + 1, 0);
+    launch_xpass_mul<double>(ctx->st, 1, 1, 0, g, ctx->P64, ctx->plan, ug, nullptr, nullptr, np + 1);
+    double* prod;
+    TRY(getbuf(ctx, "sgp_prod", (size_t)2 * np * N3, &prod));
+    {
+      const size_t nn = (size_t)np * N3;
+      ++g_launches;
+      k_pair_product<<<(int)std::min<size_t>((nn + 255) / 256, 152 * 8), 256, 0, ctx->st>>>(
+          (size_t)N3, np, ug, ug + (size_t)np * N3, 1.0 / ctx->vol, prod);
+    }
+    // phi = v^1/2 |p* e> (real and imaginary parts as real fields), [np][2][N3]
+    TRY(getbuf(ctx, "sgp_seeds", (size_t)2 * np * N3, &seeds));
+    TRY(sqrtv<double>(ctx, prod, 2 * np, seeds, nullptr));
+    TRY(getbuf(ctx, "sgp_n2", 2 * np, &n2));
+    TRY(ensure_work(ctx, 64));
+    for (int j = 0; j < 2 * np; ++j)
+      launch_dot(ctx->st, N3, seeds + (size_t)j * N3, seeds + (size_t)j * N3, wgt, 0, ctx->work, n2 + j);
+    std::vector<double> hn2(2 * np);
+    CK(cudaMemcpyAsync(hn2.data(), n2, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    TRY(sync(ctx, "sigma_p seeds"));
+    TRY(getbuf(ctx, "sgp_al", k, &al));
+    TRY(getbuf(ctx, "sgp_be", k, &be));
+    TRY(getbuf(ctx, "sgp_Q", (size_t)2 * k * N3, &Q));
+    TRY(getbuf(ctx, "sgp_Ti", (size_t)k * k, &Ti));
+    TRY(getbuf(ctx, "sgp_d", k, &d));
+    TRY(getbuf(ctx, "sgp_l", k, &l));
+    TRY(getbuf(ctx, "sgp_stat", 1, &stat));
+    double* x0;
+    TRY(getbuf(ctx, "sgp_x0", (size_t)2 * N3, &x0));
+    for (int i = 0; i < np; ++i) {
+      const double nr = hn2[2 * i], ni = hn2[2 * i + 1];
+      const double nt = nr + ni;
+      if (!(nt > 0.0)) continue;                       // a vanishing seed: the term is 0
+      // a real seed (states real in real space) runs on N_g entries, a complex one on 2 N_g
+      const bool cplx = ni > 1e-24 * nt;
+      const double* src = seeds + (size_t)(2 * i + (cplx || nr > 0.0 ? 0 : 1)) * N3;
+      const int width = cplx ? 2 : 1;
+      CK(cudaMemcpyAsync(x0, src, (size_t)width * N3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+      const std::vector<double2> om{make_double2(pom[i], 0.0)};
+      int steps = 0;
+      gw_status st = (prec == GW_FP64) ? lanczos_core<double>(ctx, x0, k, om, al, be, Q, width, &steps)
+                                       : lanczos_core<float>(ctx, x0, k, om, al, be, Q, width, &steps);
+      if (st != GW_OK && st != GW_E_BREAKDOWN) return st;
+      ctx->err.clear();
+      launch_tridiag_inv(ctx->st, steps, al, be, d, l, Ti, stat);
+      double t11 = 0.0;
+      int hs = 0;
+      CK(cudaMemcpyAsync(&t11, Ti, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+      CK(cudaMemcpyAsync(&hs, stat, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+      TRY(sync(ctx, "sigma_p element"));
+      if (hs) return fail(ctx, GW_E_BREAKDOWN, "singular Lanczos matrix in a Sigma^P element");
+      hterms[pole[i]] = pw_[i] * (cplx ? nt : (nr > 0.0 ? nr : ni)) * (t11 - 1.0);
+    }
+    for (int j = 0; j < n; ++j) total += hterms[j];
+  }
+  *total_out = total;
+  return GW_OK;
+}
+
+// Gauss-Legendre nodes (ascending) and weights on [-1, 1]: Newton iteration on
+// P_n from the three-term recurrence, P_n'(x) = n (x P_n - P_{n-1}) / (x^2 - 1).
+static void gauss_legendre(int n, std::vector<double>* t, std::vector<double>* w) {
+  t->assign(n, 0.0);
+  w->assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double x = std::cos(pi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (x * p1 - p0) / (x * x - 1.0);
+      const double dx = p1 / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = x;
+    for (int k = 2; k <= n; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = (n == 1) ? 1.0 : n * (x * p1 - p0) / (x * x - 1.0);
+    (*t)[n - 1 - i] = x;
+    (*w)[n - 1 - i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+}
+
+// Eq. e_c in the basis of the fields F (see gw_sigma_c in include/gw.h):
+// out = {Sigma^c, frequency integral, Sigma^A, Sigma^P}.
+template <typename S>
+gw_status sigma_c_core(gw_ctx* ctx, int e, double delta, double alpha, int nf, const double* F, int nl, int kh,
+                       int kp, gw_prec prec, double* out) {
+  const int npw = ctx->npw, nocc = ctx->nocc, N3 = ctx->N3;
+  const double c = ctx->eps[e] + delta;
+  const double pi = 3.14159265358979323846;
+  // frequency nodes w = (1 + t)/(1 - t) with weights of (1/pi) int_0^inf dw
+  std::vector<double> t, wt, wall(1, 0.0), Wt(nf);
+  gauss_legendre(nf, &t, &wt);
+  for (int i = 0; i < nf; ++i) {
+    wall.push_back((1.0 + t[i]) / (1.0 - t[i]));
+    Wt[i] = wt[i] * 2.0 / ((1.0 - t[i]) * (1.0 - t[i])) / pi;
+  }
+  double* dw;
+  TRY(upload_table(ctx, "sc_w", wall, &dw));
+  // M(i w) = (1 + E(i w))^-1 - 1 in the basis, E from the recycled bases
+  double *E, *V, *M;
+  int* sw;
+  const size_t nn = (size_t)nl * nl;
+  TRY(getbuf(ctx, "sc_E", (nf + 1) * nn, &E));
+  TRY(getbuf(ctx, "sc_V", (nf + 1) * nn, &V));
+  TRY(getbuf(ctx, "sc_M", (nf + 1) * nn, &M));
+  TRY(getbuf(ctx, "sc_sw", (size_t)nf + 2, &sw));
+  int kept = 0;
+  TRY(recycle_core<S>(ctx, F, nl, dw, nf + 1, 1e-6, E, &kept));
+  launch_add_identity(ctx->st, nf + 1, nl, E);
+  launch_symmetrize(ctx->st, nf + 1, nl, E);
+  CK(launch_jacobi_sym(ctx->st, nf + 1, nl, E, V, 1e-14, 40, sw));
+  launch_eig_function(ctx->st, nf + 1, nl, E, V, 0, M);
+  // z_l = Sphere(u_e (v^1/2 F_l)): the phase-space vectors Phi_e v^1/2 |l*>
+  double* y;
+  TRY(getbuf(ctx, "sc_y", (size_t)nl * N3, &y));
+  TRY(sqrtv<double>(ctx, F, nl, y, nullptr));
+  std::vector<int> ca(nl, e), cy(nl);
+  for (int l = 0; l < nl; ++l) cy[l] = l;
+  int *dca, *dcy;
+  TRY(upload_table(ctx, "sc_ca", ca, &dca));
+  TRY(upload_table(ctx, "sc_cy", cy, &dcy));
+  double2 *grid, *Z, *X0, *Qh;
+  TRY(getbuf(ctx, "sc_grid", (size_t)nl * N3, &grid));
+  TRY(getbuf(ctx, "sc_Z", (size_t)nl * npw, &Z));
+  TRY(getbuf(ctx, "sc_X0", (size_t)nl * npw, &X0));
+  TRY(getbuf(ctx, "sc_Q", (size_t)kh * nl * npw, &Qh));
+  const Geometry& g = ctx->geo;
+  launch_xpass_prod_fwd<double>(ctx->st, g, ctx->P64, ctx->plan, reinterpret_cast<const double2*>(y), 0,
+                                ctx->P64.U, 0, 0, dca, dcy, grid, nl);
+  launch_ypass<double>(ctx->st, 0, 0, 1, g, ctx->P64, ctx->plan, grid, nullptr, nl, 0);
+  launch_zpass<double>(ctx->st, Z_GATHER_FWD, g, ctx->P64, ctx->plan, grid, Z, nullptr, nullptr, nullptr, nullptr,
+                       nullptr, nullptr, nullptr, nl);
+  CK(cudaMemcpyAsync(X0, Z, (size_t)nl * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
+  // shift-Lanczos: one block recursion on H - c serves every frequency
+  std::vector<double2> Ec(nl, make_double2(c, 0.0));
+  double2* dEc;
+  TRY(upload_table(ctx, "sc_Ec", Ec, &dEc));
+  auto op = [&](double2* Qk, double2* W) -> gw_status { return h_apply<double>(ctx, Qk, nl, dEc, nullptr, W); };
+  std::vector<zcd> Ah, Bh, R0;
+  TRY(block_lanczos_run(ctx, (size_t)npw, 1.0, false, nl, kh, X0, Qh, op, &Ah, &Bh, &R0));
+  const int m = kh * nl;
+  std::vector<double> T((size_t)m * m, 0.0), R(nn);
+  for (int k = 0; k < kh; ++k)
+    for (int i = 0; i < nl; ++i)
+      for (int j = 0; j < nl; ++j) {
+        T[(size_t)(k * nl + i) * m + k * nl + j] = Ah[(size_t)k * nn + i * nl + j].real();
+        if (k + 1 < kh) {
+          const double b = Bh[(size_t)k * nn + i * nl + j].real();
+          T[(size_t)((k + 1) * nl + i) * m + k * nl + j] = b;
+          T[(size_t)(k * nl + j) * m + (k + 1) * nl + i] = b;
+        }
+      }
+  for (size_t i = 0; i < nn; ++i) R[i] = R0[i].real();
+  double *dT, *dU, *dR, *G, *K;
+  TRY(upload(ctx, "sc_T", T, &dT));
+  TRY(upload(ctx, "sc_R", R, &dR));
+  TRY(getbuf(ctx, "sc_U", (size_t)m * m, &dU));
+  TRY(getbuf(ctx, "sc_G", (size_t)nf * nn, &G));
+  TRY(getbuf(ctx, "sc_K", (size_t)nf * nn, &K));
+  launch_symmetrize(ctx->st, 1, m, dT);
+  CK(launch_jacobi_sym(ctx->st, 1, m, dT, dU, 1e-14, 40, sw + nf + 1));
+  launch_shift_quadrature(ctx->st, m, nl, dT, dU, dR, dw + 1, nf, G, K);
+  // Sigma^A: h+ = alpha (H - c + alpha)^-1 P_c z in the conduction space; P_e part in closed form
+  double2 *bz, *hp, *cg, *gpart, *a;
+  unsigned* gcnt;
+  TRY(getbuf(ctx, "sc_bz", (size_t)nl * npw, &bz));
+  TRY(getbuf(ctx, "sc_hp", (size_t)nl * npw, &hp));
+  CK(cudaMemcpyAsync(bz, Z, (size_t)nl * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
+  TRY(ensure_work(ctx, std::max(nl, 64)));
+  launch_proj<double>(ctx->st, ctx->P64.C, nocc, npw, bz, nl, nullptr, ctx->work, nullptr, nullptr);
+  std::vector<double2> Ea(nl, make_double2(c - alpha, 0.0));
+  std::vector<double> tk(nl, ctx->tkin[e]);
+  double2* dEa;
+  double* dtk = nullptr;
+  TRY(upload_table(ctx, "sc_Ea", Ea, &dEa));
+  if (ctx->precond) TRY(upload_table(ctx, "sc_tk", tk, &dtk));
+  TRY(solve<S>(ctx, nl, bz, dEa, hp, false, dtk));
+  double *Hp, *Hm, *deps, *forms;
+  TRY(getbuf(ctx, "sc_cg", nn, &cg));
+  TRY(getbuf(ctx, "sc_gpart", (size_t)((npw + 4095) / 4096) * nn, &gpart));
+  if (!ctx->bufs.count("sc_gcnt") || ctx->bufs["sc_gcnt"].second < (size_t)nl * sizeof(unsigned)) {
+    TRY(getbuf(ctx, "sc_gcnt", (size_t)nl, &gcnt));
+    CK(cudaMemsetAsync(gcnt, 0, (size_t)nl * sizeof(unsigned), ctx->st));
+  } else {
+    TRY(getbuf(ctx, "sc_gcnt", (size_t)nl, &gcnt));
+  }
+  TRY(getbuf(ctx, "sc_Hp", nn, &Hp));
+  TRY(getbuf(ctx, "sc_Hm", nn, &Hm));
+  TRY(getbuf(ctx, "sc_a", (size_t)nocc * nl, &a));
+  launch_cgram(ctx->st, Z, nl, hp, nl, npw, 1, alpha, gpart, gcnt, cg);
+  launch_real_part(ctx->st, nn, cg, Hp);
+  launch_gram<double>(ctx->st, ctx->P64.C, nocc, npw, Z, nl, ctx->work, a);
+  TRY(upload(ctx, "sc_eps", ctx->eps, &deps));
+  launch_pe_form(ctx->st, nocc, nl, a, deps, c, alpha, Hm);
+  // Frobenius forms: node i: (M(i w_i) - f(w_i) M(0)) . K_i; then M(0) . Hp and M(0) . Hm
+  std::vector<int> ia(nf + 2), ib(nf + 2, 0), ic(nf + 2);
+  std::vector<double> fa(nf + 2, 0.0);
+  for (int i = 0; i < nf; ++i) {
+    ia[i] = 1 + i;
+    ic[i] = i;
+    fa[i] = alpha * alpha / (wall[1 + i] * wall[1 + i] + alpha * alpha);
+  }
+  int *dia, *dib, *dic;
+  double* dfa;
+  TRY(upload_table(ctx, "sc_ia", ia, &dia));
+  TRY(upload_table(ctx, "sc_ib", ib, &dib));
+  TRY(upload_table(ctx, "sc_ic", ic, &dic));
+  TRY(upload_table(ctx, "sc_fa", fa, &dfa));
+  TRY(getbuf(ctx, "sc_forms", (size_t)nf + 2, &forms));
+  launch_frob_forms(ctx->st, nf, (int)nn, M, dia, dfa, M, dib, K, dic, forms);
+  launch_frob_forms(ctx->st, 1, (int)nn, M, dib, dfa + nf, M, dib, Hp, dib, forms + nf);
+  launch_frob_forms(ctx->st, 1, (int)nn, M, dib, dfa + nf, M, dib, Hm, dib, forms + nf + 1);
+  std::vector<double> hf(nf + 2);
+  std::vector<int> hsw(nf + 2);
+  CK(cudaMemcpyAsync(hf.data(), forms, (nf + 2) * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(hsw.data(), sw, (nf + 2) * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  TRY(sync(ctx, "sigma_c"));
+  for (int x : hsw)
+    if (x > 40) return fail(ctx, GW_E_NOCONV, "Jacobi eigensolver did not converge in the self-energy");
+  double integral = 0.0;
+  for (int i = 0; i < nf; ++i) integral += Wt[i] * hf[i];
+  const double SA = 0.5 * (hf[nf] + hf[nf + 1]);
+  // Sigma^P: occupied states at or above c (w_ve >= 0); e_HOMO <= c leaves only e_v = c
+  const std::vector<int> ho(nocc, 1);
+  double SP = 0.0;
+  std::vector<double> terms;
+  TRY(sigma_p_core(ctx, ctx->P64.C + (size_t)e * npw, ctx->eps[e], delta, nocc, ctx->P64.C, ctx->eps, ho, kp, prec,
+                   &SP, &terms));
+  out[0] = integral + SA + SP;
+  out[1] = integral;
+  out[2] = SA;
+  out[3] = SP;
+  (void)kept;
+  return GW_OK;
+}
+
 extern "C" {
 
 gw_status gw_setup(gw_ctx** out, double L, int n_grid, double ecut, const double* vloc, int coulomb,
@@ -2309,92 +2605,14 @@ gw_status gw_sigma_p(gw_ctx* ctx, const double* psi_e, double eps_e, double delt
       std::copy(occ, occ + n, ho.begin());
     }
   }
-  // the poles that Theta keeps, with their weights -Theta(w) (occupied) or Theta(-w)
-  std::vector<int> pole;
-  std::vector<double> pw_, pom;
-  for (int j = 0; j < n; ++j) {
-    if (!std::isfinite(he[j])) return fail(ctx, GW_E_NONFINITE, "non-finite energy");
-    const double om = he[j] - eps_e - delta;
-    const double th = ho[j] ? (om > 0 ? 1.0 : (om == 0 ? 0.5 : 0.0)) : (om < 0 ? 1.0 : (om == 0 ? 0.5 : 0.0));
-    if (th == 0.0) continue;
-    pole.push_back(j);
-    pw_.push_back(ho[j] ? -th : th);
-    pom.push_back(om);
-  }
-  std::vector<double> hterms(n, 0.0);
+  std::vector<double> hterms;
   double total = 0.0;
-  const int np = (int)pole.size();
-  if (np > 0) {
-    // grids u_e and u_p of the states (sphere -> grid, FP64), then the pair products
-    const void *pe, *pp;
+  {
+    const void *pe, *pp = nullptr;
     TRY(stage_in(ctx, "sgp_psie", psi_e, (size_t)npw * sizeof(double2), dev, &pe));
-    TRY(stage_in(ctx, "sgp_psi", psi, (size_t)n * npw * sizeof(double2), dev, &pp));
-    double2 *cs, *ug;
-    double *seeds, *al, *be, *Q, *n2, *Ti, *d, *l;
-    int* stat;
-    TRY(getbuf(ctx, "sgp_cs", (size_t)(np + 1) * npw, &cs));
-    TRY(getbuf(ctx, "sgp_ug", (size_t)(np + 1) * N3, &ug));
-    for (int i = 0; i < np; ++i)
-      CK(cudaMemcpyAsync(cs + (size_t)i * npw, reinterpret_cast<const double2*>(pp) + (size_t)pole[i] * npw,
-                         npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
-    CK(cudaMemcpyAsync(cs + (size_t)np * npw, pe, npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
-    const Geometry& g = ctx->geo;
-    launch_zpass<double>(ctx->st, Z_SCATTER_INV, g, ctx->P64, ctx->plan, ug, cs, nullptr, nullptr, nullptr, nullptr,
-                         nullptr, nullptr, nullptr, np + 1);
-    launch_ypass<double>(ctx->st, 1, 1, 0, g, ctx->P64, ctx->plan, ug, nullptr, np + 1, 0);
-    launch_xpass_mul<double>(ctx->st, 1, 1, 0, g, ctx->P64, ctx->plan, ug, nullptr, nullptr, np + 1);
-    double* prod;
-    TRY(getbuf(ctx, "sgp_prod", (size_t)2 * np * N3, &prod));
-    {
-      const size_t nn = (size_t)np * N3;
-      ++g_launches;
-      k_pair_product<<<(int)std::min<size_t>((nn + 255) / 256, 152 * 8), 256, 0, ctx->st>>>(
-          (size_t)N3, np, ug, ug + (size_t)np * N3, 1.0 / ctx->vol, prod);
-    }
-    // phi = v^1/2 |p* e> (real and imaginary parts as real fields), [np][2][N3]
-    TRY(getbuf(ctx, "sgp_seeds", (size_t)2 * np * N3, &seeds));
-    TRY(sqrtv<double>(ctx, prod, 2 * np, seeds, nullptr));
-    TRY(getbuf(ctx, "sgp_n2", 2 * np, &n2));
-    TRY(ensure_work(ctx, 64));
-    for (int j = 0; j < 2 * np; ++j)
-      launch_dot(ctx->st, N3, seeds + (size_t)j * N3, seeds + (size_t)j * N3, wgt, 0, ctx->work, n2 + j);
-    std::vector<double> hn2(2 * np);
-    CK(cudaMemcpyAsync(hn2.data(), n2, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-    TRY(sync(ctx, "sigma_p seeds"));
-    TRY(getbuf(ctx, "sgp_al", k, &al));
-    TRY(getbuf(ctx, "sgp_be", k, &be));
-    TRY(getbuf(ctx, "sgp_Q", (size_t)2 * k * N3, &Q));
-    TRY(getbuf(ctx, "sgp_Ti", (size_t)k * k, &Ti));
-    TRY(getbuf(ctx, "sgp_d", k, &d));
-    TRY(getbuf(ctx, "sgp_l", k, &l));
-    TRY(getbuf(ctx, "sgp_stat", 1, &stat));
-    double* x0;
-    TRY(getbuf(ctx, "sgp_x0", (size_t)2 * N3, &x0));
-    for (int i = 0; i < np; ++i) {
-      const double nr = hn2[2 * i], ni = hn2[2 * i + 1];
-      const double nt = nr + ni;
-      if (!(nt > 0.0)) continue;                       // a vanishing seed: the term is 0
-      // a real seed (states real in real space) runs on N_g entries, a complex one on 2 N_g
-      const bool cplx = ni > 1e-24 * nt;
-      const double* src = seeds + (size_t)(2 * i + (cplx || nr > 0.0 ? 0 : 1)) * N3;
-      const int width = cplx ? 2 : 1;
-      CK(cudaMemcpyAsync(x0, src, (size_t)width * N3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
-      const std::vector<double2> om{make_double2(pom[i], 0.0)};
-      int steps = 0;
-      gw_status st = (prec == GW_FP64) ? lanczos_core<double>(ctx, x0, k, om, al, be, Q, width, &steps)
-                                       : lanczos_core<float>(ctx, x0, k, om, al, be, Q, width, &steps);
-      if (st != GW_OK && st != GW_E_BREAKDOWN) return st;
-      ctx->err.clear();
-      launch_tridiag_inv(ctx->st, steps, al, be, d, l, Ti, stat);
-      double t11 = 0.0;
-      int hs = 0;
-      CK(cudaMemcpyAsync(&t11, Ti, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-      CK(cudaMemcpyAsync(&hs, stat, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-      TRY(sync(ctx, "sigma_p element"));
-      if (hs) return fail(ctx, GW_E_BREAKDOWN, "singular Lanczos matrix in a Sigma^P element");
-      hterms[pole[i]] = pw_[i] * (cplx ? nt : (nr > 0.0 ? nr : ni)) * (t11 - 1.0);
-    }
-    for (int j = 0; j < n; ++j) total += hterms[j];
+    if (n > 0) TRY(stage_in(ctx, "sgp_psi", psi, (size_t)n * npw * sizeof(double2), dev, &pp));
+    TRY(sigma_p_core(ctx, reinterpret_cast<const double2*>(pe), eps_e, delta, n,
+                     reinterpret_cast<const double2*>(pp), he, ho, k, prec, &total, &hterms));
   }
   if (dev) {
     CK(cudaMemcpyAsync(sigma, &total, sizeof(double), cudaMemcpyHostToDevice, ctx->st));
@@ -2438,6 +2656,39 @@ gw_status gw_recycle_eps(gw_ctx* ctx, const double* fields, int nl, const double
   TRY(copy_back(ctx, out, o, (size_t)nw * nl * nl * sizeof(double), dev));
   if (kept) *kept = km;
   if (ctx->stats[0] > 0) ctx->stats[2] /= ctx->stats[0];
+  return finish(ctx, GW_OK);
+}
+
+gw_status gw_sigma_c(gw_ctx* ctx, int e, double delta, double alpha, int n_freq, const double* fields, int nl,
+                     int k_h, int k_p, double* out, gw_prec prec, int dev) {
+  TRY(begin(ctx));
+  TRY(need_occ(ctx));
+  if (!fields || !out || e < 0 || e >= ctx->nocc || !(alpha > 0.0) || n_freq < 1 || n_freq > 64 || nl < 1 ||
+      nl > 16 || k_h < 1 || k_h * nl > 512 || k_p < 1 || k_p > 256)
+    return fail(ctx, GW_E_ARG, "bad arguments");
+  if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_E_ARG, "bad precision");
+  if (!std::isfinite(delta) || !std::isfinite(alpha)) return fail(ctx, GW_E_NONFINITE, "non-finite argument");
+  if (ctx->op != GW_OP_STERNHEIMER) return fail(ctx, GW_E_UNSUPPORTED, "the self-energy uses the Sternheimer operator");
+  const double ehomo = *std::max_element(ctx->eps.begin(), ctx->eps.end());
+  if (ctx->eps[e] + delta < ehomo)
+    return fail(ctx, GW_E_UNSUPPORTED, "e_e + delta below the highest occupied energy (Q_e is not P_c)");
+  for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
+  const void* F;
+  TRY(stage_in(ctx, "sce_F", fields, (size_t)nl * ctx->N3 * sizeof(double), dev, &F));
+  double res[4];
+  gw_status st = (prec == GW_FP64)
+                     ? sigma_c_core<double>(ctx, e, delta, alpha, n_freq, reinterpret_cast<const double*>(F), nl, k_h,
+                                            k_p, prec, res)
+                     : sigma_c_core<float>(ctx, e, delta, alpha, n_freq, reinterpret_cast<const double*>(F), nl, k_h,
+                                           k_p, prec, res);
+  if (st != GW_OK) return st;
+  for (double x : res)
+    if (!std::isfinite(x)) return fail(ctx, GW_E_NONFINITE, "non-finite self-energy");
+  if (dev) {
+    CK(cudaMemcpyAsync(out, res, sizeof(res), cudaMemcpyHostToDevice, ctx->st));
+  } else {
+    std::copy(res, res + 4, out);
+  }
   return finish(ctx, GW_OK);
 }
 

@@ -269,4 +269,127 @@ void launch_recycled_form(cudaStream_t s, int nbat, int m, int nl, int nw, const
   k_recycled_form<<<dim3(nl, nl, nw), kST, 0, s>>>(nbat, m, nl, L, c, w, out);
 }
 
+// out[b] = V[b] f(L[b]) V[b]^T for symmetric matrices diagonalised by
+// k_jacobi_sym (eigenvalues on the diagonal of L[b], eigenvectors in the
+// columns of V[b]); f(x) = 1/x - 1 (mode 0: eps^-1 - 1 from eps)
+__global__ void k_eig_function(int m, const double* __restrict__ Lb, const double* __restrict__ Vb, int mode,
+                               double* __restrict__ out) {
+  const double* L = Lb + (size_t)blockIdx.x * m * m;
+  const double* V = Vb + (size_t)blockIdx.x * m * m;
+  double* O = out + (size_t)blockIdx.x * m * m;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e - i * m;
+    double acc = 0.0;
+    for (int k = 0; k < m; ++k) {
+      const double lam = L[(size_t)k * m + k];
+      const double f = (mode == 0) ? 1.0 / lam - 1.0 : lam;
+      acc += V[(size_t)i * m + k] * f * V[(size_t)j * m + k];
+    }
+    O[e] = acc;
+  }
+}
+
+void launch_eig_function(cudaStream_t s, int nb, int m, const double* L, const double* V, int mode, double* out) {
+  if (nb == 0) return;
+  ++g_launches;
+  k_eig_function<<<nb, kST, 0, s>>>(m, L, V, mode, out);
+}
+
+// A[b] += diag(1)
+__global__ void k_add_identity(int m, double* __restrict__ Ab) {
+  double* A = Ab + (size_t)blockIdx.x * m * m;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) A[(size_t)i * m + i] += 1.0;
+}
+
+void launch_add_identity(cudaStream_t s, int nb, int m, double* A) {
+  if (nb == 0) return;
+  ++g_launches;
+  k_add_identity<<<nb, kST, 0, s>>>(m, A);
+}
+
+// Shift-Lanczos quadrature of <z_l| g(H - c, w) |z_l'>, g(h) = h / (w^2 + h^2):
+// out[o] = R^T U1 g(Theta, w_o) U1^T R with Theta on the diagonal of L (m x m,
+// from k_jacobi_sym), U1 the first b rows of U, R (b x b); grid nw, one CTA
+// per frequency; scratch G [nw][b][b]
+__global__ void __launch_bounds__(kST)
+k_shift_quadrature(int m, int b, const double* __restrict__ L, const double* __restrict__ U,
+                   const double* __restrict__ R, const double* __restrict__ w, double* __restrict__ G,
+                   double* __restrict__ out) {
+  const int o = blockIdx.x;
+  const double w2 = w[o] * w[o];
+  double* Go = G + (size_t)o * b * b;
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int i = e / b, j = e - i * b;
+    double acc = 0.0;
+    for (int k = 0; k < m; ++k) {
+      const double th = L[(size_t)k * m + k];
+      const double den = w2 + th * th;
+      if (den == 0.0) continue;
+      acc += U[(size_t)i * m + k] * (th / den) * U[(size_t)j * m + k];
+    }
+    Go[e] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int i = e / b, j = e - i * b;
+    double acc = 0.0;
+    for (int p = 0; p < b; ++p)
+      for (int q = 0; q < b; ++q) acc += R[(size_t)p * b + i] * Go[(size_t)p * b + q] * R[(size_t)q * b + j];
+    out[(size_t)o * b * b + e] = acc;
+  }
+}
+
+void launch_shift_quadrature(cudaStream_t s, int m, int b, const double* L, const double* U, const double* R,
+                             const double* w, int nw, double* G, double* out) {
+  if (nw == 0) return;
+  ++g_launches;
+  k_shift_quadrature<<<nw, kST, 0, s>>>(m, b, L, U, R, w, G, out);
+}
+
+// P_e part of Eq. khe in closed form on the occupied states below c:
+// out[l][l'] = sum_{v: e_v < c} Re(conj(a[v][l]) a[v][l']) alpha / (e_v - c - alpha)
+__global__ void k_pe_form(int nocc, int nl, const double2* __restrict__ a, const double* __restrict__ eps, double c,
+                          double alpha, double* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nl * nl; e += gridDim.x * blockDim.x) {
+    const int l = e / nl, lp = e - l * nl;
+    double acc = 0.0;
+    for (int v = 0; v < nocc; ++v) {
+      if (!(eps[v] < c)) continue;
+      const double2 x = a[(size_t)v * nl + l], y = a[(size_t)v * nl + lp];
+      acc += (x.x * y.x + x.y * y.y) * alpha / (eps[v] - c - alpha);
+    }
+    out[e] = acc;
+  }
+}
+
+void launch_pe_form(cudaStream_t s, int nocc, int nl, const double2* a, const double* eps, double c, double alpha,
+                    double* out) {
+  ++g_launches;
+  k_pe_form<<<1, kST, 0, s>>>(nocc, nl, a, eps, c, alpha, out);
+}
+
+// out[j] = sum_e (A[ia[j]] - fa[j] B[ib[j]])[e] C[ic[j]][e] over n entries (Frobenius forms)
+__global__ void __launch_bounds__(kST)
+k_frob_forms(int n, const double* __restrict__ A, const int* __restrict__ ia, const double* __restrict__ fa,
+             const double* __restrict__ B, const int* __restrict__ ib, const double* __restrict__ C,
+             const int* __restrict__ ic, double* __restrict__ out) {
+  __shared__ double sh[32];
+  const int j = blockIdx.x;
+  const double* a = A + (size_t)ia[j] * n;
+  const double* bb = B + (size_t)ib[j] * n;
+  const double* cc = C + (size_t)ic[j] * n;
+  const double f = fa[j];
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) acc += (a[e] - f * bb[e]) * cc[e];
+  acc = sum_block_all(acc, sh);
+  if (threadIdx.x == 0) out[j] = acc;
+}
+
+void launch_frob_forms(cudaStream_t s, int nj, int n, const double* A, const int* ia, const double* fa,
+                       const double* B, const int* ib, const double* C, const int* ic, double* out) {
+  if (nj == 0) return;
+  ++g_launches;
+  k_frob_forms<<<nj, kST, 0, s>>>(n, A, ia, fa, B, ib, C, ic, out);
+}
+
 }  // namespace gw

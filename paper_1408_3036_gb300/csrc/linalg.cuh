@@ -131,6 +131,14 @@ void launch_orth_transform(cudaStream_t s, int nb, int m, const double* S, const
                            int* kept);
 void launch_recycled_form(cudaStream_t s, int nbat, int m, int nl, int nw, const double* L, const double* c,
                           const double* w, double* out);
+void launch_eig_function(cudaStream_t s, int nb, int m, const double* L, const double* V, int mode, double* out);
+void launch_add_identity(cudaStream_t s, int nb, int m, double* A);
+void launch_shift_quadrature(cudaStream_t s, int m, int b, const double* L, const double* U, const double* R,
+                             const double* w, int nw, double* G, double* out);
+void launch_pe_form(cudaStream_t s, int nocc, int nl, const double2* a, const double* eps, double c, double alpha,
+                    double* out);
+void launch_frob_forms(cudaStream_t s, int nj, int n, const double* A, const int* ia, const double* fa,
+                       const double* B, const int* ib, const double* C, const int* ic, double* out);
 
 // block Lanczos helpers (complex grid fields)
 void launch_cgram(cudaStream_t s, const double2* X, int mx, const double2* Y, int my, size_t n, int conj_x,
