@@ -20,7 +20,9 @@ Eq. pe for the highest occupied state, one four-step Lanczos per pole at its
 real frequency (``--sigma-p-k 0`` skips it), and ``recycle`` builds
 eps~(i w) - 1 in the first Lanczos vectors at many imaginary frequencies from
 one recycled basis per occupied state (Eq. recy_eq; ``--recycle-nl 0`` skips
-it), against one direct application at w = 0.5i.
+it), against one direct application at w = 0.5i; ``sigma_c`` times the
+correlation self-energy of the highest occupied state (Eq. e_c) in the first
+eight Lanczos vectors (``--sigma-c-nl 0`` skips it).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 instead, on a bounded sample of the same workload.
@@ -461,6 +463,24 @@ def run_gpu(args):
                    direct_ms_one_frequency=t_dir,
                    rel_err_vs_direct_at_0p5i=float(np.abs(Er - Ed).max() / np.abs(Ed).max()))
 
+    # --- Sigma^c of the highest occupied state (Eq. e_c) in the first Lanczos vectors
+    sigc = None
+    if args.sigma_c_nl > 0:
+        nl = min(args.sigma_c_nl, K, 16)
+        Fq = Q[:nl].contiguous()
+        so = torch.zeros(4, dtype=torch.float64, device=dev)
+        gw.gw_sigma_c(cell.ctx, c.n_occ - 1, 0.0, 1.0, 8, Fq, 8, 4, so, prec)    # warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gw.gw_sigma_c(cell.ctx, c.n_occ - 1, 0.0, 1.0, 8, Fq, 8, 4, so, prec)
+        e1.record(stream)
+        e1.synchronize()
+        sv = so.cpu().numpy()
+        sigc = dict(state="HOMO", delta=0.0, alpha=1.0, frequencies=8, fields=nl, lanczos_h_steps=8,
+                    precision=args.prec, ms=e0.elapsed_time(e1), sigma_c=float(sv[0]), integral=float(sv[1]),
+                    sigma_a=float(sv[2]), sigma_p=float(sv[3]))
+
     # --- model operator (Eq. model_eq) on the same cell and start vector
     model = None
     if args.model_k > 0:
@@ -573,7 +593,7 @@ def run_gpu(args):
                         column_iterations_per_step=it_cols / args.steps, geometry=geo),
             roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
             clocks=clk.summary(), fp64=fp64, profile_ms={k: v[0] for k, v in prof.items() if v[1]},
-            model_operator=model, sigma_p=sigp, recycle=rec,
+            model_operator=model, sigma_p=sigp, recycle=rec, sigma_c=sigc,
         )
         print(json.dumps(line))
     cell.close()
@@ -597,6 +617,8 @@ def main():
     ap.add_argument("--profile-class", default="persistent_cg")
     ap.add_argument("--model-k", type=int, default=100,
                     help="Lanczos steps timed on the model operator of Eq. model_eq (0: skip)")
+    ap.add_argument("--sigma-c-nl", type=int, default=8,
+                    help="Lanczos vectors of the Sigma^c leg (Eq. e_c, HOMO, 8 frequencies; 0: skip)")
     ap.add_argument("--recycle-nl", type=int, default=20,
                     help="Lanczos vectors in which eps~(i w) - 1 is built from recycled bases (Eq. recy_eq; 0: skip)")
     ap.add_argument("--sigma-p-k", type=int, default=4,
