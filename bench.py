@@ -474,10 +474,12 @@ def run_gpu(args):
         gw.gw_sigma_c(cell.ctx, c.n_occ - 1, 0.0, 1.0, 8, Fq, 8, 4, so, prec)    # warm-up
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("sigma_c")
         e0.record(stream)
         gw.gw_sigma_c(cell.ctx, c.n_occ - 1, 0.0, 1.0, 8, Fq, 8, 4, so, prec)
         e1.record(stream)
         e1.synchronize()
+        torch.cuda.nvtx.range_pop()
         sv = so.cpu().numpy()
         sigc = dict(state="HOMO", delta=0.0, alpha=1.0, frequencies=8, fields=nl, lanczos_h_steps=8,
                     precision=args.prec, ms=e0.elapsed_time(e1), sigma_c=float(sv[0]), integral=float(sv[1]),

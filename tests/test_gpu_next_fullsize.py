@@ -10,7 +10,10 @@ size (the oracle cannot diagonalise this cell in test time):
     applications (the static solutions lie in the recycled bases);
   * Sigma^P at delta = 0 for the highest occupied state is minus half its own
     pole element at w = 0 (Theta(0) = 1/2, no other pole), and the mixed path
-    follows FP64.
+    follows FP64;
+  * Sigma^c of the highest occupied state in the first eight Lanczos vectors:
+    the mixed path follows FP64 part by part, and its residue part equals the
+    Sigma^P entry's.
 """
 import numpy as np
 import pytest
@@ -90,3 +93,23 @@ def test_sigma_p_full_size(molecule):
     assert abs(tot + el) < 1e-12 * abs(el)          # -1/2 (occupied) against +1/2 (conduction)
     tot32, _ = cell.sigma_p(cand[e], ce[e], 0.0, cand, ce, occ, k=4, prec=gw.GW_MIXED)
     assert abs(tot32 - tot) < 1e-6 * abs(tot)
+
+
+def test_sigma_c_full_size(molecule):
+    import torch
+    wl, c, cell, eps, psi = molecule
+    n = c.n_occ
+    dev = torch.device("cuda")
+    start = torch.tensor(wl.starts[0][0], dtype=torch.float64, device=dev)
+    a = torch.empty(8, dtype=torch.float64, device=dev)
+    b = torch.empty(8, dtype=torch.float64, device=dev)
+    Q = torch.empty((8, c.N ** 3), dtype=torch.float64, device=dev)
+    gw.gw_lanczos(cell.ctx, start, 8, 0.0, a, b, Q, gw.GW_FP64)
+    F = Q.cpu().numpy()
+    r64 = cell.sigma_c(n - 1, 0.0, F, alpha=1.0, n_freq=8, k_h=8, k_p=4, prec=gw.GW_FP64)
+    r32 = cell.sigma_c(n - 1, 0.0, F, alpha=1.0, n_freq=8, k_h=8, k_p=4, prec=gw.GW_MIXED)
+    scale = max(abs(r64[k]) for k in ("integral", "SA", "SP"))
+    for k in ("total", "integral", "SA", "SP"):
+        assert abs(r32[k] - r64[k]) < 1e-6 * scale, k
+    sp, _ = cell.sigma_p(psi[n - 1], eps[n - 1], 0.0, psi[:n], eps[:n], np.ones(n, int), k=4, prec=gw.GW_FP64)
+    assert abs(r64["SP"] - sp) < 1e-9 * abs(sp)
