@@ -1202,7 +1202,7 @@ gw_status block_lanczos_run(gw_ctx* ctx, size_t n, double wgt, bool bil, int blk
   unsigned* cnt;
   TRY(getbuf(ctx, "bl_W", (size_t)blk * n, &W));
   TRY(getbuf(ctx, "bl_gram", (size_t)mmax * blk, &gram));
-  TRY(getbuf(ctx, "bl_part", ((n + 4095) / 4096) * (size_t)mmax * blk, &part));
+  TRY(getbuf(ctx, "bl_part", cgram_partials(n, mmax, blk), &part));
   TRY(getbuf(ctx, "bl_M", (size_t)blk * mmax, &M));
   TRY(getbuf(ctx, "bl_cnt", (size_t)(blk + 7) / 8 + 1, &cnt));
   CK(cudaMemsetAsync(cnt, 0, ((size_t)(blk + 7) / 8 + 1) * sizeof(unsigned), ctx->st));
@@ -1754,9 +1754,8 @@ gw_status recycle_core(gw_ctx* ctx, const double* F, int nl, const double* dw, i
   // fields and the occupied states are real in real space)
   double2 *cg, *gpart;
   unsigned* gcnt;
-  const int nchunk = (npw + 4095) / 4096;
   TRY(getbuf(ctx, "rc_cg", (size_t)m * m, &cg));
-  TRY(getbuf(ctx, "rc_gpart", (size_t)nchunk * m * m, &gpart));
+  TRY(getbuf(ctx, "rc_gpart", std::max(cgram_partials(npw, m, m), cgram_partials(npw, m, nl)), &gpart));
   if (!ctx->bufs.count("rc_gcnt") || ctx->bufs["rc_gcnt"].second < (size_t)m * sizeof(unsigned)) {
     TRY(getbuf(ctx, "rc_gcnt", (size_t)m, &gcnt));
     CK(cudaMemsetAsync(gcnt, 0, (size_t)m * sizeof(unsigned), ctx->st));
@@ -2039,7 +2038,7 @@ gw_status sigma_c_core(gw_ctx* ctx, int e, double delta, double alpha, int nf, c
   TRY(solve<S>(ctx, nl, bz, dEa, hp, false, dtk));
   double *Hp, *Hm, *deps, *forms;
   TRY(getbuf(ctx, "sc_cg", nn, &cg));
-  TRY(getbuf(ctx, "sc_gpart", (size_t)((npw + 4095) / 4096) * nn, &gpart));
+  TRY(getbuf(ctx, "sc_gpart", cgram_partials(npw, nl, nl), &gpart));
   if (!ctx->bufs.count("sc_gcnt") || ctx->bufs["sc_gcnt"].second < (size_t)nl * sizeof(unsigned)) {
     TRY(getbuf(ctx, "sc_gcnt", (size_t)nl, &gcnt));
     CK(cudaMemsetAsync(gcnt, 0, (size_t)nl * sizeof(unsigned), ctx->st));

@@ -1044,16 +1044,16 @@ namespace gw {
 // block Lanczos on complex grid fields (Sec. Lanczos, block form; bilinear
 // form at complex frequency): Gram matrices and small-matrix combinations
 // ---------------------------------------------------------------------------
-constexpr int kGChunk = 4096;   // grid points per block in the Gram kernel
 constexpr int kGT = 8;          // Y columns per block
 
 // out[i * my + j] = wgt * sum_r op(X[i][r]) Y[j][r], op = conj (Hermitian) or identity (bilinear)
-// grid (nchunk, ceil(my / kGT)); one warp per i (strided), lanes over r
+// grid (nchunk, ceil(my / kGT)), chunk entries per CTA; one warp per i (strided), lanes over r
 __global__ void __launch_bounds__(kLT)
 k_cgram(const double2* __restrict__ X, int mx, const double2* __restrict__ Y, int my, size_t n, int conj_x,
-        double wgt, double2* __restrict__ partial, unsigned* __restrict__ cnt, double2* __restrict__ out) {
+        double wgt, double2* __restrict__ partial, unsigned* __restrict__ cnt, double2* __restrict__ out,
+        size_t chunk) {
   const int nchunk = gridDim.x;
-  const size_t r0 = (size_t)blockIdx.x * kGChunk, r1 = min(n, r0 + kGChunk);
+  const size_t r0 = (size_t)blockIdx.x * chunk, r1 = min(n, r0 + chunk);
   const int j0 = blockIdx.y * kGT;
   const int nj = min(kGT, my - j0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -1095,10 +1095,11 @@ k_cgram(const double2* __restrict__ X, int mx, const double2* __restrict__ Y, in
 
 void launch_cgram(cudaStream_t s, const double2* X, int mx, const double2* Y, int my, size_t n, int conj_x,
                   double wgt, double2* partial, unsigned* cnt, double2* out) {
-  const int nchunk = (int)((n + kGChunk - 1) / kGChunk);
+  const size_t chunk = cgram_chunk(n, my);
+  const int nchunk = (int)((n + chunk - 1) / chunk);
   dim3 g(nchunk, (my + kGT - 1) / kGT);
   ++g_launches;
-  k_cgram<<<g, kLT, 0, s>>>(X, mx, Y, my, n, conj_x, wgt, partial, cnt, out);
+  k_cgram<<<g, kLT, 0, s>>>(X, mx, Y, my, n, conj_x, wgt, partial, cnt, out, chunk);
 }
 
 // Y[j][r] = (accumulate ? Y[j][r] : 0) + sign * sum_i M[j * mx + i] X[i][r],  j < my (<= 16)

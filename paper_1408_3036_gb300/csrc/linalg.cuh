@@ -141,6 +141,24 @@ void launch_frob_forms(cudaStream_t s, int nj, int n, const double* A, const int
                        const double* B, const int* ib, const double* C, const int* ic, double* out);
 
 // block Lanczos helpers (complex grid fields)
+// Entries per CTA of the complex Gram kernel for vectors of length n and my
+// columns: halved from 4096 (down to 256) while fewer than 128 CTAs would run
+// and the sum over chunks stays under 64 records; cgram_partials is the
+// partial-sum storage (double2 entries) a launch with mx rows needs.
+inline size_t cgram_chunk(size_t n, int my) {
+  const size_t groups = ((size_t)my + 7) / 8;
+  size_t chunk = 4096;
+  while (chunk > 256) {
+    const size_t nc = (n + chunk - 1) / chunk;
+    if (nc * groups >= 128 || 2 * nc > 64) break;
+    chunk /= 2;
+  }
+  return chunk;
+}
+inline size_t cgram_partials(size_t n, int mx, int my) {
+  const size_t chunk = cgram_chunk(n, my);
+  return ((n + chunk - 1) / chunk) * (size_t)mx * (size_t)my;
+}
 void launch_cgram(cudaStream_t s, const double2* X, int mx, const double2* Y, int my, size_t n, int conj_x,
                   double wgt, double2* partial, unsigned* cnt, double2* out);
 void launch_cgemm_n(cudaStream_t s, const double2* M, int my, int mx, const double2* X, size_t n, double2* Y,
