@@ -2170,7 +2170,7 @@ gw_status gw_set_occupied(gw_ctx* ctx, int n_occ, const double* psi, const doubl
   if (!ctx) return GW_E_ARG;
   if (n_occ < 1 || n_occ > kMaxOcc || !psi || !eps) return fail(ctx, GW_E_ARG, "bad n_occ / pointers");
   TRY(begin(ctx));
-  const int npw = ctx->npw, N = ctx->N;
+  const int npw = ctx->npw;
   for (int v = 0; v < n_occ; ++v) {
     if (!std::isfinite(eps[v])) return fail(ctx, GW_E_NONFINITE, "non-finite energy");
     if (v > 0 && eps[v] < eps[v - 1]) return fail(ctx, GW_E_ARG, "energies must be ascending");
@@ -2589,8 +2589,7 @@ gw_status gw_sigma_p(gw_ctx* ctx, const double* psi_e, double eps_e, double delt
   if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_E_ARG, "bad precision");
   if (!std::isfinite(eps_e) || !std::isfinite(delta)) return fail(ctx, GW_E_NONFINITE, "non-finite energy");
   for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
-  const int npw = ctx->npw, N3 = ctx->N3;
-  const double wgt = ctx->vol / N3;
+  const int npw = ctx->npw;
   // host copies of the small per-state inputs
   std::vector<double> he(n);
   std::vector<int> ho(n);
