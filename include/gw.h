@@ -49,7 +49,7 @@ typedef enum {
   GW_E_BREAKDOWN = 5,    /* Lanczos or CG breakdown (beta ~ 0, indefinite operator) */
   GW_E_TIMEOUT = 6,      /* reserved: a bounded device wait gave up */
   GW_E_NONFINITE = 7,    /* NaN or Inf in an input or a result */
-  GW_E_UNSUPPORTED = 8   /* configuration not supported by this build */
+  GW_E_UNSUPPORTED = 8   /* configuration the library does not handle */
 } gw_status;
 
 typedef enum {
@@ -164,7 +164,7 @@ gw_status gw_apply_eps_c(gw_ctx* ctx, const double* x, int nb, const double* ome
  *   q_1 = x0/|x0|;  w = eps~ q_k - beta_{k-1} q_{k-1};  alpha_k = <q_k|w>;
  *   w -= alpha_k q_k;  w -= Q (Q^T w) twice;  beta_k = |w|;  q_{k+1} = w / beta_k
  *   start   [N^3] real
- *   blk     block size; this build supports 1
+ *   blk     block size, 1 (blocks: gw_block_lanczos)
  *   omega   real (imaginary part 0); complex frequencies: gw_block_lanczos
  *   alpha   [k] real;  beta [k-1] real
  *   basis   [k][N^3] real Lanczos vectors (orthonormal in <.|.>), or NULL

@@ -2316,7 +2316,7 @@ gw_status gw_lanczos(gw_ctx* ctx, const double* start, int blk, int k, const dou
   TRY(begin(ctx));
   TRY(need_occ(ctx));
   if (!start || !alpha || k < 1 || (k > 1 && !beta) || !omega) return fail(ctx, GW_E_ARG, "bad arguments");
-  if (blk != 1) return fail(ctx, GW_E_UNSUPPORTED, "block Lanczos is not supported by this build");
+  if (blk != 1) return fail(ctx, GW_E_UNSUPPORTED, "gw_lanczos takes blk = 1; blocks go through gw_block_lanczos");
   std::vector<double2> om;
   TRY(check_omega(ctx, omega, 1, &om));
   if (om[0].y != 0.0)
@@ -2420,7 +2420,7 @@ gw_status gw_epsinv_elements(gw_ctx* ctx, const double* alpha, const double* bet
                              int dev) {
   TRY(begin(ctx));
   if (!alpha || !out || k < 1 || (k > 1 && !beta)) return fail(ctx, GW_E_ARG, "bad arguments");
-  if (blk != 1) return fail(ctx, GW_E_UNSUPPORTED, "block tridiagonal inverse is not supported by this build");
+  if (blk != 1) return fail(ctx, GW_E_UNSUPPORTED, "gw_epsinv_elements takes blk = 1; blocks go through gw_epsinv_block");
   const void *a, *b = nullptr;
   TRY(stage_in(ctx, "ei_a", alpha, k * sizeof(double), dev, &a));
   if (k > 1) TRY(stage_in(ctx, "ei_b", beta, (k - 1) * sizeof(double), dev, &b));
