@@ -379,7 +379,8 @@ gw_status gw_sigma_p(gw_ctx* ctx, const double* psi_e, double eps_e, double delt
  * frequency costs only small dense algebra.  Exact at w = 0 and whenever the
  * recycled vectors span the conduction space.  Uses the Sternheimer operator
  * (GW_E_UNSUPPORTED under GW_OP_MODEL).
- *   fields  [nl][N^3] real (e.g. the Lanczos basis of eps~(0)), 1 <= nl <= 256
+ *   fields  [nl][N^3] real (e.g. the Lanczos basis of eps~(0)), 1 <= nl <= 256 and
+ *           2 nl n_occ <= 65535
  *   w       [nw] imaginary frequencies w (the frequency is i w), 1 <= nw <= 4096
  *   rtol    relative singular-value cut-off (0: 1e-6)
  *   out     [nw][nl][nl] real;  kept (optional, host int): the smallest number

@@ -2632,6 +2632,8 @@ gw_status gw_recycle_eps(gw_ctx* ctx, const double* fields, int nl, const double
   if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_E_ARG, "bad precision");
   if (ctx->op != GW_OP_STERNHEIMER)
     return fail(ctx, GW_E_UNSUPPORTED, "the recycled basis is built from Sternheimer solutions");
+  if ((size_t)ctx->nocc * 2 * nl > 65535)
+    return fail(ctx, GW_E_ARG, "2 nl n_occ recycled vectors exceed one launch (65535)");
   if (rtol == 0.0) rtol = 1e-6;
   for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
   const void *F, *W;
