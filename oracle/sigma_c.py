@@ -59,9 +59,9 @@ def F_ne(w_ne, alpha):
     return 0.5 * alpha / (w_ne + alpha * np.sign(w_ne))
 
 
-def sigma_c_plain(gs, e, delta, alpha, n_freq, kind=coulomb.TRUNCATED):
-    """Sigma^c_e(delta) and its parts (integral, Sigma^A, Sigma^P) from the sum
-    over all states and dense inverses."""
+def _plain_parts(gs, e, delta, kind):
+    """Seeds v^1/2 |n* e> of every state, w_ne, and the elements
+    <e n*| v^1/2 (eps^-1(omega) - 1) v^1/2 |n* e> (dense inverse) as a function."""
     sph = gs.sph
     wg = sph.omega_vol / sph.ng
     sqv = np.sqrt(coulomb.vcoul(sph, kind))
@@ -75,6 +75,22 @@ def sigma_c_plain(gs, e, delta, alpha, n_freq, kind=coulomb.TRUNCATED):
         E = Dielectric(gs, omega, kind).dense()
         Ei = np.linalg.inv(E)
         return np.array([(wg * np.vdot(p, Ei @ p - p)).real for p in phis])
+
+    return phis, wne, elements
+
+
+def sigma_n_plain(gs, e, delta, w, kind=coulomb.TRUNCATED):
+    """sigma^N_e(i w, delta) of Eq. dge by the sum over all states."""
+    _, wne, elements = _plain_parts(gs, e, delta, kind)
+    return float(np.dot(elements(1j * w if w else 0.0), wne / (w * w + wne * wne)))
+
+
+def sigma_c_plain(gs, e, delta, alpha, n_freq, kind=coulomb.TRUNCATED):
+    """Sigma^c_e(delta) and its parts (integral, Sigma^A, Sigma^P) from the sum
+    over all states and dense inverses."""
+    sph = gs.sph
+    wg = sph.omega_vol / sph.ng
+    phis, wne, elements = _plain_parts(gs, e, delta, kind)
 
     el0 = elements(0.0)
     ws, W = frequency_nodes(n_freq)

@@ -74,3 +74,38 @@ def test_complete_basis_equals_sum_over_states(frac):
         assert parts_ref["SP"] != 0.0
     else:
         assert parts_ref["SP"] == 0.0
+
+
+def test_sigma_n_free_electron_closed_form():
+    """V_loc = 0, one occupied state (G = 0, e_e = 0): eps~(i w) is diagonal in G
+    and <e n*| v^1/2 (eps^-1 - 1) v^1/2 |n* e> = v(G)/Omega (1/eps~(G, i w) - 1)
+    for n the plane wave G, with eps~ = 1 - v(G) chi0(G, i w),
+    chi0 = -(2/Omega) |G|^2 / ((|G|^2/2)^2 + w^2); so
+        sigma^N(i w) = sum_{G != 0} v(G)/Omega (1/eps~ - 1) w_G / (w^2 + w_G^2),
+    w_G = |G|^2/2 - delta (the G = 0 term vanishes: chi0(0) = 0)."""
+    from oracle import coulomb
+    L, N, ecut = 6.0, 8, 2.0
+    sph = pw.Sphere(L, N, ecut)
+    gs = pw.ground_state_dense(sph, np.zeros(sph.ng), 1)
+    delta, w = 0.05, 0.4
+    got = SC.sigma_n_plain(gs, 0, delta, w)
+    vG = coulomb.vcoul(sph)[sph.index]
+    G2 = 2.0 * sph.kin
+    m = G2 > 0
+    chi = -(2.0 / sph.omega_vol) * G2[m] / ((G2[m] / 2) ** 2 + w * w)
+    epsr = 1.0 - vG[m] * chi
+    wG = G2[m] / 2 - delta
+    want = np.sum(vG[m] / sph.omega_vol * (1.0 / epsr - 1.0) * wG / (w * w + wG * wG))
+    assert abs(got - want) < 1e-12 * abs(want)
+
+
+def test_sigma_c_independent_of_the_model_width():
+    """The Lorentzian model is subtracted under the integral and added back as
+    Sigma^A (Eqs. e_c, dhe): with enough frequency nodes the total does not
+    depend on alpha, while the parts do."""
+    sph, gs = _cell()
+    delta = 0.3 * (gs.eps_all[gs.n_occ] - gs.eps_all[gs.n_occ - 1])
+    a, pa = SC.sigma_c_plain(gs, 1, delta, 0.5, 48)
+    b, pb = SC.sigma_c_plain(gs, 1, delta, 2.0, 48)
+    assert abs(pa["SA"] - pb["SA"]) > 1e-3 * abs(a)
+    assert abs(a - b) < 1e-7 * abs(a)
