@@ -60,3 +60,28 @@ def test_incomplete_basis_properties(small_case):
     assert (np.diff(np.array([np.diag(g) for g in got]), axis=0) < 0).all()
     # six recycled vectors per state (the paper's bases hold hundreds): ~1% here
     assert rel(got[1], _exact(gs, F, 0.5)) < 2e-2
+
+
+def test_complete_basis_matches_squared_route():
+    """Eq. P2+ solved directly (CG on ((H - e_v)^2 + w^2)) gives y = x^- + x^+;
+    the dielectric matrix is then 2 sum_v <b_{l,v}|y_{l',v}>, which the recycled
+    route reproduces when its basis spans the conduction space."""
+    from oracle import coulomb
+    wl = W.small(N=8, L=6.0, ecut=2.0, n_occ=2, seed_idx=11)
+    c = wl.cells[0]
+    sph = pw.Sphere(c.L, c.N, c.ecut)
+    gs = pw.ground_state_dense(sph, c.vloc, c.n_occ)
+    F = W.random_fields(64, 14, sph.ng)
+    w = 0.8
+    got = recycle.recycle_eps(gs, F, [w])[0]
+    sqv = np.sqrt(coulomb.vcoul(sph))
+    Y = [coulomb.sqrt_v_apply(sph, sqv, f) for f in F[:3]]
+    for v in range(gs.n_occ):
+        B = recycle.b_vectors(gs, F[:3], v)
+        Ys = [response.f_sum_imag(gs, v, y, w) for y in Y]
+        part = np.array([[2.0 * np.vdot(B[i], Ys[j]).real for j in range(3)] for i in range(3)])
+        if v == 0:
+            want = part
+        else:
+            want = want + part
+    assert rel(got[:3, :3], want) < 1e-10
