@@ -107,6 +107,35 @@ def test_truncated_coulomb_limits():
     assert np.all(v >= 0)
 
 
+def test_truncated_coulomb_potential_of_a_gaussian_charge():
+    """Sec. Results: the Coulomb interaction is cut off on a sphere of radius
+    half the cell edge.  A unit Gaussian charge of width sigma at the cell
+    centre then has, at distance d with d + 7 sigma < L/2 (the whole charge
+    inside the cut-off sphere around the point, no periodic image within it),
+    the potential of the unbounded space, erf(d / (sqrt(2) sigma)) / d
+    (sqrt(2/pi)/sigma at d = 0).  Applying v(G) (and v^1/2 twice, as the
+    dielectric operator does) on the grid must reproduce it; a wrong radius
+    (L instead of L/2) misses by 0.16, a wrong prefactor by its ratio."""
+    from scipy.special import erf
+    L, N, sig = 20.0, 64, 1.0
+    sph = pw.Sphere(L, N, 1.0)
+    x = np.arange(N) * (L / N)
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    d = np.sqrt((X - L / 2) ** 2 + (Y - L / 2) ** 2 + (Z - L / 2) ** 2).reshape(-1)
+    rho = (2 * np.pi * sig ** 2) ** -1.5 * np.exp(-d ** 2 / (2 * sig ** 2))
+    inside = d + 7 * sig < L / 2
+    dd = np.where(d > 0, d, 1.0)
+    expect = np.where(d > 0, erf(d / (np.sqrt(2) * sig)) / dd, np.sqrt(2 / np.pi) / sig)
+    v = coulomb.vcoul(sph, coulomb.TRUNCATED)
+    phi = sph.inv(v * sph.fwd(rho))
+    assert np.abs(phi.imag).max() < 1e-12
+    assert inside.sum() > 3000
+    assert np.abs(phi.real[inside] - expect[inside]).max() < 1e-8
+    sq = np.sqrt(v)
+    phi2 = coulomb.sqrt_v_apply(sph, sq, coulomb.sqrt_v_apply(sph, sq, rho)).real
+    assert np.abs(phi2[inside] - expect[inside]).max() < 1e-8
+
+
 def test_invariants(small_case):
     _, c, sph, gs = small_case
     wgt = sph.omega_vol / sph.ng
