@@ -47,7 +47,7 @@ typedef enum {
   GW_E_NOMEM = 3,        /* device allocation failed */
   GW_E_NOCONV = 4,       /* a Sternheimer solve did not reach its tolerance */
   GW_E_BREAKDOWN = 5,    /* Lanczos or CG breakdown (beta ~ 0, indefinite operator) */
-  GW_E_TIMEOUT = 6,      /* reserved: a bounded device wait gave up */
+  GW_E_TIMEOUT = 6,      /* a bounded device wait gave up (see gw_set_cg_kernel) */
   GW_E_NONFINITE = 7,    /* NaN or Inf in an input or a result */
   GW_E_UNSUPPORTED = 8   /* configuration the library does not handle */
 } gw_status;
@@ -277,6 +277,29 @@ gw_status gw_stats(const gw_ctx* ctx, double* out, int n);
  * The paper solves Eq. P2 until |A x - b|^2 < 1e-20 Ha^2 (Sec. Results).
  */
 gw_status gw_set_solver(gw_ctx* ctx, double tol, double tol_inner, int max_iter, int max_outer);
+
+/* Kernel of the CG passes at omega = 0 (gw_set_cg_kernel). */
+typedef enum {
+  GW_CG_PERSISTENT = 0,    /* one cooperative persistent launch per pass (default) */
+  GW_CG_MULTI_LAUNCH = 1,  /* one launch per transform pass, projector and update, per iteration */
+  GW_CG_CLUSTER = 2        /* one thread-block cluster per column (falls back to the persistent
+                              kernel when a column's planes do not fit in a cluster) */
+} gw_cg_kernel;
+
+/*
+ * gw_set_cg_kernel -- which kernel runs the conjugate-gradient passes of the
+ * Sternheimer solves at omega = 0 (Eq. P2; all three solve the same equations
+ * to the same tolerance), and the bound on the device waits of the persistent
+ * kernel.
+ *   kind        a gw_cg_kernel value
+ *   wait_limit  polls (about 64 ns apart) that one CTA of the persistent kernel
+ *               makes at one wait for other CTAs before it gives up; the kernel
+ *               then returns early on every CTA and the call reports
+ *               GW_E_TIMEOUT (the context stays usable).  0 keeps the current
+ *               value (default 2^24, about a second); negative is GW_E_ARG.
+ * GW_E_ARG for an unknown kind.
+ */
+gw_status gw_set_cg_kernel(gw_ctx* ctx, int kind, long long wait_limit);
 
 /*
  * gw_set_precond -- preconditioner of the Sternheimer solvers (CG and SQMR):

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libgw.so")
 GW_FP64, GW_MIXED = 0, 1
 GW_COULOMB_TRUNCATED, GW_COULOMB_BARE = 0, 1
 GW_OP_STERNHEIMER, GW_OP_MODEL = 0, 1
+GW_CG_PERSISTENT, GW_CG_MULTI_LAUNCH, GW_CG_CLUSTER = 0, 1, 2
 STATUS = {0: "GW_OK", 1: "GW_E_ARG", 2: "GW_E_CUDA", 3: "GW_E_NOMEM", 4: "GW_E_NOCONV",
           5: "GW_E_BREAKDOWN", 6: "GW_E_TIMEOUT", 7: "GW_E_NONFINITE", 8: "GW_E_UNSUPPORTED"}
 EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "gw_apply_chi0",
@@ -29,7 +30,8 @@ EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "
            "gw_set_solver", "gw_set_precond", "gw_set_deflation", "gw_profile", "gw_profile_read", "gw_last_error", "gw_destroy",
            "gw_epsinv_elements_noalloc", "gw_apply_chi0_c", "gw_apply_eps_c", "gw_block_lanczos",
            "gw_epsinv_block", "gw_batch_setup", "gw_batch_size", "gw_batch_cell", "gw_batch_lanczos",
-           "gw_batch_last_error", "gw_batch_destroy", "gw_set_operator", "gw_epsinv_split", "gw_sigma_p", "gw_recycle_eps", "gw_sigma_c")
+           "gw_batch_last_error", "gw_batch_destroy", "gw_set_operator", "gw_epsinv_split", "gw_sigma_p", "gw_recycle_eps", "gw_sigma_c",
+           "gw_set_cg_kernel")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
                    "refine_fp64", "persistent_cg")
 
@@ -71,6 +73,7 @@ def load(path=LIB_PATH):
         "gw_stats": (I, [P, P, I]),
         "gw_set_solver": (I, [P, D, D, I, I]),
         "gw_set_precond": (I, [P, I]),
+        "gw_set_cg_kernel": (I, [P, I, ctypes.c_longlong]),
         "gw_set_operator": (I, [P, I]),
         "gw_epsinv_split": (I, [P, P, I, P, P, P, I, P, P, P, I, D, P, I]),
         "gw_sigma_p": (I, [P, P, D, D, I, P, P, P, I, P, P, I, I]),
@@ -243,13 +246,40 @@ def gw_epsinv_elements(ctx, alpha, beta, k, out, blk=1):
 
 def gw_epsinv_elements_noalloc(alpha, beta, k, out, cuda_stream=None):
     """T_K^-1 without a context or any device allocation (device tensors only);
-    see include/gw.h for the shared fixed scratch and its limits."""
-    pa, d = _ptr(alpha)
-    pb, _ = _ptr(beta)
-    po, e = _ptr(out)
-    if not (d and e):
-        raise ValueError("device buffers required")
-    _check(None, load().gw_epsinv_elements_noalloc(pa, pb, int(k), po, cuda_stream))
+    see include/gw.h for the shared fixed scratch and its limits.
+
+    The kernel reads k + (k - 1) doubles and writes k * k doubles through raw
+    pointers, so every buffer is checked here first: contiguous float64 CUDA
+    tensors on the current device, alpha with at least k entries, beta with at
+    least k - 1 (it may be None only when k == 1), out with at least k * k."""
+    import torch
+    k = int(k)
+    if k < 1:
+        raise ValueError("k must be >= 1")
+    cur = torch.cuda.current_device()
+
+    def need(name, t, n):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != torch.float64:
+            raise ValueError(f"{name} must be float64")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.device.index != cur:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{cur}")
+        if t.numel() < n:
+            raise ValueError(f"{name} holds {t.numel()} values, {n} needed")
+        return t.data_ptr()
+
+    pa = need("alpha", alpha, k)
+    if beta is None:
+        if k > 1:
+            raise ValueError("beta is required for k > 1")
+        pb = None
+    else:
+        pb = need("beta", beta, k - 1)
+    po = need("out", out, k * k)
+    _check(None, load().gw_epsinv_elements_noalloc(pa, pb, k, po, cuda_stream))
     return out
 
 
@@ -283,6 +313,12 @@ def gw_set_deflation(ctx, psi, eps):
 
 def gw_set_precond(ctx, kind):
     _check(ctx, load().gw_set_precond(ctx, int(kind)))
+
+
+def gw_set_cg_kernel(ctx, kind, wait_limit=0):
+    """GW_CG_PERSISTENT, GW_CG_MULTI_LAUNCH or GW_CG_CLUSTER, and the bound on the
+    persistent kernel's device waits (0 keeps it)."""
+    _check(ctx, load().gw_set_cg_kernel(ctx, int(kind), int(wait_limit)))
 
 
 def gw_set_operator(ctx, op):
@@ -472,6 +508,9 @@ class Cell:
 
     def set_precond(self, kind):
         gw_set_precond(self.ctx, kind)
+
+    def set_cg_kernel(self, kind, wait_limit=0):
+        gw_set_cg_kernel(self.ctx, kind, wait_limit)
 
     def set_operator(self, op):
         gw_set_operator(self.ctx, op)

@@ -43,8 +43,8 @@ struct gw_ctx {
   size_t work_cols = 0;
   double tol = 1e-13, tol_mixed = 1e-10, tol_inner = 1e-5;   // backward errors (FP64 / mixed), inner
   double anorm = 1.0;           // bound on |H - E| used by the backward error
-  bool no_persistent = false;   // force the multi-launch CG (tests)
-  bool use_cluster = false;     // one thread-block cluster per column instead of the grid-wide kernel
+  int cg_kernel = GW_CG_PERSISTENT;   // kernel of the CG passes (gw_set_cg_kernel)
+  unsigned long long wait_limit = 1ull << 24;   // spins of one device wait before GW_E_TIMEOUT
   long long pcg_iters = 0;      // iterations run by persistent launches
   int pcg_launch_blocks = 0;
   int pcg_cluster = 0;          // cluster size of the last persistent launch (0: grid-wide kernel)
@@ -89,6 +89,16 @@ gw_status fail(gw_ctx* ctx, gw_status s, const std::string& msg) {
   do {                                                                                             \
     gw_status s_ = (call);                                                                         \
     if (s_ != GW_OK) return s_;                                                                    \
+  } while (0)
+
+// As TRY, except that GW_E_NOCONV is kept in `var` and the work goes on, so
+// that the outputs of a solve that missed its tolerance are still written
+// (the best iterate) before the status is returned.
+#define SOFT(var, call)                                                                            \
+  do {                                                                                             \
+    gw_status s_ = (call);                                                                         \
+    if (s_ == GW_E_NOCONV) var = s_;                                                               \
+    else if (s_ != GW_OK) return s_;                                                               \
   } while (0)
 
 template <class X>
@@ -389,17 +399,10 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
   int used = 0;
   const int pa = prof_begin(ctx, PC_PCG);
   unsigned long long* ptime = nullptr;
-  if (std::getenv("GW_DEBUG_PHASES")) {
-    TRY(getbuf(ctx, "pcg_ptime", 16, &ptime));
-    if (!ctx->ptime_init) {
-      CK(cudaMemsetAsync(ptime, 0, 16 * sizeof(unsigned long long), ctx->st));
-      ctx->ptime_init = true;
-    }
-  }
   // the cooperative grid-wide kernel, or (opt-in) one thread-block cluster per
   // column when the column's planes fit in the cluster's shared memory
   cudaError_t le = cudaErrorNotSupported;
-  if (ctx->use_cluster) {
+  if (ctx->cg_kernel == GW_CG_CLUSTER) {
     int q = 0;
     le = launch_cg_cluster<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), nproj(ctx), npw, ncol, b64, outer_active,
                               E, rr_abs, tk, tol * tol, ctx->max_iter, x, r, p, Ap, iters, flags, rr_out, &q, ptime);
@@ -412,7 +415,7 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
     CK(launch_cg_persistent<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), nproj(ctx), npw, ncol, b64,
                                outer_active, E, rr_abs, tol * tol, ctx->max_iter, x, r, p, Ap, grid, dpart, ppart,
                                rpart, zpart, tk, bar, err, iters, flags, rr_out, &used, ptime, ctx->cta_div,
-                               nchunk));
+                               nchunk, ctx->wait_limit));
   } else {
     CK(le);
   }
@@ -431,22 +434,6 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
     imax = std::max(imax, its[c]);
     if (fl[c] == 2 && std::is_same<T, double>::value)
       return fail(ctx, GW_E_BREAKDOWN, "CG breakdown: (H - E) is not positive definite on P_c");
-  }
-  if (ptime) {
-    unsigned long long h[16];
-    CK(cudaMemcpyAsync(h, ptime, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
-    TRY(sync(ctx, "ptime"));
-    long long cit = 0;
-    for (int c = 0; c < ncol; ++c) cit += its[c];
-    const double w = 1e-6 / std::max(used, 1);   // mean work per CTA
-    std::fprintf(stderr,
-                 "pcg launch: column-iterations %lld, iterations %d; cumulative phases(ms) A %.2f B %.2f C %.2f "
-                 "D %.2f E %.2f conv %.2f  blocks %d  work A %.2f B %.2f C %.2f E %.2f\n", cit, imax,
-                 h[0] * 1e-6, h[1] * 1e-6, h[2] * 1e-6, h[3] * 1e-6, h[4] * 1e-6, h[5] * 1e-6, used, h[8] * w,
-                 h[9] * w, h[10] * w, h[12] * w);
-    std::fprintf(stderr, "  column iterations:");
-    for (int c = 0; c < ncol && c < 64; ++c) std::fprintf(stderr, " %d", its[c]);
-    std::fprintf(stderr, "\n");
   }
   ctx->pcg_iters += imax;       // iterations of the whole launch (bounded by the slowest column)
   ctx->pcg_launch_blocks = used;
@@ -530,16 +517,6 @@ gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E,
     *it_sum += its[c];
     *it_max = std::max(*it_max, its[c]);
   }
-  if (std::getenv("GW_DEBUG_QMR")) {
-    std::vector<double> qb(ncol), rs(ncol);
-    CK(cudaMemcpyAsync(qb.data(), st.qbest, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-    CK(cudaMemcpyAsync(rs.data(), st.rr_stop, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-    TRY(sync(ctx, "qmr debug"));
-    for (int c = 0; c < ncol; ++c)
-      if (its[c] > 150 || c == 18)
-        std::fprintf(stderr, "qmr %s col %d it %d flag %d best/stop %.2e\n", tname<T>(), c, its[c], flags[c],
-                     std::sqrt(qb[c] / rs[c]));
-  }
   for (int c = 0; c < ncol; ++c)
     if (flags[c] == 2 && std::is_same<T, double>::value)
       return fail(ctx, GW_E_BREAKDOWN, "SQMR serious breakdown: [q, A q] = 0");
@@ -561,7 +538,7 @@ gw_status inner_solve(gw_ctx* ctx, bool qmr, int ncol, const double2* r64, const
                       cpx<U>* d, double tol_in, const double* rra, const double* tk, long long* it_sum,
                       int* it_max) {
   if (qmr) return qmr_solve<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, tk, it_sum, it_max);
-  if (ncol <= kPersistentMaxCols && !ctx->no_persistent)
+  if (ncol <= kPersistentMaxCols && ctx->cg_kernel != GW_CG_MULTI_LAUNCH)
     return cg_solve_persistent<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, tk, it_sum, it_max);
   return cg_solve<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, tk, it_sum, it_max);
 }
@@ -656,12 +633,6 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
     CK(cudaMemcpyAsync(hb.data(), bb, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaMemcpyAsync(hx.data(), xx, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     TRY(sync(ctx, "solve"));
-    if (std::getenv("GW_DEBUG_QMR")) {
-      for (int c = 0; c < ncol; ++c)
-        if (act[c] && hb[c] > 0 && std::sqrt(hr[c] / hb[c]) > 1e-9)
-          std::fprintf(stderr, "pass %d col %d |r|/|b| %.3e |x|/|b| %.3e\n", outer, c, std::sqrt(hr[c] / hb[c]),
-                       std::sqrt(hx[c] / hb[c]));
-    }
     if (hprev.empty()) hprev = hb;
     int nact = 0;
     for (int c = 0; c < ncol; ++c) {
@@ -888,10 +859,12 @@ gw_status chi0_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, const std::
   TRY(getbuf(ctx, "bcol", (size_t)ncol * npw, &bcol));
   TRY(getbuf(ctx, "xcol", (size_t)ncol * npw, &xcol));
   launch_gather_rows<double, double>(ctx->st, npw, ncol, rhs64, dsrc, bcol);
-  TRY(solve<S>(ctx, ncol, bcol, dE, xcol, qmr, dtk));
+  gw_status sv = GW_OK;
+  SOFT(sv, (solve<S>(ctx, ncol, bcol, dE, xcol, qmr, dtk)));
   // -- combine: x^- + x^+, or 2 x at omega = 0 (x^- = x^+)
   launch_combine(ctx->st, npw, nsol, xcol, ds0, ds1, 1.0, 2.0, sol64);
-  return chi0_reduce(ctx, sol64, nb, nom, dn, dn_cplx);
+  TRY(chi0_reduce(ctx, sol64, nb, nom, dn, dn_cplx));
+  return sv;
 }
 
 // density reduction of Eq. P1: dn_{o,b} = -(2/Omega) sum_v u_v IFFT(sol_{o,b,v}),
@@ -1014,10 +987,12 @@ gw_status eps_core(gw_ctx* ctx, const void* x, bool x_cplx, int nb, const std::v
     TRY(getbuf(ctx, "eps_y", (size_t)nb * N3, &y));
     TRY(getbuf(ctx, "eps_dn", (size_t)nom * nb * N3, &dn));
     TRY(sqrtv<double>(ctx, x64, nb, y, nullptr));
-    TRY(chi0_core<S>(ctx, y, false, nb, omega, dn, false));
+    gw_status sv = GW_OK;
+    SOFT(sv, (chi0_core<S>(ctx, y, false, nb, omega, dn, false)));
     for (int k = 0; k < nom; ++k)
       TRY(sqrtv<double>(ctx, dn + (size_t)k * nb * N3, nb, out64 + (size_t)k * nb * N3, x64));
-    return launch_check(ctx, "eps out");
+    TRY(launch_check(ctx, "eps out"));
+    return sv;
   }
   // complex pipeline: promote a real input
   const double2* xc = reinterpret_cast<const double2*>(x);
@@ -1036,10 +1011,12 @@ gw_status eps_core(gw_ctx* ctx, const void* x, bool x_cplx, int nb, const std::v
   TRY(getbuf(ctx, "eps_yc", (size_t)nb * N3, &y));
   TRY(getbuf(ctx, "eps_dnc", (size_t)nom * nb * N3, &dn));
   TRY(sqrtv_c(ctx, xc, nb, y, nullptr));
-  TRY(chi0_core<S>(ctx, y, true, nb, omega, dn, true));
+  gw_status sv = GW_OK;
+  SOFT(sv, (chi0_core<S>(ctx, y, true, nb, omega, dn, true)));
   for (int k = 0; k < nom; ++k)
     TRY(sqrtv_c(ctx, dn + (size_t)k * nb * N3, nb, outc + (size_t)k * nb * N3, xc));
-  return launch_check(ctx, "eps out");
+  TRY(launch_check(ctx, "eps out"));
+  return sv;
 }
 
 gw_status check_omega(gw_ctx* ctx, const double* omega, int n, std::vector<double2>* out) {
@@ -2126,8 +2103,6 @@ gw_status gw_setup(gw_ctx** out, double L, int n_grid, double ecut, const double
   }
   if (cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming) != cudaSuccess) return bail(GW_E_CUDA);
   if (cudaMallocHost(&ctx->host_pin, 64) != cudaSuccess) return bail(GW_E_CUDA);
-  if (const char* e = std::getenv("GW_MULTI_LAUNCH_CG")) ctx->no_persistent = (e[0] == '1');
-  if (const char* e = std::getenv("GW_CLUSTER_CG")) ctx->use_cluster = (e[0] == '1');
   if (fft_set_smem_limits<double>() != cudaSuccess || fft_set_smem_limits<float>() != cudaSuccess)
     return bail(GW_E_CUDA);
   gw_status s = build_geometry(ctx);
@@ -2284,11 +2259,12 @@ static gw_status apply_common(gw_ctx* ctx, const double* x, int nb, const double
   void* o;
   TRY(stage_in(ctx, "io_in", x, ib, dev, &xin));
   TRY(stage_out(ctx, "io_out", out, ob, dev, &o));
-  if (prec == GW_FP64) TRY(eps_core<double>(ctx, xin, x_cplx, nb, om, o, chi0_only));
-  else TRY(eps_core<float>(ctx, xin, x_cplx, nb, om, o, chi0_only));
+  gw_status sv = GW_OK;
+  if (prec == GW_FP64) SOFT(sv, (eps_core<double>(ctx, xin, x_cplx, nb, om, o, chi0_only)));
+  else SOFT(sv, (eps_core<float>(ctx, xin, x_cplx, nb, om, o, chi0_only)));
   TRY(copy_back(ctx, out, o, ob, dev));
   if (ctx->stats[0] > 0) ctx->stats[2] /= ctx->stats[0];
-  return finish(ctx, GW_OK);
+  return finish(ctx, sv);
 }
 
 gw_status gw_apply_chi0(gw_ctx* ctx, const double* dV, int nb, const double* omega, int n_omega, double* dn,
@@ -2484,6 +2460,15 @@ gw_status gw_set_solver(gw_ctx* ctx, double tol, double tol_inner, int max_iter,
   if (tol_inner > 0) ctx->tol_inner = tol_inner;
   if (max_iter > 0) ctx->max_iter = max_iter;
   if (max_outer > 0) ctx->max_outer = max_outer;
+  return GW_OK;
+}
+
+gw_status gw_set_cg_kernel(gw_ctx* ctx, int kind, long long wait_limit) {
+  if (!ctx) return GW_E_ARG;
+  if (kind < GW_CG_PERSISTENT || kind > GW_CG_CLUSTER) return fail(ctx, GW_E_ARG, "unknown CG kernel");
+  if (wait_limit < 0) return fail(ctx, GW_E_ARG, "wait_limit must be >= 0");
+  ctx->cg_kernel = kind;
+  if (wait_limit > 0) ctx->wait_limit = (unsigned long long)wait_limit;
   return GW_OK;
 }
 

@@ -34,7 +34,6 @@
 namespace gw {
 
 constexpr int kPT = 256;        // threads per CTA
-constexpr unsigned kSpinLimit = 1u << 24;
 
 template <typename T>
 struct PcgArgs {
@@ -67,20 +66,22 @@ struct PcgArgs {
   int* flag_out;
   double* rr_out;
   unsigned long long* ptime;   // optional [16] phase timing (see the kernel)
+  unsigned long long spin_limit;   // spins of one barrier wait before the error flag is set
 };
 
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned nblk) {
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned nblk,
+                                             unsigned long long limit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned old = atomicAdd(bar, 1u);
     const unsigned target = (old / nblk + 1u) * nblk;
-    unsigned spins = 0;
+    unsigned long long spins = 0;
     int good = 1;
     while (*(volatile unsigned*)bar < target) {
       if (*(volatile int*)err) { good = 0; break; }
-      if (++spins > kSpinLimit) { atomicExch(err, 1); good = 0; break; }
+      if (++spins > limit) { atomicExch(err, 1); good = 0; break; }
       __nanosleep(64);
     }
     __threadfence();
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
     accz = tsum_block<T>(accz, redT);
     if (threadIdx.x == 0) a.zpart[(size_t)c * a.nchunk + ch] = (double)accz;
   }
-  if (!grid_barrier(a.bar, a.err, nblk)) return;
+  if (!grid_barrier(a.bar, a.err, nblk, a.spin_limit)) return;
   column_sums(a.rpart, a.zpart, a.nchunk, ncol, st_s, st_z);
   for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
     const double s = st_s[c], z = st_z[c];
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
       __syncthreads();
     }
     work(0);
-    if (!grid_barrier(a.bar, a.err, nblk)) return;
+    if (!grid_barrier(a.bar, a.err, nblk, a.spin_limit)) return;
     mark(0);
 
     // ---- phase B: x-IFFT, * V / N_g, x-FFT on (column, i1) slabs: pencils along i0
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
       __syncthreads();
     }
     work(1);
-    if (!grid_barrier(a.bar, a.err, nblk)) return;
+    if (!grid_barrier(a.bar, a.err, nblk, a.spin_limit)) return;
     mark(1);
 
     // ---- phase C: y-FFT, z-FFT of the disc rows, gather + kinetic + shift, and
@@ -383,7 +384,7 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
       plane_dots_rec<T>(a.C, a.npw, a.nocc, S, Wv, s0, ns, rec, red);
     }
     work(2);
-    if (!grid_barrier(a.bar, a.err, nblk)) return;
+    if (!grid_barrier(a.bar, a.err, nblk, a.spin_limit)) return;
     mark(2);
 
     // ---- phase E: coef = sum of the plane partials, p^H P_c A p, alpha;
@@ -484,7 +485,7 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
       __syncthreads();
     }
     work(4);
-    if (!grid_barrier(a.bar, a.err, nblk)) return;
+    if (!grid_barrier(a.bar, a.err, nblk, a.spin_limit)) return;
     mark(4);
 
     // ---- convergence decisions (identical in every CTA)
@@ -532,7 +533,7 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
                                  cpx<T>* Ap, cpx<T>* grid, double2* dpart, double* ppart, double* rpart,
                                  double* zpart, const double* tk, unsigned* bar, int* err, int* iters, int* flags,
                                  double* rr_out, int* grid_used, unsigned long long* ptime, int cta_div,
-                                 int max_chunks) {
+                                 int max_chunks, unsigned long long spin_limit) {
   PcgArgs<T> a;
   a.g = g; a.pl = pl; a.tw = P.tw; a.kin = P.kin; a.vloc_s = P.vloc_s; a.C = P.C;
   a.nocc = nocc; a.npw = npw; a.ncol = ncol;
@@ -540,6 +541,7 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
   a.x = x; a.r = r; a.p = p; a.Ap = Ap; a.grid = grid; a.dpart = dpart; a.ppart = ppart; a.rpart = rpart;
   a.zpart = zpart; a.tk = tk;
   a.bar = bar; a.err = err; a.iters_out = iters; a.flag_out = flags; a.rr_out = rr_out; a.ptime = ptime;
+  a.spin_limit = spin_limit;
   const size_t sm = pcg_smem<T>(g.N, ncol, nocc);
   cudaError_t e = cudaSuccess;
   {
@@ -581,12 +583,12 @@ template cudaError_t launch_cg_persistent<float>(cudaStream_t, const Geometry&, 
                                                  const double*, double, int, float2*, float2*, float2*, float2*,
                                                  float2*, double2*, double*, double*, double*, const double*,
                                                  unsigned*, int*, int*, int*, double*, int*, unsigned long long*,
-                                                 int, int);
+                                                 int, int, unsigned long long);
 template cudaError_t launch_cg_persistent<double>(cudaStream_t, const Geometry&, const FftPlan&, const Prec<double>&,
                                                   int, int, int, const double2*, const int*, const double2*,
                                                   const double*, double, int, double2*, double2*, double2*,
                                                   double2*, double2*, double2*, double*, double*, double*,
                                                   const double*, unsigned*, int*, int*, int*, double*, int*,
-                                                  unsigned long long*, int, int);
+                                                  unsigned long long*, int, int, unsigned long long);
 
 }  // namespace gw

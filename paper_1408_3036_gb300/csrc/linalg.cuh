@@ -175,7 +175,7 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
                                  cpx<T>* Ap, cpx<T>* grid, double2* dpart, double* ppart, double* rpart,
                                  double* zpart, const double* tk, unsigned* bar, int* err, int* iters, int* flags,
                                  double* rr_out, int* grid_used, unsigned long long* ptime, int cta_div,
-                                 int max_chunks);
+                                 int max_chunks, unsigned long long spin_limit);
 // One thread-block cluster per column (kernels_cgc.cu); cudaErrorNotSupported
 // when the column's planes do not fit in the shared memory of a cluster.
 template <typename T>

@@ -62,8 +62,13 @@ extern "C" gw_status gw_epsinv_elements_noalloc(const double* alpha, const doubl
   double* d = scratch;
   double* l = scratch + kNoallocMaxK;
   int* flag = reinterpret_cast<int*>(scratch + 2 * kNoallocMaxK);
-  // d, l and the flag are written by the kernel before they are read, so the
-  // previous call's contents need no clearing.
+  // An error left pending by the caller's own earlier work is reported as it
+  // is, before this launch, so that the check after the launch concerns this
+  // launch alone (and the caller's error is not consumed here).
+  if (cudaPeekAtLastError() != cudaSuccess) return GW_E_CUDA;
+  // d, l and the flag are written by the kernel before they are read (the
+  // flag on every call, 0 or 1), so the previous call's contents need no
+  // clearing.
   gw::launch_tridiag_inv(s, k, alpha, beta, d, l, out, flag);
   if (cudaGetLastError() != cudaSuccess) return GW_E_CUDA;
   int hflag = 0;                               // pageable host copy: no allocation

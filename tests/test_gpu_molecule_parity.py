@@ -1,0 +1,90 @@
+"""Parity against the oracle at the benchmarked molecule configuration.
+
+L = 20 bohr, 48^3 grid, 10 Ha (12053 plane waves), 8 Gaussian wells, 16
+occupied states, omega = 0: the cell, the start vector and the launch
+configuration (16 Sternheimer columns in one persistent CG launch per
+refinement pass) that bench.py times.  The occupied states come from the
+oracle's own iterative eigensolver (LOBPCG on its FFT H application) and are
+handed to both sides; the oracle applies eps~ by its Sternheimer route (plain
+CG to a relative residual of 1e-14 per occupied state, Eqs. P1, P2).
+
+Compared element by element (reading 14, normwise relative error):
+* one eps~ application to the normalised start vector q_1;
+* the first three Lanczos steps, alpha_1..3 and beta_1..2 (Sec. Lanczos);
+FP64 path <= 1e-10, mixed path <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import lanczos, pw, response
+from tests.conftest import rel
+
+pytestmark = pytest.mark.gpu
+
+gw = pytest.importorskip("paper_1408_3036_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1408_3036_gb300 import _build
+    _build.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+K = 3
+
+
+@pytest.fixture(scope="module")
+def molecule_oracle():
+    wl = W.molecule()
+    cell = wl.cells[0]
+    sph = pw.Sphere(cell.L, cell.N, cell.ecut)
+    gs, w, _ = pw.ground_state_iterative(sph, cell.vloc, cell.n_occ, tol=1e-11, maxiter=2000)
+    assert pw.residuals(sph, cell.vloc, gs.eps, gs.C).max() < 1e-10
+    gap = w[cell.n_occ] - w[cell.n_occ - 1]
+    assert gap > 1e-3                       # reading 10: no cut inside a degenerate shell
+    D = response.Dielectric(gs, 0.0, route="sternheimer", tol=1e-14, gaps=w[cell.n_occ] - gs.eps)
+    wgt = sph.omega_vol / sph.ng
+    x0 = wl.starts[0][0]
+    applied = []
+
+    def apply(q):
+        y = D.apply(q)
+        applied.append(y)
+        return y
+
+    alpha, beta, Q = lanczos.lanczos(apply, x0, K, weight=wgt)
+    return dict(wl=wl, cell=cell, gs=gs, q1=Q[0], eq1=applied[0], alpha=np.real(alpha), beta=np.real(beta),
+                wgt=wgt)
+
+
+def _cell(o):
+    c = gw.Cell(o["cell"].L, o["cell"].N, o["cell"].ecut, o["cell"].vloc)
+    c.set_occupied(o["gs"].C, o["gs"].eps)
+    return c
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-6)])
+def test_molecule_eps_application_matches_oracle(molecule_oracle, prec, tol):
+    o = molecule_oracle
+    c = _cell(o)
+    p = gw.GW_FP64 if prec == "fp64" else gw.GW_MIXED
+    out = c.apply_eps(o["q1"][None, :], [0.0], p)[0][0]
+    assert rel(out, o["eq1"]) < tol
+    st = c.stats()
+    assert st["launch_ctas"] > 0            # the persistent kernel ran (the benchmarked launch form)
+    c.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-6)])
+def test_molecule_lanczos_matches_oracle(molecule_oracle, prec, tol):
+    o = molecule_oracle
+    c = _cell(o)
+    p = gw.GW_FP64 if prec == "fp64" else gw.GW_MIXED
+    a, b, _ = c.lanczos(o["wl"].starts[0][0], K, 0.0, p)
+    assert rel(a, o["alpha"]) < tol
+    assert rel(b, o["beta"]) < tol
+    c.close()

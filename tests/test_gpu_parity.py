@@ -156,30 +156,62 @@ def test_free_electron_closed_form_gpu():
     c.close()
 
 
-def test_persistent_cg_matches_multi_launch(tiny, monkeypatch):
+def test_persistent_cg_matches_multi_launch(tiny):
     """The one-launch CG (the grid-wide cooperative kernel, or one cluster per
     column) and the multi-launch CG agree."""
     wl, cell, sph, gs = tiny
     f = W.random_fields(103, 2, sph.ng)
-    c1 = make(cell, gs)
-    out1 = c1.apply_eps(f, [0.0], gw.GW_FP64)
-    out1m = c1.apply_eps(f, [0.0], gw.GW_MIXED)
-    c1.close()
-    monkeypatch.setenv("GW_CLUSTER_CG", "1")        # one thread-block cluster per column
-    c3 = make(cell, gs)
-    out3 = c3.apply_eps(f, [0.0], gw.GW_FP64)
-    out3m = c3.apply_eps(f, [0.0], gw.GW_MIXED)
-    c3.close()
-    monkeypatch.delenv("GW_CLUSTER_CG")
-    monkeypatch.setenv("GW_MULTI_LAUNCH_CG", "1")
-    c2 = make(cell, gs)
-    out2 = c2.apply_eps(f, [0.0], gw.GW_FP64)
-    out2m = c2.apply_eps(f, [0.0], gw.GW_MIXED)
-    c2.close()
-    assert rel(out1, out2) < 1e-12
-    assert rel(out1m, out2m) < 1e-8
-    assert rel(out1, out3) < 1e-12
-    assert rel(out1m, out3m) < 1e-8
+    outs = {}
+    for kind in (gw.GW_CG_PERSISTENT, gw.GW_CG_CLUSTER, gw.GW_CG_MULTI_LAUNCH):
+        c = make(cell, gs)
+        c.set_cg_kernel(kind)
+        outs[kind] = (c.apply_eps(f, [0.0], gw.GW_FP64), c.apply_eps(f, [0.0], gw.GW_MIXED))
+        c.close()
+    o1, o1m = outs[gw.GW_CG_PERSISTENT]
+    for kind in (gw.GW_CG_CLUSTER, gw.GW_CG_MULTI_LAUNCH):
+        o, om = outs[kind]
+        assert rel(o1, o) < 1e-12
+        assert rel(o1m, om) < 1e-8
+
+
+def test_solver_iteration_cap_reports_noconv(tiny):
+    """Sec. "Avoiding summations": a Sternheimer solve that does not reach its
+    tolerance is a failure of the method; with one inner iteration per pass and
+    two passes the library must say so (GW_E_NOCONV, status 4) and still write
+    finite outputs, and the context must work normally afterwards."""
+    wl, cell, sph, gs = tiny
+    f = W.random_fields(104, 1, sph.ng)
+    c = make(cell, gs)
+    good = c.apply_eps(f, [0.0], gw.GW_FP64)
+    c.set_solver(max_iter=1, max_outer=2)
+    out = np.full((1, 1, sph.ng), np.nan)
+    with pytest.raises(gw.GwError) as ei:
+        gw.gw_apply_eps(c.ctx, np.ascontiguousarray(f), [0.0], out, gw.GW_FP64)
+    assert ei.value.status == 4
+    assert "did not converge" in gw.gw_last_error(c.ctx)
+    assert np.all(np.isfinite(out))
+    c.set_solver(max_iter=20000, max_outer=12)
+    assert rel(c.apply_eps(f, [0.0], gw.GW_FP64), good) < 1e-12
+    c.close()
+
+
+@pytest.mark.parametrize("prec", [gw.GW_FP64, gw.GW_MIXED])
+def test_persistent_wait_bound_reports_timeout(tiny, prec):
+    """Every device wait of the persistent CG is bounded: with the bound cut to
+    one poll the CTAs that arrive first give up, every CTA returns, and the
+    call reports GW_E_TIMEOUT (status 6) instead of hanging; the context then
+    solves normally with the default bound."""
+    wl, cell, sph, gs = tiny
+    f = W.random_fields(105, 2, sph.ng)
+    c = make(cell, gs)
+    good = c.apply_eps(f, [0.0], prec)
+    c.set_cg_kernel(gw.GW_CG_PERSISTENT, 1)
+    with pytest.raises(gw.GwError) as ei:
+        c.apply_eps(f, [0.0], prec)
+    assert ei.value.status == 6
+    c.set_cg_kernel(gw.GW_CG_PERSISTENT, 1 << 24)
+    assert rel(c.apply_eps(f, [0.0], prec), good) < (1e-12 if prec == gw.GW_FP64 else 1e-8)
+    c.close()
 
 
 @pytest.mark.parametrize("omega", [0.3 + 0.1j, 0.25j, 0.9, 1.7 + 0.05j])
