@@ -251,6 +251,21 @@ gw_status gw_grad_vloc(gw_ctx* ctx, const double* phi, int k, double* s, double*
                        int device_ptrs);
 
 /*
+ * gw_grad_vloc_basis -- the same s and ds/dV_loc as gw_grad_vloc, from a
+ * Lanczos basis the caller kept: basis [k][N^3], alpha [k], beta [k-1] as
+ * returned by gw_lanczos(ctx, phi, 1, k, omega = 0, ...) on this context (the
+ * checkpoint of a forward pass).  T^-1, s = |phi|^2 (T^-1)_11 and
+ * u = |phi| sum_k q_k (T^-1)_k1 come from it; the first-order orbitals dpsi_v
+ * and the adjoint solutions lambda_v are computed here and not kept, so a
+ * caller that stores only the basis between a forward and a backward pass
+ * holds k N^3 doubles, not the 2 n_occ N_PW complex orbitals as well.
+ * Pointers all host or all device (device_ptrs).  GW_E_BREAKDOWN for a zero
+ * pivot of T.
+ */
+gw_status gw_grad_vloc_basis(gw_ctx* ctx, const double* phi, const double* basis, const double* alpha,
+                             const double* beta, int k, double* s, double* grad, gw_prec prec, int device_ptrs);
+
+/*
  * gw_stats -- counters of the last solve on the context:
  *   out[0] Sternheimer columns solved, out[1] max inner iterations,
  *   out[2] mean inner iterations, out[3] outer (FP64 residual) passes,
@@ -322,11 +337,11 @@ gw_status gw_set_precond(gw_ctx* ctx, int kind);
  *   f~_v(-/+) = P_c [ (|G|^2/2 - e_v -/+ omega)^-1 P_c (psi_v* dV) ],
  * summed over both signs and reduced as in Eq. P1.  The energies are the
  * absolute e_v given to gw_set_occupied; a denominator that is exactly zero
- * contributes zero (pseudo-inverse).  Under GW_OP_MODEL, GW_FP64 runs every
- * step in FP64; GW_MIXED runs the transforms, projections and divisions of
- * real fields at real frequencies in FP32 with the fields at the boundary and
- * the Lanczos recursion in FP64 (complex fields or frequencies stay FP64).  No
- * solver statistics are produced, and gw_grad_vloc returns GW_E_UNSUPPORTED.
+ * contributes zero (pseudo-inverse).  Under GW_OP_MODEL both precisions run
+ * every step in FP64: the model has no Sternheimer solve whose FP64 residual
+ * could recover what FP32 transforms lose (about 1e-5 on the Lanczos
+ * coefficients after 20 steps), so GW_MIXED gives the FP64 result.  No solver
+ * statistics are produced, and gw_grad_vloc returns GW_E_UNSUPPORTED.
  * GW_E_ARG for any other value.
  */
 gw_status gw_set_operator(gw_ctx* ctx, int op);

@@ -31,7 +31,7 @@ EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "
            "gw_epsinv_elements_noalloc", "gw_apply_chi0_c", "gw_apply_eps_c", "gw_block_lanczos",
            "gw_epsinv_block", "gw_batch_setup", "gw_batch_size", "gw_batch_cell", "gw_batch_lanczos",
            "gw_batch_last_error", "gw_batch_destroy", "gw_set_operator", "gw_epsinv_split", "gw_sigma_p", "gw_recycle_eps", "gw_sigma_c",
-           "gw_set_cg_kernel")
+           "gw_set_cg_kernel", "gw_grad_vloc_basis")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
                    "refine_fp64", "persistent_cg")
 
@@ -70,6 +70,7 @@ def load(path=LIB_PATH):
         "gw_block_lanczos": (I, [P, P, I, I, P, P, P, P, I, I]),
         "gw_epsinv_block": (I, [P, P, P, I, I, I, P, I]),
         "gw_grad_vloc": (I, [P, P, I, P, P, I, I]),
+        "gw_grad_vloc_basis": (I, [P, P, P, P, P, I, P, P, I, I]),
         "gw_stats": (I, [P, P, I]),
         "gw_set_solver": (I, [P, D, D, I, I]),
         "gw_set_precond": (I, [P, I]),
@@ -288,6 +289,20 @@ def gw_grad_vloc(ctx, phi, k, s, grad, prec=GW_FP64):
     ps, _ = _ptr(s)
     pg, _ = _ptr(grad)
     _check(ctx, load().gw_grad_vloc(ctx, pp, int(k), ps, pg, int(prec), d))
+    return s, grad
+
+
+def gw_grad_vloc_basis(ctx, phi, basis, alpha, beta, k, s, grad, prec=GW_FP64):
+    """s and ds/dV_loc from a kept Lanczos basis (gw_lanczos at omega = 0 from phi)."""
+    pp, d = _ptr(phi)
+    pq, d2 = _ptr(basis)
+    pa, d3 = _ptr(alpha)
+    pb, d4 = _ptr(beta)
+    ps, d5 = _ptr(s)
+    pg, d6 = _ptr(grad)
+    if len({d, d2, d3, d5, d6} | ({d4} if beta is not None else set())) != 1:
+        raise ValueError("mixed host/device buffers")
+    _check(ctx, load().gw_grad_vloc_basis(ctx, pp, pq, pa, pb, int(k), ps, pg, int(prec), d))
     return s, grad
 
 

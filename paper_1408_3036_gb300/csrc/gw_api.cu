@@ -44,6 +44,7 @@ struct gw_ctx {
   double tol = 1e-13, tol_mixed = 1e-10, tol_inner = 1e-5;   // backward errors (FP64 / mixed), inner
   double anorm = 1.0;           // bound on |H - E| used by the backward error
   int cg_kernel = GW_CG_PERSISTENT;   // kernel of the CG passes (gw_set_cg_kernel)
+  int maxplane = 0;                   // most sphere entries in one plane i0
   unsigned long long wait_limit = 1ull << 24;   // spins of one device wait before GW_E_TIMEOUT
   long long pcg_iters = 0;      // iterations run by persistent launches
   int pcg_launch_blocks = 0;
@@ -371,62 +372,73 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
 // ---------------------------------------------------------------------------
 template <typename T>
 gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, const int* outer_active,
-                              cpx<T>* x, double tol, const double* rr_abs, const double* tk, long long* it_sum,
-                              int* it_max) {
+                              cpx<T>* x, double tol, const double* rr_abs, const double* tk, bool sym,
+                              long long* it_sum, int* it_max, bool* ran) {
   const int npw = ctx->npw;
   const std::string t = tname<T>();
-  const int nchunk = (npw + kPcgChunkMin - 1) / kPcgChunkMin;   // partial-sum slots per column
-  cpx<T>*r, *p, *Ap, *grid;
-  TRY(getbuf(ctx, "cg_r" + t, (size_t)ncol * npw, &r));
-  TRY(getbuf(ctx, "cg_p" + t, (size_t)ncol * npw, &p));
-  TRY(getbuf(ctx, "cg_Ap" + t, (size_t)ncol * npw, &Ap));
-  TRY(getbuf(ctx, "g_cg" + t, (size_t)ncol * ctx->N3, &grid));
-  double2* dpart;
-  double *ppart, *rpart, *zpart, *rr_out;
-  unsigned* bar;
-  int *err, *iters, *flags;
-  TRY(getbuf(ctx, "pcg_dpart", (size_t)ncol * ctx->geo.nplanes * (2 * nproj(ctx) + 1), &dpart));
-  TRY(getbuf(ctx, "pcg_ppart", (size_t)ncol * nchunk, &ppart));
-  TRY(getbuf(ctx, "pcg_rpart", (size_t)ncol * nchunk, &rpart));
-  TRY(getbuf(ctx, "pcg_zpart", (size_t)ncol * nchunk, &zpart));
+  *ran = true;
+  int *iters, *flags;
+  double* rr_out;
   TRY(getbuf(ctx, "pcg_rr", ncol, &rr_out));
-  TRY(getbuf(ctx, "pcg_bar", 1, &bar));
-  TRY(getbuf(ctx, "pcg_err", 1, &err));
   TRY(getbuf(ctx, "pcg_iters", ncol, &iters));
   TRY(getbuf(ctx, "pcg_flags", ncol, &flags));
-  CK(cudaMemsetAsync(bar, 0, sizeof(unsigned), ctx->st));
-  CK(cudaMemsetAsync(err, 0, sizeof(int), ctx->st));
   int used = 0;
   const int pa = prof_begin(ctx, PC_PCG);
-  unsigned long long* ptime = nullptr;
-  // the cooperative grid-wide kernel, or (opt-in) one thread-block cluster per
-  // column when the column's planes fit in the cluster's shared memory
   cudaError_t le = cudaErrorNotSupported;
+  unsigned* ctl = nullptr;
   if (ctx->cg_kernel == GW_CG_CLUSTER) {
+    // opt-in: one thread-block cluster per column when the column's planes
+    // fit in the cluster's shared memory
+    cpx<T>*r, *p, *Ap;
+    TRY(getbuf(ctx, "cg_r" + t, (size_t)ncol * npw, &r));
+    TRY(getbuf(ctx, "cg_p" + t, (size_t)ncol * npw, &p));
+    TRY(getbuf(ctx, "cg_Ap" + t, (size_t)ncol * npw, &Ap));
     int q = 0;
     le = launch_cg_cluster<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), nproj(ctx), npw, ncol, b64, outer_active,
-                              E, rr_abs, tk, tol * tol, ctx->max_iter, x, r, p, Ap, iters, flags, rr_out, &q, ptime);
+                              E, rr_abs, tk, tol * tol, ctx->max_iter, x, r, p, Ap, iters, flags, rr_out, &q, nullptr);
     used = ncol * q;
     ctx->pcg_cluster = q;
   }
   if (le == cudaErrorNotSupported) {
     cudaGetLastError();
     ctx->pcg_cluster = 0;
-    CK(launch_cg_persistent<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), nproj(ctx), npw, ncol, b64,
-                               outer_active, E, rr_abs, tol * tol, ctx->max_iter, x, r, p, Ap, grid, dpart, ppart,
-                               rpart, zpart, tk, bar, err, iters, flags, rr_out, &used, ptime, ctx->cta_div,
-                               nchunk, ctx->wait_limit));
-  } else {
-    CK(le);
+    // the grid-wide task-queue kernel: real-in-real-space columns in packed pairs
+    const PcgSizes z = pcg_sizes(nproj(ctx), npw, ncol, sym ? 2 : 1, ctx->geo.nplanes, ctx->N3,
+                                 (int)sizeof(cpx<T>));
+    cpx<T>*r, *p, *sv, *Y, *grid;
+    unsigned char* rec;
+    double* apart;
+    PcgCol* cst;
+    TRY(getbuf(ctx, "cg_r" + t, (size_t)ncol * npw, &r));
+    TRY(getbuf(ctx, "cg_p" + t, (size_t)ncol * npw, &p));
+    TRY(getbuf(ctx, "cg_Ap" + t, (size_t)ncol * npw, &sv));
+    TRY(getbuf(ctx, "pcg_Y" + t, z.Y, &Y));
+    TRY(getbuf(ctx, "g_cg" + t, z.grid, &grid));
+    TRY(getbuf(ctx, "pcg_rec", z.rec_total, &rec));
+    TRY(getbuf(ctx, "pcg_apart", z.apart, &apart));
+    TRY(getbuf(ctx, "pcg_cst", z.cst, &cst));
+    TRY(getbuf(ctx, "pcg_ctl", z.ctl, &ctl));
+    CK(cudaMemsetAsync(ctl, 0, z.ctl * sizeof(unsigned), ctx->st));
+    le = launch_cg_persistent<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), nproj(ctx), npw, ncol, z,
+                                 ctx->maxplane, b64, outer_active, E, rr_abs, tk, tol * tol, ctx->max_iter, x, r, p,
+                                 sv, Y, grid, rec, apart, cst, ctl, iters, flags, rr_out, &used, ctx->cta_div,
+                                 ctx->wait_limit);
+    if (le == cudaErrorNotSupported) {      // shared memory beyond one SM: the multi-launch CG
+      cudaGetLastError();
+      prof_end(ctx, PC_PCG, pa);
+      *ran = false;
+      return GW_OK;
+    }
   }
+  CK(le);
   prof_end(ctx, PC_PCG, pa);
   std::vector<int> its(ncol), fl(ncol);
-  int herr = 0;
+  unsigned herr = 0;
   CK(cudaMemcpyAsync(its.data(), iters, ncol * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaMemcpyAsync(fl.data(), flags, ncol * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  if (ctl) CK(cudaMemcpyAsync(&herr, ctl + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->st));
   TRY(sync(ctx, "cg_persistent"));
-  if (herr) return fail(ctx, GW_E_TIMEOUT, "persistent CG: a grid barrier timed out");
+  if (herr) return fail(ctx, GW_E_TIMEOUT, "persistent CG: a bounded device wait gave up");
   int imax = 0;
   for (int c = 0; c < ncol; ++c) {
     *it_sum += its[c];
@@ -535,11 +547,14 @@ gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E,
 // when the columns fit, else the multi-launch form).
 template <typename U>
 gw_status inner_solve(gw_ctx* ctx, bool qmr, int ncol, const double2* r64, const double2* E, const int* oact,
-                      cpx<U>* d, double tol_in, const double* rra, const double* tk, long long* it_sum,
+                      cpx<U>* d, double tol_in, const double* rra, const double* tk, bool sym, long long* it_sum,
                       int* it_max) {
   if (qmr) return qmr_solve<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, tk, it_sum, it_max);
-  if (ncol <= kPersistentMaxCols && ctx->cg_kernel != GW_CG_MULTI_LAUNCH)
-    return cg_solve_persistent<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, tk, it_sum, it_max);
+  if (ncol <= kPersistentMaxCols && ctx->cg_kernel != GW_CG_MULTI_LAUNCH) {
+    bool ran = false;
+    TRY(cg_solve_persistent<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, tk, sym, it_sum, it_max, &ran));
+    if (ran) return GW_OK;
+  }
   return cg_solve<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, tk, it_sum, it_max);
 }
 
@@ -574,6 +589,21 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
   }
   CK(cudaMemsetAsync(x64, 0, (size_t)ncol * npw * sizeof(double2), ctx->st));
   CK(cudaMemcpyAsync(r64, b64, (size_t)ncol * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
+  // Right-hand sides that are real in real space (b(-G) = conj b(G): real
+  // fields, realified occupied states) have real-in-real-space solutions; the
+  // CG then packs two columns into one complex transform.  Decided from the
+  // data, to the FP64 rounding of the right-hand sides.
+  bool sym = false;
+  if (!qmr) {
+    double* symv;
+    TRY(getbuf(ctx, "sv_sym", (size_t)2 * ncol, &symv));
+    launch_sym_check(ctx->st, npw, ncol, b64, ctx->geo.sph_neg, symv);
+    std::vector<double> hs(2 * ncol);
+    CK(cudaMemcpyAsync(hs.data(), symv, 2 * ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    TRY(sync(ctx, "symmetry check"));
+    sym = true;
+    for (int c = 0; c < ncol; ++c) sym = sym && (hs[c] <= 1e-12 * hs[ncol + c]);
+  }
   std::vector<int> act(ncol, 1);
   TRY(upload(ctx, "sv_oact", act, &oact));
   std::vector<double> hr(ncol, 0.0), hb(ncol, 0.0), hx(ncol, 0.0), habs(ncol, 0.0);
@@ -603,11 +633,14 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
     if (esc) {
       if (!d64) TRY(getbuf(ctx, "sv_d64", (size_t)ncol * npw, &d64));
       TRY(inner_solve<double>(ctx, qmr, ncol, r64, E, oact, reinterpret_cast<cpx<double>*>(d64),
-                              std::max(1e2 * ctx->tol, 1e-11), rra, tk, &it_sum, &it_max));
-      launch_add_conv<double>(ctx->st, npw, ncol, reinterpret_cast<cpx<double>*>(d64), x64, oact);
+                              std::max(1e2 * ctx->tol, 1e-11), rra, tk, sym, &it_sum, &it_max));
+      if (sym) launch_add_conv_sym<double>(ctx->st, npw, ncol, reinterpret_cast<cpx<double>*>(d64), x64, oact,
+                                           ctx->geo.sph_neg);
+      else launch_add_conv<double>(ctx->st, npw, ncol, reinterpret_cast<cpx<double>*>(d64), x64, oact);
     } else {
-      TRY(inner_solve<T>(ctx, qmr, ncol, r64, E, oact, d, tol_in, rra, tk, &it_sum, &it_max));
-      launch_add_conv<T>(ctx->st, npw, ncol, d, x64, oact);
+      TRY(inner_solve<T>(ctx, qmr, ncol, r64, E, oact, d, tol_in, rra, tk, sym, &it_sum, &it_max));
+      if (sym) launch_add_conv_sym<T>(ctx->st, npw, ncol, d, x64, oact, ctx->geo.sph_neg);
+      else launch_add_conv<T>(ctx->st, npw, ncol, d, x64, oact);
     }
     if (ctx->ndef > 0)                // the deflated components, exactly
       launch_proj_update<double>(ctx->st, ctx->P64.C + (size_t)ctx->nocc * npw, ctx->ndef, npw, x64, ncol, oact,
@@ -960,28 +993,6 @@ gw_status eps_core(gw_ctx* ctx, const void* x, bool x_cplx, int nb, const std::v
   if (!out_cplx) {
     const double* x64 = reinterpret_cast<const double*>(x);
     double* out64 = reinterpret_cast<double*>(out);
-    if (ctx->op == GW_OP_MODEL && std::is_same<S, float>::value) {
-      // model operator, mixed: the transforms and projections in FP32, the
-      // fields at the boundary in FP64 (eps~ x = x - z with z from FP32)
-      float *x32, *y32, *dn32;
-      const size_t n = (size_t)nb * N3;
-      TRY(getbuf(ctx, "m32_x", n, &x32));
-      TRY(getbuf(ctx, "m32_y", n, &y32));
-      TRY(getbuf(ctx, "m32_dn", (size_t)nom * n, &dn32));
-      launch_cast(ctx->st, n, x64, x32);
-      if (chi0_only) {
-        TRY(chi0_model_core<float>(ctx, x32, false, nb, omega, dn32, false));
-        launch_cast(ctx->st, (size_t)nom * n, dn32, out64);
-        return launch_check(ctx, "chi0 model mixed");
-      }
-      TRY(sqrtv<float>(ctx, x32, nb, y32, nullptr));
-      TRY(chi0_model_core<float>(ctx, y32, false, nb, omega, dn32, false));
-      for (int k = 0; k < nom; ++k) {
-        TRY(sqrtv<float>(ctx, dn32 + (size_t)k * n, nb, y32, nullptr));
-        launch_sub_mixed(ctx->st, n, x64, y32, out64 + (size_t)k * n);
-      }
-      return launch_check(ctx, "eps model mixed");
-    }
     if (chi0_only) return chi0_core<S>(ctx, x64, false, nb, omega, out64, false);
     double *y, *dn;
     TRY(getbuf(ctx, "eps_y", (size_t)nb * N3, &y));
@@ -1272,15 +1283,15 @@ gw_status block_lanczos_core(gw_ctx* ctx, const double* start, int blk, int K, d
 // dpsi is recomputed from them rather than stored across the Lanczos run.
 // ---------------------------------------------------------------------------
 template <typename S>
+gw_status grad_from_basis(gw_ctx* ctx, const double* phi, const double* Q, const double* a, const double* b, int K,
+                          double* s_out, double* grad);
+
+template <typename S>
 gw_status grad_core(gw_ctx* ctx, const double* phi, int K, double* s_out, double* grad) {
-  const int N3 = ctx->N3, npw = ctx->npw, nocc = ctx->nocc;
-  const double vol = ctx->vol, wgt = vol / N3;
-  const Geometry& g = ctx->geo;
-  auto& P = ctx->P64;
-  TRY(ensure_work(ctx, std::max(K + 1, nocc * nocc)));
+  const int N3 = ctx->N3;
+  TRY(ensure_work(ctx, std::max(K + 1, ctx->nocc * ctx->nocc)));
   // -- Lanczos from phi with the basis kept
-  double *a, *b, *Q, *x0c, *Ti, *d, *l, *u, *w, *h;
-  int* stat;
+  double *a, *b, *Q, *x0c;
   TRY(getbuf(ctx, "gr_alpha", K, &a));
   TRY(getbuf(ctx, "gr_beta", std::max(K - 1, 1), &b));
   TRY(getbuf(ctx, "gr_Q", (size_t)K * N3, &Q));
@@ -1289,6 +1300,23 @@ gw_status grad_core(gw_ctx* ctx, const double* phi, int K, double* s_out, double
   std::vector<double2> om(1, make_double2(0.0, 0.0));
   gw_status st = lanczos_core<S>(ctx, x0c, K, om, a, b, Q);
   if (st != GW_OK && st != GW_E_BREAKDOWN) return st;
+  return grad_from_basis<S>(ctx, phi, Q, a, b, K, s_out, grad);
+}
+
+// The gradient from a kept Lanczos basis Q [K][N_g] of eps~(0) started at phi
+// (alpha [K], beta [K-1] on the device): T^-1, s, u = |phi| Q T^-1 e_1, then
+// the Sternheimer and adjoint solves (dpsi is computed here, never stored
+// with the basis).
+template <typename S>
+gw_status grad_from_basis(gw_ctx* ctx, const double* phi, const double* Q, const double* a, const double* b, int K,
+                          double* s_out, double* grad) {
+  const int N3 = ctx->N3, npw = ctx->npw, nocc = ctx->nocc;
+  const double vol = ctx->vol, wgt = vol / N3;
+  const Geometry& g = ctx->geo;
+  auto& P = ctx->P64;
+  TRY(ensure_work(ctx, std::max(K + 1, nocc * nocc)));
+  double *Ti, *d, *l, *u, *w, *h;
+  int* stat;
   // -- T^-1 and s
   TRY(getbuf(ctx, "gr_Ti", (size_t)K * K, &Ti));
   TRY(getbuf(ctx, "gr_d", K, &d));
@@ -1484,6 +1512,8 @@ gw_status build_geometry(gw_ctx* ctx) {
   TRY(upload(ctx, "geo_allp", allp, &g.all_planes));
   TRY(upload(ctx, "geo_pmask", pmask, &g.plane_mask));
   TRY(upload(ctx, "geo_plane_sph", plane_sph, &g.plane_sph));
+  ctx->maxplane = 0;
+  for (size_t q = 0; q + 1 < plane_sph.size(); ++q) ctx->maxplane = std::max(ctx->maxplane, plane_sph[q + 1] - plane_sph[q]);
   TRY(upload(ctx, "geo_plane_pen", plane_pen, &g.plane_pen));
   TRY(upload(ctx, "geo_i1", i1s, &g.sph_i1));
   TRY(upload(ctx, "geo_neg", negs, &g.sph_neg));
@@ -1640,6 +1670,20 @@ gw_status realify_block(gw_ctx* ctx, int n_occ, const double* psi, const double*
     if (!(n2 > 0.5)) return fail(ctx, GW_E_ARG, std::string(what) + " states are not orthonormal");
     const double inv = 1.0 / std::sqrt(n2);
     for (int s = 0; s < npw; ++s) a[s] *= inv;
+  }
+  // exact K-symmetry of every row (c_{-G} = conj c_G to the last bit), so that
+  // solver vectors built from these rows stay exactly real in real space
+  for (int v = 0; v < n_occ; ++v) {
+    zc* a = &R[(size_t)v * npw];
+    for (int s = 0; s < npw; ++s) {
+      if (neg[s] > s) {
+        const zc h = 0.5 * (a[s] + std::conj(a[neg[s]]));
+        a[s] = h;
+        a[neg[s]] = std::conj(h);
+      } else if (neg[s] == s) {
+        a[s] = zc(a[s].real(), 0.0);
+      }
+    }
   }
   *Rout = std::move(R);
   *eout = std::move(e);
@@ -2435,6 +2479,40 @@ gw_status gw_grad_vloc(gw_ctx* ctx, const double* phi, int k, double* s, double*
   gw_status st = (prec == GW_FP64)
                      ? grad_core<double>(ctx, reinterpret_cast<const double*>(ph), k, &sv, reinterpret_cast<double*>(go))
                      : grad_core<float>(ctx, reinterpret_cast<const double*>(ph), k, &sv, reinterpret_cast<double*>(go));
+  if (st != GW_OK) return st;
+  TRY(copy_back(ctx, grad, go, fb, dev));
+  TRY(sync(ctx, "grad"));
+  if (dev) CK(cudaMemcpy(s, &sv, sizeof(double), cudaMemcpyHostToDevice));
+  else *s = sv;
+  if (ctx->stats[0] > 0) ctx->stats[2] /= ctx->stats[0];
+  return GW_OK;
+}
+
+gw_status gw_grad_vloc_basis(gw_ctx* ctx, const double* phi, const double* basis, const double* alpha,
+                             const double* beta, int k, double* s, double* grad, gw_prec prec, int dev) {
+  TRY(begin(ctx));
+  TRY(need_occ(ctx));
+  if (ctx->op != GW_OP_STERNHEIMER)
+    return fail(ctx, GW_E_UNSUPPORTED, "the gradient is of the Sternheimer operator; set GW_OP_STERNHEIMER");
+  if (!phi || !basis || !alpha || (k > 1 && !beta) || !s || !grad || k < 1) return fail(ctx, GW_E_ARG, "bad arguments");
+  if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_E_ARG, "bad precision");
+  for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
+  const size_t fb = (size_t)ctx->N3 * sizeof(double);
+  const void *ph, *qb, *ab, *bb;
+  void* go;
+  TRY(stage_in(ctx, "gr_phi", phi, fb, dev, &ph));
+  TRY(stage_in(ctx, "grb_Q", basis, fb * k, dev, &qb));
+  TRY(stage_in(ctx, "grb_a", alpha, (size_t)k * sizeof(double), dev, &ab));
+  if (k > 1) TRY(stage_in(ctx, "grb_b", beta, (size_t)(k - 1) * sizeof(double), dev, &bb));
+  else bb = ab;
+  TRY(stage_out(ctx, "gr_out", grad, fb, dev, &go));
+  double sv = 0.0;
+  const double* P = reinterpret_cast<const double*>(ph);
+  const double* Q = reinterpret_cast<const double*>(qb);
+  const double* A = reinterpret_cast<const double*>(ab);
+  const double* B = reinterpret_cast<const double*>(bb);
+  gw_status st = (prec == GW_FP64) ? grad_from_basis<double>(ctx, P, Q, A, B, k, &sv, reinterpret_cast<double*>(go))
+                                   : grad_from_basis<float>(ctx, P, Q, A, B, k, &sv, reinterpret_cast<double*>(go));
   if (st != GW_OK) return st;
   TRY(copy_back(ctx, grad, go, fb, dev));
   TRY(sync(ctx, "grad"));

@@ -1,26 +1,52 @@
 // Persistent conjugate-gradient solver for the Sternheimer equations
-// (Eq. P2: (H - e_v -/+ w) x = P_c psi_v* dV, projected on the conduction
-// space at every step as in Sec. Avoiding summations).
+// (Eq. P2: (H - e_v) x = P_c psi_v* dV, projected on the conduction space at
+// every step as in Sec. Avoiding summations).
 //
 // One cooperative launch runs a whole CG pass for every column (occupied
-// state x field x frequency) with per-column convergence masks.  The CTAs are
-// all resident and step through four phases per iteration, separated by a
-// grid barrier (bounded spin: a barrier that waits too long sets an error flag
-// and every CTA returns):
-//   A  per (column, plane i0): p = K r + beta p on the plane's sphere entries
-//      (K: kinetic preconditioner, 1 without one),
-//      scatter, z-IFFT of the disc rows, y-IFFT of the plane (all in shared
-//      memory), store the plane
-//   B  per (column, i1, 16 i2): x-IFFT, * V(r)/N_g, x-FFT (planes of the sphere)
-//   C  per (column, plane): y-FFT, z-FFT of the disc rows, gather the sphere
-//      entries, Ap = (Vp)_G + (|G|^2/2 - E) p_G, the plane's partial sums
-//      <C_v|Ap>, <C_v|p> and p^H Ap
-//   E  per (column, 1024 entries): coef = sum of the plane partials,
-//      p^H P_c A p = p^H A p - sum_v conj(<C_v|p>) coef_v, alpha = r^H K r /
-//      p^H P_c A p, x += alpha p, r -= alpha (Ap - C coef) (P_c on the fly),
-//      partials |r|^2 and r^H K r
-// After E every CTA sums the partials of every column in the same order, so
-// all CTAs take the same convergence decisions without another barrier.
+// state x field) with per-column convergence masks.  The work of an iteration
+// is cut into tasks that the CTAs draw, in one fixed global order, from an
+// atomic ticket counter; a task waits only for the tasks of its own group that
+// it depends on (per-group completion counters; every wait is bounded and, when
+// the bound runs out, sets an error flag on which every CTA returns).  No
+// grid-wide barrier: a group whose columns converge early stops holding the
+// others, and the tasks of different groups overlap.
+//
+// Groups: two columns whose right-hand sides are real in real space
+// (b(-G) = conj b(G), true for real fields at omega = 0) share one complex
+// transform, z = u_1 + i u_2; V(r) is real, so F(V z)(G) = F(V u_1)(G) +
+// i F(V u_2)(G) and each part is recovered from G and -G:
+//   F(V u_1)(G) = (Y(G) + conj Y(-G)) / 2,  F(V u_2)(G) = (Y(G) - conj Y(-G)) / 2i.
+// The vectors of such a pair stay exactly Hermitian-symmetric in floating
+// point (the right-hand side is symmetrised on entry, the projector rows are
+// symmetric, every update combines G and -G the same way).  Other columns run
+// one per group.
+//
+// Recurrences: the one-reduction form of preconditioned CG of Chronopoulos and
+// Gear (J. Comput. Appl. Math. 25, 153 (1989)): with u = K r and
+// w = P_c (H - E) u,
+//   gamma = r^H u,  delta = u^H w,  beta = gamma / gamma_prev,
+//   alpha = gamma / (delta - beta gamma / alpha_prev),
+//   p = u + beta p,  s = w + beta s,  x += alpha p,  r -= alpha s,
+// so both inner products of an iteration come out of the one reduction that
+// follows the operator application (K: kinetic preconditioner, 1 without one).
+//
+// Tasks of iteration it for group g (tickets: all A tasks of the iteration,
+// then all B, then all C; group by group):
+//   A (g, plane i0)  sum the group's C records of it - 1 (projector
+//      coefficients, delta) and A partials (gamma, |r|^2) in plane order,
+//      decide per column (the same bits in every A task of the group), update
+//      x, r, p, s on the plane's sphere entries, u = K r, the plane's partial
+//      gamma and |r|^2; scatter the packed u, z-IFFT of the disc rows and
+//      y-IFFT of the plane in shared memory, store the plane.
+//      Depends on every C task of the group at it - 1 (none at it = 0, which
+//      sets r = b, x = p = s = 0).
+//   B (g, i1)  x-IFFT, * V(r)/N_g, x-FFT on the (i0, i2) slab.  Depends on the
+//      group's A tasks of it.
+//   C (g, plane)  y-FFT, z-FFT of the disc rows, gather Y = F(V z) on the
+//      plane's entries, and the plane's record: <C_v|Y>, <C_v|kin u_c>,
+//      <C_v|u_c>, u_c^H Y, sum kin |u_c|^2, sum |u_c|^2.  Depends on the
+//      group's B tasks of it.
+// Data read across CTAs goes through L2 (ld.global.cg).
 #include <algorithm>
 #include <cstdio>
 
@@ -34,6 +60,7 @@
 namespace gw {
 
 constexpr int kPT = 256;        // threads per CTA
+constexpr int kCtlHead = 4;     // control words: ticket, groups done, error flag, unused
 
 template <typename T>
 struct PcgArgs {
@@ -43,118 +70,668 @@ struct PcgArgs {
   const T* kin;
   const T* vloc_s;
   const cpx<T>* C;
-  int nocc, npw, ncol, nchunk, chunk;   // phases 0 and E: nchunk tasks of chunk entries per column
+  int nocc, npw, ncol, ngrp, W, maxplane;
   const double2* b64;
   const int* outer_active;
-  const double2* E;
+  const double2* E;           // per-column shift (real)
   const double* rr_abs;
+  const double* tk;           // per-column T_ref of the kinetic preconditioner, or null (none)
   double tol_in2;
   int maxit;
   cpx<T>* x;
   cpx<T>* r;
   cpx<T>* p;
-  cpx<T>* Ap;
-  cpx<T>* grid;
-  double2* dpart;   // [ncol][nplanes][2 nocc + 1] plane partial sums
-  double* ppart;    // [ncol][nchunk]: entry 0 of a column holds p^H P_c A p
-  double* rpart;    // [ncol][nchunk]
-  double* zpart;    // [ncol][nchunk] partial r^H K r
-  const double* tk; // per-column T_ref of the kinetic preconditioner, or null (none)
-  unsigned* bar;
-  int* err;
+  cpx<T>* s;
+  cpx<T>* Y;                  // [ngrp][npw]
+  cpx<T>* grid;               // [ngrp][N3]
+  unsigned char* rec;         // [ngrp][nplanes] records of the C tasks
+  size_t rec_bytes;
+  double* apart;              // [2][ngrp][nplanes][W][2] partial gamma, |r|^2 of the A tasks
+  PcgCol* cst;                // [2][ncol] column state, by iteration parity
+  unsigned* ctl;              // kCtlHead words, then per group: count A, count B, count C, done + 1
   int* iters_out;
   int* flag_out;
   double* rr_out;
-  unsigned long long* ptime;   // optional [16] phase timing (see the kernel)
-  unsigned long long spin_limit;   // spins of one barrier wait before the error flag is set
+  unsigned long long spin_limit;
 };
 
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned nblk,
-                                             unsigned long long limit) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned old = atomicAdd(bar, 1u);
-    const unsigned target = (old / nblk + 1u) * nblk;
-    unsigned long long spins = 0;
-    int good = 1;
-    while (*(volatile unsigned*)bar < target) {
-      if (*(volatile int*)err) { good = 0; break; }
-      if (++spins > limit) { atomicExch(err, 1); good = 0; break; }
-      __nanosleep(64);
-    }
-    __threadfence();
-    ok = good;
-  }
-  __syncthreads();
-  return ok != 0;
+template <typename V> __device__ __forceinline__ V ldcg(const V* p);
+template <> __device__ __forceinline__ float2 ldcg<float2>(const float2* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ double2 ldcg<double2>(const double2* p) { return __ldcg(p); }
+
+// Column state written by another CTA: read through L2.
+__device__ __forceinline__ PcgCol ld_col(const PcgCol* p) {
+  PcgCol c;
+  c.gam = __ldcg(&p->gam);
+  c.alpha = __ldcg(&p->alpha);
+  c.stop = __ldcg(&p->stop);
+  c.rmin = __ldcg(&p->rmin);
+  c.rbest = __ldcg(&p->rbest);
+  c.it = __ldcg(&p->it);
+  c.itb = __ldcg(&p->itb);
+  c.active = __ldcg(&p->active);
+  c.flag = __ldcg(&p->flag);
+  return c;
 }
 
-template <typename T>
-__device__ __forceinline__ double dsum_block(double v, double* sh) {
-  return dsum_block_f(v, sh);
-}
-
-// Copies n elements (e = 0..n-1, strided over the block) with U loads in
-// flight per thread: every load of a round is issued before the first store.
-constexpr int kLd = 4;
-template <int U, typename X, typename Ld, typename St>
-__device__ __forceinline__ void staged_copy(int n, Ld ld, St st) {
-  for (int e0 = threadIdx.x; e0 < n; e0 += U * (int)blockDim.x) {
-    X t[U];
+// Sums over the block of NV values per thread, in FP64 (the NV sums land in
+// out[0 .. NV), visible to every thread after the call).
+template <int NV>
+__device__ __forceinline__ void block_sum_n(double (&v)[NV], double* sh, double* out) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * (int)blockDim.x;
-      if (e < n) t[u] = ld(e);
-    }
+  for (int k = 0; k < NV; ++k)
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0)
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * (int)blockDim.x;
-      if (e < n) st(e, t[u]);
-    }
-  }
-}
-
-// Per column c: s[c] = sum of rp[c][0 .. n), z[c] = sum of zp[c][0 .. n), one
-// warp per column (lane l adds records l, l + 32, ... in order, then a fixed
-// shuffle tree; lane 0's value is kept), so that every CTA gets the same bits.
-__device__ __forceinline__ void column_sums(const double* __restrict__ rp, const double* __restrict__ zp, int n,
-                                            int ncol, double* s, double* z) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int c = warp; c < ncol; c += nw) {
-    double a = 0.0, b = 0.0;
-    for (int k = lane; k < n; k += 32) {
-      a += rp[(size_t)c * n + k];
-      b += zp[(size_t)c * n + k];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, o);
-      b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    if (lane == 0) { s[c] = a; z[c] = b; }
+    for (int k = 0; k < NV; ++k) sh[k * 8 + w] = v[k];
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double t = 0.0;
+    for (int q = 0; q < nw; ++q) t += sh[threadIdx.x * 8 + q];
+    out[threadIdx.x] = t;
   }
   __syncthreads();
 }
 
 struct PcgLayout {
-  size_t dbl, ints, red, coef, tv, tw, A, B, total;
+  size_t A, B, U, tw, rowmap, red, S, coef, dsum, col, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline PcgLayout pcg_layout(int N, int ncol, int nocc, int vsize) {
+// Shared memory of one CTA: two FFT tiles N x (N+1), the plane's u_c (C
+// tasks), twiddles, the row map of a plane's disc pencils, reduction scratch,
+// the summed records, the group's projector coefficients and <C_v|u_c> (A
+// tasks), FP64 sums, and per-column scalars.
+__host__ __device__ inline PcgLayout pcg_layout(int N, int nocc, int W, int maxplane, int vsize) {
   PcgLayout L;
-  L.dbl = 0;
-  L.ints = align16(L.dbl + (size_t)8 * ncol * sizeof(double));
-  L.red = align16(L.ints + (size_t)(4 * ncol + N) * sizeof(int));
-  L.coef = align16(L.red + 32 * sizeof(double));
-  L.tv = align16(L.coef + (size_t)(2 * nocc + 1) * 2 * sizeof(double));
-  L.tw = align16(L.tv + align16((size_t)(ncol + 1) * (vsize / 2)) + (size_t)2 * nocc * vsize);
-  L.A = align16(L.tw + (size_t)N * vsize);
+  L.A = 0;
   L.B = align16(L.A + (size_t)N * (N + 1) * vsize);
-  L.total = align16(L.B + (size_t)N * (N + 1) * vsize);
+  L.U = align16(L.B + (size_t)N * (N + 1) * vsize);
+  L.tw = align16(L.U + (size_t)W * maxplane * vsize);
+  L.rowmap = align16(L.tw + (size_t)N * vsize);
+  L.red = align16(L.rowmap + (size_t)N * sizeof(int));
+  L.S = align16(L.red + 8 * 8 * sizeof(double));
+  L.coef = align16(L.S + (size_t)(1 + 2 * W) * nocc * vsize);
+  L.dsum = align16(L.coef + (size_t)2 * W * nocc * vsize);
+  L.col = align16(L.dsum + 24 * sizeof(double));
+  L.total = align16(L.col + 2 * 8 * sizeof(double));
   return L;
+}
+
+// Record of one (group, plane) C task:
+//   V [nocc]        D_v   = sum conj(C_v) Y
+//   V [W][nocc]     K_c,v = sum conj(C_v) kin u_c
+//   V [W][nocc]     U_c,v = sum conj(C_v) u_c
+//   double [W][4]   Re, Im of u_c^H Y, sum kin |u_c|^2, sum |u_c|^2
+__host__ __device__ inline size_t pcg_rec_bytes(int nocc, int W, int vsize) {
+  return align16((size_t)(1 + 2 * W) * nocc * vsize) + (size_t)32 * W;
+}
+
+// Bounded wait of thread 0 for cnt >= target.  Returns 0 to run the task, 1 to
+// skip it (the group finished at an A task of iteration done1 - 1 with
+// done1 <= skip_le), 2 on error (the bound ran out here or elsewhere).
+__device__ __forceinline__ int wait_dep(const unsigned* cnt, unsigned target, const unsigned* done1, unsigned skip_le,
+                                        unsigned* ctl, unsigned long long limit) {
+  unsigned long long spins = 0;
+  while (true) {
+    const unsigned d = *(volatile const unsigned*)done1;
+    if (d != 0u && d <= skip_le) return 1;
+    if (*(volatile const unsigned*)cnt >= target) break;
+    if (*(volatile unsigned*)&ctl[2]) return 2;
+    if (++spins > limit) { atomicExch(&ctl[2], 1u); return 2; }
+    __nanosleep(32);
+  }
+  __threadfence();
+  const unsigned d = *(volatile const unsigned*)done1;
+  return (d != 0u && d <= skip_le) ? 1 : 0;
+}
+
+// Completion of a task: every thread's writes fenced, then one count.
+__device__ __forceinline__ void signal_done(unsigned* cnt) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(cnt, 1u);
+}
+
+// ---------------------------------------------------------------------------
+// A task
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned char* sm, const PcgLayout& L,
+                       int* s_ctl) {
+  using V = cpx<T>;
+  const Geometry& g = a.g;
+  const int N = g.N, LDp = N + 1, P = g.nplanes, W = a.W, nocc = a.nocc;
+  const int c0 = gi * W, nc = min(W, a.ncol - c0);
+  unsigned* gc = a.ctl + kCtlHead + 4 * gi;
+  V* Ab = reinterpret_cast<V*>(sm + L.A);
+  V* Bb = reinterpret_cast<V*>(sm + L.B);
+  const V* stw = reinterpret_cast<const V*>(sm + L.tw);
+  int* rowmap = reinterpret_cast<int*>(sm + L.rowmap);
+  double* red = reinterpret_cast<double*>(sm + L.red);
+  V* Ssum = reinterpret_cast<V*>(sm + L.S);            // the records' projector sums over planes
+  V* coefT = reinterpret_cast<V*>(sm + L.coef);        // [W][nocc] coefficients, then [W][nocc] <C_v|u_c>
+  double* dsum = reinterpret_cast<double*>(sm + L.dsum);
+  double* colv = reinterpret_cast<double*>(sm + L.col);   // [c * 8 + k]: alpha, beta, active, E, rtk
+  if (threadIdx.x == 0) {
+    int w = 0;
+    if (it > 0) w = wait_dep(gc + 2, (unsigned)(it * P), gc + 3, (unsigned)it, a.ctl, a.spin_limit);
+    s_ctl[0] = w;
+  }
+  __syncthreads();
+  if (s_ctl[0] == 2) return;
+  if (s_ctl[0] == 1) return;           // the group finished earlier: nothing left to do
+  const int i0 = g.planes[pi];
+  const int s0 = g.plane_sph[pi], s1 = g.plane_sph[pi + 1];
+  const int q0 = g.plane_pen[pi], npp = g.plane_pen[pi + 1] - q0;
+  const int ns = s1 - s0;
+  const size_t rb = a.rec_bytes;
+  const int nv = (1 + 2 * W) * nocc;
+
+  // ---- column scalars
+  if (it == 0) {
+    for (int c = threadIdx.x; c < W; c += blockDim.x) {
+      const bool present = c < nc;
+      colv[c * 8 + 0] = 0.0;
+      colv[c * 8 + 1] = 0.0;
+      colv[c * 8 + 2] = present ? 1.0 : 0.0;
+      colv[c * 8 + 3] = present ? a.E[c0 + c].x : 0.0;
+      colv[c * 8 + 4] = (present && a.tk) ? 1.0 / a.tk[c0 + c] : 0.0;
+    }
+  } else {
+    // stage the group's P records (shared-memory tiles A and B) when they fit
+    const unsigned char* src = a.rec + (size_t)gi * P * rb;
+    const size_t nb16 = (size_t)P * rb / 16;
+    const bool staged = nb16 * 16 <= L.U - L.A;
+    const unsigned char* stg = staged ? sm + L.A : src;
+    if (staged) {
+      const float4* s4 = reinterpret_cast<const float4*>(src);
+      float4* d4 = reinterpret_cast<float4*>(sm + L.A);
+      for (size_t e = threadIdx.x; e < nb16; e += blockDim.x) d4[e] = __ldcg(s4 + e);
+    }
+    __syncthreads();
+    // projector sums in T, plane order: value j of every record
+    const size_t dbase = align16((size_t)nv * sizeof(V));
+    for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+      T sx = 0, sy = 0;
+      for (int q = 0; q < P; ++q) {
+        const V v = staged ? reinterpret_cast<const V*>(stg + (size_t)q * rb)[j]
+                           : ldcg(reinterpret_cast<const V*>(stg + (size_t)q * rb) + j);
+        sx += v.x;
+        sy += v.y;
+      }
+      Ssum[j] = mk<T>(sx, sy);
+    }
+    __syncthreads();
+    // FP64 sums: per column Re/Im u^H Y, kin|u|^2, |u|^2 (records) and gamma, |r|^2 (A partials)
+    const double* ap = a.apart + ((size_t)((it - 1) & 1) * a.ngrp + gi) * P * W * 2;
+    for (int j = threadIdx.x; j < 6 * W; j += blockDim.x) {
+      double t = 0.0;
+      if (j < 4 * W) {
+        for (int q = 0; q < P; ++q) {
+          const double* d = reinterpret_cast<const double*>(stg + (size_t)q * rb + dbase);
+          t += staged ? d[j] : __ldcg(d + j);
+        }
+      } else {
+        const int k = j - 4 * W;        // c * 2 + (0 gamma, 1 |r|^2)
+        for (int q = 0; q < P; ++q) t += __ldcg(ap + (size_t)q * W * 2 + k);
+      }
+      dsum[j] = t;
+    }
+    __syncthreads();
+    // coefficients per column c: coef_v = FV_c,v + K_c,v - E_c U_c,v, with
+    // FV = Re D (c = 0) or Im D (c = 1) for a packed pair (real: taken real), D otherwise
+    for (int j = threadIdx.x; j < W * nocc; j += blockDim.x) {
+      const int c = j / nocc, v = j - c * nocc;
+      const T Ec = (T)((c < nc) ? a.E[c0 + c].x : 0.0);
+      const V D = Ssum[v], K = Ssum[(1 + c) * nocc + v], U = Ssum[(1 + W + c) * nocc + v];
+      V cf;
+      if (W == 2) {
+        const T fv = (c == 0) ? D.x : D.y;
+        cf = mk<T>(fv + K.x - Ec * U.x, (T)0);
+      } else {
+        cf = mk<T>(D.x + K.x - Ec * U.x, D.y + K.y - Ec * U.y);
+      }
+      coefT[j] = cf;
+      coefT[W * nocc + j] = U;
+    }
+    __syncthreads();
+    // delta correction sum_v Re(conj(U_v) coef_v), one warp per column
+    {
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      if (warp < W) {
+        double t = 0.0;
+        for (int v = lane; v < nocc; v += 32) {
+          const V cf = coefT[warp * nocc + v], U = coefT[W * nocc + warp * nocc + v];
+          t += (double)(U.x * cf.x + U.y * cf.y);
+        }
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) red[warp] = t;
+      }
+    }
+    __syncthreads();
+    // decisions (thread c for column c; identical in every A task of the group)
+    if (threadIdx.x < W) {
+      const int c = threadIdx.x;
+      double* cv = colv + c * 8;
+      cv[2] = 0.0;
+      if (c < nc) {
+        const int col = c0 + c;
+        const double Ec = a.E[col].x;
+        const double uY = (W == 2) ? dsum[c * 4 + ((c == 0) ? 0 : 1)] : dsum[c * 4];
+        const double delta = uY + dsum[c * 4 + 2] - Ec * dsum[c * 4 + 3] - red[c];
+        const double gam = dsum[4 * W + c * 2], rr = dsum[4 * W + c * 2 + 1];
+        PcgCol st;
+        if (it == 1) {
+          const bool on = !a.outer_active || a.outer_active[col];
+          st.gam = 0.0;
+          st.alpha = 0.0;
+          st.stop = fmax(a.tol_in2 * rr, a.rr_abs ? a.rr_abs[col] : 0.0);
+          st.rmin = rr;
+          st.rbest = rr;
+          st.it = 0;
+          st.itb = 0;
+          st.active = (on && rr > 0.0) ? 1 : 0;
+          st.flag = 0;
+          if (!st.active) st.flag = 0;
+        } else {
+          st = ld_col(a.cst + (size_t)((it - 1) & 1) * a.ncol + col);
+        }
+        const bool was = st.active != 0;
+        if (st.active) {
+          const int itc = it - 1;               // updates done so far
+          st.rmin = fmin(st.rmin, rr);
+          if (rr < 0.25 * st.rbest) { st.rbest = rr; st.itb = itc; }
+          int stop = 0;
+          if (!isfinite(rr)) { st.flag = 2; stop = 1; }
+          else if (rr <= st.stop) { st.flag = 0; stop = 1; }
+          else if (rr > 1e4 * st.rmin) { st.flag = 3; stop = 1; }
+          else if (itc >= a.maxit) { st.flag = 1; stop = 1; }
+          else if (itc - st.itb > max(kCgStagWindow, 2 * st.itb)) { st.flag = 4; stop = 1; }
+          double al = 0.0, bt = 0.0;
+          if (!stop) {
+            double den = delta;
+            if (it > 1) {
+              bt = gam / st.gam;
+              den = delta - bt * gam / st.alpha;
+            }
+            if (!(den > 0.0) || !isfinite(den) || !(gam > 0.0)) { st.flag = 2; stop = 1; }
+            else al = gam / den;
+          }
+          st.it = itc;
+          if (stop) {
+            st.active = 0;
+          } else {
+            st.gam = gam;
+            st.alpha = al;
+            cv[0] = al;
+            cv[1] = bt;
+            cv[2] = 1.0;
+          }
+        }
+        cv[3] = Ec;
+        cv[4] = a.tk ? 1.0 / a.tk[col] : 0.0;
+        if (pi == 0) {
+          a.cst[(size_t)(it & 1) * a.ncol + col] = st;
+          if (!st.active && (was || it == 1)) {
+            a.iters_out[col] = st.it;
+            a.flag_out[col] = st.flag;
+            a.rr_out[col] = rr;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // group finished: mark it (plane-0 task) and stop here
+    {
+      int any = 0;
+      for (int c = 0; c < W; ++c) any |= (colv[c * 8 + 2] != 0.0);
+      if (!any) {
+        if (pi == 0 && threadIdx.x == 0) {
+          __threadfence();
+          atomicExch(gc + 3, (unsigned)(it + 1));
+          atomicAdd(&a.ctl[1], 1u);
+        }
+        signal_done(gc + 0);
+        return;
+      }
+    }
+  }
+
+  // ---- update the plane's entries and scatter the packed u = K r
+  for (int e = threadIdx.x; e < npp * LDp; e += blockDim.x) Ab[e] = mk<T>(0, 0);
+  for (int k = threadIdx.x; k < N; k += blockDim.x) rowmap[k] = -1;
+  __syncthreads();
+  for (int k = threadIdx.x; k < npp; k += blockDim.x) rowmap[g.pencils[q0 + k].y] = k;
+  T gacc[2] = {0, 0}, racc[2] = {0, 0};
+  T c_al[2], c_bt[2], c_E[2], c_rtk[2];
+  bool c_act[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int cc = (c < W) ? c : 0;
+    c_al[c] = (T)colv[cc * 8 + 0];
+    c_bt[c] = (T)colv[cc * 8 + 1];
+    c_act[c] = (c < W) && colv[cc * 8 + 2] != 0.0;
+    c_E[c] = (T)colv[cc * 8 + 3];
+    c_rtk[c] = (T)colv[cc * 8 + 4];
+  }
+  const V* Yg = a.Y + (size_t)gi * a.npw;
+  for (int e = threadIdx.x; e < ns; e += blockDim.x) {
+    const int G = s0 + e;
+    const T kinG = a.kin[G];
+    V z = mk<T>(0, 0);
+    if (it == 0) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (c >= nc) break;
+        const int col = c0 + c;
+        const size_t i = (size_t)col * a.npw + G;
+        const bool on = !a.outer_active || a.outer_active[col];
+        double2 b = on ? a.b64[i] : make_double2(0.0, 0.0);
+        if (W == 2 && on) {
+          const double2 bn = a.b64[(size_t)col * a.npw + g.sph_neg[G]];
+          b = make_double2(0.5 * (b.x + bn.x), 0.5 * (b.y - bn.y));
+        }
+        const V rv = from_d<T>(b);
+        a.r[i] = rv;
+        a.x[i] = mk<T>(0, 0);
+        a.p[i] = mk<T>(0, 0);
+        a.s[i] = mk<T>(0, 0);
+        const T rtk = c_rtk[c];
+        const T K = (rtk != (T)0) ? tpa<T>(kinG * rtk) : (T)1;
+        const V u = mk<T>(K * rv.x, K * rv.y);
+        const T n2 = rv.x * rv.x + rv.y * rv.y;
+        racc[c] += n2;
+        gacc[c] += K * n2;
+        if (W == 2 && c == 1) z = mk<T>(z.x - u.y, z.y + u.x);
+        else z = mk<T>(z.x + u.x, z.y + u.y);
+      }
+    } else {
+      const V y1 = ldcg(Yg + G);
+      V y2 = ldcg(Yg + g.sph_neg[G]);
+      y2.y = -y2.y;                                   // conj Y(-G)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (c >= nc || !c_act[c]) continue;
+        const int col = c0 + c;
+        const size_t i = (size_t)col * a.npw + G;
+        const T al = c_al[c], bt = c_bt[c], Ec = c_E[c];
+        const T rtk = c_rtk[c];
+        const T K = (rtk != (T)0) ? tpa<T>(kinG * rtk) : (T)1;
+        V rv = ldcg(a.r + i), pv = ldcg(a.p + i), sv = ldcg(a.s + i), xv = ldcg(a.x + i);
+        const V u = mk<T>(K * rv.x, K * rv.y);
+        V fv;
+        if (W == 2) {
+          if (c == 0) fv = mk<T>((T)0.5 * (y1.x + y2.x), (T)0.5 * (y1.y + y2.y));
+          else fv = mk<T>((T)0.5 * (y1.y - y2.y), (T)-0.5 * (y1.x - y2.x));
+        } else {
+          fv = y1;
+        }
+        const T kd = kinG - Ec;
+        V w = mk<T>(fv.x + kd * u.x, fv.y + kd * u.y);
+        const V* cf = coefT + c * nocc;
+        int v = 0;
+        for (; v + 4 <= nocc; v += 4) {
+          V cv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cv[q] = a.C[(size_t)(v + q) * a.npw + G];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const V k = cf[v + q];
+            w.x -= cv[q].x * k.x - cv[q].y * k.y;
+            w.y -= cv[q].x * k.y + cv[q].y * k.x;
+          }
+        }
+        for (; v < nocc; ++v) {
+          const V cv = a.C[(size_t)v * a.npw + G];
+          const V k = cf[v];
+          w.x -= cv.x * k.x - cv.y * k.y;
+          w.y -= cv.x * k.y + cv.y * k.x;
+        }
+        pv = mk<T>(u.x + bt * pv.x, u.y + bt * pv.y);
+        sv = mk<T>(w.x + bt * sv.x, w.y + bt * sv.y);
+        xv = mk<T>(xv.x + al * pv.x, xv.y + al * pv.y);
+        rv = mk<T>(rv.x - al * sv.x, rv.y - al * sv.y);
+        a.p[i] = pv;
+        a.s[i] = sv;
+        a.x[i] = xv;
+        a.r[i] = rv;
+        const V un = mk<T>(K * rv.x, K * rv.y);
+        const T n2 = rv.x * rv.x + rv.y * rv.y;
+        racc[c] += n2;
+        gacc[c] += K * n2;
+        if (W == 2 && c == 1) z = mk<T>(z.x - un.y, z.y + un.x);
+        else z = mk<T>(z.x + un.x, z.y + un.y);
+      }
+    }
+    Ab[(g.sph_pen[G] - q0) * LDp + g.sph_i2[G]] = z;
+  }
+  {
+    double v4[4] = {(double)gacc[0], (double)racc[0], (double)gacc[1], (double)racc[1]};
+    block_sum_n<4>(v4, red, dsum + 16);
+    if (threadIdx.x < 2 * W) {
+      double* ap = a.apart + (((size_t)(it & 1) * a.ngrp + gi) * P + pi) * W * 2;
+      ap[threadIdx.x] = dsum[16 + threadIdx.x];
+    }
+  }
+  __syncthreads();
+  // ---- z-IFFT of the disc rows, transpose into the plane, y-IFFT, store
+  V* R = fft_tile2<T, +1, false>(Ab, Bb, npp, LDp, 1, a.pl, stw);
+  V* Q = (R == Ab) ? Bb : Ab;
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int i1 = a.pl.dN.div(e), i2 = e - i1 * N;
+    const int k = rowmap[i1];
+    Q[i1 * LDp + i2] = (k >= 0) ? R[k * LDp + i2] : mk<T>(0, 0);
+  }
+  __syncthreads();
+  V* S = fft_tile2<T, +1, true>(Q, R, N, 1, LDp, a.pl, stw);
+  const size_t base = (size_t)gi * g.N3 + (size_t)i0 * g.N2;
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int i1 = a.pl.dN.div(e), i2 = e - i1 * N;
+    a.grid[base + e] = S[i1 * LDp + i2];
+  }
+  signal_done(gc + 0);
+}
+
+// ---------------------------------------------------------------------------
+// B task: x-IFFT, * V / N_g, x-FFT on the (group, i1) slab: pencils along i0
+// for every i2, element (i0, i2) at tile[i0 * LDp + i2]
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void task_B(const PcgArgs<T>& a, int it, int gi, int i1, unsigned char* sm, const PcgLayout& L,
+                       int* s_ctl) {
+  using V = cpx<T>;
+  const Geometry& g = a.g;
+  const int N = g.N, LDp = N + 1, P = g.nplanes;
+  unsigned* gc = a.ctl + kCtlHead + 4 * gi;
+  V* Ab = reinterpret_cast<V*>(sm + L.A);
+  V* Bb = reinterpret_cast<V*>(sm + L.B);
+  const V* stw = reinterpret_cast<const V*>(sm + L.tw);
+  if (threadIdx.x == 0)
+    s_ctl[0] = wait_dep(gc + 0, (unsigned)((it + 1) * P), gc + 3, (unsigned)(it + 1), a.ctl, a.spin_limit);
+  __syncthreads();
+  if (s_ctl[0] != 0) return;
+  const size_t base = (size_t)gi * g.N3 + (size_t)i1 * N;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int i0 = a.pl.dN.div(e), i2 = e - i0 * N;
+    Ab[i0 * LDp + i2] = g.plane_mask[i0] ? ldcg(a.grid + base + (size_t)i0 * g.N2 + i2) : mk<T>(0, 0);
+  }
+  __syncthreads();
+  V* R = fft_tile2<T, +1, true>(Ab, Bb, N, 1, LDp, a.pl, stw);
+  V* Q = (R == Ab) ? Bb : Ab;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int i0 = a.pl.dN.div(e), i2 = e - i0 * N;
+    const T m = a.vloc_s[(size_t)i0 * g.N2 + (size_t)i1 * N + i2];
+    const V v = R[i0 * LDp + i2];
+    R[i0 * LDp + i2] = mk<T>(v.x * m, v.y * m);
+  }
+  __syncthreads();
+  V* S = fft_tile2<T, -1, true>(R, Q, N, 1, LDp, a.pl, stw);
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int i0 = a.pl.dN.div(e), i2 = e - i0 * N;
+    if (g.plane_mask[i0]) a.grid[base + (size_t)i0 * g.N2 + i2] = S[i0 * LDp + i2];
+  }
+  signal_done(gc + 1);
+}
+
+// ---------------------------------------------------------------------------
+// C task: y-FFT, z-FFT of the disc rows, gather Y, the plane's record
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned char* sm, const PcgLayout& L,
+                       int* s_ctl) {
+  using V = cpx<T>;
+  const Geometry& g = a.g;
+  const int N = g.N, LDp = N + 1, W = a.W, nocc = a.nocc;
+  const int c0 = gi * W, nc = min(W, a.ncol - c0);
+  unsigned* gc = a.ctl + kCtlHead + 4 * gi;
+  V* Ab = reinterpret_cast<V*>(sm + L.A);
+  V* Bb = reinterpret_cast<V*>(sm + L.B);
+  V* Us = reinterpret_cast<V*>(sm + L.U);          // [W][maxplane] u_c on the plane's entries
+  const V* stw = reinterpret_cast<const V*>(sm + L.tw);
+  double* red = reinterpret_cast<double*>(sm + L.red);
+  double* dsum = reinterpret_cast<double*>(sm + L.dsum);
+  if (threadIdx.x == 0)
+    s_ctl[0] = wait_dep(gc + 1, (unsigned)((it + 1) * N), gc + 3, (unsigned)(it + 1), a.ctl, a.spin_limit);
+  __syncthreads();
+  if (s_ctl[0] != 0) return;
+  const int i0 = g.planes[pi];
+  const int s0 = g.plane_sph[pi], s1 = g.plane_sph[pi + 1];
+  const int q0 = g.plane_pen[pi], npp = g.plane_pen[pi + 1] - q0;
+  const int ns = s1 - s0;
+  const size_t base = (size_t)gi * g.N3 + (size_t)i0 * g.N2;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int i1 = a.pl.dN.div(e), i2 = e - i1 * N;
+    Ab[i1 * LDp + i2] = ldcg(a.grid + base + e);
+  }
+  // u_c = K r_c on the plane's entries (0 for an absent column)
+  T c_rtk[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) c_rtk[c] = (a.tk && c < nc) ? (T)(1.0 / a.tk[c0 + c]) : (T)0;
+  for (int e = threadIdx.x; e < ns; e += blockDim.x) {
+    const int G = s0 + e;
+    const T kinG = a.kin[G];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (c >= W) break;
+      V u = mk<T>(0, 0);
+      if (c < nc) {
+        const int col = c0 + c;
+        const T rtk = c_rtk[c];
+        const T K = (rtk != (T)0) ? tpa<T>(kinG * rtk) : (T)1;
+        const V rv = ldcg(a.r + (size_t)col * a.npw + G);
+        u = mk<T>(K * rv.x, K * rv.y);
+      }
+      Us[c * a.maxplane + e] = u;
+    }
+  }
+  __syncthreads();
+  V* R = fft_tile2<T, -1, true>(Ab, Bb, N, 1, LDp, a.pl, stw);
+  V* Q = (R == Ab) ? Bb : Ab;
+  for (int e = threadIdx.x; e < npp * N; e += blockDim.x) {
+    const int k = a.pl.dN.div(e), i2 = e - k * N;
+    Q[k * LDp + i2] = R[g.pencils[q0 + k].y * LDp + i2];
+  }
+  __syncthreads();
+  V* S = fft_tile2<T, -1, false>(Q, R, npp, LDp, 1, a.pl, stw);
+  V* Wv = (S == Q) ? R : Q;                       // free tile: the plane's Y values
+  V* Yg = a.Y + (size_t)gi * a.npw;
+  for (int e = threadIdx.x; e < ns; e += blockDim.x) {
+    const int s = s0 + e;
+    const V val = S[(g.sph_pen[s] - q0) * LDp + g.sph_i2[s]];
+    Yg[s] = val;
+    Wv[e] = val;
+  }
+  __syncthreads();
+  // ---- the record: projector sums (warp per pair of occupied states, lanes
+  // over entries, eight entries in flight), then the FP64 scalar sums
+  unsigned char* rec = a.rec + ((size_t)gi * g.nplanes + pi) * a.rec_bytes;
+  V* rv = reinterpret_cast<V*>(rec);
+  {
+    constexpr int UE = 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const V* U0 = Us;
+    const V* U1 = Us + a.maxplane;
+    for (int v = warp; v < nocc; v += nw) {
+      const V* Cv = a.C + (size_t)v * a.npw + s0;
+      T acc[10];
+#pragma unroll
+      for (int k = 0; k < 10; ++k) acc[k] = (T)0;
+      for (int e0 = lane; e0 < ns; e0 += 32 * UE) {
+        V cv[UE];
+#pragma unroll
+        for (int u = 0; u < UE; ++u) {
+          const int e = e0 + 32 * u;
+          cv[u] = (e < ns) ? Cv[e] : mk<T>(0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < UE; ++u) {
+          const int e = e0 + 32 * u;
+          if (e < ns) {
+            const V y = Wv[e];
+            const T kk = a.kin[s0 + e];
+            const V c = cv[u];
+            acc[0] += c.x * y.x + c.y * y.y;            // conj(C) Y
+            acc[1] += c.x * y.y - c.y * y.x;
+            const V u0 = U0[e];
+            acc[2] += kk * (c.x * u0.x + c.y * u0.y);   // conj(C) kin u_0
+            acc[3] += kk * (c.x * u0.y - c.y * u0.x);
+            acc[4] += c.x * u0.x + c.y * u0.y;          // conj(C) u_0
+            acc[5] += c.x * u0.y - c.y * u0.x;
+            if (W == 2) {
+              const V u1 = U1[e];
+              acc[6] += kk * (c.x * u1.x + c.y * u1.y);
+              acc[7] += kk * (c.x * u1.y - c.y * u1.x);
+              acc[8] += c.x * u1.x + c.y * u1.y;
+              acc[9] += c.x * u1.y - c.y * u1.x;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 10; ++k)
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+      if (lane == 0) {
+        rv[v] = mk<T>(acc[0], acc[1]);
+        rv[(1 + 0) * nocc + v] = mk<T>(acc[2], acc[3]);
+        rv[(1 + W + 0) * nocc + v] = mk<T>(acc[4], acc[5]);
+        if (W == 2) {
+          rv[(1 + 1) * nocc + v] = mk<T>(acc[6], acc[7]);
+          rv[(1 + W + 1) * nocc + v] = mk<T>(acc[8], acc[9]);
+        }
+      }
+    }
+  }
+  {
+    T t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int e = threadIdx.x; e < ns; e += blockDim.x) {
+      const V y = Wv[e];
+      const T kk = a.kin[s0 + e];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (c >= W) break;
+        const V u = Us[c * a.maxplane + e];
+        t[c * 4 + 0] += u.x * y.x + u.y * y.y;        // conj(u) Y
+        t[c * 4 + 1] += u.x * y.y - u.y * y.x;
+        const T n2 = u.x * u.x + u.y * u.y;
+        t[c * 4 + 2] += kk * n2;
+        t[c * 4 + 3] += n2;
+      }
+    }
+    double v8[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v8[k] = (double)t[k];
+    block_sum_n<8>(v8, red, dsum);
+    double* rd = reinterpret_cast<double*>(rec + align16((size_t)(1 + 2 * W) * nocc * sizeof(V)));
+    if (threadIdx.x < 4 * W) rd[threadIdx.x] = dsum[threadIdx.x];
+  }
+  signal_done(gc + 2);
 }
 
 template <typename T>
@@ -162,387 +739,77 @@ __global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
   using V = cpx<T>;
   extern __shared__ unsigned char smem_raw[];
   const Geometry& g = a.g;
-  const int N = g.N, LDp = N + 1;
-  const int ncol = a.ncol;
-  // ---- shared memory: column state, then the FFT work area (offsets: pcg_layout)
-  const PcgLayout L = pcg_layout(N, ncol, a.nocc, (int)sizeof(V));
-  double* st_rr = reinterpret_cast<double*>(smem_raw + L.dbl);
-  double* st_min = st_rr + ncol;
-  double* st_stop = st_min + ncol;
-  double* st_beta = st_stop + ncol;
-  double* st_rz = st_beta + ncol;                             // r^H K r
-  double* st_best = st_rz + ncol;                             // stagnation guard
-  double* st_s = st_best + ncol;                              // this iteration's |r|^2 and r^H K r
-  double* st_z = st_s + ncol;
-  int* st_act = reinterpret_cast<int*>(smem_raw + L.ints);
-  int* st_it = st_act + ncol;
-  int* st_flag = st_it + ncol;
-  int* st_itb = st_flag + ncol;
-  int* rowmap = st_itb + ncol;                                // [N]
-  double* red = reinterpret_cast<double*>(smem_raw + L.red);  // [32] block sums
-  double2* coef = reinterpret_cast<double2*>(smem_raw + L.coef);  // [2 nocc + 1] plane sums
-  T* st_rtk = reinterpret_cast<T*>(smem_raw + L.tv);          // [ncol] 1 / T_ref (0: no preconditioner)
-  T* s_al = st_rtk + ncol;                                    // alpha of the current column
-  V* coefT = reinterpret_cast<V*>(smem_raw + L.tv + align16((size_t)(ncol + 1) * sizeof(T)));   // [2 nocc]
-  T* redT = reinterpret_cast<T*>(red);
-  V* stw = reinterpret_cast<V*>(smem_raw + L.tw);             // [N]
-  V* A = reinterpret_cast<V*>(smem_raw + L.A);                // [N][LDp]
-  V* B = reinterpret_cast<V*>(smem_raw + L.B);                // [N][LDp]
-  __shared__ double bcast;
-
+  const int N = g.N, P = g.nplanes;
+  const PcgLayout L = pcg_layout(N, a.nocc, a.W, a.maxplane, (int)sizeof(V));
+  __shared__ int s_task[4];
+  __shared__ int s_ctl[2];
+  V* stw = reinterpret_cast<V*>(smem_raw + L.tw);
   for (int k = threadIdx.x; k < N; k += blockDim.x) stw[k] = a.tw[k];
-  for (int c = threadIdx.x; c < ncol; c += blockDim.x) st_rtk[c] = a.tk ? (T)1 / (T)a.tk[c] : (T)0;
   __syncthreads();
-  const unsigned nblk = gridDim.x;
-  const int npl = g.nplanes;
-
-  // ---- phase 0: r = b, x = 0, partial |b|^2
-  for (int task = blockIdx.x; task < ncol * a.nchunk; task += gridDim.x) {
-    const int c = task / a.nchunk, ch = task - c * a.nchunk;
-    const bool on = !a.outer_active || a.outer_active[c];
-    const int g0 = ch * a.chunk, g1 = min(a.npw, g0 + a.chunk);
-    const T rtk = st_rtk[c];
-    T acc = 0, accz = 0;
-    for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
-      const size_t i = (size_t)c * a.npw + G;
-      const V bv = on ? from_d<T>(a.b64[i]) : mk<T>(0, 0);
-      a.r[i] = bv;
-      a.x[i] = mk<T>(0, 0);
-      const T n2 = bv.x * bv.x + bv.y * bv.y;
-      acc += n2;
-      accz += (rtk != (T)0 ? tpa<T>(a.kin[G] * rtk) : (T)1) * n2;
-    }
-    acc = tsum_block<T>(acc, redT);
-    if (threadIdx.x == 0) a.rpart[(size_t)c * a.nchunk + ch] = (double)acc;
-    accz = tsum_block<T>(accz, redT);
-    if (threadIdx.x == 0) a.zpart[(size_t)c * a.nchunk + ch] = (double)accz;
-  }
-  if (!grid_barrier(a.bar, a.err, nblk, a.spin_limit)) return;
-  column_sums(a.rpart, a.zpart, a.nchunk, ncol, st_s, st_z);
-  for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
-    const double s = st_s[c], z = st_z[c];
-    const bool on = !a.outer_active || a.outer_active[c];
-    st_rr[c] = s;
-    st_rz[c] = z;
-    st_min[c] = s;
-    st_best[c] = s;
-    st_itb[c] = 0;
-    st_stop[c] = fmax(a.tol_in2 * s, a.rr_abs ? a.rr_abs[c] : 0.0);
-    st_beta[c] = -1.0;
-    st_act[c] = (on && s > 0.0) ? 1 : 0;
-    st_it[c] = 0;
-    st_flag[c] = 0;
-  }
-  __syncthreads();
-
-  unsigned long long tprev = gtimer(), tphase = tprev;
-  // Optional timing (a.ptime): [ph] wall time of phase ph seen by CTA 0,
-  // [8 + ph] work time of phase ph summed over CTAs (before its barrier).
-  auto work = [&](int ph) {
-    if (a.ptime && threadIdx.x == 0) atomicAdd(&a.ptime[8 + ph], gtimer() - tphase);
-  };
-  auto mark = [&](int ph) {
-    if (a.ptime && threadIdx.x == 0) {
-      const unsigned long long t = gtimer();
-      if (blockIdx.x == 0) a.ptime[ph] += t - tprev;
-      tprev = t;
-      tphase = t;
-    }
-  };
-  for (int it = 0; it < a.maxit; ++it) {
-    int any = 0;
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) any |= st_act[c];
-    if (!__syncthreads_or(any)) break;
-
-    // ---- phase A: p update, scatter, z-IFFT (disc rows), y-IFFT (plane)
-    for (int task = blockIdx.x; task < ncol * npl; task += gridDim.x) {
-      const int c = task / npl, pi = task - c * npl;
-      if (!st_act[c]) continue;
-      const int i0 = g.planes[pi];
-      const int s0 = g.plane_sph[pi], s1 = g.plane_sph[pi + 1];
-      const int q0 = g.plane_pen[pi], npp = g.plane_pen[pi + 1] - q0;
-      const double bt = st_beta[c];
-      const T btT = (T)bt;
-      const T rtk = st_rtk[c];
-      const size_t sc = (size_t)c * a.npw;
-      for (int e = threadIdx.x; e < npp * LDp; e += blockDim.x) A[e] = mk<T>(0, 0);
-      for (int k = threadIdx.x; k < N; k += blockDim.x) rowmap[k] = -1;
-      __syncthreads();
-      for (int k = threadIdx.x; k < npp; k += blockDim.x) rowmap[g.pencils[q0 + k].y] = k;
-      for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-        V rv = a.r[sc + s];
-        if (rtk != (T)0) {                         // z = K r
-          const T k = tpa<T>(a.kin[s] * rtk);
-          rv.x *= k;
-          rv.y *= k;
-        }
-        V val = rv;
-        if (bt >= 0.0) {
-          const V pv = a.p[sc + s];
-          val = mk<T>(rv.x + btT * pv.x, rv.y + btT * pv.y);
-        }
-        a.p[sc + s] = val;
-        A[(g.sph_pen[s] - q0) * LDp + g.sph_i2[s]] = val;
+  const unsigned nA = (unsigned)a.ngrp * P, nB = (unsigned)a.ngrp * N;
+  const unsigned per_it = 2u * nA + nB;
+  while (true) {
+    if (threadIdx.x == 0) {
+      int ph = -1;
+      if (!*(volatile unsigned*)&a.ctl[2] && *(volatile unsigned*)&a.ctl[1] < (unsigned)a.ngrp) {
+        const unsigned t = atomicAdd(&a.ctl[0], 1u);
+        const unsigned it = t / per_it;
+        unsigned rem = t - it * per_it;
+        if (rem < nA) { ph = 0; s_task[2] = rem / P; s_task[3] = rem % P; }
+        else if ((rem -= nA) < nB) { ph = 1; s_task[2] = rem / N; s_task[3] = rem % N; }
+        else { rem -= nB; ph = 2; s_task[2] = rem / P; s_task[3] = rem % P; }
+        s_task[0] = (int)it;
       }
-      __syncthreads();
-      V* R = fft_tile2<T, +1, false>(A, B, npp, LDp, 1, a.pl, stw);
-      V* Q = (R == A) ? B : A;
-      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const int i1 = a.pl.dN.div(e), i2 = e - i1 * N;
-        const int k = rowmap[i1];
-        Q[i1 * LDp + i2] = (k >= 0) ? R[k * LDp + i2] : mk<T>(0, 0);
-      }
-      __syncthreads();
-      V* S = fft_tile2<T, +1, true>(Q, R, N, 1, LDp, a.pl, stw);
-      const size_t base = (size_t)c * g.N3 + (size_t)i0 * g.N2;
-      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const int i1 = a.pl.dN.div(e), i2 = e - i1 * N;
-        a.grid[base + e] = S[i1 * LDp + i2];
-      }
-      __syncthreads();
-    }
-    work(0);
-    if (!grid_barrier(a.bar, a.err, nblk, a.spin_limit)) return;
-    mark(0);
-
-    // ---- phase B: x-IFFT, * V / N_g, x-FFT on (column, i1) slabs: pencils along i0
-    // for every i2, element (i0, i2) at A[i0 * LDp + i2] (consecutive threads take
-    // consecutive i2: coalesced global rows, conflict-free shared accesses)
-    for (int task = blockIdx.x; task < ncol * N; task += gridDim.x) {
-      const int c = task / N, i1 = task - c * N;
-      if (!st_act[c]) continue;
-      const size_t base = (size_t)c * g.N3 + (size_t)i1 * N;
-#pragma unroll 4
-      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const int i0 = a.pl.dN.div(e), i2 = e - i0 * N;
-        A[i0 * LDp + i2] = g.plane_mask[i0] ? a.grid[base + (size_t)i0 * g.N2 + i2] : mk<T>(0, 0);
-      }
-      __syncthreads();
-      V* R = fft_tile2<T, +1, true>(A, B, N, 1, LDp, a.pl, stw);
-      V* Q = (R == A) ? B : A;
-#pragma unroll 4
-      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const int i0 = a.pl.dN.div(e), i2 = e - i0 * N;
-        const T m = a.vloc_s[(size_t)i0 * g.N2 + (size_t)i1 * N + i2];
-        const V v = R[i0 * LDp + i2];
-        R[i0 * LDp + i2] = mk<T>(v.x * m, v.y * m);
-      }
-      __syncthreads();
-      V* S = fft_tile2<T, -1, true>(R, Q, N, 1, LDp, a.pl, stw);
-      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const int i0 = a.pl.dN.div(e), i2 = e - i0 * N;
-        if (g.plane_mask[i0]) a.grid[base + (size_t)i0 * g.N2 + i2] = S[i0 * LDp + i2];
-      }
-      __syncthreads();
-    }
-    work(1);
-    if (!grid_barrier(a.bar, a.err, nblk, a.spin_limit)) return;
-    mark(1);
-
-    // ---- phase C: y-FFT, z-FFT of the disc rows, gather + kinetic + shift, and
-    // the plane's partial sums <C_v|Ap>, <C_v|p> and p^H Ap (Ap before P_c)
-    const size_t rbytes = plane_rec_bytes(a.nocc, (int)sizeof(V));
-    for (int task = blockIdx.x; task < ncol * npl; task += gridDim.x) {
-      const int c = task / npl, pi = task - c * npl;
-      if (!st_act[c]) continue;
-      const int i0 = g.planes[pi];
-      const int s0 = g.plane_sph[pi], s1 = g.plane_sph[pi + 1];
-      const int q0 = g.plane_pen[pi], npp = g.plane_pen[pi + 1] - q0;
-      const size_t sc = (size_t)c * a.npw;
-      const size_t base = (size_t)c * g.N3 + (size_t)i0 * g.N2;
-#pragma unroll 4
-      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const int i1 = a.pl.dN.div(e), i2 = e - i1 * N;
-        A[i1 * LDp + i2] = a.grid[base + e];
-      }
-      __syncthreads();
-      V* R = fft_tile2<T, -1, true>(A, B, N, 1, LDp, a.pl, stw);
-      V* Q = (R == A) ? B : A;
-      for (int e = threadIdx.x; e < npp * N; e += blockDim.x) {
-        const int k = a.pl.dN.div(e), i2 = e - k * N;
-        Q[k * LDp + i2] = R[g.pencils[q0 + k].y * LDp + i2];
-      }
-      __syncthreads();
-      V* S = fft_tile2<T, -1, false>(Q, R, npp, LDp, 1, a.pl, stw);
-      V* Wv = (S == Q) ? R : Q;                     // free buffer: the plane's Ap values
-      const V Ec = from_d<T>(a.E[c]);
-      const int ns = s1 - s0;
-      for (int e = threadIdx.x; e < ns; e += blockDim.x) {
-        const int s = s0 + e;
-        V val = S[(g.sph_pen[s] - q0) * LDp + g.sph_i2[s]];
-        const V pv = a.p[sc + s];
-        const T dr = a.kin[s] - Ec.x, di = -Ec.y;
-        val.x += dr * pv.x - di * pv.y;
-        val.y += dr * pv.y + di * pv.x;
-        a.Ap[sc + s] = val;
-        Wv[e] = val;
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < ns; e += blockDim.x) S[e] = a.p[sc + s0 + e];   // the plane's p values
-      __syncthreads();
-      unsigned char* rec = reinterpret_cast<unsigned char*>(a.dpart) + ((size_t)c * npl + pi) * rbytes;
-      plane_dots_rec<T>(a.C, a.npw, a.nocc, S, Wv, s0, ns, rec, red);
-    }
-    work(2);
-    if (!grid_barrier(a.bar, a.err, nblk, a.spin_limit)) return;
-    mark(2);
-
-    // ---- phase E: coef = sum of the plane partials, p^H P_c A p, alpha;
-    // x += alpha p, r -= alpha P_c Ap (P_c applied on the fly), partials
-    // |r|^2 and r^H K r
-    for (int task = blockIdx.x; task < ncol * a.nchunk; task += gridDim.x) {
-      const int c = task / a.nchunk, ch = task - c * a.nchunk;
-      if (!st_act[c]) continue;
-      {
-        // stage the column's plane records in shared memory (every thread
-        // loading: independent loads in flight), then add them in plane
-        // order: the projector sums in T, p^H Ap in FP64 (one warp, planes
-        // strided over the lanes, a fixed shuffle tree)
-        const unsigned char* src = reinterpret_cast<const unsigned char*>(a.dpart) + (size_t)c * npl * rbytes;
-        const size_t nb16 = (size_t)npl * rbytes / 16;
-        const bool staged = nb16 * 16 <= 2 * (size_t)N * LDp * sizeof(V);
-        const unsigned char* stage = staged ? reinterpret_cast<const unsigned char*>(A) : src;
-        if (staged) {
-          const float4* s4 = reinterpret_cast<const float4*>(src);
-          float4* d4 = reinterpret_cast<float4*>(A);
-          staged_copy<kLd, float4>((int)nb16, [&](int e) { return s4[e]; }, [&](int e, float4 v) { d4[e] = v; });
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < 2 * a.nocc; j += blockDim.x) {
-          T sx = 0, sy = 0;
-          for (int q = 0; q < npl; ++q) {
-            const V v = reinterpret_cast<const V*>(stage + (size_t)q * rbytes)[j];
-            sx += v.x;
-            sy += v.y;
-          }
-          coefT[j] = mk<T>(sx, sy);
-        }
-        if (threadIdx.x < 32) {
-          double t = 0.0;
-          for (int q = threadIdx.x; q < npl; q += 32)
-            t += *reinterpret_cast<const double*>(stage + (size_t)q * rbytes + rbytes - 16);
-          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-          if (threadIdx.x == 0) bcast = t;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          // p^H P_c A p = p^H A p - sum_v conj(<C_v|p>) <C_v|Ap>  (the correction
-          // is of the order of the rounding of p's occupied components: T)
-          T corr = 0;
-          for (int v = 0; v < a.nocc; ++v) {
-            const V k = coefT[v], q = coefT[a.nocc + v];
-            corr += q.x * k.x + q.y * k.y;
-          }
-          const double pap = bcast - (double)corr;
-          *s_al = (T)((pap > 0.0) ? st_rz[c] / pap : 0.0);
-          if (ch == 0) a.ppart[(size_t)c * a.nchunk] = pap;
-        }
-        __syncthreads();
-      }
-      const T al = *s_al;
-      const int g0 = ch * a.chunk, g1 = min(a.npw, g0 + a.chunk);
-      const size_t sc = (size_t)c * a.npw;
-      const T rtk = st_rtk[c];
-      T acc = 0, accz = 0;
-      for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
-        const size_t i = sc + G;
-        V y = a.Ap[i];
-        const V pv = a.p[i];
-        V xv = a.x[i], rv = a.r[i];
-        const T kin = a.kin[G];
-        int v = 0;
-        for (; v + 4 <= a.nocc; v += 4) {          // four independent loads in flight
-          V cv[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) cv[u] = a.C[(size_t)(v + u) * a.npw + G];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const V k = coefT[v + u];
-            y.x -= cv[u].x * k.x - cv[u].y * k.y;
-            y.y -= cv[u].x * k.y + cv[u].y * k.x;
-          }
-        }
-        for (; v < a.nocc; ++v) {
-          const V cv = a.C[(size_t)v * a.npw + G];
-          const V k = coefT[v];
-          y.x -= cv.x * k.x - cv.y * k.y;
-          y.y -= cv.x * k.y + cv.y * k.x;
-        }
-        xv.x += al * pv.x;
-        xv.y += al * pv.y;
-        rv.x -= al * y.x;
-        rv.y -= al * y.y;
-        a.x[i] = xv;
-        a.r[i] = rv;
-        const T n2 = rv.x * rv.x + rv.y * rv.y;
-        acc += n2;
-        accz += (rtk != (T)0 ? tpa<T>(kin * rtk) : (T)1) * n2;
-      }
-      acc = tsum_block<T>(acc, redT);
-      if (threadIdx.x == 0) a.rpart[(size_t)c * a.nchunk + ch] = (double)acc;
-      accz = tsum_block<T>(accz, redT);
-      if (threadIdx.x == 0) a.zpart[(size_t)c * a.nchunk + ch] = (double)accz;
-      __syncthreads();
-    }
-    work(4);
-    if (!grid_barrier(a.bar, a.err, nblk, a.spin_limit)) return;
-    mark(4);
-
-    // ---- convergence decisions (identical in every CTA)
-    column_sums(a.rpart, a.zpart, a.nchunk, ncol, st_s, st_z);
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
-      if (!st_act[c]) continue;
-      const double s = st_s[c], z = st_z[c];
-      const double pp = a.ppart[(size_t)c * a.nchunk];
-      const int itc = st_it[c] + 1;
-      st_it[c] = itc;
-      st_beta[c] = z / st_rz[c];
-      st_rz[c] = z;
-      st_rr[c] = s;
-      st_min[c] = fmin(st_min[c], s);
-      if (s < 0.25 * st_best[c]) { st_best[c] = s; st_itb[c] = itc; }
-      int stop = 0;
-      if (!(pp > 0.0) || !isfinite(s)) { st_flag[c] = 2; stop = 1; }
-      else if (s <= st_stop[c]) { st_flag[c] = 0; stop = 1; }
-      else if (s > 1e4 * st_min[c]) { st_flag[c] = 3; stop = 1; }
-      else if (itc >= a.maxit) { st_flag[c] = 1; stop = 1; }
-      else if (itc - st_itb[c] > max(kCgStagWindow, 2 * st_itb[c])) { st_flag[c] = 4; stop = 1; }
-      if (stop) st_act[c] = 0;
+      s_task[1] = ph;
     }
     __syncthreads();
-    mark(5);
-  }
-  if (blockIdx.x == 0) {
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
-      a.iters_out[c] = st_it[c];
-      a.flag_out[c] = st_act[c] ? 1 : st_flag[c];
-      a.rr_out[c] = st_rr[c];
-    }
+    const int ph = s_task[1], it = s_task[0], gi = s_task[2], k = s_task[3];
+    __syncthreads();
+    if (ph < 0) break;
+    if (ph == 0) task_A<T>(a, it, gi, k, smem_raw, L, s_ctl);
+    else if (ph == 1) task_B<T>(a, it, gi, k, smem_raw, L, s_ctl);
+    else task_C<T>(a, it, gi, k, smem_raw, L, s_ctl);
+    __syncthreads();
   }
 }
 
 template <typename T>
-static size_t pcg_smem(int N, int ncol, int nocc) {
-  return pcg_layout(N, ncol, nocc, (int)sizeof(cpx<T>)).total;
+static size_t pcg_smem(int N, int nocc, int W, int maxplane) {
+  return pcg_layout(N, nocc, W, maxplane, (int)sizeof(cpx<T>)).total;
+}
+
+PcgSizes pcg_sizes(int nocc, int npw, int ncol, int W, int nplanes, int N3, int csize) {
+  PcgSizes z;
+  z.W = W;
+  z.ngrp = (ncol + W - 1) / W;
+  z.rec_bytes = pcg_rec_bytes(nocc, W, csize);
+  z.rec_total = z.rec_bytes * (size_t)z.ngrp * nplanes;
+  z.apart = (size_t)2 * z.ngrp * nplanes * W * 2;
+  z.cst = (size_t)2 * ncol;
+  z.ctl = (size_t)kCtlHead + 4 * (size_t)z.ngrp;
+  z.Y = (size_t)z.ngrp * npw;
+  z.grid = (size_t)z.ngrp * N3;
+  return z;
 }
 
 template <typename T>
 cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPlan& pl, const Prec<T>& P, int nocc,
-                                 int npw, int ncol, const double2* b64, const int* outer_active, const double2* E,
-                                 const double* rr_abs, double tol_in2, int maxit, cpx<T>* x, cpx<T>* r, cpx<T>* p,
-                                 cpx<T>* Ap, cpx<T>* grid, double2* dpart, double* ppart, double* rpart,
-                                 double* zpart, const double* tk, unsigned* bar, int* err, int* iters, int* flags,
-                                 double* rr_out, int* grid_used, unsigned long long* ptime, int cta_div,
-                                 int max_chunks, unsigned long long spin_limit) {
+                                 int npw, int ncol, const PcgSizes& z, int maxplane, const double2* b64,
+                                 const int* outer_active, const double2* E, const double* rr_abs, const double* tk,
+                                 double tol_in2, int maxit, cpx<T>* x, cpx<T>* r, cpx<T>* p, cpx<T>* sv, cpx<T>* Y,
+                                 cpx<T>* grid, unsigned char* rec, double* apart, PcgCol* cst, unsigned* ctl,
+                                 int* iters, int* flags, double* rr_out, int* grid_used, int cta_div,
+                                 unsigned long long spin_limit) {
   PcgArgs<T> a;
   a.g = g; a.pl = pl; a.tw = P.tw; a.kin = P.kin; a.vloc_s = P.vloc_s; a.C = P.C;
-  a.nocc = nocc; a.npw = npw; a.ncol = ncol;
-  a.b64 = b64; a.outer_active = outer_active; a.E = E; a.rr_abs = rr_abs; a.tol_in2 = tol_in2; a.maxit = maxit;
-  a.x = x; a.r = r; a.p = p; a.Ap = Ap; a.grid = grid; a.dpart = dpart; a.ppart = ppart; a.rpart = rpart;
-  a.zpart = zpart; a.tk = tk;
-  a.bar = bar; a.err = err; a.iters_out = iters; a.flag_out = flags; a.rr_out = rr_out; a.ptime = ptime;
-  a.spin_limit = spin_limit;
-  const size_t sm = pcg_smem<T>(g.N, ncol, nocc);
+  a.nocc = nocc; a.npw = npw; a.ncol = ncol; a.ngrp = z.ngrp; a.W = z.W; a.maxplane = maxplane;
+  a.b64 = b64; a.outer_active = outer_active; a.E = E; a.rr_abs = rr_abs; a.tk = tk; a.tol_in2 = tol_in2;
+  a.maxit = maxit;
+  a.x = x; a.r = r; a.p = p; a.s = sv; a.Y = Y; a.grid = grid; a.rec = rec; a.rec_bytes = z.rec_bytes;
+  a.apart = apart; a.cst = cst; a.ctl = ctl;
+  a.iters_out = iters; a.flag_out = flags; a.rr_out = rr_out; a.spin_limit = spin_limit;
+  const size_t sm = pcg_smem<T>(g.N, nocc, z.W, maxplane);
+  if (sm > 227 * 1024) return cudaErrorNotSupported;
   cudaError_t e = cudaSuccess;
   {
     // The attribute is per function and per process: only ever raise it, so a
@@ -561,34 +828,25 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_persistent<T>, kPT, sm)) != cudaSuccess)
     return e;
-  if (per < 1) return cudaErrorInvalidConfiguration;
-  const int ntask = ncol * std::max(g.N, g.nplanes);
+  if (per < 1) return cudaErrorNotSupported;
   // cta_div contexts run concurrently (batch mode): each takes an equal share
   // of the resident slots, so all their grids can be co-resident at once.
   const int cap = std::max(1, per * nsm / std::max(cta_div, 1));
-  const int nblk = std::min(cap, std::max(ntask, 1));
+  const int per_it = z.ngrp * (2 * g.nplanes + g.N);
+  const int nblk = std::min(cap, std::max(per_it, 1));
   *grid_used = nblk;
-  // phases 0 and E: one round of tasks (columns x chunks <= CTAs), chunks a
-  // multiple of 32 entries, at most max_chunks per column (partial-sum slots)
-  a.nchunk = std::max(1, std::min(max_chunks, nblk / std::max(ncol, 1)));
-  a.chunk = (((npw + a.nchunk - 1) / a.nchunk) + 31) / 32 * 32;
-  a.nchunk = (npw + a.chunk - 1) / a.chunk;
   void* args[] = {&a};
   ++g_launches;
   return cudaLaunchCooperativeKernel((const void*)k_cg_persistent<T>, dim3(nblk), dim3(kPT), args, sm, s);
 }
 
-template cudaError_t launch_cg_persistent<float>(cudaStream_t, const Geometry&, const FftPlan&, const Prec<float>&,
-                                                 int, int, int, const double2*, const int*, const double2*,
-                                                 const double*, double, int, float2*, float2*, float2*, float2*,
-                                                 float2*, double2*, double*, double*, double*, const double*,
-                                                 unsigned*, int*, int*, int*, double*, int*, unsigned long long*,
-                                                 int, int, unsigned long long);
-template cudaError_t launch_cg_persistent<double>(cudaStream_t, const Geometry&, const FftPlan&, const Prec<double>&,
-                                                  int, int, int, const double2*, const int*, const double2*,
-                                                  const double*, double, int, double2*, double2*, double2*,
-                                                  double2*, double2*, double2*, double*, double*, double*,
-                                                  const double*, unsigned*, int*, int*, int*, double*, int*,
-                                                  unsigned long long*, int, int, unsigned long long);
+#define GW_PCG_INST(T)                                                                                      \
+  template cudaError_t launch_cg_persistent<T>(                                                            \
+      cudaStream_t, const Geometry&, const FftPlan&, const Prec<T>&, int, int, int, const PcgSizes&, int,    \
+      const double2*, const int*, const double2*, const double*, const double*, double, int, cpx<T>*,       \
+      cpx<T>*, cpx<T>*, cpx<T>*, cpx<T>*, cpx<T>*, unsigned char*, double*, PcgCol*, unsigned*, int*, int*,  \
+      double*, int*, int, unsigned long long);
+GW_PCG_INST(float)
+GW_PCG_INST(double)
 
 }  // namespace gw

@@ -635,6 +635,61 @@ void launch_add_conv(cudaStream_t s, int npw, int ncol, const cpx<T>* d, double2
   k_add_conv<T><<<g, kLT, 0, s>>>((size_t)npw, d, x, active);
 }
 
+// x += (d(G) + conj d(-G)) / 2: the correction of a column whose solution is
+// real in real space, with any antisymmetric rounding of d dropped.
+template <typename T>
+__global__ void k_add_conv_sym(size_t npw, const cpx<T>* __restrict__ d, double2* __restrict__ x,
+                               const int* __restrict__ active, const int* __restrict__ neg) {
+  const int c = blockIdx.y;
+  if (active && !active[c]) return;
+  for (size_t G = blockIdx.x * (size_t)blockDim.x + threadIdx.x; G < npw; G += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = (size_t)c * npw + G;
+    const double2 dv = to_d(d[i]);
+    const double2 dn = to_d(d[(size_t)c * npw + neg[G]]);
+    double2 xv = x[i];
+    xv.x += 0.5 * (dv.x + dn.x);
+    xv.y += 0.5 * (dv.y - dn.y);
+    x[i] = xv;
+  }
+}
+
+template <typename T>
+void launch_add_conv_sym(cudaStream_t s, int npw, int ncol, const cpx<T>* d, double2* x, const int* active,
+                         const int* neg) {
+  dim3 g((npw + kLT - 1) / kLT, ncol);
+  ++g_launches;
+  k_add_conv_sym<T><<<g, kLT, 0, s>>>((size_t)npw, d, x, active, neg);
+}
+
+// out[c] = max_G |b(G) - conj b(-G)|, out[ncol + c] = max_G |b(G)| (one block per column)
+__global__ void __launch_bounds__(kLT) k_sym_check(int npw, const double2* __restrict__ b, const int* __restrict__ neg,
+                                                   double* __restrict__ out, int ncol) {
+  __shared__ double sa[kLT / 32], sb[kLT / 32];
+  const int c = blockIdx.x;
+  double ma = 0.0, mb = 0.0;
+  for (int G = threadIdx.x; G < npw; G += blockDim.x) {
+    const double2 v = b[(size_t)c * npw + G], w = b[(size_t)c * npw + neg[G]];
+    ma = fmax(ma, fabs(v.x - w.x) + fabs(v.y + w.y));
+    mb = fmax(mb, fabs(v.x) + fabs(v.y));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ma = fmax(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+    mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  }
+  if ((threadIdx.x & 31) == 0) { sa[threadIdx.x >> 5] = ma; sb[threadIdx.x >> 5] = mb; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) { ma = fmax(ma, sa[k]); mb = fmax(mb, sb[k]); }
+    out[c] = fmax(ma, sa[0]);
+    out[ncol + c] = fmax(mb, sb[0]);
+  }
+}
+
+void launch_sym_check(cudaStream_t s, int npw, int ncol, const double2* b, const int* neg, double* out) {
+  ++g_launches;
+  k_sym_check<<<ncol, kLT, 0, s>>>(npw, b, neg, out, ncol);
+}
+
 // r = b - Ax (in place over Ax), res2[c] = |r|^2, bb[c] = |b|^2, xx[c] = |x|^2.
 // With C: r = P_c (b - Ax) = b - Ax - sum_v C_v (cb[v][c] - cax[v][c]), where
 // cb = C^H b and cax = C^H Ax (coefficients [nocc][ncol]).
@@ -795,33 +850,6 @@ template void launch_model_scale<float>(cudaStream_t, int, int, const float*, co
                                         const double2*, const double2*, float2*);
 
 // precision changes at the boundary of an FP32 pipeline; out = x - z (FP64 result)
-__global__ void k_cast_df(size_t n, const double* __restrict__ x, float* __restrict__ y) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    y[i] = (float)x[i];
-}
-__global__ void k_cast_fd(size_t n, const float* __restrict__ x, double* __restrict__ y) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    y[i] = (double)x[i];
-}
-__global__ void k_sub_fd(size_t n, const double* __restrict__ x, const float* __restrict__ z,
-                         double* __restrict__ y) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    y[i] = x[i] - (double)z[i];
-}
-static int elem_blocks(size_t n) { return (int)std::min<size_t>((n + kLT - 1) / kLT, 152 * 8); }
-void launch_cast(cudaStream_t s, size_t n, const double* x, float* y) {
-  ++g_launches;
-  k_cast_df<<<elem_blocks(n), kLT, 0, s>>>(n, x, y);
-}
-void launch_cast(cudaStream_t s, size_t n, const float* x, double* y) {
-  ++g_launches;
-  k_cast_fd<<<elem_blocks(n), kLT, 0, s>>>(n, x, y);
-}
-void launch_sub_mixed(cudaStream_t s, size_t n, const double* x, const float* z, double* y) {
-  ++g_launches;
-  k_sub_fd<<<elem_blocks(n), kLT, 0, s>>>(n, x, z, y);
-}
-
 // Eq. subs_epsilon in the two bases: out[i][j] = sum_ab a_ia (Ti_ab - (M^-1)_ab) a_jb
 // + sum_ab am_ia (Tmi_ab - delta_ab) am_jb; one block per (i, j), rows a over
 // the threads, then an ordered block sum.  Mi holds the inverse of M^T, i.e.
@@ -1028,7 +1056,8 @@ void launch_tridiag_inv(cudaStream_t s, int K, const double* alpha, const double
                                           const int*, Work&, CgState, const T*, double, double);           \
   template void launch_cg_update<T>(cudaStream_t, int, int, cpx<T>*, cpx<T>*, const cpx<T>*,              \
                                     const cpx<T>*, const double*, Work&, CgState, const T*, double, int); \
-  template void launch_add_conv<T>(cudaStream_t, int, int, const cpx<T>*, double2*, const int*);
+  template void launch_add_conv<T>(cudaStream_t, int, int, const cpx<T>*, double2*, const int*);        \
+  template void launch_add_conv_sym<T>(cudaStream_t, int, int, const cpx<T>*, double2*, const int*, const int*);
 
 GW_LINST(double)
 GW_LINST(float)

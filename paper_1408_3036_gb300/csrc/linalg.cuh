@@ -87,6 +87,11 @@ void launch_cg_update(cudaStream_t s, int npw, int ncol, cpx<T>* x, cpx<T>* r, c
                       int maxit);
 template <typename T>
 void launch_add_conv(cudaStream_t s, int npw, int ncol, const cpx<T>* d, double2* x, const int* active);
+template <typename T>
+void launch_add_conv_sym(cudaStream_t s, int npw, int ncol, const cpx<T>* d, double2* x, const int* active,
+                         const int* neg);
+// out[c] = max |b(G) - conj b(-G)|, out[ncol + c] = max |b(G)| per column
+void launch_sym_check(cudaStream_t s, int npw, int ncol, const double2* b, const int* neg, double* out);
 void launch_defl_scale(cudaStream_t s, double2* coef, const double* eps, const double2* E, int ndef, int ncol,
                        const int* active);
 void launch_residual(cudaStream_t s, int npw, int ncol, const double2* b, double2* ax, const double2* x,
@@ -98,9 +103,6 @@ void launch_combine(cudaStream_t s, int npw, int nout, const double2* in, const 
 template <typename T>
 void launch_model_scale(cudaStream_t s, int npw, int nout, const T* kin, const cpx<T>* in, const int* src,
                         const double2* Em, const double2* Ep, cpx<T>* out);
-void launch_cast(cudaStream_t s, size_t n, const double* x, float* y);
-void launch_cast(cudaStream_t s, size_t n, const float* x, double* y);
-void launch_sub_mixed(cudaStream_t s, size_t n, const double* x, const float* z, double* y);   // y = x - z
 // Eq. subs_epsilon: out[m][m] from the coefficients a [m][k], am [m][km] and the
 // inverses Ti (exact basis), Mi (model in the exact basis, complex), Tmi (model basis)
 void launch_split_form(cudaStream_t s, int m, int k, int km, const double* a, const double* Ti,
@@ -168,14 +170,31 @@ void launch_block_tridiag(cudaStream_t s, int K, int blk, const double2* A, cons
                           double2* T);
 
 // whole CG pass in one cooperative launch (kernels_cg.cu)
+// Per-column state of the persistent CG carried between iterations.
+struct PcgCol {
+  double gam, alpha, stop, rmin, rbest;
+  int it, itb, active, flag;
+};
+// Sizes of the persistent CG's work buffers for ncol columns in groups of W
+// (2: packed pairs of real-in-real-space columns; 1: one column per group).
+struct PcgSizes {
+  int W = 1, ngrp = 0;
+  size_t rec_bytes = 0, rec_total = 0;   // bytes of one plane record, of all
+  size_t apart = 0, cst = 0, ctl = 0;    // doubles, PcgCol entries, control words
+  size_t Y = 0, grid = 0;                // complex entries
+};
+PcgSizes pcg_sizes(int nocc, int npw, int ncol, int W, int nplanes, int N3, int csize);
+// One cooperative launch = one CG pass over ncol columns (kernels_cg.cu); ctl
+// (z.ctl words) must be zero at launch.  cudaErrorNotSupported when the
+// kernel's shared memory does not fit (the caller then uses the multi-launch CG).
 template <typename T>
 cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPlan& pl, const Prec<T>& P, int nocc,
-                                 int npw, int ncol, const double2* b64, const int* outer_active, const double2* E,
-                                 const double* rr_abs, double tol_in2, int maxit, cpx<T>* x, cpx<T>* r, cpx<T>* p,
-                                 cpx<T>* Ap, cpx<T>* grid, double2* dpart, double* ppart, double* rpart,
-                                 double* zpart, const double* tk, unsigned* bar, int* err, int* iters, int* flags,
-                                 double* rr_out, int* grid_used, unsigned long long* ptime, int cta_div,
-                                 int max_chunks, unsigned long long spin_limit);
+                                 int npw, int ncol, const PcgSizes& z, int maxplane, const double2* b64,
+                                 const int* outer_active, const double2* E, const double* rr_abs, const double* tk,
+                                 double tol_in2, int maxit, cpx<T>* x, cpx<T>* r, cpx<T>* p, cpx<T>* sv, cpx<T>* Y,
+                                 cpx<T>* grid, unsigned char* rec, double* apart, PcgCol* cst, unsigned* ctl,
+                                 int* iters, int* flags, double* rr_out, int* grid_used, int cta_div,
+                                 unsigned long long spin_limit);
 // One thread-block cluster per column (kernels_cgc.cu); cudaErrorNotSupported
 // when the column's planes do not fit in the shared memory of a cluster.
 template <typename T>

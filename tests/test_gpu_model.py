@@ -3,9 +3,9 @@ the two-basis split (Eq. subs_epsilon) on the GPU against the FP64 oracle.
 
 The model path has no iterative solve: with GW_FP64 every step is FP64
 arithmetic, so the applications agree with the oracle to rounding (1e-12
-relative) and the Lanczos coefficients and the split to 1e-10; with GW_MIXED
-the transforms run in FP32 with no refinement (1e-6 for one application of
-chi0 or eps~, 1e-5 for the Lanczos coefficients after 20 steps).
+relative) and the Lanczos coefficients and the split to 1e-10.  GW_MIXED runs
+the model in FP64 too (it has no solve whose FP64 residual could refine FP32
+transforms), so the mixed results meet 1e-6 everywhere.
 """
 import numpy as np
 import pytest
@@ -58,7 +58,7 @@ def test_model_chi0_and_eps(tiny, omega):
         ref = response.chi0_model(gs, f[b], omega)
         assert rel(dn[b], ref if np.iscomplexobj(dn) else ref.real) < 1e-12
     out = c.apply_eps(f[:2], [omega], gw.GW_FP64)[0]
-    out32 = c.apply_eps(f[:2], [omega], gw.GW_MIXED)[0]    # FP32 transforms at real omega
+    out32 = c.apply_eps(f[:2], [omega], gw.GW_MIXED)[0]
     dn32 = c.apply_chi0(f, [omega], gw.GW_MIXED)[0]
     for b in range(2):
         ref = D.apply(f[b])
@@ -130,11 +130,10 @@ def test_model_lanczos(tiny):
     a, b, Q = c.lanczos(x0, K, 0.0, gw.GW_FP64, basis=True)
     assert rel(a, ar) < 1e-10 and rel(b, br) < 1e-10
     assert np.abs(w * Q @ Q.T - np.eye(K)).max() < 1e-12
-    # FP32 model operator, no refinement: each application carries the rounding
-    # of about a dozen FP32 transform passes (~1e-6 relative); the recursion
-    # passes it on to alpha and beta with a modest growth over K steps
+    # the mixed precision runs the model operator in FP64 (no solve whose
+    # residual could refine FP32 transforms): the benchmark spec's 1e-6 holds
     a32, b32, _ = c.lanczos(x0, K, 0.0, gw.GW_MIXED)
-    assert rel(a32, ar) < 1e-5 and rel(b32, br) < 1e-5
+    assert rel(a32, ar) < 1e-6 and rel(b32, br) < 1e-6
     c.close()
 
 
