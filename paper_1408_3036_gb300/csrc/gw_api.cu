@@ -275,6 +275,41 @@ gw_status h_apply(gw_ctx* ctx, cpx<T>* x, int ncol, const double2* E, const int*
   return launch_check(ctx, "h_apply");
 }
 
+// (H - E) x in FP64 for columns that are real in real space, two per complex
+// transform (pack, the pruned passes, split through G and -G with the kinetic
+// part added); act: host mask of the columns wanted (a pair runs when one of
+// its columns is wanted, and both of its outputs are written).
+gw_status h_apply_sym(gw_ctx* ctx, const double2* x, int ncol, const double2* E, const std::vector<int>& act,
+                      double2* out) {
+  const int npw = ctx->npw, npair = (ncol + 1) / 2;
+  std::vector<int> ia(npair), ib(npair), pact(npair);
+  for (int j = 0; j < npair; ++j) {
+    ia[j] = 2 * j;
+    ib[j] = (2 * j + 1 < ncol) ? 2 * j + 1 : -1;
+    pact[j] = act[2 * j] || (ib[j] >= 0 && act[2 * j + 1]);
+  }
+  int *dia, *dib, *dpact;
+  TRY(upload_table(ctx, "hs_ia", ia, &dia));
+  TRY(upload_table(ctx, "hs_ib", ib, &dib));
+  TRY(upload(ctx, "hs_act", pact, &dpact));
+  double2 *xp, *yp, *grid;
+  TRY(getbuf(ctx, "hs_xp", (size_t)npair * npw, &xp));
+  TRY(getbuf(ctx, "hs_yp", (size_t)npair * npw, &yp));
+  TRY(getbuf(ctx, "g_hs", (size_t)npair * ctx->N3, &grid));
+  auto& P = ctx->P64;
+  const Geometry& g = ctx->geo;
+  launch_pack_pairs(ctx->st, npw, npair, x, dia, dib, dpact, xp);
+  launch_zpass<double>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, grid, xp, nullptr, nullptr, nullptr, nullptr, dpact,
+                       nullptr, nullptr, npair);
+  launch_ypass<double>(ctx->st, 1, 1, 0, g, P, ctx->plan, grid, dpact, npair, 0);
+  launch_xpass_mul<double>(ctx->st, 1, 1, 1, g, P, ctx->plan, grid, P.vloc_s, dpact, npair);
+  launch_ypass<double>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, dpact, npair, 0);
+  launch_zpass<double>(ctx->st, Z_GATHER_FWD, g, P, ctx->plan, grid, yp, nullptr, nullptr, nullptr, nullptr, dpact,
+                       nullptr, nullptr, npair);
+  launch_unpack_pairs(ctx->st, npw, npair, yp, g.sph_neg, dia, dib, dpact, P.kin, E, x, out);
+  return launch_check(ctx, "h_apply_sym");
+}
+
 // ---------------------------------------------------------------------------
 // batched CG on P_c (H - E) P_c x = b, precision T, rhs FP64
 // ---------------------------------------------------------------------------
@@ -649,14 +684,20 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
     // last transform pass, C^H b computed once per solve
     {
       const int pa = prof_begin(ctx, PC_REFINE);
-      GatherDots dots;
-      dots.C = ctx->P64.C;
-      dots.nocc = ctx->nocc;
-      dots.ncol = ncol;
-      dots.part = ctx->work.part_d;
-      dots.cnt = ctx->work.cnt_d;
-      dots.coef = cax;
-      TRY(h_apply<double>(ctx, x64, ncol, E, oact, ax, &dots));
+      if (sym) {
+        // two real-in-real-space columns per FP64 transform
+        TRY(h_apply_sym(ctx, x64, ncol, E, act, ax));
+        launch_gram<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, ax, ncol, ctx->work, cax);
+      } else {
+        GatherDots dots;
+        dots.C = ctx->P64.C;
+        dots.nocc = ctx->nocc;
+        dots.ncol = ncol;
+        dots.part = ctx->work.part_d;
+        dots.cnt = ctx->work.cnt_d;
+        dots.coef = cax;
+        TRY(h_apply<double>(ctx, x64, ncol, E, oact, ax, &dots));
+      }
       prof_end(ctx, PC_REFINE, pa);
     }
     launch_residual(ctx->st, npw, ncol, b64, ax, x64, oact, ctx->work, res2, bb, xx, ctx->P64.C, ctx->nocc, cb,
@@ -758,16 +799,49 @@ gw_status rhs_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, double2** ou
   int *dca, *dcy;
   TRY(upload_table(ctx, "rhs_ca", ca, &dca));
   TRY(upload_table(ctx, "rhs_cy", cy, &dcy));
-  cpx<T>* grid;
-  TRY(getbuf(ctx, "g_rhs" + t, (size_t)nr * N3, &grid));
   double2* rhs64;
   TRY(getbuf(ctx, "rhs64", (size_t)nr * npw, &rhs64));
   TRY(ensure_work(ctx, std::max(nr, 1)));
-  launch_xpass_prod_fwd<T>(ctx->st, g, P, ctx->plan, reinterpret_cast<const cpx<T>*>(y), y_cplx ? 1 : 0, P.U, 0, 1,
-                           dca, dcy, grid, nr);
-  launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, nullptr, nr, 0);
-  launch_zpass<T>(ctx->st, Z_GATHER_FWD, g, P, ctx->plan, grid, rhs64, nullptr, nullptr, nullptr, nullptr, nullptr,
-                  nullptr, nullptr, nr);
+  if (!y_cplx) {
+    // real fields and real u_v: the products of states 2k and 2k+1 with the
+    // same field share one complex transform, split afterwards through G, -G
+    const int hp = (nocc + 1) / 2, npair = hp * nb;
+    std::vector<int> pa(npair), py(npair), pa2(npair), ia(npair), ib(npair);
+    for (int b = 0; b < nb; ++b)
+      for (int k = 0; k < hp; ++k) {
+        const int j = b * hp + k;
+        const bool two = 2 * k + 1 < nocc;
+        pa[j] = 2 * k;
+        py[j] = b;
+        pa2[j] = two ? 2 * k + 1 : -1;
+        ia[j] = b * nocc + 2 * k;
+        ib[j] = two ? b * nocc + 2 * k + 1 : -1;
+      }
+    int *dpa, *dpy, *dpa2, *dia, *dib;
+    TRY(upload_table(ctx, "rhsp_a", pa, &dpa));
+    TRY(upload_table(ctx, "rhsp_y", py, &dpy));
+    TRY(upload_table(ctx, "rhsp_a2", pa2, &dpa2));
+    TRY(upload_table(ctx, "rhsp_ia", ia, &dia));
+    TRY(upload_table(ctx, "rhsp_ib", ib, &dib));
+    cpx<T>* grid;
+    double2* yp;
+    TRY(getbuf(ctx, "g_rhs" + t, (size_t)npair * N3, &grid));
+    TRY(getbuf(ctx, "rhs_pk", (size_t)npair * npw, &yp));
+    launch_xpass_prod_fwd<T>(ctx->st, g, P, ctx->plan, reinterpret_cast<const cpx<T>*>(y), 0, P.U, 0, 0, dpa, dpy,
+                             grid, npair, dpa2, dpy);
+    launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, nullptr, npair, 0);
+    launch_zpass<T>(ctx->st, Z_GATHER_FWD, g, P, ctx->plan, grid, yp, nullptr, nullptr, nullptr, nullptr, nullptr,
+                    nullptr, nullptr, npair);
+    launch_unpack_pairs(ctx->st, npw, npair, yp, g.sph_neg, dia, dib, nullptr, nullptr, nullptr, nullptr, rhs64);
+  } else {
+    cpx<T>* grid;
+    TRY(getbuf(ctx, "g_rhs" + t, (size_t)nr * N3, &grid));
+    launch_xpass_prod_fwd<T>(ctx->st, g, P, ctx->plan, reinterpret_cast<const cpx<T>*>(y), 1, P.U, 0, 1, dca, dcy,
+                             grid, nr);
+    launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, nullptr, nr, 0);
+    launch_zpass<T>(ctx->st, Z_GATHER_FWD, g, P, ctx->plan, grid, rhs64, nullptr, nullptr, nullptr, nullptr, nullptr,
+                    nullptr, nullptr, nr);
+  }
   // P_c once: psi_v* y has a large component along the occupied states (e.g.
   // <psi_v|y psi_v>) and one pass leaves |C C^H - 1| times it behind; the
   // solver's FP64 residual P_c (b - A x) removes that remnant
@@ -909,6 +983,42 @@ gw_status chi0_reduce(gw_ctx* ctx, const double2* sol64, int nb, int nom, void* 
   auto& P = ctx->P64;
   const Geometry& g = ctx->geo;
   const std::string t = tname<T>();
+  cpx<T>* parts;
+  const size_t nparts = (size_t)kMaxReduceParts * N3;   // enough whenever a split pays (few groups)
+  TRY(getbuf(ctx, "dn_parts" + t, nparts, &parts));
+  if (!dn_cplx) {
+    // real densities: the solutions of states 2k and 2k+1 (real in real
+    // space) share one inverse transform, f_2k + i f_2k+1
+    const int hp = (nocc + 1) / 2, ng = nom * nb, npair = hp * ng;
+    std::vector<int> ia(npair), ib(npair), gs(ng + 1), cv(npair), cv2(npair);
+    for (int o = 0; o < ng; ++o)
+      for (int k = 0; k < hp; ++k) {
+        const int j = o * hp + k;
+        const bool two = 2 * k + 1 < nocc;
+        ia[j] = o * nocc + 2 * k;
+        ib[j] = two ? o * nocc + 2 * k + 1 : -1;
+        cv[j] = 2 * k;
+        cv2[j] = two ? 2 * k + 1 : -1;
+      }
+    for (int o = 0; o <= ng; ++o) gs[o] = o * hp;
+    int *dia, *dib, *dgs, *dcv, *dcv2;
+    TRY(upload_table(ctx, "dnp_ia", ia, &dia));
+    TRY(upload_table(ctx, "dnp_ib", ib, &dib));
+    TRY(upload_table(ctx, "dnp_gs", gs, &dgs));
+    TRY(upload_table(ctx, "dnp_cv", cv, &dcv));
+    TRY(upload_table(ctx, "dnp_cv2", cv2, &dcv2));
+    double2* xp;
+    cpx<T>* gd;
+    TRY(getbuf(ctx, "dn_pk", (size_t)npair * ctx->npw, &xp));
+    TRY(getbuf(ctx, "g_dn" + t, (size_t)npair * N3, &gd));
+    launch_pack_pairs(ctx->st, ctx->npw, npair, sol64, dia, dib, nullptr, xp);
+    launch_zpass<T>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, gd, xp, nullptr, nullptr, nullptr, nullptr, nullptr,
+                    nullptr, nullptr, npair);
+    launch_ypass<T>(ctx->st, 1, 1, 0, g, P, ctx->plan, gd, nullptr, npair, 0);
+    launch_xpass_inv_reduce<T>(ctx->st, g, P, ctx->plan, gd, dgs, dcv, ng, -2.0 / ctx->vol,
+                               reinterpret_cast<double*>(dn), nullptr, 0, parts, nparts, hp, dcv2);
+    return launch_check(ctx, "chi0");
+  }
   cpx<T>* gd;
   TRY(getbuf(ctx, "g_dn" + t, (size_t)nsol * N3, &gd));
   launch_zpass<T>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, gd, const_cast<double2*>(sol64), nullptr, nullptr,
@@ -920,9 +1030,6 @@ gw_status chi0_reduce(gw_ctx* ctx, const double2* sol64, int nb, int nom, void* 
   int *dgs, *dcv;
   TRY(upload_table(ctx, "dn_gs", gstart, &dgs));
   TRY(upload_table(ctx, "dn_cv", colv, &dcv));
-  cpx<T>* parts;
-  const size_t nparts = (size_t)kMaxReduceParts * N3;   // enough whenever a split pays (few groups)
-  TRY(getbuf(ctx, "dn_parts" + t, nparts, &parts));
   launch_xpass_inv_reduce<T>(ctx->st, g, P, ctx->plan, gd, dgs, dcv, nom * nb, -2.0 / ctx->vol,
                              dn_cplx ? nullptr : reinterpret_cast<double*>(dn),
                              dn_cplx ? reinterpret_cast<double2*>(dn) : nullptr, 0, parts, nparts, nocc);

@@ -198,11 +198,16 @@ void launch_xpass_mul(cudaStream_t s, int first_inverse, int pruned_in, int prun
                       const Prec<T>& P, const FftPlan& pl, cpx<T>* grid, const T* mul, const int* active,
                       int ncol);
 // out(v,b) = FFT_x(conj(U[v]) * Y[b]) / N_g   (first pass of a pruned forward transform)
+// Pair mode (col_a2, col_y2 given; A and Y real): out = FFT_x(A[a] Y[y] + i A[a2] Y[y2]) / N_g
+// (col_a2[col] < 0: the first product alone).
 template <typename T>
 void launch_xpass_prod_fwd(cudaStream_t s, const Geometry& g, const Prec<T>& P, const FftPlan& pl,
                            const cpx<T>* Y, int y_complex, const cpx<T>* A, int a_per_col, int conj_a,
-                           const int* col_a, const int* col_y, cpx<T>* out, int ncol);
-// dn[o] += scale * sum_{v} U[v] * IFFT_x(grid[col])   for col in group o (last pass of inverse).
+                           const int* col_a, const int* col_y, cpx<T>* out, int ncol,
+                           const int* col_a2 = nullptr, const int* col_y2 = nullptr);
+// dn[o] += scale * sum_{v} U[v] * IFFT_x(grid[col])   for col in group o (last pass of inverse);
+// pair mode (col_v2 given, real output): grid[col] holds f_1 + i f_2 of two
+// real fields and the sum takes Re U[col_v] f_1 + Re U[col_v2] f_2.
 // scratch (optional, scratch_elems complex entries) lets the sum over the at
 // most max_cols columns of a group be split over several CTAs.
 constexpr int kMaxReduceParts = 8;
@@ -210,6 +215,7 @@ template <typename T>
 void launch_xpass_inv_reduce(cudaStream_t s, const Geometry& g, const Prec<T>& P, const FftPlan& pl,
                              const cpx<T>* grid, const int* group_start, const int* col_v, int ngroups,
                              double scale, T* out_real, cpx<T>* out_cplx, int accumulate,
-                             cpx<T>* scratch = nullptr, size_t scratch_elems = 0, int max_cols = 1);
+                             cpx<T>* scratch = nullptr, size_t scratch_elems = 0, int max_cols = 1,
+                             const int* col_v2 = nullptr);
 
 }  // namespace gw

@@ -334,7 +334,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_xpass_prod_fwd(Geometry g, Prec<T> P, FftPlan pl, const cpx<T>* __restrict__ Y, int y_complex,
                  const cpx<T>* __restrict__ Aarr, int conj_a, const int* __restrict__ col_a,
-                 const int* __restrict__ col_y, cpx<T>* __restrict__ out, int nchunk) {
+                 const int* __restrict__ col_y, cpx<T>* __restrict__ out, int nchunk,
+                 const int* __restrict__ col_a2, const int* __restrict__ col_y2) {
   using V = cpx<T>;
   extern __shared__ unsigned char smem_raw[];
   const int N = g.N, LD = N + 1;
@@ -351,15 +352,26 @@ k_xpass_prod_fwd(Geometry g, Prec<T> P, FftPlan pl, const cpx<T>* __restrict__ Y
   const size_t ybase = (size_t)col_y[col] * g.N3 + off1;
   const T* Yr = reinterpret_cast<const T*>(Y);
   const T sc = (T)(1.0 / (double)g.N3);
+  // pair mode (col_a2 given; real A and real Y): the products of two columns
+  // packed as a + i b, each real in real space
+  const int a2 = col_a2 ? col_a2[col] : -1;
+  const size_t a2base = (size_t)(a2 >= 0 ? a2 : 0) * g.N3 + off1;
+  const size_t y2base = (size_t)(col_y2 ? col_y2[col] : 0) * g.N3 + off1;
   for (int e = threadIdx.x; e < N * kP; e += blockDim.x) {
     const int i0 = e / kP, dz = e - i0 * kP;
     if (dz < np) {
       const size_t o = (size_t)i0 * g.N2 + dz;
-      V a = Aarr[abase + o];
-      if (conj_a) a.y = -a.y;
-      V y = y_complex ? Y[ybase + o] : mk<T>(Yr[ybase + o], (T)0);
-      V p = cmul(a, y);
-      A[dz * LD + i0] = mk<T>(p.x * sc, p.y * sc);
+      if (col_a2) {
+        const T p1 = Aarr[abase + o].x * Yr[ybase + o];
+        const T p2 = (a2 >= 0) ? Aarr[a2base + o].x * Yr[y2base + o] : (T)0;
+        A[dz * LD + i0] = mk<T>(p1 * sc, p2 * sc);
+      } else {
+        V a = Aarr[abase + o];
+        if (conj_a) a.y = -a.y;
+        V y = y_complex ? Y[ybase + o] : mk<T>(Yr[ybase + o], (T)0);
+        V p = cmul(a, y);
+        A[dz * LD + i0] = mk<T>(p.x * sc, p.y * sc);
+      }
     }
   }
   __syncthreads();
@@ -374,13 +386,15 @@ k_xpass_prod_fwd(Geometry g, Prec<T> P, FftPlan pl, const cpx<T>* __restrict__ Y
 template <typename T>
 void launch_xpass_prod_fwd(cudaStream_t s, const Geometry& g, const Prec<T>& P, const FftPlan& pl,
                            const cpx<T>* Y, int y_complex, const cpx<T>* A, int /*a_per_col*/, int conj_a,
-                           const int* col_a, const int* col_y, cpx<T>* out, int ncol) {
+                           const int* col_a, const int* col_y, cpx<T>* out, int ncol, const int* col_a2,
+                           const int* col_y2) {
   const int nchunk = (g.N + kP - 1) / kP;
   if (ncol == 0) return;
   dim3 grd(g.N * nchunk, ncol);
   const size_t sm = tile_smem<T>(g.N, 2);
   ++g_launches;
-  k_xpass_prod_fwd<T><<<grd, kThreads, sm, s>>>(g, P, pl, Y, y_complex, A, conj_a, col_a, col_y, out, nchunk);
+  k_xpass_prod_fwd<T><<<grd, kThreads, sm, s>>>(g, P, pl, Y, y_complex, A, conj_a, col_a, col_y, out, nchunk,
+                                                 col_a2, col_y2);
 }
 
 // ---------------------------------------------------------------------------
@@ -397,7 +411,7 @@ __global__ void __launch_bounds__(kThreads)
 k_xpass_inv_reduce(Geometry g, Prec<T> P, FftPlan pl, const cpx<T>* __restrict__ grid,
                    const int* __restrict__ gstart, const int* __restrict__ col_v, double scale,
                    T* __restrict__ out_real, cpx<T>* __restrict__ out_c, int accumulate, int nchunk,
-                   int ngrp, cpx<T>* __restrict__ part) {
+                   int ngrp, cpx<T>* __restrict__ part, const int* __restrict__ col_v2) {
   using V = cpx<T>;
   extern __shared__ unsigned char smem_raw[];
   const int N = g.N, LD = N + 1;
@@ -429,14 +443,23 @@ k_xpass_inv_reduce(Geometry g, Prec<T> P, FftPlan pl, const cpx<T>* __restrict__
     __syncthreads();
     V* R = fft_tile<T, +1>(A, B, np, LD, pl, stw);
     const size_t ubase = (size_t)col_v[col] * g.N3 + off1;
+    const int v2 = col_v2 ? col_v2[col] : -1;
+    const size_t u2base = (size_t)(v2 >= 0 ? v2 : 0) * g.N3 + off1;
     for (int e = threadIdx.x; e < N * kP; e += blockDim.x) {
       const int i0 = e / kP, dz = e - i0 * kP;
       if (dz < np) {
-        const V u = P.U[ubase + (size_t)i0 * g.N2 + dz];
         const V x = R[dz * LD + i0];
         V a = Acc[dz * LD + i0];
-        a.x += u.x * x.x - u.y * x.y;
-        a.y += u.x * x.y + u.y * x.x;
+        if (col_v2) {
+          // pair mode: x = f_1 + i f_2 of two real fields, real u_v (real output)
+          const T u1 = P.U[ubase + (size_t)i0 * g.N2 + dz].x;
+          const T u2 = (v2 >= 0) ? P.U[u2base + (size_t)i0 * g.N2 + dz].x : (T)0;
+          a.x += u1 * x.x + u2 * x.y;
+        } else {
+          const V u = P.U[ubase + (size_t)i0 * g.N2 + dz];
+          a.x += u.x * x.x - u.y * x.y;
+          a.y += u.x * x.y + u.y * x.x;
+        }
         Acc[dz * LD + i0] = a;
       }
     }
@@ -495,7 +518,7 @@ template <typename T>
 void launch_xpass_inv_reduce(cudaStream_t s, const Geometry& g, const Prec<T>& P, const FftPlan& pl,
                              const cpx<T>* grid, const int* group_start, const int* col_v, int ngroups,
                              double scale, T* out_real, cpx<T>* out_cplx, int accumulate, cpx<T>* scratch,
-                             size_t scratch_elems, int max_cols) {
+                             size_t scratch_elems, int max_cols, const int* col_v2) {
   const int nchunk = (g.N + kP - 1) / kP;
   if (ngroups == 0) return;
   // split the column sums until about four CTAs per SM are in flight
@@ -510,7 +533,7 @@ void launch_xpass_inv_reduce(cudaStream_t s, const Geometry& g, const Prec<T>& P
   const size_t sm = tile_smem<T>(g.N, 3);
   ++g_launches;
   k_xpass_inv_reduce<T><<<grd, kThreads, sm, s>>>(g, P, pl, grid, group_start, col_v, scale, out_real,
-                                                   out_cplx, accumulate, nchunk, ngrp, scratch);
+                                                   out_cplx, accumulate, nchunk, ngrp, scratch, col_v2);
   if (ngrp > 1) {
     const size_t n = (size_t)g.N3 * ngroups;
     ++g_launches;
@@ -547,10 +570,10 @@ cudaError_t fft_set_smem_limits() {
                                     const FftPlan&, cpx<T>*, const T*, const int*, int);                 \
   template void launch_xpass_prod_fwd<T>(cudaStream_t, const Geometry&, const Prec<T>&, const FftPlan&,  \
                                          const cpx<T>*, int, const cpx<T>*, int, int, const int*,        \
-                                         const int*, cpx<T>*, int);                                      \
+                                         const int*, cpx<T>*, int, const int*, const int*);              \
   template void launch_xpass_inv_reduce<T>(cudaStream_t, const Geometry&, const Prec<T>&,                \
                                            const FftPlan&, const cpx<T>*, const int*, const int*, int,   \
-                                           double, T*, cpx<T>*, int, cpx<T>*, size_t, int);              \
+                                           double, T*, cpx<T>*, int, cpx<T>*, size_t, int, const int*);  \
   template cudaError_t fft_set_smem_limits<T>();
 
 GW_INST(double)

@@ -661,6 +661,67 @@ void launch_add_conv_sym(cudaStream_t s, int npw, int ncol, const cpx<T>* d, dou
   k_add_conv_sym<T><<<g, kLT, 0, s>>>((size_t)npw, d, x, active, neg);
 }
 
+// Two columns that are real in real space in one complex vector:
+//   out[j](G) = x[ia[j]](G) + i x[ib[j]](G)   (ib[j] < 0: the first alone)
+__global__ void k_pack_pairs(size_t npw, const double2* __restrict__ x, const int* __restrict__ ia,
+                             const int* __restrict__ ib, const int* __restrict__ active, double2* __restrict__ out) {
+  const int j = blockIdx.y;
+  if (active && !active[j]) return;
+  const int a = ia[j], b = ib[j];
+  for (size_t G = blockIdx.x * (size_t)blockDim.x + threadIdx.x; G < npw; G += (size_t)gridDim.x * blockDim.x) {
+    const double2 u = x[(size_t)a * npw + G];
+    const double2 v = (b >= 0) ? x[(size_t)b * npw + G] : make_double2(0.0, 0.0);
+    out[(size_t)j * npw + G] = make_double2(u.x - v.y, u.y + v.x);
+  }
+}
+
+void launch_pack_pairs(cudaStream_t s, int npw, int npair, const double2* x, const int* ia, const int* ib,
+                       const int* active, double2* out) {
+  dim3 g((npw + kLT - 1) / kLT, npair);
+  ++g_launches;
+  k_pack_pairs<<<g, kLT, 0, s>>>((size_t)npw, x, ia, ib, active, out);
+}
+
+// The two parts of a packed transform Y_j = F(f_a) + i F(f_b) of real fields:
+//   out[ia[j]](G) = (Y_j(G) + conj Y_j(-G)) / 2,  out[ib[j]](G) = (Y_j(G) - conj Y_j(-G)) / 2i,
+// plus (kin(G) - E_c) x_c(G) when kin is given (the kinetic part of (H - E) x).
+__global__ void k_unpack_pairs(size_t npw, const double2* __restrict__ Y, const int* __restrict__ neg,
+                               const int* __restrict__ ia, const int* __restrict__ ib, const int* __restrict__ active,
+                               const double* __restrict__ kin, const double2* __restrict__ E,
+                               const double2* __restrict__ x, double2* __restrict__ out) {
+  const int j = blockIdx.y;
+  if (active && !active[j]) return;
+  const int a = ia[j], b = ib[j];
+  for (size_t G = blockIdx.x * (size_t)blockDim.x + threadIdx.x; G < npw; G += (size_t)gridDim.x * blockDim.x) {
+    const double2 y1 = Y[(size_t)j * npw + G];
+    const double2 yn = Y[(size_t)j * npw + neg[G]];
+    double2 o0 = make_double2(0.5 * (y1.x + yn.x), 0.5 * (y1.y - yn.y));
+    double2 o1 = make_double2(0.5 * (y1.y + yn.y), -0.5 * (y1.x - yn.x));
+    if (kin) {
+      const double2 xa = x[(size_t)a * npw + G];
+      const double dr = kin[G] - E[a].x, di = -E[a].y;
+      o0.x += dr * xa.x - di * xa.y;
+      o0.y += dr * xa.y + di * xa.x;
+      if (b >= 0) {
+        const double2 xb = x[(size_t)b * npw + G];
+        const double er = kin[G] - E[b].x, ei = -E[b].y;
+        o1.x += er * xb.x - ei * xb.y;
+        o1.y += er * xb.y + ei * xb.x;
+      }
+    }
+    out[(size_t)a * npw + G] = o0;
+    if (b >= 0) out[(size_t)b * npw + G] = o1;
+  }
+}
+
+void launch_unpack_pairs(cudaStream_t s, int npw, int npair, const double2* Y, const int* neg, const int* ia,
+                         const int* ib, const int* active, const double* kin, const double2* E, const double2* x,
+                         double2* out) {
+  dim3 g((npw + kLT - 1) / kLT, npair);
+  ++g_launches;
+  k_unpack_pairs<<<g, kLT, 0, s>>>((size_t)npw, Y, neg, ia, ib, active, kin, E, x, out);
+}
+
 // out[c] = max_G |b(G) - conj b(-G)|, out[ncol + c] = max_G |b(G)| (one block per column)
 __global__ void __launch_bounds__(kLT) k_sym_check(int npw, const double2* __restrict__ b, const int* __restrict__ neg,
                                                    double* __restrict__ out, int ncol) {

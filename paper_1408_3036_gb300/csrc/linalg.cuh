@@ -90,6 +90,14 @@ void launch_add_conv(cudaStream_t s, int npw, int ncol, const cpx<T>* d, double2
 template <typename T>
 void launch_add_conv_sym(cudaStream_t s, int npw, int ncol, const cpx<T>* d, double2* x, const int* active,
                          const int* neg);
+// Packed pairs of real-in-real-space columns (see kernels_linalg.cu):
+// out[j] = x[ia[j]] + i x[ib[j]]; and the inverse split of a transform of such
+// a pair, optionally adding (kin - E_c) x_c.
+void launch_pack_pairs(cudaStream_t s, int npw, int npair, const double2* x, const int* ia, const int* ib,
+                       const int* active, double2* out);
+void launch_unpack_pairs(cudaStream_t s, int npw, int npair, const double2* Y, const int* neg, const int* ia,
+                         const int* ib, const int* active, const double* kin, const double2* E, const double2* x,
+                         double2* out);
 // out[c] = max |b(G) - conj b(-G)|, out[ncol + c] = max |b(G)| per column
 void launch_sym_check(cudaStream_t s, int npw, int ncol, const double2* b, const int* neg, double* out);
 void launch_defl_scale(cudaStream_t s, double2* coef, const double* eps, const double2* E, int ndef, int ncol,

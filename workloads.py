@@ -122,6 +122,20 @@ def block_freq(attempt=0):
     return Workload("block_freq", [cell], omegas, starts, 60, blk=8)
 
 
+def block_freq_slice(attempt=0):
+    """Reduced slice of the block complex-frequency workload for oracle
+    parity: its structure (24 wells, D=-3, sigma=0.8; N_occ=64; blocks of 8;
+    omega = U(0,2) + 0.1i) on a cell the oracle diagonalises densely --
+    L=16, 32^3, 5 Ha (2109 plane waves); 2 frequencies, 2 block steps."""
+    rng = _rng(7, attempt)
+    L = 16.0
+    centres = rng.uniform(0.0, L, size=(24, 3))
+    cell = Cell(L, 32, 5.0, 64, centres, -3.0, 0.8)
+    starts = [_starts(rng, cell.ng, 8)]
+    omegas = rng.uniform(0.0, 2.0, size=2) + 0.1j
+    return Workload("block_freq_slice", [cell], omegas, starts, 2, blk=8)
+
+
 ALLOWED_N = (24, 30, 32, 36, 40, 45, 48)
 
 
