@@ -275,9 +275,19 @@ gw_status gw_grad_vloc_basis(gw_ctx* ctx, const double* phi, const double* basis
  *          iterations of its slowest column)
  *   out[8] CTAs of the last persistent CG launch, out[9] its cluster size
  *          (0: the grid-wide cooperative kernel)
- *   n: entries wanted (<= 10)
+ *   out[10] CUDA-graph replays of SQMR iterations in the last SQMR solve
+ *   n: entries wanted (<= 11)
  */
 gw_status gw_stats(const gw_ctx* ctx, double* out, int n);
+
+/*
+ * gw_set_graphs -- on (default 1): the ten launches of one simplified-QMR
+ * iteration (the transform passes of H, the projector, the four update
+ * steps) are captured once per solve into a CUDA graph and replayed every
+ * iteration; 0: launched one by one.  Same arithmetic either way; a stream
+ * that cannot be captured falls back to direct launches.
+ */
+gw_status gw_set_graphs(gw_ctx* ctx, int on);
 
 /*
  * gw_set_solver -- Sternheimer solver controls (0 or negative keeps a value):

@@ -31,7 +31,7 @@ EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "
            "gw_epsinv_elements_noalloc", "gw_apply_chi0_c", "gw_apply_eps_c", "gw_block_lanczos",
            "gw_epsinv_block", "gw_batch_setup", "gw_batch_size", "gw_batch_cell", "gw_batch_lanczos",
            "gw_batch_last_error", "gw_batch_destroy", "gw_set_operator", "gw_epsinv_split", "gw_sigma_p", "gw_recycle_eps", "gw_sigma_c",
-           "gw_set_cg_kernel", "gw_grad_vloc_basis")
+           "gw_set_cg_kernel", "gw_grad_vloc_basis", "gw_set_graphs")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
                    "refine_fp64", "persistent_cg")
 
@@ -75,6 +75,7 @@ def load(path=LIB_PATH):
         "gw_set_solver": (I, [P, D, D, I, I]),
         "gw_set_precond": (I, [P, I]),
         "gw_set_cg_kernel": (I, [P, I, ctypes.c_longlong]),
+        "gw_set_graphs": (I, [P, I]),
         "gw_set_operator": (I, [P, I]),
         "gw_epsinv_split": (I, [P, P, I, P, P, P, I, P, P, P, I, D, P, I]),
         "gw_sigma_p": (I, [P, P, D, D, I, P, P, P, I, P, P, I, I]),
@@ -307,11 +308,16 @@ def gw_grad_vloc_basis(ctx, phi, basis, alpha, beta, k, s, grad, prec=GW_FP64):
 
 
 def gw_stats(ctx):
-    out = np.zeros(10)
-    _check(ctx, load().gw_stats(ctx, out.ctypes.data, 10))
+    out = np.zeros(11)
+    _check(ctx, load().gw_stats(ctx, out.ctypes.data, 11))
     return dict(columns=out[0], max_iter=out[1], mean_iter=out[2], outer=out[3], max_residual=out[4],
                 h_columns=out[5], launches=int(out[6]), launch_iterations=int(out[7]), launch_ctas=int(out[8]),
-                cluster=int(out[9]))
+                cluster=int(out[9]), graph_replays=int(out[10]))
+
+
+def gw_set_graphs(ctx, on):
+    """SQMR iterations replayed from a captured CUDA graph (1, default) or launched one by one (0)."""
+    _check(ctx, load().gw_set_graphs(ctx, int(on)))
 
 
 def gw_set_solver(ctx, tol=0.0, tol_inner=0.0, max_iter=0, max_outer=0):
@@ -523,6 +529,9 @@ class Cell:
 
     def set_precond(self, kind):
         gw_set_precond(self.ctx, kind)
+
+    def set_graphs(self, on):
+        gw_set_graphs(self.ctx, on)
 
     def set_cg_kernel(self, kind, wait_limit=0):
         gw_set_cg_kernel(self.ctx, kind, wait_limit)

@@ -45,6 +45,8 @@ struct gw_ctx {
   double anorm = 1.0;           // bound on |H - E| used by the backward error
   int cg_kernel = GW_CG_PERSISTENT;   // kernel of the CG passes (gw_set_cg_kernel)
   int maxplane = 0;                   // most sphere entries in one plane i0
+  bool use_graphs = true;             // SQMR iterations replayed from a captured CUDA graph
+  long long graph_replays = 0;        // replays in the last SQMR solve
   unsigned long long wait_limit = 1ull << 24;   // spins of one device wait before GW_E_TIMEOUT
   long long pcg_iters = 0;      // iterations run by persistent launches
   int pcg_launch_blocks = 0;
@@ -535,8 +537,12 @@ gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E,
   dots.cnt = ctx->work.cnt_d;
   dots.coef = ctx->work.coef;
   const int check = 8;
-  for (int it = 0; it < ctx->max_iter; ++it) {
-    // t = P_c (H - E) q
+  // One iteration: t = P_c (H - E) q, then the four update steps.  Its ten
+  // launches read all per-column state from device memory, so the same
+  // sequence serves every iteration: it is captured once into a CUDA graph
+  // and replayed (one launch instead of ten per iteration); the direct
+  // launches remain for a stream that cannot be captured.
+  auto iteration = [&]() {
     launch_zpass<T>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, grid, q, nullptr, nullptr, nullptr, nullptr, st.active,
                     nullptr, nullptr, ncol);
     launch_ypass<T>(ctx->st, 1, 1, 0, g, P, ctx->plan, grid, st.active, ncol, 0);
@@ -548,8 +554,37 @@ gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E,
                           nullptr);
     for (int step = 1; step <= 4; ++step)
       launch_qmr<T>(ctx->st, step, npw, ncol, b64, x, r, q, dd, tt, neg, outer_active, ctx->work, st, P.kin,
-                    tol * tol,
-                    ctx->max_iter);
+                    tol * tol, ctx->max_iter);
+  };
+  struct ExecGuard {
+    cudaGraphExec_t e = nullptr;
+    ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
+  } guard;
+  cudaGraphExec_t& exec = guard.e;
+  unsigned long long per_iter = 0;
+  ctx->graph_replays = 0;
+  if (ctx->use_graphs) {
+    const unsigned long long l0 = g_launches;
+    if (cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      iteration();
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamEndCapture(ctx->st, &graph) == cudaSuccess && graph) {
+        if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+        cudaGraphDestroy(graph);
+      }
+    }
+    cudaGetLastError();
+    per_iter = g_launches - l0;
+    g_launches = l0;           // nothing ran during the capture
+  }
+  for (int it = 0; it < ctx->max_iter; ++it) {
+    if (exec) {
+      CK(cudaGraphLaunch(exec, ctx->st));
+      g_launches += per_iter;
+      ++ctx->graph_replays;
+    } else {
+      iteration();
+    }
     if ((it % check) == check - 1 || it == ctx->max_iter - 1) {
       CK(cudaMemcpyAsync(ctx->host_pin, st.n_done, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
       TRY(sync(ctx, "qmr_solve"));
@@ -2636,6 +2671,13 @@ gw_status gw_stats(const gw_ctx* ctx, double* out, int n) {
   if (n > 7) out[7] = (double)ctx->pcg_iters;
   if (n > 8) out[8] = (double)ctx->pcg_launch_blocks;
   if (n > 9) out[9] = (double)ctx->pcg_cluster;
+  if (n > 10) out[10] = (double)ctx->graph_replays;
+  return GW_OK;
+}
+
+gw_status gw_set_graphs(gw_ctx* ctx, int on) {
+  if (!ctx) return GW_E_ARG;
+  ctx->use_graphs = (on != 0);
   return GW_OK;
 }
 
