@@ -280,6 +280,24 @@ gw_status gw_grad_vloc_basis(gw_ctx* ctx, const double* phi, const double* basis
  */
 gw_status gw_stats(const gw_ctx* ctx, double* out, int n);
 
+/* Solver of purely imaginary frequencies omega = i w (gw_set_imaginary_route). */
+typedef enum {
+  GW_IMAG_SQMR = 0,      /* the pair (H - e_v -/+ i w) x = b by simplified QMR (default) */
+  GW_IMAG_SQUARED = 1    /* Eq. P2+: ((H - e_v)^2 + w^2) y = 2 (H - e_v) b by CG */
+} gw_imag_route;
+
+/*
+ * gw_set_imaginary_route -- how gw_apply_chi0(_c), gw_apply_eps(_c) and the
+ * Lanczos entries solve at a purely imaginary frequency i w.  GW_IMAG_SQUARED
+ * solves the squared Hermitian positive definite system of Eq. P2+ (Sec.
+ * "Avoiding summations"), whose solution is x^- + x^+ directly (Eq. fv): one
+ * solve per occupied state instead of two, two H applications per CG
+ * iteration, the kinetic preconditioner squared; P_c between the two
+ * applications, and the FP64 refinement residual of the squared system.
+ * Frequencies with a real part keep Eq. P2.  GW_E_ARG for another value.
+ */
+gw_status gw_set_imaginary_route(gw_ctx* ctx, int route);
+
 /*
  * gw_set_graphs -- on (default 1): the ten launches of one simplified-QMR
  * iteration (the transform passes of H, the projector, the four update

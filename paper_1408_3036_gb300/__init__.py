@@ -23,6 +23,7 @@ GW_FP64, GW_MIXED = 0, 1
 GW_COULOMB_TRUNCATED, GW_COULOMB_BARE = 0, 1
 GW_OP_STERNHEIMER, GW_OP_MODEL = 0, 1
 GW_CG_PERSISTENT, GW_CG_MULTI_LAUNCH, GW_CG_CLUSTER = 0, 1, 2
+GW_IMAG_SQMR, GW_IMAG_SQUARED = 0, 1
 STATUS = {0: "GW_OK", 1: "GW_E_ARG", 2: "GW_E_CUDA", 3: "GW_E_NOMEM", 4: "GW_E_NOCONV",
           5: "GW_E_BREAKDOWN", 6: "GW_E_TIMEOUT", 7: "GW_E_NONFINITE", 8: "GW_E_UNSUPPORTED"}
 EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "gw_apply_chi0",
@@ -31,7 +32,7 @@ EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "
            "gw_epsinv_elements_noalloc", "gw_apply_chi0_c", "gw_apply_eps_c", "gw_block_lanczos",
            "gw_epsinv_block", "gw_batch_setup", "gw_batch_size", "gw_batch_cell", "gw_batch_lanczos",
            "gw_batch_last_error", "gw_batch_destroy", "gw_set_operator", "gw_epsinv_split", "gw_sigma_p", "gw_recycle_eps", "gw_sigma_c",
-           "gw_set_cg_kernel", "gw_grad_vloc_basis", "gw_set_graphs")
+           "gw_set_cg_kernel", "gw_grad_vloc_basis", "gw_set_graphs", "gw_set_imaginary_route")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
                    "refine_fp64", "persistent_cg")
 
@@ -76,6 +77,7 @@ def load(path=LIB_PATH):
         "gw_set_precond": (I, [P, I]),
         "gw_set_cg_kernel": (I, [P, I, ctypes.c_longlong]),
         "gw_set_graphs": (I, [P, I]),
+        "gw_set_imaginary_route": (I, [P, I]),
         "gw_set_operator": (I, [P, I]),
         "gw_epsinv_split": (I, [P, P, I, P, P, P, I, P, P, P, I, D, P, I]),
         "gw_sigma_p": (I, [P, P, D, D, I, P, P, P, I, P, P, I, I]),
@@ -315,6 +317,11 @@ def gw_stats(ctx):
                 cluster=int(out[9]), graph_replays=int(out[10]))
 
 
+def gw_set_imaginary_route(ctx, route):
+    """GW_IMAG_SQMR (default) or GW_IMAG_SQUARED (Eq. P2+) at purely imaginary frequencies."""
+    _check(ctx, load().gw_set_imaginary_route(ctx, int(route)))
+
+
 def gw_set_graphs(ctx, on):
     """SQMR iterations replayed from a captured CUDA graph (1, default) or launched one by one (0)."""
     _check(ctx, load().gw_set_graphs(ctx, int(on)))
@@ -529,6 +536,9 @@ class Cell:
 
     def set_precond(self, kind):
         gw_set_precond(self.ctx, kind)
+
+    def set_imaginary_route(self, route):
+        gw_set_imaginary_route(self.ctx, route)
 
     def set_graphs(self, on):
         gw_set_graphs(self.ctx, on)

@@ -46,6 +46,7 @@ struct gw_ctx {
   int cg_kernel = GW_CG_PERSISTENT;   // kernel of the CG passes (gw_set_cg_kernel)
   int maxplane = 0;                   // most sphere entries in one plane i0
   bool use_graphs = true;             // SQMR iterations replayed from a captured CUDA graph
+  int imag_route = GW_IMAG_SQMR;      // solver of purely imaginary frequencies (gw_set_imaginary_route)
   long long graph_replays = 0;        // replays in the last SQMR solve
   unsigned long long wait_limit = 1ull << 24;   // spins of one device wait before GW_E_TIMEOUT
   long long pcg_iters = 0;      // iterations run by persistent launches
@@ -317,7 +318,8 @@ gw_status h_apply_sym(gw_ctx* ctx, const double2* x, int ncol, const double2* E,
 // ---------------------------------------------------------------------------
 template <typename T>
 gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, const int* outer_active,
-                   cpx<T>* x, double tol, const double* rr_abs, const double* tk, long long* it_sum, int* it_max) {
+                   cpx<T>* x, double tol, const double* rr_abs, const double* tk, long long* it_sum, int* it_max,
+                   const double* w2 = nullptr) {
   const int npw = ctx->npw;
   const std::string t = tname<T>();
   cpx<T>*r, *p, *Ap, *grid;
@@ -343,8 +345,12 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
   TRY(getbuf(ctx, "cg_itbest", ncol, &st.it_best));
   st.rr_abs = rr_abs;
   st.tk = tk;
+  st.ppow = w2 ? 2 : 1;        // (H - E)^2 + w^2: the kinetic preconditioner squared
+  cpx<T>* Ap2 = nullptr;
+  if (w2) TRY(getbuf(ctx, "cg_Ap2" + t, (size_t)ncol * npw, &Ap2));
   TRY(ensure_work(ctx, ncol));
   CK(cudaMemsetAsync(st.cnt, 0, ncol * sizeof(unsigned), ctx->st));
+  CK(cudaMemsetAsync(ctx->work.cnt_c, 0, ncol * sizeof(unsigned), ctx->st));
   CK(cudaMemsetAsync(st.n_done, 0, sizeof(int), ctx->st));
   auto& P = prec_of<T>(ctx);
   const Geometry& g = ctx->geo;
@@ -360,16 +366,34 @@ gw_status cg_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, 
   const int check = 8;
   for (int it = 0; it < ctx->max_iter; ++it) {
     PROF(PC_ZSCAT, launch_zpass<T>(ctx->st, Z_SCATTER_INV_PUPD, g, P, ctx->plan, grid, p, r, st.beta, nullptr,
-                                   nullptr, st.active, nullptr, nullptr, ncol, nullptr, tk));
+                                   nullptr, st.active, nullptr, nullptr, ncol, nullptr, tk, st.ppow));
     PROF(PC_YINV, launch_ypass<T>(ctx->st, 1, 1, 0, g, P, ctx->plan, grid, st.active, ncol, 0));
     PROF(PC_XH, launch_xpass_mul<T>(ctx->st, 1, 1, 1, g, P, ctx->plan, grid, P.vloc_s, st.active, ncol));
     PROF(PC_YFWD, launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, st.active, ncol, 0));
     PROF(PC_ZGATH, launch_zpass<T>(ctx->st, Z_GATHER_FWD_H, g, P, ctx->plan, grid, Ap, nullptr, nullptr, p, E,
                                    st.active, nullptr, nullptr, ncol, &dots));
+    if (w2) {
+      // Eq. P2+: A p = P_c (H - E) P_c (H - E) p + w^2 p, two H applications
+      PROF(PC_PROJ, launch_proj_update<T>(ctx->st, P.C, nproj(ctx), npw, Ap, ncol, st.active, ctx->work.coef,
+                                          ctx->work, nullptr, nullptr));
+      launch_zpass<T>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, grid, Ap, nullptr, nullptr, nullptr, nullptr,
+                      st.active, nullptr, nullptr, ncol);
+      launch_ypass<T>(ctx->st, 1, 1, 0, g, P, ctx->plan, grid, st.active, ncol, 0);
+      launch_xpass_mul<T>(ctx->st, 1, 1, 1, g, P, ctx->plan, grid, P.vloc_s, st.active, ncol);
+      launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, st.active, ncol, 0);
+      launch_zpass<T>(ctx->st, Z_GATHER_FWD_H, g, P, ctx->plan, grid, Ap2, nullptr, nullptr, Ap, E, st.active,
+                      nullptr, nullptr, ncol, &dots);
+      launch_proj_update<T>(ctx->st, P.C, nproj(ctx), npw, Ap2, ncol, st.active, ctx->work.coef, ctx->work,
+                            nullptr, nullptr);
+      launch_sq_shift<T>(ctx->st, npw, ncol, Ap2, p, w2, st.active, ctx->work, pap);
+      PROF(PC_CGUPD, launch_cg_update<T>(ctx->st, npw, ncol, x, r, p, Ap2, pap, ctx->work, st, P.kin, tol2,
+                                             ctx->max_iter));
+    } else {
     PROF(PC_PROJ, launch_proj_update<T>(ctx->st, P.C, nproj(ctx), npw, Ap, ncol, st.active, ctx->work.coef,
                                         ctx->work, p, pap));
     PROF(PC_CGUPD, launch_cg_update<T>(ctx->st, npw, ncol, x, r, p, Ap, pap, ctx->work, st, P.kin, tol2,
                                            ctx->max_iter));
+    }
     if ((it % check) == check - 1 || it == ctx->max_iter - 1) {
       CK(cudaMemcpyAsync(ctx->host_pin, st.n_done, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
       TRY(sync(ctx, "cg_solve"));
@@ -618,7 +642,8 @@ gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E,
 template <typename U>
 gw_status inner_solve(gw_ctx* ctx, bool qmr, int ncol, const double2* r64, const double2* E, const int* oact,
                       cpx<U>* d, double tol_in, const double* rra, const double* tk, bool sym, long long* it_sum,
-                      int* it_max) {
+                      int* it_max, const double* w2 = nullptr) {
+  if (w2) return cg_solve<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, tk, it_sum, it_max, w2);
   if (qmr) return qmr_solve<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, tk, it_sum, it_max);
   if (ncol <= kPersistentMaxCols && ctx->cg_kernel != GW_CG_MULTI_LAUNCH) {
     bool ran = false;
@@ -628,9 +653,11 @@ gw_status inner_solve(gw_ctx* ctx, bool qmr, int ncol, const double2* r64, const
   return cg_solve<U>(ctx, ncol, r64, E, oact, d, tol_in, rra, tk, it_sum, it_max);
 }
 
+// w2 (optional, device [ncol]): solve the squared system of Eq. P2+,
+// (P_c (H - E) P_c)^2 x + w2 x = b, by CG (w2max: the largest w2, for |A|).
 template <typename T>
 gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, double2* x64, bool qmr = false,
-                const double* tk = nullptr) {
+                const double* tk = nullptr, const double* w2 = nullptr, double w2max = 0.0) {
   const int npw = ctx->npw;
   const bool mixed = !std::is_same<T, double>::value;
   const double tol = mixed ? ctx->tol_mixed : ctx->tol;
@@ -703,12 +730,12 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
     if (esc) {
       if (!d64) TRY(getbuf(ctx, "sv_d64", (size_t)ncol * npw, &d64));
       TRY(inner_solve<double>(ctx, qmr, ncol, r64, E, oact, reinterpret_cast<cpx<double>*>(d64),
-                              std::max(1e2 * ctx->tol, 1e-11), rra, tk, sym, &it_sum, &it_max));
+                              std::max(1e2 * ctx->tol, 1e-11), rra, tk, sym, &it_sum, &it_max, w2));
       if (sym) launch_add_conv_sym<double>(ctx->st, npw, ncol, reinterpret_cast<cpx<double>*>(d64), x64, oact,
                                            ctx->geo.sph_neg);
       else launch_add_conv<double>(ctx->st, npw, ncol, reinterpret_cast<cpx<double>*>(d64), x64, oact);
     } else {
-      TRY(inner_solve<T>(ctx, qmr, ncol, r64, E, oact, d, tol_in, rra, tk, sym, &it_sum, &it_max));
+      TRY(inner_solve<T>(ctx, qmr, ncol, r64, E, oact, d, tol_in, rra, tk, sym, &it_sum, &it_max, w2));
       if (sym) launch_add_conv_sym<T>(ctx->st, npw, ncol, d, x64, oact, ctx->geo.sph_neg);
       else launch_add_conv<T>(ctx->st, npw, ncol, d, x64, oact);
     }
@@ -717,7 +744,26 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
                                  cdef, ctx->work, nullptr, nullptr);
     // r64 = P_c (b - (H - E) x64): C^H (H - E) x64 from the dots fused into the
     // last transform pass, C^H b computed once per solve
-    {
+    if (w2) {
+      // Eq. P2+ residual in FP64: ax = P_c (H - E) P_c (H - E) x + w2 x
+      const int pa = prof_begin(ctx, PC_REFINE);
+      double2* ax1;
+      TRY(getbuf(ctx, "sv_ax1", (size_t)ncol * npw, &ax1));
+      GatherDots dots;
+      dots.C = ctx->P64.C;
+      dots.nocc = ctx->nocc;
+      dots.ncol = ncol;
+      dots.part = ctx->work.part_d;
+      dots.cnt = ctx->work.cnt_d;
+      dots.coef = cax;
+      TRY(h_apply<double>(ctx, x64, ncol, E, oact, ax1, &dots));
+      launch_proj_update<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, ax1, ncol, oact, cax, ctx->work, nullptr,
+                                 nullptr);
+      TRY(h_apply<double>(ctx, ax1, ncol, E, oact, ax, &dots));
+      launch_sq_shift<double>(ctx->st, npw, ncol, ax, x64, w2, oact, ctx->work, nullptr);
+      launch_gram<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, ax, ncol, ctx->work, cax);
+      prof_end(ctx, PC_REFINE, pa);
+    } else {
       const int pa = prof_begin(ctx, PC_REFINE);
       if (sym) {
         // two real-in-real-space columns per FP64 transform
@@ -744,9 +790,10 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
     TRY(sync(ctx, "solve"));
     if (hprev.empty()) hprev = hb;
     int nact = 0;
+    const double anorm = w2 ? ctx->anorm * ctx->anorm + w2max : ctx->anorm;
     for (int c = 0; c < ncol; ++c) {
       if (!act[c]) continue;
-      const double scale = ctx->anorm * std::sqrt(hx[c]) + std::sqrt(hb[c]);
+      const double scale = anorm * std::sqrt(hx[c]) + std::sqrt(hb[c]);
       const double be = scale > 0 ? std::sqrt(hr[c]) / scale : 0.0;
       if (!std::isfinite(be)) return fail(ctx, GW_E_NONFINITE, "non-finite Sternheimer residual");
       habs[c] = 0.01 * tol * tol * scale * scale;
@@ -763,7 +810,7 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
     // and by the accuracy of the occupied states)
     double worst = 0.0;
     for (int c = 0; c < ncol; ++c) {
-      const double scale = ctx->anorm * std::sqrt(hx[c]) + std::sqrt(hb[c]);
+      const double scale = anorm * std::sqrt(hx[c]) + std::sqrt(hb[c]);
       if (act[c] && scale > 0) worst = std::max(worst, std::sqrt(hr[c]) / scale);
     }
     done = (nact == 0) || (outer > 0 && worst > 0.5 * prev_worst && worst <= 10.0 * tol);
@@ -790,9 +837,10 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
   if (!done) {
     int wc = -1;
     double wbe = -1.0;
+    const double anorm = w2 ? ctx->anorm * ctx->anorm + w2max : ctx->anorm;
     for (int c = 0; c < ncol; ++c) {
       if (!act[c]) continue;
-      const double scale = ctx->anorm * std::sqrt(hx[c]) + std::sqrt(hb[c]);
+      const double scale = anorm * std::sqrt(hx[c]) + std::sqrt(hb[c]);
       const double be = scale > 0 ? std::sqrt(hr[c]) / scale : 0.0;
       if (be > wbe) { wbe = be; wc = c; }
     }
@@ -966,29 +1014,45 @@ gw_status chi0_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, const std::
   double2* sol64;
   const int nsol = nom * nb * nocc;
   TRY(getbuf(ctx, "sol64", (size_t)nsol * npw, &sol64));
-  // -- solver columns
-  std::vector<int> src, s0, s1;
+  // -- solver columns: the frequencies solved as Eq. P2 (CG at 0, SQMR
+  // otherwise) first, then the purely imaginary ones when the squared route of
+  // Eq. P2+ is selected (one Hermitian positive definite solve per state)
+  std::vector<int> src, s0(nsol, -1), s1(nsol, -1);
   std::vector<double2> E;
-  std::vector<double> tk;
+  std::vector<double> tk, w2v;
   bool qmr = false;
-  for (int o = 0; o < nom; ++o) {
-    const bool zero = (omega[o].x == 0.0 && omega[o].y == 0.0);
-    qmr |= !zero;
-    const int ns = zero ? 1 : 2;
-    for (int b = 0; b < nb; ++b)
-      for (int v = 0; v < nocc; ++v) {
-        const int first = (int)src.size();
-        for (int sg = 0; sg < ns; ++sg) {
-          src.push_back(b * nocc + v);
-          const double sgn = (sg == 0) ? 1.0 : -1.0;     // x^-: H - e_v - w;  x^+: H - e_v + w
-          E.push_back(make_double2(ctx->eps[v] + sgn * omega[o].x, sgn * omega[o].y));
-          tk.push_back(ctx->tkin[v]);
+  const bool sq_route = ctx->imag_route == GW_IMAG_SQUARED;
+  auto squared = [&](int o) { return sq_route && omega[o].x == 0.0 && omega[o].y != 0.0; };
+  int nstd = 0;
+  double w2max = 0.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int o = 0; o < nom; ++o) {
+      if (squared(o) != (pass == 1)) continue;
+      const bool zero = (omega[o].x == 0.0 && omega[o].y == 0.0);
+      if (pass == 0) qmr |= !zero;
+      const int ns = (zero || pass == 1) ? 1 : 2;
+      for (int b = 0; b < nb; ++b)
+        for (int v = 0; v < nocc; ++v) {
+          const int k = (o * nb + b) * nocc + v;
+          const int first = (int)src.size();
+          for (int sg = 0; sg < ns; ++sg) {
+            src.push_back(b * nocc + v);
+            const double sgn = (sg == 0) ? 1.0 : -1.0;     // x^-: H - e_v - w;  x^+: H - e_v + w
+            if (pass == 0) E.push_back(make_double2(ctx->eps[v] + sgn * omega[o].x, sgn * omega[o].y));
+            else E.push_back(make_double2(ctx->eps[v], 0.0));
+            tk.push_back(ctx->tkin[v]);
+            if (pass == 1) {
+              w2v.push_back(omega[o].y * omega[o].y);
+              w2max = std::max(w2max, omega[o].y * omega[o].y);
+            }
+          }
+          s0[k] = first;
+          s1[k] = ns == 2 ? first + 1 : -1;
         }
-        s0.push_back(first);
-        s1.push_back(ns == 2 ? first + 1 : -1);
-      }
+    }
+    if (pass == 0) nstd = (int)src.size();
   }
-  const int ncol = (int)src.size();
+  const int ncol = (int)src.size(), nsq = ncol - nstd;
   int *dsrc, *ds0, *ds1;
   double2* dE;
   TRY(upload_table(ctx, "col_src", src, &dsrc));
@@ -1002,8 +1066,22 @@ gw_status chi0_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, const std::
   TRY(getbuf(ctx, "xcol", (size_t)ncol * npw, &xcol));
   launch_gather_rows<double, double>(ctx->st, npw, ncol, rhs64, dsrc, bcol);
   gw_status sv = GW_OK;
-  SOFT(sv, (solve<S>(ctx, ncol, bcol, dE, xcol, qmr, dtk)));
-  // -- combine: x^- + x^+, or 2 x at omega = 0 (x^- = x^+)
+  if (nstd > 0) SOFT(sv, (solve<S>(ctx, nstd, bcol, dE, xcol, qmr, dtk)));
+  if (nsq > 0) {
+    // Eq. P2+: ((H - e_v)^2 + w^2) y = 2 (H - e_v) b gives y = x^- + x^+ at
+    // omega = i w; solved for x = y / 2 from the right-hand side P_c (H - e_v) b
+    double2* bs = bcol + (size_t)nstd * npw;
+    double2* hb;
+    double* dw2;
+    TRY(getbuf(ctx, "sq_hb", (size_t)nsq * npw, &hb));
+    TRY(upload(ctx, "sq_w2", w2v, &dw2));
+    TRY(h_apply<double>(ctx, bs, nsq, dE + nstd, nullptr, hb, nullptr));
+    launch_proj<double>(ctx->st, ctx->P64.C, nocc, npw, hb, nsq, nullptr, ctx->work, nullptr, nullptr);
+    CK(cudaMemcpyAsync(bs, hb, (size_t)nsq * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
+    SOFT(sv, (solve<S>(ctx, nsq, bs, dE + nstd, xcol + (size_t)nstd * npw, false, dtk ? dtk + nstd : nullptr, dw2,
+                       w2max)));
+  }
+  // -- combine: x^- + x^+, or 2 x at omega = 0 (x^- = x^+) and on the squared route
   launch_combine(ctx->st, npw, nsol, xcol, ds0, ds1, 1.0, 2.0, sol64);
   TRY(chi0_reduce(ctx, sol64, nb, nom, dn, dn_cplx));
   return sv;
@@ -2672,6 +2750,13 @@ gw_status gw_stats(const gw_ctx* ctx, double* out, int n) {
   if (n > 8) out[8] = (double)ctx->pcg_launch_blocks;
   if (n > 9) out[9] = (double)ctx->pcg_cluster;
   if (n > 10) out[10] = (double)ctx->graph_replays;
+  return GW_OK;
+}
+
+gw_status gw_set_imaginary_route(gw_ctx* ctx, int route) {
+  if (!ctx) return GW_E_ARG;
+  if (route != GW_IMAG_SQMR && route != GW_IMAG_SQUARED) return fail(ctx, GW_E_ARG, "unknown imaginary-frequency route");
+  ctx->imag_route = route;
   return GW_OK;
 }
 

@@ -189,7 +189,8 @@ template <typename T>
 void launch_zpass(cudaStream_t s, int mode, const Geometry& g, const Prec<T>& P, const FftPlan& pl,
                   cpx<T>* grid, cpx<T>* sph, const cpx<T>* sph_r, const double* beta,
                   const cpx<T>* sph_p, const double2* E, const int* active, const T* real_in,
-                  T* real_out, int ncol, const GatherDots* dots = nullptr, const double* tk = nullptr);
+                  T* real_out, int ncol, const GatherDots* dots = nullptr, const double* tk = nullptr,
+                  int ppow = 1);
 template <typename T>
 void launch_ypass(cudaStream_t s, int inverse, int pruned_in, int pruned_out, const Geometry& g,
                   const Prec<T>& P, const FftPlan& pl, cpx<T>* grid, const int* active, int ncol, int full_planes);

@@ -44,7 +44,8 @@ __global__ void __launch_bounds__(kThreads)
 k_zpass(int mode, Geometry g, Prec<T> P, FftPlan pl, cpx<T>* __restrict__ grid,
         cpx<T>* __restrict__ sph, const cpx<T>* __restrict__ sph_r, const double* __restrict__ beta,
         const cpx<T>* __restrict__ sph_p, const double2* __restrict__ E, const int* __restrict__ active,
-        const T* __restrict__ real_in, T* __restrict__ real_out, GatherDots dots, const double* __restrict__ tk) {
+        const T* __restrict__ real_in, T* __restrict__ real_out, GatherDots dots, const double* __restrict__ tk,
+        int ppow) {
   using V = cpx<T>;
   extern __shared__ unsigned char smem_raw[];
   const int N = g.N, LD = N + 1;
@@ -78,8 +79,9 @@ k_zpass(int mode, Geometry g, Prec<T> P, FftPlan pl, cpx<T>* __restrict__ grid,
       V val;
       if (mode == Z_SCATTER_INV_PUPD) {
         V rv = sph_r[scol + s];
-        if (rtk != (T)0) {                           // z = K r
-          const T k = tpa<T>(P.kin[s] * rtk);
+        if (rtk != (T)0) {                           // z = K r  (K^2 r for a squared operator)
+          T k = tpa<T>(P.kin[s] * rtk);
+          if (ppow == 2) k *= k;
           rv.x *= k;
           rv.y *= k;
         }
@@ -179,7 +181,7 @@ template <typename T>
 void launch_zpass(cudaStream_t s, int mode, const Geometry& g, const Prec<T>& P, const FftPlan& pl,
                   cpx<T>* grid, cpx<T>* sph, const cpx<T>* sph_r, const double* beta,
                   const cpx<T>* sph_p, const double2* E, const int* active, const T* real_in,
-                  T* real_out, int ncol, const GatherDots* dots, const double* tk) {
+                  T* real_out, int ncol, const GatherDots* dots, const double* tk, int ppow) {
   const bool disc_list = (mode == Z_SCATTER_INV || mode == Z_SCATTER_INV_PUPD || mode == Z_GATHER_FWD ||
                           mode == Z_GATHER_FWD_H);
   const int npen = disc_list ? g.npen : g.N2;
@@ -190,7 +192,7 @@ void launch_zpass(cudaStream_t s, int mode, const Geometry& g, const Prec<T>& P,
   GatherDots d;
   if (dots) d = *dots;
   k_zpass<T><<<grd, kThreads, sm, s>>>(mode, g, P, pl, grid, sph, sph_r, beta, sph_p, E, active,
-                                        real_in, real_out, d, tk);
+                                        real_in, real_out, d, tk, ppow);
 }
 
 // ---------------------------------------------------------------------------
@@ -563,7 +565,7 @@ cudaError_t fft_set_smem_limits() {
   template void launch_zpass<T>(cudaStream_t, int, const Geometry&, const Prec<T>&, const FftPlan&,      \
                                 cpx<T>*, cpx<T>*, const cpx<T>*, const double*, const cpx<T>*,           \
                                 const double2*, const int*, const T*, T*, int, const GatherDots*,        \
-                                const double*);                                                          \
+                                const double*, int);                                                          \
   template void launch_ypass<T>(cudaStream_t, int, int, int, const Geometry&, const Prec<T>&,            \
                                 const FftPlan&, cpx<T>*, const int*, int, int);                          \
   template void launch_xpass_mul<T>(cudaStream_t, int, int, int, const Geometry&, const Prec<T>&,        \

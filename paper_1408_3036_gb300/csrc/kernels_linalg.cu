@@ -230,6 +230,46 @@ void launch_grad_combine(cudaStream_t s, int n, const double* g1, const double* 
   k_grad_combine<<<nb, kLT, 0, s>>>(n, g1, g2, wgt, grad);
 }
 
+// Ap += w2[c] p (the shift of (H - E)^2 + w^2); optionally pap[c] = Re <p|Ap>
+// (FP64, deterministic two-level sum).  grid (nchunk, ncol)
+template <typename T>
+__global__ void __launch_bounds__(kLT)
+k_sq_shift(int npw, cpx<T>* __restrict__ Ap, const cpx<T>* __restrict__ p, const double* __restrict__ w2,
+           const int* __restrict__ active, double* __restrict__ partial, unsigned* __restrict__ cnt,
+           double* __restrict__ pap, int ncol) {
+  const int c = blockIdx.y;
+  if (active && !active[c]) return;
+  const T s2 = (T)w2[c];
+  const int g0 = blockIdx.x * kChunk, g1 = min(npw, g0 + kChunk);
+  double acc = 0.0;
+  for (int G = g0 + threadIdx.x; G < g1; G += blockDim.x) {
+    const size_t i = (size_t)c * npw + G;
+    const cpx<T> pv = p[i];
+    cpx<T> a = Ap[i];
+    a.x += s2 * pv.x;
+    a.y += s2 * pv.y;
+    Ap[i] = a;
+    acc += (double)(pv.x * a.x + pv.y * a.y);
+  }
+  if (!pap) return;
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ncol + c] = acc;
+  if (!last_block(&cnt[c], gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double q;
+    sum_records<1>(partial + c, gridDim.x, ncol, &q);
+    pap[c] = q;
+  }
+}
+
+template <typename T>
+void launch_sq_shift(cudaStream_t s, int npw, int ncol, cpx<T>* Ap, const cpx<T>* p, const double* w2,
+                     const int* active, Work& w, double* pap) {
+  dim3 g((npw + kChunk - 1) / kChunk, ncol);
+  ++g_launches;
+  k_sq_shift<T><<<g, kLT, 0, s>>>(npw, Ap, p, w2, active, w.part1, w.cnt_c, pap, ncol);
+}
+
 template <typename T>
 void launch_proj_update(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, int ncol,
                         const int* active, const double2* coef, Work& w, const cpx<T>* Pv, double* pap) {
@@ -247,6 +287,12 @@ void launch_proj_update(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<
 template <typename T>
 __device__ __forceinline__ T precond(const T* kin, const double* tk, int c, int G) {
   return tk ? tpa<T>(kin[G] * (T)(1.0 / tk[c])) : (T)1;
+}
+// The CG's preconditioner: K, or K^2 for the squared operator (H - E)^2 + w^2.
+template <typename T>
+__device__ __forceinline__ T precond_cg(const T* kin, const CgState& st, int c, int G) {
+  const T k = precond<T>(kin, st.tk, c, G);
+  return st.ppow == 2 ? k * k : k;
 }
 
 // init: x = 0, r = b (converted), rr = rr0 = |b|^2, rz = r^H K r, beta = -1 (first p = K r)
@@ -267,7 +313,7 @@ k_cg_init(int npw, const cpx<U>* __restrict__ b, cpx<T>* __restrict__ x, cpx<T>*
     const double2 bd = to_d(bv);
     const double n2 = bd.x * bd.x + bd.y * bd.y;
     acc += n2;
-    accz += (double)precond<T>(kin, st.tk, c, G) * n2;
+    accz += (double)precond_cg<T>(kin, st, c, G) * n2;
   }
   acc = block_sum(acc);
   accz = block_sum(accz);
@@ -319,7 +365,7 @@ k_cg_update(int npw, cpx<T>* __restrict__ x, cpx<T>* __restrict__ r, const cpx<T
     const double2 rd = to_d(rv);
     const double n2 = rd.x * rd.x + rd.y * rd.y;
     acc += n2;
-    accz += (double)precond<T>(kin, st.tk, c, G) * n2;
+    accz += (double)precond_cg<T>(kin, st, c, G) * n2;
   }
   acc = block_sum(acc);
   accz = block_sum(accz);
@@ -1118,6 +1164,8 @@ void launch_tridiag_inv(cudaStream_t s, int K, const double* alpha, const double
   template void launch_cg_update<T>(cudaStream_t, int, int, cpx<T>*, cpx<T>*, const cpx<T>*,              \
                                     const cpx<T>*, const double*, Work&, CgState, const T*, double, int); \
   template void launch_add_conv<T>(cudaStream_t, int, int, const cpx<T>*, double2*, const int*);        \
+  template void launch_sq_shift<T>(cudaStream_t, int, int, cpx<T>*, const cpx<T>*, const double*, const int*, \
+                                   Work&, double*);                                                      \
   template void launch_add_conv_sym<T>(cudaStream_t, int, int, const cpx<T>*, double2*, const int*, const int*);
 
 GW_LINST(double)

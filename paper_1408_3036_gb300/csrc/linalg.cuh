@@ -37,6 +37,7 @@ struct CgState {
   const double* tk = nullptr;       // per-column T_ref of the preconditioner, or null (none)
   int* n_done = nullptr;    // columns that stopped (atomic)
   unsigned* cnt = nullptr;  // tickets [ncol]
+  int ppow = 1;             // preconditioner K (1) or K^2 (2: squared operator)
 };
 
 // Per-column state of a batched simplified-QMR solve (device arrays).
@@ -71,6 +72,10 @@ void launch_qmr(cudaStream_t s, int step, int npw, int ncol, const double2* b, c
 template <typename T>
 void launch_proj_update(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, int ncol,
                         const int* active, const double2* coef, Work& w, const cpx<T>* Pv, double* pap);
+// Ap += w2[c] p per column; pap[c] = Re <p|Ap> when pap is given
+template <typename T>
+void launch_sq_shift(cudaStream_t s, int npw, int ncol, cpx<T>* Ap, const cpx<T>* p, const double* w2,
+                     const int* active, Work& w, double* pap);
 template <typename T>
 void launch_gram(cudaStream_t s, const cpx<T>* C, int nocc, int npw, const cpx<T>* Y, int ncol, Work& w,
                  double2* out);

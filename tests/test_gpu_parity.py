@@ -376,3 +376,25 @@ def test_sqmr_graph_replay_matches_direct_launches(tiny):
     assert c.stats()["graph_replays"] == 0
     c.close()
     assert rel(on, off) < 1e-14
+
+
+@pytest.mark.parametrize("prec,tol", [(gw.GW_FP64, 1e-10), (gw.GW_MIXED, 1e-6)])
+def test_squared_route_at_imaginary_frequency(tiny, prec, tol):
+    """Eq. P2+ on the GPU: at omega = i w the squared Hermitian system gives
+    x^- + x^+ directly; chi0 through it equals the sum over states, and equals
+    the SQMR pair route, in one call that also holds a static and a complex
+    frequency (those keep Eq. P2)."""
+    wl, cell, sph, gs = tiny
+    f = W.random_fields(107, 2, sph.ng)
+    om = [0.25j, 0.0, 0.7j, 0.3 + 0.1j]
+    c = make(cell, gs)
+    c.set_imaginary_route(gw.GW_IMAG_SQUARED)
+    sq = c.apply_chi0(f, om, prec)
+    c.set_imaginary_route(gw.GW_IMAG_SQMR)
+    pair = c.apply_chi0(f, om, prec)
+    c.close()
+    for k, w in enumerate(om):
+        for b in range(2):
+            ref = response.chi0_sos(gs, f[b], w)
+            assert rel(sq[k][b], ref) < tol
+            assert rel(pair[k][b], ref) < tol
