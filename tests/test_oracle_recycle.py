@@ -85,3 +85,32 @@ def test_complete_basis_matches_squared_route():
         else:
             want = want + part
     assert rel(got[:3, :3], want) < 1e-10
+
+
+def test_x_at_imaginary_frequency_against_sum_over_states(small_case):
+    """x(i w0) = A_v^-1(i w0) b (Eq. recy_eq, Eq. P2+) by CG on the squared
+    operator equals sum_c psi_c (e_c - e_v) / ((e_c - e_v)^2 + w0^2) <psi_c|b>."""
+    _, c, sph, gs = small_case
+    F = W.random_fields(64, 2, sph.ng)
+    Cc = gs.C_all[gs.n_occ:]
+    for v in range(gs.n_occ):
+        B = recycle.b_vectors(gs, F, v)
+        d = gs.eps_all[gs.n_occ:] - gs.eps[v]
+        for w0 in (0.1, 0.7):
+            x = recycle.x_imag(gs, v, B[1], w0)
+            ref = ((np.conj(Cc) @ B[1]) * d / (d * d + w0 * w0)) @ Cc
+            assert rel(x, ref) < 1e-12
+
+
+def test_augmented_basis(small_case):
+    """The solutions at one more frequency (Sec. "... at different frequencies":
+    the accuracy control with x(i w0), w0 = 1 Ha): still exact at w = 0, and
+    much closer to the exact matrix near w0 than the basis of x(0), x(i inf)."""
+    _, c, sph, gs = small_case
+    F = W.random_fields(63, 3, sph.ng)
+    ws = [0.0, 1.0]
+    plain = recycle.recycle_eps(gs, F, ws)
+    aug = recycle.recycle_eps(gs, F, ws, w0=1.0)
+    assert rel(aug[0], _exact(gs, F, 0.0)) < 1e-10
+    e1 = _exact(gs, F, 1.0)
+    assert rel(aug[1], e1) < 0.2 * rel(plain[1], e1)
