@@ -280,6 +280,17 @@ gw_status gw_grad_vloc_basis(gw_ctx* ctx, const double* phi, const double* basis
  */
 gw_status gw_stats(const gw_ctx* ctx, double* out, int n);
 
+/*
+ * gw_set_recycle_augment -- w0 > 0 adds to every recycled basis of
+ * gw_recycle_eps (and gw_sigma_c, which uses it) the solutions at one more
+ * imaginary frequency, x_{l,v}(i w0) = ((H - e_v)^2 + w0^2)^-1 (H - e_v) b_{l,v}
+ * (Eq. P2+, CG on the squared operator): the accuracy control of the
+ * recycling section (the paper takes w0 = 1 Ha).  3 nl vectors per state
+ * then enter the decomposition, and 3 nl n_occ <= 65535.  0 (default) builds
+ * the basis from x(0) and x(i inf) alone.  GW_E_ARG for w0 < 0 or non-finite.
+ */
+gw_status gw_set_recycle_augment(gw_ctx* ctx, double w0);
+
 /* Solver of purely imaginary frequencies omega = i w (gw_set_imaginary_route). */
 typedef enum {
   GW_IMAG_SQMR = 0,      /* the pair (H - e_v -/+ i w) x = b by simplified QMR (default) */

@@ -32,7 +32,8 @@ EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "
            "gw_epsinv_elements_noalloc", "gw_apply_chi0_c", "gw_apply_eps_c", "gw_block_lanczos",
            "gw_epsinv_block", "gw_batch_setup", "gw_batch_size", "gw_batch_cell", "gw_batch_lanczos",
            "gw_batch_last_error", "gw_batch_destroy", "gw_set_operator", "gw_epsinv_split", "gw_sigma_p", "gw_recycle_eps", "gw_sigma_c",
-           "gw_set_cg_kernel", "gw_grad_vloc_basis", "gw_set_graphs", "gw_set_imaginary_route")
+           "gw_set_cg_kernel", "gw_grad_vloc_basis", "gw_set_graphs", "gw_set_imaginary_route",
+           "gw_set_recycle_augment")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
                    "refine_fp64", "persistent_cg")
 
@@ -78,6 +79,7 @@ def load(path=LIB_PATH):
         "gw_set_cg_kernel": (I, [P, I, ctypes.c_longlong]),
         "gw_set_graphs": (I, [P, I]),
         "gw_set_imaginary_route": (I, [P, I]),
+        "gw_set_recycle_augment": (I, [P, D]),
         "gw_set_operator": (I, [P, I]),
         "gw_epsinv_split": (I, [P, P, I, P, P, P, I, P, P, P, I, D, P, I]),
         "gw_sigma_p": (I, [P, P, D, D, I, P, P, P, I, P, P, I, I]),
@@ -317,6 +319,11 @@ def gw_stats(ctx):
                 cluster=int(out[9]), graph_replays=int(out[10]))
 
 
+def gw_set_recycle_augment(ctx, w0):
+    """Recycled bases augmented with x(i w0) (w0 > 0), or not (0)."""
+    _check(ctx, load().gw_set_recycle_augment(ctx, float(w0)))
+
+
 def gw_set_imaginary_route(ctx, route):
     """GW_IMAG_SQMR (default) or GW_IMAG_SQUARED (Eq. P2+) at purely imaginary frequencies."""
     _check(ctx, load().gw_set_imaginary_route(ctx, int(route)))
@@ -536,6 +543,9 @@ class Cell:
 
     def set_precond(self, kind):
         gw_set_precond(self.ctx, kind)
+
+    def set_recycle_augment(self, w0):
+        gw_set_recycle_augment(self.ctx, w0)
 
     def set_imaginary_route(self, route):
         gw_set_imaginary_route(self.ctx, route)

@@ -47,6 +47,7 @@ struct gw_ctx {
   int maxplane = 0;                   // most sphere entries in one plane i0
   bool use_graphs = true;             // SQMR iterations replayed from a captured CUDA graph
   int imag_route = GW_IMAG_SQMR;      // solver of purely imaginary frequencies (gw_set_imaginary_route)
+  double recycle_w0 = 0.0;            // > 0: recycled bases augmented with x(i w0)
   long long graph_replays = 0;        // replays in the last SQMR solve
   unsigned long long wait_limit = 1ull << 24;   // spins of one device wait before GW_E_TIMEOUT
   long long pcg_iters = 0;      // iterations run by persistent launches
@@ -1936,7 +1937,9 @@ template <typename S>
 gw_status recycle_core(gw_ctx* ctx, const double* F, int nl, const double* dw, int nw, double rtol, double* out,
                        int* kept_min) {
   const int npw = ctx->npw, nocc = ctx->nocc, N3 = ctx->N3;
-  const int m = 2 * nl, nc = nl * nocc, nx = nocc * m;
+  const double w0 = ctx->recycle_w0;                 // > 0: x(i w0) joins the basis
+  const int nblk = (w0 > 0.0) ? 3 : 2;
+  const int m = nblk * nl, nc = nl * nocc, nx = nocc * m;
   auto& P = ctx->P64;
   // right-hand sides b[l * nocc + v]
   double* y;
@@ -1959,7 +1962,7 @@ gw_status recycle_core(gw_ctx* ctx, const double* F, int nl, const double* dw, i
   TRY(upload_table(ctx, "rc_E", E, &dE));
   if (ctx->precond) TRY(upload_table(ctx, "rc_tk", tk, &dtk));
   double2* xc;
-  TRY(getbuf(ctx, "rc_x", (size_t)2 * nc * npw, &xc));
+  TRY(getbuf(ctx, "rc_x", (size_t)nblk * nc * npw, &xc));
   for (int j0 = 0; j0 < nc; j0 += kPersistentMaxCols) {
     const int nj = std::min(kPersistentMaxCols, nc - j0);
     TRY(solve<S>(ctx, nj, bcp + (size_t)j0 * npw, dE + j0, xc + (size_t)j0 * npw, false, dtk ? dtk + j0 : nullptr));
@@ -1967,11 +1970,27 @@ gw_status recycle_core(gw_ctx* ctx, const double* F, int nl, const double* dw, i
   TRY(h_apply<double>(ctx, bcp, nc, dE, nullptr, xc + (size_t)nc * npw));
   TRY(ensure_work(ctx, std::max(nx, nc)));
   launch_proj<double>(ctx->st, P.C, nocc, npw, xc + (size_t)nc * npw, nc, nullptr, ctx->work, nullptr, nullptr);
-  // per state v: X_v rows [x_{l,v}(0); x_{l,v}(i inf)] normalised, and b_v rows
+  if (w0 > 0.0) {
+    // x(i w0) = ((H - e_v)^2 + w0^2)^-1 (H - e_v) b (Eq. P2+), the right-hand
+    // side being the high-frequency rows P_c (H - e_v) b just computed
+    std::vector<double> w2(nc, w0 * w0);
+    double* dw2;
+    TRY(upload_table(ctx, "rc_w2", w2, &dw2));
+    double2* rhs_sq;
+    TRY(getbuf(ctx, "rc_rsq", (size_t)nc * npw, &rhs_sq));
+    CK(cudaMemcpyAsync(rhs_sq, xc + (size_t)nc * npw, (size_t)nc * npw * sizeof(double2), cudaMemcpyDeviceToDevice,
+                       ctx->st));
+    for (int j0 = 0; j0 < nc; j0 += kPersistentMaxCols) {
+      const int nj = std::min(kPersistentMaxCols, nc - j0);
+      TRY(solve<S>(ctx, nj, rhs_sq + (size_t)j0 * npw, dE + j0, xc + (size_t)(2 * nc + j0) * npw, false,
+                   dtk ? dtk + j0 : nullptr, dw2 + j0, w0 * w0));
+    }
+  }
+  // per state v: X_v rows [x_{l,v}(0); x_{l,v}(i inf); x_{l,v}(i w0)] normalised, and b_v rows
   std::vector<int> ix(nx), ib(nc), vrow(nx);
   for (int v = 0; v < nocc; ++v)
     for (int i = 0; i < m; ++i) {
-      ix[v * m + i] = (i < nl) ? i * nocc + v : nc + (i - nl) * nocc + v;
+      ix[v * m + i] = (i / nl) * nc + (i % nl) * nocc + v;
       vrow[v * m + i] = v;
     }
   for (int v = 0; v < nocc; ++v)
@@ -2753,6 +2772,13 @@ gw_status gw_stats(const gw_ctx* ctx, double* out, int n) {
   return GW_OK;
 }
 
+gw_status gw_set_recycle_augment(gw_ctx* ctx, double w0) {
+  if (!ctx) return GW_E_ARG;
+  if (!(w0 >= 0.0) || !std::isfinite(w0)) return fail(ctx, GW_E_ARG, "w0 must be finite and >= 0");
+  ctx->recycle_w0 = w0;
+  return GW_OK;
+}
+
 gw_status gw_set_imaginary_route(gw_ctx* ctx, int route) {
   if (!ctx) return GW_E_ARG;
   if (route != GW_IMAG_SQMR && route != GW_IMAG_SQUARED) return fail(ctx, GW_E_ARG, "unknown imaginary-frequency route");
@@ -2929,8 +2955,8 @@ gw_status gw_recycle_eps(gw_ctx* ctx, const double* fields, int nl, const double
   if (prec != GW_FP64 && prec != GW_MIXED) return fail(ctx, GW_E_ARG, "bad precision");
   if (ctx->op != GW_OP_STERNHEIMER)
     return fail(ctx, GW_E_UNSUPPORTED, "the recycled basis is built from Sternheimer solutions");
-  if ((size_t)ctx->nocc * 2 * nl > 65535)
-    return fail(ctx, GW_E_ARG, "2 nl n_occ recycled vectors exceed one launch (65535)");
+  if ((size_t)ctx->nocc * (ctx->recycle_w0 > 0.0 ? 3 : 2) * nl > 65535)
+    return fail(ctx, GW_E_ARG, "the recycled vectors (2 or 3 nl n_occ) exceed one launch (65535)");
   if (rtol == 0.0) rtol = 1e-6;
   for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
   const void *F, *W;

@@ -92,3 +92,23 @@ def test_recycle_arguments():
         cell.recycle_eps(F, [0.1])
     assert e.value.status == 8
     cell.close()
+
+
+def test_recycle_augmented_parity():
+    """Bases augmented with x(i w0), w0 = 1 Ha (the recycling section's accuracy
+    control): equal to the oracle's augmented recycling (FP64 1e-10, mixed
+    1e-6), 3 nl directions kept per state, and closer to the exact matrix than
+    the plain basis at w = 0.5 and 2 Ha."""
+    c, sph, gs, cell = _setup(W.small())
+    F = W.random_fields(71, 4, sph.ng)
+    ref = recycle.recycle_eps(gs, F, WS, w0=1.0)
+    plain, _ = cell.recycle_eps(F, WS, prec=gw.GW_FP64)
+    cell.set_recycle_augment(1.0)
+    got, kept = cell.recycle_eps(F, WS, prec=gw.GW_FP64)
+    assert kept == 12
+    assert rel(got, ref) < 1e-10
+    got32, _ = cell.recycle_eps(F, WS, prec=gw.GW_MIXED)
+    assert rel(got32, ref) < 1e-6
+    assert rel(got[WS.index(2.0)], _exact(gs, F, 2.0)) < rel(plain[WS.index(2.0)], _exact(gs, F, 2.0))
+    assert rel(got[WS.index(0.5)], _exact(gs, F, 0.5)) < rel(plain[WS.index(0.5)], _exact(gs, F, 0.5))
+    cell.close()
