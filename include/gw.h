@@ -281,6 +281,31 @@ gw_status gw_grad_vloc_basis(gw_ctx* ctx, const double* phi, const double* basis
 gw_status gw_stats(const gw_ctx* ctx, double* out, int n);
 
 /*
+ * gw_proj_coef -- coef[v][j] = <C_v|y_j> = sum_G conj(C_v(G)) y_j(G), the
+ * coefficients of the conduction projector P_c y = y - sum_v C_v <C_v|y>
+ * (Sec. "Avoiding summations": orthogonalisation to the valence space at
+ * every solver step; C_v: the occupied rows, then any deflation rows) for
+ * ncol FP32 solver columns.
+ *   kernel 0  CUDA cores (FP32 products, FP32 partial sums)
+ *   kernel 1  tensor cores: tcgen05.mma kind::tf32 with both operands split
+ *             into TF32 hi and lo parts (three products, FP32 accumulation in
+ *             tensor memory), partial sums over K blocks added in FP64; up to
+ *             64 projector rows
+ *   y     [ncol][N_PW] complex FP32 (interleaved), DEVICE pointer
+ *   coef  [n_proj][ncol] complex FP64 (interleaved), DEVICE pointer
+ * GW_E_UNSUPPORTED for kernel 1 with more than 64 rows (or without a
+ * tensor-map encoder in the driver).  The mixed simplified-QMR solver uses
+ * kernel 1 from 256 columns on (gw_set_tensor_cores).
+ */
+gw_status gw_proj_coef(gw_ctx* ctx, const float* y, int ncol, double* coef, int kernel);
+
+/* gw_set_tensor_cores -- 1 (default): the mixed simplified-QMR solver takes
+   its projector coefficients from the tensor cores (gw_proj_coef kernel 1)
+   when it has at least 256 columns and at most 64 projector rows; 0: CUDA
+   cores always. */
+gw_status gw_set_tensor_cores(gw_ctx* ctx, int on);
+
+/*
  * gw_set_recycle_augment -- w0 > 0 adds to every recycled basis of
  * gw_recycle_eps (and gw_sigma_c, which uses it) the solutions at one more
  * imaginary frequency, x_{l,v}(i w0) = ((H - e_v)^2 + w0^2)^-1 (H - e_v) b_{l,v}

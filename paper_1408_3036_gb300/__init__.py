@@ -33,7 +33,7 @@ EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "
            "gw_epsinv_block", "gw_batch_setup", "gw_batch_size", "gw_batch_cell", "gw_batch_lanczos",
            "gw_batch_last_error", "gw_batch_destroy", "gw_set_operator", "gw_epsinv_split", "gw_sigma_p", "gw_recycle_eps", "gw_sigma_c",
            "gw_set_cg_kernel", "gw_grad_vloc_basis", "gw_set_graphs", "gw_set_imaginary_route",
-           "gw_set_recycle_augment")
+           "gw_set_recycle_augment", "gw_proj_coef", "gw_set_tensor_cores")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
                    "refine_fp64", "persistent_cg")
 
@@ -80,6 +80,8 @@ def load(path=LIB_PATH):
         "gw_set_graphs": (I, [P, I]),
         "gw_set_imaginary_route": (I, [P, I]),
         "gw_set_recycle_augment": (I, [P, D]),
+        "gw_proj_coef": (I, [P, P, I, P, I]),
+        "gw_set_tensor_cores": (I, [P, I]),
         "gw_set_operator": (I, [P, I]),
         "gw_epsinv_split": (I, [P, P, I, P, P, P, I, P, P, P, I, D, P, I]),
         "gw_sigma_p": (I, [P, P, D, D, I, P, P, P, I, P, P, I, I]),
@@ -319,6 +321,20 @@ def gw_stats(ctx):
                 cluster=int(out[9]), graph_replays=int(out[10]))
 
 
+def gw_proj_coef(ctx, y, coef, kernel=1):
+    """coef [n_proj][ncol] complex128 = <C_v|y_j> for y [ncol][N_PW] complex64 (both CUDA tensors)."""
+    py, d = _ptr(y)
+    pc, d2 = _ptr(coef)
+    if not (d and d2):
+        raise ValueError("device buffers required")
+    _check(ctx, load().gw_proj_coef(ctx, py, int(y.shape[0]), pc, int(kernel)))
+    return coef
+
+
+def gw_set_tensor_cores(ctx, on):
+    _check(ctx, load().gw_set_tensor_cores(ctx, int(on)))
+
+
 def gw_set_recycle_augment(ctx, w0):
     """Recycled bases augmented with x(i w0) (w0 > 0), or not (0)."""
     _check(ctx, load().gw_set_recycle_augment(ctx, float(w0)))
@@ -543,6 +559,9 @@ class Cell:
 
     def set_precond(self, kind):
         gw_set_precond(self.ctx, kind)
+
+    def set_tensor_cores(self, on):
+        gw_set_tensor_cores(self.ctx, on)
 
     def set_recycle_augment(self, w0):
         gw_set_recycle_augment(self.ctx, w0)

@@ -48,6 +48,9 @@ struct gw_ctx {
   bool use_graphs = true;             // SQMR iterations replayed from a captured CUDA graph
   int imag_route = GW_IMAG_SQMR;      // solver of purely imaginary frequencies (gw_set_imaginary_route)
   double recycle_w0 = 0.0;            // > 0: recycled bases augmented with x(i w0)
+  bool use_tc = true;                 // tensor-core projector coefficients where they apply
+  bool tc_ok = false;                 // the split occupied rows and their tensor maps are ready
+  TcMaps tc_maps;
   long long graph_replays = 0;        // replays in the last SQMR solve
   unsigned long long wait_limit = 1ull << 24;   // spins of one device wait before GW_E_TIMEOUT
   long long pcg_iters = 0;      // iterations run by persistent launches
@@ -561,6 +564,16 @@ gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E,
   dots.part = ctx->work.part_d;
   dots.cnt = ctx->work.cnt_d;
   dots.coef = ctx->work.coef;
+  // Mixed path with many columns: the projector coefficients <C_v|t> on the
+  // tensor cores (kernels_tc.cu) instead of the dots fused into the gather
+  const bool tc = std::is_same<T, float>::value && ctx->use_tc && ctx->tc_ok && ncol >= kTcMinCols;
+  float* tc_part = nullptr;
+  int* tc_err = nullptr;
+  if (tc) {
+    TRY(getbuf(ctx, "tc_part", tc_part_elems(npw, ncol), &tc_part));
+    TRY(getbuf(ctx, "tc_err", 1, &tc_err));
+    CK(cudaMemsetAsync(tc_err, 0, sizeof(int), ctx->st));
+  }
   const int check = 8;
   // One iteration: t = P_c (H - E) q, then the four update steps.  Its ten
   // launches read all per-column state from device memory, so the same
@@ -574,7 +587,12 @@ gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E,
     launch_xpass_mul<T>(ctx->st, 1, 1, 1, g, P, ctx->plan, grid, P.vloc_s, st.active, ncol);
     launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, st.active, ncol, 0);
     launch_zpass<T>(ctx->st, Z_GATHER_FWD_H, g, P, ctx->plan, grid, tt, nullptr, nullptr, q, E, st.active, nullptr,
-                    nullptr, ncol, &dots);
+                    nullptr, ncol, tc ? nullptr : &dots);
+    if constexpr (std::is_same<T, float>::value) {
+      if (tc)
+        launch_tc_dots(ctx->st, ctx->tc_maps, tt, npw, ncol, nproj(ctx), tc_part, ctx->work.coef, tc_err,
+                       std::max<unsigned long long>(ctx->wait_limit / 16, 1024));
+    }
     launch_proj_update<T>(ctx->st, P.C, nproj(ctx), npw, tt, ncol, st.active, ctx->work.coef, ctx->work, nullptr,
                           nullptr);
     for (int step = 1; step <= 4; ++step)
@@ -617,9 +635,12 @@ gw_status qmr_solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E,
     }
   }
   std::vector<int> its(ncol), flags(ncol);
+  int herr = 0;
   CK(cudaMemcpyAsync(its.data(), st.iters, ncol * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaMemcpyAsync(flags.data(), st.flag, ncol * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  if (tc) CK(cudaMemcpyAsync(&herr, tc_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   TRY(sync(ctx, "qmr_solve stats"));
+  if (herr) return fail(ctx, GW_E_TIMEOUT, "tensor-core projector: a bounded device wait gave up");
   for (int c = 0; c < ncol; ++c) {
     *it_sum += its[c];
     *it_max = std::max(*it_max, its[c]);
@@ -1923,6 +1944,20 @@ gw_status upload_projector(gw_ctx* ctx, const std::vector<zc>& cdef) {
   }
   TRY(upload(ctx, "occ_C64", c64, &ctx->P64.C));
   TRY(upload(ctx, "occ_C32", c32, &ctx->P32.C));
+  // the rows split into TF32 hi / lo parts for the tensor-core projector
+  // coefficients (up to 64 rows); without a tensor-map encoder the CUDA-core
+  // dots remain
+  ctx->tc_ok = false;
+  const int rows = (int)(n / std::max(ctx->npw, 1));
+  if (rows >= 1 && rows <= 64 && tc_prepare() == cudaSuccess) {
+    std::vector<float> hi, lo;
+    tc_split_rows(c64, rows, ctx->npw, &hi, &lo);
+    float *dhi, *dlo;
+    TRY(upload(ctx, "tc_Ahi", hi, &dhi));
+    TRY(upload(ctx, "tc_Alo", lo, &dlo));
+    ctx->tc_ok = (tc_maps(dhi, dlo, ctx->npw, &ctx->tc_maps) == cudaSuccess);
+  }
+  cudaGetLastError();
   return GW_OK;
 }
 
@@ -2770,6 +2805,40 @@ gw_status gw_stats(const gw_ctx* ctx, double* out, int n) {
   if (n > 9) out[9] = (double)ctx->pcg_cluster;
   if (n > 10) out[10] = (double)ctx->graph_replays;
   return GW_OK;
+}
+
+gw_status gw_set_tensor_cores(gw_ctx* ctx, int on) {
+  if (!ctx) return GW_E_ARG;
+  ctx->use_tc = (on != 0);
+  return GW_OK;
+}
+
+gw_status gw_proj_coef(gw_ctx* ctx, const float* y, int ncol, double* coef, int kernel) {
+  TRY(begin(ctx));
+  TRY(need_occ(ctx));
+  if (!y || !coef || ncol < 1 || (kernel != 0 && kernel != 1)) return fail(ctx, GW_E_ARG, "bad arguments");
+  const int npw = ctx->npw, np = nproj(ctx);
+  const float2* Y = reinterpret_cast<const float2*>(y);
+  double2* out = reinterpret_cast<double2*>(coef);
+  TRY(ensure_work(ctx, ncol));
+  if (kernel == 0) {
+    launch_gram<float>(ctx->st, ctx->P32.C, np, npw, Y, ncol, ctx->work, out);
+  } else {
+    if (!ctx->tc_ok) return fail(ctx, GW_E_UNSUPPORTED, "tensor-core projector unavailable (more than 64 rows?)");
+    float* part;
+    int* err;
+    TRY(getbuf(ctx, "tc_part", tc_part_elems(npw, ncol), &part));
+    TRY(getbuf(ctx, "tc_err", 1, &err));
+    CK(cudaMemsetAsync(err, 0, sizeof(int), ctx->st));
+    CK(launch_tc_dots(ctx->st, ctx->tc_maps, Y, npw, ncol, np, part, out, err,
+                      std::max<unsigned long long>(ctx->wait_limit / 16, 1024)));
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    TRY(sync(ctx, "proj_coef"));
+    if (herr) return fail(ctx, GW_E_TIMEOUT, "tensor-core projector: a bounded device wait gave up");
+  }
+  TRY(launch_check(ctx, "proj_coef"));
+  return finish(ctx, GW_OK);
 }
 
 gw_status gw_set_recycle_augment(gw_ctx* ctx, double w0) {

@@ -1,6 +1,8 @@
 // Launch interfaces of the solver / Lanczos kernels (kernels_linalg.cu).
 #pragma once
 
+#include <vector>
+
 #include "gw_common.cuh"
 
 namespace gw {
@@ -183,6 +185,24 @@ void launch_block_tridiag(cudaStream_t s, int K, int blk, const double2* A, cons
                           double2* T);
 
 // whole CG pass in one cooperative launch (kernels_cg.cu)
+// Tensor-core projector coefficients (kernels_tc.cu): coef[v * ncol + j] =
+// <C_v|Y_j> for FP32 columns Y [ncol][npw] and up to 64 occupied rows, from
+// the rows split once into TF32 hi / lo parts (A [128][kpad], FP32, device),
+// described by two TMA tensor maps.
+struct TcMaps {
+  alignas(64) unsigned char hi[128];   // CUtensorMap of A_hi
+  alignas(64) unsigned char lo[128];   // CUtensorMap of A_lo
+  int kpad = 0;
+};
+int tc_kpad(int npw);
+void tc_split_rows(const std::vector<double2>& C, int nocc, int npw, std::vector<float>* hi, std::vector<float>* lo);
+cudaError_t tc_maps(const float* Ahi, const float* Alo, int npw, TcMaps* maps);
+size_t tc_part_elems(int npw, int ncol);     // FP32 scratch of launch_tc_dots
+cudaError_t tc_prepare();                    // kernel attributes (once, before any capture)
+constexpr int kTcMinCols = 256;              // solver columns from which the tensor cores take the dots
+cudaError_t launch_tc_dots(cudaStream_t s, const TcMaps& maps, const float2* Y, int npw, int ncol, int nocc,
+                           float* part, double2* coef, int* err, unsigned long long limit);
+
 // Per-column state of the persistent CG carried between iterations.
 struct PcgCol {
   double gam, alpha, stop, rmin, rbest;
