@@ -88,9 +88,10 @@ def project_c(gs, y):
     return y - (np.conj(gs.C) @ y) @ gs.C
 
 
-def solve_cg(apply_A, b, tol=1e-14, maxiter=20000):
-    """Textbook conjugate gradients for a Hermitian positive definite A.
-    Returns (x, iterations, relative residual of the recursion)."""
+def solve_cg(apply_A, b, tol=1e-14, maxiter=20000, atol=0.0):
+    """Textbook conjugate gradients for a Hermitian positive definite A, until
+    |r| <= max(tol |b|, atol).  Returns (x, iterations, relative residual of
+    the recursion)."""
     x = np.zeros_like(b)
     r = b.copy()
     p = r.copy()
@@ -98,8 +99,9 @@ def solve_cg(apply_A, b, tol=1e-14, maxiter=20000):
     bb = rr
     if bb == 0.0:
         return x, 0, 0.0
+    stop2 = max(tol * tol * bb, atol * atol)
     it = 0
-    while np.sqrt(rr / bb) > tol and it < maxiter:
+    while rr > stop2 and it < maxiter:
         Ap = apply_A(p)
         alpha = rr / np.vdot(p, Ap).real
         x = x + alpha * p
@@ -111,22 +113,23 @@ def solve_cg(apply_A, b, tol=1e-14, maxiter=20000):
     return x, it, np.sqrt(rr / bb)
 
 
-def solve_general(apply_A, b, tol=1e-13):
+def solve_general(apply_A, b, tol=1e-13, atol=0.0):
     """Non-Hermitian-positive cases (indefinite or complex shift): GMRES
     (library routine) on the same projected operator."""
     n = b.shape[0]
     A = scipy.sparse.linalg.LinearOperator((n, n), matvec=apply_A,
                                            dtype=np.complex128)
-    x, info = scipy.sparse.linalg.gmres(A, b, rtol=tol, atol=0.0,
+    x, info = scipy.sparse.linalg.gmres(A, b, rtol=tol, atol=atol,
                                         restart=min(n, 400), maxiter=200)
     if info != 0:
         raise RuntimeError(f"gmres did not converge ({info})")
     return x
 
 
-def sternheimer_solve(gs, v, shift, b, tol=1e-14, gap=None):
+def sternheimer_solve(gs, v, shift, b, tol=1e-14, gap=None, atol=0.0):
     """Solve (H - e_v + shift) x = b in the conduction space (Eq. P2 with
-    shift = -/+ omega), P_c applied at every iteration."""
+    shift = -/+ omega), P_c applied at every iteration, until the residual is
+    below max(tol |b|, atol)."""
     sph, vloc = gs.sph, gs.vloc
     e = gs.eps[v]
 
@@ -135,9 +138,9 @@ def sternheimer_solve(gs, v, shift, b, tol=1e-14, gap=None):
 
     hpd = (np.imag(shift) == 0.0) and (gap is not None) and (np.real(shift) > -gap)
     if hpd:
-        x, _, _ = solve_cg(A, b, tol)
+        x, _, _ = solve_cg(A, b, tol, atol=atol)
     else:
-        x = solve_general(A, b, tol)
+        x = solve_general(A, b, tol, atol=atol)
     return project_c(gs, x)
 
 
@@ -150,13 +153,19 @@ def chi0_sternheimer(gs, f, omega, tol=1e-14, gaps=None, states=None):
     u = gs.u
     out = np.zeros(sph.ng, dtype=np.complex128)
     for v in (range(gs.n_occ) if states is None else states):
-        b = project_c(gs, sph.to_sphere(np.conj(u[v]) * f))
+        # The target is relative to psi_v* f before P_c: the projected right-hand
+        # side carries rounding of that size, so a target relative to b alone
+        # is out of reach when P_c removes most of psi_v* f (the paper's own
+        # criterion is absolute, Sec. Results).
+        g = sph.to_sphere(np.conj(u[v]) * f)
+        b = project_c(gs, g)
+        atol = tol * np.linalg.norm(g)
         gap = None if gaps is None else gaps[v]
-        xm = sternheimer_solve(gs, v, -omega, b, tol, gap)
+        xm = sternheimer_solve(gs, v, -omega, b, tol, gap, atol)
         if omega == 0:
             xs = 2.0 * xm
         else:
-            xs = xm + sternheimer_solve(gs, v, +omega, b, tol, gap)
+            xs = xm + sternheimer_solve(gs, v, +omega, b, tol, gap, atol)
         out += u[v] * sph.to_grid(xs)
     return -2.0 / vol * out
 
