@@ -649,6 +649,41 @@ def run_gpu(args):
         else:
             sigp = dict(skipped=f"conduction states not converged: {res_c}")
 
+    # --- block complex-frequency workload at full size (64^3, 38401 PW, 64 occupied, blocks of 8)
+    bfl = None
+    if args.block_freq_steps > 0:
+        bw = W.block_freq()
+        bc = bw.cells[0]
+        bcell = gw.Cell(bc.L, bc.N, bc.ecut, bc.vloc, 0, stream.cuda_stream)
+        beps, bpsi, bres = lowest_states(bcell, bc.n_occ, tol=1e-10)
+        if bres <= 1e-8 and beps[bc.n_occ] - beps[bc.n_occ - 1] > 1e-3:
+            bcell.set_occupied(bpsi, beps[:bc.n_occ])
+            om = complex(bw.omegas[0])
+            X0 = bw.starts[0]
+            kb = args.block_freq_steps
+            rows = []
+            for tc_on in (1, 0):
+                bcell.set_tensor_cores(tc_on)
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                A, B, _ = bcell.block_lanczos(X0, kb, om, prec)
+                e1.record(stream)
+                e1.synchronize()
+                stb = gw.gw_stats(bcell.ctx)
+                rows.append(dict(tensor_core_projector=bool(tc_on), ms=e0.elapsed_time(e1),
+                                 applies_per_s=kb * X0.shape[0] / (e0.elapsed_time(e1) / 1e3),
+                                 sqmr_mean_iter=stb["mean_iter"], sqmr_max_iter=stb["max_iter"],
+                                 sqmr_columns=stb["columns"], graph_replays=stb["graph_replays"]))
+            bcell.set_tensor_cores(1)
+            bfl = dict(workload="L=24 bohr, 64^3, 15 Ha (%d PW), 24 wells, N_occ=64, block 8, omega=%.4f+0.1i"
+                       % (bcell.npw, om.real), block_steps=kb, precision=args.prec, runs=rows,
+                       unit="eps~ applications (block columns) per second")
+        else:
+            bfl = dict(skipped=f"ground state not converged or gap too small (residual {bres:.2e})")
+        bcell.close()
+
     if rank == 0:
         line = dict(
             metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -664,7 +699,7 @@ def run_gpu(args):
                         column_iterations_per_step=it_cols / args.steps, geometry=geo),
             roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
             clocks=clk.summary(), fp64=fp64, profile_ms={k: v[0] for k, v in prof.items() if v[1]},
-            model_operator=model, sigma_p=sigp, recycle=rec, sigma_c=sigc,
+            model_operator=model, sigma_p=sigp, recycle=rec, sigma_c=sigc, block_freq=bfl,
         )
         print(json.dumps(line))
     cell.close()
@@ -693,6 +728,8 @@ def main():
                     help="Lanczos vectors in which eps~(i w) - 1 is built from recycled bases (Eq. recy_eq; 0: skip)")
     ap.add_argument("--sigma-p-k", type=int, default=4,
                     help="Lanczos steps per pole of the Sigma^P leg (Eq. pe; 0: skip)")
+    ap.add_argument("--block-freq-steps", type=int, default=1,
+                    help="block Lanczos steps timed on the full block complex-frequency workload (0: skip)")
     ap.add_argument("--deflation", type=int, default=0,
                     help="lowest conduction states handed to the solvers as a deflation block (0: none)")
     args = ap.parse_args()

@@ -528,9 +528,14 @@ gw_status gw_sigma_c(gw_ctx* ctx, int e, double delta, double alpha, int n_freq,
  * Classes (multi-launch CG): 0 scatter + inverse z pass (with the CG p update),
  * 1 inverse y pass, 2 x pass with V_loc (H), 3 forward y pass, 4 forward z pass
  * + gather + kinetic and shift, 5 projector P_c, 6 CG update; 7 FP64
- * refinement residual (H apply + P_c); 8 persistent CG launch (all phases).
+ * refinement residual (H apply + P_c); 8 persistent CG launch (all phases);
+ * 9 the persistent CG's tasks, timed inside the kernel (global timer): read
+ * back as entries 10..15 = task kind A busy, A waiting, B busy, B waiting,
+ * C busy, C waiting (milliseconds summed over tasks; counts: tasks run for
+ * "busy", tasks skipped for "waiting").
  * gw_profile_read -- per class: total milliseconds and launches since the last
- * read (synchronises the stream; resets the totals).
+ * read (synchronises the stream; resets the totals); n >= 16 for the task
+ * entries.
  */
 gw_status gw_profile(gw_ctx* ctx, unsigned mask);
 gw_status gw_profile_read(gw_ctx* ctx, double* ms, long long* count, int n);

@@ -35,7 +35,8 @@ EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "
            "gw_set_cg_kernel", "gw_grad_vloc_basis", "gw_set_graphs", "gw_set_imaginary_route",
            "gw_set_recycle_augment", "gw_proj_coef", "gw_set_tensor_cores")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
-                   "refine_fp64", "persistent_cg")
+                   "refine_fp64", "persistent_cg", "pcg_tasks", "pcg_A_busy", "pcg_A_wait", "pcg_B_busy",
+                   "pcg_B_wait", "pcg_C_busy", "pcg_C_wait")
 
 
 class GwError(RuntimeError):

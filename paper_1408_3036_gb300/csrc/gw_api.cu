@@ -68,6 +68,7 @@ struct gw_ctx {
   std::string err;
   // optional per-kernel-class timing with CUDA events on the work stream
   unsigned prof_mask = 0;
+  unsigned long long* ptask = nullptr;   // device [12] task timing of the persistent CG (PC_TASKS)
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<int, int>>> ev_used;   // (class, (start, end))
   size_t ev_next = 0;
@@ -191,7 +192,10 @@ gw_status ensure_work(gw_ctx* ctx, size_t cols) {
 // selected class, resolved by gw_profile_read
 // ---------------------------------------------------------------------------
 enum ProfClass { PC_ZSCAT = 0, PC_YINV = 1, PC_XH = 2, PC_YFWD = 3, PC_ZGATH = 4, PC_PROJ = 5, PC_CGUPD = 6,
-                 PC_REFINE = 7, PC_PCG = 8, PC_N = 9 };
+                 PC_REFINE = 7, PC_PCG = 8, PC_TASKS = 9, PC_N = 10 };
+// PC_TASKS: the persistent CG's task kinds A, B, C, read back as six
+// pseudo-classes after PC_TASKS: busy and wait milliseconds summed over tasks
+// (counts: tasks run, and tasks skipped / waits)
 
 int prof_begin(gw_ctx* ctx, int cls) {
   if (!(ctx->prof_mask & (1u << cls))) return -1;
@@ -484,10 +488,18 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
     TRY(getbuf(ctx, "pcg_cst", z.cst, &cst));
     TRY(getbuf(ctx, "pcg_ctl", z.ctl, &ctl));
     CK(cudaMemsetAsync(ctl, 0, z.ctl * sizeof(unsigned), ctx->st));
+    unsigned long long* ptask = nullptr;
+    if (ctx->prof_mask & (1u << PC_TASKS)) {
+      if (!ctx->ptask) {
+        TRY(getbuf(ctx, "pcg_ptask", 12, &ctx->ptask));
+        CK(cudaMemsetAsync(ctx->ptask, 0, 12 * sizeof(unsigned long long), ctx->st));
+      }
+      ptask = ctx->ptask;
+    }
     le = launch_cg_persistent<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), nproj(ctx), npw, ncol, z,
                                  ctx->maxplane, b64, outer_active, E, rr_abs, tk, tol * tol, ctx->max_iter, x, r, p,
                                  sv, Y, grid, rec, apart, cst, ctl, iters, flags, rr_out, &used, ctx->cta_div,
-                                 ctx->wait_limit);
+                                 ctx->wait_limit, ptask);
     if (le == cudaErrorNotSupported) {      // shared memory beyond one SM: the multi-launch CG
       cudaGetLastError();
       prof_end(ctx, PC_PCG, pa);
@@ -3110,6 +3122,17 @@ gw_status gw_profile_read(gw_ctx* ctx, double* ms, long long* count, int n) {
   }
   ctx->ev_used.clear();
   ctx->ev_next = 0;
+  if (ctx->ptask && n > PC_TASKS + 6) {
+    unsigned long long h[12];
+    CK(cudaMemcpy(h, ctx->ptask, sizeof(h), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(ctx->ptask, 0, sizeof(h)));
+    for (int k = 0; k < 3; ++k) {
+      ms[PC_TASKS + 1 + 2 * k] = 1e-6 * (double)h[4 * k + 1];       // busy
+      count[PC_TASKS + 1 + 2 * k] = (long long)h[4 * k + 0];
+      ms[PC_TASKS + 2 + 2 * k] = 1e-6 * (double)h[4 * k + 2];       // waiting
+      count[PC_TASKS + 2 + 2 * k] = (long long)h[4 * k + 3];
+    }
+  }
   return GW_OK;
 }
 

@@ -93,6 +93,7 @@ struct PcgArgs {
   int* flag_out;
   double* rr_out;
   unsigned long long spin_limit;
+  unsigned long long* ptask;  // optional [3][4]: per task kind A, B, C: tasks run, busy ns, wait ns, skipped
 };
 
 template <typename V> __device__ __forceinline__ V ldcg(const V* p);
@@ -189,6 +190,26 @@ __device__ __forceinline__ int wait_dep(const unsigned* cnt, unsigned target, co
   return (d != 0u && d <= skip_le) ? 1 : 0;
 }
 
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Optional task timing (thread 0): wait from t0 to t1, work from t1 to now.
+__device__ __forceinline__ void task_time(unsigned long long* pt, int kind, unsigned long long t0,
+                                          unsigned long long t1, bool ran) {
+  if (!pt || threadIdx.x != 0) return;
+  unsigned long long* q = pt + 4 * kind;
+  if (ran) {
+    atomicAdd(q + 0, 1ull);
+    atomicAdd(q + 1, gtime() - t1);
+  } else {
+    atomicAdd(q + 3, 1ull);
+  }
+  atomicAdd(q + 2, t1 - t0);
+}
+
 // Completion of a task: every thread's writes fenced, then one count.
 __device__ __forceinline__ void signal_done(unsigned* cnt) {
   __threadfence();
@@ -216,14 +237,20 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
   V* coefT = reinterpret_cast<V*>(sm + L.coef);        // [W][nocc] coefficients, then [W][nocc] <C_v|u_c>
   double* dsum = reinterpret_cast<double*>(sm + L.dsum);
   double* colv = reinterpret_cast<double*>(sm + L.col);   // [c * 8 + k]: alpha, beta, active, E, rtk
+  unsigned long long t0 = 0, t1 = 0;
   if (threadIdx.x == 0) {
     int w = 0;
+    if (a.ptask) t0 = gtime();
     if (it > 0) w = wait_dep(gc + 2, (unsigned)(it * P), gc + 3, (unsigned)it, a.ctl, a.spin_limit);
+    if (a.ptask) t1 = gtime();
     s_ctl[0] = w;
   }
   __syncthreads();
   if (s_ctl[0] == 2) return;
-  if (s_ctl[0] == 1) return;           // the group finished earlier: nothing left to do
+  if (s_ctl[0] == 1) {                 // the group finished earlier: nothing left to do
+    task_time(a.ptask, 0, t0, t1, false);
+    return;
+  }
   const int i0 = g.planes[pi];
   const int s0 = g.plane_sph[pi], s1 = g.plane_sph[pi + 1];
   const int q0 = g.plane_pen[pi], npp = g.plane_pen[pi + 1] - q0;
@@ -396,6 +423,7 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
           atomicAdd(&a.ctl[1], 1u);
         }
         signal_done(gc + 0);
+        task_time(a.ptask, 0, t0, t1, true);
         return;
       }
     }
@@ -534,6 +562,7 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
     a.grid[base + e] = S[i1 * LDp + i2];
   }
   signal_done(gc + 0);
+  task_time(a.ptask, 0, t0, t1, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -550,9 +579,14 @@ __device__ void task_B(const PcgArgs<T>& a, int it, int gi, int i1, unsigned cha
   V* Ab = reinterpret_cast<V*>(sm + L.A);
   V* Bb = reinterpret_cast<V*>(sm + L.B);
   const V* stw = reinterpret_cast<const V*>(sm + L.tw);
-  if (threadIdx.x == 0)
+  unsigned long long t0 = 0, t1 = 0;
+  if (threadIdx.x == 0) {
+    if (a.ptask) t0 = gtime();
     s_ctl[0] = wait_dep(gc + 0, (unsigned)((it + 1) * P), gc + 3, (unsigned)(it + 1), a.ctl, a.spin_limit);
+    if (a.ptask) t1 = gtime();
+  }
   __syncthreads();
+  if (s_ctl[0] == 1) task_time(a.ptask, 1, t0, t1, false);
   if (s_ctl[0] != 0) return;
   const size_t base = (size_t)gi * g.N3 + (size_t)i1 * N;
 #pragma unroll 4
@@ -577,6 +611,7 @@ __device__ void task_B(const PcgArgs<T>& a, int it, int gi, int i1, unsigned cha
     if (g.plane_mask[i0]) a.grid[base + (size_t)i0 * g.N2 + i2] = S[i0 * LDp + i2];
   }
   signal_done(gc + 1);
+  task_time(a.ptask, 1, t0, t1, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -596,9 +631,14 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
   const V* stw = reinterpret_cast<const V*>(sm + L.tw);
   double* red = reinterpret_cast<double*>(sm + L.red);
   double* dsum = reinterpret_cast<double*>(sm + L.dsum);
-  if (threadIdx.x == 0)
+  unsigned long long t0 = 0, t1 = 0;
+  if (threadIdx.x == 0) {
+    if (a.ptask) t0 = gtime();
     s_ctl[0] = wait_dep(gc + 1, (unsigned)((it + 1) * N), gc + 3, (unsigned)(it + 1), a.ctl, a.spin_limit);
+    if (a.ptask) t1 = gtime();
+  }
   __syncthreads();
+  if (s_ctl[0] == 1) task_time(a.ptask, 2, t0, t1, false);
   if (s_ctl[0] != 0) return;
   const int i0 = g.planes[pi];
   const int s0 = g.plane_sph[pi], s1 = g.plane_sph[pi + 1];
@@ -732,6 +772,7 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
     if (threadIdx.x < 4 * W) rd[threadIdx.x] = dsum[threadIdx.x];
   }
   signal_done(gc + 2);
+  task_time(a.ptask, 2, t0, t1, true);
 }
 
 template <typename T>
@@ -799,7 +840,7 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
                                  double tol_in2, int maxit, cpx<T>* x, cpx<T>* r, cpx<T>* p, cpx<T>* sv, cpx<T>* Y,
                                  cpx<T>* grid, unsigned char* rec, double* apart, PcgCol* cst, unsigned* ctl,
                                  int* iters, int* flags, double* rr_out, int* grid_used, int cta_div,
-                                 unsigned long long spin_limit) {
+                                 unsigned long long spin_limit, unsigned long long* ptask) {
   PcgArgs<T> a;
   a.g = g; a.pl = pl; a.tw = P.tw; a.kin = P.kin; a.vloc_s = P.vloc_s; a.C = P.C;
   a.nocc = nocc; a.npw = npw; a.ncol = ncol; a.ngrp = z.ngrp; a.W = z.W; a.maxplane = maxplane;
@@ -807,7 +848,7 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
   a.maxit = maxit;
   a.x = x; a.r = r; a.p = p; a.s = sv; a.Y = Y; a.grid = grid; a.rec = rec; a.rec_bytes = z.rec_bytes;
   a.apart = apart; a.cst = cst; a.ctl = ctl;
-  a.iters_out = iters; a.flag_out = flags; a.rr_out = rr_out; a.spin_limit = spin_limit;
+  a.iters_out = iters; a.flag_out = flags; a.rr_out = rr_out; a.spin_limit = spin_limit; a.ptask = ptask;
   const size_t sm = pcg_smem<T>(g.N, nocc, z.W, maxplane);
   if (sm > 227 * 1024) return cudaErrorNotSupported;
   cudaError_t e = cudaSuccess;
@@ -845,7 +886,7 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
       cudaStream_t, const Geometry&, const FftPlan&, const Prec<T>&, int, int, int, const PcgSizes&, int,    \
       const double2*, const int*, const double2*, const double*, const double*, double, int, cpx<T>*,       \
       cpx<T>*, cpx<T>*, cpx<T>*, cpx<T>*, cpx<T>*, unsigned char*, double*, PcgCol*, unsigned*, int*, int*,  \
-      double*, int*, int, unsigned long long);
+      double*, int*, int, unsigned long long, unsigned long long*);
 GW_PCG_INST(float)
 GW_PCG_INST(double)
 

@@ -44,10 +44,14 @@ def molecule_oracle():
     wl = W.molecule()
     cell = wl.cells[0]
     sph = pw.Sphere(cell.L, cell.N, cell.ecut)
-    # both sides take these states as they are, so the parity does not depend
-    # on how tightly they are converged
-    gs, w, _ = pw.ground_state_iterative(sph, cell.vloc, cell.n_occ, tol=1e-9, maxiter=500)
-    assert pw.residuals(sph, cell.vloc, gs.eps, gs.C).max() < 1e-7
+    # Both sides take these states, but the library makes each state real in
+    # real space (its K-symmetric part, Sec. "Avoiding summations" needs only
+    # the projector): the states must be eigenstates to well below the parity
+    # tolerance, or the near-gap Sternheimer columns (condition ~3000) see the
+    # difference.
+    gs, w, _ = pw.ground_state_iterative(sph, cell.vloc, cell.n_occ, tol=1e-12, maxiter=3000)
+    res = pw.residuals(sph, cell.vloc, gs.eps, gs.C).max()
+    assert res < 1e-10, res
     gap = w[cell.n_occ] - w[cell.n_occ - 1]
     assert gap > 1e-3                       # reading 10: no cut inside a degenerate shell
     D = response.Dielectric(gs, 0.0)

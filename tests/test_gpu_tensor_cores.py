@@ -44,10 +44,13 @@ def test_tensor_core_projector_coefficients(name, ncol):
     gw.gw_proj_coef(cell.ctx, ty, c1, 1)
     a0, a1 = c0.cpu().numpy(), c1.cpu().numpy()
     cell.close()
+    # both kernels carry FP32 rounding over ~2 N_PW terms (~1e-6 of the largest
+    # coefficient); the FP64 invariant checks each of them
     scale = np.abs(a0).max()
-    assert np.abs(a1 - a0).max() < 2e-6 * scale
+    assert np.abs(a1 - a0).max() < 1e-5 * scale
     ref = (np.abs(np.conj(gs.C) @ y.astype(np.complex128).T) ** 2).sum(0)     # |P_v y_j|^2
-    assert np.abs((np.abs(a1) ** 2).sum(0) - ref).max() < 1e-5 * ref.max()
+    for a in (a0, a1):
+        assert np.abs((np.abs(a) ** 2).sum(0) - ref).max() < 1e-5 * ref.max()
 
 
 def test_tensor_cores_in_the_mixed_sqmr_solver():
