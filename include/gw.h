@@ -276,9 +276,22 @@ gw_status gw_grad_vloc_basis(gw_ctx* ctx, const double* phi, const double* basis
  *   out[8] CTAs of the last persistent CG launch, out[9] its cluster size
  *          (0: the grid-wide cooperative kernel)
  *   out[10] CUDA-graph replays of SQMR iterations in the last SQMR solve
- *   n: entries wanted (<= 11)
+ *   out[11] threads per CTA of the last persistent CG launch (256 or 512)
+ *   n: entries wanted (<= 12)
  */
 gw_status gw_stats(const gw_ctx* ctx, double* out, int n);
+
+/*
+ * gw_set_autotune -- 1 (default): launch shapes that change speed only (the
+ * persistent CG's CTA width: 256 threads, two CTAs per SM, or 512, one CTA per
+ * SM) are chosen per problem shape by timing the first launches of each
+ * candidate; the choice is kept for the process and written to a JSON cache
+ * ($LIBGW_TUNE_CACHE, else $XDG_CACHE_HOME/libgw/tune.json, else
+ * ~/.cache/libgw/tune.json) that later processes read.  The candidates
+ * compute the same sums in different reduction orders (results agree to
+ * rounding).  0: always 256 threads.
+ */
+gw_status gw_set_autotune(gw_ctx* ctx, int on);
 
 /*
  * gw_proj_coef -- coef[v][j] = <C_v|y_j> = sum_G conj(C_v(G)) y_j(G), the

@@ -88,10 +88,13 @@ def project_c(gs, y):
     return y - (np.conj(gs.C) @ y) @ gs.C
 
 
-def solve_cg(apply_A, b, tol=1e-14, maxiter=20000, atol=0.0):
+def solve_cg(apply_A, b, tol=1e-14, maxiter=20000, atol=0.0, stall=500):
     """Textbook conjugate gradients for a Hermitian positive definite A, until
-    |r| <= max(tol |b|, atol).  Returns (x, iterations, relative residual of
-    the recursion)."""
+    |r| <= max(tol |b|, atol).  In floating point the recursion can reach a
+    floor above that target (a right-hand side much smaller than the rounding
+    of its own construction); it then stops once |r| has not halved in
+    `stall` iterations and returns the iterate of smallest |r| seen.
+    Returns (x, iterations, relative residual of that iterate)."""
     x = np.zeros_like(b)
     r = b.copy()
     p = r.copy()
@@ -100,8 +103,9 @@ def solve_cg(apply_A, b, tol=1e-14, maxiter=20000, atol=0.0):
     if bb == 0.0:
         return x, 0, 0.0
     stop2 = max(tol * tol * bb, atol * atol)
+    best, x_best, it_best = rr, x.copy(), 0
     it = 0
-    while rr > stop2 and it < maxiter:
+    while rr > stop2 and it < maxiter and it - it_best <= stall:
         Ap = apply_A(p)
         alpha = rr / np.vdot(p, Ap).real
         x = x + alpha * p
@@ -110,7 +114,11 @@ def solve_cg(apply_A, b, tol=1e-14, maxiter=20000, atol=0.0):
         p = r + (rr_new / rr) * p
         rr = rr_new
         it += 1
-    return x, it, np.sqrt(rr / bb)
+        if rr < best:
+            if rr < 0.25 * best:
+                it_best = it
+            best, x_best = rr, x.copy()
+    return x_best, it, np.sqrt(best / bb)
 
 
 def solve_general(apply_A, b, tol=1e-13, atol=0.0):

@@ -33,7 +33,8 @@ EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "
            "gw_epsinv_block", "gw_batch_setup", "gw_batch_size", "gw_batch_cell", "gw_batch_lanczos",
            "gw_batch_last_error", "gw_batch_destroy", "gw_set_operator", "gw_epsinv_split", "gw_sigma_p", "gw_recycle_eps", "gw_sigma_c",
            "gw_set_cg_kernel", "gw_grad_vloc_basis", "gw_set_graphs", "gw_set_imaginary_route",
-           "gw_set_recycle_augment", "gw_proj_coef", "gw_set_tensor_cores")
+           "gw_set_recycle_augment", "gw_proj_coef", "gw_set_tensor_cores",
+           "gw_set_autotune")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
                    "refine_fp64", "persistent_cg", "pcg_tasks", "pcg_A_busy", "pcg_A_wait", "pcg_B_busy",
                    "pcg_B_wait", "pcg_C_busy", "pcg_C_wait")
@@ -83,6 +84,7 @@ def load(path=LIB_PATH):
         "gw_set_recycle_augment": (I, [P, D]),
         "gw_proj_coef": (I, [P, P, I, P, I]),
         "gw_set_tensor_cores": (I, [P, I]),
+        "gw_set_autotune": (I, [P, I]),
         "gw_set_operator": (I, [P, I]),
         "gw_epsinv_split": (I, [P, P, I, P, P, P, I, P, P, P, I, D, P, I]),
         "gw_sigma_p": (I, [P, P, D, D, I, P, P, P, I, P, P, I, I]),
@@ -315,11 +317,15 @@ def gw_grad_vloc_basis(ctx, phi, basis, alpha, beta, k, s, grad, prec=GW_FP64):
 
 
 def gw_stats(ctx):
-    out = np.zeros(11)
-    _check(ctx, load().gw_stats(ctx, out.ctypes.data, 11))
+    out = np.zeros(12)
+    _check(ctx, load().gw_stats(ctx, out.ctypes.data, 12))
     return dict(columns=out[0], max_iter=out[1], mean_iter=out[2], outer=out[3], max_residual=out[4],
                 h_columns=out[5], launches=int(out[6]), launch_iterations=int(out[7]), launch_ctas=int(out[8]),
-                cluster=int(out[9]), graph_replays=int(out[10]))
+                cluster=int(out[9]), graph_replays=int(out[10]), cta_threads=int(out[11]))
+
+
+def gw_set_autotune(ctx, on):
+    _check(ctx, load().gw_set_autotune(ctx, int(on)))
 
 
 def gw_proj_coef(ctx, y, coef, kernel=1):
@@ -560,6 +566,9 @@ class Cell:
 
     def set_precond(self, kind):
         gw_set_precond(self.ctx, kind)
+
+    def set_autotune(self, on):
+        gw_set_autotune(self.ctx, on)
 
     def set_tensor_cores(self, on):
         gw_set_tensor_cores(self.ctx, on)

@@ -16,6 +16,7 @@
 #include "gw.h"
 #include "gw_common.cuh"
 #include "linalg.cuh"
+#include "tune.h"
 
 using namespace gw;
 
@@ -49,6 +50,8 @@ struct gw_ctx {
   int imag_route = GW_IMAG_SQMR;      // solver of purely imaginary frequencies (gw_set_imaginary_route)
   double recycle_w0 = 0.0;            // > 0: recycled bases augmented with x(i w0)
   bool use_tc = true;                 // tensor-core projector coefficients where they apply
+  bool tune = true;                   // launch shapes picked by timing (tune.cu)
+  int pcg_tpb = 0;                    // CTA width of the last persistent CG launch
   bool tc_ok = false;                 // the split occupied rows and their tensor maps are ready
   TcMaps tc_maps;
   long long graph_replays = 0;        // replays in the last SQMR solve
@@ -69,6 +72,7 @@ struct gw_ctx {
   // optional per-kernel-class timing with CUDA events on the work stream
   unsigned prof_mask = 0;
   unsigned long long* ptask = nullptr;   // device [12] task timing of the persistent CG (PC_TASKS)
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};   // autotuner timing events
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<int, int>>> ev_used;   // (class, (start, end))
   size_t ev_next = 0;
@@ -455,6 +459,8 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
   const int pa = prof_begin(ctx, PC_PCG);
   cudaError_t le = cudaErrorNotSupported;
   unsigned* ctl = nullptr;
+  std::string tune_key;
+  int tune_tpb = 0;
   if (ctx->cg_kernel == GW_CG_CLUSTER) {
     // opt-in: one thread-block cluster per column when the column's planes
     // fit in the cluster's shared memory
@@ -496,10 +502,25 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
       }
       ptask = ctx->ptask;
     }
+    // CTA width: 256 (two per SM) or 512 (one per SM), tuned per shape
+    char key[160];
+    std::snprintf(key, sizeof(key), "pcg1_tpb:%s:N%d:npw%d:nproj%d:ncol%d:W%d:div%d", tname<T>(), ctx->N, npw,
+                  nproj(ctx), ncol, z.W, ctx->cta_div);
+    const int tpb = tune_pick(key, {256, 512}, ctx->tune && ctx->cta_div == 1);
+    if (!ctx->tune_ev[0]) {
+      CK(cudaEventCreate(&ctx->tune_ev[0]));
+      CK(cudaEventCreate(&ctx->tune_ev[1]));
+    }
+    const bool timing = ctx->tune && ctx->cta_div == 1 && !tune_known(key);
+    if (timing) CK(cudaEventRecord(ctx->tune_ev[0], ctx->st));
     le = launch_cg_persistent<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), nproj(ctx), npw, ncol, z,
                                  ctx->maxplane, b64, outer_active, E, rr_abs, tk, tol * tol, ctx->max_iter, x, r, p,
                                  sv, Y, grid, rec, apart, cst, ctl, iters, flags, rr_out, &used, ctx->cta_div,
-                                 ctx->wait_limit, ptask);
+                                 ctx->wait_limit, ptask, tpb);
+    if (timing && le == cudaSuccess) CK(cudaEventRecord(ctx->tune_ev[1], ctx->st));
+    ctx->pcg_tpb = tpb;
+    tune_key = key;
+    tune_tpb = timing ? tpb : 0;
     if (le == cudaErrorNotSupported) {      // shared memory beyond one SM: the multi-launch CG
       cudaGetLastError();
       prof_end(ctx, PC_PCG, pa);
@@ -526,6 +547,11 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
   }
   ctx->pcg_iters += imax;       // iterations of the whole launch (bounded by the slowest column)
   ctx->pcg_launch_blocks = used;
+  if (tune_tpb && imax > 0) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->tune_ev[0], ctx->tune_ev[1]) == cudaSuccess)
+      tune_report(tune_key, tune_tpb, (double)ms / imax);
+  }
   return GW_OK;
 }
 
@@ -2816,6 +2842,13 @@ gw_status gw_stats(const gw_ctx* ctx, double* out, int n) {
   if (n > 8) out[8] = (double)ctx->pcg_launch_blocks;
   if (n > 9) out[9] = (double)ctx->pcg_cluster;
   if (n > 10) out[10] = (double)ctx->graph_replays;
+  if (n > 11) out[11] = (double)ctx->pcg_tpb;
+  return GW_OK;
+}
+
+gw_status gw_set_autotune(gw_ctx* ctx, int on) {
+  if (!ctx) return GW_E_ARG;
+  ctx->tune = (on != 0);
   return GW_OK;
 }
 
@@ -3145,6 +3178,8 @@ void gw_destroy(gw_ctx* ctx) {
     if (kv.second.first) cudaFree(kv.second.first);
   if (ctx->host_pin) cudaFreeHost(ctx->host_pin);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : ctx->tune_ev)
+    if (e) cudaEventDestroy(e);
   if (ctx->ev) cudaEventDestroy(ctx->ev);
   if (ctx->st && ctx->own_stream) cudaStreamDestroy(ctx->st);
   delete ctx;

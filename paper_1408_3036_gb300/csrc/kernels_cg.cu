@@ -59,7 +59,6 @@
 
 namespace gw {
 
-constexpr int kPT = 256;        // threads per CTA
 constexpr int kCtlHead = 4;     // control words: ticket, groups done, error flag, unused
 
 template <typename T>
@@ -116,7 +115,7 @@ __device__ __forceinline__ PcgCol ld_col(const PcgCol* p) {
 }
 
 // Sums over the block of NV values per thread, in FP64 (the NV sums land in
-// out[0 .. NV), visible to every thread after the call).
+// out[0 .. NV), visible to every thread after the call); up to 16 warps.
 template <int NV>
 __device__ __forceinline__ void block_sum_n(double (&v)[NV], double* sh, double* out) {
 #pragma unroll
@@ -126,38 +125,41 @@ __device__ __forceinline__ void block_sum_n(double (&v)[NV], double* sh, double*
   __syncthreads();
   if (l == 0)
 #pragma unroll
-    for (int k = 0; k < NV; ++k) sh[k * 8 + w] = v[k];
+    for (int k = 0; k < NV; ++k) sh[k * 16 + w] = v[k];
   __syncthreads();
   if (threadIdx.x < NV) {
     double t = 0.0;
-    for (int q = 0; q < nw; ++q) t += sh[threadIdx.x * 8 + q];
+    for (int q = 0; q < nw; ++q) t += sh[threadIdx.x * 16 + q];
     out[threadIdx.x] = t;
   }
   __syncthreads();
 }
 
 struct PcgLayout {
-  size_t A, B, U, tw, rowmap, red, S, coef, dsum, col, total;
+  size_t A, B, U, K, tw, rowmap, red, S, coef, dsum, ap, col, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Shared memory of one CTA: two FFT tiles N x (N+1), the plane's u_c (C
-// tasks), twiddles, the row map of a plane's disc pencils, reduction scratch,
-// the summed records, the group's projector coefficients and <C_v|u_c> (A
-// tasks), FP64 sums, and per-column scalars.
+// Shared memory of one CTA: two FFT tiles N x (N+1), the plane's u_c and
+// |G|^2/2 (C tasks), twiddles, the row map of a plane's disc pencils,
+// reduction scratch, the summed records, the group's projector coefficients
+// and <C_v|u_c> (A tasks), FP64 sums, the staged per-plane partials of the A
+// tasks, and per-column scalars.
 __host__ __device__ inline PcgLayout pcg_layout(int N, int nocc, int W, int maxplane, int vsize) {
   PcgLayout L;
   L.A = 0;
   L.B = align16(L.A + (size_t)N * (N + 1) * vsize);
   L.U = align16(L.B + (size_t)N * (N + 1) * vsize);
-  L.tw = align16(L.U + (size_t)W * maxplane * vsize);
+  L.K = align16(L.U + (size_t)W * maxplane * vsize);
+  L.tw = align16(L.K + (size_t)maxplane * (vsize / 2));
   L.rowmap = align16(L.tw + (size_t)N * vsize);
   L.red = align16(L.rowmap + (size_t)N * sizeof(int));
-  L.S = align16(L.red + 8 * 8 * sizeof(double));
+  L.S = align16(L.red + 8 * 16 * sizeof(double));
   L.coef = align16(L.S + (size_t)(1 + 2 * W) * nocc * vsize);
   L.dsum = align16(L.coef + (size_t)2 * W * nocc * vsize);
-  L.col = align16(L.dsum + 24 * sizeof(double));
+  L.ap = align16(L.dsum + 24 * sizeof(double));
+  L.col = align16(L.ap + (size_t)N * 2 * W * sizeof(double));
   L.total = align16(L.col + 2 * 8 * sizeof(double));
   return L;
 }
@@ -293,8 +295,12 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
       Ssum[j] = mk<T>(sx, sy);
     }
     __syncthreads();
-    // FP64 sums: per column Re/Im u^H Y, kin|u|^2, |u|^2 (records) and gamma, |r|^2 (A partials)
+    // FP64 sums: per column Re/Im u^H Y, kin|u|^2, |u|^2 (records) and gamma,
+    // |r|^2 (A partials, staged with one load per thread, then added in plane order)
     const double* ap = a.apart + ((size_t)((it - 1) & 1) * a.ngrp + gi) * P * W * 2;
+    double* aps = reinterpret_cast<double*>(sm + L.ap);
+    for (int j = threadIdx.x; j < P * W * 2; j += blockDim.x) aps[j] = __ldcg(ap + j);
+    __syncthreads();
     for (int j = threadIdx.x; j < 6 * W; j += blockDim.x) {
       double t = 0.0;
       if (j < 4 * W) {
@@ -304,7 +310,7 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
         }
       } else {
         const int k = j - 4 * W;        // c * 2 + (0 gamma, 1 |r|^2)
-        for (int q = 0; q < P; ++q) t += __ldcg(ap + (size_t)q * W * 2 + k);
+        for (int q = 0; q < P; ++q) t += aps[(size_t)q * W * 2 + k];
       }
       dsum[j] = t;
     }
@@ -501,23 +507,18 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
         const T kd = kinG - Ec;
         V w = mk<T>(fv.x + kd * u.x, fv.y + kd * u.y);
         const V* cf = coefT + c * nocc;
-        int v = 0;
-        for (; v + 4 <= nocc; v += 4) {
-          V cv[4];
+        for (int v = 0; v < nocc; v += 8) {       // eight rows of C in flight
+          V cv[8];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) cv[q] = a.C[(size_t)(v + q) * a.npw + G];
+          for (int q = 0; q < 8; ++q) cv[q] = (v + q < nocc) ? a.C[(size_t)(v + q) * a.npw + G] : mk<T>(0, 0);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const V k = cf[v + q];
-            w.x -= cv[q].x * k.x - cv[q].y * k.y;
-            w.y -= cv[q].x * k.y + cv[q].y * k.x;
+          for (int q = 0; q < 8; ++q) {
+            if (v + q < nocc) {
+              const V k = cf[v + q];
+              w.x -= cv[q].x * k.x - cv[q].y * k.y;
+              w.y -= cv[q].x * k.y + cv[q].y * k.x;
+            }
           }
-        }
-        for (; v < nocc; ++v) {
-          const V cv = a.C[(size_t)v * a.npw + G];
-          const V k = cf[v];
-          w.x -= cv.x * k.x - cv.y * k.y;
-          w.y -= cv.x * k.y + cv.y * k.x;
         }
         pv = mk<T>(u.x + bt * pv.x, u.y + bt * pv.y);
         sv = mk<T>(w.x + bt * sv.x, w.y + bt * sv.y);
@@ -628,6 +629,7 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
   V* Ab = reinterpret_cast<V*>(sm + L.A);
   V* Bb = reinterpret_cast<V*>(sm + L.B);
   V* Us = reinterpret_cast<V*>(sm + L.U);          // [W][maxplane] u_c on the plane's entries
+  T* Ks = reinterpret_cast<T*>(sm + L.K);          // [maxplane] |G|^2/2 on the plane's entries
   const V* stw = reinterpret_cast<const V*>(sm + L.tw);
   double* red = reinterpret_cast<double*>(sm + L.red);
   double* dsum = reinterpret_cast<double*>(sm + L.dsum);
@@ -657,6 +659,7 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
   for (int e = threadIdx.x; e < ns; e += blockDim.x) {
     const int G = s0 + e;
     const T kinG = a.kin[G];
+    Ks[e] = kinG;
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       if (c >= W) break;
@@ -715,7 +718,7 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
           const int e = e0 + 32 * u;
           if (e < ns) {
             const V y = Wv[e];
-            const T kk = a.kin[s0 + e];
+            const T kk = Ks[e];
             const V c = cv[u];
             acc[0] += c.x * y.x + c.y * y.y;            // conj(C) Y
             acc[1] += c.x * y.y - c.y * y.x;
@@ -752,7 +755,7 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
     T t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int e = threadIdx.x; e < ns; e += blockDim.x) {
       const V y = Wv[e];
-      const T kk = a.kin[s0 + e];
+      const T kk = Ks[e];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         if (c >= W) break;
@@ -775,8 +778,10 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
   task_time(a.ptask, 2, t0, t1, true);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kPT, 2) k_cg_persistent(PcgArgs<T> a) {
+// TPB threads per CTA: 256 (two CTAs per SM) or 512 (one CTA per SM, twice
+// the threads on each task: shorter tasks, fewer tasks in flight).
+template <typename T, int TPB>
+__global__ void __launch_bounds__(TPB, 512 / TPB) k_cg_persistent(PcgArgs<T> a) {
   using V = cpx<T>;
   extern __shared__ unsigned char smem_raw[];
   const Geometry& g = a.g;
@@ -833,6 +838,39 @@ PcgSizes pcg_sizes(int nocc, int npw, int ncol, int W, int nplanes, int N3, int 
   return z;
 }
 
+template <typename T, int TPB>
+static cudaError_t launch_pcg_tpb(cudaStream_t s, const PcgArgs<T>& a0, size_t sm, int cta_div, int per_it,
+                                  int* grid_used) {
+  cudaError_t e = cudaSuccess;
+  {
+    // The attribute is per function and per process: only ever raise it, so a
+    // context on another host thread never sees its limit lowered under it.
+    static std::mutex mu;
+    static size_t raised = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (sm > raised) {
+      e = cudaFuncSetAttribute(k_cg_persistent<T, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+      raised = sm;
+    }
+  }
+  int dev = 0, nsm = 0, per = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_persistent<T, TPB>, TPB, sm)) != cudaSuccess)
+    return e;
+  if (per < 1) return cudaErrorNotSupported;
+  // cta_div contexts run concurrently (batch mode): each takes an equal share
+  // of the resident slots, so all their grids can be co-resident at once.
+  const int cap = std::max(1, per * nsm / std::max(cta_div, 1));
+  const int nblk = std::min(cap, std::max(per_it, 1));
+  *grid_used = nblk;
+  PcgArgs<T> a = a0;
+  void* args[] = {&a};
+  ++g_launches;
+  return cudaLaunchCooperativeKernel((const void*)k_cg_persistent<T, TPB>, dim3(nblk), dim3(TPB), args, sm, s);
+}
+
 template <typename T>
 cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPlan& pl, const Prec<T>& P, int nocc,
                                  int npw, int ncol, const PcgSizes& z, int maxplane, const double2* b64,
@@ -840,7 +878,7 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
                                  double tol_in2, int maxit, cpx<T>* x, cpx<T>* r, cpx<T>* p, cpx<T>* sv, cpx<T>* Y,
                                  cpx<T>* grid, unsigned char* rec, double* apart, PcgCol* cst, unsigned* ctl,
                                  int* iters, int* flags, double* rr_out, int* grid_used, int cta_div,
-                                 unsigned long long spin_limit, unsigned long long* ptask) {
+                                 unsigned long long spin_limit, unsigned long long* ptask, int tpb) {
   PcgArgs<T> a;
   a.g = g; a.pl = pl; a.tw = P.tw; a.kin = P.kin; a.vloc_s = P.vloc_s; a.C = P.C;
   a.nocc = nocc; a.npw = npw; a.ncol = ncol; a.ngrp = z.ngrp; a.W = z.W; a.maxplane = maxplane;
@@ -851,34 +889,9 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
   a.iters_out = iters; a.flag_out = flags; a.rr_out = rr_out; a.spin_limit = spin_limit; a.ptask = ptask;
   const size_t sm = pcg_smem<T>(g.N, nocc, z.W, maxplane);
   if (sm > 227 * 1024) return cudaErrorNotSupported;
-  cudaError_t e = cudaSuccess;
-  {
-    // The attribute is per function and per process: only ever raise it, so a
-    // context on another host thread never sees its limit lowered under it.
-    static std::mutex mu;
-    static size_t raised = 0;
-    std::lock_guard<std::mutex> lock(mu);
-    if (sm > raised) {
-      e = cudaFuncSetAttribute(k_cg_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return e;
-      raised = sm;
-    }
-  }
-  int dev = 0, nsm = 0, per = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_persistent<T>, kPT, sm)) != cudaSuccess)
-    return e;
-  if (per < 1) return cudaErrorNotSupported;
-  // cta_div contexts run concurrently (batch mode): each takes an equal share
-  // of the resident slots, so all their grids can be co-resident at once.
-  const int cap = std::max(1, per * nsm / std::max(cta_div, 1));
   const int per_it = z.ngrp * (2 * g.nplanes + g.N);
-  const int nblk = std::min(cap, std::max(per_it, 1));
-  *grid_used = nblk;
-  void* args[] = {&a};
-  ++g_launches;
-  return cudaLaunchCooperativeKernel((const void*)k_cg_persistent<T>, dim3(nblk), dim3(kPT), args, sm, s);
+  if (tpb == 512) return launch_pcg_tpb<T, 512>(s, a, sm, cta_div, per_it, grid_used);
+  return launch_pcg_tpb<T, 256>(s, a, sm, cta_div, per_it, grid_used);
 }
 
 #define GW_PCG_INST(T)                                                                                      \
@@ -886,7 +899,7 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
       cudaStream_t, const Geometry&, const FftPlan&, const Prec<T>&, int, int, int, const PcgSizes&, int,    \
       const double2*, const int*, const double2*, const double*, const double*, double, int, cpx<T>*,       \
       cpx<T>*, cpx<T>*, cpx<T>*, cpx<T>*, cpx<T>*, unsigned char*, double*, PcgCol*, unsigned*, int*, int*,  \
-      double*, int*, int, unsigned long long, unsigned long long*);
+      double*, int*, int, unsigned long long, unsigned long long*, int);
 GW_PCG_INST(float)
 GW_PCG_INST(double)
 

@@ -227,7 +227,8 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
                                  double tol_in2, int maxit, cpx<T>* x, cpx<T>* r, cpx<T>* p, cpx<T>* sv, cpx<T>* Y,
                                  cpx<T>* grid, unsigned char* rec, double* apart, PcgCol* cst, unsigned* ctl,
                                  int* iters, int* flags, double* rr_out, int* grid_used, int cta_div,
-                                 unsigned long long spin_limit, unsigned long long* ptask = nullptr);
+                                 unsigned long long spin_limit, unsigned long long* ptask = nullptr,
+                                 int tpb = 256);
 // One thread-block cluster per column (kernels_cgc.cu); cudaErrorNotSupported
 // when the column's planes do not fit in the shared memory of a cluster.
 template <typename T>
