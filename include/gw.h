@@ -545,10 +545,13 @@ gw_status gw_sigma_c(gw_ctx* ctx, int e, double delta, double alpha, int n_freq,
  * 9 the persistent CG's tasks, timed inside the kernel (global timer): read
  * back as entries 10..15 = task kind A busy, A waiting, B busy, B waiting,
  * C busy, C waiting (milliseconds summed over tasks; counts: tasks run for
- * "busy", tasks skipped for "waiting").
+ * "busy", tasks skipped for "waiting"), then 16..24 the busy time of sub-phases:
+ * A sums and decisions, A update and scatter, A transforms; B slab load, B
+ * transforms and V; C plane load, C transforms and gather (the remainder of a
+ * task's busy time: stores, dot products, signalling).
  * gw_profile_read -- per class: total milliseconds and launches since the last
  * read (synchronises the stream; resets the totals); n >= 16 for the task
- * entries.
+ * entries, n >= 25 for the sub-phases.
  */
 gw_status gw_profile(gw_ctx* ctx, unsigned mask);
 gw_status gw_profile_read(gw_ctx* ctx, double* ms, long long* count, int n);

@@ -37,7 +37,8 @@ EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "
            "gw_set_autotune")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
                    "refine_fp64", "persistent_cg", "pcg_tasks", "pcg_A_busy", "pcg_A_wait", "pcg_B_busy",
-                   "pcg_B_wait", "pcg_C_busy", "pcg_C_wait")
+                   "pcg_B_wait", "pcg_C_busy", "pcg_C_wait", "pcg_A_sums", "pcg_A_update", "pcg_A_fft",
+                   "pcg_B_load", "pcg_B_fft", "pcg_B_unused", "pcg_C_load", "pcg_C_fft", "pcg_C_unused")
 
 
 class GwError(RuntimeError):

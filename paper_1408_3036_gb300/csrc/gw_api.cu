@@ -71,7 +71,7 @@ struct gw_ctx {
   std::string err;
   // optional per-kernel-class timing with CUDA events on the work stream
   unsigned prof_mask = 0;
-  unsigned long long* ptask = nullptr;   // device [12] task timing of the persistent CG (PC_TASKS)
+  unsigned long long* ptask = nullptr;   // device [24] task timing of the persistent CG (PC_TASKS)
   cudaEvent_t tune_ev[2] = {nullptr, nullptr};   // autotuner timing events
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<int, int>>> ev_used;   // (class, (start, end))
@@ -497,8 +497,8 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
     unsigned long long* ptask = nullptr;
     if (ctx->prof_mask & (1u << PC_TASKS)) {
       if (!ctx->ptask) {
-        TRY(getbuf(ctx, "pcg_ptask", 12, &ctx->ptask));
-        CK(cudaMemsetAsync(ctx->ptask, 0, 12 * sizeof(unsigned long long), ctx->st));
+        TRY(getbuf(ctx, "pcg_ptask", 24, &ctx->ptask));
+        CK(cudaMemsetAsync(ctx->ptask, 0, 24 * sizeof(unsigned long long), ctx->st));
       }
       ptask = ctx->ptask;
     }
@@ -3156,14 +3156,16 @@ gw_status gw_profile_read(gw_ctx* ctx, double* ms, long long* count, int n) {
   ctx->ev_used.clear();
   ctx->ev_next = 0;
   if (ctx->ptask && n > PC_TASKS + 6) {
-    unsigned long long h[12];
+    unsigned long long h[24];
     CK(cudaMemcpy(h, ctx->ptask, sizeof(h), cudaMemcpyDeviceToHost));
     CK(cudaMemset(ctx->ptask, 0, sizeof(h)));
     for (int k = 0; k < 3; ++k) {
-      ms[PC_TASKS + 1 + 2 * k] = 1e-6 * (double)h[4 * k + 1];       // busy
-      count[PC_TASKS + 1 + 2 * k] = (long long)h[4 * k + 0];
-      ms[PC_TASKS + 2 + 2 * k] = 1e-6 * (double)h[4 * k + 2];       // waiting
-      count[PC_TASKS + 2 + 2 * k] = (long long)h[4 * k + 3];
+      ms[PC_TASKS + 1 + 2 * k] = 1e-6 * (double)h[8 * k + 1];       // busy
+      count[PC_TASKS + 1 + 2 * k] = (long long)h[8 * k + 0];
+      ms[PC_TASKS + 2 + 2 * k] = 1e-6 * (double)h[8 * k + 2];       // waiting
+      count[PC_TASKS + 2 + 2 * k] = (long long)h[8 * k + 3];
+      for (int j = 0; j < 3; ++j)                                      // sub-phases
+        if (n > PC_TASKS + 7 + 3 * k + j) ms[PC_TASKS + 7 + 3 * k + j] = 1e-6 * (double)h[8 * k + 4 + j];
     }
   }
   return GW_OK;

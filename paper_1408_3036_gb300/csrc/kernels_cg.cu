@@ -92,7 +92,8 @@ struct PcgArgs {
   int* flag_out;
   double* rr_out;
   unsigned long long spin_limit;
-  unsigned long long* ptask;  // optional [3][4]: per task kind A, B, C: tasks run, busy ns, wait ns, skipped
+  unsigned long long* ptask;  // optional [3][8]: per task kind A, B, C: tasks run, busy ns, wait ns, skipped,
+                              // then the busy time of up to three sub-phases (ns)
 };
 
 template <typename V> __device__ __forceinline__ V ldcg(const V* p);
@@ -202,7 +203,7 @@ __device__ __forceinline__ unsigned long long gtime() {
 __device__ __forceinline__ void task_time(unsigned long long* pt, int kind, unsigned long long t0,
                                           unsigned long long t1, bool ran) {
   if (!pt || threadIdx.x != 0) return;
-  unsigned long long* q = pt + 4 * kind;
+  unsigned long long* q = pt + 8 * kind;
   if (ran) {
     atomicAdd(q + 0, 1ull);
     atomicAdd(q + 1, gtime() - t1);
@@ -210,6 +211,15 @@ __device__ __forceinline__ void task_time(unsigned long long* pt, int kind, unsi
     atomicAdd(q + 3, 1ull);
   }
   atomicAdd(q + 2, t1 - t0);
+}
+
+// Optional sub-phase mark (thread 0): adds now - *t to slot 4 + k of the task
+// kind and moves *t to now.
+__device__ __forceinline__ void task_mark(unsigned long long* pt, int kind, int k, unsigned long long* t) {
+  if (!pt || threadIdx.x != 0) return;
+  const unsigned long long now = gtime();
+  atomicAdd(pt + 8 * kind + 4 + k, now - *t);
+  *t = now;
 }
 
 // Completion of a task: every thread's writes fenced, then one count.
@@ -435,6 +445,8 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
     }
   }
 
+  unsigned long long tm = t1;
+  task_mark(a.ptask, 0, 0, &tm);       // sums and decisions
   // ---- update the plane's entries and scatter the packed u = K r
   for (int e = threadIdx.x; e < npp * LDp; e += blockDim.x) Ab[e] = mk<T>(0, 0);
   for (int k = threadIdx.x; k < N; k += blockDim.x) rowmap[k] = -1;
@@ -547,6 +559,7 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
     }
   }
   __syncthreads();
+  task_mark(a.ptask, 0, 1, &tm);       // update and scatter
   // ---- z-IFFT of the disc rows, transpose into the plane, y-IFFT, store
   V* R = fft_tile2<T, +1, false>(Ab, Bb, npp, LDp, 1, a.pl, stw);
   V* Q = (R == Ab) ? Bb : Ab;
@@ -557,6 +570,7 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
   }
   __syncthreads();
   V* S = fft_tile2<T, +1, true>(Q, R, N, 1, LDp, a.pl, stw);
+  task_mark(a.ptask, 0, 2, &tm);       // transforms
   const size_t base = (size_t)gi * g.N3 + (size_t)i0 * g.N2;
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int i1 = a.pl.dN.div(e), i2 = e - i1 * N;
@@ -596,6 +610,8 @@ __device__ void task_B(const PcgArgs<T>& a, int it, int gi, int i1, unsigned cha
     Ab[i0 * LDp + i2] = g.plane_mask[i0] ? ldcg(a.grid + base + (size_t)i0 * g.N2 + i2) : mk<T>(0, 0);
   }
   __syncthreads();
+  unsigned long long tm = t1;
+  task_mark(a.ptask, 1, 0, &tm);       // slab load
   V* R = fft_tile2<T, +1, true>(Ab, Bb, N, 1, LDp, a.pl, stw);
   V* Q = (R == Ab) ? Bb : Ab;
 #pragma unroll 4
@@ -607,6 +623,7 @@ __device__ void task_B(const PcgArgs<T>& a, int it, int gi, int i1, unsigned cha
   }
   __syncthreads();
   V* S = fft_tile2<T, -1, true>(R, Q, N, 1, LDp, a.pl, stw);
+  task_mark(a.ptask, 1, 1, &tm);       // transforms and V
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int i0 = a.pl.dN.div(e), i2 = e - i0 * N;
     if (g.plane_mask[i0]) a.grid[base + (size_t)i0 * g.N2 + i2] = S[i0 * LDp + i2];
@@ -675,6 +692,8 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
     }
   }
   __syncthreads();
+  unsigned long long tm = t1;
+  task_mark(a.ptask, 2, 0, &tm);       // plane and u loads
   V* R = fft_tile2<T, -1, true>(Ab, Bb, N, 1, LDp, a.pl, stw);
   V* Q = (R == Ab) ? Bb : Ab;
   for (int e = threadIdx.x; e < npp * N; e += blockDim.x) {
@@ -692,6 +711,7 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
     Wv[e] = val;
   }
   __syncthreads();
+  task_mark(a.ptask, 2, 1, &tm);       // transforms and gather
   // ---- the record: projector sums (warp per pair of occupied states, lanes
   // over entries, eight entries in flight), then the FP64 scalar sums
   unsigned char* rec = a.rec + ((size_t)gi * g.nplanes + pi) * a.rec_bytes;
