@@ -137,7 +137,7 @@ __device__ __forceinline__ void block_sum_n(double (&v)[NV], double* sh, double*
 }
 
 struct PcgLayout {
-  size_t A, B, U, K, tw, rowmap, red, S, coef, dsum, ap, col, total;
+  size_t A, B, U, K, tw, rowmap, red, S, coef, dsum, ap, col, pre, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -161,7 +161,8 @@ __host__ __device__ inline PcgLayout pcg_layout(int N, int nocc, int W, int maxp
   L.dsum = align16(L.coef + (size_t)2 * W * nocc * vsize);
   L.ap = align16(L.dsum + 24 * sizeof(double));
   L.col = align16(L.ap + (size_t)N * 2 * W * sizeof(double));
-  L.total = align16(L.col + 2 * 8 * sizeof(double));
+  L.pre = align16(L.col + 2 * 8 * sizeof(double));
+  L.total = align16(L.pre + 2 * (4 * sizeof(double) + sizeof(PcgCol)));
   return L;
 }
 
@@ -281,7 +282,9 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
       colv[c * 8 + 4] = (present && a.tk) ? 1.0 / a.tk[c0 + c] : 0.0;
     }
   } else {
-    // stage the group's P records (shared-memory tiles A and B) when they fit
+    // One round of loads: the group's P records (shared-memory tiles A and B,
+    // when they fit), the A partials of the previous iteration, and each
+    // column's state and inputs; then every sum from shared memory.
     const unsigned char* src = a.rec + (size_t)gi * P * rb;
     const size_t nb16 = (size_t)P * rb / 16;
     const bool staged = nb16 * 16 <= L.U - L.A;
@@ -291,45 +294,55 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
       float4* d4 = reinterpret_cast<float4*>(sm + L.A);
       for (size_t e = threadIdx.x; e < nb16; e += blockDim.x) d4[e] = __ldcg(s4 + e);
     }
-    __syncthreads();
-    // projector sums in T, plane order: value j of every record
-    const size_t dbase = align16((size_t)nv * sizeof(V));
-    for (int j = threadIdx.x; j < nv; j += blockDim.x) {
-      T sx = 0, sy = 0;
-      for (int q = 0; q < P; ++q) {
-        const V v = staged ? reinterpret_cast<const V*>(stg + (size_t)q * rb)[j]
-                           : ldcg(reinterpret_cast<const V*>(stg + (size_t)q * rb) + j);
-        sx += v.x;
-        sy += v.y;
-      }
-      Ssum[j] = mk<T>(sx, sy);
-    }
-    __syncthreads();
-    // FP64 sums: per column Re/Im u^H Y, kin|u|^2, |u|^2 (records) and gamma,
-    // |r|^2 (A partials, staged with one load per thread, then added in plane order)
     const double* ap = a.apart + ((size_t)((it - 1) & 1) * a.ngrp + gi) * P * W * 2;
     double* aps = reinterpret_cast<double*>(sm + L.ap);
     for (int j = threadIdx.x; j < P * W * 2; j += blockDim.x) aps[j] = __ldcg(ap + j);
+    double* pre = reinterpret_cast<double*>(sm + L.pre);                  // [W][4]: E, T_ref, on, |r|^2 target
+    PcgCol* pcs = reinterpret_cast<PcgCol*>(sm + L.pre + 2 * 4 * sizeof(double));
+    if (threadIdx.x < nc) {
+      const int col = c0 + threadIdx.x;
+      pre[threadIdx.x * 4 + 0] = a.E[col].x;
+      pre[threadIdx.x * 4 + 1] = a.tk ? a.tk[col] : 0.0;
+      pre[threadIdx.x * 4 + 2] = (!a.outer_active || a.outer_active[col]) ? 1.0 : 0.0;
+      pre[threadIdx.x * 4 + 3] = a.rr_abs ? a.rr_abs[col] : 0.0;
+      if (it > 1) pcs[threadIdx.x] = ld_col(a.cst + (size_t)((it - 1) & 1) * a.ncol + col);
+    }
     __syncthreads();
-    for (int j = threadIdx.x; j < 6 * W; j += blockDim.x) {
-      double t = 0.0;
-      if (j < 4 * W) {
+    // projector sums in T (threads j < nv) and the FP64 sums (the next 6 W
+    // threads: per column Re/Im u^H Y, kin|u|^2, |u|^2 of the records, gamma
+    // and |r|^2 of the A partials), each over the planes in order
+    const size_t dbase = align16((size_t)nv * sizeof(V));
+    for (int j = threadIdx.x; j < nv + 6 * W; j += blockDim.x) {
+      if (j < nv) {
+        T sx = 0, sy = 0;
         for (int q = 0; q < P; ++q) {
-          const double* d = reinterpret_cast<const double*>(stg + (size_t)q * rb + dbase);
-          t += staged ? d[j] : __ldcg(d + j);
+          const V v = staged ? reinterpret_cast<const V*>(stg + (size_t)q * rb)[j]
+                             : ldcg(reinterpret_cast<const V*>(stg + (size_t)q * rb) + j);
+          sx += v.x;
+          sy += v.y;
         }
+        Ssum[j] = mk<T>(sx, sy);
       } else {
-        const int k = j - 4 * W;        // c * 2 + (0 gamma, 1 |r|^2)
-        for (int q = 0; q < P; ++q) t += aps[(size_t)q * W * 2 + k];
+        const int jj = j - nv;
+        double t = 0.0;
+        if (jj < 4 * W) {
+          for (int q = 0; q < P; ++q) {
+            const double* d = reinterpret_cast<const double*>(stg + (size_t)q * rb + dbase);
+            t += staged ? d[jj] : __ldcg(d + jj);
+          }
+        } else {
+          const int k = jj - 4 * W;        // c * 2 + (0 gamma, 1 |r|^2)
+          for (int q = 0; q < P; ++q) t += aps[(size_t)q * W * 2 + k];
+        }
+        dsum[jj] = t;
       }
-      dsum[j] = t;
     }
     __syncthreads();
     // coefficients per column c: coef_v = FV_c,v + K_c,v - E_c U_c,v, with
     // FV = Re D (c = 0) or Im D (c = 1) for a packed pair (real: taken real), D otherwise
     for (int j = threadIdx.x; j < W * nocc; j += blockDim.x) {
       const int c = j / nocc, v = j - c * nocc;
-      const T Ec = (T)((c < nc) ? a.E[c0 + c].x : 0.0);
+      const T Ec = (T)((c < nc) ? pre[c * 4 + 0] : 0.0);
       const V D = Ssum[v], K = Ssum[(1 + c) * nocc + v], U = Ssum[(1 + W + c) * nocc + v];
       V cf;
       if (W == 2) {
@@ -363,16 +376,16 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
       cv[2] = 0.0;
       if (c < nc) {
         const int col = c0 + c;
-        const double Ec = a.E[col].x;
+        const double Ec = pre[c * 4 + 0];
         const double uY = (W == 2) ? dsum[c * 4 + ((c == 0) ? 0 : 1)] : dsum[c * 4];
         const double delta = uY + dsum[c * 4 + 2] - Ec * dsum[c * 4 + 3] - red[c];
         const double gam = dsum[4 * W + c * 2], rr = dsum[4 * W + c * 2 + 1];
         PcgCol st;
         if (it == 1) {
-          const bool on = !a.outer_active || a.outer_active[col];
+          const bool on = pre[c * 4 + 2] != 0.0;
           st.gam = 0.0;
           st.alpha = 0.0;
-          st.stop = fmax(a.tol_in2 * rr, a.rr_abs ? a.rr_abs[col] : 0.0);
+          st.stop = fmax(a.tol_in2 * rr, pre[c * 4 + 3]);
           st.rmin = rr;
           st.rbest = rr;
           st.it = 0;
@@ -381,7 +394,7 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
           st.flag = 0;
           if (!st.active) st.flag = 0;
         } else {
-          st = ld_col(a.cst + (size_t)((it - 1) & 1) * a.ncol + col);
+          st = pcs[c];
         }
         const bool was = st.active != 0;
         if (st.active) {
@@ -416,7 +429,7 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
           }
         }
         cv[3] = Ec;
-        cv[4] = a.tk ? 1.0 / a.tk[col] : 0.0;
+        cv[4] = pre[c * 4 + 1] != 0.0 ? 1.0 / pre[c * 4 + 1] : 0.0;
         if (pi == 0) {
           a.cst[(size_t)(it & 1) * a.ncol + col] = st;
           if (!st.active && (was || it == 1)) {
@@ -519,12 +532,13 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
         const T kd = kinG - Ec;
         V w = mk<T>(fv.x + kd * u.x, fv.y + kd * u.y);
         const V* cf = coefT + c * nocc;
-        for (int v = 0; v < nocc; v += 8) {       // eight rows of C in flight
-          V cv[8];
+        constexpr int RB = (sizeof(T) == 4) ? 16 : 8;   // rows of C in flight
+        for (int v = 0; v < nocc; v += RB) {
+          V cv[RB];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) cv[q] = (v + q < nocc) ? a.C[(size_t)(v + q) * a.npw + G] : mk<T>(0, 0);
+          for (int q = 0; q < RB; ++q) cv[q] = (v + q < nocc) ? a.C[(size_t)(v + q) * a.npw + G] : mk<T>(0, 0);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
+          for (int q = 0; q < RB; ++q) {
             if (v + q < nocc) {
               const V k = cf[v + q];
               w.x -= cv[q].x * k.x - cv[q].y * k.y;
@@ -604,7 +618,7 @@ __device__ void task_B(const PcgArgs<T>& a, int it, int gi, int i1, unsigned cha
   if (s_ctl[0] == 1) task_time(a.ptask, 1, t0, t1, false);
   if (s_ctl[0] != 0) return;
   const size_t base = (size_t)gi * g.N3 + (size_t)i1 * N;
-#pragma unroll 4
+#pragma unroll 8
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int i0 = a.pl.dN.div(e), i2 = e - i0 * N;
     Ab[i0 * LDp + i2] = g.plane_mask[i0] ? ldcg(a.grid + base + (size_t)i0 * g.N2 + i2) : mk<T>(0, 0);
@@ -664,7 +678,7 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
   const int q0 = g.plane_pen[pi], npp = g.plane_pen[pi + 1] - q0;
   const int ns = s1 - s0;
   const size_t base = (size_t)gi * g.N3 + (size_t)i0 * g.N2;
-#pragma unroll 4
+#pragma unroll 8
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int i1 = a.pl.dN.div(e), i2 = e - i1 * N;
     Ab[i1 * LDp + i2] = ldcg(a.grid + base + e);
@@ -717,21 +731,29 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
   unsigned char* rec = a.rec + ((size_t)gi * g.nplanes + pi) * a.rec_bytes;
   V* rv = reinterpret_cast<V*>(rec);
   {
-    constexpr int UE = 4;
+    // a warp takes the occupied states v and v + nw together, its lanes UE
+    // entries each with all their loads of C in flight before the products
+    constexpr int UE = (sizeof(T) == 4) ? 8 : 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const V* U0 = Us;
     const V* U1 = Us + a.maxplane;
-    for (int v = warp; v < nocc; v += nw) {
-      const V* Cv = a.C + (size_t)v * a.npw + s0;
-      T acc[10];
+    for (int v0 = warp; v0 < nocc; v0 += 2 * nw) {
+      const int v1 = v0 + nw;
+      const bool two = v1 < nocc;
+      const V* C0 = a.C + (size_t)v0 * a.npw + s0;
+      const V* C1 = a.C + (size_t)(two ? v1 : v0) * a.npw + s0;
+      T acc[2][10];
 #pragma unroll
-      for (int k = 0; k < 10; ++k) acc[k] = (T)0;
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int k = 0; k < 10; ++k) acc[h][k] = (T)0;
       for (int e0 = lane; e0 < ns; e0 += 32 * UE) {
-        V cv[UE];
+        V cv[2][UE];
 #pragma unroll
         for (int u = 0; u < UE; ++u) {
           const int e = e0 + 32 * u;
-          cv[u] = (e < ns) ? Cv[e] : mk<T>(0, 0);
+          cv[0][u] = (e < ns) ? C0[e] : mk<T>(0, 0);
+          cv[1][u] = (e < ns && two) ? C1[e] : mk<T>(0, 0);
         }
 #pragma unroll
         for (int u = 0; u < UE; ++u) {
@@ -739,34 +761,46 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
           if (e < ns) {
             const V y = Wv[e];
             const T kk = Ks[e];
-            const V c = cv[u];
-            acc[0] += c.x * y.x + c.y * y.y;            // conj(C) Y
-            acc[1] += c.x * y.y - c.y * y.x;
             const V u0 = U0[e];
-            acc[2] += kk * (c.x * u0.x + c.y * u0.y);   // conj(C) kin u_0
-            acc[3] += kk * (c.x * u0.y - c.y * u0.x);
-            acc[4] += c.x * u0.x + c.y * u0.y;          // conj(C) u_0
-            acc[5] += c.x * u0.y - c.y * u0.x;
-            if (W == 2) {
-              const V u1 = U1[e];
-              acc[6] += kk * (c.x * u1.x + c.y * u1.y);
-              acc[7] += kk * (c.x * u1.y - c.y * u1.x);
-              acc[8] += c.x * u1.x + c.y * u1.y;
-              acc[9] += c.x * u1.y - c.y * u1.x;
+            const V u1 = (W == 2) ? U1[e] : mk<T>(0, 0);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const V c = cv[h][u];
+              T* A = acc[h];
+              A[0] += c.x * y.x + c.y * y.y;            // conj(C) Y
+              A[1] += c.x * y.y - c.y * y.x;
+              A[2] += kk * (c.x * u0.x + c.y * u0.y);   // conj(C) kin u_0
+              A[3] += kk * (c.x * u0.y - c.y * u0.x);
+              A[4] += c.x * u0.x + c.y * u0.y;          // conj(C) u_0
+              A[5] += c.x * u0.y - c.y * u0.x;
+              if (W == 2) {
+                A[6] += kk * (c.x * u1.x + c.y * u1.y);
+                A[7] += kk * (c.x * u1.y - c.y * u1.x);
+                A[8] += c.x * u1.x + c.y * u1.y;
+                A[9] += c.x * u1.y - c.y * u1.x;
+              }
             }
           }
         }
       }
 #pragma unroll
-      for (int k = 0; k < 10; ++k)
-        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int k = 0; k < 10; ++k)
+          for (int o = 16; o > 0; o >>= 1) acc[h][k] += __shfl_xor_sync(0xffffffffu, acc[h][k], o);
       if (lane == 0) {
-        rv[v] = mk<T>(acc[0], acc[1]);
-        rv[(1 + 0) * nocc + v] = mk<T>(acc[2], acc[3]);
-        rv[(1 + W + 0) * nocc + v] = mk<T>(acc[4], acc[5]);
-        if (W == 2) {
-          rv[(1 + 1) * nocc + v] = mk<T>(acc[6], acc[7]);
-          rv[(1 + W + 1) * nocc + v] = mk<T>(acc[8], acc[9]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && !two) break;
+          const int v = h ? v1 : v0;
+          const T* A = acc[h];
+          rv[v] = mk<T>(A[0], A[1]);
+          rv[(1 + 0) * nocc + v] = mk<T>(A[2], A[3]);
+          rv[(1 + W + 0) * nocc + v] = mk<T>(A[4], A[5]);
+          if (W == 2) {
+            rv[(1 + 1) * nocc + v] = mk<T>(A[6], A[7]);
+            rv[(1 + W + 1) * nocc + v] = mk<T>(A[8], A[9]);
+          }
         }
       }
     }
