@@ -684,6 +684,53 @@ def run_gpu(args):
             bfl = dict(skipped=f"ground state not converged or gap too small (residual {bres:.2e})")
         bcell.close()
 
+    # --- many uneven cells at once (32 cells, K = 40, four real frequencies each)
+    bat = None
+    if args.batch_cells > 0:
+        from paper_1408_3036_gb300.groundstate import levels_below
+        bw = W.batch(n_cells=args.batch_cells)
+        bt = gw.Batch([(x.L, x.N, x.ecut, x.vloc) for x in bw.cells], workers=8)
+        bom = np.tile(np.array(bw.omegas, complex), (len(bw.cells), 1))
+        t_prep = time.perf_counter()
+        nredraw = 0
+        for i, x in enumerate(bw.cells):
+            # input preparation on a context of its own on the bench stream (a
+            # batch cell's context works on the batch's stream)
+            prep = gw.Cell(x.L, x.N, x.ecut, x.vloc, 0, stream.cuda_stream)
+            e_occ, p_occ, _ = lowest_states(prep, x.n_occ, tol=1e-10)
+            bt.cell(i).set_occupied(p_occ, e_occ[:x.n_occ])
+            lev = levels_below(prep, e_occ[x.n_occ - 1] + 1.01, x.n_occ + 1)
+            prep.close()
+            tr = np.subtract.outer(lev[x.n_occ:], lev[:x.n_occ]).ravel()
+            for w in range(bom.shape[1]):
+                att = 0
+                while tr.size and np.abs(tr - bom[i, w].real).min() <= 1e-3:   # re-drawn per cell
+                    att += 1
+                    nredraw += 1
+                    bom[i, w] = W.redraw_omega(W.BASE_SEED + 3 + 1000 * att + 100 * i + w, 0.0, 1.0)
+        t_prep = time.perf_counter() - t_prep
+        bst = [x[0] for x in bw.starts]
+        rows = []
+        for graphs in (1, 0):
+            for i in range(len(bw.cells)):
+                bt.cell(i).set_graphs(graphs)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bt.lanczos(bst, bw.k, bom, prec)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            replays = sum(gw.gw_stats(bt.cell(i).ctx)["graph_replays"] for i in range(len(bw.cells)))
+            rows.append(dict(cuda_graphs=bool(graphs), s=dt,
+                             applies_per_s=len(bw.cells) * bom.shape[1] * bw.k / dt,
+                             status_ok=int((bt.last_status == 0).sum()),
+                             graph_replays_last_solve=int(replays)))
+        bat = dict(workload="%d uneven cells (L 8-16 bohr, N 24-48, 5-10 Ha, N_occ 4-32), K=%d, "
+                   "4 real omega in [0,1] per cell" % (len(bw.cells), bw.k),
+                   precision=args.prec, frequencies_redrawn=nredraw, prep_s=t_prep, runs=rows,
+                   timing="host wall clock around the whole batch call (all cells, all frequencies)",
+                   unit="eps~ applications per second (all cells)")
+        bt.close()
+
     if rank == 0:
         line = dict(
             metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -700,6 +747,7 @@ def run_gpu(args):
             roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
             clocks=clk.summary(), fp64=fp64, profile_ms={k: v[0] for k, v in prof.items() if v[1]},
             model_operator=model, sigma_p=sigp, recycle=rec, sigma_c=sigc, block_freq=bfl,
+            batch=bat,
         )
         print(json.dumps(line))
     cell.close()
@@ -730,6 +778,8 @@ def main():
                     help="Lanczos steps per pole of the Sigma^P leg (Eq. pe; 0: skip)")
     ap.add_argument("--block-freq-steps", type=int, default=1,
                     help="block Lanczos steps timed on the full block complex-frequency workload (0: skip)")
+    ap.add_argument("--batch-cells", type=int, default=32,
+                    help="cells of the many-cell leg (0: skip)")
     ap.add_argument("--deflation", type=int, default=0,
                     help="lowest conduction states handed to the solvers as a deflation block (0: none)")
     args = ap.parse_args()

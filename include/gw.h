@@ -174,6 +174,26 @@ gw_status gw_lanczos(gw_ctx* ctx, const double* start, int blk, int k, const dou
                      double* alpha, double* beta, double* basis, gw_prec prec, int device_ptrs);
 
 /*
+ * gw_lanczos_resume -- continue a real-frequency recursion of gw_lanczos from
+ * a saved state (checkpoint/resume; not in the paper): the first k0 + 1
+ * vectors and the coefficients of its first k0 steps, e.g. the output of a
+ * gw_lanczos call with k0 + 1 steps.  Steps k0 .. k-1 then run as in
+ * gw_lanczos (step k0 is recomputed from the saved vectors), so alpha and beta
+ * equal those of an uninterrupted k-step run to rounding.
+ *   basis_in  [k0 + 1][N^3] real: q_1 .. q_{k0+1}
+ *   alpha_in  [k0] real;  beta_in [k0] real (beta_1 .. beta_k0)
+ *   k0 >= 1, k > k0;  omega real (imaginary part 0)
+ *   alpha     [k] real;  beta [k-1] real;  basis [k][N^3] or NULL
+ * The saved state is checked before any step: coefficients finite, beta > 0,
+ * vectors orthonormal in <.|.> to 1e-8; a state that fails returns GW_E_ARG
+ * (a damaged checkpoint) and nothing is written.  With device_ptrs, basis may
+ * equal basis_in (resumed in place; it must then hold k rows).
+ */
+gw_status gw_lanczos_resume(gw_ctx* ctx, const double* basis_in, const double* alpha_in, const double* beta_in,
+                            int k0, int k, const double* omega, double* alpha, double* beta, double* basis,
+                            gw_prec prec, int device_ptrs);
+
+/*
  * gw_block_lanczos -- k block steps of the Lanczos recursion on eps~(omega)
  * from a block of blk real start fields (Sec. Lanczos; block form, with
  * classical Gram-Schmidt applied twice against all previous blocks):
@@ -545,13 +565,15 @@ gw_status gw_sigma_c(gw_ctx* ctx, int e, double delta, double alpha, int n_freq,
  * 9 the persistent CG's tasks, timed inside the kernel (global timer): read
  * back as entries 10..15 = task kind A busy, A waiting, B busy, B waiting,
  * C busy, C waiting (milliseconds summed over tasks; counts: tasks run for
- * "busy", tasks skipped for "waiting"), then 16..24 the busy time of sub-phases:
- * A sums and decisions, A update and scatter, A transforms; B slab load, B
- * transforms and V; C plane load, C transforms and gather (the remainder of a
- * task's busy time: stores, dot products, signalling).
+ * "busy", tasks skipped for "waiting"), then 16..27 the busy time of four
+ * sub-phases per kind: A loads (records, partials, column state), A sums and
+ * decisions, A update and scatter, A transforms; B slab load, B transforms and
+ * V, B store, (unused); C plane and u loads, C transforms and gather, C
+ * projector dots, C scalar sums and record (the remainder of a task's busy
+ * time is its stores and signalling).
  * gw_profile_read -- per class: total milliseconds and launches since the last
  * read (synchronises the stream; resets the totals); n >= 16 for the task
- * entries, n >= 25 for the sub-phases.
+ * entries, n >= 28 for the sub-phases.
  */
 gw_status gw_profile(gw_ctx* ctx, unsigned mask);
 gw_status gw_profile_read(gw_ctx* ctx, double* ms, long long* count, int n);

@@ -34,11 +34,12 @@ EXPORTS = ("gw_setup", "gw_npw", "gw_sphere", "gw_set_occupied", "gw_apply_h", "
            "gw_batch_last_error", "gw_batch_destroy", "gw_set_operator", "gw_epsinv_split", "gw_sigma_p", "gw_recycle_eps", "gw_sigma_c",
            "gw_set_cg_kernel", "gw_grad_vloc_basis", "gw_set_graphs", "gw_set_imaginary_route",
            "gw_set_recycle_augment", "gw_proj_coef", "gw_set_tensor_cores",
-           "gw_set_autotune")
+           "gw_set_autotune", "gw_lanczos_resume")
 PROFILE_CLASSES = ("z_scatter_inv", "y_inv", "x_h", "y_fwd", "z_gather_h", "proj", "cg_update",
                    "refine_fp64", "persistent_cg", "pcg_tasks", "pcg_A_busy", "pcg_A_wait", "pcg_B_busy",
-                   "pcg_B_wait", "pcg_C_busy", "pcg_C_wait", "pcg_A_sums", "pcg_A_update", "pcg_A_fft",
-                   "pcg_B_load", "pcg_B_fft", "pcg_B_unused", "pcg_C_load", "pcg_C_fft", "pcg_C_unused")
+                   "pcg_B_wait", "pcg_C_busy", "pcg_C_wait", "pcg_A_load", "pcg_A_sums", "pcg_A_update",
+                   "pcg_A_fft", "pcg_B_load", "pcg_B_fft", "pcg_B_store", "pcg_B_unused", "pcg_C_load",
+                   "pcg_C_fft", "pcg_C_dots", "pcg_C_sums")
 
 
 class GwError(RuntimeError):
@@ -70,6 +71,7 @@ def load(path=LIB_PATH):
         "gw_apply_chi0_c": (I, [P, P, I, P, I, P, I, I]),
         "gw_apply_eps_c": (I, [P, P, I, P, I, P, I, I]),
         "gw_lanczos": (I, [P, P, I, I, P, P, P, P, I, I]),
+        "gw_lanczos_resume": (I, [P, P, P, P, I, I, P, P, P, P, I, I]),
         "gw_epsinv_elements": (I, [P, P, P, I, I, P, I]),
         "gw_epsinv_elements_noalloc": (I, [P, P, I, P, P]),
         "gw_block_lanczos": (I, [P, P, I, I, P, P, P, P, I, I]),
@@ -226,6 +228,19 @@ def gw_lanczos(ctx, start, k, omega, alpha, beta, basis=None, prec=GW_FP64, blk=
     pb, _ = _ptr(beta)
     pq, _ = _ptr(basis)
     _check(ctx, load().gw_lanczos(ctx, ps, int(blk), int(k), om.ctypes.data, pa, pb, pq, int(prec), d))
+    return alpha, beta, basis
+
+
+def gw_lanczos_resume(ctx, basis_in, alpha_in, beta_in, k0, k, omega, alpha, beta, basis=None, prec=GW_FP64):
+    om = _omega_buf([omega])
+    pqi, d = _ptr(basis_in)
+    pai, _ = _ptr(alpha_in)
+    pbi, _ = _ptr(beta_in)
+    pa, _ = _ptr(alpha)
+    pb, _ = _ptr(beta)
+    pq, _ = _ptr(basis)
+    _check(ctx, load().gw_lanczos_resume(ctx, pqi, pai, pbi, int(k0), int(k), om.ctypes.data, pa, pb, pq,
+                                         int(prec), d))
     return alpha, beta, basis
 
 
@@ -529,6 +544,45 @@ class Cell:
         Q = np.empty((k, self.ng)) if basis else None
         gw_lanczos(self.ctx, start, k, omega, a, b, Q, prec)
         return a, b[:k - 1], Q
+
+    def lanczos_resume(self, Q, alpha, beta, k, omega=0.0, prec=GW_FP64):
+        """Continue a recursion from a saved state: Q rows q_1 .. q_{k0+1},
+        alpha[:k0], beta[:k0] (k0 = len(Q) - 1); returns alpha [k], beta [k-1]
+        and the basis [k][N^3] of the k-step recursion."""
+        Q = np.ascontiguousarray(np.asarray(Q, np.float64))
+        k0 = Q.shape[0] - 1
+        ai = np.ascontiguousarray(np.asarray(alpha, np.float64)[:k0])
+        bi = np.ascontiguousarray(np.asarray(beta, np.float64)[:k0])
+        if ai.size != k0 or bi.size != k0:
+            raise ValueError("a saved state with k0 + 1 vectors needs k0 alpha and k0 beta values")
+        a = np.empty(k)
+        b = np.empty(max(k - 1, 1))
+        Qo = np.empty((k, self.ng))
+        gw_lanczos_resume(self.ctx, Q, ai, bi, k0, k, omega, a, b, Qo, prec)
+        return a, b[:k - 1], Qo
+
+    def lanczos_checkpointed(self, start, k, path, every, omega=0.0, prec=GW_FP64):
+        """k Lanczos steps in segments of ``every`` steps, the state written to
+        ``path`` (checkpoint.save_lanczos) after each segment; returns alpha,
+        beta, basis as ``lanczos``."""
+        from .checkpoint import save_lanczos
+        k1 = min(max(int(every), 2), k)
+        a, b, Q = self.lanczos(start, k1, omega, prec, basis=True)
+        save_lanczos(path, Q, a, b, omega)
+        while k1 < k:
+            k2 = min(k1 + every, k)
+            a, b, Q = self.lanczos_resume(Q, a[:k1 - 1], b[:k1 - 1], k2, omega, prec)
+            save_lanczos(path, Q, a, b, omega)
+            k1 = k2
+        return a, b, Q
+
+    def lanczos_from_checkpoint(self, path, k, prec=GW_FP64):
+        """Continue to k steps from a checkpoint file (checked: checksum in
+        load_lanczos, then the state itself in gw_lanczos_resume)."""
+        from .checkpoint import load_lanczos
+        Q, a, b, omega = load_lanczos(path)
+        k1 = Q.shape[0]
+        return self.lanczos_resume(Q, a[:k1 - 1], b[:k1 - 1], k, omega, prec)
 
     def block_lanczos(self, start, k, omega=0.0, prec=GW_FP64, basis=False):
         start = np.ascontiguousarray(np.atleast_2d(np.asarray(start, np.float64)))

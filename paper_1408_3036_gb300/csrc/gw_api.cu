@@ -71,7 +71,7 @@ struct gw_ctx {
   std::string err;
   // optional per-kernel-class timing with CUDA events on the work stream
   unsigned prof_mask = 0;
-  unsigned long long* ptask = nullptr;   // device [24] task timing of the persistent CG (PC_TASKS)
+  unsigned long long* ptask = nullptr;   // device [36] task timing of the persistent CG (PC_TASKS)
   cudaEvent_t tune_ev[2] = {nullptr, nullptr};   // autotuner timing events
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<int, int>>> ev_used;   // (class, (start, end))
@@ -478,7 +478,7 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
     cudaGetLastError();
     ctx->pcg_cluster = 0;
     // the grid-wide task-queue kernel: real-in-real-space columns in packed pairs
-    const PcgSizes z = pcg_sizes(nproj(ctx), npw, ncol, sym ? 2 : 1, ctx->geo.nplanes, ctx->N3,
+    const PcgSizes z = pcg_sizes(nproj(ctx), npw, ncol, sym ? 2 : 1, ctx->geo.nplanes, ctx->N,
                                  (int)sizeof(cpx<T>));
     cpx<T>*r, *p, *sv, *Y, *grid;
     unsigned char* rec;
@@ -493,12 +493,14 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
     TRY(getbuf(ctx, "pcg_apart", z.apart, &apart));
     TRY(getbuf(ctx, "pcg_cst", z.cst, &cst));
     TRY(getbuf(ctx, "pcg_ctl", z.ctl, &ctl));
+    T* cin;
+    TRY(getbuf(ctx, "pcg_cin" + t, (size_t)4 * ncol, &cin));
     CK(cudaMemsetAsync(ctl, 0, z.ctl * sizeof(unsigned), ctx->st));
     unsigned long long* ptask = nullptr;
     if (ctx->prof_mask & (1u << PC_TASKS)) {
       if (!ctx->ptask) {
-        TRY(getbuf(ctx, "pcg_ptask", 24, &ctx->ptask));
-        CK(cudaMemsetAsync(ctx->ptask, 0, 24 * sizeof(unsigned long long), ctx->st));
+        TRY(getbuf(ctx, "pcg_ptask", 36, &ctx->ptask));
+        CK(cudaMemsetAsync(ctx->ptask, 0, 36 * sizeof(unsigned long long), ctx->st));
       }
       ptask = ctx->ptask;
     }
@@ -515,7 +517,7 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
     if (timing) CK(cudaEventRecord(ctx->tune_ev[0], ctx->st));
     le = launch_cg_persistent<T>(ctx->st, ctx->geo, ctx->plan, prec_of<T>(ctx), nproj(ctx), npw, ncol, z,
                                  ctx->maxplane, b64, outer_active, E, rr_abs, tk, tol * tol, ctx->max_iter, x, r, p,
-                                 sv, Y, grid, rec, apart, cst, ctl, iters, flags, rr_out, &used, ctx->cta_div,
+                                 sv, Y, grid, rec, apart, cst, ctl, cin, iters, flags, rr_out, &used, ctx->cta_div,
                                  ctx->wait_limit, ptask, tpb);
     if (timing && le == cudaSuccess) CK(cudaEventRecord(ctx->tune_ev[1], ctx->st));
     ctx->pcg_tpb = tpb;
@@ -1368,8 +1370,10 @@ gw_status need_occ(gw_ctx* ctx) {
 // the Hermitian inner product.  *done (optional) receives the steps completed
 // (fewer than K at an invariant subspace, where GW_E_BREAKDOWN is returned).
 template <typename T>
+// k0 > 0: resume at step k0 from rows 0..k0 of Q and alpha[0..k0), beta[0..k0)
+// (x0 unused).
 gw_status lanczos_core(gw_ctx* ctx, const double* x0, int K, const std::vector<double2>& omega, double* alpha,
-                       double* beta, double* Q, int width = 1, int* done = nullptr) {
+                       double* beta, double* Q, int width = 1, int* done = nullptr, int k0 = 0) {
   const int N3 = width * ctx->N3;
   const double wgt = ctx->vol / ctx->N3;
   if (done) *done = 0;
@@ -1378,9 +1382,11 @@ gw_status lanczos_core(gw_ctx* ctx, const double* x0, int K, const std::vector<d
   TRY(getbuf(ctx, "lz_h", K + 1, &h));
   TRY(getbuf(ctx, "lz_nrm", 1, &nrm));
   TRY(ensure_work(ctx, (size_t)width * (K + 1)));   // partial sums of the stacked length
-  launch_dot(ctx->st, N3, x0, x0, wgt, 1, ctx->work, nrm);
-  launch_lz_axpy(ctx->st, N3, 2, nrm, const_cast<double*>(x0), nullptr, Q);
-  for (int k = 0; k < K; ++k) {
+  if (k0 == 0) {
+    launch_dot(ctx->st, N3, x0, x0, wgt, 1, ctx->work, nrm);
+    launch_lz_axpy(ctx->st, N3, 2, nrm, const_cast<double*>(x0), nullptr, Q);
+  }
+  for (int k = k0; k < K; ++k) {
     double* qk = Q + (size_t)k * N3;
     TRY(eps_core<T>(ctx, qk, false, width, omega, w, false));
     if (done) *done = k + 1;
@@ -1792,6 +1798,17 @@ gw_status build_geometry(gw_ctx* ctx) {
   TRY(upload(ctx, "geo_allp", allp, &g.all_planes));
   TRY(upload(ctx, "geo_pmask", pmask, &g.plane_mask));
   TRY(upload(ctx, "geo_plane_sph", plane_sph, &g.plane_sph));
+  {
+    // the plane holding -G of each plane's entries (i0 -> -i0 mod N)
+    std::vector<int> mirror(planes.size(), -1);
+    for (size_t pi = 0; pi < planes.size(); ++pi)
+      for (size_t q = 0; q < planes.size(); ++q)
+        if (planes[q] == (N - planes[pi]) % N) mirror[pi] = (int)q;
+    for (size_t pi = 0; pi < planes.size(); ++pi)
+      if (mirror[pi] < 0 || plane_sph[mirror[pi] + 1] - plane_sph[mirror[pi]] != plane_sph[pi + 1] - plane_sph[pi])
+        return fail(ctx, GW_E_ARG, "sphere planes not symmetric");
+    TRY(upload(ctx, "geo_plane_mirror", mirror, &g.plane_mirror));
+  }
   ctx->maxplane = 0;
   for (size_t q = 0; q + 1 < plane_sph.size(); ++q) ctx->maxplane = std::max(ctx->maxplane, plane_sph[q + 1] - plane_sph[q]);
   TRY(upload(ctx, "geo_plane_pen", plane_pen, &g.plane_pen));
@@ -2682,6 +2699,80 @@ gw_status gw_lanczos(gw_ctx* ctx, const double* start, int blk, int k, const dou
   return finish(ctx, s);
 }
 
+gw_status gw_lanczos_resume(gw_ctx* ctx, const double* basis_in, const double* alpha_in, const double* beta_in,
+                            int k0, int k, const double* omega, double* alpha, double* beta, double* basis,
+                            gw_prec prec, int dev) {
+  TRY(begin(ctx));
+  TRY(need_occ(ctx));
+  if (!basis_in || !omega || !alpha || !beta || k0 < 1 || k <= k0) return fail(ctx, GW_E_ARG, "bad arguments");
+  std::vector<double2> om;
+  TRY(check_omega(ctx, omega, 1, &om));
+  if (om[0].y != 0.0)
+    return fail(ctx, GW_E_UNSUPPORTED, "gw_lanczos_resume is the real-frequency recursion");
+  for (int i = 0; i < 6; ++i) ctx->stats[i] = 0;
+  ctx->pcg_iters = 0;
+  const size_t fb = (size_t)ctx->N3 * sizeof(double);
+  // the saved coefficients: finite, beta > 0
+  std::vector<double> ha(k0), hbv(k0);
+  if (dev) {
+    CK(cudaMemcpyAsync(ha.data(), alpha_in, k0 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(hbv.data(), beta_in, k0 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    TRY(sync(ctx, "resume"));
+  } else {
+    std::memcpy(ha.data(), alpha_in, k0 * sizeof(double));
+    std::memcpy(hbv.data(), beta_in, k0 * sizeof(double));
+  }
+  for (int i = 0; i < k0; ++i)
+    if (!std::isfinite(ha[i]) || !std::isfinite(hbv[i]) || !(hbv[i] > 0.0))
+      return fail(ctx, GW_E_ARG, "Lanczos state rejected: non-finite or non-positive coefficient");
+  double *a, *b, *Q;
+  TRY(getbuf(ctx, "lz_alpha", k, &a));
+  TRY(getbuf(ctx, "lz_beta", std::max(k - 1, 1), &b));
+  if (dev && basis && basis != basis_in) Q = basis;
+  else TRY(getbuf(ctx, "lz_Q", (size_t)k * ctx->N3, &Q));
+  CK(cudaMemcpyAsync(Q, basis_in, (size_t)(k0 + 1) * fb, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     ctx->st));
+  CK(cudaMemcpyAsync(a, ha.data(), k0 * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(b, hbv.data(), k0 * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  // the saved vectors: orthonormal in <.|.> to 1e-8 (a damaged state fails here)
+  {
+    const double wgt = ctx->vol / ctx->N3;
+    double* h;
+    TRY(getbuf(ctx, "lz_h", k + 1, &h));
+    TRY(ensure_work(ctx, (size_t)k + 1));
+    std::vector<double> hh(k0 + 1);
+    double worst = 0.0;
+    for (int j = 0; j <= k0; ++j) {
+      launch_gemv_t(ctx->st, Q, ctx->N3, ctx->N3, Q + (size_t)j * ctx->N3, wgt, k0 + 1, ctx->work, h);
+      CK(cudaMemcpyAsync(hh.data(), h, (k0 + 1) * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+      TRY(sync(ctx, "resume check"));
+      for (int i = 0; i <= k0; ++i) {
+        const double d = std::fabs(hh[i] - (i == j ? 1.0 : 0.0));
+        worst = std::isfinite(d) ? std::max(worst, d) : 1e300;
+      }
+    }
+    if (!(worst <= 1e-8)) {
+      char m[128];
+      std::snprintf(m, sizeof(m), "Lanczos state rejected: vectors not orthonormal (max |Q^T Q - I| = %.3g)", worst);
+      return fail(ctx, GW_E_ARG, m);
+    }
+  }
+  gw_status s = (prec == GW_FP64) ? lanczos_core<double>(ctx, nullptr, k, om, a, b, Q, 1, nullptr, k0)
+                                  : lanczos_core<float>(ctx, nullptr, k, om, a, b, Q, 1, nullptr, k0);
+  if (s != GW_OK && s != GW_E_BREAKDOWN) return s;
+  if (dev) {
+    CK(cudaMemcpyAsync(alpha, a, k * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(beta, b, (k - 1) * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+    if (basis && basis != Q) CK(cudaMemcpyAsync(basis, Q, (size_t)k * fb, cudaMemcpyDeviceToDevice, ctx->st));
+  } else {
+    CK(cudaMemcpyAsync(alpha, a, k * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(beta, b, (k - 1) * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    if (basis) CK(cudaMemcpyAsync(basis, Q, (size_t)k * fb, cudaMemcpyDeviceToHost, ctx->st));
+  }
+  if (ctx->stats[0] > 0) ctx->stats[2] /= ctx->stats[0];
+  return finish(ctx, s);
+}
+
 gw_status gw_block_lanczos(gw_ctx* ctx, const double* start, int blk, int k, const double* omega, double* A,
                            double* B, double* basis, gw_prec prec, int dev) {
   TRY(begin(ctx));
@@ -3156,16 +3247,16 @@ gw_status gw_profile_read(gw_ctx* ctx, double* ms, long long* count, int n) {
   ctx->ev_used.clear();
   ctx->ev_next = 0;
   if (ctx->ptask && n > PC_TASKS + 6) {
-    unsigned long long h[24];
+    unsigned long long h[36];
     CK(cudaMemcpy(h, ctx->ptask, sizeof(h), cudaMemcpyDeviceToHost));
     CK(cudaMemset(ctx->ptask, 0, sizeof(h)));
     for (int k = 0; k < 3; ++k) {
-      ms[PC_TASKS + 1 + 2 * k] = 1e-6 * (double)h[8 * k + 1];       // busy
-      count[PC_TASKS + 1 + 2 * k] = (long long)h[8 * k + 0];
-      ms[PC_TASKS + 2 + 2 * k] = 1e-6 * (double)h[8 * k + 2];       // waiting
-      count[PC_TASKS + 2 + 2 * k] = (long long)h[8 * k + 3];
-      for (int j = 0; j < 3; ++j)                                      // sub-phases
-        if (n > PC_TASKS + 7 + 3 * k + j) ms[PC_TASKS + 7 + 3 * k + j] = 1e-6 * (double)h[8 * k + 4 + j];
+      ms[PC_TASKS + 1 + 2 * k] = 1e-6 * (double)h[12 * k + 1];      // busy
+      count[PC_TASKS + 1 + 2 * k] = (long long)h[12 * k + 0];
+      ms[PC_TASKS + 2 + 2 * k] = 1e-6 * (double)h[12 * k + 2];      // waiting
+      count[PC_TASKS + 2 + 2 * k] = (long long)h[12 * k + 3];
+      for (int j = 0; j < 4; ++j)                                      // sub-phases
+        if (n > PC_TASKS + 7 + 4 * k + j) ms[PC_TASKS + 7 + 4 * k + j] = 1e-6 * (double)h[12 * k + 4 + j];
     }
   }
   return GW_OK;

@@ -95,6 +95,7 @@ struct Geometry {
   uint8_t* ones = nullptr; // [N2] all ones
   int* planes = nullptr;   // [nplanes] i0 values
   int* plane_sph = nullptr;  // [nplanes + 1] first sphere entry of each plane (entries are i0-major)
+  int* plane_mirror = nullptr;  // [nplanes] the plane holding -G of a plane's entries
   int* plane_pen = nullptr;  // [nplanes + 1] first disc pencil of each plane
   int* sph_i1 = nullptr;     // [npw] y index of each sphere point
   int* sph_neg = nullptr;    // [npw] sphere index of -G (bilinear form sum_G x(-G) y(G))

@@ -6,10 +6,13 @@
 // state x field) with per-column convergence masks.  The work of an iteration
 // is cut into tasks that the CTAs draw, in one fixed global order, from an
 // atomic ticket counter; a task waits only for the tasks of its own group that
-// it depends on (per-group completion counters; every wait is bounded and, when
-// the bound runs out, sets an error flag on which every CTA returns).  No
-// grid-wide barrier: a group whose columns converge early stops holding the
-// others, and the tasks of different groups overlap.
+// it depends on (per-group completion counters), and loads what it can while
+// it waits.  Every wait is bounded and, when the bound runs out, sets an error
+// flag on which every CTA returns.  No grid-wide barrier: a group whose
+// columns converge early stops holding the others, and the tasks of different
+// groups overlap.  (A dataflow variant -- tasks queued by the last task of the
+// phase they depend on -- measured slower: the solve is bound by each group's
+// chain of dependent tasks, and the queue adds a hop to every link of it.)
 //
 // Groups: two columns whose right-hand sides are real in real space
 // (b(-G) = conj b(G), true for real fields at omega = 0) share one complex
@@ -38,8 +41,8 @@
 //      x, r, p, s on the plane's sphere entries, u = K r, the plane's partial
 //      gamma and |r|^2; scatter the packed u, z-IFFT of the disc rows and
 //      y-IFFT of the plane in shared memory, store the plane.
-//      Depends on every C task of the group at it - 1 (none at it = 0, which
-//      sets r = b, x = p = s = 0).
+//      Depends on every C task of the group at it - 1 (none at it = 0: the
+//      launch before sets r = b, x = p = s = 0).
 //   B (g, i1)  x-IFFT, * V(r)/N_g, x-FFT on the (i0, i2) slab.  Depends on the
 //      group's A tasks of it.
 //   C (g, plane)  y-FFT, z-FFT of the disc rows, gather Y = F(V z) on the
@@ -59,7 +62,10 @@
 
 namespace gw {
 
-constexpr int kCtlHead = 4;     // control words: ticket, groups done, error flag, unused
+// Control words: [0] ticket, [1] groups done, [2] error flag, [3] unused;
+// then per group the completed A, B and C tasks and done + 1 (the iteration
+// + 1 at which the group finished).
+constexpr int kCtlHead = 4;
 
 template <typename T>
 struct PcgArgs {
@@ -70,13 +76,11 @@ struct PcgArgs {
   const T* vloc_s;
   const cpx<T>* C;
   int nocc, npw, ncol, ngrp, W, maxplane;
-  const double2* b64;
-  const int* outer_active;
-  const double2* E;           // per-column shift (real)
-  const double* rr_abs;
-  const double* tk;           // per-column T_ref of the kinetic preconditioner, or null (none)
-  double tol_in2;
+  const T* cin;               // [ncol][4] per column, in T: E, 1 / T_ref (0: no preconditioner), |r|^2 floor,
+                              // 1 when the column is solved (written by k_pcg_prep)
+  T tol2;
   int maxit;
+  int pf;                     // 1: the A tasks prefetch r, p, s, x into shared memory
   cpx<T>* x;
   cpx<T>* r;
   cpx<T>* p;
@@ -85,24 +89,69 @@ struct PcgArgs {
   cpx<T>* grid;               // [ngrp][N3]
   unsigned char* rec;         // [ngrp][nplanes] records of the C tasks
   size_t rec_bytes;
-  double* apart;              // [2][ngrp][nplanes][W][2] partial gamma, |r|^2 of the A tasks
-  PcgCol* cst;                // [2][ncol] column state, by iteration parity
-  unsigned* ctl;              // kCtlHead words, then per group: count A, count B, count C, done + 1
+  unsigned char* apart;       // [2][ngrp][nplanes][W][2] Acc<T>: partial gamma, |r|^2 of the A tasks
+  unsigned char* cst;         // [2][ncol] PcgColT<T> column state, by iteration parity
+  unsigned* ctl;              // control words (above)
   int* iters_out;
   int* flag_out;
   double* rr_out;
   unsigned long long spin_limit;
-  unsigned long long* ptask;  // optional [3][8]: per task kind A, B, C: tasks run, busy ns, wait ns, skipped,
-                              // then the busy time of up to three sub-phases (ns)
+  unsigned long long* ptask;  // optional [3][12]: per task kind A, B, C: tasks run, busy ns, wait ns, skipped,
+                              // then the busy time of up to eight sub-phases (ns)
 };
 
 template <typename V> __device__ __forceinline__ V ldcg(const V* p);
 template <> __device__ __forceinline__ float2 ldcg<float2>(const float2* p) { return __ldcg(p); }
 template <> __device__ __forceinline__ double2 ldcg<double2>(const double2* p) { return __ldcg(p); }
 
+// Scalar sums of the CG (inner products, |r|^2, the plane records): FP64 in
+// the FP64 kernel; in the FP32 kernel a pair of floats hi + lo whose
+// additions are error-free transformations (Knuth's TwoSum, then a
+// renormalising FastTwoSum; products by Dekker's splitting through an FMA),
+// which keeps the sums close to FP64 accuracy with FP32 instructions only --
+// this GPU runs FP64 at a small fraction of its FP32 rate.
+template <typename T> struct AccOf { using type = double; };
+template <> struct AccOf<float> { using type = float2; };
+template <typename T> using Acc = typename AccOf<T>::type;
+
+__device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
+__device__ __forceinline__ float2 acc_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  const float t = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  const float h = __fadd_rn(s, t);
+  return make_float2(h, __fsub_rn(t, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ double acc_scale(double a, double c) { return a * c; }
+__device__ __forceinline__ float2 acc_scale(float2 a, float c) {
+  const float p = __fmul_rn(a.x, c);
+  const float e = fmaf(a.y, c, fmaf(a.x, c, -p));
+  const float h = __fadd_rn(p, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, p)));
+}
+__device__ __forceinline__ double acc_of(double x) { return x; }
+__device__ __forceinline__ float2 acc_of(float x) { return make_float2(x, 0.f); }
+__device__ __forceinline__ double acc_val(double a) { return a; }
+__device__ __forceinline__ float acc_val(float2 a) { return __fadd_rn(a.x, a.y); }
+__device__ __forceinline__ double acc_shfl(double a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+__device__ __forceinline__ float2 acc_shfl(float2 a, int o) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o));
+}
+__device__ __forceinline__ double acc_ldcg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float2 acc_ldcg(const float2* p) { return __ldcg(p); }
+
+// Per-column CG state, in the precision of the vectors.
+template <typename T>
+struct PcgColT {
+  T gam, alpha, stop, rmin, rbest;
+  int it, itb, active, flag;
+};
+
 // Column state written by another CTA: read through L2.
-__device__ __forceinline__ PcgCol ld_col(const PcgCol* p) {
-  PcgCol c;
+template <typename T>
+__device__ __forceinline__ PcgColT<T> ld_col(const PcgColT<T>* p) {
+  PcgColT<T> c;
   c.gam = __ldcg(&p->gam);
   c.alpha = __ldcg(&p->alpha);
   c.stop = __ldcg(&p->stop);
@@ -115,13 +164,14 @@ __device__ __forceinline__ PcgCol ld_col(const PcgCol* p) {
   return c;
 }
 
-// Sums over the block of NV values per thread, in FP64 (the NV sums land in
+// Sums over the block of NV values per thread, in Acc (the NV sums land in
 // out[0 .. NV), visible to every thread after the call); up to 16 warps.
-template <int NV>
-__device__ __forceinline__ void block_sum_n(double (&v)[NV], double* sh, double* out) {
+template <int NV, typename A>
+__device__ __forceinline__ void block_sum_n(A (&v)[NV], A* sh, A* out) {
 #pragma unroll
   for (int k = 0; k < NV; ++k)
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] = acc_add(v[k], acc_shfl(v[k], o));
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
   __syncthreads();
   if (l == 0)
@@ -129,25 +179,27 @@ __device__ __forceinline__ void block_sum_n(double (&v)[NV], double* sh, double*
     for (int k = 0; k < NV; ++k) sh[k * 16 + w] = v[k];
   __syncthreads();
   if (threadIdx.x < NV) {
-    double t = 0.0;
-    for (int q = 0; q < nw; ++q) t += sh[threadIdx.x * 16 + q];
+    A t = sh[threadIdx.x * 16];
+    for (int q = 1; q < nw; ++q) t = acc_add(t, sh[threadIdx.x * 16 + q]);
     out[threadIdx.x] = t;
   }
   __syncthreads();
 }
 
 struct PcgLayout {
-  size_t A, B, U, K, tw, rowmap, red, S, coef, dsum, ap, col, pre, total;
+  size_t A, B, U, K, tw, rowmap, red, S, coef, dsum, ap, col, pre, IX, X, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Shared memory of one CTA: two FFT tiles N x (N+1), the plane's u_c and
-// |G|^2/2 (C tasks), twiddles, the row map of a plane's disc pencils,
-// reduction scratch, the summed records, the group's projector coefficients
-// and <C_v|u_c> (A tasks), FP64 sums, the staged per-plane partials of the A
-// tasks, and per-column scalars.
-__host__ __device__ inline PcgLayout pcg_layout(int N, int nocc, int W, int maxplane, int vsize) {
+// Shared memory of one CTA: two FFT tiles N x (N+1), the plane's u_c (C
+// tasks) or Y(G), conj Y(-G) (A tasks), |G|^2/2 on the plane's entries,
+// twiddles, the row map of a plane's disc pencils, reduction scratch, the
+// summed records, the group's projector coefficients and <C_v|u_c> (A tasks),
+// scalar sums, the staged per-plane partials of the A tasks, per-column
+// scalars, the plane's -G indices and scatter positions (A tasks), and with
+// pf the plane's r, p, s, x prefetched by the A tasks.
+__host__ __device__ inline PcgLayout pcg_layout(int N, int nocc, int W, int maxplane, int vsize, bool pf) {
   PcgLayout L;
   L.A = 0;
   L.B = align16(L.A + (size_t)N * (N + 1) * vsize);
@@ -162,7 +214,9 @@ __host__ __device__ inline PcgLayout pcg_layout(int N, int nocc, int W, int maxp
   L.ap = align16(L.dsum + 24 * sizeof(double));
   L.col = align16(L.ap + (size_t)N * 2 * W * sizeof(double));
   L.pre = align16(L.col + 2 * 8 * sizeof(double));
-  L.total = align16(L.pre + 2 * (4 * sizeof(double) + sizeof(PcgCol)));
+  L.IX = align16(L.pre + 2 * (4 * sizeof(double) + sizeof(PcgCol)));
+  L.X = align16(L.IX + (size_t)2 * maxplane * sizeof(int));
+  L.total = align16(L.X + (pf ? (size_t)W * 4 * maxplane * vsize : 0));
   return L;
 }
 
@@ -170,7 +224,7 @@ __host__ __device__ inline PcgLayout pcg_layout(int N, int nocc, int W, int maxp
 //   V [nocc]        D_v   = sum conj(C_v) Y
 //   V [W][nocc]     K_c,v = sum conj(C_v) kin u_c
 //   V [W][nocc]     U_c,v = sum conj(C_v) u_c
-//   double [W][4]   Re, Im of u_c^H Y, sum kin |u_c|^2, sum |u_c|^2
+//   Acc<T> [W][4]   Re, Im of u_c^H Y, sum kin |u_c|^2, sum |u_c|^2 (8 bytes each)
 __host__ __device__ inline size_t pcg_rec_bytes(int nocc, int W, int vsize) {
   return align16((size_t)(1 + 2 * W) * nocc * vsize) + (size_t)32 * W;
 }
@@ -194,6 +248,13 @@ __device__ __forceinline__ int wait_dep(const unsigned* cnt, unsigned target, co
   return (d != 0u && d <= skip_le) ? 1 : 0;
 }
 
+// Completion of a task: every thread's writes fenced, then one count.
+__device__ __forceinline__ void signal_done(unsigned* cnt) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(cnt, 1u);
+}
+
 __device__ __forceinline__ unsigned long long gtime() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -204,7 +265,7 @@ __device__ __forceinline__ unsigned long long gtime() {
 __device__ __forceinline__ void task_time(unsigned long long* pt, int kind, unsigned long long t0,
                                           unsigned long long t1, bool ran) {
   if (!pt || threadIdx.x != 0) return;
-  unsigned long long* q = pt + 8 * kind;
+  unsigned long long* q = pt + 12 * kind;
   if (ran) {
     atomicAdd(q + 0, 1ull);
     atomicAdd(q + 1, gtime() - t1);
@@ -219,15 +280,59 @@ __device__ __forceinline__ void task_time(unsigned long long* pt, int kind, unsi
 __device__ __forceinline__ void task_mark(unsigned long long* pt, int kind, int k, unsigned long long* t) {
   if (!pt || threadIdx.x != 0) return;
   const unsigned long long now = gtime();
-  atomicAdd(pt + 8 * kind + 4 + k, now - *t);
+  atomicAdd(pt + 12 * kind + 4 + k, now - *t);
   *t = now;
 }
 
-// Completion of a task: every thread's writes fenced, then one count.
-__device__ __forceinline__ void signal_done(unsigned* cnt) {
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) atomicAdd(cnt, 1u);
+
+// Rows of n contiguous complex values between device memory (row k at
+// g + k * stride) and a shared tile (row k at t + k * LDp), for k < nrow;
+// rows whose mask entry is 0 are zero in the tile and left alone in memory.
+// FP32 values move in pairs (16-byte accesses) when every row start is even.
+template <typename T>
+__device__ __forceinline__ void load_rows(cpx<T>* t, int LDp, const cpx<T>* g, size_t stride, int nrow, int n,
+                                          const unsigned char* mask) {
+  using V = cpx<T>;
+  if (sizeof(T) == 4 && (n & 1) == 0 && (stride & 1) == 0 && ((reinterpret_cast<size_t>(g) & 15) == 0)) {
+    const int h = n >> 1, tot = nrow * h;
+#pragma unroll 4
+    for (int f = threadIdx.x; f < tot; f += blockDim.x) {
+      const int k = f / h, j = 2 * (f - k * h);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (!mask || mask[k]) v = __ldcg(reinterpret_cast<const float4*>(g + (size_t)k * stride + j));
+      t[k * LDp + j] = mk<T>((T)v.x, (T)v.y);
+      t[k * LDp + j + 1] = mk<T>((T)v.z, (T)v.w);
+    }
+  } else {
+    const int tot = nrow * n;
+#pragma unroll 8
+    for (int f = threadIdx.x; f < tot; f += blockDim.x) {
+      const int k = f / n, j = f - k * n;
+      t[k * LDp + j] = (!mask || mask[k]) ? ldcg(g + (size_t)k * stride + j) : mk<T>(0, 0);
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_rows(cpx<T>* g, size_t stride, const cpx<T>* t, int LDp, int nrow, int n,
+                                           const unsigned char* mask) {
+  if (sizeof(T) == 4 && (n & 1) == 0 && (stride & 1) == 0 && ((reinterpret_cast<size_t>(g) & 15) == 0)) {
+    const int h = n >> 1, tot = nrow * h;
+#pragma unroll 4
+    for (int f = threadIdx.x; f < tot; f += blockDim.x) {
+      const int k = f / h, j = 2 * (f - k * h);
+      if (mask && !mask[k]) continue;
+      const cpx<T> u = t[k * LDp + j], v = t[k * LDp + j + 1];
+      *reinterpret_cast<float4*>(g + (size_t)k * stride + j) = make_float4((float)u.x, (float)u.y, (float)v.x,
+                                                                           (float)v.y);
+    }
+  } else {
+    const int tot = nrow * n;
+    for (int f = threadIdx.x; f < tot; f += blockDim.x) {
+      const int k = f / n, j = f - k * n;
+      if (!mask || mask[k]) g[(size_t)k * stride + j] = t[k * LDp + j];
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -237,6 +342,7 @@ template <typename T>
 __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned char* sm, const PcgLayout& L,
                        int* s_ctl) {
   using V = cpx<T>;
+  using SA = Acc<T>;
   const Geometry& g = a.g;
   const int N = g.N, LDp = N + 1, P = g.nplanes, W = a.W, nocc = a.nocc;
   const int c0 = gi * W, nc = min(W, a.ncol - c0);
@@ -245,16 +351,33 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
   V* Bb = reinterpret_cast<V*>(sm + L.B);
   const V* stw = reinterpret_cast<const V*>(sm + L.tw);
   int* rowmap = reinterpret_cast<int*>(sm + L.rowmap);
-  double* red = reinterpret_cast<double*>(sm + L.red);
+  SA* red = reinterpret_cast<SA*>(sm + L.red);
   V* Ssum = reinterpret_cast<V*>(sm + L.S);            // the records' projector sums over planes
   V* coefT = reinterpret_cast<V*>(sm + L.coef);        // [W][nocc] coefficients, then [W][nocc] <C_v|u_c>
-  double* dsum = reinterpret_cast<double*>(sm + L.dsum);
-  double* colv = reinterpret_cast<double*>(sm + L.col);   // [c * 8 + k]: alpha, beta, active, E, rtk
+  SA* dsum = reinterpret_cast<SA*>(sm + L.dsum);
+  T* colv = reinterpret_cast<T*>(sm + L.col);          // [c * 8 + k]: alpha, beta, active, E, 1 / T_ref
+  const int i0 = g.planes[pi];
+  const int s0 = g.plane_sph[pi], s1 = g.plane_sph[pi + 1];
+  const int q0 = g.plane_pen[pi], npp = g.plane_pen[pi + 1] - q0;
+  const int ns = s1 - s0;
+  const size_t rb = a.rec_bytes;
+  const int nv = (1 + 2 * W) * nocc;
+  const bool pf = a.pf != 0;
+  V* X = reinterpret_cast<V*>(sm + L.X);              // [W][4][maxplane]: r, p, s, x (pf)
+  int* IXn = reinterpret_cast<int*>(sm + L.IX);       // [maxplane]: position of -G in the mirror plane
+  int* IXs = IXn + a.maxplane;                        // [maxplane]: position in tile A
+  T* Ks = reinterpret_cast<T*>(sm + L.K);             // [maxplane]: |G|^2/2
+  V* Ys = reinterpret_cast<V*>(sm + L.U);             // [maxplane]: Y on the plane, then (W = 2) on its mirror
+  const int pm = g.plane_mirror[pi];
+  const int s0m = g.plane_sph[pm];
   unsigned long long t0 = 0, t1 = 0;
+  // First wait (it > 0, pf): the group's A tasks of it - 1 are done, so the
+  // plane's r, p, s, x are final; they and the plane's static per-entry values
+  // are loaded while the C tasks of it - 1 finish (second wait).
   if (threadIdx.x == 0) {
     int w = 0;
     if (a.ptask) t0 = gtime();
-    if (it > 0) w = wait_dep(gc + 2, (unsigned)(it * P), gc + 3, (unsigned)it, a.ctl, a.spin_limit);
+    if (it > 0 && pf) w = wait_dep(gc + 0, (unsigned)(it * P), gc + 3, (unsigned)it, a.ctl, a.spin_limit);
     if (a.ptask) t1 = gtime();
     s_ctl[0] = w;
   }
@@ -264,22 +387,46 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
     task_time(a.ptask, 0, t0, t1, false);
     return;
   }
-  const int i0 = g.planes[pi];
-  const int s0 = g.plane_sph[pi], s1 = g.plane_sph[pi + 1];
-  const int q0 = g.plane_pen[pi], npp = g.plane_pen[pi + 1] - q0;
-  const int ns = s1 - s0;
-  const size_t rb = a.rec_bytes;
-  const int nv = (1 + 2 * W) * nocc;
+  for (int e = threadIdx.x; e < ns; e += blockDim.x) {
+    const int G = s0 + e;
+    Ks[e] = a.kin[G];
+    IXn[e] = g.sph_neg[G] - s0m;
+    IXs[e] = (g.sph_pen[G] - q0) * LDp + g.sph_i2[G];
+  }
+  if (pf) {
+    const int nvec = (it == 0) ? 1 : 4, tot = nc * nvec * ns;
+#pragma unroll 8
+    for (int f = threadIdx.x; f < tot; f += blockDim.x) {
+      const int cv = f / ns, e = f - cv * ns;
+      const int c = cv / nvec, k = cv - c * nvec;
+      const V* src = (k == 0) ? a.r : (k == 1) ? a.p : (k == 2) ? a.s : a.x;
+      X[((size_t)c * 4 + k) * a.maxplane + e] = ldcg(src + (size_t)(c0 + c) * a.npw + s0 + e);
+    }
+  }
+  // Second wait (it > 0): the group's C tasks of it - 1 are done.
+  if (threadIdx.x == 0) {
+    int w = 0;
+    if (it > 0) w = wait_dep(gc + 2, (unsigned)(it * P), gc + 3, (unsigned)it, a.ctl, a.spin_limit);
+    if (a.ptask) t1 = gtime();
+    s_ctl[0] = w;
+  }
+  __syncthreads();
+  if (s_ctl[0] == 2) return;
+  if (s_ctl[0] == 1) {
+    task_time(a.ptask, 0, t0, t1, false);
+    return;
+  }
+  unsigned long long tm = t1;
 
   // ---- column scalars
   if (it == 0) {
     for (int c = threadIdx.x; c < W; c += blockDim.x) {
       const bool present = c < nc;
-      colv[c * 8 + 0] = 0.0;
-      colv[c * 8 + 1] = 0.0;
-      colv[c * 8 + 2] = present ? 1.0 : 0.0;
-      colv[c * 8 + 3] = present ? a.E[c0 + c].x : 0.0;
-      colv[c * 8 + 4] = (present && a.tk) ? 1.0 / a.tk[c0 + c] : 0.0;
+      colv[c * 8 + 0] = (T)0;
+      colv[c * 8 + 1] = (T)0;
+      colv[c * 8 + 2] = present ? (T)1 : (T)0;
+      colv[c * 8 + 3] = present ? a.cin[(c0 + c) * 4 + 0] : (T)0;
+      colv[c * 8 + 4] = present ? a.cin[(c0 + c) * 4 + 1] : (T)0;
     }
   } else {
     // One round of loads: the group's P records (shared-memory tiles A and B,
@@ -292,49 +439,65 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
     if (staged) {
       const float4* s4 = reinterpret_cast<const float4*>(src);
       float4* d4 = reinterpret_cast<float4*>(sm + L.A);
+#pragma unroll 4
       for (size_t e = threadIdx.x; e < nb16; e += blockDim.x) d4[e] = __ldcg(s4 + e);
     }
-    const double* ap = a.apart + ((size_t)((it - 1) & 1) * a.ngrp + gi) * P * W * 2;
-    double* aps = reinterpret_cast<double*>(sm + L.ap);
-    for (int j = threadIdx.x; j < P * W * 2; j += blockDim.x) aps[j] = __ldcg(ap + j);
-    double* pre = reinterpret_cast<double*>(sm + L.pre);                  // [W][4]: E, T_ref, on, |r|^2 target
-    PcgCol* pcs = reinterpret_cast<PcgCol*>(sm + L.pre + 2 * 4 * sizeof(double));
+    {
+      const V* Yg = a.Y + (size_t)gi * a.npw;
+#pragma unroll 4
+      for (int e = threadIdx.x; e < ns; e += blockDim.x) {
+        Ys[e] = ldcg(Yg + s0 + e);
+        if (W == 2) Ys[a.maxplane + e] = ldcg(Yg + s0m + e);     // the mirror plane, in its own order
+      }
+    }
+    const SA* ap = reinterpret_cast<const SA*>(a.apart) + ((size_t)((it - 1) & 1) * a.ngrp + gi) * P * W * 2;
+    SA* aps = reinterpret_cast<SA*>(sm + L.ap);
+    for (int j = threadIdx.x; j < P * W * 2; j += blockDim.x) aps[j] = acc_ldcg(ap + j);
+    T* pre = reinterpret_cast<T*>(sm + L.pre);                            // [W][4]: E, 1/T_ref, floor, on
+    PcgColT<T>* pcs = reinterpret_cast<PcgColT<T>*>(sm + L.pre + 2 * 4 * sizeof(double));
     if (threadIdx.x < nc) {
       const int col = c0 + threadIdx.x;
-      pre[threadIdx.x * 4 + 0] = a.E[col].x;
-      pre[threadIdx.x * 4 + 1] = a.tk ? a.tk[col] : 0.0;
-      pre[threadIdx.x * 4 + 2] = (!a.outer_active || a.outer_active[col]) ? 1.0 : 0.0;
-      pre[threadIdx.x * 4 + 3] = a.rr_abs ? a.rr_abs[col] : 0.0;
-      if (it > 1) pcs[threadIdx.x] = ld_col(a.cst + (size_t)((it - 1) & 1) * a.ncol + col);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) pre[threadIdx.x * 4 + k] = a.cin[col * 4 + k];
+      if (it > 1)
+        pcs[threadIdx.x] = ld_col(reinterpret_cast<const PcgColT<T>*>(a.cst) + (size_t)((it - 1) & 1) * a.ncol + col);
     }
     __syncthreads();
-    // projector sums in T (threads j < nv) and the FP64 sums (the next 6 W
-    // threads: per column Re/Im u^H Y, kin|u|^2, |u|^2 of the records, gamma
-    // and |r|^2 of the A partials), each over the planes in order
+    task_mark(a.ptask, 0, 0, &tm);     // loads
+    // projector sums in T over the planes in order (threads j < nv)
     const size_t dbase = align16((size_t)nv * sizeof(V));
-    for (int j = threadIdx.x; j < nv + 6 * W; j += blockDim.x) {
-      if (j < nv) {
-        T sx = 0, sy = 0;
-        for (int q = 0; q < P; ++q) {
-          const V v = staged ? reinterpret_cast<const V*>(stg + (size_t)q * rb)[j]
-                             : ldcg(reinterpret_cast<const V*>(stg + (size_t)q * rb) + j);
-          sx += v.x;
-          sy += v.y;
-        }
-        Ssum[j] = mk<T>(sx, sy);
-      } else {
-        const int jj = j - nv;
-        double t = 0.0;
-        if (jj < 4 * W) {
-          for (int q = 0; q < P; ++q) {
-            const double* d = reinterpret_cast<const double*>(stg + (size_t)q * rb + dbase);
-            t += staged ? d[jj] : __ldcg(d + jj);
+    for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+      T sx = 0, sy = 0;
+      for (int q = 0; q < P; ++q) {
+        const V v = staged ? reinterpret_cast<const V*>(stg + (size_t)q * rb)[j]
+                           : ldcg(reinterpret_cast<const V*>(stg + (size_t)q * rb) + j);
+        sx += v.x;
+        sy += v.y;
+      }
+      Ssum[j] = mk<T>(sx, sy);
+    }
+    // the 6 W scalar sums in Acc (per column: Re/Im u^H Y, kin |u|^2, |u|^2 of
+    // the records, gamma and |r|^2 of the A partials) by the block's last
+    // warps: eight threads per value, each over every eighth plane, then a
+    // shuffle reduction (a fixed order: the same bits in every A task)
+    {
+      const int nval = 6 * W, R = (8 * nval + 31) & ~31;
+      const int t = (int)threadIdx.x - ((int)blockDim.x - R);
+      if (t >= 0) {
+        const int j = t >> 3, part = t & 7;
+        SA acc = acc_of((T)0);
+        if (j < 4 * W) {
+          for (int q = part; q < P; q += 8) {
+            const SA* d = reinterpret_cast<const SA*>(stg + (size_t)q * rb + dbase);
+            acc = acc_add(acc, staged ? d[j] : acc_ldcg(d + j));
           }
-        } else {
-          const int k = jj - 4 * W;        // c * 2 + (0 gamma, 1 |r|^2)
-          for (int q = 0; q < P; ++q) t += aps[(size_t)q * W * 2 + k];
+        } else if (j < nval) {
+          const int k = j - 4 * W;          // c * 2 + (0 gamma, 1 |r|^2)
+          for (int q = part; q < P; q += 8) acc = acc_add(acc, aps[(size_t)q * W * 2 + k]);
         }
-        dsum[jj] = t;
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) acc = acc_add(acc, acc_shfl(acc, o));
+        if (part == 0 && j < nval) dsum[j] = acc;
       }
     }
     __syncthreads();
@@ -342,7 +505,7 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
     // FV = Re D (c = 0) or Im D (c = 1) for a packed pair (real: taken real), D otherwise
     for (int j = threadIdx.x; j < W * nocc; j += blockDim.x) {
       const int c = j / nocc, v = j - c * nocc;
-      const T Ec = (T)((c < nc) ? pre[c * 4 + 0] : 0.0);
+      const T Ec = (c < nc) ? pre[c * 4 + 0] : (T)0;
       const V D = Ssum[v], K = Ssum[(1 + c) * nocc + v], U = Ssum[(1 + W + c) * nocc + v];
       V cf;
       if (W == 2) {
@@ -359,12 +522,13 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
     {
       const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
       if (warp < W) {
-        double t = 0.0;
+        SA t = acc_of((T)0);
         for (int v = lane; v < nocc; v += 32) {
           const V cf = coefT[warp * nocc + v], U = coefT[W * nocc + warp * nocc + v];
-          t += (double)(U.x * cf.x + U.y * cf.y);
+          t = acc_add(t, acc_of(U.x * cf.x + U.y * cf.y));
         }
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t = acc_add(t, acc_shfl(t, o));
         if (lane == 0) red[warp] = t;
       }
     }
@@ -372,49 +536,51 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
     // decisions (thread c for column c; identical in every A task of the group)
     if (threadIdx.x < W) {
       const int c = threadIdx.x;
-      double* cv = colv + c * 8;
-      cv[2] = 0.0;
+      T* cv = colv + c * 8;
+      cv[2] = (T)0;
       if (c < nc) {
         const int col = c0 + c;
-        const double Ec = pre[c * 4 + 0];
-        const double uY = (W == 2) ? dsum[c * 4 + ((c == 0) ? 0 : 1)] : dsum[c * 4];
-        const double delta = uY + dsum[c * 4 + 2] - Ec * dsum[c * 4 + 3] - red[c];
-        const double gam = dsum[4 * W + c * 2], rr = dsum[4 * W + c * 2 + 1];
-        PcgCol st;
+        const T Ec = pre[c * 4 + 0];
+        const SA uY = (W == 2) ? dsum[c * 4 + ((c == 0) ? 0 : 1)] : dsum[c * 4];
+        const SA dl = acc_add(acc_add(uY, dsum[c * 4 + 2]),
+                             acc_add(acc_scale(dsum[c * 4 + 3], -Ec), acc_scale(red[c], (T)-1)));
+        const T delta = acc_val(dl);
+        const T gam = acc_val(dsum[4 * W + c * 2]), rr = acc_val(dsum[4 * W + c * 2 + 1]);
+        PcgColT<T> st;
         if (it == 1) {
-          const bool on = pre[c * 4 + 2] != 0.0;
-          st.gam = 0.0;
-          st.alpha = 0.0;
-          st.stop = fmax(a.tol_in2 * rr, pre[c * 4 + 3]);
+          const bool on = pre[c * 4 + 3] != (T)0;
+          const T s1v = a.tol2 * rr, s2v = pre[c * 4 + 2];
+          st.gam = (T)0;
+          st.alpha = (T)0;
+          st.stop = s1v > s2v ? s1v : s2v;
           st.rmin = rr;
           st.rbest = rr;
           st.it = 0;
           st.itb = 0;
-          st.active = (on && rr > 0.0) ? 1 : 0;
+          st.active = (on && rr > (T)0) ? 1 : 0;
           st.flag = 0;
-          if (!st.active) st.flag = 0;
         } else {
           st = pcs[c];
         }
         const bool was = st.active != 0;
         if (st.active) {
           const int itc = it - 1;               // updates done so far
-          st.rmin = fmin(st.rmin, rr);
-          if (rr < 0.25 * st.rbest) { st.rbest = rr; st.itb = itc; }
+          st.rmin = rr < st.rmin ? rr : st.rmin;
+          if (rr < (T)0.25 * st.rbest) { st.rbest = rr; st.itb = itc; }
           int stop = 0;
           if (!isfinite(rr)) { st.flag = 2; stop = 1; }
           else if (rr <= st.stop) { st.flag = 0; stop = 1; }
-          else if (rr > 1e4 * st.rmin) { st.flag = 3; stop = 1; }
+          else if (rr > (T)1e4 * st.rmin) { st.flag = 3; stop = 1; }
           else if (itc >= a.maxit) { st.flag = 1; stop = 1; }
           else if (itc - st.itb > max(kCgStagWindow, 2 * st.itb)) { st.flag = 4; stop = 1; }
-          double al = 0.0, bt = 0.0;
+          T al = 0, bt = 0;
           if (!stop) {
-            double den = delta;
+            T den = delta;
             if (it > 1) {
               bt = gam / st.gam;
               den = delta - bt * gam / st.alpha;
             }
-            if (!(den > 0.0) || !isfinite(den) || !(gam > 0.0)) { st.flag = 2; stop = 1; }
+            if (!(den > (T)0) || !isfinite(den) || !(gam > (T)0)) { st.flag = 2; stop = 1; }
             else al = gam / den;
           }
           st.it = itc;
@@ -425,17 +591,17 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
             st.alpha = al;
             cv[0] = al;
             cv[1] = bt;
-            cv[2] = 1.0;
+            cv[2] = (T)1;
           }
         }
         cv[3] = Ec;
-        cv[4] = pre[c * 4 + 1] != 0.0 ? 1.0 / pre[c * 4 + 1] : 0.0;
+        cv[4] = pre[c * 4 + 1];
         if (pi == 0) {
-          a.cst[(size_t)(it & 1) * a.ncol + col] = st;
+          reinterpret_cast<PcgColT<T>*>(a.cst)[(size_t)(it & 1) * a.ncol + col] = st;
           if (!st.active && (was || it == 1)) {
             a.iters_out[col] = st.it;
             a.flag_out[col] = st.flag;
-            a.rr_out[col] = rr;
+            a.rr_out[col] = (double)rr;
           }
         }
       }
@@ -444,7 +610,7 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
     // group finished: mark it (plane-0 task) and stop here
     {
       int any = 0;
-      for (int c = 0; c < W; ++c) any |= (colv[c * 8 + 2] != 0.0);
+      for (int c = 0; c < W; ++c) any |= (colv[c * 8 + 2] != (T)0);
       if (!any) {
         if (pi == 0 && threadIdx.x == 0) {
           __threadfence();
@@ -458,8 +624,7 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
     }
   }
 
-  unsigned long long tm = t1;
-  task_mark(a.ptask, 0, 0, &tm);       // sums and decisions
+  task_mark(a.ptask, 0, 1, &tm);       // sums and decisions
   // ---- update the plane's entries and scatter the packed u = K r
   for (int e = threadIdx.x; e < npp * LDp; e += blockDim.x) Ab[e] = mk<T>(0, 0);
   for (int k = threadIdx.x; k < N; k += blockDim.x) rowmap[k] = -1;
@@ -471,34 +636,22 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
     const int cc = (c < W) ? c : 0;
-    c_al[c] = (T)colv[cc * 8 + 0];
-    c_bt[c] = (T)colv[cc * 8 + 1];
-    c_act[c] = (c < W) && colv[cc * 8 + 2] != 0.0;
-    c_E[c] = (T)colv[cc * 8 + 3];
-    c_rtk[c] = (T)colv[cc * 8 + 4];
+    c_al[c] = colv[cc * 8 + 0];
+    c_bt[c] = colv[cc * 8 + 1];
+    c_act[c] = (c < nc) && colv[cc * 8 + 2] != (T)0;
+    c_E[c] = colv[cc * 8 + 3];
+    c_rtk[c] = colv[cc * 8 + 4];
   }
-  const V* Yg = a.Y + (size_t)gi * a.npw;
   for (int e = threadIdx.x; e < ns; e += blockDim.x) {
     const int G = s0 + e;
-    const T kinG = a.kin[G];
+    const T kinG = Ks[e];
     V z = mk<T>(0, 0);
     if (it == 0) {
+      // r = b (symmetrised), x = p = s = 0: written by k_pcg_prep
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         if (c >= nc) break;
-        const int col = c0 + c;
-        const size_t i = (size_t)col * a.npw + G;
-        const bool on = !a.outer_active || a.outer_active[col];
-        double2 b = on ? a.b64[i] : make_double2(0.0, 0.0);
-        if (W == 2 && on) {
-          const double2 bn = a.b64[(size_t)col * a.npw + g.sph_neg[G]];
-          b = make_double2(0.5 * (b.x + bn.x), 0.5 * (b.y - bn.y));
-        }
-        const V rv = from_d<T>(b);
-        a.r[i] = rv;
-        a.x[i] = mk<T>(0, 0);
-        a.p[i] = mk<T>(0, 0);
-        a.s[i] = mk<T>(0, 0);
+        const V rv = pf ? X[(size_t)c * 4 * a.maxplane + e] : a.r[(size_t)(c0 + c) * a.npw + G];
         const T rtk = c_rtk[c];
         const T K = (rtk != (T)0) ? tpa<T>(kinG * rtk) : (T)1;
         const V u = mk<T>(K * rv.x, K * rv.y);
@@ -509,19 +662,39 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
         else z = mk<T>(z.x + u.x, z.y + u.y);
       }
     } else {
-      const V y1 = ldcg(Yg + G);
-      V y2 = ldcg(Yg + g.sph_neg[G]);
-      y2.y = -y2.y;                                   // conj Y(-G)
+      // every load of the entry (both columns, the rows of C) before any store
+      const V y1 = Ys[e];
+      V y2 = mk<T>(0, 0);
+      if (W == 2) {
+        y2 = Ys[a.maxplane + IXn[e]];
+        y2.y = -y2.y;                                 // conj Y(-G)
+      }
+      V rv[2], pv[2], sv[2], xv[2];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        if (c >= nc || !c_act[c]) continue;
-        const int col = c0 + c;
-        const size_t i = (size_t)col * a.npw + G;
-        const T al = c_al[c], bt = c_bt[c], Ec = c_E[c];
+        if (c_act[c] && pf) {
+          const V* xc = X + (size_t)c * 4 * a.maxplane + e;
+          rv[c] = xc[0];
+          pv[c] = xc[a.maxplane];
+          sv[c] = xc[2 * a.maxplane];
+          xv[c] = xc[3 * a.maxplane];
+        } else if (c_act[c]) {
+          const size_t i = (size_t)(c0 + c) * a.npw + G;
+          rv[c] = ldcg(a.r + i);
+          pv[c] = ldcg(a.p + i);
+          sv[c] = ldcg(a.s + i);
+          xv[c] = ldcg(a.x + i);
+        } else {
+          rv[c] = pv[c] = sv[c] = xv[c] = mk<T>(0, 0);
+        }
+      }
+      V w[2];
+      T Kc[2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
         const T rtk = c_rtk[c];
-        const T K = (rtk != (T)0) ? tpa<T>(kinG * rtk) : (T)1;
-        V rv = ldcg(a.r + i), pv = ldcg(a.p + i), sv = ldcg(a.s + i), xv = ldcg(a.x + i);
-        const V u = mk<T>(K * rv.x, K * rv.y);
+        Kc[c] = (rtk != (T)0) ? tpa<T>(kinG * rtk) : (T)1;
+        const V u = mk<T>(Kc[c] * rv[c].x, Kc[c] * rv[c].y);
         V fv;
         if (W == 2) {
           if (c == 0) fv = mk<T>((T)0.5 * (y1.x + y2.x), (T)0.5 * (y1.y + y2.y));
@@ -529,51 +702,63 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
         } else {
           fv = y1;
         }
-        const T kd = kinG - Ec;
-        V w = mk<T>(fv.x + kd * u.x, fv.y + kd * u.y);
-        const V* cf = coefT + c * nocc;
-        constexpr int RB = (sizeof(T) == 4) ? 16 : 8;   // rows of C in flight
-        for (int v = 0; v < nocc; v += RB) {
-          V cv[RB];
+        const T kd = kinG - c_E[c];
+        w[c] = mk<T>(fv.x + kd * u.x, fv.y + kd * u.y);
+      }
+      // w_c -= sum_v C_v(G) coef_c,v: the rows of C read once for both columns
+      constexpr int RB = (sizeof(T) == 4) ? 16 : 4;   // rows of C in flight
+      for (int v = 0; v < nocc; v += RB) {
+        V cv[RB];
 #pragma unroll
-          for (int q = 0; q < RB; ++q) cv[q] = (v + q < nocc) ? a.C[(size_t)(v + q) * a.npw + G] : mk<T>(0, 0);
+        for (int q = 0; q < RB; ++q) cv[q] = (v + q < nocc) ? a.C[(size_t)(v + q) * a.npw + G] : mk<T>(0, 0);
 #pragma unroll
-          for (int q = 0; q < RB; ++q) {
-            if (v + q < nocc) {
-              const V k = cf[v + q];
-              w.x -= cv[q].x * k.x - cv[q].y * k.y;
-              w.y -= cv[q].x * k.y + cv[q].y * k.x;
+        for (int q = 0; q < RB; ++q) {
+          if (v + q < nocc) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              if (c < W) {
+                const V k = coefT[c * nocc + v + q];
+                w[c].x -= cv[q].x * k.x - cv[q].y * k.y;
+                w[c].y -= cv[q].x * k.y + cv[q].y * k.x;
+              }
             }
           }
         }
-        pv = mk<T>(u.x + bt * pv.x, u.y + bt * pv.y);
-        sv = mk<T>(w.x + bt * sv.x, w.y + bt * sv.y);
-        xv = mk<T>(xv.x + al * pv.x, xv.y + al * pv.y);
-        rv = mk<T>(rv.x - al * sv.x, rv.y - al * sv.y);
-        a.p[i] = pv;
-        a.s[i] = sv;
-        a.x[i] = xv;
-        a.r[i] = rv;
-        const V un = mk<T>(K * rv.x, K * rv.y);
-        const T n2 = rv.x * rv.x + rv.y * rv.y;
+      }
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (!c_act[c]) continue;
+        const size_t i = (size_t)(c0 + c) * a.npw + G;
+        const T al = c_al[c], bt = c_bt[c], K = Kc[c];
+        const V u = mk<T>(K * rv[c].x, K * rv[c].y);
+        const V pn = mk<T>(u.x + bt * pv[c].x, u.y + bt * pv[c].y);
+        const V sn = mk<T>(w[c].x + bt * sv[c].x, w[c].y + bt * sv[c].y);
+        const V xn = mk<T>(xv[c].x + al * pn.x, xv[c].y + al * pn.y);
+        const V rn = mk<T>(rv[c].x - al * sn.x, rv[c].y - al * sn.y);
+        a.p[i] = pn;
+        a.s[i] = sn;
+        a.x[i] = xn;
+        a.r[i] = rn;
+        const V un = mk<T>(K * rn.x, K * rn.y);
+        const T n2 = rn.x * rn.x + rn.y * rn.y;
         racc[c] += n2;
         gacc[c] += K * n2;
         if (W == 2 && c == 1) z = mk<T>(z.x - un.y, z.y + un.x);
         else z = mk<T>(z.x + un.x, z.y + un.y);
       }
     }
-    Ab[(g.sph_pen[G] - q0) * LDp + g.sph_i2[G]] = z;
+    Ab[IXs[e]] = z;
   }
   {
-    double v4[4] = {(double)gacc[0], (double)racc[0], (double)gacc[1], (double)racc[1]};
+    SA v4[4] = {acc_of(gacc[0]), acc_of(racc[0]), acc_of(gacc[1]), acc_of(racc[1])};
     block_sum_n<4>(v4, red, dsum + 16);
     if (threadIdx.x < 2 * W) {
-      double* ap = a.apart + (((size_t)(it & 1) * a.ngrp + gi) * P + pi) * W * 2;
+      SA* ap = reinterpret_cast<SA*>(a.apart) + (((size_t)(it & 1) * a.ngrp + gi) * P + pi) * W * 2;
       ap[threadIdx.x] = dsum[16 + threadIdx.x];
     }
   }
   __syncthreads();
-  task_mark(a.ptask, 0, 1, &tm);       // update and scatter
+  task_mark(a.ptask, 0, 2, &tm);       // update and scatter
   // ---- z-IFFT of the disc rows, transpose into the plane, y-IFFT, store
   V* R = fft_tile2<T, +1, false>(Ab, Bb, npp, LDp, 1, a.pl, stw);
   V* Q = (R == Ab) ? Bb : Ab;
@@ -584,12 +769,9 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
   }
   __syncthreads();
   V* S = fft_tile2<T, +1, true>(Q, R, N, 1, LDp, a.pl, stw);
-  task_mark(a.ptask, 0, 2, &tm);       // transforms
+  task_mark(a.ptask, 0, 3, &tm);       // transforms
   const size_t base = (size_t)gi * g.N3 + (size_t)i0 * g.N2;
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int i1 = a.pl.dN.div(e), i2 = e - i1 * N;
-    a.grid[base + e] = S[i1 * LDp + i2];
-  }
+  store_rows<T>(a.grid + base, N, S, LDp, N, N, nullptr);
   signal_done(gc + 0);
   task_time(a.ptask, 0, t0, t1, true);
 }
@@ -618,11 +800,7 @@ __device__ void task_B(const PcgArgs<T>& a, int it, int gi, int i1, unsigned cha
   if (s_ctl[0] == 1) task_time(a.ptask, 1, t0, t1, false);
   if (s_ctl[0] != 0) return;
   const size_t base = (size_t)gi * g.N3 + (size_t)i1 * N;
-#pragma unroll 8
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int i0 = a.pl.dN.div(e), i2 = e - i0 * N;
-    Ab[i0 * LDp + i2] = g.plane_mask[i0] ? ldcg(a.grid + base + (size_t)i0 * g.N2 + i2) : mk<T>(0, 0);
-  }
+  load_rows<T>(Ab, LDp, a.grid + base, g.N2, N, N, g.plane_mask);
   __syncthreads();
   unsigned long long tm = t1;
   task_mark(a.ptask, 1, 0, &tm);       // slab load
@@ -638,11 +816,9 @@ __device__ void task_B(const PcgArgs<T>& a, int it, int gi, int i1, unsigned cha
   __syncthreads();
   V* S = fft_tile2<T, -1, true>(R, Q, N, 1, LDp, a.pl, stw);
   task_mark(a.ptask, 1, 1, &tm);       // transforms and V
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int i0 = a.pl.dN.div(e), i2 = e - i0 * N;
-    if (g.plane_mask[i0]) a.grid[base + (size_t)i0 * g.N2 + i2] = S[i0 * LDp + i2];
-  }
+  store_rows<T>(a.grid + base, g.N2, S, LDp, N, N, g.plane_mask);
   signal_done(gc + 1);
+  task_mark(a.ptask, 1, 2, &tm);       // store and signal
   task_time(a.ptask, 1, t0, t1, true);
 }
 
@@ -662,12 +838,15 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
   V* Us = reinterpret_cast<V*>(sm + L.U);          // [W][maxplane] u_c on the plane's entries
   T* Ks = reinterpret_cast<T*>(sm + L.K);          // [maxplane] |G|^2/2 on the plane's entries
   const V* stw = reinterpret_cast<const V*>(sm + L.tw);
-  double* red = reinterpret_cast<double*>(sm + L.red);
-  double* dsum = reinterpret_cast<double*>(sm + L.dsum);
+  Acc<T>* red = reinterpret_cast<Acc<T>*>(sm + L.red);
+  Acc<T>* dsum = reinterpret_cast<Acc<T>*>(sm + L.dsum);
   unsigned long long t0 = 0, t1 = 0;
+  // First wait: the group's A tasks of it are done (r is final): u = K r and
+  // |G|^2/2 on the plane's entries are loaded while the B tasks finish.
   if (threadIdx.x == 0) {
     if (a.ptask) t0 = gtime();
-    s_ctl[0] = wait_dep(gc + 1, (unsigned)((it + 1) * N), gc + 3, (unsigned)(it + 1), a.ctl, a.spin_limit);
+    s_ctl[0] = wait_dep(gc + 0, (unsigned)((it + 1) * g.nplanes), gc + 3, (unsigned)(it + 1), a.ctl,
+                        a.spin_limit);
     if (a.ptask) t1 = gtime();
   }
   __syncthreads();
@@ -678,15 +857,10 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
   const int q0 = g.plane_pen[pi], npp = g.plane_pen[pi + 1] - q0;
   const int ns = s1 - s0;
   const size_t base = (size_t)gi * g.N3 + (size_t)i0 * g.N2;
-#pragma unroll 8
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int i1 = a.pl.dN.div(e), i2 = e - i1 * N;
-    Ab[i1 * LDp + i2] = ldcg(a.grid + base + e);
-  }
   // u_c = K r_c on the plane's entries (0 for an absent column)
   T c_rtk[2];
 #pragma unroll
-  for (int c = 0; c < 2; ++c) c_rtk[c] = (a.tk && c < nc) ? (T)(1.0 / a.tk[c0 + c]) : (T)0;
+  for (int c = 0; c < 2; ++c) c_rtk[c] = (c < nc) ? a.cin[(c0 + c) * 4 + 1] : (T)0;
   for (int e = threadIdx.x; e < ns; e += blockDim.x) {
     const int G = s0 + e;
     const T kinG = a.kin[G];
@@ -705,6 +879,15 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
       Us[c * a.maxplane + e] = u;
     }
   }
+  // Second wait: the group's B tasks of it are done; the plane.
+  if (threadIdx.x == 0) {
+    s_ctl[0] = wait_dep(gc + 1, (unsigned)((it + 1) * N), gc + 3, (unsigned)(it + 1), a.ctl, a.spin_limit);
+    if (a.ptask) t1 = gtime();
+  }
+  __syncthreads();
+  if (s_ctl[0] == 1) task_time(a.ptask, 2, t0, t1, false);
+  if (s_ctl[0] != 0) return;
+  load_rows<T>(Ab, LDp, a.grid + base, N, N, N, nullptr);
   __syncthreads();
   unsigned long long tm = t1;
   task_mark(a.ptask, 2, 0, &tm);       // plane and u loads
@@ -805,6 +988,7 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
       }
     }
   }
+  task_mark(a.ptask, 2, 2, &tm);       // projector dots
   {
     T t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int e = threadIdx.x; e < ns; e += blockDim.x) {
@@ -821,14 +1005,15 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
         t[c * 4 + 3] += n2;
       }
     }
-    double v8[8];
+    Acc<T> v8[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v8[k] = (double)t[k];
+    for (int k = 0; k < 8; ++k) v8[k] = acc_of(t[k]);
     block_sum_n<8>(v8, red, dsum);
-    double* rd = reinterpret_cast<double*>(rec + align16((size_t)(1 + 2 * W) * nocc * sizeof(V)));
+    Acc<T>* rd = reinterpret_cast<Acc<T>*>(rec + align16((size_t)(1 + 2 * W) * nocc * sizeof(V)));
     if (threadIdx.x < 4 * W) rd[threadIdx.x] = dsum[threadIdx.x];
   }
   signal_done(gc + 2);
+  task_mark(a.ptask, 2, 3, &tm);       // scalar sums, record and signal
   task_time(a.ptask, 2, t0, t1, true);
 }
 
@@ -839,13 +1024,14 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_cg_persistent(PcgArgs<T> a) 
   using V = cpx<T>;
   extern __shared__ unsigned char smem_raw[];
   const Geometry& g = a.g;
-  const int N = g.N, P = g.nplanes;
-  const PcgLayout L = pcg_layout(N, a.nocc, a.W, a.maxplane, (int)sizeof(V));
+  const int N = g.N;
+  const PcgLayout L = pcg_layout(N, a.nocc, a.W, a.maxplane, (int)sizeof(V), a.pf != 0);
   __shared__ int s_task[4];
   __shared__ int s_ctl[2];
   V* stw = reinterpret_cast<V*>(smem_raw + L.tw);
   for (int k = threadIdx.x; k < N; k += blockDim.x) stw[k] = a.tw[k];
   __syncthreads();
+  const int P = g.nplanes;
   const unsigned nA = (unsigned)a.ngrp * P, nB = (unsigned)a.ngrp * N;
   const unsigned per_it = 2u * nA + nB;
   while (true) {
@@ -874,14 +1060,16 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_cg_persistent(PcgArgs<T> a) 
 }
 
 template <typename T>
-static size_t pcg_smem(int N, int nocc, int W, int maxplane) {
-  return pcg_layout(N, nocc, W, maxplane, (int)sizeof(cpx<T>)).total;
+static size_t pcg_smem(int N, int nocc, int W, int maxplane, bool pf) {
+  return pcg_layout(N, nocc, W, maxplane, (int)sizeof(cpx<T>), pf).total;
 }
 
-PcgSizes pcg_sizes(int nocc, int npw, int ncol, int W, int nplanes, int N3, int csize) {
+PcgSizes pcg_sizes(int nocc, int npw, int ncol, int W, int nplanes, int N, int csize) {
+  const int N3 = N * N * N;
   PcgSizes z;
   z.W = W;
   z.ngrp = (ncol + W - 1) / W;
+
   z.rec_bytes = pcg_rec_bytes(nocc, W, csize);
   z.rec_total = z.rec_bytes * (size_t)z.ngrp * nplanes;
   z.apart = (size_t)2 * z.ngrp * nplanes * W * 2;
@@ -925,24 +1113,66 @@ static cudaError_t launch_pcg_tpb(cudaStream_t s, const PcgArgs<T>& a0, size_t s
   return cudaLaunchCooperativeKernel((const void*)k_cg_persistent<T, TPB>, dim3(nblk), dim3(TPB), args, sm, s);
 }
 
+// r = b (two packed columns: b symmetrised, b(G) <- (b(G) + conj b(-G)) / 2),
+// x = p = s = 0, and the per-column inputs in T; absent or finished columns
+// (outer_active 0) get r = 0.
+template <typename T>
+__global__ void k_pcg_prep(int npw, int ncol, int W, const double2* __restrict__ b64, const int* outer_active,
+                           const double2* E, const double* rr_abs, const double* tk, const int* __restrict__ sph_neg,
+                           cpx<T>* x, cpx<T>* r, cpx<T>* p, cpx<T>* sv, T* cin) {
+  const size_t n = (size_t)npw * ncol;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int col = (int)(i / (size_t)npw), G = (int)(i - (size_t)col * npw);
+    const bool on = !outer_active || outer_active[col];
+    double2 b = on ? b64[i] : make_double2(0.0, 0.0);
+    if (W == 2 && on) {
+      const double2 bn = b64[(size_t)col * npw + sph_neg[G]];
+      b = make_double2(0.5 * (b.x + bn.x), 0.5 * (b.y - bn.y));
+    }
+    r[i] = from_d<T>(b);
+    x[i] = mk<T>(0, 0);
+    p[i] = mk<T>(0, 0);
+    sv[i] = mk<T>(0, 0);
+    if (G == 0) {
+      cin[col * 4 + 0] = (T)E[col].x;
+      cin[col * 4 + 1] = (tk && tk[col] != 0.0) ? (T)(1.0 / tk[col]) : (T)0;
+      cin[col * 4 + 2] = rr_abs ? (T)rr_abs[col] : (T)0;
+      cin[col * 4 + 3] = on ? (T)1 : (T)0;
+    }
+  }
+}
+
 template <typename T>
 cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPlan& pl, const Prec<T>& P, int nocc,
                                  int npw, int ncol, const PcgSizes& z, int maxplane, const double2* b64,
                                  const int* outer_active, const double2* E, const double* rr_abs, const double* tk,
                                  double tol_in2, int maxit, cpx<T>* x, cpx<T>* r, cpx<T>* p, cpx<T>* sv, cpx<T>* Y,
                                  cpx<T>* grid, unsigned char* rec, double* apart, PcgCol* cst, unsigned* ctl,
-                                 int* iters, int* flags, double* rr_out, int* grid_used, int cta_div,
+                                 T* cin, int* iters, int* flags, double* rr_out, int* grid_used, int cta_div,
                                  unsigned long long spin_limit, unsigned long long* ptask, int tpb) {
+  // the A tasks' prefetch of r, p, s, x when it fits beside the rest
+  const bool pf = pcg_smem<T>(g.N, nocc, z.W, maxplane, true) <= 227 * 1024;
+  const size_t sm = pcg_smem<T>(g.N, nocc, z.W, maxplane, pf);
+  if (sm > 227 * 1024) return cudaErrorNotSupported;
+  {
+    const size_t n = (size_t)npw * ncol;
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+    ++g_launches;
+    k_pcg_prep<T><<<blocks, 256, 0, s>>>(npw, ncol, z.W, b64, outer_active, E, rr_abs, tk, g.sph_neg, x, r, p, sv,
+                                         cin);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   PcgArgs<T> a;
   a.g = g; a.pl = pl; a.tw = P.tw; a.kin = P.kin; a.vloc_s = P.vloc_s; a.C = P.C;
   a.nocc = nocc; a.npw = npw; a.ncol = ncol; a.ngrp = z.ngrp; a.W = z.W; a.maxplane = maxplane;
-  a.b64 = b64; a.outer_active = outer_active; a.E = E; a.rr_abs = rr_abs; a.tk = tk; a.tol_in2 = tol_in2;
+  a.cin = cin; a.tol2 = (T)tol_in2; a.pf = pf ? 1 : 0;
   a.maxit = maxit;
   a.x = x; a.r = r; a.p = p; a.s = sv; a.Y = Y; a.grid = grid; a.rec = rec; a.rec_bytes = z.rec_bytes;
-  a.apart = apart; a.cst = cst; a.ctl = ctl;
+  a.apart = reinterpret_cast<unsigned char*>(apart);
+  a.cst = reinterpret_cast<unsigned char*>(cst);
+  a.ctl = ctl;
   a.iters_out = iters; a.flag_out = flags; a.rr_out = rr_out; a.spin_limit = spin_limit; a.ptask = ptask;
-  const size_t sm = pcg_smem<T>(g.N, nocc, z.W, maxplane);
-  if (sm > 227 * 1024) return cudaErrorNotSupported;
   const int per_it = z.ngrp * (2 * g.nplanes + g.N);
   if (tpb == 512) return launch_pcg_tpb<T, 512>(s, a, sm, cta_div, per_it, grid_used);
   return launch_pcg_tpb<T, 256>(s, a, sm, cta_div, per_it, grid_used);
@@ -952,8 +1182,8 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
   template cudaError_t launch_cg_persistent<T>(                                                            \
       cudaStream_t, const Geometry&, const FftPlan&, const Prec<T>&, int, int, int, const PcgSizes&, int,    \
       const double2*, const int*, const double2*, const double*, const double*, double, int, cpx<T>*,       \
-      cpx<T>*, cpx<T>*, cpx<T>*, cpx<T>*, cpx<T>*, unsigned char*, double*, PcgCol*, unsigned*, int*, int*,  \
-      double*, int*, int, unsigned long long, unsigned long long*, int);
+      cpx<T>*, cpx<T>*, cpx<T>*, cpx<T>*, cpx<T>*, unsigned char*, double*, PcgCol*, unsigned*, T*, int*,    \
+      int*, double*, int*, int, unsigned long long, unsigned long long*, int);
 GW_PCG_INST(float)
 GW_PCG_INST(double)
 

@@ -216,9 +216,10 @@ struct PcgSizes {
   size_t apart = 0, cst = 0, ctl = 0;    // doubles, PcgCol entries, control words
   size_t Y = 0, grid = 0;                // complex entries
 };
-PcgSizes pcg_sizes(int nocc, int npw, int ncol, int W, int nplanes, int N3, int csize);
-// One cooperative launch = one CG pass over ncol columns (kernels_cg.cu); ctl
-// (z.ctl words) must be zero at launch.  cudaErrorNotSupported when the
+PcgSizes pcg_sizes(int nocc, int npw, int ncol, int W, int nplanes, int N, int csize);
+// One cooperative launch = one CG pass over ncol columns (kernels_cg.cu), after
+// a small launch that sets r = b, x = p = s = 0 and the per-column inputs cin
+// ([ncol][4] in T); ctl (z.ctl words) must be zero at launch.  cudaErrorNotSupported when the
 // kernel's shared memory does not fit (the caller then uses the multi-launch CG).
 template <typename T>
 cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPlan& pl, const Prec<T>& P, int nocc,
@@ -226,7 +227,7 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
                                  const int* outer_active, const double2* E, const double* rr_abs, const double* tk,
                                  double tol_in2, int maxit, cpx<T>* x, cpx<T>* r, cpx<T>* p, cpx<T>* sv, cpx<T>* Y,
                                  cpx<T>* grid, unsigned char* rec, double* apart, PcgCol* cst, unsigned* ctl,
-                                 int* iters, int* flags, double* rr_out, int* grid_used, int cta_div,
+                                 T* cin, int* iters, int* flags, double* rr_out, int* grid_used, int cta_div,
                                  unsigned long long spin_limit, unsigned long long* ptask = nullptr,
                                  int tpb = 256);
 // One thread-block cluster per column (kernels_cgc.cu); cudaErrorNotSupported
