@@ -1,4 +1,5 @@
-// Batched shared-memory FFT of short pencils (N <= 128, radices 4, 2, 3, 5).
+// Batched shared-memory FFT of short pencils (N <= 128, radices 4, 2, 3, 5),
+// with register-resident pencils for the common sizes in FP32 (below).
 //
 // Self-sorting Stockham formulation: stage s with radix r and span Ns (the
 // product of the earlier radices) takes butterfly j in [0, N/r):
@@ -100,6 +101,60 @@ __device__ __forceinline__ void fft_stage(const cpx<T>* __restrict__ a, cpx<T>* 
   }
 }
 
+// Register-resident pencils for N = L M (M lanes per pencil, L values per
+// lane; L in 1..5, M a power of two dividing 32): lane m holds x[m + M l].
+// Cooley-Tukey with n = m + M l, k = k1 + L k2:
+//   X[k1 + L k2] = sum_m w_M^(m k2) [ w_N^(m k1) sum_l x[m + M l] w_L^(l k1) ],
+// the L-point DFTs in each lane's registers, the M-point DFTs across the
+// lanes as radix-2 decimation-in-frequency stages with warp shuffles (lane m
+// ends with output k2 = bitreverse(m)).  No barrier between stages; the
+// result goes to the other buffer.  Every lane of a warp takes part in every
+// shuffle (pencils beyond npen run on zeros and store nothing).
+template <typename T, int SIGN, int N, int M>
+__device__ __forceinline__ cpx<T>* fft_tile_reg(const cpx<T>* __restrict__ a, cpx<T>* __restrict__ b, int npen,
+                                                int ps, int es, const cpx<T>* tw) {
+  using V = cpx<T>;
+  constexpr int L = N / M;
+  static_assert(L * M == N && L >= 1 && L <= 5 && (M & (M - 1)) == 0 && M <= 32, "unsupported split");
+  constexpr int LOGM = (M >= 32) ? 5 : (M >= 16) ? 4 : (M >= 8) ? 3 : (M >= 4) ? 2 : (M >= 2) ? 1 : 0;
+  const int lane = threadIdx.x & (M - 1);
+  const int grp = threadIdx.x / M, ngrp = blockDim.x / M;
+  const int k2 = (LOGM > 0) ? (int)(__brev((unsigned)lane) >> (32 - LOGM)) : 0;
+  for (int base = 0; base < npen; base += ngrp) {
+    const int p = base + grp;
+    const bool on = p < npen;
+    V v[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) v[l] = on ? a[p * ps + (lane + M * l) * es] : mk<T>(0, 0);
+    if (L > 1) butterfly<T, SIGN>(v, L);
+#pragma unroll
+    for (int k1 = 1; k1 < L; ++k1) {
+      V w = tw[(lane * k1) % N];
+      if (SIGN > 0) w.y = -w.y;
+      v[k1] = cmul(v[k1], w);
+    }
+#pragma unroll
+    for (int h = M / 2; h >= 1; h >>= 1) {
+      const bool bot = (lane & h) != 0;
+      V w = tw[(lane & (h - 1)) * (N / (2 * h))];
+      if (SIGN > 0) w.y = -w.y;
+#pragma unroll
+      for (int k1 = 0; k1 < L; ++k1) {
+        V o;
+        o.x = __shfl_xor_sync(0xffffffffu, v[k1].x, h);
+        o.y = __shfl_xor_sync(0xffffffffu, v[k1].y, h);
+        v[k1] = bot ? cmul(csub(o, v[k1]), w) : cadd(v[k1], o);
+      }
+    }
+    if (on) {
+#pragma unroll
+      for (int k1 = 0; k1 < L; ++k1) b[p * ps + (k1 + L * k2) * es] = v[k1];
+    }
+  }
+  __syncthreads();
+  return b;
+}
+
 // Generalised tile FFT: npen pencils, pencil p element k at buf[p * ps + k * es].
 // PFAST selects the thread mapping: consecutive threads take consecutive
 // pencils (PFAST, for pencils adjacent in memory: es > 1, ps = 1) or
@@ -112,6 +167,20 @@ __device__ cpx<T>* fft_tile2(cpx<T>* a, cpx<T>* b, int npen, int ps, int es, con
                              const cpx<T>* tw) {
   using V = cpx<T>;
   const int N = pl.N;
+  if (sizeof(T) == 4 && (blockDim.x & 31) == 0) {
+    // register-resident pencils for the common grid sizes (FP32: in FP64 the
+    // shuffle stages' extra twiddle products cost more than the barriers they
+    // save, on this GPU's FP64 rate)
+    switch (N) {
+      case 16: return fft_tile_reg<T, SIGN, 16, 16>(a, b, npen, ps, es, tw);
+      case 24: return fft_tile_reg<T, SIGN, 24, 8>(a, b, npen, ps, es, tw);
+      case 32: return fft_tile_reg<T, SIGN, 32, 16>(a, b, npen, ps, es, tw);
+      case 40: return fft_tile_reg<T, SIGN, 40, 8>(a, b, npen, ps, es, tw);
+      case 48: return fft_tile_reg<T, SIGN, 48, 16>(a, b, npen, ps, es, tw);
+      case 64: return fft_tile_reg<T, SIGN, 64, 16>(a, b, npen, ps, es, tw);
+      default: break;
+    }
+  }
   FastDiv dpen = pl.dN;
   if (PFAST && npen != N) dpen.set((unsigned)npen);
   for (int s = 0; s < pl.nst; ++s) {

@@ -49,7 +49,7 @@ struct gw_ctx {
   bool use_graphs = true;             // SQMR iterations replayed from a captured CUDA graph
   int imag_route = GW_IMAG_SQMR;      // solver of purely imaginary frequencies (gw_set_imaginary_route)
   double recycle_w0 = 0.0;            // > 0: recycled bases augmented with x(i w0)
-  bool use_tc = true;                 // tensor-core projector coefficients where they apply
+  bool use_tc = false;                // tensor-core projector coefficients where they apply (opt-in)
   bool tune = true;                   // launch shapes picked by timing (tune.cu)
   int pcg_tpb = 0;                    // CTA width of the last persistent CG launch
   bool tc_ok = false;                 // the split occupied rows and their tensor maps are ready

@@ -790,6 +790,17 @@ __device__ void task_B(const PcgArgs<T>& a, int it, int gi, int i1, unsigned cha
   V* Ab = reinterpret_cast<V*>(sm + L.A);
   V* Bb = reinterpret_cast<V*>(sm + L.B);
   const V* stw = reinterpret_cast<const V*>(sm + L.tw);
+  // V(r)/N_g on the slab (static) goes to shared memory before the wait when
+  // the prefetch region holds it
+  T* Vs = reinterpret_cast<T*>(sm + L.X);
+  const bool vpf = L.total - L.X >= (size_t)N * N * sizeof(T);
+  if (vpf) {
+#pragma unroll 8
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+      const int i0 = a.pl.dN.div(e), i2 = e - i0 * N;
+      Vs[e] = a.vloc_s[(size_t)i0 * g.N2 + (size_t)i1 * N + i2];
+    }
+  }
   unsigned long long t0 = 0, t1 = 0;
   if (threadIdx.x == 0) {
     if (a.ptask) t0 = gtime();
@@ -809,7 +820,7 @@ __device__ void task_B(const PcgArgs<T>& a, int it, int gi, int i1, unsigned cha
 #pragma unroll 4
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int i0 = a.pl.dN.div(e), i2 = e - i0 * N;
-    const T m = a.vloc_s[(size_t)i0 * g.N2 + (size_t)i1 * N + i2];
+    const T m = vpf ? Vs[e] : a.vloc_s[(size_t)i0 * g.N2 + (size_t)i1 * N + i2];
     const V v = R[i0 * LDp + i2];
     R[i0 * LDp + i2] = mk<T>(v.x * m, v.y * m);
   }
