@@ -14,11 +14,14 @@
 // split over CTAs so that one wave covers the SMs.
 //
 // Precision: kind::tf32 MMAs with FP32 accumulation in tensor memory, and the
-// operands split as x = hi + lo (hi: x with the 13 low mantissa bits cleared,
-// exact in TF32; lo = x - hi): D = A_hi B_hi + A_hi B_lo + A_lo B_hi carries
-// the FP32 accuracy of the CUDA-core dots (the dropped A_lo B_lo term is
-// 2^-22 relative).  A (static: the occupied rows) is split once on the host;
-// each B tile is split in shared memory after it is loaded.
+// operands split as x = hi + lo, hi = x rounded to the nearest TF32 value (10
+// explicit mantissa bits), lo = x - hi (|lo| <= 2^-11 |x|) rounded to TF32 in
+// turn, so that hi + lo meets x to 2^-22 relative; the MMA reads only the TF32
+// bits of its operands, and a truncated split (hi with the low bits cleared)
+// would leave a lo of up to 2^-10 |x| truncated again, 2^-20 relative.
+// D = A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped A_lo B_lo term is 2^-22
+// relative).  A (static: the occupied rows) is split once on the host; each B
+// tile is split in shared memory after it is loaded.
 //
 // Data movement: the A tiles (128 rows x 32 FP32 = one 128-byte swizzle row
 // per row) arrive by TMA (cp.async.bulk.tensor, 128-byte swizzle) on an
@@ -134,8 +137,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// x = hi + lo with hi exact in TF32 (low 13 mantissa bits cleared)
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// The TF32 value nearest to x (ties away from zero): the magnitude bits
+// rounded at the 13th mantissa bit, which stays within the exponent field's
+// carry for finite x.
+__device__ __forceinline__ float tf32_round(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
 
 // Byte offset of the 8-byte element q (0..15) of row n in a 128-byte-swizzled tile.
 __device__ __forceinline__ uint32_t sw_off(int n, int q) {
@@ -206,8 +213,8 @@ k_tc_dots(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUte
       const int j = n0 + n, G = g0 + q;
       float2 v = make_float2(0.f, 0.f);
       if (j < ncol && G < npw) v = Y[(size_t)j * npw + G];
-      const float2 hi = make_float2(tf32_hi(v.x), tf32_hi(v.y));
-      const float2 lo = make_float2(v.x - hi.x, v.y - hi.y);
+      const float2 hi = make_float2(tf32_round(v.x), tf32_round(v.y));
+      const float2 lo = make_float2(tf32_round(v.x - hi.x), tf32_round(v.y - hi.y));
       const uint32_t off = sw_off(n, q);
       *reinterpret_cast<float2*>(Bhi + off) = hi;
       *reinterpret_cast<float2*>(Blo + off) = lo;
@@ -317,14 +324,17 @@ void tc_split_rows(const std::vector<double2>& C, int nocc, int npw, std::vector
   const int kpad = tc_kpad(npw);
   hi->assign((size_t)kTcM * kpad, 0.f);
   lo->assign((size_t)kTcM * kpad, 0.f);
-  auto put = [&](int m, int k, double x) {
-    float h = (float)x;
+  auto round_tf32 = [](float f) {   // as tf32_round on the device
     uint32_t u;
-    std::memcpy(&u, &h, 4);
-    u &= 0xFFFFE000u;
-    std::memcpy(&h, &u, 4);
+    std::memcpy(&u, &f, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    std::memcpy(&f, &u, 4);
+    return f;
+  };
+  auto put = [&](int m, int k, double x) {
+    const float h = round_tf32((float)x);
     (*hi)[(size_t)m * kpad + k] = h;
-    (*lo)[(size_t)m * kpad + k] = (float)(x - (double)h);
+    (*lo)[(size_t)m * kpad + k] = round_tf32((float)(x - (double)h));
   };
   for (int v = 0; v < nocc; ++v)
     for (int G = 0; G < npw; ++G) {

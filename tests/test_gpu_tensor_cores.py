@@ -44,13 +44,15 @@ def test_tensor_core_projector_coefficients(name, ncol):
     gw.gw_proj_coef(cell.ctx, ty, c1, 1)
     a0, a1 = c0.cpu().numpy(), c1.cpu().numpy()
     cell.close()
-    # both kernels carry FP32 rounding over ~2 N_PW terms (~1e-6 of the largest
-    # coefficient); the FP64 invariant checks each of them
+    # both kernels carry FP32-level rounding over ~2 N_PW terms: the CUDA-core
+    # dots FP32 products and sums, the tensor cores the 2^-22 of the TF32
+    # hi/lo split per product; the FP64 invariant checks each of them
     scale = np.abs(a0).max()
-    assert np.abs(a1 - a0).max() < 1e-5 * scale
+    print(f"max |tensor - CUDA cores| / max |coef| = {np.abs(a1 - a0).max() / scale:.2e}")
+    assert np.abs(a1 - a0).max() < 1e-6 * scale
     ref = (np.abs(np.conj(gs.C) @ y.astype(np.complex128).T) ** 2).sum(0)     # |P_v y_j|^2
     for a in (a0, a1):
-        assert np.abs((np.abs(a) ** 2).sum(0) - ref).max() < 1e-5 * ref.max()
+        assert np.abs((np.abs(a) ** 2).sum(0) - ref).max() < 2e-6 * ref.max()
 
 
 def test_tensor_cores_in_the_mixed_sqmr_solver():
@@ -69,9 +71,14 @@ def test_tensor_cores_in_the_mixed_sqmr_solver():
     d64 = cell.apply_chi0(f, om, gw.GW_FP64)
     cell.set_tensor_cores(1)
     dtc = cell.apply_chi0(f, om, gw.GW_MIXED)
+    it_tc = cell.stats()["mean_iter"]
     cell.set_tensor_cores(0)
     dcc = cell.apply_chi0(f, om, gw.GW_MIXED)
+    it_cc = cell.stats()["mean_iter"]
     cell.close()
     s = np.abs(d64).max()
     assert np.abs(dtc - d64).max() < 1e-6 * s
     assert np.abs(dcc - d64).max() < 1e-6 * s
+    # the coefficients' accuracy must not cost the solver iterations
+    print(f"mean SQMR iterations: tensor cores {it_tc:.1f}, CUDA cores {it_cc:.1f}")
+    assert it_tc <= 1.15 * it_cc
