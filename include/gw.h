@@ -335,10 +335,11 @@ gw_status gw_proj_coef(gw_ctx* ctx, const float* y, int ncol, double* coef, int 
 /* gw_set_tensor_cores -- 1: the mixed simplified-QMR solver takes its
    projector coefficients from the tensor cores (gw_proj_coef kernel 1) when
    it has at least 256 columns and at most 64 projector rows; 0 (default):
-   CUDA cores always.  Off by default: the three-product TF32 coefficients
-   carry about 2e-6 relative error against about 1e-7 for the CUDA-core FP32
-   dots, and on the 64^3 cell with 64 occupied states the solver then needs
-   about four times as many iterations. */
+   CUDA cores always.  Off by default: the tensor-core coefficients carry
+   about 2e-6 relative error (the FP32 accumulation in tensor memory) against
+   about 1e-7 for the CUDA-core FP32 dots, and on the 64^3 cell with 64
+   occupied states the solver then needs about four times as many
+   iterations. */
 gw_status gw_set_tensor_cores(gw_ctx* ctx, int on);
 
 /*

@@ -739,7 +739,6 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
   TRY(getbuf(ctx, "sv_cb", (size_t)ctx->nocc * ncol, &cb));
   TRY(getbuf(ctx, "sv_cax", (size_t)ctx->nocc * ncol, &cax));
   TRY(ensure_work(ctx, ncol));
-  launch_gram<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, b64, ncol, ctx->work, cb);   // C^H b
   double2* cdef = nullptr;
   double* edef = nullptr;
   if (ctx->ndef > 0) {
@@ -763,6 +762,8 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
     sym = true;
     for (int c = 0; c < ncol; ++c) sym = sym && (hs[c] <= 1e-12 * hs[ncol + c]);
   }
+  // C^H b (real coefficients for real-in-real-space columns: the occupied rows are too)
+  launch_gram<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, b64, ncol, ctx->work, cb, sym);
   std::vector<int> act(ncol, 1);
   TRY(upload(ctx, "sv_oact", act, &oact));
   std::vector<double> hr(ncol, 0.0), hb(ncol, 0.0), hx(ncol, 0.0), habs(ncol, 0.0);
@@ -830,7 +831,7 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
       if (sym) {
         // two real-in-real-space columns per FP64 transform
         TRY(h_apply_sym(ctx, x64, ncol, E, act, ax));
-        launch_gram<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, ax, ncol, ctx->work, cax);
+        launch_gram<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, ax, ncol, ctx->work, cax, true);
       } else {
         GatherDots dots;
         dots.C = ctx->P64.C;
@@ -885,7 +886,7 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
   // The solution lies in P_c.  Inner passes in FP32 leave valence components
   // at the FP32 rounding level that the residual cannot see (P_c removes them
   // from A x) but the density reduction would: project them out in FP64.
-  launch_proj<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, x64, ncol, nullptr, ctx->work, nullptr, nullptr);
+  launch_proj<double>(ctx->st, ctx->P64.C, ctx->nocc, npw, x64, ncol, nullptr, ctx->work, nullptr, nullptr, sym);
   {
     double fin = 0.0;        // final relative FP64 residual |b - A x| / |b| over all columns
     for (int c = 0; c < ncol; ++c) fin = std::max(fin, hb[c] > 0 ? std::sqrt(hr[c] / hb[c]) : 0.0);
@@ -990,7 +991,7 @@ gw_status rhs_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, double2** ou
   // P_c once: psi_v* y has a large component along the occupied states (e.g.
   // <psi_v|y psi_v>) and one pass leaves |C C^H - 1| times it behind; the
   // solver's FP64 residual P_c (b - A x) removes that remnant
-  launch_proj<double>(ctx->st, ctx->P64.C, nocc, npw, rhs64, nr, nullptr, ctx->work, nullptr, nullptr);
+  launch_proj<double>(ctx->st, ctx->P64.C, nocc, npw, rhs64, nr, nullptr, ctx->work, nullptr, nullptr, !y_cplx);
   *out = rhs64;
   return launch_check(ctx, "rhs");
 }

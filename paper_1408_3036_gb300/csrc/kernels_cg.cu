@@ -81,6 +81,7 @@ struct PcgArgs {
   T tol2;
   int maxit;
   int pf;                     // 1: the A tasks prefetch r, p, s, x into shared memory
+  int crs;                    // 1: A and C tasks stage the plane's occupied rows C in shared memory
   cpx<T>* x;
   cpx<T>* r;
   cpx<T>* p;
@@ -187,7 +188,7 @@ __device__ __forceinline__ void block_sum_n(A (&v)[NV], A* sh, A* out) {
 }
 
 struct PcgLayout {
-  size_t A, B, U, K, tw, rowmap, red, S, coef, dsum, ap, col, pre, IX, X, total;
+  size_t A, B, U, K, tw, rowmap, red, S, coef, dsum, ap, col, pre, IX, X, CR, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -197,9 +198,11 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 // twiddles, the row map of a plane's disc pencils, reduction scratch, the
 // summed records, the group's projector coefficients and <C_v|u_c> (A tasks),
 // scalar sums, the staged per-plane partials of the A tasks, per-column
-// scalars, the plane's -G indices and scatter positions (A tasks), and with
-// pf the plane's r, p, s, x prefetched by the A tasks.
-__host__ __device__ inline PcgLayout pcg_layout(int N, int nocc, int W, int maxplane, int vsize, bool pf) {
+// scalars, the plane's -G indices and scatter positions (A tasks), with pf
+// the plane's r, p, s, x prefetched by the A tasks, and with crs the plane's
+// occupied rows C staged by the A and C tasks.
+__host__ __device__ inline PcgLayout pcg_layout(int N, int nocc, int W, int maxplane, int vsize, bool pf,
+                                                bool crs) {
   PcgLayout L;
   L.A = 0;
   L.B = align16(L.A + (size_t)N * (N + 1) * vsize);
@@ -216,7 +219,8 @@ __host__ __device__ inline PcgLayout pcg_layout(int N, int nocc, int W, int maxp
   L.pre = align16(L.col + 2 * 8 * sizeof(double));
   L.IX = align16(L.pre + 2 * (4 * sizeof(double) + sizeof(PcgCol)));
   L.X = align16(L.IX + (size_t)2 * maxplane * sizeof(int));
-  L.total = align16(L.X + (pf ? (size_t)W * 4 * maxplane * vsize : 0));
+  L.CR = align16(L.X + (pf ? (size_t)W * 4 * maxplane * vsize : 0));
+  L.total = align16(L.CR + (crs ? (size_t)nocc * maxplane * vsize : 0));
   return L;
 }
 
@@ -335,6 +339,19 @@ __device__ __forceinline__ void store_rows(cpx<T>* g, size_t stride, const cpx<T
   }
 }
 
+// The plane's occupied rows C[v][s0 .. s0 + ns) into CR[v][0 .. ns) (static
+// data: loaded at the start of a task, before its waits).
+template <typename T>
+__device__ __forceinline__ void stage_rows(cpx<T>* CR, int maxplane, const cpx<T>* C, int npw, int nocc, int s0,
+                                           int ns) {
+  const int tot = nocc * ns;
+#pragma unroll 8
+  for (int f = threadIdx.x; f < tot; f += blockDim.x) {
+    const int v = f / ns, e = f - v * ns;
+    CR[(size_t)v * maxplane + e] = C[(size_t)v * npw + s0 + e];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // A task
 // ---------------------------------------------------------------------------
@@ -370,6 +387,7 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
   V* Ys = reinterpret_cast<V*>(sm + L.U);             // [maxplane]: Y on the plane, then (W = 2) on its mirror
   const int pm = g.plane_mirror[pi];
   const int s0m = g.plane_sph[pm];
+  V* CR = reinterpret_cast<V*>(sm + L.CR);            // [nocc][maxplane]: the plane's rows of C (crs)
   unsigned long long t0 = 0, t1 = 0;
   // First wait (it > 0, pf): the group's A tasks of it - 1 are done, so the
   // plane's r, p, s, x are final; they and the plane's static per-entry values
@@ -393,6 +411,7 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
     IXn[e] = g.sph_neg[G] - s0m;
     IXs[e] = (g.sph_pen[G] - q0) * LDp + g.sph_i2[G];
   }
+  if (a.crs) stage_rows<T>(CR, a.maxplane, a.C, a.npw, nocc, s0, ns);
   if (pf) {
     const int nvec = (it == 0) ? 1 : 4, tot = nc * nvec * ns;
 #pragma unroll 8
@@ -710,7 +729,9 @@ __device__ void task_A(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
       for (int v = 0; v < nocc; v += RB) {
         V cv[RB];
 #pragma unroll
-        for (int q = 0; q < RB; ++q) cv[q] = (v + q < nocc) ? a.C[(size_t)(v + q) * a.npw + G] : mk<T>(0, 0);
+        for (int q = 0; q < RB; ++q)
+          cv[q] = (v + q < nocc) ? (a.crs ? CR[(size_t)(v + q) * a.maxplane + e] : a.C[(size_t)(v + q) * a.npw + G])
+                                 : mk<T>(0, 0);
 #pragma unroll
         for (int q = 0; q < RB; ++q) {
           if (v + q < nocc) {
@@ -851,6 +872,7 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
   const V* stw = reinterpret_cast<const V*>(sm + L.tw);
   Acc<T>* red = reinterpret_cast<Acc<T>*>(sm + L.red);
   Acc<T>* dsum = reinterpret_cast<Acc<T>*>(sm + L.dsum);
+  V* CR = reinterpret_cast<V*>(sm + L.CR);            // [nocc][maxplane]: the plane's rows of C (crs)
   unsigned long long t0 = 0, t1 = 0;
   // First wait: the group's A tasks of it are done (r is final): u = K r and
   // |G|^2/2 on the plane's entries are loaded while the B tasks finish.
@@ -868,6 +890,7 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
   const int q0 = g.plane_pen[pi], npp = g.plane_pen[pi + 1] - q0;
   const int ns = s1 - s0;
   const size_t base = (size_t)gi * g.N3 + (size_t)i0 * g.N2;
+  if (a.crs) stage_rows<T>(CR, a.maxplane, a.C, a.npw, nocc, s0, ns);
   // u_c = K r_c on the plane's entries (0 for an absent column)
   T c_rtk[2];
 #pragma unroll
@@ -934,8 +957,8 @@ __device__ void task_C(const PcgArgs<T>& a, int it, int gi, int pi, unsigned cha
     for (int v0 = warp; v0 < nocc; v0 += 2 * nw) {
       const int v1 = v0 + nw;
       const bool two = v1 < nocc;
-      const V* C0 = a.C + (size_t)v0 * a.npw + s0;
-      const V* C1 = a.C + (size_t)(two ? v1 : v0) * a.npw + s0;
+      const V* C0 = a.crs ? CR + (size_t)v0 * a.maxplane : a.C + (size_t)v0 * a.npw + s0;
+      const V* C1 = a.crs ? CR + (size_t)(two ? v1 : v0) * a.maxplane : a.C + (size_t)(two ? v1 : v0) * a.npw + s0;
       T acc[2][10];
 #pragma unroll
       for (int h = 0; h < 2; ++h)
@@ -1036,7 +1059,7 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_cg_persistent(PcgArgs<T> a) 
   extern __shared__ unsigned char smem_raw[];
   const Geometry& g = a.g;
   const int N = g.N;
-  const PcgLayout L = pcg_layout(N, a.nocc, a.W, a.maxplane, (int)sizeof(V), a.pf != 0);
+  const PcgLayout L = pcg_layout(N, a.nocc, a.W, a.maxplane, (int)sizeof(V), a.pf != 0, a.crs != 0);
   __shared__ int s_task[4];
   __shared__ int s_ctl[2];
   V* stw = reinterpret_cast<V*>(smem_raw + L.tw);
@@ -1071,8 +1094,8 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_cg_persistent(PcgArgs<T> a) 
 }
 
 template <typename T>
-static size_t pcg_smem(int N, int nocc, int W, int maxplane, bool pf) {
-  return pcg_layout(N, nocc, W, maxplane, (int)sizeof(cpx<T>), pf).total;
+static size_t pcg_smem(int N, int nocc, int W, int maxplane, bool pf, bool crs) {
+  return pcg_layout(N, nocc, W, maxplane, (int)sizeof(cpx<T>), pf, crs).total;
 }
 
 PcgSizes pcg_sizes(int nocc, int npw, int ncol, int W, int nplanes, int N, int csize) {
@@ -1161,9 +1184,11 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
                                  cpx<T>* grid, unsigned char* rec, double* apart, PcgCol* cst, unsigned* ctl,
                                  T* cin, int* iters, int* flags, double* rr_out, int* grid_used, int cta_div,
                                  unsigned long long spin_limit, unsigned long long* ptask, int tpb) {
-  // the A tasks' prefetch of r, p, s, x when it fits beside the rest
-  const bool pf = pcg_smem<T>(g.N, nocc, z.W, maxplane, true) <= 227 * 1024;
-  const size_t sm = pcg_smem<T>(g.N, nocc, z.W, maxplane, pf);
+  // the A tasks' prefetch of r, p, s, x when it fits beside the rest; with one
+  // CTA per SM (512 threads) also the plane's occupied rows, when they fit
+  const bool pf = pcg_smem<T>(g.N, nocc, z.W, maxplane, true, false) <= 227 * 1024;
+  const bool crs = pf && tpb == 512 && pcg_smem<T>(g.N, nocc, z.W, maxplane, true, true) <= 227 * 1024;
+  const size_t sm = pcg_smem<T>(g.N, nocc, z.W, maxplane, pf, crs);
   if (sm > 227 * 1024) return cudaErrorNotSupported;
   {
     const size_t n = (size_t)npw * ncol;
@@ -1177,7 +1202,7 @@ cudaError_t launch_cg_persistent(cudaStream_t s, const Geometry& g, const FftPla
   PcgArgs<T> a;
   a.g = g; a.pl = pl; a.tw = P.tw; a.kin = P.kin; a.vloc_s = P.vloc_s; a.C = P.C;
   a.nocc = nocc; a.npw = npw; a.ncol = ncol; a.ngrp = z.ngrp; a.W = z.W; a.maxplane = maxplane;
-  a.cin = cin; a.tol2 = (T)tol_in2; a.pf = pf ? 1 : 0;
+  a.cin = cin; a.tol2 = (T)tol_in2; a.pf = pf ? 1 : 0; a.crs = crs ? 1 : 0;
   a.maxit = maxit;
   a.x = x; a.r = r; a.p = p; a.s = sv; a.Y = Y; a.grid = grid; a.rec = rec; a.rec_bytes = z.rec_bytes;
   a.apart = reinterpret_cast<unsigned char*>(apart);

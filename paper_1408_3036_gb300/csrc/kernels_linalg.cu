@@ -41,8 +41,11 @@ __device__ __forceinline__ R block_sum(R v) {
 // ---------------------------------------------------------------------------
 constexpr int kChunkP = 128;  // sphere entries per block in the projector coefficients (spreads over all SMs)
 
-// (a) coef[v * ncol + b] = sum_G conj(C[v][G]) Y[b][G]; grid (nchunk, ceil(ncol / kCT))
-template <typename T>
+// (a) coef[v * ncol + b] = sum_G conj(C[v][G]) Y[b][G]; grid (nchunk, ceil(ncol / kCT)).
+// REAL: rows and columns real in real space (x(-G) = conj x(G)), so every
+// coefficient is real: only Re is summed (half the products and reductions)
+// and Im is 0.
+template <typename T, bool REAL>
 __global__ void __launch_bounds__(kLT)
 k_proj_dots(const cpx<T>* __restrict__ C, int nocc, int npw, const cpx<T>* __restrict__ Y, int ncol,
             const int* __restrict__ active, double2* __restrict__ partial, unsigned* __restrict__ cnt,
@@ -67,7 +70,7 @@ k_proj_dots(const cpx<T>* __restrict__ C, int nocc, int npw, const cpx<T>* __res
         if (j < nb) {
           const cpx<T> y = Y[(size_t)(b0 + j) * npw + G];
           ax[j] += c.x * y.x + c.y * y.y;
-          ay[j] += c.x * y.y - c.y * y.x;
+          if (!REAL) ay[j] += c.x * y.y - c.y * y.x;
         }
       }
     }
@@ -76,7 +79,7 @@ k_proj_dots(const cpx<T>* __restrict__ C, int nocc, int npw, const cpx<T>* __res
       T sx = ax[j], sy = ay[j];
       for (int o = 16; o > 0; o >>= 1) {
         sx += __shfl_xor_sync(0xffffffffu, sx, o);
-        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        if (!REAL) sy += __shfl_xor_sync(0xffffffffu, sy, o);
       }
       if (lane == 0 && j < nb) part[((size_t)blockIdx.x * nocc + v) * ncol + b0 + j] = mk<T>(sx, sy);
     }
@@ -93,7 +96,7 @@ k_proj_dots(const cpx<T>* __restrict__ C, int nocc, int npw, const cpx<T>* __res
 
 // (b) Y[b] -= sum_v C[v] coef[v][b] (precision T); optionally pap[b] = Re <P[b]|Y[b]> (new Y),
 // accumulated in FP64.  grid (nchunk, ncol)
-template <typename T>
+template <typename T, bool REAL>
 __global__ void __launch_bounds__(kLT)
 k_proj_update(const cpx<T>* __restrict__ C, int nocc, int npw, cpx<T>* __restrict__ Y, int ncol,
               const int* __restrict__ active, const double2* __restrict__ coef,
@@ -111,8 +114,13 @@ k_proj_update(const cpx<T>* __restrict__ C, int nocc, int npw, cpx<T>* __restric
     for (int v = 0; v < nocc; ++v) {
       const cpx<T> c = C[(size_t)v * npw + G];
       const cpx<T> a = sc[v];
-      y.x -= c.x * a.x - c.y * a.y;
-      y.y -= c.x * a.y + c.y * a.x;
+      if (REAL) {                   // real coefficient
+        y.x -= c.x * a.x;
+        y.y -= c.y * a.x;
+      } else {
+        y.x -= c.x * a.x - c.y * a.y;
+        y.y -= c.x * a.y + c.y * a.x;
+      }
     }
     Y[(size_t)b * npw + G] = y;
     if (Pv) {
@@ -133,24 +141,26 @@ k_proj_update(const cpx<T>* __restrict__ C, int nocc, int npw, cpx<T>* __restric
 
 template <typename T>
 void launch_proj(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, int ncol, const int* active,
-                 Work& w, const cpx<T>* Pv, double* pap) {
+                 Work& w, const cpx<T>* Pv, double* pap, bool real) {
   if (ncol == 0 || nocc == 0) return;
   const int nchunk = (npw + kChunkP - 1) / kChunkP;
   dim3 g1(nchunk, (ncol + kCT - 1) / kCT);
   ++g_launches;
-  k_proj_dots<T><<<g1, kLT, 0, s>>>(C, nocc, npw, Y, ncol, active, w.part2, w.cnt_a, w.coef);
-  launch_proj_update<T>(s, C, nocc, npw, Y, ncol, active, w.coef, w, Pv, pap);
+  if (real) k_proj_dots<T, true><<<g1, kLT, 0, s>>>(C, nocc, npw, Y, ncol, active, w.part2, w.cnt_a, w.coef);
+  else k_proj_dots<T, false><<<g1, kLT, 0, s>>>(C, nocc, npw, Y, ncol, active, w.part2, w.cnt_a, w.coef);
+  launch_proj_update<T>(s, C, nocc, npw, Y, ncol, active, w.coef, w, Pv, pap, real);
 }
 
 // Gram matrix only: coef[v * ncol + b] = sum_G conj(C[v][G]) Y[b][G]
 template <typename T>
 void launch_gram(cudaStream_t s, const cpx<T>* C, int nocc, int npw, const cpx<T>* Y, int ncol, Work& w,
-                 double2* out) {
+                 double2* out, bool real) {
   if (ncol == 0 || nocc == 0) return;
   const int nchunk = (npw + kChunkP - 1) / kChunkP;
   dim3 g1(nchunk, (ncol + kCT - 1) / kCT);
   ++g_launches;
-  k_proj_dots<T><<<g1, kLT, 0, s>>>(C, nocc, npw, Y, ncol, nullptr, w.part2, w.cnt_a, out);
+  if (real) k_proj_dots<T, true><<<g1, kLT, 0, s>>>(C, nocc, npw, Y, ncol, nullptr, w.part2, w.cnt_a, out);
+  else k_proj_dots<T, false><<<g1, kLT, 0, s>>>(C, nocc, npw, Y, ncol, nullptr, w.part2, w.cnt_a, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -272,12 +282,13 @@ void launch_sq_shift(cudaStream_t s, int npw, int ncol, cpx<T>* Ap, const cpx<T>
 
 template <typename T>
 void launch_proj_update(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, int ncol,
-                        const int* active, const double2* coef, Work& w, const cpx<T>* Pv, double* pap) {
+                        const int* active, const double2* coef, Work& w, const cpx<T>* Pv, double* pap, bool real) {
   if (ncol == 0 || nocc == 0) return;
   const int nchunk = (npw + kChunk - 1) / kChunk;
   dim3 g2(nchunk, ncol);
   ++g_launches;
-  k_proj_update<T><<<g2, kLT, 0, s>>>(C, nocc, npw, Y, ncol, active, coef, Pv, w.part1, w.cnt_b, pap);
+  if (real) k_proj_update<T, true><<<g2, kLT, 0, s>>>(C, nocc, npw, Y, ncol, active, coef, Pv, w.part1, w.cnt_b, pap);
+  else k_proj_update<T, false><<<g2, kLT, 0, s>>>(C, nocc, npw, Y, ncol, active, coef, Pv, w.part1, w.cnt_b, pap);
 }
 
 // ---------------------------------------------------------------------------
@@ -1154,11 +1165,12 @@ void launch_tridiag_inv(cudaStream_t s, int K, const double* alpha, const double
   template void launch_qmr<T>(cudaStream_t, int, int, int, const double2*, cpx<T>*, cpx<T>*, cpx<T>*,       \
                               cpx<T>*, const cpx<T>*, const int*, const int*, Work&, QmrState, const T*, double,   \
                               int);                                                                        \
-  template void launch_gram<T>(cudaStream_t, const cpx<T>*, int, int, const cpx<T>*, int, Work&, double2*); \
+  template void launch_gram<T>(cudaStream_t, const cpx<T>*, int, int, const cpx<T>*, int, Work&, double2*, \
+                               bool);                                                                      \
   template void launch_proj_update<T>(cudaStream_t, const cpx<T>*, int, int, cpx<T>*, int, const int*,     \
-                                      const double2*, Work&, const cpx<T>*, double*);                      \
+                                      const double2*, Work&, const cpx<T>*, double*, bool);                \
   template void launch_proj<T>(cudaStream_t, const cpx<T>*, int, int, cpx<T>*, int, const int*, Work&,     \
-                               const cpx<T>*, double*);                                                    \
+                               const cpx<T>*, double*, bool);                                              \
   template void launch_cg_init<T, double>(cudaStream_t, int, int, const double2*, cpx<T>*, cpx<T>*,       \
                                           const int*, Work&, CgState, const T*, double, double);           \
   template void launch_cg_update<T>(cudaStream_t, int, int, cpx<T>*, cpx<T>*, const cpx<T>*,              \

@@ -65,7 +65,7 @@ struct QmrState {
 
 template <typename T>
 void launch_proj(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, int ncol, const int* active,
-                 Work& w, const cpx<T>* Pv, double* pap);
+                 Work& w, const cpx<T>* Pv, double* pap, bool real = false);
 // step 0 init, 1 sigma/alpha, 2 residual, 3 d/x/rho/beta + stop test, 4 q update
 template <typename T>
 void launch_qmr(cudaStream_t s, int step, int npw, int ncol, const double2* b, cpx<T>* x, cpx<T>* r, cpx<T>* q,
@@ -73,14 +73,14 @@ void launch_qmr(cudaStream_t s, int step, int npw, int ncol, const double2* b, c
                 const T* kin, double tol_in2, int maxit);
 template <typename T>
 void launch_proj_update(cudaStream_t s, const cpx<T>* C, int nocc, int npw, cpx<T>* Y, int ncol,
-                        const int* active, const double2* coef, Work& w, const cpx<T>* Pv, double* pap);
+                        const int* active, const double2* coef, Work& w, const cpx<T>* Pv, double* pap, bool real = false);
 // Ap += w2[c] p per column; pap[c] = Re <p|Ap> when pap is given
 template <typename T>
 void launch_sq_shift(cudaStream_t s, int npw, int ncol, cpx<T>* Ap, const cpx<T>* p, const double* w2,
                      const int* active, Work& w, double* pap);
 template <typename T>
 void launch_gram(cudaStream_t s, const cpx<T>* C, int nocc, int npw, const cpx<T>* Y, int ncol, Work& w,
-                 double2* out);
+                 double2* out, bool real = false);
 void launch_wmat(cudaStream_t s, const double2* U, const double* w, int n, int nocc, Work& wk, double2* W);
 void launch_g1(cudaStream_t s, const double2* dU, const double2* U, const double2* S, int n, int nocc,
                double inv_vol, double* g1);
