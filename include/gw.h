@@ -248,8 +248,7 @@ gw_status gw_epsinv_elements(gw_ctx* ctx, const double* alpha, const double* bet
  * multipliers and zero-pivot flag live in one fixed 64 KB __device__ array in
  * the library, which every GPU that loads the library keeps until the process
  * exits.  The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress with the device current); make that first call before
- * any stream capture on the device.  All calls on a device share the array:
+ * (cudaGetSymbolAddress with the device current).  All calls on a device share the array:
  * calls that overlap on the GPU (other streams, other host threads) race and
  * must be serialised by the caller.  Returns GW_E_BREAKDOWN for a zero pivot.
  */

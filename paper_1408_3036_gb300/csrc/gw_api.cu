@@ -1048,9 +1048,13 @@ gw_status chi0_model_core(gw_ctx* ctx, const T* y, bool y_cplx, int nb, const st
   launch_ypass<T>(ctx->st, 0, 0, 1, g, P, ctx->plan, grid, nullptr, nr, 0);
   launch_zpass<T>(ctx->st, Z_GATHER_FWD, g, P, ctx->plan, grid, rhs, nullptr, nullptr, nullptr, nullptr, nullptr,
                   nullptr, nullptr, nr);
-  launch_proj<T>(ctx->st, P.C, nocc, npw, rhs, nr, nullptr, ctx->work, nullptr, nullptr);
+  // real fields and realified states: real-in-real-space right-hand sides and,
+  // at real frequencies (denominators even in G), solutions: real coefficients
+  bool real_w = !y_cplx;
+  for (const double2& w : omega) real_w = real_w && w.y == 0.0;
+  launch_proj<T>(ctx->st, P.C, nocc, npw, rhs, nr, nullptr, ctx->work, nullptr, nullptr, !y_cplx);
   launch_model_scale<T>(ctx->st, npw, nsol, P.kin, rhs, dsrc, dEm, dEp, sol);
-  launch_proj<T>(ctx->st, P.C, nocc, npw, sol, nsol, nullptr, ctx->work, nullptr, nullptr);
+  launch_proj<T>(ctx->st, P.C, nocc, npw, sol, nsol, nullptr, ctx->work, nullptr, nullptr, real_w);
   launch_zpass<T>(ctx->st, Z_SCATTER_INV, g, P, ctx->plan, grid, sol, nullptr, nullptr, nullptr, nullptr, nullptr,
                   nullptr, nullptr, nsol);
   launch_ypass<T>(ctx->st, 1, 1, 0, g, P, ctx->plan, grid, nullptr, nsol, 0);
