@@ -719,7 +719,7 @@ gw_status inner_solve(gw_ctx* ctx, bool qmr, int ncol, const double2* r64, const
 // (P_c (H - E) P_c)^2 x + w2 x = b, by CG (w2max: the largest w2, for |A|).
 template <typename T>
 gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, double2* x64, bool qmr = false,
-                const double* tk = nullptr, const double* w2 = nullptr, double w2max = 0.0) {
+                const double* tk = nullptr, const double* w2 = nullptr, double w2max = 0.0, int sym_hint = -1) {
   const int npw = ctx->npw;
   const bool mixed = !std::is_same<T, double>::value;
   const double tol = mixed ? ctx->tol_mixed : ctx->tol;
@@ -749,10 +749,13 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
   CK(cudaMemcpyAsync(r64, b64, (size_t)ncol * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
   // Right-hand sides that are real in real space (b(-G) = conj b(G): real
   // fields, realified occupied states) have real-in-real-space solutions; the
-  // CG then packs two columns into one complex transform.  Decided from the
-  // data, to the FP64 rounding of the right-hand sides.
+  // CG then packs two columns into one complex transform.  Given by the caller
+  // when it knows (sym_hint 0 or 1), else decided from the data, to the FP64
+  // rounding of the right-hand sides.
   bool sym = false;
-  if (!qmr) {
+  if (!qmr && sym_hint >= 0) {
+    sym = sym_hint != 0;             // known to the caller (real fields and states)
+  } else if (!qmr) {
     double* symv;
     TRY(getbuf(ctx, "sv_sym", (size_t)2 * ncol, &symv));
     launch_sym_check(ctx->st, npw, ncol, b64, ctx->geo.sph_neg, symv);
@@ -845,7 +848,7 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
       prof_end(ctx, PC_REFINE, pa);
     }
     launch_residual(ctx->st, npw, ncol, b64, ax, x64, oact, ctx->work, res2, bb, xx, ctx->P64.C, ctx->nocc, cb,
-                    cax);
+                    cax, sym && !w2);
     CK(cudaMemcpyAsync(r64, ax, (size_t)ncol * npw * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st));
     CK(cudaMemcpyAsync(hr.data(), res2, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaMemcpyAsync(hb.data(), bb, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
@@ -1133,7 +1136,8 @@ gw_status chi0_core(gw_ctx* ctx, const void* y, bool y_cplx, int nb, const std::
   TRY(getbuf(ctx, "xcol", (size_t)ncol * npw, &xcol));
   launch_gather_rows<double, double>(ctx->st, npw, ncol, rhs64, dsrc, bcol);
   gw_status sv = GW_OK;
-  if (nstd > 0) SOFT(sv, (solve<S>(ctx, nstd, bcol, dE, xcol, qmr, dtk)));
+  // real fields at omega = 0: right-hand sides real in real space by construction
+  if (nstd > 0) SOFT(sv, (solve<S>(ctx, nstd, bcol, dE, xcol, qmr, dtk, nullptr, 0.0, (!qmr && !y_cplx) ? 1 : -1)));
   if (nsq > 0) {
     // Eq. P2+: ((H - e_v)^2 + w^2) y = 2 (H - e_v) b gives y = x^- + x^+ at
     // omega = i w; solved for x = y / 2 from the right-hand side P_c (H - e_v) b

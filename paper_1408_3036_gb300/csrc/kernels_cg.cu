@@ -240,12 +240,15 @@ __device__ __forceinline__ int wait_dep(const unsigned* cnt, unsigned target, co
                                         unsigned* ctl, unsigned long long limit) {
   unsigned long long spins = 0;
   while (true) {
+    // the three words loaded back to back: one L2 round trip per poll
     const unsigned d = *(volatile const unsigned*)done1;
+    const unsigned c = *(volatile const unsigned*)cnt;
+    const unsigned e = *(volatile const unsigned*)&ctl[2];
     if (d != 0u && d <= skip_le) return 1;
-    if (*(volatile const unsigned*)cnt >= target) break;
-    if (*(volatile unsigned*)&ctl[2]) return 2;
+    if (c >= target) break;
+    if (e) return 2;
     if (++spins > limit) { atomicExch(&ctl[2], 1u); return 2; }
-    __nanosleep(32);
+    if (spins > 8) __nanosleep(32);
   }
   __threadfence();
   const unsigned d = *(volatile const unsigned*)done1;

@@ -816,7 +816,7 @@ k_residual(int npw, const double2* __restrict__ b, double2* __restrict__ ax, con
            const int* __restrict__ active, double* __restrict__ partial, unsigned* __restrict__ cnt,
            double* __restrict__ res2, double* __restrict__ bb, double* __restrict__ xx, int ncol,
            const double2* __restrict__ C, int nocc, const double2* __restrict__ cb,
-           const double2* __restrict__ cax) {
+           const double2* __restrict__ cax, int real) {
   __shared__ double2 sc[kMaxOcc];
   const int c = blockIdx.y;
   if (active && !active[c]) return;
@@ -835,7 +835,14 @@ k_residual(int npw, const double2* __restrict__ b, double2* __restrict__ ax, con
     double2 r = ax[i];
     r.x = bv.x - r.x;
     r.y = bv.y - r.y;
-    if (C) {
+    if (C && real) {               // real coefficients (real-in-real-space columns)
+      for (int v = 0; v < nocc; ++v) {
+        const double2 cv = C[(size_t)v * npw + G];
+        const double k = sc[v].x;
+        r.x -= cv.x * k;
+        r.y -= cv.y * k;
+      }
+    } else if (C) {
       for (int v = 0; v < nocc; ++v) {
         const double2 cv = C[(size_t)v * npw + G], k = sc[v];
         r.x -= cv.x * k.x - cv.y * k.y;
@@ -867,11 +874,11 @@ k_residual(int npw, const double2* __restrict__ b, double2* __restrict__ ax, con
 
 void launch_residual(cudaStream_t s, int npw, int ncol, const double2* b, double2* ax, const double2* x,
                      const int* active, Work& w, double* res2, double* bb, double* xx, const double2* C, int nocc,
-                     const double2* cb, const double2* cax) {
+                     const double2* cb, const double2* cax, bool real) {
   dim3 g((npw + kChunk - 1) / kChunk, ncol);
   ++g_launches;
   k_residual<<<g, kLT, 0, s>>>(npw, b, ax, x, active, reinterpret_cast<double*>(w.part2), w.cnt_b, res2, bb,
-                                xx, ncol, C, nocc, cb, cax);
+                                xx, ncol, C, nocc, cb, cax, real ? 1 : 0);
 }
 
 // Deflated components of a Sternheimer pass: coef[d][c] = <D_d|r_c> on entry;

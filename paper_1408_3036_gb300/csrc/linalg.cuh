@@ -111,7 +111,7 @@ void launch_defl_scale(cudaStream_t s, double2* coef, const double* eps, const d
                        const int* active);
 void launch_residual(cudaStream_t s, int npw, int ncol, const double2* b, double2* ax, const double2* x,
                      const int* active, Work& w, double* res2, double* bb, double* xx, const double2* C = nullptr,
-                     int nocc = 0, const double2* cb = nullptr, const double2* cax = nullptr);
+                     int nocc = 0, const double2* cb = nullptr, const double2* cax = nullptr, bool real = false);
 void launch_combine(cudaStream_t s, int npw, int nout, const double2* in, const int* src0, const int* src1,
                     double w_pair, double w_single, double2* out);
 // Eq. model_eq: out[j] = (pinv(T - Em_j) + pinv(T - Ep_j)) in[src_j] on the sphere
