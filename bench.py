@@ -280,7 +280,7 @@ def class_bytes(miller, N, npw, nocc, s):
     return col, shared, dict(D=D, P0=P0)
 
 
-def survey_bytes(N, npw, s):
+def cg_bytes_per_col_iter(N, npw, s):
     """Algorithmic bytes of one Sternheimer iteration of one column (the byte
     model of the measurement plan): s (11 N_PW + 4 N_g), s = bytes per complex
     value -- p in / Hp out in the sphere, one grid round trip for each of the
@@ -427,7 +427,7 @@ def run_gpu(args):
     miller = cell.sphere()
     s = 8 if prec == gw.GW_MIXED else 16
     colb, shared, geo = class_bytes(miller, c.N, cell.npw, c.n_occ, s)
-    b_it = survey_bytes(c.N, cell.npw, s)
+    b_it = cg_bytes_per_col_iter(c.N, cell.npw, s)
     ms_dom, n_dom = prof[dominant]
     hbm, hbm_kind = peaks()
     alg_bytes = it_cols * b_it

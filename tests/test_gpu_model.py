@@ -131,7 +131,7 @@ def test_model_lanczos(tiny):
     assert rel(a, ar) < 1e-10 and rel(b, br) < 1e-10
     assert np.abs(w * Q @ Q.T - np.eye(K)).max() < 1e-12
     # the mixed precision runs the model operator in FP64 (no solve whose
-    # residual could refine FP32 transforms): the benchmark spec's 1e-6 holds
+    # residual could refine FP32 transforms): the mixed path's 1e-6 holds
     a32, b32, _ = c.lanczos(x0, K, 0.0, gw.GW_MIXED)
     assert rel(a32, ar) < 1e-6 and rel(b32, br) < 1e-6
     c.close()
