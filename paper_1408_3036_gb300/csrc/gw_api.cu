@@ -68,6 +68,8 @@ struct gw_ctx {
   int max_iter = 20000, max_outer = 12;
   double stats[6] = {0, 0, 0, 0, 0, 0};
   int* host_pin = nullptr;      // pinned scratch for small read-backs
+  unsigned char* stage = nullptr;  // pinned staging ring for small uploads (no stream sync on copy)
+  size_t stage_off = 0;
   std::string err;
   // optional per-kernel-class timing with CUDA events on the work stream
   unsigned prof_mask = 0;
@@ -129,10 +131,40 @@ gw_status getbuf(gw_ctx* ctx, const std::string& name, size_t count, X** out) {
   return GW_OK;
 }
 
+// Small uploads go through a pinned staging ring: a copy from pageable host
+// memory makes the runtime wait for the stream first, one from pinned memory
+// is queued like a kernel.  A slot is reused only after the stream has passed
+// every copy out of it (the ring wraps with a stream synchronisation).
+constexpr size_t kStageBytes = 1 << 20, kStageMax = 64 << 10;
+
 template <class X>
 gw_status upload(gw_ctx* ctx, const std::string& name, const std::vector<X>& v, X** out) {
   TRY(getbuf(ctx, name, v.size(), out));
-  if (!v.empty()) CK(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, ctx->st));
+  if (v.empty()) return GW_OK;
+  const size_t bytes = v.size() * sizeof(X);
+  if (bytes <= kStageMax) {
+    if (!ctx->stage) {
+      void* p = nullptr;
+      if (cudaMallocHost(&p, kStageBytes) != cudaSuccess) {
+        cudaGetLastError();
+        CK(cudaMemcpyAsync(*out, v.data(), bytes, cudaMemcpyHostToDevice, ctx->st));
+        return GW_OK;
+      }
+      ctx->stage = static_cast<unsigned char*>(p);
+      ctx->stage_off = 0;
+    }
+    const size_t len = (bytes + 255) & ~(size_t)255;
+    if (ctx->stage_off + len > kStageBytes) {
+      CK(cudaStreamSynchronize(ctx->st));        // every earlier copy out of the ring is done
+      ctx->stage_off = 0;
+    }
+    unsigned char* slot = ctx->stage + ctx->stage_off;
+    ctx->stage_off += len;
+    std::memcpy(slot, v.data(), bytes);
+    CK(cudaMemcpyAsync(*out, slot, bytes, cudaMemcpyHostToDevice, ctx->st));
+    return GW_OK;
+  }
+  CK(cudaMemcpyAsync(*out, v.data(), bytes, cudaMemcpyHostToDevice, ctx->st));
   return GW_OK;
 }
 
@@ -3279,6 +3311,7 @@ void gw_destroy(gw_ctx* ctx) {
   for (auto& kv : ctx->bufs)
     if (kv.second.first) cudaFree(kv.second.first);
   if (ctx->host_pin) cudaFreeHost(ctx->host_pin);
+  if (ctx->stage) cudaFreeHost(ctx->stage);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   for (cudaEvent_t e : ctx->tune_ev)
     if (e) cudaEventDestroy(e);
