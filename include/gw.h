@@ -407,11 +407,12 @@ typedef enum {
  * to the same tolerance), and the bound on the device waits of the persistent
  * kernel.
  *   kind        a gw_cg_kernel value
- *   wait_limit  polls (about 64 ns apart) that one CTA of the persistent kernel
- *               makes at one wait for other CTAs before it gives up; the kernel
- *               then returns early on every CTA and the call reports
- *               GW_E_TIMEOUT (the context stays usable).  0 keeps the current
- *               value (default 2^24, about a second); negative is GW_E_ARG.
+ *   wait_limit  polls (each one memory round trip, with a short sleep after
+ *               the first eight) that one CTA of the persistent kernel makes at
+ *               one wait for other CTAs before it gives up; the kernel then
+ *               returns early on every CTA and the call reports GW_E_TIMEOUT
+ *               (the context stays usable).  0 keeps the current value
+ *               (default 2^24, seconds); negative is GW_E_ARG.
  * GW_E_ARG for an unknown kind.
  */
 gw_status gw_set_cg_kernel(gw_ctx* ctx, int kind, long long wait_limit);
