@@ -100,15 +100,16 @@ def lowest_states(cell, n, tol=1e-10, max_iter=400, extra=None, seed=0, verbose=
     return eps, psi, float(res.max())
 
 
-def levels_below(cell, emax, n_start, tol=1e-6, max_states=2048):
+def levels_below(cell, emax, n_start, tol=1e-6, max_states=2048, apply=None, device="cuda"):
     """Eigenvalues of H up to ``emax`` (at least ``n_start`` of them), for
     placing frequencies away from the cell's transitions.  Runs the block
     eigensolver with a growing block until its highest converged eigenvalue
-    passes ``emax``; the eigenvalues are accurate to about ``tol``."""
+    passes ``emax``; the eigenvalues are accurate to about ``tol``.
+    ``apply`` and ``device`` as in ``lowest_states``."""
     n = max(int(n_start), 1)
     while True:
         n = min(n, cell.npw - 1, max_states)
-        eps, _, _ = lowest_states(cell, n, tol=tol, extra=max(8, n // 4))
+        eps, _, _ = lowest_states(cell, n, tol=tol, extra=max(8, n // 4), apply=apply, device=device)
         if eps[-1] > emax or n >= min(cell.npw - 1, max_states):
             return eps[eps <= emax]
         n = 2 * n

@@ -33,3 +33,30 @@ def test_lobpcg_matches_dense():
     P1 = gs.C.T @ gs.C.conj()
     P2 = psi.T @ psi.conj()
     assert np.abs(P1 - P2).max() < 1e-9
+
+
+def test_levels_below_covers_the_window():
+    """Every eigenvalue of H up to the window's top, starting from a block
+    smaller than their number (the block grows), against dense eigenvalues."""
+    from paper_1408_3036_gb300.groundstate import levels_below
+    wl = W.tiny()
+    c = wl.cells[0]
+    sph = pw.Sphere(c.L, c.N, c.ecut)
+    ev = np.linalg.eigvalsh(pw.dense_h(sph, c.vloc))
+
+    class Fake:
+        npw = sph.npw
+        L = c.L
+
+        @staticmethod
+        def sphere():
+            return sph.miller
+
+    def apply(Yt):
+        return torch.tensor(pw.h_apply(sph, c.vloc, Yt.numpy()))
+
+    emax = ev[c.n_occ - 1] + 1.0
+    lev = levels_below(Fake, emax, c.n_occ + 1, tol=1e-8, apply=apply, device="cpu")
+    ref = ev[ev <= emax]
+    assert len(lev) == len(ref) > c.n_occ + 1
+    assert np.abs(lev - ref).max() < 1e-9
