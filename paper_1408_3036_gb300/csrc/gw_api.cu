@@ -58,6 +58,14 @@ struct gw_ctx {
   unsigned long long wait_limit = 1ull << 24;   // spins of one device wait before GW_E_TIMEOUT
   long long pcg_iters = 0;      // iterations run by persistent launches
   int pcg_launch_blocks = 0;
+  int* pcg_pin = nullptr;       // pinned read-back of the last persistent launch: iterations, flags, error
+  size_t pcg_pin_n = 0;
+  struct PcgPending {           // that launch, until the caller's next synchronisation (pcg_finish)
+    bool on = false;
+    int ncol = 0, used = 0, tune_tpb = 0;
+    bool fp64 = false;
+    std::string tune_key;
+  } pcg_pend;
   int pcg_cluster = 0;          // cluster size of the last persistent launch (0: grid-wide kernel)
   int cta_div = 1;              // contexts sharing the GPU concurrently (batch mode)
   int precond = 1;              // 1: kinetic (TPA) preconditioner in the Sternheimer solvers; 0: none
@@ -564,27 +572,55 @@ gw_status cg_solve_persistent(gw_ctx* ctx, int ncol, const double2* b64, const d
   }
   CK(le);
   prof_end(ctx, PC_PCG, pa);
-  std::vector<int> its(ncol), fl(ncol);
-  unsigned herr = 0;
-  CK(cudaMemcpyAsync(its.data(), iters, ncol * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaMemcpyAsync(fl.data(), flags, ncol * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-  if (ctl) CK(cudaMemcpyAsync(&herr, ctl + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->st));
-  TRY(sync(ctx, "cg_persistent"));
-  if (herr) return fail(ctx, GW_E_TIMEOUT, "persistent CG: a bounded device wait gave up");
+  // Iteration counts, flags and the error word come back into pinned memory
+  // and are read at the caller's next synchronisation (pcg_finish): no stream
+  // synchronisation of its own per pass.
+  if (ctx->pcg_pin_n < (size_t)(2 * ncol + 1)) {
+    if (ctx->pcg_pin) CK(cudaFreeHost(ctx->pcg_pin));
+    ctx->pcg_pin = nullptr;
+    ctx->pcg_pin_n = 0;
+    CK(cudaMallocHost(&ctx->pcg_pin, (size_t)(2 * ncol + 1) * sizeof(int)));
+    ctx->pcg_pin_n = (size_t)(2 * ncol + 1);
+  }
+  CK(cudaMemcpyAsync(ctx->pcg_pin, iters, ncol * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(ctx->pcg_pin + ncol, flags, ncol * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  ctx->pcg_pin[2 * ncol] = 0;
+  if (ctl) CK(cudaMemcpyAsync(ctx->pcg_pin + 2 * ncol, ctl + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->st));
+  ctx->pcg_pend.on = true;
+  ctx->pcg_pend.ncol = ncol;
+  ctx->pcg_pend.used = used;
+  ctx->pcg_pend.fp64 = std::is_same<T, double>::value;
+  ctx->pcg_pend.tune_key = tune_key;
+  ctx->pcg_pend.tune_tpb = tune_tpb;
+  (void)it_sum;
+  (void)it_max;
+  return GW_OK;
+}
+
+// The read-back of the last persistent launch, after the stream has been
+// synchronised: a bounded wait that gave up (GW_E_TIMEOUT), an FP64 breakdown,
+// the iteration statistics and the autotuner's sample.
+gw_status pcg_finish(gw_ctx* ctx, long long* it_sum, int* it_max) {
+  if (!ctx->pcg_pend.on) return GW_OK;
+  ctx->pcg_pend.on = false;
+  const int ncol = ctx->pcg_pend.ncol;
+  const int* its = ctx->pcg_pin;
+  const int* fl = ctx->pcg_pin + ncol;
+  if (ctx->pcg_pin[2 * ncol]) return fail(ctx, GW_E_TIMEOUT, "persistent CG: a bounded device wait gave up");
   int imax = 0;
   for (int c = 0; c < ncol; ++c) {
     *it_sum += its[c];
     *it_max = std::max(*it_max, its[c]);
     imax = std::max(imax, its[c]);
-    if (fl[c] == 2 && std::is_same<T, double>::value)
+    if (fl[c] == 2 && ctx->pcg_pend.fp64)
       return fail(ctx, GW_E_BREAKDOWN, "CG breakdown: (H - E) is not positive definite on P_c");
   }
   ctx->pcg_iters += imax;       // iterations of the whole launch (bounded by the slowest column)
-  ctx->pcg_launch_blocks = used;
-  if (tune_tpb && imax > 0) {
+  ctx->pcg_launch_blocks = ctx->pcg_pend.used;
+  if (ctx->pcg_pend.tune_tpb && imax > 0) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ctx->tune_ev[0], ctx->tune_ev[1]) == cudaSuccess)
-      tune_report(tune_key, tune_tpb, (double)ms / imax);
+      tune_report(ctx->pcg_pend.tune_key, ctx->pcg_pend.tune_tpb, (double)ms / imax);
   }
   return GW_OK;
 }
@@ -754,6 +790,7 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
                 const double* tk = nullptr, const double* w2 = nullptr, double w2max = 0.0, int sym_hint = -1) {
   const int npw = ctx->npw;
   const bool mixed = !std::is_same<T, double>::value;
+  ctx->pcg_pend.on = false;
   const double tol = mixed ? ctx->tol_mixed : ctx->tol;
   const double tol_in = mixed ? ctx->tol_inner : std::max(1e2 * ctx->tol, 1e-11);
   double2 *r64, *ax;
@@ -886,6 +923,7 @@ gw_status solve(gw_ctx* ctx, int ncol, const double2* b64, const double2* E, dou
     CK(cudaMemcpyAsync(hb.data(), bb, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaMemcpyAsync(hx.data(), xx, ncol * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     TRY(sync(ctx, "solve"));
+    TRY(pcg_finish(ctx, &it_sum, &it_max));
     if (hprev.empty()) hprev = hb;
     int nact = 0;
     const double anorm = w2 ? ctx->anorm * ctx->anorm + w2max : ctx->anorm;
@@ -3312,6 +3350,7 @@ void gw_destroy(gw_ctx* ctx) {
     if (kv.second.first) cudaFree(kv.second.first);
   if (ctx->host_pin) cudaFreeHost(ctx->host_pin);
   if (ctx->stage) cudaFreeHost(ctx->stage);
+  if (ctx->pcg_pin) cudaFreeHost(ctx->pcg_pin);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   for (cudaEvent_t e : ctx->tune_ev)
     if (e) cudaEventDestroy(e);
